@@ -1,0 +1,169 @@
+"""FP64 CPU oracle for Sparse Approximate Map construction (arXiv 2406.17656).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
+benchmark's CPU-baseline leg may import this module; the product path never
+does, and it shares no code with the CUDA library (neither imports the
+other).  The arithmetic lives in `sam_oracle.c` (plain C, FP64, textbook
+Householder QR); this file compiles it with gcc on first use and marshals
+numpy arrays through ctypes.
+
+Matrices are passed as any object with attributes `n`, `indptr`, `indices`,
+`data` (CSR, 0-based, column indices ascending within a row).
+
+Pins: every function here is checked against something other than itself in
+`tests/test_oracle_pins.py` (paper-printed pattern counts, closed forms,
+brute force on tiny graphs, LAPACK least squares, exact recovery, dense
+residuals).  The adjoint functions are pinned by finite differences.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sam_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+_i32p = ctypes.POINTER(ctypes.c_int)
+_f64p = ctypes.POINTER(ctypes.c_double)
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile sam_oracle.c into a shared library (gcc, -O2, OpenMP)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build_oracle())
+            lib.so_free.argtypes = [ctypes.c_void_p]
+            lib.so_max_threads.restype = ctypes.c_int
+            lib.so_check_csr.argtypes = [ctypes.c_int, _i32p, _i32p]
+            lib.so_pattern.argtypes = [ctypes.c_int, _i32p, _i32p, ctypes.c_int,
+                                       ctypes.POINTER(_i32p), ctypes.POINTER(_i32p)]
+            lib.so_shadow.argtypes = [ctypes.c_int, _i32p, _i32p, _i32p, _i32p,
+                                      ctypes.POINTER(_i32p), ctypes.POINTER(_i32p)]
+            lib.so_build.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p,
+                                     _i32p, _i32p, ctypes.c_int, _f64p, _f64p, _f64p]
+            lib.so_residual.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p,
+                                        _i32p, _i32p, _f64p, _f64p, _f64p]
+            _lib = lib
+    return _lib
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_i32p)
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_f64p)
+
+
+def _take(ptr, count, dtype):
+    lib = _load()
+    out = np.ctypeslib.as_array(ptr, shape=(max(int(count), 1),))[: int(count)].astype(dtype, copy=True)
+    lib.so_free(ctypes.cast(ptr, ctypes.c_void_p))
+    return out
+
+
+def _check(st, what):
+    if st != 0:
+        raise RuntimeError("oracle %s failed with status %d" % (what, st))
+
+
+def max_threads() -> int:
+    return int(_load().so_max_threads())
+
+
+def pattern(A, level: int):
+    """Level-`level` neighbour pattern of every column of G(A) (Sec. 3),
+    as a CSC structure (colptr[n+1], rowidx[nnz]) with ascending rows."""
+    lib = _load()
+    rp, rpp = _i32(A.indptr)
+    ci, cip = _i32(A.indices)
+    cp, ri = _i32p(), _i32p()
+    _check(lib.so_pattern(int(A.n), rpp, cip, int(level), ctypes.byref(cp), ctypes.byref(ri)), "pattern")
+    colptr = _take(cp, A.n + 1, np.int32)
+    rowidx = _take(ri, colptr[-1], np.int32)
+    return colptr, rowidx
+
+
+def shadow(A, colptr, rowidx):
+    """Shadow rows I_j (rows where A(:, J_j) has stored entries), CSC form."""
+    lib = _load()
+    rp, rpp = _i32(A.indptr)
+    ci, cip = _i32(A.indices)
+    jc, jcp = _i32(colptr)
+    jr, jrp = _i32(rowidx)
+    ic, ir = _i32p(), _i32p()
+    _check(lib.so_shadow(int(A.n), rpp, cip, jcp, jrp, ctypes.byref(ic), ctypes.byref(ir)), "shadow")
+    icp = _take(ic, A.n + 1, np.int32)
+    iri = _take(ir, icp[-1], np.int32)
+    return icp, iri
+
+
+def build(Ak, A0, colptr, rowidx, nthreads: int = 0):
+    """SAM build (Eq. (approx_map), column decomposition of Sec. 2) in FP64.
+
+    Returns a dict with `mval` (map values in the pattern's CSC order),
+    `res2[j]` = ||B_j m_j - c_j||^2 and `out2[j]` = squared A_0 entries of
+    column j outside the shadow rows."""
+    lib = _load()
+    n = int(Ak.n)
+    a = [_i32(Ak.indptr), _i32(Ak.indices), _f64(Ak.data), _i32(A0.indptr), _i32(A0.indices), _f64(A0.data)]
+    jc, jcp = _i32(colptr)
+    jr, jrp = _i32(rowidx)
+    mval = np.zeros(int(colptr[-1]), dtype=np.float64)
+    res2 = np.zeros(n, dtype=np.float64)
+    out2 = np.zeros(n, dtype=np.float64)
+    st = lib.so_build(n, a[0][1], a[1][1], a[2][1], a[3][1], a[4][1], a[5][1], jcp, jrp, int(nthreads),
+                      mval.ctypes.data_as(_f64p), res2.ctypes.data_as(_f64p), out2.ctypes.data_as(_f64p))
+    _check(st, "build")
+    return {"mval": mval, "res2": res2, "out2": out2}
+
+
+def to_csr(n, colptr, rowidx, mval):
+    """Map values in CSC order -> CSR arrays (indptr, indices, data) of N_k."""
+    import scipy.sparse as sp
+
+    m = sp.csc_matrix((np.asarray(mval, np.float64), np.asarray(rowidx), np.asarray(colptr)), shape=(n, n)).tocsr()
+    m.sort_indices()
+    return m.indptr.astype(np.int32), m.indices.astype(np.int32), m.data.astype(np.float64)
+
+
+def residual(Ak, colptr, rowidx, mval, A0):
+    """||R_k||_F and ||R_k||_F / ||A_0||_F for R_k = A_k N_k - A_0 (Eq. (res)),
+    evaluated from the definition column by column."""
+    lib = _load()
+    n = int(Ak.n)
+    a = [_i32(Ak.indptr), _i32(Ak.indices), _f64(Ak.data), _i32(colptr), _i32(rowidx), _f64(mval),
+         _i32(A0.indptr), _i32(A0.indices), _f64(A0.data)]
+    fro2, a02 = ctypes.c_double(), ctypes.c_double()
+    st = lib.so_residual(n, *(x[1] for x in a), ctypes.byref(fro2), ctypes.byref(a02))
+    _check(st, "residual")
+    fro = float(np.sqrt(fro2.value))
+    return fro, fro / float(np.sqrt(a02.value))
+
+
+def apply(indptr, indices, data, x):
+    """y = N_k x for N_k in CSR (the preconditioner application, Sec. 1)."""
+    import scipy.sparse as sp
+
+    n = len(indptr) - 1
+    return sp.csr_matrix((data, indices, indptr), shape=(n, n)) @ np.asarray(x, np.float64)

@@ -1,0 +1,434 @@
+/*
+ * sam_oracle.c -- plain, slow, FP64 CPU reference for Sparse Approximate Map
+ * (SAM) construction.  TEST INFRASTRUCTURE ONLY: it is loaded by the tests,
+ * by the package's smoke check and by the benchmark's CPU-baseline leg, never
+ * by the product path.  It shares no code with the CUDA library.
+ *
+ * What it computes (arXiv 2406.17656):
+ *   - Sec. 3: the level-L neighbour pattern of column j in the adjacency
+ *     graph G(A) (edge i->j iff A(i,j) is stored, i != j): all vertices with
+ *     a path of length <= L pointing to j, plus j itself.  Level 1 is the
+ *     column pattern of A with the diagonal, level 2 is paths of length <= 2.
+ *   - Eq. (approx_map), and the column decomposition that follows it in
+ *     Sec. 2: N_k = argmin ||A_k N - A_0||_F over the pattern, solved as n
+ *     independent least-squares problems  min_m ||A_k(I_j, J_j) m - A_0(I_j, j)||
+ *     where J_j is the pattern of column j and I_j the rows in which the
+ *     columns A_k(:, J_j) have stored entries.  Rows outside I_j are zero in
+ *     A_k(:, J_j), so they do not change the minimiser; their A_0 entries
+ *     enter the residual only.
+ *   - Eq. (res): R_k = A_k N_k - A_0 and the relative residual
+ *     ||R_k||_F / ||A_0||_F used in Sec. 5.
+ *
+ * Each least-squares problem is solved with textbook Householder QR
+ * (Golub & Van Loan, Matrix Computations, Sec. 5.1.2 "house" and Sec. 5.2.1
+ * Householder QR), applied to the augmented matrix [B c] so that Q^T c comes
+ * out of the same sweep, followed by back substitution.  Columns are
+ * independent, so an OpenMP loop over them changes no arithmetic.
+ *
+ * Memory: every array that a function returns through an `int **` /
+ * `double **` argument is malloc'ed here and released with so_free().
+ * Return value: 0 on success, 1 on allocation failure, 2 on invalid input,
+ * 3 when a least-squares matrix is rank deficient (an exact zero pivot).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+void so_free(void *p) { free(p); }
+
+int so_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Transpose a CSR matrix: returns the CSR of A^T, i.e. the CSC of A.
+ * Entries of each output row come out in ascending column order because the
+ * input rows are visited in ascending order. */
+static int transpose(int n, const int *rp, const int *ci, const double *v,
+                     int **tp_out, int **ti_out, double **tv_out) {
+    int nnz = rp[n];
+    int *tp = (int *)calloc((size_t)n + 1, sizeof(int));
+    int *ti = (int *)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+    double *tv = v ? (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1)) : NULL;
+    int *fill = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    if (!tp || !ti || (v && !tv) || !fill) {
+        free(tp); free(ti); free(tv); free(fill);
+        return 1;
+    }
+    for (int e = 0; e < nnz; ++e) tp[ci[e] + 1]++;
+    for (int i = 0; i < n; ++i) tp[i + 1] += tp[i];
+    for (int i = 0; i < n; ++i) fill[i] = tp[i];
+    for (int i = 0; i < n; ++i)
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            int p = fill[ci[e]]++;
+            ti[p] = i;
+            if (v) tv[p] = v[e];
+        }
+    free(fill);
+    *tp_out = tp;
+    *ti_out = ti;
+    if (tv_out) *tv_out = tv;
+    return 0;
+}
+
+static int cmp_int(const void *a, const void *b) {
+    int x = *(const int *)a, y = *(const int *)b;
+    return (x > y) - (x < y);
+}
+
+/* Check that a CSR structure is well formed: monotone row pointers, column
+ * indices in range, strictly ascending within each row. */
+int so_check_csr(int n, const int *rp, const int *ci) {
+    if (n < 0 || rp[0] != 0) return 2;
+    for (int i = 0; i < n; ++i) {
+        if (rp[i + 1] < rp[i]) return 2;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            if (ci[e] < 0 || ci[e] >= n) return 2;
+            if (e > rp[i] && ci[e] <= ci[e - 1]) return 2;
+        }
+    }
+    return 0;
+}
+
+/*
+ * Level-L pattern (Sec. 3).  Column j of the result lists, ascending, every
+ * vertex i with a directed path i -> ... -> j of at most L edges in G(A),
+ * and j itself.  Predecessors of vertex l are the rows stored in column l of
+ * A, so the set is grown L times by adding the column patterns of the
+ * vertices reached so far (a breadth-first search backwards from j).
+ * Output: CSC structure colptr[n+1], rowidx[nnz].
+ */
+int so_pattern(int n, const int *rp, const int *ci, int level, int **colptr_out, int **rowidx_out) {
+    if (level < 0 || so_check_csr(n, rp, ci)) return 2;
+    int *cp, *cr;
+    if (transpose(n, rp, ci, NULL, &cp, &cr, NULL)) return 1;
+    char *mark = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int *set = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int *colptr = (int *)calloc((size_t)n + 1, sizeof(int));
+    size_t cap = (size_t)rp[n] + (size_t)n + 16, used = 0;
+    int *rowidx = (int *)malloc(sizeof(int) * cap);
+    if (!mark || !set || !colptr || !rowidx) {
+        free(cp); free(cr); free(mark); free(set); free(colptr); free(rowidx);
+        return 1;
+    }
+    for (int j = 0; j < n; ++j) {
+        int cnt = 0, frontier_begin = 0;
+        set[cnt++] = j;
+        mark[j] = 1;
+        for (int lev = 0; lev < level; ++lev) {
+            int frontier_end = cnt;
+            for (int t = frontier_begin; t < frontier_end; ++t) {
+                int l = set[t];
+                for (int e = cp[l]; e < cp[l + 1]; ++e) {
+                    int i = cr[e];
+                    if (!mark[i]) {
+                        mark[i] = 1;
+                        set[cnt++] = i;
+                    }
+                }
+            }
+            frontier_begin = frontier_end;
+        }
+        qsort(set, (size_t)cnt, sizeof(int), cmp_int);
+        if (used + (size_t)cnt > cap) {
+            while (used + (size_t)cnt > cap) cap *= 2;
+            int *tmp = (int *)realloc(rowidx, sizeof(int) * cap);
+            if (!tmp) {
+                free(cp); free(cr); free(mark); free(set); free(colptr); free(rowidx);
+                return 1;
+            }
+            rowidx = tmp;
+        }
+        for (int t = 0; t < cnt; ++t) {
+            rowidx[used++] = set[t];
+            mark[set[t]] = 0;
+        }
+        colptr[j + 1] = (int)used;
+    }
+    free(cp); free(cr); free(mark); free(set);
+    *colptr_out = colptr;
+    *rowidx_out = rowidx;
+    return 0;
+}
+
+/*
+ * Shadow rows: I_j = union over c in J_j of the rows stored in column c of
+ * A, ascending.  These are the only rows in which A(:, J_j) is nonzero.
+ */
+int so_shadow(int n, const int *rp, const int *ci, const int *jcp, const int *jri,
+              int **icp_out, int **iri_out) {
+    if (so_check_csr(n, rp, ci)) return 2;
+    int *cp, *cr;
+    if (transpose(n, rp, ci, NULL, &cp, &cr, NULL)) return 1;
+    char *mark = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int *set = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int *icp = (int *)calloc((size_t)n + 1, sizeof(int));
+    size_t cap = 4 * (size_t)rp[n] + 16, used = 0;
+    int *iri = (int *)malloc(sizeof(int) * cap);
+    if (!mark || !set || !icp || !iri) {
+        free(cp); free(cr); free(mark); free(set); free(icp); free(iri);
+        return 1;
+    }
+    for (int j = 0; j < n; ++j) {
+        int cnt = 0;
+        for (int t = jcp[j]; t < jcp[j + 1]; ++t) {
+            int c = jri[t];
+            for (int e = cp[c]; e < cp[c + 1]; ++e)
+                if (!mark[cr[e]]) {
+                    mark[cr[e]] = 1;
+                    set[cnt++] = cr[e];
+                }
+        }
+        qsort(set, (size_t)cnt, sizeof(int), cmp_int);
+        if (used + (size_t)cnt > cap) {
+            while (used + (size_t)cnt > cap) cap *= 2;
+            int *tmp = (int *)realloc(iri, sizeof(int) * cap);
+            if (!tmp) {
+                free(cp); free(cr); free(mark); free(set); free(icp); free(iri);
+                return 1;
+            }
+            iri = tmp;
+        }
+        for (int t = 0; t < cnt; ++t) {
+            iri[used++] = set[t];
+            mark[set[t]] = 0;
+        }
+        icp[j + 1] = (int)used;
+    }
+    free(cp); free(cr); free(mark); free(set);
+    *icp_out = icp;
+    *iri_out = iri;
+    return 0;
+}
+
+/* position of key in the ascending array a[0..len), or -1 */
+static int find_sorted(const int *a, int len, int key) {
+    int lo = 0, hi = len - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) / 2;
+        if (a[mid] == key) return mid;
+        if (a[mid] < key) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+/*
+ * Householder QR of the m-by-(n+1) column-major matrix X = [B c] (leading
+ * dimension m), m >= n, in place: on return the upper triangle of the first
+ * n columns holds R and column n holds Q^T c.  For each k the reflector
+ * P = I - beta v v^T with v(k) = 1 maps X(k:m, k) to mu e_1, mu = its norm
+ * (Golub & Van Loan's "house", which avoids cancellation by choosing v(k)
+ * = -sigma / (x_k + mu) when x_k > 0).  Returns 3 if a pivot is exactly 0.
+ */
+static int householder_qr(int m, int n, double *X, double *v) {
+    for (int k = 0; k < n; ++k) {
+        double *xk = X + (size_t)k * m;
+        double sigma = 0.0;
+        for (int i = k + 1; i < m; ++i) sigma += xk[i] * xk[i];
+        double x1 = xk[k];
+        double beta, mu;
+        v[k] = 1.0;
+        for (int i = k + 1; i < m; ++i) v[i] = xk[i];
+        if (sigma == 0.0) {
+            /* already triangular in this column: no reflection needed */
+            beta = 0.0;
+            mu = x1;
+        } else {
+            mu = sqrt(x1 * x1 + sigma);
+            double v1 = (x1 <= 0.0) ? x1 - mu : -sigma / (x1 + mu);
+            beta = 2.0 * v1 * v1 / (sigma + v1 * v1);
+            for (int i = k + 1; i < m; ++i) v[i] /= v1;
+        }
+        if (mu == 0.0) return 3;
+        /* apply P to columns k+1..n (the last one is the right-hand side) */
+        for (int c = k + 1; c <= n; ++c) {
+            double *xc = X + (size_t)c * m;
+            double w = 0.0;
+            for (int i = k; i < m; ++i) w += v[i] * xc[i];
+            w *= beta;
+            for (int i = k; i < m; ++i) xc[i] -= w * v[i];
+        }
+        xk[k] = mu;
+        for (int i = k + 1; i < m; ++i) xk[i] = 0.0;
+    }
+    return 0;
+}
+
+/*
+ * SAM build (Eq. (approx_map) and the column decomposition of Sec. 2).
+ * Inputs: A_k and A_0 in CSR, the pattern J in CSC (jcp, jri; every column
+ * must be nonempty).  Outputs (caller-allocated):
+ *   mval[nnz(J)]  values of N_k in the pattern's CSC order (column j's values
+ *                 at jcp[j]..jcp[j+1]-1, matching rows jri[...]),
+ *   res2[n]       ||A_k(I_j,J_j) m_j - A_0(I_j,j)||^2, evaluated from the
+ *                 original (unfactored) FP64 entries,
+ *   out2[n]       sum of A_0(i,j)^2 over stored rows i outside I_j.
+ * So ||R_k||_F^2 = sum_j (res2[j] + out2[j]).
+ */
+int so_build(int n, const int *krp, const int *kci, const double *kv,
+             const int *zrp, const int *zci, const double *zv,
+             const int *jcp, const int *jri, int nthreads,
+             double *mval, double *res2, double *out2) {
+    if (so_check_csr(n, krp, kci) || so_check_csr(n, zrp, zci)) return 2;
+    for (int j = 0; j < n; ++j)
+        if (jcp[j + 1] <= jcp[j]) return 2;
+    int *kcp, *kcr, *zcp, *zcr;
+    double *kcv, *zcv;
+    if (transpose(n, krp, kci, kv, &kcp, &kcr, &kcv)) return 1;
+    if (transpose(n, zrp, zci, zv, &zcp, &zcr, &zcv)) {
+        free(kcp); free(kcr); free(kcv);
+        return 1;
+    }
+    /* shadow rows of every column */
+    int *icp, *iri;
+    int st = so_shadow(n, krp, kci, jcp, jri, &icp, &iri);
+    if (st) {
+        free(kcp); free(kcr); free(kcv); free(zcp); free(zcr); free(zcv);
+        return st;
+    }
+    int maxm = 1, maxn = 1;
+    for (int j = 0; j < n; ++j) {
+        if (icp[j + 1] - icp[j] > maxm) maxm = icp[j + 1] - icp[j];
+        if (jcp[j + 1] - jcp[j] > maxn) maxn = jcp[j + 1] - jcp[j];
+    }
+    int status = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel
+    {
+        double *X = (double *)malloc(sizeof(double) * (size_t)maxm * (size_t)(maxn + 1));
+        double *B = (double *)malloc(sizeof(double) * (size_t)maxm * (size_t)maxn);
+        double *v = (double *)malloc(sizeof(double) * (size_t)maxm);
+        double *m = (double *)malloc(sizeof(double) * (size_t)maxn);
+        if (!X || !B || !v || !m) {
+#pragma omp atomic write
+            status = 1;
+        } else {
+#pragma omp for schedule(dynamic, 64)
+            for (int j = 0; j < n; ++j) {
+                const int *I = iri + icp[j];
+                const int *J = jri + jcp[j];
+                int mi = icp[j + 1] - icp[j], nj = jcp[j + 1] - jcp[j];
+                if (mi < nj) {
+#pragma omp atomic write
+                    status = 3;
+                    continue;
+                }
+                /* B = A_k(I, J), column major */
+                memset(B, 0, sizeof(double) * (size_t)mi * (size_t)nj);
+                for (int c = 0; c < nj; ++c) {
+                    int col = J[c];
+                    for (int e = kcp[col]; e < kcp[col + 1]; ++e) {
+                        int p = find_sorted(I, mi, kcr[e]);
+                        B[(size_t)c * mi + p] = kcv[e];
+                    }
+                }
+                memcpy(X, B, sizeof(double) * (size_t)mi * (size_t)nj);
+                /* right-hand side A_0(I, j); entries of A_0(:, j) outside I */
+                double *rhs = X + (size_t)nj * mi;
+                memset(rhs, 0, sizeof(double) * (size_t)mi);
+                double o2 = 0.0;
+                for (int e = zcp[j]; e < zcp[j + 1]; ++e) {
+                    int p = find_sorted(I, mi, zcr[e]);
+                    if (p >= 0) rhs[p] = zcv[e];
+                    else o2 += zcv[e] * zcv[e];
+                }
+                if (householder_qr(mi, nj, X, v)) {
+#pragma omp atomic write
+                    status = 3;
+                    continue;
+                }
+                /* back substitution R m = (Q^T c)(1:nj) */
+                for (int r = nj - 1; r >= 0; --r) {
+                    double s = rhs[r];
+                    for (int c = r + 1; c < nj; ++c) s -= X[(size_t)c * mi + r] * m[c];
+                    m[r] = s / X[(size_t)r * mi + r];
+                }
+                /* residual from the original entries: c - B m */
+                double r2 = 0.0;
+                for (int i = 0; i < mi; ++i) {
+                    double ri = 0.0;
+                    for (int e = zcp[j]; e < zcp[j + 1]; ++e)
+                        if (zcr[e] == I[i]) ri = zcv[e];
+                    for (int c = 0; c < nj; ++c) ri -= B[(size_t)c * mi + i] * m[c];
+                    r2 += ri * ri;
+                }
+                for (int c = 0; c < nj; ++c) mval[jcp[j] + c] = m[c];
+                res2[j] = r2;
+                out2[j] = o2;
+            }
+        }
+        free(X); free(B); free(v); free(m);
+    }
+    free(kcp); free(kcr); free(kcv); free(zcp); free(zcr); free(zcv);
+    free(icp); free(iri);
+    return status;
+}
+
+/*
+ * Residual of Eq. (res) straight from its definition, one column at a time:
+ * R(:, j) = sum_c A_k(:, c) N(c, j) - A_0(:, j) accumulated in a dense
+ * length-n vector.  N is given in CSC (ncp, nri, nv).  Returns
+ * fro2 = ||R||_F^2 and a02 = ||A_0||_F^2.
+ */
+int so_residual(int n, const int *krp, const int *kci, const double *kv,
+                const int *ncp, const int *nri, const double *nv,
+                const int *zrp, const int *zci, const double *zv,
+                double *fro2, double *a02) {
+    if (so_check_csr(n, krp, kci) || so_check_csr(n, zrp, zci)) return 2;
+    int *kcp, *kcr, *zcp, *zcr;
+    double *kcv, *zcv;
+    if (transpose(n, krp, kci, kv, &kcp, &kcr, &kcv)) return 1;
+    if (transpose(n, zrp, zci, zv, &zcp, &zcr, &zcv)) {
+        free(kcp); free(kcr); free(kcv);
+        return 1;
+    }
+    /* dense accumulator plus the list of rows it touched in this column */
+    double *w = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    char *hit = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int *rows = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    if (!w || !hit || !rows) {
+        free(w); free(hit); free(rows);
+        free(kcp); free(kcr); free(kcv); free(zcp); free(zcr); free(zcv);
+        return 1;
+    }
+    double total = 0.0, a0 = 0.0;
+    for (int j = 0; j < n; ++j) {
+        int nt = 0;
+        for (int t = ncp[j]; t < ncp[j + 1]; ++t) {
+            int c = nri[t];
+            for (int e = kcp[c]; e < kcp[c + 1]; ++e) {
+                int i = kcr[e];
+                if (!hit[i]) { hit[i] = 1; rows[nt++] = i; }
+                w[i] += kcv[e] * nv[t];
+            }
+        }
+        for (int e = zcp[j]; e < zcp[j + 1]; ++e) {
+            int i = zcr[e];
+            if (!hit[i]) { hit[i] = 1; rows[nt++] = i; }
+            w[i] -= zcv[e];
+            a0 += zcv[e] * zcv[e];
+        }
+        for (int t = 0; t < nt; ++t) {
+            int i = rows[t];
+            total += w[i] * w[i];
+            w[i] = 0.0;
+            hit[i] = 0;
+        }
+    }
+    free(hit); free(rows);
+    free(w);
+    free(kcp); free(kcr); free(kcv); free(zcp); free(zcr); free(zcv);
+    *fro2 = total;
+    *a02 = a0;
+    return 0;
+}
