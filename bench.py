@@ -1,0 +1,452 @@
+"""Benchmark: batched SAM construction on the 256x256 Q1 diffusion sequence.
+
+Workload (one "step" = the whole hot path once): the sequence of 10
+variable-coefficient diffusion matrices (9-point Q1 stencil, n = 65536,
+kappa_k = kappa_0 exp(0.05 k GRF_k)), level-2 patterns of every A_k, and the
+10 maps M_k = argmin ||A_k M - A_0||_F built in one batched pass: CSR->CSC,
+patterns, shadow rows and size bins, gather + FP32 Householder QR + FP64
+refinement, scatter into CSR, FP64 residual ||A_k M_k - A_0||_F per map.
+Metric: map columns per second (10 x 65536 columns per step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank builds its own
+copy of the sequence (weak scaling, no data-path collective); time is the
+maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+METRIC = "SAM columns/s (batched FP32+refine vs FP64, same GB300, <=1e-10 rel err); % roofline"
+UNIT = "columns/s"
+# size classes of the least-squares kernels: |I| <= maxi, |J| <= maxj, nnz(B) <= 8 maxi
+BIN_MAXI = [14, 26, 40, 52, 64]
+BIN_MAXJ = [5, 9, 23, 27, 27]
+# nominal ALU peaks of a GB300 at its maximum SM clock (2070 MHz), 152 SMs:
+# FP32: 128 lanes x 2 flops per SM per clock; FP64: 1.25 TFLOP/s nominal
+# (= 2 FMA per SM per clock)
+SM_COUNT, SM_MHZ = 152, 2070.0
+PEAK_FP32 = SM_COUNT * 128 * 2 * SM_MHZ * 1e6
+PEAK_FP64 = SM_COUNT * 2 * 2 * SM_MHZ * 1e6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=256)
+    ap.add_argument("--maps", type=int, default=10)
+    ap.add_argument("--level", type=int, default=2)
+    ap.add_argument("--refine", type=int, default=1)
+    ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------- accounting
+
+
+def column_sizes(mats, level):
+    """|I_j|, |J_j|, nnz(B_j) of every column from the matrix structures
+    (pattern = level-L reachability, shadow = rows reached by A(:, J_j))."""
+    import scipy.sparse as sp
+
+    out = []
+    for a in mats:
+        s = a.to_scipy().copy()
+        s.data[:] = 1.0
+        s = s.tocsc()
+        st = (s + sp.eye(a.n, format="csc")).astype(bool).astype(np.float64)
+        pat = sp.eye(a.n, format="csc")
+        for _ in range(level):
+            pat = (st @ pat).astype(bool).astype(np.float64)
+        J = np.diff(pat.indptr)
+        I = np.diff((s @ pat).astype(bool).tocsc().indptr)
+        colcnt = np.diff(s.indptr).astype(np.float64)
+        nB = np.asarray(pat.T @ colcnt).ravel()
+        out.append((I.astype(np.int64), J.astype(np.int64), nB.astype(np.int64)))
+    return out
+
+
+def bin_of(I, J, nB):
+    b = np.full(I.shape, -1)
+    for q in range(len(BIN_MAXI) - 1, -1, -1):
+        ok = (I <= BIN_MAXI[q]) & (J <= BIN_MAXJ[q]) & (nB <= 8 * BIN_MAXI[q]) & (I >= J)
+        b[ok] = q
+    return b
+
+
+def algorithmic_flops(I, J, nB, precision, steps):
+    m, n = I.astype(np.float64), J.astype(np.float64)
+    qr = 2 * n * n * (m - n / 3) + (4 * m * n - 2 * n * n) + n * n
+    final_res = 2 * nB + 2 * m
+    if precision == "fp64":
+        return 0.0 * qr, qr + final_res
+    f32 = qr + steps * 2 * n * n
+    f64 = steps * 4 * nB + final_res
+    return f32, f64
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index, self.proc, self.path = index, None, None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.path = "/tmp/sam_clocks_%d.csv" % os.getpid()
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                               f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- reference
+
+
+def run_reference(args, rank):
+    """The FP64 CPU oracle as the reference arm (rank 0 only)."""
+    import oracle
+    from paper_2406_17656_gb300 import workloads as W
+
+    if rank != 0:
+        return
+    seq = W.config2(nx=args.nx, nmat=args.maps, level=args.level)
+    a0 = seq.mats[0]
+    cores = oracle.max_threads()
+    times = []
+
+    def step(k):
+        ak = seq.mats[k % len(seq.mats)]
+        t = time.perf_counter()
+        cp, ri = oracle.pattern(ak, args.level)
+        oracle.build(ak, a0, cp, ri, nthreads=cores)
+        return time.perf_counter() - t
+
+    for w in range(args.warmup):
+        step(w)
+    for s in range(args.steps):
+        times.append(step(s))
+    per = float(np.mean(times))
+    value = a0.n / per
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": seq.name + "_seq%d_level%d" % (args.maps, args.level), "n": a0.n,
+                       "maps": args.maps, "level": args.level},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "each step: one map (all %d columns) of the sequence, pattern + build" % a0.n},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(seq, level, budget_s=12.0):
+    """Times the FP64 oracle (as it stands) on whole maps until the budget."""
+    import oracle
+
+    cores = oracle.max_threads()
+    a0 = seq.mats[0]
+    cols, t_tot, maps = 0, 0.0, 0
+    for ak in seq.mats:
+        t = time.perf_counter()
+        cp, ri = oracle.pattern(ak, level)
+        oracle.build(ak, a0, cp, ri, nthreads=cores)
+        t_tot += time.perf_counter() - t
+        cols += ak.n
+        maps += 1
+        if t_tot >= budget_s:
+            break
+    return {"value": cols / t_tot, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of %d maps, all columns, pattern + build, %d OpenMP threads, %.1f s" % (
+                maps, len(seq.mats), cores, t_tot)}, seq.mats[:maps]
+
+
+# ------------------------------------------------------------------- ours
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+
+    from paper_2406_17656_gb300 import build as _build
+    from paper_2406_17656_gb300 import sam
+    from paper_2406_17656_gb300 import workloads as W
+
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    sam.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    seq = W.config2(nx=args.nx, nmat=args.maps, level=args.level)
+    a0h = seq.mats[0]
+    n, K = a0h.n, len(seq.mats)
+    stream = torch.cuda.current_stream()
+    h = sam.Handle(stream=stream)
+    aks = [sam.Csr.from_host(m, dev) for m in seq.mats]
+    a0 = sam.Csr.from_host(a0h, dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def make_outputs(level):
+        pats = h.sam_pattern_build_batched(aks, level)
+        offs = np.zeros(K + 1, np.int64)
+        offs[1:] = np.cumsum([p.nnz for p in pats])
+        out = (torch.empty(K * (n + 1), dtype=torch.int32, device=dev),
+               torch.empty(int(offs[-1]), dtype=torch.int32, device=dev),
+               torch.empty(int(offs[-1]), dtype=torch.float64, device=dev))
+        for p in pats:
+            p.destroy()
+        return offs, out
+
+    def step(level, precision, steps, offs, out):
+        pats = h.sam_pattern_build_batched(aks, level)
+        res = h.sam_build_batched(aks, a0, pats, precision, steps, M_row_ptr=out[0], M_col_idx=out[1],
+                                  M_val=out[2], want_fro=True, offsets=offs)
+        for p in pats:
+            p.destroy()
+        return res[4]
+
+    def timed(level, precision, steps, nsteps, nwarm, profile=False):
+        offs, out = make_outputs(level)
+        for _ in range(nwarm):
+            step(level, precision, steps, offs, out)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        if profile:
+            h.sam_profile(True)
+        ms = 0.0
+        fro = None
+        for _ in range(nsteps):
+            flush.zero_()  # evict L2 between steps (outside the timed interval)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fro = step(level, precision, steps, offs, out)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        prof = h.sam_profile_read() if profile else None
+        if profile:
+            h.sam_profile(False)
+        ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.barrier()
+            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        return float(ms_t.item()) / nsteps, fro, prof, (offs, out)
+
+    # ---- headline: FP32 QR + FP64 refinement, level 2
+    with ClockSampler(local) as clk:
+        ms, fro, prof, (offs, out) = timed(args.level, "fp32r", args.refine, args.steps, args.warmup, profile=True)
+    clocks = clk.summary()
+    cols_per_step = K * n
+    value = cols_per_step * world / (ms * 1e-3)
+    launches_total, lsq_ms, lsq_n = prof
+    gpu_launches = int(launches_total)
+
+    extra = {}
+    # accuracy: FP32+refine against the FP64 GPU build (all columns) and the oracle (a sample, below)
+    v32 = out[2].clone()
+    if not args.quick:
+        ms64, fro64, _, (offs64, out64) = timed(args.level, "fp64", 0, max(2, args.steps // 3), 1)
+        extra["fp64_columns_per_s"] = cols_per_step * world / (ms64 * 1e-3)
+        extra["fp64_ms_per_step"] = ms64
+        extra["speedup_fp32r_vs_fp64"] = value / extra["fp64_columns_per_s"]
+        errs = []
+        for k in range(K):
+            a, b = v32[offs[k]:offs[k + 1]], out64[2][offs64[k]:offs64[k + 1]]
+            errs.append(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)))
+        extra["max_rel_fro_vs_fp64_gpu"] = max(errs)
+        ms1, _, _, _ = timed(1, "fp32r", args.refine, max(2, args.steps // 2), 1)
+        extra["level1_columns_per_s"] = cols_per_step * world / (ms1 * 1e-3)
+        extra["rel_residual_per_map"] = [float(f) / float(np.linalg.norm(a0h.data)) for f in fro]
+
+    # ---- roofline of the dominant kernel (largest least-squares size class)
+    sizes = column_sizes(seq.mats, args.level)
+    dom = int(np.argmax(lsq_ms))
+    f32 = f64 = 0.0
+    for (I, J, nB) in sizes:
+        sel = bin_of(I, J, nB) == dom
+        a, b = algorithmic_flops(I[sel], J[sel], nB[sel], "fp32r", args.refine)
+        f32 += float(np.sum(a))
+        f64 += float(np.sum(b))
+    t_launch = lsq_ms[dom] / max(lsq_n[dom], 1) * 1e-3
+    nsteps_prof = args.steps
+    f32_l, f64_l = f32, f64  # per launch: one launch per size class covers all maps of a step
+    t_roof = max(f32_l / PEAK_FP32, f64_l / PEAK_FP64)
+    fp32_frac = f32_l / t_launch / PEAK_FP32
+    fp64_frac = f64_l / t_launch / PEAK_FP64
+    if f32_l / PEAK_FP32 >= f64_l / PEAK_FP64:
+        ach, peak = f32_l / t_launch, PEAK_FP32
+    else:
+        ach, peak = f64_l / t_launch, PEAK_FP64
+    traffic = None
+    tf = os.path.join(HERE, "profiles", "traffic.json")
+    if os.path.exists(tf):
+        try:
+            import hashlib
+
+            rec = json.load(open(tf))
+            src = open(os.path.join(HERE, "paper_2406_17656_gb300", "csrc", "lsq.cu"), "rb").read()
+            if rec.get("lsq_sha256") == hashlib.sha256(src).hexdigest() and str(dom) in rec.get("bytes_per_launch", {}):
+                traffic = rec["bytes_per_launch"][str(dom)]
+        except Exception:
+            traffic = None
+    roofline = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": t_roof / t_launch, "traffic": traffic,
+                "kernel": "lsq_kernel size class %d (|I|<=%d, |J|<=%d)" % (dom, BIN_MAXI[dom], BIN_MAXJ[dom]),
+                "launch_ms": t_launch * 1e3, "fp32_flops_per_launch": f32_l, "fp64_flops_per_launch": f64_l,
+                "fp32_frac": fp32_frac, "fp64_frac": fp64_frac,
+                "peak_source": "nominal: 152 SMs x 2070 MHz; FP32 128 lanes x 2, FP64 1.25 TFLOP/s (2 FMA/SM/clk)"}
+    if not args.quick:
+        p32, p64 = h.sam_peak_flops(100.0)
+        roofline["probe_fp32_tflops"] = p32 / 1e12
+        roofline["probe_fp64_tflops"] = p64 / 1e12
+
+    # ---- end to end through the C ABI with host buffers
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    hk = [sam.Csr(pin(m.indptr), pin(m.indices), pin(m.data), n=n) for m in seq.mats]
+    h0 = sam.Csr(pin(a0h.indptr), pin(a0h.indices), pin(a0h.data), n=n)
+    hout = (torch.empty(K * (n + 1), dtype=torch.int32).pin_memory(),
+            torch.empty(int(offs[-1]), dtype=torch.int32).pin_memory(),
+            torch.empty(int(offs[-1]), dtype=torch.float64).pin_memory())
+    h2d = sum(m.indptr.nbytes + m.indices.nbytes for m in seq.mats)  # pattern build
+    h2d += sum(m.indptr.nbytes + m.indices.nbytes + m.data.nbytes for m in seq.mats)
+    h2d += a0h.indptr.nbytes + a0h.indices.nbytes + a0h.data.nbytes
+    d2h = sum(int(t.numel() * t.element_size()) for t in hout) + 8 * K
+
+    def e2e_step():
+        pats = h.sam_pattern_build_batched(hk, args.level)
+        h.sam_build_batched(hk, h0, pats, "fp32r", args.refine, M_row_ptr=hout[0], M_col_idx=hout[1],
+                            M_val=hout[2], want_fro=True, offsets=offs)
+        for p in pats:
+            p.destroy()
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    ne = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(ne):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ne
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = cols_per_step * world / float(e2e_t.item())
+
+    # ---- CPU oracle baseline and sampled parity (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu, timed_maps = cpu_baseline(seq, args.level)
+        if not args.quick:
+            import oracle
+
+            k = len(timed_maps) - 1
+            ak = seq.mats[k]
+            cp, ri = oracle.pattern(ak, args.level)
+            rng = np.random.default_rng(0)
+            cols = np.sort(rng.choice(n, 2000, replace=False)).astype(np.int32)
+            ref = oracle.build_cols(ak, a0h, cp, ri, cols)
+            import scipy.sparse as sp
+
+            m = sp.csr_matrix((v32[offs[k]:offs[k + 1]].cpu().numpy(), out[1][offs[k]:offs[k + 1]].cpu().numpy(),
+                               out[0][k * (n + 1):(k + 1) * (n + 1)].cpu().numpy()), shape=(n, n)).tocsc()
+            m.sort_indices()
+            idx = np.concatenate([np.arange(cp[j], cp[j + 1]) for j in cols])
+            extra["sample_rel_fro_vs_oracle"] = float(np.linalg.norm(m.data[idx] - ref["mval"][idx]) /
+                                                      np.linalg.norm(ref["mval"][idx]))
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": seq.name + "_seq%d_level%d" % (K, args.level), "n": n, "maps": K,
+                           "level": args.level, "precision": "fp32 Householder QR + %d FP64 CSNE step(s)" % args.refine,
+                           "columns_per_step": cols_per_step, "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "flushed between steps (256 MiB write outside the timed interval)"},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks, "cpu_baseline": cpu}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * sam.h -- C ABI of libsam, a GB300 (sm_103a) library that builds Sparse
+ * Approximate Maps (SAMs) as defined in arXiv 2406.17656, "Optimization of
+ * Approximate Maps for Linear Systems Arising in Discretized PDEs".
+ *
+ * Given a sequence of sparse matrices A_0, A_1, ..., the SAM of A_k is
+ * (Sec. 2, Eq. (approx_map))
+ *
+ *     N_k = argmin_N || A_k N - A_0 ||_F   over N with sparsity pattern S,
+ *
+ * which splits into one small least-squares problem per column j:
+ * min_m || A_k(I_j, J_j) m - A_0(I_j, j) ||, with J_j the pattern of column
+ * j and I_j the "shadow" rows, the rows in which A_k(:, J_j) has stored
+ * entries.  The patterns used here are the level-L neighbourhoods of the
+ * adjacency graph G(A_k) (Sec. 3): level 1 is S(A_k) plus the diagonal,
+ * level 2 adds every vertex with a path of length <= 2 to j (the pattern of
+ * (A_k + I)^2).  The map is returned in CSR and is called M_k below
+ * (the paper's N_k).
+ *
+ * Conventions common to every call
+ *  - Indices are 0-based int32; a matrix is square, n <= 2^31-1 rows, at
+ *    most 2^31-1 stored entries.  CSR rows list column indices in strictly
+ *    ascending order.  Values are IEEE double.
+ *  - Pointers in `sam_csr` and the vector/array arguments may point to
+ *    device memory (cudaMalloc, managed) or to host memory (pinned or
+ *    pageable); the library checks each pointer with
+ *    cudaPointerGetAttributes and stages host arrays through its own device
+ *    workspace, copying host outputs back before the call returns.  With
+ *    device pointers every call is asynchronous on the handle's stream.
+ *  - All memory passed in is owned by the caller and never freed by the
+ *    library.  Objects returned through `sam_handle*` / `sam_pattern*` are
+ *    owned by the library and released with the matching destroy call.
+ *  - No call aborts, traps or throws.  Each returns a sam_status.  Errors
+ *    detected on the device (a rank-deficient or non-finite column, an
+ *    unsupported column size) are recorded in a sticky status word that
+ *    sam_sync() returns; calls that return host scalars synchronise and
+ *    report it themselves.
+ */
+#ifndef SAM_H
+#define SAM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t sam_status;
+
+enum {
+    SAM_OK = 0,
+    SAM_ERR_INVALID_ARG = 1,    /* null pointer, bad size, level, precision, ... */
+    SAM_ERR_BAD_CSR = 2,        /* row pointers not monotone, index out of range, unsorted/duplicate */
+    SAM_ERR_RANK_DEFICIENT = 3, /* a column's least-squares matrix has a zero pivot */
+    SAM_ERR_NONFINITE = 4,      /* NaN/Inf met in a column's solve */
+    SAM_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+    SAM_ERR_OOM = 6,            /* device allocation failed */
+    SAM_ERR_TIMEOUT = 7,        /* a host-side wait ran out */
+    SAM_ERR_UNSUPPORTED = 8     /* a column exceeds the kernels' size limits (see sam_limits) */
+};
+
+/* precision of the per-column least-squares solves */
+enum {
+    SAM_FP64 = 0,        /* Householder QR, triangular solves and residuals in FP64 */
+    SAM_FP32_REFINE = 1  /* Householder QR in FP32, then `refine_steps` corrected
+                            semi-normal-equation steps with FP64 residuals */
+};
+
+/* flag bits for sam_set_flags */
+enum {
+    SAM_FLAG_TRUSTED = 1 /* skip CSR validation of inputs */
+};
+
+/* A square sparse matrix in CSR form. */
+typedef struct {
+    int32_t n;              /* rows = columns */
+    int64_t nnz;            /* stored entries = row_ptr[n] */
+    const int32_t *row_ptr; /* [n+1] */
+    const int32_t *col_idx; /* [nnz], ascending within each row */
+    const double *val;      /* [nnz]; may be NULL for structure-only calls */
+} sam_csr;
+
+typedef struct sam_handle_t *sam_handle;   /* stream, device workspace, sticky status */
+typedef struct sam_pattern_t *sam_pattern; /* a map sparsity pattern S (device resident) */
+
+/* Largest column sizes the least-squares kernels accept:
+ * |J_j| <= *max_cols and |I_j| <= *max_rows. */
+void sam_limits(int32_t *max_rows, int32_t *max_cols);
+
+/* Human-readable text of a status code (static storage). */
+const char *sam_status_string(sam_status s);
+
+/* Create a handle bound to the current CUDA device and the given stream
+ * (a cudaStream_t, NULL for the legacy default stream). */
+sam_status sam_create(sam_handle *h, void *cuda_stream);
+sam_status sam_destroy(sam_handle h);
+sam_status sam_set_stream(sam_handle h, void *cuda_stream);
+sam_status sam_set_flags(sam_handle h, uint32_t flags);
+/* Wait for the handle's stream and return (then clear) the sticky status. */
+sam_status sam_sync(sam_handle h);
+
+/*
+ * sam_pattern_build -- level-`level` neighbour pattern of every column of
+ * G(A_k) (Sec. 3): column j holds, ascending, every vertex i with a directed
+ * path i -> ... -> j of at most `level` edges (edge i -> j iff A_k(i, j) is
+ * stored, i != j) and j itself.  level 0 is the diagonal, 1 is S(A_k) plus
+ * the diagonal, 2 the pattern of (A_k + I)^2, 3 of (A_k + I)^3.
+ * Only the structure of A_k is read (A_k->val may be NULL).  The pattern is
+ * stored on the device in CSC form (= the CSC structure of the map) together
+ * with the CSR structure of the map.  Synchronises once (to size the
+ * output).  *out is library-owned: release with sam_pattern_destroy.
+ */
+sam_status sam_pattern_build(sam_handle h, const sam_csr *A_k, int level, sam_pattern *out);
+
+/* The same for K matrices at once, with a single synchronisation. */
+sam_status sam_pattern_build_batched(sam_handle h, int K, const sam_csr *A_k, int level, sam_pattern *out);
+
+/* Wrap a caller-chosen pattern given in CSC (colptr[n+1], rowidx[nnz], rows
+ * ascending within a column, every column nonempty); the arrays are copied.
+ * Lets a map use e.g. the target's pattern S(A_0), the choice the paper
+ * compares against (Sec. 5). */
+sam_status sam_pattern_from_csc(sam_handle h, int32_t n, int64_t nnz, const int32_t *colptr,
+                                const int32_t *rowidx, sam_pattern *out);
+
+/* Device views of a pattern: n, nnz, CSC colptr[n+1] and rowidx[nnz] of the
+ * map's pattern, valid until sam_pattern_destroy.  Any output may be NULL. */
+sam_status sam_pattern_get(sam_pattern S, int32_t *n, int64_t *nnz, const int32_t **colptr,
+                           const int32_t **rowidx);
+sam_status sam_pattern_destroy(sam_pattern S);
+
+/*
+ * sam_build -- the SAM M_k = argmin ||A_k M - A_0||_F on the pattern S
+ * (Eq. (approx_map), column decomposition of Sec. 2), one least-squares
+ * problem per column, written as CSR:
+ *   M_row_ptr[n+1], M_col_idx[nnz(S)], M_val[nnz(S)] (caller-allocated,
+ *   nnz from sam_pattern_get).  Column indices ascend within each row.
+ * precision: SAM_FP64 or SAM_FP32_REFINE; refine_steps (0..4) is used by
+ * SAM_FP32_REFINE only.  col_status (nullable, int32[n]) receives 0 or a
+ * sam_status per column.  res2 (nullable, double[n]) receives per column
+ * ||A_k(I_j,J_j) m_j - A_0(I_j,j)||^2 + sum of A_0(i,j)^2 over rows i
+ * outside I_j, so that ||R_k||_F^2 = sum_j res2[j] (Eq. (res)).
+ * A_k must have the structure the pattern's shadow rows are taken from
+ * (any A_k works: shadows are computed here from A_k and S).
+ */
+sam_status sam_build(sam_handle h, const sam_csr *A_k, const sam_csr *A_0, sam_pattern S, int precision,
+                     int refine_steps, int32_t *M_row_ptr, int32_t *M_col_idx, double *M_val,
+                     int32_t *col_status, double *res2);
+
+/*
+ * sam_build_batched -- K maps M_k for the sources A_k[0..K-1] against the
+ * one target A_0, in one pass: all maps' columns are binned by size and each
+ * size class runs as a single persistent launch over every map.
+ * M_offsets[K+1] (host, int64) gives each map's offset into M_col_idx /
+ * M_val; map k's row pointers go to M_row_ptr + k*(n+1) (relative to its own
+ * offset).  col_status and res2 (nullable) are laid out as [K][n].
+ * fro (nullable, host double[K]) receives ||A_k M_k - A_0||_F per map and
+ * forces a synchronisation.
+ */
+sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0,
+                             const sam_pattern *S, int precision, int refine_steps,
+                             const int64_t *M_offsets, int32_t *M_row_ptr, int32_t *M_col_idx,
+                             double *M_val, int32_t *col_status, double *res2, double *fro);
+
+/*
+ * sam_residual -- ||R_k||_F and ||R_k||_F / ||A_0||_F for R_k = A_k M_k - A_0
+ * (Eq. (res); the relative form is the metric of Sec. 5), computed in FP64
+ * column by column with a deterministic reduction.  fro and rel are host
+ * pointers (either may be NULL); the call synchronises.
+ */
+sam_status sam_residual(sam_handle h, const sam_csr *A_k, const sam_csr *M_k, const sam_csr *A_0,
+                        double *fro, double *rel);
+
+/*
+ * sam_apply -- y = M_k x (FP64 CSR product).  Used as the preconditioner
+ * update of Sec. 1/2: since A_k M_k ~ A_0, A_k (M_k P_0) ~ A_0 P_0 ~ I for a
+ * preconditioner P_0 of A_0, so the right preconditioner applied to v is
+ * M_k (P_0 v): apply P_0 first, then this call.  x and y must not overlap.
+ */
+sam_status sam_apply(sam_handle h, const sam_csr *M_k, const double *x, double *y);
+
+/*
+ * sam_build_backward -- adjoint of sam_build on a fixed pattern.  Given
+ * dM_val = dL/dM_k (CSR order of the map, nnz(S) values), returns
+ * dA_k_val = dL/dA_k and dA_0_val = dL/dA_0 on the stored entries of A_k
+ * and A_0 (CSR order).  Per column, with B = A_k(I_j, J_j), c = A_0(I_j, j),
+ * m = B^+ c, r = c - B m and g = dL/dm:  lambda = (B^T B)^{-1} g,
+ * dL/dc = B lambda, dL/dB = r lambda^T - (B lambda) m^T; entries of dL/dB at
+ * positions not stored in A_k are dropped, and the per-column contributions
+ * are summed deterministically.  M_val must be the map built from the same
+ * A_k, A_0 and S.  precision as in sam_build (the QR is recomputed).
+ */
+sam_status sam_build_backward(sam_handle h, const sam_csr *A_k, const sam_csr *A_0, sam_pattern S,
+                              int precision, int refine_steps, const double *M_val,
+                              const double *dM_val, double *dA_k_val, double *dA_0_val);
+
+/*
+ * sam_tune -- time the least-squares kernels' launch shapes on the columns of
+ * the given problems and keep the fastest per size class in the handle (and
+ * in the text file cache_path when it is not NULL).  Optional: the defaults
+ * are used until it is called.
+ */
+sam_status sam_tune(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0, const sam_pattern *S,
+                    int precision, int refine_steps, const char *cache_path);
+
+/*
+ * sam_profile -- tracing.  enable != 0 starts timing every least-squares
+ * launch (one per size class and build call) with CUDA events recorded on
+ * the handle's stream; any call resets the counters.
+ * sam_profile_read -- launches: kernels this handle launched since the last
+ * reset; lsq_ms[5] / lsq_launches[5] (nullable): accumulated event time and
+ * launch count of the least-squares kernel of each size class.  Synchronises.
+ */
+sam_status sam_profile(sam_handle h, int enable);
+sam_status sam_profile_read(sam_handle h, int64_t *launches, double *lsq_ms, int64_t *lsq_launches);
+
+/*
+ * sam_peak_flops -- measured FP32 and FP64 FMA throughput of this GPU in
+ * FLOP/s (2 flops per FMA), from dependent-chain FMA kernels filling every
+ * SM for about `ms` milliseconds each.  Used as roofline denominators.
+ */
+sam_status sam_peak_flops(sam_handle h, double ms, double *fp32_flops, double *fp64_flops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAM_H */

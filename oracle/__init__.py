@@ -59,6 +59,8 @@ def _load():
                                       ctypes.POINTER(_i32p), ctypes.POINTER(_i32p)]
             lib.so_build.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p,
                                      _i32p, _i32p, ctypes.c_int, _f64p, _f64p, _f64p]
+            lib.so_build_cols.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p,
+                                          _i32p, _i32p, ctypes.c_int, _i32p, ctypes.c_int, _f64p, _f64p, _f64p]
             lib.so_residual.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p,
                                         _i32p, _i32p, _f64p, _f64p, _f64p]
             _lib = lib
@@ -135,6 +137,25 @@ def build(Ak, A0, colptr, rowidx, nthreads: int = 0):
     st = lib.so_build(n, a[0][1], a[1][1], a[2][1], a[3][1], a[4][1], a[5][1], jcp, jrp, int(nthreads),
                       mval.ctypes.data_as(_f64p), res2.ctypes.data_as(_f64p), out2.ctypes.data_as(_f64p))
     _check(st, "build")
+    return {"mval": mval, "res2": res2, "out2": out2}
+
+
+def build_cols(Ak, A0, colptr, rowidx, cols, nthreads: int = 0):
+    """`build` for the listed columns only (a sample of a large problem).
+    Returns mval (entries of other columns are NaN), res2, out2."""
+    lib = _load()
+    n = int(Ak.n)
+    a = [_i32(Ak.indptr), _i32(Ak.indices), _f64(Ak.data), _i32(A0.indptr), _i32(A0.indices), _f64(A0.data)]
+    jc, jcp = _i32(colptr)
+    jr, jrp = _i32(rowidx)
+    cl, clp = _i32(cols)
+    mval = np.full(int(colptr[-1]), np.nan, dtype=np.float64)
+    res2 = np.full(n, np.nan, dtype=np.float64)
+    out2 = np.full(n, np.nan, dtype=np.float64)
+    st = lib.so_build_cols(n, a[0][1], a[1][1], a[2][1], a[3][1], a[4][1], a[5][1], jcp, jrp, int(nthreads),
+                           clp, int(len(cl)), mval.ctypes.data_as(_f64p), res2.ctypes.data_as(_f64p),
+                           out2.ctypes.data_as(_f64p))
+    _check(st, "build_cols")
     return {"mval": mval, "res2": res2, "out2": out2}
 
 

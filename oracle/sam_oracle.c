@@ -271,13 +271,16 @@ static int householder_qr(int m, int n, double *X, double *v) {
  *   out2[n]       sum of A_0(i,j)^2 over stored rows i outside I_j.
  * So ||R_k||_F^2 = sum_j (res2[j] + out2[j]).
  */
-int so_build(int n, const int *krp, const int *kci, const double *kv,
-             const int *zrp, const int *zci, const double *zv,
-             const int *jcp, const int *jri, int nthreads,
-             double *mval, double *res2, double *out2) {
+static int build_impl(int n, const int *krp, const int *kci, const double *kv,
+                      const int *zrp, const int *zci, const double *zv,
+                      const int *jcp, const int *jri, int nthreads,
+                      const int *cols, int ncols,
+                      double *mval, double *res2, double *out2) {
     if (so_check_csr(n, krp, kci) || so_check_csr(n, zrp, zci)) return 2;
     for (int j = 0; j < n; ++j)
         if (jcp[j + 1] <= jcp[j]) return 2;
+    for (int t = 0; cols && t < ncols; ++t)
+        if (cols[t] < 0 || cols[t] >= n) return 2;
     int *kcp, *kcr, *zcp, *zcr;
     double *kcv, *zcv;
     if (transpose(n, krp, kci, kv, &kcp, &kcr, &kcv)) return 1;
@@ -314,7 +317,8 @@ int so_build(int n, const int *krp, const int *kci, const double *kv,
             status = 1;
         } else {
 #pragma omp for schedule(dynamic, 64)
-            for (int j = 0; j < n; ++j) {
+            for (int t = 0; t < ncols; ++t) {
+                const int j = cols ? cols[t] : t;
                 const int *I = iri + icp[j];
                 const int *J = jri + jcp[j];
                 int mi = icp[j + 1] - icp[j], nj = jcp[j + 1] - jcp[j];
@@ -372,6 +376,23 @@ int so_build(int n, const int *krp, const int *kci, const double *kv,
     free(kcp); free(kcr); free(kcv); free(zcp); free(zcr); free(zcv);
     free(icp); free(iri);
     return status;
+}
+
+int so_build(int n, const int *krp, const int *kci, const double *kv,
+             const int *zrp, const int *zci, const double *zv,
+             const int *jcp, const int *jri, int nthreads,
+             double *mval, double *res2, double *out2) {
+    return build_impl(n, krp, kci, kv, zrp, zci, zv, jcp, jri, nthreads, NULL, n, mval, res2, out2);
+}
+
+/* The same for the listed columns only (cols[0..ncols)); the outputs of
+ * other columns are left untouched.  Used to check sampled columns of large
+ * problems. */
+int so_build_cols(int n, const int *krp, const int *kci, const double *kv,
+                  const int *zrp, const int *zci, const double *zv,
+                  const int *jcp, const int *jri, int nthreads, const int *cols, int ncols,
+                  double *mval, double *res2, double *out2) {
+    return build_impl(n, krp, kci, kv, zrp, zci, zv, jcp, jri, nthreads, cols, ncols, mval, res2, out2);
 }
 
 /*

@@ -1,0 +1,262 @@
+// misc.cu -- deterministic FP64 reductions, the residual of Eq. (res) for an
+// arbitrary map, the map application y = M x, the status reduction and the
+// FMA-throughput probes used as roofline denominators.
+#include <climits>
+
+#include "common.cuh"
+
+namespace sam {
+namespace {
+
+constexpr int kSumBlocks = 256;
+constexpr int kSumThreads = 256;
+
+// Fixed grid and fixed per-thread strides: the summation order does not
+// depend on scheduling, so results are bit-reproducible.
+__global__ void __launch_bounds__(kSumThreads) sum_partial_kernel(const double *x, int64_t n, bool squares,
+                                                                  double *part) {
+    __shared__ double sh[kSumThreads];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kSumThreads + threadIdx.x; i < n; i += (int64_t)kSumBlocks * kSumThreads) {
+        double v = x[i];
+        s += squares ? v * v : v;
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kSumThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(kSumBlocks) sum_final_kernel(const double *part, double *out) {
+    __shared__ double sh[kSumBlocks];
+    sh[threadIdx.x] = part[threadIdx.x];
+    __syncthreads();
+    for (int o = kSumBlocks / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+// y = M x, one warp per row, fixed shuffle tree
+__global__ void spmv_kernel(int n, const int32_t *rp, const int32_t *ci, const double *v, const double *x,
+                            double *y) {
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (w >= n) return;
+    double s = 0.0;
+    for (int e = rp[w] + lane; e < rp[w + 1]; e += 32) s = fma(v[e], x[ci[e]], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[w] = s;
+}
+
+// Row i of R = A_k M - A_0: products A_k(i, c) M(c, :) and -A_0(i, :) are
+// gathered as (column, value) pairs, sorted by column with a fixed bitonic
+// network, summed per column and squared.
+constexpr int kResWarps = 2;
+constexpr int kResBuf = 1024;
+
+__global__ void __launch_bounds__(kResWarps * 32) residual_rows_kernel(
+    int n, const int32_t *krp, const int32_t *kci, const double *kv, const int32_t *mrp, const int32_t *mci,
+    const double *mv, const int32_t *zrp, const int32_t *zci, const double *zv, double *row_r2, int32_t *flag) {
+    __shared__ int keys[kResWarps][kResBuf];
+    __shared__ double vals[kResWarps][kResBuf];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *K = keys[warp];
+    double *V = vals[warp];
+    for (int64_t i = (int64_t)blockIdx.x * kResWarps + warp; i < n; i += (int64_t)gridDim.x * kResWarps) {
+        // count candidates
+        int cnt = zrp[i + 1] - zrp[i];
+        int tot = 0;
+        for (int base = krp[i]; base < krp[i + 1]; base += 32) {
+            int e = base + lane;
+            int len = (e < krp[i + 1]) ? mrp[kci[e] + 1] - mrp[kci[e]] : 0;
+            for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(0xffffffffu, len, o);
+            tot += len;
+        }
+        cnt += tot;
+        if (cnt > kResBuf) {
+            if (lane == 0) {
+                row_r2[i] = 0.0;
+                atomicCAS(flag, 0, SAM_ERR_UNSUPPORTED);
+            }
+            continue;
+        }
+        // fill: target entries first, then products (fixed order)
+        int off = 0;
+        int zb = zrp[i], ze = zrp[i + 1];
+        for (int t = zb + lane; t < ze; t += 32) {
+            K[t - zb] = zci[t];
+            V[t - zb] = -zv[t];
+        }
+        off = ze - zb;
+        for (int e = krp[i]; e < krp[i + 1]; ++e) {
+            int c = kci[e];
+            double a = kv[e];
+            int mb = mrp[c], me = mrp[c + 1];
+            for (int t = mb + lane; t < me; t += 32) {
+                K[off + t - mb] = mci[t];
+                V[off + t - mb] = a * mv[t];
+            }
+            off += me - mb;
+        }
+        __syncwarp();
+        int p2 = 32;
+        while (p2 < cnt) p2 <<= 1;
+        for (int t = cnt + lane; t < p2; t += 32) {
+            K[t] = INT_MAX;
+            V[t] = 0.0;
+        }
+        __syncwarp();
+        for (int k = 2; k <= p2; k <<= 1)
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int t = lane; t < p2; t += 32) {
+                    int u = t ^ jj;
+                    if (u > t) {
+                        bool up = (t & k) == 0;
+                        int a = K[t], b = K[u];
+                        if ((a > b) == up) {
+                            K[t] = b;
+                            K[u] = a;
+                            double va = V[t];
+                            V[t] = V[u];
+                            V[u] = va;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        // segmented sums: the lane holding the first entry of a column sums it
+        double r2 = 0.0;
+        for (int t = lane; t < cnt; t += 32) {
+            if (t == 0 || K[t - 1] != K[t]) {
+                double s = 0.0;
+                for (int q = t; q < cnt && K[q] == K[t]; ++q) s += V[q];
+                r2 = fma(s, s, r2);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+        if (lane == 0) row_r2[i] = r2;
+        __syncwarp();
+    }
+}
+
+__global__ void status_max_kernel(const int32_t *st, int64_t n, int32_t *flag) {
+    int m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, st[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m != 0) atomicMax(flag, m);
+}
+
+// ------------------------------------------------------- throughput probes
+
+constexpr int kChains = 8;
+
+template <typename T>
+__global__ void fma_probe_kernel(int iters, T seed, T *sink) {
+    T x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = seed + T(threadIdx.x + c);
+    const T m = T(0.999999), a = T(1e-7);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], m, a);
+    }
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+    if (s == T(-1.2345)) sink[threadIdx.x] = s;  // never true; keeps the chains live
+}
+
+template <typename T>
+double probe(sam_handle h, double ms, int blocks, int threads) {
+    cudaStream_t st = handle_stream(h);
+    T *sink = (T *)pool_alloc(h, sizeof(T) * 1024);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int iters = 64;
+    double flops = 0.0;
+    for (int rep = 0; rep < 8; ++rep) {
+        cudaEventRecord(e0, st);
+        fma_probe_kernel<T><<<blocks, threads, 0, st>>>(iters, T(1), sink);
+        count_launch(h);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        flops = 2.0 * kChains * 16.0 * (double)iters * blocks * threads / (t * 1e-3);
+        if (t >= 0.8 * ms) break;
+        double scale = ms / (t > 1e-3 ? t : 1e-3);
+        if (scale > 64) scale = 64;
+        iters = (int)(iters * scale) + 1;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pool_free(h, sink);
+    return flops;
+}
+
+}  // namespace
+
+cudaError_t sum_f64(sam_handle h, const double *x, int64_t n, double *out_dev, bool squares) {
+    cudaStream_t st = handle_stream(h);
+    double *part = (double *)pool_alloc(h, sizeof(double) * kSumBlocks);
+    if (!part) return cudaErrorMemoryAllocation;
+    sum_partial_kernel<<<kSumBlocks, kSumThreads, 0, st>>>(x, n, squares, part);
+    count_launch(h);
+    sum_final_kernel<<<1, kSumBlocks, 0, st>>>(part, out_dev);
+    count_launch(h);
+    pool_free(h, part);
+    return cudaGetLastError();
+}
+
+cudaError_t csr_spmv(sam_handle h, int n, const int32_t *rp, const int32_t *ci, const double *v, const double *x,
+                     double *y) {
+    if (n == 0) return cudaSuccess;
+    int64_t threads = (int64_t)n * 32;
+    spmv_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, handle_stream(h)>>>(n, rp, ci, v, x, y);
+    count_launch(h);
+    return cudaGetLastError();
+}
+
+cudaError_t residual_rows(sam_handle h, int n, const int32_t *krp, const int32_t *kci, const double *kv,
+                          const int32_t *mrp, const int32_t *mci, const double *mv, const int32_t *zrp,
+                          const int32_t *zci, const double *zv, double *row_r2, int32_t *flag) {
+    if (n == 0) return cudaSuccess;
+    int blocks = (n + kResWarps - 1) / kResWarps;
+    int cap = handle_sms(h) * 32;
+    if (blocks > cap) blocks = cap;
+    residual_rows_kernel<<<blocks, kResWarps * 32, 0, handle_stream(h)>>>(n, krp, kci, kv, mrp, mci, mv, zrp, zci,
+                                                                          zv, row_r2, flag);
+    count_launch(h);
+    return cudaGetLastError();
+}
+
+cudaError_t status_reduce(sam_handle h, const int32_t *colstat, int64_t n, int32_t *flag) {
+    if (n == 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    status_max_kernel<<<(unsigned)blocks, 256, 0, handle_stream(h)>>>(colstat, n, flag);
+    count_launch(h);
+    return cudaGetLastError();
+}
+
+cudaError_t peak_fma(sam_handle h, double ms, double *f32, double *f64) {
+    int blocks = handle_sms(h) * 8, threads = 256;
+    probe<float>(h, ms * 0.25, blocks, threads);  // warm-up / clock ramp
+    if (f32) *f32 = probe<float>(h, ms, blocks, threads);
+    if (f64) *f64 = probe<double>(h, ms, blocks, threads);
+    return cudaGetLastError();
+}
+
+}  // namespace sam

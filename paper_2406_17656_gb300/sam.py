@@ -1,0 +1,374 @@
+"""Python binding of libsam (include/sam.h): argument marshalling only.
+
+Every step of the SAM pipeline runs in the CUDA library; this module turns
+torch tensors / numpy arrays into the plain pointers and sizes of the C ABI
+and raises `SamError` on a non-zero status.  There is no CPU fallback: if
+libsam.so is missing or no GPU is present, calls fail loudly.
+
+Functions keep the C names (`sam_pattern_build`, `sam_build`,
+`sam_build_batched`, `sam_residual`, `sam_apply`, `sam_build_backward`, ...)
+as methods of `Handle`, which owns a `sam_handle` bound to a CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SAM_OK = 0
+SAM_ERR_INVALID_ARG = 1
+SAM_ERR_BAD_CSR = 2
+SAM_ERR_RANK_DEFICIENT = 3
+SAM_ERR_NONFINITE = 4
+SAM_ERR_CUDA = 5
+SAM_ERR_OOM = 6
+SAM_ERR_TIMEOUT = 7
+SAM_ERR_UNSUPPORTED = 8
+SAM_FP64 = 0
+SAM_FP32_REFINE = 1
+SAM_FLAG_TRUSTED = 1
+
+PRECISIONS = {"fp64": SAM_FP64, "fp32r": SAM_FP32_REFINE}
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+class sam_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("row_ptr", _vp), ("col_idx", _vp), ("val", _vp)]
+
+
+class SamError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = int(status)
+        super().__init__("%s failed: %s (status %d)" % (what, status_string(status), status))
+
+
+_lib = None
+_lock = threading.Lock()
+
+# (name, restype, argtypes)
+_SIGS = [
+    ("sam_limits", None, [_i32p, _i32p]),
+    ("sam_status_string", ctypes.c_char_p, [ctypes.c_int32]),
+    ("sam_create", ctypes.c_int32, [ctypes.POINTER(_vp), _vp]),
+    ("sam_destroy", ctypes.c_int32, [_vp]),
+    ("sam_set_stream", ctypes.c_int32, [_vp, _vp]),
+    ("sam_set_flags", ctypes.c_int32, [_vp, ctypes.c_uint32]),
+    ("sam_sync", ctypes.c_int32, [_vp]),
+    ("sam_pattern_build", ctypes.c_int32, [_vp, ctypes.POINTER(sam_csr), ctypes.c_int, ctypes.POINTER(_vp)]),
+    ("sam_pattern_build_batched", ctypes.c_int32,
+     [_vp, ctypes.c_int, ctypes.POINTER(sam_csr), ctypes.c_int, ctypes.POINTER(_vp)]),
+    ("sam_pattern_from_csc", ctypes.c_int32, [_vp, ctypes.c_int32, ctypes.c_int64, _vp, _vp, ctypes.POINTER(_vp)]),
+    ("sam_pattern_get", ctypes.c_int32, [_vp, _i32p, _i64p, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+    ("sam_pattern_destroy", ctypes.c_int32, [_vp]),
+    ("sam_build", ctypes.c_int32,
+     [_vp, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
+      _vp]),
+    ("sam_build_batched", ctypes.c_int32,
+     [_vp, ctypes.c_int, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(_vp), ctypes.c_int,
+      ctypes.c_int, _i64p, _vp, _vp, _vp, _vp, _vp, _f64p]),
+    ("sam_residual", ctypes.c_int32,
+     [_vp, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), _f64p, _f64p]),
+    ("sam_apply", ctypes.c_int32, [_vp, ctypes.POINTER(sam_csr), _vp, _vp]),
+    ("sam_build_backward", ctypes.c_int32,
+     [_vp, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]),
+    ("sam_tune", ctypes.c_int32,
+     [_vp, ctypes.c_int, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(_vp), ctypes.c_int,
+      ctypes.c_int, ctypes.c_char_p]),
+    ("sam_profile", ctypes.c_int32, [_vp, ctypes.c_int]),
+    ("sam_profile_read", ctypes.c_int32, [_vp, _i64p, ctypes.POINTER(ctypes.c_double), _i64p]),
+    ("sam_peak_flops", ctypes.c_int32, [_vp, ctypes.c_double, _f64p, _f64p]),
+]
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = False):
+    """Load libsam.so (building it first if asked and it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB_PATH
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise RuntimeError("libsam.so is not built (%s); run paper_2406_17656_gb300.build.build()" % path)
+                _build.build()
+            lib = ctypes.CDLL(path)
+            for name, res, args in _SIGS:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return [s[0] for s in _SIGS]
+
+
+def status_string(s: int) -> str:
+    try:
+        return load().sam_status_string(int(s)).decode()
+    except Exception:  # library not loadable: still give a message
+        return "status %d" % s
+
+
+def limits() -> tuple[int, int]:
+    r, c = ctypes.c_int32(), ctypes.c_int32()
+    load().sam_limits(ctypes.byref(r), ctypes.byref(c))
+    return r.value, c.value
+
+
+def _check(st: int, what: str):
+    if st != SAM_OK:
+        raise SamError(st, what)
+
+
+def _addr(x) -> int:
+    """Raw address of a torch tensor or numpy array (contiguity required)."""
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return int(x.ctypes.data)
+    raise TypeError("expected a torch tensor or numpy array, got %r" % type(x))
+
+
+class Csr:
+    """A CSR matrix given by three arrays (torch tensors on any device, or
+    numpy arrays): indptr int32[n+1], indices int32[nnz], data float64[nnz]."""
+
+    def __init__(self, indptr, indices, data=None, n: int | None = None):
+        self.indptr, self.indices, self.data = indptr, indices, data
+        self.n = int(n if n is not None else len(indptr) - 1)
+        self.nnz = int(indices.shape[0])
+        for a, dt in ((indptr, "int32"), (indices, "int32")):
+            if str(a.dtype).split(".")[-1] != dt:
+                raise TypeError("CSR index arrays must be int32")
+        if data is not None and str(data.dtype).split(".")[-1] != "float64":
+            raise TypeError("CSR values must be float64")
+
+    def c(self) -> sam_csr:
+        return sam_csr(self.n, self.nnz, _addr(self.indptr), _addr(self.indices), _addr(self.data))
+
+    @staticmethod
+    def from_host(m, device="cuda") -> "Csr":
+        """Copy an object with n/indptr/indices/data numpy arrays to torch tensors on `device`."""
+        import torch
+
+        return Csr(torch.from_numpy(np.ascontiguousarray(m.indptr, np.int32)).to(device),
+                   torch.from_numpy(np.ascontiguousarray(m.indices, np.int32)).to(device),
+                   torch.from_numpy(np.ascontiguousarray(m.data, np.float64)).to(device), n=m.n)
+
+
+class _CudaView:
+    """Exposes a library-owned device array through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, count: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (ptr, False), "version": 3}
+
+
+class Pattern:
+    """A map sparsity pattern owned by libsam (CSC: colptr[n+1], rowidx[nnz])."""
+
+    def __init__(self, handle: "Handle", ptr: int):
+        self.handle, self.ptr = handle, ptr
+        n, nnz, cp, ri = ctypes.c_int32(), ctypes.c_int64(), _vp(), _vp()
+        _check(load().sam_pattern_get(ptr, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(cp), ctypes.byref(ri)),
+               "sam_pattern_get")
+        self.n, self.nnz = n.value, nnz.value
+        self._cp, self._ri = cp.value, ri.value
+
+    def colptr(self):
+        import torch
+
+        return torch.as_tensor(_CudaView(self._cp, self.n + 1, "<i4"), device="cuda")
+
+    def rowidx(self):
+        import torch
+
+        return torch.as_tensor(_CudaView(self._ri, self.nnz, "<i4"), device="cuda")
+
+    def destroy(self):
+        if self.ptr:
+            load().sam_pattern_destroy(self.ptr)
+            self.ptr = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Handle:
+    """A sam_handle bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, stream=None, trusted: bool = False):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libsam needs a CUDA GPU")
+        lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = _vp()
+        _check(lib.sam_create(ctypes.byref(h), _vp(int(stream.cuda_stream))), "sam_create")
+        self.ptr = h.value
+        if trusted:
+            _check(lib.sam_set_flags(self.ptr, SAM_FLAG_TRUSTED), "sam_set_flags")
+
+    def close(self):
+        if getattr(self, "ptr", 0):
+            load().sam_destroy(self.ptr)
+            self.ptr = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sam_sync(self):
+        _check(load().sam_sync(self.ptr), "sam_sync")
+
+    def sam_set_flags(self, flags: int):
+        _check(load().sam_set_flags(self.ptr, int(flags)), "sam_set_flags")
+
+    # -------------------------------------------------------------- patterns
+    def sam_pattern_build(self, A: Csr, level: int) -> Pattern:
+        out = _vp()
+        c = A.c()
+        _check(load().sam_pattern_build(self.ptr, ctypes.byref(c), int(level), ctypes.byref(out)), "sam_pattern_build")
+        return Pattern(self, out.value)
+
+    def sam_pattern_build_batched(self, As: list, level: int) -> list:
+        K = len(As)
+        arr = (sam_csr * K)(*[a.c() for a in As])
+        outs = (_vp * K)()
+        _check(load().sam_pattern_build_batched(self.ptr, K, arr, int(level), outs), "sam_pattern_build_batched")
+        return [Pattern(self, outs[k]) for k in range(K)]
+
+    def sam_pattern_from_csc(self, n: int, colptr, rowidx) -> Pattern:
+        out = _vp()
+        _check(load().sam_pattern_from_csc(self.ptr, int(n), int(rowidx.shape[0]), _addr(colptr), _addr(rowidx),
+                                           ctypes.byref(out)), "sam_pattern_from_csc")
+        return Pattern(self, out.value)
+
+    # ----------------------------------------------------------------- build
+    def sam_build(self, A_k: Csr, A_0: Csr, S: Pattern, precision="fp32r", refine_steps: int = 1,
+                  out=None, col_status=None, res2=None):
+        """Build the map on pattern S; `out` = (indptr, indices, data) arrays
+        (allocated on the device if None).  Returns `out`."""
+        import torch
+
+        prec = PRECISIONS.get(precision, precision)
+        if out is None:
+            dev = A_k.indptr.device if hasattr(A_k.indptr, "device") else "cuda"
+            out = (torch.empty(A_k.n + 1, dtype=torch.int32, device=dev),
+                   torch.empty(S.nnz, dtype=torch.int32, device=dev),
+                   torch.empty(S.nnz, dtype=torch.float64, device=dev))
+        a, z = A_k.c(), A_0.c()
+        _check(load().sam_build(self.ptr, ctypes.byref(a), ctypes.byref(z), S.ptr, int(prec), int(refine_steps),
+                                _addr(out[0]), _addr(out[1]), _addr(out[2]), _addr(col_status), _addr(res2)),
+               "sam_build")
+        return out
+
+    def sam_build_batched(self, A_ks: list, A_0: Csr, Ss: list, precision="fp32r", refine_steps: int = 1,
+                          M_row_ptr=None, M_col_idx=None, M_val=None, col_status=None, res2=None,
+                          want_fro: bool = False, offsets=None):
+        """K maps in one pass.  Output arrays are allocated on the device when
+        None.  Returns (offsets, M_row_ptr[K*(n+1)], M_col_idx, M_val, fro)."""
+        import torch
+
+        K = len(A_ks)
+        prec = PRECISIONS.get(precision, precision)
+        n = A_0.n
+        if offsets is None:
+            offsets = np.zeros(K + 1, dtype=np.int64)
+            offsets[1:] = np.cumsum([s.nnz for s in Ss])
+        tot = int(offsets[-1])
+        if M_row_ptr is None:
+            M_row_ptr = torch.empty(K * (n + 1), dtype=torch.int32, device="cuda")
+        if M_col_idx is None:
+            M_col_idx = torch.empty(tot, dtype=torch.int32, device="cuda")
+        if M_val is None:
+            M_val = torch.empty(tot, dtype=torch.float64, device="cuda")
+        arr = (sam_csr * K)(*[a.c() for a in A_ks])
+        z = A_0.c()
+        pats = (_vp * K)(*[s.ptr for s in Ss])
+        fro = np.zeros(K, dtype=np.float64) if want_fro else None
+        _check(load().sam_build_batched(
+            self.ptr, K, arr, ctypes.byref(z), pats, int(prec), int(refine_steps),
+            offsets.ctypes.data_as(_i64p), _addr(M_row_ptr), _addr(M_col_idx), _addr(M_val), _addr(col_status),
+            _addr(res2), fro.ctypes.data_as(_f64p) if fro is not None else None), "sam_build_batched")
+        return offsets, M_row_ptr, M_col_idx, M_val, fro
+
+    # -------------------------------------------------------------- residual
+    def sam_residual(self, A_k: Csr, M_k: Csr, A_0: Csr):
+        fro, rel = ctypes.c_double(), ctypes.c_double()
+        a, m, z = A_k.c(), M_k.c(), A_0.c()
+        _check(load().sam_residual(self.ptr, ctypes.byref(a), ctypes.byref(m), ctypes.byref(z), ctypes.byref(fro),
+                                   ctypes.byref(rel)), "sam_residual")
+        return fro.value, rel.value
+
+    def sam_apply(self, M_k: Csr, x, y=None):
+        import torch
+
+        if y is None:
+            y = torch.empty_like(x) if hasattr(x, "data_ptr") else np.empty_like(x)
+        m = M_k.c()
+        _check(load().sam_apply(self.ptr, ctypes.byref(m), _addr(x), _addr(y)), "sam_apply")
+        return y
+
+    def sam_build_backward(self, A_k: Csr, A_0: Csr, S: Pattern, M_val, dM_val, precision="fp32r",
+                           refine_steps: int = 1, dA_k_val=None, dA_0_val=None):
+        import torch
+
+        prec = PRECISIONS.get(precision, precision)
+        if dA_k_val is None:
+            dA_k_val = torch.empty(A_k.nnz, dtype=torch.float64, device="cuda")
+        if dA_0_val is None:
+            dA_0_val = torch.empty(A_0.nnz, dtype=torch.float64, device="cuda")
+        a, z = A_k.c(), A_0.c()
+        _check(load().sam_build_backward(self.ptr, ctypes.byref(a), ctypes.byref(z), S.ptr, int(prec),
+                                         int(refine_steps), _addr(M_val), _addr(dM_val), _addr(dA_k_val),
+                                         _addr(dA_0_val)), "sam_build_backward")
+        return dA_k_val, dA_0_val
+
+    def sam_profile(self, enable: bool):
+        _check(load().sam_profile(self.ptr, int(bool(enable))), "sam_profile")
+
+    def sam_profile_read(self):
+        """(kernel launches, per-size-class least-squares ms, per-class launches)."""
+        n = ctypes.c_int64()
+        ms = (ctypes.c_double * 5)()
+        cnt = (ctypes.c_int64 * 5)()
+        _check(load().sam_profile_read(self.ptr, ctypes.byref(n), ms, cnt), "sam_profile_read")
+        return n.value, list(ms), list(cnt)
+
+    def sam_peak_flops(self, ms: float = 50.0):
+        f32, f64 = ctypes.c_double(), ctypes.c_double()
+        _check(load().sam_peak_flops(self.ptr, float(ms), ctypes.byref(f32), ctypes.byref(f64)), "sam_peak_flops")
+        return f32.value, f64.value

@@ -1,0 +1,287 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle
+on the same seeded inputs.
+
+Bars: patterns, shadow-derived CSR structure and row pointers bit-exact;
+map values within a relative Frobenius error of 1e-12 (SAM_FP64) and 1e-10
+(SAM_FP32_REFINE); residuals within 1e-10 relative."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from paper_2406_17656_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32r": 1e-10}
+
+
+@pytest.fixture(scope="module")
+def sam():
+    import torch
+
+    from paper_2406_17656_gb300 import build, sam as S
+
+    build.build()
+    assert torch.cuda.is_available()
+    return S
+
+
+@pytest.fixture(scope="module")
+def handle(sam):
+    h = sam.Handle()
+    yield h
+    h.close()
+
+
+def dev(sam, m):
+    return sam.Csr.from_host(m)
+
+
+def oracle_map(Ak, A0, level):
+    cp, ri = oracle.pattern(Ak, level)
+    out = oracle.build(Ak, A0, cp, ri)
+    ip, ix, dv = oracle.to_csr(Ak.n, cp, ri, out["mval"])
+    return {"cp": cp, "ri": ri, "ip": ip, "ix": ix, "dv": dv, "res2": out["res2"] + out["out2"],
+            "mval": out["mval"]}
+
+
+def rel_fro(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+CASES = {
+    "poisson5_32_L1": lambda: (W.config1(), 1),
+    "q1_40_L1": lambda: (W.config2(nx=40, nmat=3), 1),
+    "q1_40_L2": lambda: (W.config2(nx=40, nmat=3), 2),
+    "upwind7_11_L2": lambda: (W.config3(nx=11, nmat=4), 2),
+    "fem_36_L1": lambda: (W.config4(ncell=36, nmat=3, flip_frac=0.05), 1),
+    "fem_36_L2": lambda: (W.config4(ncell=36, nmat=3, flip_frac=0.05), 2),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_pattern_bit_exact(sam, handle, case):
+    seq, level = CASES[case]()
+    for Ak in seq.mats:
+        cp, ri = oracle.pattern(Ak, level)
+        S = handle.sam_pattern_build(dev(sam, Ak), level)
+        assert S.nnz == len(ri)
+        assert np.array_equal(S.colptr().cpu().numpy(), cp)
+        assert np.array_equal(S.rowidx().cpu().numpy(), ri)
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("level", [0, 1, 2, 3])
+def test_pattern_random_nonsymmetric(sam, handle, seed, level):
+    rng = np.random.default_rng(100 + seed)
+    n = 300
+    p = (rng.random((n, n)) < 0.01) | np.eye(n, dtype=bool)
+    p[:, rng.integers(0, n, 3)] = False  # a few empty columns
+    a = np.where(p, rng.uniform(1.0, 2.0, (n, n)), 0.0)
+    A = W.CSR.from_dense(a)
+    cp, ri = oracle.pattern(A, level)
+    S = handle.sam_pattern_build(dev(sam, A), level)
+    assert np.array_equal(S.colptr().cpu().numpy(), cp)
+    assert np.array_equal(S.rowidx().cpu().numpy(), ri)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_build_matches_oracle(sam, handle, case, precision):
+    import torch
+
+    seq, level = CASES[case]()
+    A0 = seq.mats[0]
+    for Ak in seq.mats[1:]:
+        ref = oracle_map(Ak, A0, level)
+        S = handle.sam_pattern_build(dev(sam, Ak), level)
+        st = torch.empty(Ak.n, dtype=torch.int32, device="cuda")
+        r2 = torch.empty(Ak.n, dtype=torch.float64, device="cuda")
+        ip, ix, dv = handle.sam_build(dev(sam, Ak), dev(sam, A0), S, precision, refine_steps=1,
+                                      col_status=st, res2=r2)
+        handle.sam_sync()
+        assert np.array_equal(ip.cpu().numpy(), ref["ip"])
+        assert np.array_equal(ix.cpu().numpy(), ref["ix"])
+        assert int(st.abs().max()) == 0
+        err = rel_fro(dv.cpu().numpy(), ref["dv"])
+        assert err <= TOL[precision], err
+        got_r2 = r2.cpu().numpy()
+        assert abs(got_r2.sum() - ref["res2"].sum()) <= 1e-10 * ref["res2"].sum()
+
+
+@pytest.mark.parametrize("steps", [0, 1, 2])
+def test_refinement_steps_converge(sam, handle, steps):
+    seq = W.config2(nx=32, nmat=4)
+    Ak, A0 = seq.mats[3], seq.mats[0]
+    ref = oracle_map(Ak, A0, 2)
+    S = handle.sam_pattern_build(dev(sam, Ak), 2)
+    _, _, dv = handle.sam_build(dev(sam, Ak), dev(sam, A0), S, "fp32r", refine_steps=steps)
+    err = rel_fro(dv.cpu().numpy(), ref["dv"])
+    bound = {0: 1e-5, 1: 1e-10, 2: 1e-13}[steps]
+    assert err <= bound, err
+
+
+def test_batched_build_matches_oracle(sam, handle):
+    seq = W.config2(nx=36, nmat=5, level=2)
+    A0 = seq.mats[0]
+    Aks = [dev(sam, m) for m in seq.mats]
+    Ss = handle.sam_pattern_build_batched(Aks, 2)
+    offs, rp, ci, v, fro = handle.sam_build_batched(Aks, dev(sam, A0), Ss, "fp32r", 1, want_fro=True)
+    n = A0.n
+    rp, ci, v = rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy()
+    for k, Ak in enumerate(seq.mats):
+        ref = oracle_map(Ak, A0, 2)
+        assert np.array_equal(rp[k * (n + 1):(k + 1) * (n + 1)], ref["ip"])
+        assert np.array_equal(ci[offs[k]:offs[k + 1]], ref["ix"])
+        assert rel_fro(v[offs[k]:offs[k + 1]], ref["dv"]) <= 1e-10
+        ofro, _ = oracle.residual(Ak, ref["cp"], ref["ri"], ref["mval"], A0)
+        assert abs(fro[k] - ofro) <= 1e-10 * max(ofro, 1e-300) + 1e-14
+
+
+def test_identity_map_when_source_is_target(sam, handle):
+    A = W.config2(nx=30, nmat=1).mats[0]
+    S = handle.sam_pattern_build(dev(sam, A), 2)
+    for prec in ("fp64", "fp32r"):
+        ip, ix, dv = handle.sam_build(dev(sam, A), dev(sam, A), S, prec, 1)
+        m = sp.csr_matrix((dv.cpu().numpy(), ix.cpu().numpy(), ip.cpu().numpy()), shape=(A.n, A.n))
+        assert abs(m - sp.eye(A.n)).max() < 1e-12
+
+
+def test_residual_matches_oracle(sam, handle):
+    seq = W.config4(ncell=30, nmat=4, flip_frac=0.2)
+    Ak, A0 = seq.mats[3], seq.mats[0]
+    for level in (0, 1, 2):
+        ref = oracle_map(Ak, A0, level)
+        M = sam.Csr.from_host(W.CSR(Ak.n, ref["ip"], ref["ix"], ref["dv"]))
+        fro, rel = handle.sam_residual(dev(sam, Ak), M, dev(sam, A0))
+        ofro, orel = oracle.residual(Ak, ref["cp"], ref["ri"], ref["mval"], A0)
+        assert abs(fro - ofro) <= 1e-12 * ofro
+        assert abs(rel - orel) <= 1e-12 * orel
+
+
+def test_apply_matches_sparse_product(sam, handle):
+    import torch
+
+    seq = W.config2(nx=24, nmat=2)
+    ref = oracle_map(seq.mats[1], seq.mats[0], 2)
+    M = sam.Csr.from_host(W.CSR(seq.mats[1].n, ref["ip"], ref["ix"], ref["dv"]))
+    x = np.random.default_rng(3).standard_normal(seq.mats[1].n)
+    y = handle.sam_apply(M, torch.from_numpy(x).cuda()).cpu().numpy()
+    want = oracle.apply(ref["ip"], ref["ix"], ref["dv"], x)
+    assert np.max(np.abs(y - want)) <= 1e-14 * np.max(np.abs(want))
+
+
+def test_host_buffers_give_the_device_result(sam, handle):
+    """The same C-ABI call with host (numpy) inputs and outputs."""
+    seq = W.config2(nx=20, nmat=2)
+    Ak, A0 = seq.mats[1], seq.mats[0]
+    S = handle.sam_pattern_build(dev(sam, Ak), 2)
+    ipd, ixd, dvd = handle.sam_build(dev(sam, Ak), dev(sam, A0), S, "fp32r", 1)
+    hk = sam.Csr(Ak.indptr, Ak.indices, Ak.data)
+    h0 = sam.Csr(A0.indptr, A0.indices, A0.data)
+    out = (np.empty(Ak.n + 1, np.int32), np.empty(S.nnz, np.int32), np.empty(S.nnz, np.float64))
+    handle.sam_build(hk, h0, S, "fp32r", 1, out=out)
+    assert np.array_equal(out[0], ipd.cpu().numpy())
+    assert np.array_equal(out[1], ixd.cpu().numpy())
+    assert np.array_equal(out[2], dvd.cpu().numpy())
+
+
+# ------------------------------------------------------------- edge cases
+
+
+def test_one_by_one(sam, handle):
+    A = W.CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([4.0]))
+    B = W.CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([3.0]))
+    S = handle.sam_pattern_build(dev(sam, A), 1)
+    for prec in ("fp64", "fp32r"):
+        ip, ix, dv = handle.sam_build(dev(sam, A), dev(sam, B), S, prec, 1)
+        assert abs(float(dv.cpu()[0]) - 0.75) < 1e-15
+
+
+def test_non_nested_target_entries_enter_the_residual(sam, handle):
+    seq = W.config4(ncell=20, nmat=6, flip_frac=0.3)
+    Ak, A0 = seq.mats[5], seq.mats[0]
+    ref = oracle_map(Ak, A0, 0)
+    assert ref["res2"].sum() > 0
+    import torch
+
+    S = handle.sam_pattern_build(dev(sam, Ak), 0)
+    r2 = torch.empty(Ak.n, dtype=torch.float64, device="cuda")
+    ip, ix, dv = handle.sam_build(dev(sam, Ak), dev(sam, A0), S, "fp64", 0, res2=r2)
+    assert rel_fro(dv.cpu().numpy(), ref["dv"]) <= 1e-12
+    assert np.allclose(r2.cpu().numpy(), ref["res2"], rtol=1e-10, atol=1e-14)
+
+
+def test_rank_deficient_column_is_reported(sam, handle):
+    import torch
+
+    A = W.config1().mats[1].to_scipy().tolil()
+    A[:, 5] = 0.0  # column 5 has no stored entries -> its problem has no rows
+    A = W.CSR.from_scipy(A.tocsr())
+    S = handle.sam_pattern_build(dev(sam, A), 1)
+    st = torch.zeros(A.n, dtype=torch.int32, device="cuda")
+    handle.sam_build(dev(sam, A), dev(sam, W.config1().mats[0]), S, "fp32r", 1, col_status=st)
+    with pytest.raises(sam.SamError) as e:
+        handle.sam_sync()
+    assert e.value.status == sam.SAM_ERR_RANK_DEFICIENT
+    assert int(st.cpu().numpy()[5]) == sam.SAM_ERR_RANK_DEFICIENT
+
+
+def test_oversized_column_is_unsupported(sam, handle):
+    n = 64
+    a = np.eye(n) * 40.0
+    a[0, 1:40] = -1.0  # column 0 of the level-1 pattern... row 0 couples to 39 columns
+    a[1:40, 0] = -1.0
+    A = W.CSR.from_dense(a)
+    S = handle.sam_pattern_build(dev(sam, A), 1)
+    handle.sam_build(dev(sam, A), dev(sam, A), S, "fp32r", 1)
+    with pytest.raises(sam.SamError) as e:
+        handle.sam_sync()
+    assert e.value.status == sam.SAM_ERR_UNSUPPORTED
+
+
+def test_malformed_csr_is_rejected_without_running_kernels(sam, handle):
+    A = W.config1().mats[0]
+    bad = W.CSR(A.n, A.indptr.copy(), A.indices.copy(), A.data.copy())
+    bad.indices[3], bad.indices[4] = bad.indices[4], bad.indices[3]  # unsorted row
+    with pytest.raises(sam.SamError) as e:
+        handle.sam_pattern_build(dev(sam, bad), 1)
+    assert e.value.status == sam.SAM_ERR_BAD_CSR
+    bad2 = W.CSR(A.n, A.indptr.copy(), A.indices.copy(), A.data.copy())
+    bad2.indices[7] = A.n + 5  # out of range
+    with pytest.raises(sam.SamError) as e:
+        handle.sam_pattern_build(dev(sam, bad2), 1)
+    assert e.value.status == sam.SAM_ERR_BAD_CSR
+
+
+# ------------------------------------------- full size, sampled columns
+
+
+def test_full_size_q1_256_level2_sampled(sam, handle):
+    """The 256x256 Q1 diffusion sequence (10 matrices, level 2) in the
+    benchmark's launch configuration; 1500 sampled columns per map against
+    the oracle."""
+    import torch
+
+    seq = W.config2(nx=256, nmat=10, level=2)
+    A0 = seq.mats[0]
+    Aks = [dev(sam, m) for m in seq.mats]
+    Ss = handle.sam_pattern_build_batched(Aks, 2)
+    offs, rp, ci, v, fro = handle.sam_build_batched(Aks, dev(sam, A0), Ss, "fp32r", 1, want_fro=True)
+    n = A0.n
+    rp, ci, v = rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy()
+    rng = np.random.default_rng(77)
+    for k in (1, 5, 9):
+        Ak = seq.mats[k]
+        cp, ri = oracle.pattern(Ak, 2)
+        assert np.array_equal(Ss[k].colptr().cpu().numpy(), cp)
+        cols = np.sort(rng.choice(n, 1500, replace=False)).astype(np.int32)
+        cols = np.unique(np.concatenate([cols, [0, n - 1, 255, n - 256]]).astype(np.int32))
+        ref = oracle.build_cols(Ak, A0, cp, ri, cols)
+        m = sp.csr_matrix((v[offs[k]:offs[k + 1]], ci[offs[k]:offs[k + 1]], rp[k * (n + 1):(k + 1) * (n + 1)]),
+                          shape=(n, n)).tocsc()
+        m.sort_indices()
+        assert np.array_equal(m.indptr, cp) and np.array_equal(m.indices, ri)
+        idx = np.concatenate([np.arange(cp[j], cp[j + 1]) for j in cols])
+        assert rel_fro(m.data[idx], ref["mval"][idx]) <= 1e-10
