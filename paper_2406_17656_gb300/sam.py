@@ -14,6 +14,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -187,6 +188,7 @@ class Pattern:
 
     def __init__(self, handle: "Handle", ptr: int):
         self.handle, self.ptr = handle, ptr
+        handle._patterns.add(self)
         n, nnz, cp, ri = ctypes.c_int32(), ctypes.c_int64(), _vp(), _vp()
         _check(load().sam_pattern_get(ptr, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(cp), ctypes.byref(ri)),
                "sam_pattern_get")
@@ -204,9 +206,11 @@ class Pattern:
         return torch.as_tensor(_CudaView(self._ri, self.nnz, "<i4"), device="cuda")
 
     def destroy(self):
-        if self.ptr:
+        # a pattern lives in its handle's memory pool: once the handle is
+        # closed the pool has released it, and the pattern must not be touched
+        if self.ptr and getattr(self.handle, "ptr", 0):
             load().sam_pattern_destroy(self.ptr)
-            self.ptr = 0
+        self.ptr = 0
 
     def __del__(self):
         try:
@@ -227,6 +231,7 @@ class Handle:
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
+        self._patterns = weakref.WeakSet()
         h = _vp()
         _check(lib.sam_create(ctypes.byref(h), _vp(int(stream.cuda_stream))), "sam_create")
         self.ptr = h.value
@@ -235,6 +240,8 @@ class Handle:
 
     def close(self):
         if getattr(self, "ptr", 0):
+            for p in list(getattr(self, "_patterns", ())):
+                p.destroy()
             load().sam_destroy(self.ptr)
             self.ptr = 0
 
