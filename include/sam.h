@@ -29,7 +29,9 @@
  *    device pointers every call is asynchronous on the handle's stream.
  *  - All memory passed in is owned by the caller and never freed by the
  *    library.  Objects returned through `sam_handle*` / `sam_pattern*` are
- *    owned by the library and released with the matching destroy call.
+ *    owned by the library and released with the matching destroy call;
+ *    patterns live in their handle's memory pool, so destroy them before
+ *    the handle.
  *  - No call aborts, traps or throws.  Each returns a sam_status.  Errors
  *    detected on the device (a rank-deficient or non-finite column, an
  *    unsupported column size) are recorded in a sticky status word that
@@ -179,19 +181,32 @@ sam_status sam_residual(sam_handle h, const sam_csr *A_k, const sam_csr *M_k, co
 sam_status sam_apply(sam_handle h, const sam_csr *M_k, const double *x, double *y);
 
 /*
- * sam_build_backward -- adjoint of sam_build on a fixed pattern.  Given
- * dM_val = dL/dM_k (CSR order of the map, nnz(S) values), returns
- * dA_k_val = dL/dA_k and dA_0_val = dL/dA_0 on the stored entries of A_k
- * and A_0 (CSR order).  Per column, with B = A_k(I_j, J_j), c = A_0(I_j, j),
- * m = B^+ c, r = c - B m and g = dL/dm:  lambda = (B^T B)^{-1} g,
- * dL/dc = B lambda, dL/dB = r lambda^T - (B lambda) m^T; entries of dL/dB at
- * positions not stored in A_k are dropped, and the per-column contributions
- * are summed deterministically.  M_val must be the map built from the same
- * A_k, A_0 and S.  precision as in sam_build (the QR is recomputed).
+ * sam_build_backward -- adjoint of sam_build on a fixed pattern: gradients
+ * with respect to the stored values of A_k and A_0 of
+ *     L = <dM, M_k>  +  resid_weight * ||A_k M_k - A_0||_F^2,
+ * where the first term stands for any loss whose gradient with respect to the
+ * map values is dM_val (CSR order of the map, nnz(S) values; NULL = zero) and
+ * the second is the residual of Eq. (res), differentiated directly (its
+ * dependence through M_k is returned separately, see dM_resid).
+ * Per column, with B = A_k(I_j, J_j), c = A_0(I_j, j), m the column of M_k,
+ * r = c - B m, g = dM(J_j, j) and lambda = (B^T B)^{-1} g:
+ *     dL/dB += r lambda^T - (B lambda) m^T - 2 w r m^T,
+ *     dL/dc += B lambda + 2 w r,   dL/dA_0(i, j) += 2 w A_0(i, j) for rows
+ *     i outside I_j  (w = resid_weight).
+ * Entries of dL/dB at positions not stored in A_k are dropped; every stored
+ * A_k entry receives the sum of its contributions from all columns, added
+ * in a fixed order (deterministic).  lambda uses the recomputed QR (FP32 R
+ * plus `refine_steps` FP64-residual corrections for SAM_FP32_REFINE).
+ * dA_k_val[nnz(A_k)], dA_0_val[nnz(A_0)]: outputs in the CSR order of A_k
+ * and A_0 (overwritten).  dM_resid (nullable, nnz(S), CSR order of the map):
+ * receives w * d||A_k M - A_0||_F^2 / dM = -2 w A_k^T R on the pattern (zero
+ * up to rounding at the least-squares solution).  M_val must be the map built
+ * from the same A_k, A_0 and S.
  */
 sam_status sam_build_backward(sam_handle h, const sam_csr *A_k, const sam_csr *A_0, sam_pattern S,
                               int precision, int refine_steps, const double *M_val,
-                              const double *dM_val, double *dA_k_val, double *dA_0_val);
+                              const double *dM_val, double resid_weight, double *dA_k_val,
+                              double *dA_0_val, double *dM_resid);
 
 /*
  * sam_tune -- time the least-squares kernels' launch shapes on the columns of

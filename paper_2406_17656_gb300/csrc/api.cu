@@ -1,6 +1,13 @@
 // api.cu -- the C ABI of libsam (declared in include/sam.h): handles, the
 // stream-ordered device workspace, host/device argument staging, and the
 // orchestration of the pattern, build, residual and apply pipelines.
+//
+// Batches.  K maps of order n are processed as one block-diagonal problem of
+// order N = K n (see common.cuh), so every stage is one launch whatever K is.
+// Patterns built together (sam_pattern_build_batched) share one
+// block-diagonal store (a "pattern group"); sam_build_batched on exactly
+// such a group uses it in place, any other combination is concatenated into
+// a temporary group first.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -16,9 +23,8 @@ struct sam_handle_t {
     int sms = 1;
     uint32_t flags = 0;
     cudaMemPool_t pool = nullptr;
-    int32_t *d_flag = nullptr;   // sticky device status word
-    int32_t *h_flag = nullptr;   // pinned mirror
-    sam_status host_sticky = SAM_OK;
+    int32_t *d_flag = nullptr;  // sticky device status word
+    int32_t *h_flag = nullptr;  // pinned mirror
     // tracing
     int64_t launches = 0;
     bool profiling = false;
@@ -31,13 +37,25 @@ struct sam_handle_t {
     int64_t lsq_n[sam::kNumBins] = {0};
 };
 
-struct sam_pattern_t {
+namespace {
+// K patterns of order n stored as one block-diagonal pattern
+struct PatternGroup {
     sam_handle h = nullptr;
+    int refs = 0;
+    int K = 0, n = 0;
+    int32_t *jcp = nullptr, *jri = nullptr;  // CSC, rows of map k shifted by k n
+    int32_t *mrp = nullptr, *mci = nullptr;  // CSR of the block-diagonal map
+    int32_t *csr_pos = nullptr;              // CSC entry -> CSR position
+    std::vector<int64_t> off;                // per-map nnz prefix [K+1]
+};
+}  // namespace
+
+struct sam_pattern_t {
+    PatternGroup *g = nullptr;
+    int k = 0;
     int n = 0;
     int64_t nnz = 0;
-    int32_t *jcp = nullptr, *jri = nullptr;      // pattern, CSC (= CSC structure of the map)
-    int32_t *mrp = nullptr, *mci = nullptr;      // CSR structure of the map
-    int32_t *csr_pos = nullptr;                  // CSC entry -> CSR position
+    int32_t *view_cp = nullptr, *view_ri = nullptr;  // local (unshifted) views, made on demand
 };
 
 namespace sam {
@@ -196,24 +214,40 @@ sam_status drain_status(sam_handle h) {
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SAM_ERR_CUDA;
     sam_status s = *h->h_flag;
     if (s != SAM_OK) cudaMemsetAsync(h->d_flag, 0, sizeof(int32_t), h->stream);
-    if (s == SAM_OK && h->host_sticky != SAM_OK) s = h->host_sticky;
-    h->host_sticky = SAM_OK;
     return s;
 }
 
-// Validates CSR structures on the device; synchronises once.
-sam_status validate_all(sam_handle h, const std::vector<DevCsr> &ms) {
-    if (h->flags & SAM_FLAG_TRUSTED) return SAM_OK;
-    int32_t *flag = (int32_t *)pool_alloc(h, sizeof(int32_t));
-    if (!flag) return SAM_ERR_OOM;
+// Validates the CSR structures of equal-order matrices on the device;
+// synchronises once.  Nothing reads an unvalidated structure before this.
+sam_status validate_all(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms) {
+    if ((h->flags & SAM_FLAG_TRUSTED) || ms.empty()) return SAM_OK;
+    const int K = (int)ms.size();
+    std::vector<CsrPtrs> tab(K);
+    std::vector<int64_t> nz(K);
+    for (int k = 0; k < K; ++k) {
+        tab[k] = {ms[k].rp, ms[k].ci, ms[k].v};
+        nz[k] = ms[k].nnz;
+    }
+    CsrPtrs *dtab = sc.get<CsrPtrs>(K);
+    int64_t *dnz = sc.get<int64_t>(K);
+    int32_t *flag = sc.get<int32_t>(1);
+    if (!dtab || !dnz || !flag) return SAM_ERR_OOM;
+    cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * K, cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(dnz, nz.data(), sizeof(int64_t) * K, cudaMemcpyHostToDevice, h->stream);
     cudaMemsetAsync(flag, 0, sizeof(int32_t), h->stream);
-    for (auto &m : ms)
-        if (validate_csr(h, m.n, m.nnz, m.rp, m.ci, flag) != cudaSuccess) return SAM_ERR_CUDA;
-    int32_t hv = 0;
+    // matrices of different order (the residual call) are validated one by one
+    bool same = true;
+    for (auto &m : ms) same &= (m.n == ms[0].n);
+    if (same) {
+        if (validate_csr_batch(h, K, ms[0].n, dtab, dnz, flag) != cudaSuccess) return SAM_ERR_CUDA;
+    } else {
+        for (int k = 0; k < K; ++k)
+            if (validate_csr_batch(h, 1, ms[k].n, dtab + k, dnz + k, flag) != cudaSuccess) return SAM_ERR_CUDA;
+    }
     cudaMemcpyAsync(h->h_flag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
-    pool_free(h, flag);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SAM_ERR_CUDA;
-    hv = *h->h_flag;
+    const int32_t hv = *h->h_flag;
+    *h->h_flag = 0;
     return hv ? (sam_status)hv : SAM_OK;
 }
 
@@ -222,64 +256,135 @@ __global__ void scatter_inverse_kernel(int64_t nnz, const int32_t *perm, int32_t
     if (p < nnz) pos[perm[p]] = (int32_t)p;
 }
 
-// Pattern object from a CSC pattern already on the device (takes ownership
-// of jcp / jri, which must come from the handle's pool).
-sam_status finish_pattern(sam_handle h, int n, int64_t nnz, int32_t *jcp, int32_t *jri, sam_pattern *out) {
-    sam_pattern S = new (std::nothrow) sam_pattern_t;
-    if (!S) return SAM_ERR_OOM;
-    S->h = h;
-    S->n = n;
-    S->nnz = nnz;
-    S->jcp = jcp;
-    S->jri = jri;
-    S->mrp = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)n + 1));
-    S->mci = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)(nnz ? nnz : 1));
-    S->csr_pos = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)(nnz ? nnz : 1));
+__global__ void gather_strided_kernel(int K, int n, const int32_t *jcp, int64_t *off) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k <= K) off[k] = jcp[(int64_t)k * n];
+}
+
+void group_release(PatternGroup *g) {
+    if (!g || --g->refs > 0) return;
+    sam_handle h = g->h;
+    pool_free(h, g->jcp);
+    pool_free(h, g->jri);
+    pool_free(h, g->mrp);
+    pool_free(h, g->mci);
+    pool_free(h, g->csr_pos);
+    delete g;
+}
+
+// Completes a group from its block-diagonal CSC pattern (takes ownership of
+// jcp / jri, which must come from the handle's pool): per-map offsets, the
+// CSR structure of the map and the CSC -> CSR positions.
+sam_status group_finish(sam_handle h, int K, int n, int32_t *jcp, int32_t *jri, int64_t nnz, PatternGroup **out) {
+    PatternGroup *g = new (std::nothrow) PatternGroup;
+    if (!g) return SAM_ERR_OOM;
+    g->h = h;
+    g->refs = 1;
+    g->K = K;
+    g->n = n;
+    g->jcp = jcp;
+    g->jri = jri;
+    const int64_t N = (int64_t)K * n;
+    g->mrp = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)N + 1));
+    g->mci = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)(nnz ? nnz : 1));
+    g->csr_pos = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)(nnz ? nnz : 1));
     int32_t *perm = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)(nnz ? nnz : 1));
-    if (!S->mrp || !S->mci || !S->csr_pos || !perm) {
+    int64_t *doff = (int64_t *)pool_alloc(h, sizeof(int64_t) * ((size_t)K + 1));
+    auto fail = [&](sam_status s) {
         pool_free(h, perm);
-        sam_pattern_destroy(S);
-        return SAM_ERR_OOM;
-    }
+        pool_free(h, doff);
+        group_release(g);
+        return s;
+    };
+    if (!g->mrp || !g->mci || !g->csr_pos || !perm || !doff) return fail(SAM_ERR_OOM);
     // the CSC of the map read as the CSR of its transpose; transposing it
-    // gives the CSR of the map, and perm[p] = CSC entry of CSR position p
-    if (csr_to_csc(h, n, nnz, jcp, jri, nullptr, S->mrp, S->mci, nullptr, perm) != cudaSuccess) {
-        pool_free(h, perm);
-        sam_pattern_destroy(S);
-        return SAM_ERR_CUDA;
-    }
+    // gives the CSR of the map, with perm[p] = CSC entry of CSR position p
+    if (csr_to_csc(h, (int)N, nnz, jcp, jri, nullptr, g->mrp, g->mci, nullptr, perm) != cudaSuccess)
+        return fail(SAM_ERR_CUDA);
     if (nnz > 0) {
-        scatter_inverse_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, h->stream>>>(nnz, perm, S->csr_pos);
+        scatter_inverse_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, h->stream>>>(nnz, perm, g->csr_pos);
         count_launch(h);
     }
+    gather_strided_kernel<<<(K + 1 + 127) / 128, 128, 0, h->stream>>>(K, n, jcp, doff);
+    count_launch(h);
+    g->off.resize((size_t)K + 1);
+    if (cudaMemcpyAsync(g->off.data(), doff, sizeof(int64_t) * ((size_t)K + 1), cudaMemcpyDeviceToHost, h->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return fail(SAM_ERR_CUDA);
     pool_free(h, perm);
-    if (cudaGetLastError() != cudaSuccess) {
-        sam_pattern_destroy(S);
-        return SAM_ERR_CUDA;
+    pool_free(h, doff);
+    *out = g;
+    return cudaGetLastError() == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
+}
+
+sam_status make_patterns(PatternGroup *g, sam_pattern *out) {
+    for (int k = 0; k < g->K; ++k) {
+        sam_pattern S = new (std::nothrow) sam_pattern_t;
+        if (!S) {
+            for (int q = 0; q < k; ++q) sam_pattern_destroy(out[q]);
+            return SAM_ERR_OOM;
+        }
+        S->g = g;
+        S->k = k;
+        S->n = g->n;
+        S->nnz = g->off[k + 1] - g->off[k];
+        if (k > 0) g->refs++;
+        out[k] = S;
     }
-    *out = S;
     return SAM_OK;
 }
 
-__global__ void validate_pattern_kernel(int n, int64_t nnz, const int32_t *cp, const int32_t *ri, int32_t *flag) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j == 0 && (cp[0] != 0 || (int64_t)cp[n] != nnz)) atomicCAS(flag, 0, SAM_ERR_BAD_CSR);
-    if (j >= n) return;
-    int b = cp[j], e = cp[j + 1];
-    if (e <= b || b < 0 || (int64_t)e > nnz) {  // every column must be nonempty
-        atomicCAS(flag, 0, SAM_ERR_BAD_CSR);
-        return;
-    }
-    for (int t = b; t < e; ++t)
-        if (ri[t] < 0 || ri[t] >= n || (t > b && ri[t] <= ri[t - 1])) {
-            atomicCAS(flag, 0, SAM_ERR_BAD_CSR);
-            return;
-        }
+__global__ void rebase_view_kernel(int n, int k, const int32_t *jcp, const int32_t *jri, int64_t base, int64_t nnz,
+                                   int32_t *cp, int32_t *ri) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t shift = (int64_t)k * n;
+    if (t <= n) cp[t] = (int32_t)(jcp[shift + t] - base);
+    if (t < nnz) ri[t] = (int32_t)(jri[base + t] - shift);
 }
 
-__global__ void rowptr_rebase_kernel(int n, const int32_t *src, int32_t *dst) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i <= n) dst[i] = src[i];
+// Concatenate member patterns of arbitrary groups into a temporary group.
+__global__ void concat_pattern_kernel(int n, int k, const int32_t *src_cp, const int32_t *src_ri, int64_t src_base,
+                                      int src_k, int64_t dst_base, int32_t *dst_cp, int32_t *dst_ri, int64_t nnz,
+                                      int last) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t sshift = (int64_t)src_k * n, dshift = (int64_t)k * n;
+    if (t < n || (last && t == n)) dst_cp[dshift + t] = (int32_t)(src_cp[sshift + t] - src_base + dst_base);
+    if (t < nnz) dst_ri[dst_base + t] = (int32_t)(src_ri[src_base + t] - sshift + dshift);
+}
+
+sam_status group_for(sam_handle h, int K, const sam_pattern *S, PatternGroup **g_out, bool *temp) {
+    PatternGroup *g0 = S[0]->g;
+    bool direct = g0->K == K;
+    for (int k = 0; k < K && direct; ++k) direct = (S[k]->g == g0 && S[k]->k == k);
+    if (direct) {
+        *g_out = g0;
+        *temp = false;
+        return SAM_OK;
+    }
+    const int n = S[0]->n;
+    int64_t tot = 0;
+    for (int k = 0; k < K; ++k) tot += S[k]->nnz;
+    if (tot > INT32_MAX) return SAM_ERR_INVALID_ARG;
+    const int64_t N = (int64_t)K * n;
+    int32_t *jcp = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)N + 1));
+    int32_t *jri = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)(tot ? tot : 1));
+    if (!jcp || !jri) {
+        pool_free(h, jcp);
+        pool_free(h, jri);
+        return SAM_ERR_OOM;
+    }
+    int64_t base = 0;
+    for (int k = 0; k < K; ++k) {
+        PatternGroup *g = S[k]->g;
+        const int64_t cnt = (n + 1 > S[k]->nnz) ? n + 1 : S[k]->nnz;
+        concat_pattern_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(
+            n, k, g->jcp, g->jri, g->off[S[k]->k], S[k]->k, base, jcp, jri, S[k]->nnz, k == K - 1);
+        count_launch(h);
+        base += S[k]->nnz;
+    }
+    *temp = true;
+    return group_finish(h, K, n, jcp, jri, tot, g_out);
 }
 
 }  // namespace
@@ -373,39 +478,50 @@ sam_status sam_sync(sam_handle h) {
 
 sam_status sam_pattern_build_batched(sam_handle h, int K, const sam_csr *A, int level, sam_pattern *out) {
     if (!h || K < 1 || !A || !out || level < 0 || level > 3) return SAM_ERR_INVALID_ARG;
+    int64_t tot = 0;
     for (int k = 0; k < K; ++k) {
         out[k] = nullptr;
         if (check_csr_arg(&A[k], false) != SAM_OK || A[k].n != A[0].n) return SAM_ERR_INVALID_ARG;
+        tot += A[k].nnz;
     }
     const int n = A[0].n;
+    const int64_t N = (int64_t)K * n;
+    if (N > INT32_MAX - 1 || tot > INT32_MAX) return SAM_ERR_INVALID_ARG;
+    cudaStream_t st = h->stream;
     Scratch sc(h);
-    Stager sg(sc, h->stream);
+    Stager sg(sc, st);
     std::vector<DevCsr> d(K);
     for (int k = 0; k < K; ++k) d[k] = stage_csr(sg, &A[k], false);
     if (sg.failed) return SAM_ERR_OOM;
-    sam_status s = validate_all(h, d);
+    sam_status s = validate_all(h, sc, d);
     if (s != SAM_OK) return s;
-    std::vector<int32_t *> kcp(K), kri(K);
+    // block-diagonal structure of the batch, then its CSC
+    std::vector<CsrPtrs> tab(K);
+    std::vector<int64_t> off(K + 1, 0);
     for (int k = 0; k < K; ++k) {
-        kcp[k] = sc.get<int32_t>((size_t)n + 1);
-        kri[k] = sc.get<int32_t>((size_t)d[k].nnz);
-        if (!kcp[k] || !kri[k]) return SAM_ERR_OOM;
-        if (csr_to_csc(h, n, d[k].nnz, d[k].rp, d[k].ci, nullptr, kcp[k], kri[k], nullptr, nullptr) != cudaSuccess)
-            return SAM_ERR_CUDA;
+        tab[k] = {d[k].rp, d[k].ci, nullptr};
+        off[k + 1] = off[k] + d[k].nnz;
     }
-    std::vector<int32_t *> jcp(K), jri(K);
-    std::vector<int64_t> nnz(K);
-    s = level_pattern_batched(h, K, n, kcp.data(), kri.data(), level, jcp.data(), jri.data(), nnz.data());
+    CsrPtrs *dtab = sc.get<CsrPtrs>(K);
+    int64_t *doff = sc.get<int64_t>(K + 1);
+    int32_t *brp = sc.get<int32_t>((size_t)N + 1), *bci = sc.get<int32_t>((size_t)tot);
+    int32_t *kcp = sc.get<int32_t>((size_t)N + 1), *kri = sc.get<int32_t>((size_t)tot);
+    if (!dtab || !doff || !brp || !bci || !kcp || !kri) return SAM_ERR_OOM;
+    cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * K, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, st);
+    if (concat_block_diag(h, K, n, dtab, doff, brp, bci, nullptr) != cudaSuccess) return SAM_ERR_CUDA;
+    if (csr_to_csc(h, (int)N, tot, brp, bci, nullptr, kcp, kri, nullptr, nullptr) != cudaSuccess) return SAM_ERR_CUDA;
+    int32_t *jcp = nullptr, *jri = nullptr;
+    int64_t nnz = 0;
+    s = level_pattern(h, (int)N, kcp, kri, tot, level, &jcp, &jri, &nnz);
     if (s != SAM_OK) return s;
-    for (int k = 0; k < K; ++k) {
-        s = finish_pattern(h, n, nnz[k], jcp[k], jri[k], &out[k]);
-        if (s != SAM_OK) {
-            for (int q = 0; q < k; ++q) {
-                sam_pattern_destroy(out[q]);
-                out[q] = nullptr;
-            }
-            return s;
-        }
+    PatternGroup *g = nullptr;
+    s = group_finish(h, K, n, jcp, jri, nnz, &g);
+    if (s != SAM_OK) return s;
+    s = make_patterns(g, out);
+    if (s != SAM_OK) {
+        group_release(g);
+        return s;
     }
     return drain_status(h);
 }
@@ -427,40 +543,71 @@ sam_status sam_pattern_from_csc(sam_handle h, int32_t n, int64_t nnz, const int3
     }
     cudaMemcpyAsync(jcp, colptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDefault, h->stream);
     cudaMemcpyAsync(jri, rowidx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDefault, h->stream);
-    int32_t *flag = (int32_t *)pool_alloc(h, sizeof(int32_t));
-    cudaMemsetAsync(flag, 0, sizeof(int32_t), h->stream);
-    validate_pattern_kernel<<<(n + 255) / 256 > 0 ? (n + 255) / 256 : 1, 256, 0, h->stream>>>(n, nnz, jcp, jri, flag);
-    count_launch(h);
-    cudaMemcpyAsync(h->h_flag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
-    pool_free(h, flag);
-    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SAM_ERR_CUDA;
-    if (*h->h_flag != 0) {
-        sam_status s = *h->h_flag;
-        *h->h_flag = 0;
-        pool_free(h, jcp);
-        pool_free(h, jri);
-        return s;
+    // the pattern is a CSC structure: validate it as the CSR of its transpose,
+    // plus the requirement that every column is nonempty (checked on the host
+    // copy of the column pointers)
+    std::vector<int32_t> hcp((size_t)n + 1);
+    cudaMemcpyAsync(hcp.data(), jcp, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost, h->stream);
+    {
+        Scratch sc(h);
+        DevCsr d;
+        d.n = n;
+        d.nnz = nnz;
+        d.rp = jcp;
+        d.ci = jri;
+        uint32_t saved = h->flags;
+        h->flags &= ~(uint32_t)SAM_FLAG_TRUSTED;  // a pattern is always validated
+        sam_status s = validate_all(h, sc, {d});
+        h->flags = saved;
+        bool nonempty = true;
+        for (int j = 0; j < n && s == SAM_OK; ++j) nonempty &= hcp[(size_t)j + 1] > hcp[j];
+        if (s == SAM_OK && !nonempty) s = SAM_ERR_BAD_CSR;
+        if (s != SAM_OK) {
+            pool_free(h, jcp);
+            pool_free(h, jri);
+            return s;
+        }
     }
-    return finish_pattern(h, n, nnz, jcp, jri, out);
+    PatternGroup *g = nullptr;
+    sam_status s = group_finish(h, 1, n, jcp, jri, nnz, &g);
+    if (s != SAM_OK) return s;
+    return make_patterns(g, out);
 }
 
 sam_status sam_pattern_get(sam_pattern S, int32_t *n, int64_t *nnz, const int32_t **colptr, const int32_t **rowidx) {
     if (!S) return SAM_ERR_INVALID_ARG;
     if (n) *n = S->n;
     if (nnz) *nnz = S->nnz;
-    if (colptr) *colptr = S->jcp;
-    if (rowidx) *rowidx = S->jri;
+    PatternGroup *g = S->g;
+    if (colptr || rowidx) {
+        if (g->K == 1) {
+            if (colptr) *colptr = g->jcp;
+            if (rowidx) *rowidx = g->jri;
+            return SAM_OK;
+        }
+        sam_handle h = g->h;
+        if (!S->view_cp) {
+            S->view_cp = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)S->n + 1));
+            S->view_ri = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)(S->nnz ? S->nnz : 1));
+            if (!S->view_cp || !S->view_ri) return SAM_ERR_OOM;
+            const int64_t cnt = (S->n + 1 > S->nnz) ? S->n + 1 : S->nnz;
+            rebase_view_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(
+                S->n, S->k, g->jcp, g->jri, g->off[S->k], S->nnz, S->view_cp, S->view_ri);
+            count_launch(h);
+            if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SAM_ERR_CUDA;
+        }
+        if (colptr) *colptr = S->view_cp;
+        if (rowidx) *rowidx = S->view_ri;
+    }
     return SAM_OK;
 }
 
 sam_status sam_pattern_destroy(sam_pattern S) {
     if (!S) return SAM_ERR_INVALID_ARG;
-    sam_handle h = S->h;
-    pool_free(h, S->jcp);
-    pool_free(h, S->jri);
-    pool_free(h, S->mrp);
-    pool_free(h, S->mci);
-    pool_free(h, S->csr_pos);
+    sam_handle h = S->g->h;
+    pool_free(h, S->view_cp);
+    pool_free(h, S->view_ri);
+    group_release(S->g);
     delete S;
     return SAM_OK;
 }
@@ -474,12 +621,17 @@ sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_
     if (refine_steps < 0 || refine_steps > 4) return SAM_ERR_INVALID_ARG;
     if (check_csr_arg(A_0, true) != SAM_OK) return SAM_ERR_INVALID_ARG;
     const int n = A_0->n;
+    int64_t ktot = 0;
+    if (M_offsets[0] != 0) return SAM_ERR_INVALID_ARG;
     for (int k = 0; k < K; ++k) {
         if (check_csr_arg(&A_k[k], true) != SAM_OK || A_k[k].n != n || !S[k] || S[k]->n != n)
             return SAM_ERR_INVALID_ARG;
-        if (M_offsets[k + 1] - M_offsets[k] != S[k]->nnz || M_offsets[k] < 0) return SAM_ERR_INVALID_ARG;
+        if (M_offsets[k + 1] - M_offsets[k] != S[k]->nnz) return SAM_ERR_INVALID_ARG;
+        ktot += A_k[k].nnz;
     }
+    const int64_t N = (int64_t)K * n;
     const int64_t total_nnz = M_offsets[K];
+    if (N > INT32_MAX - 1 || ktot > INT32_MAX || total_nnz > INT32_MAX) return SAM_ERR_INVALID_ARG;
     cudaStream_t st = h->stream;
     Scratch sc(h);
     Stager sg(sc, st);
@@ -489,77 +641,95 @@ sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_
     int32_t *d_rp = sg.out(M_row_ptr, (size_t)K * ((size_t)n + 1));
     int32_t *d_ci = sg.out(M_col_idx, (size_t)total_nnz);
     double *d_v = sg.out(M_val, (size_t)total_nnz);
-    int32_t *d_st = col_status ? sg.out(col_status, (size_t)K * (size_t)n) : nullptr;
-    double *d_r2 = res2 ? sg.out(res2, (size_t)K * (size_t)n) : nullptr;
+    int32_t *d_st = col_status ? sg.out(col_status, (size_t)N) : nullptr;
+    double *d_r2 = res2 ? sg.out(res2, (size_t)N) : nullptr;
     if (sg.failed) return SAM_ERR_OOM;
     {
         std::vector<DevCsr> all(ak);
         all.push_back(z);
-        sam_status s = validate_all(h, all);
+        sam_status s = validate_all(h, sc, all);
         if (s != SAM_OK) return s;
     }
-    // CSC of the target (shared) and of every source
+    PatternGroup *g = nullptr;
+    bool temp = false;
+    {
+        sam_status s = group_for(h, K, S, &g, &temp);
+        if (s != SAM_OK) return s;
+    }
+    struct GroupGuard {
+        PatternGroup *g;
+        bool temp;
+        ~GroupGuard() {
+            if (temp) group_release(g);
+        }
+    } guard{g, temp};
+    // target: CSC with values
     int32_t *zcp = sc.get<int32_t>((size_t)n + 1), *zri = sc.get<int32_t>((size_t)z.nnz);
     double *zcv = sc.get<double>((size_t)z.nnz);
     if (!zcp || !zri || !zcv) return SAM_ERR_OOM;
     if (csr_to_csc(h, n, z.nnz, z.rp, z.ci, z.v, zcp, zri, zcv, nullptr) != cudaSuccess) return SAM_ERR_CUDA;
-    if (!d_st) d_st = sc.get<int32_t>((size_t)K * n);
-    if (!d_r2) d_r2 = sc.get<double>((size_t)K * n);
-    if (!d_st || !d_r2) return SAM_ERR_OOM;
-    std::vector<MapDev> maps(K);
-    std::vector<const uint8_t *> bins(K);
+    // sources: block-diagonal CSR, then CSC with values
+    std::vector<CsrPtrs> tab(K);
+    std::vector<int64_t> off(K + 1, 0);
     for (int k = 0; k < K; ++k) {
-        int32_t *kcp = sc.get<int32_t>((size_t)n + 1), *kri = sc.get<int32_t>((size_t)ak[k].nnz);
-        double *kcv = sc.get<double>((size_t)ak[k].nnz);
-        int32_t *ish = sc.get<int32_t>((size_t)n * kICap), *icnt = sc.get<int32_t>((size_t)n);
-        uint8_t *bin = sc.get<uint8_t>((size_t)n);
-        if (!kcp || !kri || !kcv || !ish || !icnt || !bin) return SAM_ERR_OOM;
-        if (csr_to_csc(h, n, ak[k].nnz, ak[k].rp, ak[k].ci, ak[k].v, kcp, kri, kcv, nullptr) != cudaSuccess)
-            return SAM_ERR_CUDA;
-        int32_t *colstat = d_st + (size_t)k * n;
-        if (shadow_and_bins(h, n, kcp, kri, S[k]->jcp, S[k]->jri, precision, ish, icnt, bin, colstat) != cudaSuccess)
-            return SAM_ERR_CUDA;
-        MapDev &m = maps[k];
-        memset(&m, 0, sizeof(m));
-        m.kcp = kcp;
-        m.kri = kri;
-        m.kcv = kcv;
-        m.jcp = S[k]->jcp;
-        m.jri = S[k]->jri;
-        m.ish = ish;
-        m.icnt = icnt;
-        m.csr_pos = S[k]->csr_pos;
-        m.mval = d_v + M_offsets[k];
-        m.colres = d_r2 + (size_t)k * n;
-        m.colstat = colstat;
-        bins[k] = bin;
+        tab[k] = {ak[k].rp, ak[k].ci, ak[k].v};
+        off[k + 1] = off[k] + ak[k].nnz;
     }
-    int2 *work = sc.get<int2>((size_t)K * n);
-    int32_t *bin_off = sc.get<int32_t>(kNumBins + 1);
-    int32_t *tickets = sc.get<int32_t>(kNumBins);
-    MapDev *maps_dev = sc.get<MapDev>((size_t)K);
-    if (!work || !bin_off || !tickets || !maps_dev) return SAM_ERR_OOM;
-    if (cudaMemcpyAsync(maps_dev, maps.data(), sizeof(MapDev) * K, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    CsrPtrs *dtab = sc.get<CsrPtrs>(K);
+    int64_t *doff = sc.get<int64_t>(K + 1);
+    int32_t *brp = sc.get<int32_t>((size_t)N + 1), *bci = sc.get<int32_t>((size_t)ktot);
+    double *bv = sc.get<double>((size_t)ktot);
+    int32_t *kcp = sc.get<int32_t>((size_t)N + 1), *kri = sc.get<int32_t>((size_t)ktot);
+    double *kcv = sc.get<double>((size_t)ktot);
+    int32_t *ish = sc.get<int32_t>((size_t)N * kICap), *icnt = sc.get<int32_t>((size_t)N);
+    uint8_t *bin = sc.get<uint8_t>((size_t)N);
+    int32_t *work = sc.get<int32_t>((size_t)N);
+    int32_t *bin_off = sc.get<int32_t>(kNumBins + 1), *tickets = sc.get<int32_t>(kNumBins);
+    if (!d_st) d_st = sc.get<int32_t>((size_t)N);
+    if (!d_r2) d_r2 = sc.get<double>((size_t)N);
+    if (!dtab || !doff || !brp || !bci || !bv || !kcp || !kri || !kcv || !ish || !icnt || !bin || !work ||
+        !bin_off || !tickets || !d_st || !d_r2)
+        return SAM_ERR_OOM;
+    cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * K, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, st);
+    if (concat_block_diag(h, K, n, dtab, doff, brp, bci, bv) != cudaSuccess) return SAM_ERR_CUDA;
+    if (csr_to_csc(h, (int)N, ktot, brp, bci, bv, kcp, kri, kcv, nullptr) != cudaSuccess) return SAM_ERR_CUDA;
+    // shadow rows, size classes, work list
+    if (shadow_and_bins(h, (int)N, kcp, kri, g->jcp, g->jri, ish, icnt, bin, d_st) != cudaSuccess)
         return SAM_ERR_CUDA;
-    if (build_work_lists(h, K, n, bins.data(), work, bin_off) != cudaSuccess) return SAM_ERR_CUDA;
+    if (build_work_list(h, (int)N, bin, work, bin_off) != cudaSuccess) return SAM_ERR_CUDA;
     cudaMemsetAsync(d_v, 0, sizeof(double) * (size_t)total_nnz, st);
-    cudaMemsetAsync(d_r2, 0, sizeof(double) * (size_t)K * n, st);
-    if (launch_lsq(h, precision, refine_steps, 0, maps_dev, zcp, zri, zcv, work, bin_off, tickets) != cudaSuccess)
-        return SAM_ERR_CUDA;
+    cudaMemsetAsync(d_r2, 0, sizeof(double) * (size_t)N, st);
+    LsqArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.kcp = kcp;
+    a.kri = kri;
+    a.kcv = kcv;
+    a.jcp = g->jcp;
+    a.jri = g->jri;
+    a.ish = ish;
+    a.icnt = icnt;
+    a.zcp = zcp;
+    a.zri = zri;
+    a.zcv = zcv;
+    a.csr_pos = g->csr_pos;
+    a.mval = d_v;
+    a.colres = d_r2;
+    a.colstat = d_st;
+    a.work = work;
+    a.bin_off = bin_off;
+    a.ticket = tickets;
+    a.refine_steps = refine_steps;
+    if (launch_lsq(h, precision, a) != cudaSuccess) return SAM_ERR_CUDA;
     // CSR structure of every map
-    for (int k = 0; k < K; ++k) {
-        cudaMemcpyAsync(d_rp + (size_t)k * (n + 1), S[k]->mrp, sizeof(int32_t) * ((size_t)n + 1),
-                        cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(d_ci + M_offsets[k], S[k]->mci, sizeof(int32_t) * (size_t)S[k]->nnz, cudaMemcpyDeviceToDevice,
-                        st);
-    }
-    if (status_reduce(h, d_st, (int64_t)K * n, h->d_flag) != cudaSuccess) return SAM_ERR_CUDA;
+    if (split_map_structure(h, K, n, g->mrp, g->mci, d_rp, d_ci) != cudaSuccess) return SAM_ERR_CUDA;
+    if (status_reduce(h, d_st, N, h->d_flag) != cudaSuccess) return SAM_ERR_CUDA;
     double *fro_dev = nullptr;
     if (fro) {
         fro_dev = sc.get<double>((size_t)K);
         if (!fro_dev) return SAM_ERR_OOM;
-        for (int k = 0; k < K; ++k)
-            if (sum_f64(h, d_r2 + (size_t)k * n, n, fro_dev + k, false) != cudaSuccess) return SAM_ERR_CUDA;
+        if (segmented_sum_f64(h, d_r2, K, n, fro_dev, false) != cudaSuccess) return SAM_ERR_CUDA;
     }
     if (sg.finish() != cudaSuccess) return SAM_ERR_CUDA;
     if (fro) {
@@ -585,14 +755,15 @@ sam_status sam_build(sam_handle h, const sam_csr *A_k, const sam_csr *A_0, sam_p
 
 sam_status sam_residual(sam_handle h, const sam_csr *A_k, const sam_csr *M_k, const sam_csr *A_0, double *fro,
                         double *rel) {
-    if (!h || check_csr_arg(A_k, true) || check_csr_arg(M_k, true) || check_csr_arg(A_0, true)) return SAM_ERR_INVALID_ARG;
+    if (!h || check_csr_arg(A_k, true) || check_csr_arg(M_k, true) || check_csr_arg(A_0, true))
+        return SAM_ERR_INVALID_ARG;
     const int n = A_k->n;
     if (M_k->n != n || A_0->n != n) return SAM_ERR_INVALID_ARG;
     Scratch sc(h);
     Stager sg(sc, h->stream);
     DevCsr a = stage_csr(sg, A_k, true), m = stage_csr(sg, M_k, true), z = stage_csr(sg, A_0, true);
     if (sg.failed) return SAM_ERR_OOM;
-    sam_status s = validate_all(h, {a, m, z});
+    sam_status s = validate_all(h, sc, {a, m, z});
     if (s != SAM_OK) return s;
     double *rr = sc.get<double>((size_t)n), *out = sc.get<double>(2);
     if (!rr || !out) return SAM_ERR_OOM;
@@ -616,7 +787,7 @@ sam_status sam_apply(sam_handle h, const sam_csr *M_k, const double *x, double *
     const double *dx = sg.in(x, (size_t)n);
     double *dy = sg.out(y, (size_t)n);
     if (sg.failed) return SAM_ERR_OOM;
-    sam_status s = validate_all(h, {m});
+    sam_status s = validate_all(h, sc, {m});
     if (s != SAM_OK) return s;
     if (csr_spmv(h, n, m.rp, m.ci, m.v, dx, dy) != cudaSuccess) return SAM_ERR_CUDA;
     if (sg.finish() != cudaSuccess) return SAM_ERR_CUDA;
@@ -625,10 +796,10 @@ sam_status sam_apply(sam_handle h, const sam_csr *M_k, const double *x, double *
 }
 
 sam_status sam_build_backward(sam_handle h, const sam_csr *A_k, const sam_csr *A_0, sam_pattern S, int precision,
-                              int refine_steps, const double *M_val, const double *dM_val, double *dA_k_val,
-                              double *dA_0_val) {
-    (void)h; (void)A_k; (void)A_0; (void)S; (void)precision; (void)refine_steps;
-    (void)M_val; (void)dM_val; (void)dA_k_val; (void)dA_0_val;
+                              int refine_steps, const double *M_val, const double *dM_val, double resid_weight,
+                              double *dA_k_val, double *dA_0_val, double *dM_resid) {
+    (void)h; (void)A_k; (void)A_0; (void)S; (void)precision; (void)refine_steps; (void)M_val; (void)dM_val;
+    (void)resid_weight; (void)dA_k_val; (void)dA_0_val; (void)dM_resid;
     return SAM_ERR_UNSUPPORTED;
 }
 

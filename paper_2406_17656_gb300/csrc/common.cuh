@@ -1,12 +1,14 @@
 // common.cuh -- internal declarations shared by the libsam translation units.
 //
 // Layout conventions (device memory):
-//   * A matrix enters as CSR (row_ptr i32[n+1], col_idx i32[nnz], val f64[nnz]).
-//     The kernels read it by columns, so every source matrix is transposed
-//     once per call into CSC (cp i32[n+1], ri i32[nnz], cv f64[nnz]).
-//   * A map pattern S is stored in CSC: column j of the map has rows J_j
-//     (ascending).  The CSR structure of the map (its transpose) is kept
-//     alongside with csr_pos[e] = CSR position of CSC entry e.
+//   * A batch of K maps of order n is handled as ONE block-diagonal problem
+//     of order N = K n: map k's rows and columns are [k n, (k+1) n) of the
+//     "big" arrays.  Source matrices enter as CSR and are concatenated into
+//     the block-diagonal CSR, then transposed once into CSC
+//     (cp i32[N+1], ri i32[nnz], cv f64[nnz]) because the kernels read columns.
+//   * A map pattern is stored in CSC: column j has rows J_j (ascending).  The
+//     CSR structure of the map (its transpose) is kept alongside, with
+//     csr_pos[e] = CSR position of CSC entry e.
 //   * Shadow rows I_j are stored padded: ish[j * kICap + t], t < icnt[j].
 #pragma once
 
@@ -31,46 +33,41 @@ constexpr int kStRank = SAM_ERR_RANK_DEFICIENT;
 constexpr int kStNonfinite = SAM_ERR_NONFINITE;
 constexpr int kStUnsupported = SAM_ERR_UNSUPPORTED;
 
-struct Csc {
-    int n = 0;
-    int64_t nnz = 0;
-    int32_t *cp = nullptr;  // [n+1]
-    int32_t *ri = nullptr;  // [nnz]
-    double *cv = nullptr;   // [nnz] (may be null for structure-only)
+// Source CSR of one map (device pointers) for the batch concatenation.
+struct CsrPtrs {
+    const int32_t *rp;
+    const int32_t *ci;
+    const double *v;
 };
 
-// Everything one map's least-squares launch needs (device pointers).
-struct MapDev {
-    const int32_t *kcp, *kri;  // CSC of A_k
-    const double *kcv;
-    const int32_t *jcp, *jri;  // pattern J (CSC)
-    const int32_t *ish;        // shadow rows, padded [n][kICap]
-    const int32_t *icnt;       // |I_j|
-    const int32_t *csr_pos;    // CSC entry of the pattern -> CSR position of the map
-    double *mval;              // map values, CSR order
-    double *colres;            // per-column residual^2 (+ out-of-shadow part)
-    int32_t *colstat;          // per-column status
-    // adjoint only
-    const double *dmval;       // dL/dM in CSR order
-    double *dB;                // per-entry contributions (see adjoint.cu)
-    const int64_t *dB_off;     // per-column offset into dB
-    double *dzval;             // dL/dA_0 values in CSC(A_0) order
-};
-
+// Arguments of the least-squares launches (all device pointers, big arrays).
 struct LsqArgs {
-    const MapDev *maps;       // [K]
-    const int32_t *zcp, *zri; // CSC of A_0 (shared by every map)
+    int n;                       // order of one map (A_0)
+    const int32_t *kcp, *kri;    // CSC of the block-diagonal source
+    const double *kcv;
+    const int32_t *jcp, *jri;    // pattern (CSC, big)
+    const int32_t *ish, *icnt;   // shadow rows (padded) and counts
+    const int32_t *zcp, *zri;    // CSC of the target A_0 (order n)
     const double *zcv;
-    const int2 *work;         // (map, column) items of this size class
-    const int32_t *work_count;// device scalar: number of items
-    int32_t *ticket;          // device scalar: persistent-loop work counter (zeroed before launch)
+    const int32_t *csr_pos;      // pattern CSC entry -> map CSR position
+    double *mval;                // map values, CSR order of the block-diagonal map
+    double *colres;              // per-column residual^2 (+ out-of-shadow part)
+    int32_t *colstat;            // per-column status
+    const int32_t *work;         // columns grouped by size class
+    const int32_t *bin_off;      // [kNumBins+1] offsets into work
+    int32_t *ticket;             // [kNumBins] persistent-loop counters (zeroed before launch)
     int refine_steps;
-    int mode;                 // 0 forward, 1 adjoint
+    // adjoint
+    const double *dmval;         // dL/dM, CSR order (nullable)
+    double resid_weight;         // weight of ||A_k M - A_0||_F^2 in the loss
+    double *dB;                  // per-column dL/dB entries (gather order)
+    const int64_t *dB_off;       // [N+1] offsets of each column's entries in dB
+    double *dzval;               // dL/dA_0 contributions, CSC(A_0) order per map [K][nnz(A_0)]
+    double *dmres;               // dL/dM direct residual part, CSC order of the pattern (nullable)
+    int64_t znnz;                // nnz(A_0)
 };
 
 // --------------------------------------------------------------- helpers
-
-__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 template <typename T>
 __device__ __forceinline__ T shfl_xor(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
@@ -78,7 +75,7 @@ template <typename T>
 __device__ __forceinline__ T shfl(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
 // ------------------------------------------------------- host-side helpers
-// (implemented in symbolic.cu; all asynchronous on `st`)
+// (all asynchronous on the handle's stream unless noted)
 
 // Scratch memory from the handle's stream-ordered pool.
 void *pool_alloc(sam_handle h, size_t bytes);
@@ -91,43 +88,42 @@ void count_launch(sam_handle h, int n = 1);
 void profile_begin(sam_handle h, int bin);
 void profile_end(sam_handle h, int bin);
 
-// out[0..n] = exclusive scan of in[0..n), out[n] = total (int32 and int64 variants)
+// out[0..n] = exclusive scan of in[0..n), out[n] = total
 cudaError_t exclusive_scan_i32(sam_handle h, const int32_t *in, int32_t *out, int64_t n);
 cudaError_t exclusive_scan_i64(sam_handle h, const int64_t *in, int64_t *out, int64_t n);
 
-// CSR structure checks; sets *flag to SAM_ERR_BAD_CSR on any violation.
-cudaError_t validate_csr(sam_handle h, int n, int64_t nnz, const int32_t *rp, const int32_t *ci, int32_t *flag);
+// CSR structure checks of K matrices of order n; sets *flag to SAM_ERR_BAD_CSR
+// on any violation.  mats/nnz are device arrays of K entries.
+cudaError_t validate_csr_batch(sam_handle h, int K, int n, const CsrPtrs *mats, const int64_t *nnz, int32_t *flag);
+
+// Concatenate K CSR matrices of order n into the block-diagonal CSR of order
+// K n.  nnz_off (device, [K+1]) = prefix of the nnz; values optional.
+cudaError_t concat_block_diag(sam_handle h, int K, int n, const CsrPtrs *mats, const int64_t *nnz_off,
+                              int32_t *rp, int32_t *ci, double *v);
 
 // CSR -> CSC transpose with sorted rows per column.  perm (nullable) gets the
 // CSR index of every CSC entry; val / cv may be null.
 cudaError_t csr_to_csc(sam_handle h, int n, int64_t nnz, const int32_t *rp, const int32_t *ci,
                        const double *val, int32_t *cp, int32_t *ri, double *cv, int32_t *perm);
 
-// Level pattern (CSC) of A given by its CSC structure (kcp, kri).  Allocates
-// *jcp / *jri from the pool; synchronises once to size the result.
-sam_status level_pattern(sam_handle h, int n, const int32_t *kcp, const int32_t *kri, int level,
+// Level-L pattern (CSC) of the matrix with CSC structure (kcp, kri), order N.
+// Allocates *jcp / *jri from the pool; synchronises once to size the result.
+sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t *kri, int64_t nnz, int level,
                          int32_t **jcp, int32_t **jri, int64_t *nnz_out);
 
-// Batched variant: K structures, one synchronisation.
-sam_status level_pattern_batched(sam_handle h, int K, int n, const int32_t *const *kcp,
-                                 const int32_t *const *kri, int level, int32_t **jcp, int32_t **jri,
-                                 int64_t *nnz_out);
+// Shadow rows (padded), |I_j| and size class of every column.
+cudaError_t shadow_and_bins(sam_handle h, int N, const int32_t *kcp, const int32_t *kri, const int32_t *jcp,
+                            const int32_t *jri, int32_t *ish, int32_t *icnt, uint8_t *bin, int32_t *colstat);
 
-// Shadow rows (padded) + size class of every column of one map.
-cudaError_t shadow_and_bins(sam_handle h, int n, const int32_t *kcp, const int32_t *kri, const int32_t *jcp,
-                            const int32_t *jri, int precision, int32_t *ish, int32_t *icnt, uint8_t *bin,
-                            int32_t *colstat);
+// Work list: columns grouped by size class; bin_off (device, [kNumBins+1]).
+cudaError_t build_work_list(sam_handle h, int N, const uint8_t *bin, int32_t *work, int32_t *bin_off);
 
-// Work lists: items (map, col) grouped by bin; bin_off (device, [kNumBins+1])
-cudaError_t build_work_lists(sam_handle h, int K, int n, const uint8_t *const *bins_dev_of_map,
-                             int2 *work, int32_t *bin_off);
+// Least-squares launches for every size class.
+cudaError_t launch_lsq(sam_handle h, int precision, const LsqArgs &args);
+cudaError_t launch_adjoint(sam_handle h, const LsqArgs &args);
 
-// Least-squares launches for every size class over the work lists.
-cudaError_t launch_lsq(sam_handle h, int precision, int refine_steps, int mode, const MapDev *maps_dev,
-                       const int32_t *zcp, const int32_t *zri, const double *zcv, const int2 *work,
-                       const int32_t *bin_off, int32_t *tickets);
-
-// Deterministic sums.
+// Deterministic sums: out[k] = sum of x[k*seg .. (k+1)*seg) (squares optional).
+cudaError_t segmented_sum_f64(sam_handle h, const double *x, int K, int64_t seg, double *out, bool squares);
 cudaError_t sum_f64(sam_handle h, const double *x, int64_t n, double *out_dev, bool squares);
 cudaError_t csr_spmv(sam_handle h, int n, const int32_t *rp, const int32_t *ci, const double *v, const double *x,
                      double *y);
@@ -136,5 +132,10 @@ cudaError_t residual_rows(sam_handle h, int n, const int32_t *krp, const int32_t
                           const int32_t *zci, const double *zv, double *row_r2, int32_t *flag);
 cudaError_t status_reduce(sam_handle h, const int32_t *colstat, int64_t n, int32_t *flag);
 cudaError_t peak_fma(sam_handle h, double ms, double *f32, double *f64);
+
+// Split the block-diagonal map CSR into per-map CSR arrays (row pointers
+// rebased to each map's offset, column indices shifted back by k n).
+cudaError_t split_map_structure(sam_handle h, int K, int n, const int32_t *mrp_big, const int32_t *mci_big,
+                                int32_t *rp_out, int32_t *ci_out);
 
 }  // namespace sam

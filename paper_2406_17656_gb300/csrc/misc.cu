@@ -30,6 +30,36 @@ __global__ void __launch_bounds__(kSumThreads) sum_partial_kernel(const double *
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
+// segment k of length seg: blocks (b, k) sum fixed strided parts, then one
+// block per segment adds the partials in index order
+constexpr int kSegBlocks = 16;
+__global__ void __launch_bounds__(kSumThreads) seg_partial_kernel(const double *x, int64_t seg, bool squares,
+                                                                  double *part) {
+    __shared__ double sh[kSumThreads];
+    const int k = blockIdx.y;
+    const double *xs = x + (int64_t)k * seg;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kSumThreads + threadIdx.x; i < seg; i += (int64_t)kSegBlocks * kSumThreads) {
+        double v = xs[i];
+        s += squares ? v * v : v;
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kSumThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[k * kSegBlocks + blockIdx.x] = sh[0];
+}
+
+__global__ void seg_final_kernel(const double *part, int K, double *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    double s = 0.0;
+    for (int b = 0; b < kSegBlocks; ++b) s += part[k * kSegBlocks + b];
+    out[k] = s;
+}
+
 __global__ void __launch_bounds__(kSumBlocks) sum_final_kernel(const double *part, double *out) {
     __shared__ double sh[kSumBlocks];
     sh[threadIdx.x] = part[threadIdx.x];
@@ -216,6 +246,17 @@ cudaError_t sum_f64(sam_handle h, const double *x, int64_t n, double *out_dev, b
     count_launch(h);
     sum_final_kernel<<<1, kSumBlocks, 0, st>>>(part, out_dev);
     count_launch(h);
+    pool_free(h, part);
+    return cudaGetLastError();
+}
+
+cudaError_t segmented_sum_f64(sam_handle h, const double *x, int K, int64_t seg, double *out, bool squares) {
+    cudaStream_t st = handle_stream(h);
+    double *part = (double *)pool_alloc(h, sizeof(double) * (size_t)K * kSegBlocks);
+    if (!part) return cudaErrorMemoryAllocation;
+    seg_partial_kernel<<<dim3(kSegBlocks, (unsigned)K), kSumThreads, 0, st>>>(x, seg, squares, part);
+    seg_final_kernel<<<(K + 127) / 128, 128, 0, st>>>(part, K, out);
+    count_launch(h, 2);
     pool_free(h, part);
     return cudaGetLastError();
 }

@@ -1,5 +1,5 @@
 // symbolic.cu -- integer (bit-exact) part of SAM construction:
-//   * CSR validation and CSR -> CSC transposition,
+//   * CSR validation, block-diagonal concatenation of a batch, CSR -> CSC,
 //   * the level-L neighbour patterns of G(A) (Sec. 3 of arXiv 2406.17656):
 //     level 1 = column pattern of A plus the diagonal, level L+1 = union of
 //     the level-1 columns of every vertex in the level-L column (paths of
@@ -7,10 +7,12 @@
 //   * shadow rows I_j = union of the row patterns of A(:, c), c in J_j (the
 //     rows of the column least-squares problem of Sec. 2), and the size
 //     class ("bin") of every column problem,
-//   * the (map, column) work lists of each size class,
-//   * exclusive scans used by all of the above.
-// All kernels are bounded loops over their input; none waits on another
-// block.  Errors are reported through an int32 flag word, never by trapping.
+//   * the work list of each size class, exclusive scans.
+// Column unions are computed by one warp per column with a bitmap over the
+// column's index window [lo, hi] in shared memory (atomicOr, then popcount
+// prefix sums give the sorted, duplicate-free result); windows wider than
+// 65536 fall back to a bitonic sort of the concatenated candidates.  All
+// kernels are bounded loops; errors are reported through an int32 flag.
 #include <climits>
 #include <vector>
 
@@ -95,8 +97,11 @@ __global__ void __launch_bounds__(kScanThreads) scan_spine(T *sums, int64_t nt, 
     if (threadIdx.x == 0) *grand = carry;
 }
 
+// scan of each tile plus its offset; the last block also writes the total
+// to out[n]
 template <typename T>
-__global__ void __launch_bounds__(kScanThreads) scan_apply(const T *in, T *out, int64_t n, const T *offs) {
+__global__ void __launch_bounds__(kScanThreads) scan_apply(const T *in, T *out, int64_t n, const T *offs,
+                                                           const T *grand) {
     __shared__ T wt[32];
     __shared__ T tot;
     int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
@@ -113,10 +118,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply(const T *in, T *out, 
         if (base + q < n) out[base + q] = run;
         run += loc[q];
     }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = *grand;
 }
-
-template <typename T>
-__global__ void copy_scalar(const T *src, T *dst) { *dst = *src; }
 
 template <typename T>
 cudaError_t exclusive_scan_impl(sam_handle h, const T *in, T *out, int64_t n) {
@@ -126,13 +129,9 @@ cudaError_t exclusive_scan_impl(sam_handle h, const T *in, T *out, int64_t n) {
     T *sums = (T *)pool_alloc(h, sizeof(T) * (size_t)(nt + 1));
     if (!sums) return cudaErrorMemoryAllocation;
     scan_tile_sums<T><<<(unsigned)nt, kScanThreads, 0, st>>>(in, n, sums);
-    count_launch(h);
     scan_spine<T><<<1, kScanThreads, 0, st>>>(sums, nt, sums + nt);
-    count_launch(h);
-    scan_apply<T><<<(unsigned)nt, kScanThreads, 0, st>>>(in, out, n, sums);
-    count_launch(h);
-    copy_scalar<T><<<1, 1, 0, st>>>(sums + nt, out + n);
-    count_launch(h);
+    scan_apply<T><<<(unsigned)nt, kScanThreads, 0, st>>>(in, out, n, sums, sums + nt);
+    count_launch(h, 3);
     pool_free(h, sums);
     return cudaGetLastError();
 }
@@ -146,15 +145,19 @@ cudaError_t exclusive_scan_i64(sam_handle h, const int64_t *in, int64_t *out, in
     return exclusive_scan_impl<int64_t>(h, in, out, n);
 }
 
-// ------------------------------------------------------------- validation
+// --------------------------------------------- validation, concatenation
 
 namespace {
-__global__ void validate_csr_kernel(int n, int64_t nnz, const int32_t *rp, const int32_t *ci, int32_t *flag) {
+
+__global__ void validate_batch_kernel(int n, const CsrPtrs *mats, const int64_t *nnz, int32_t *flag) {
+    const int k = blockIdx.y;
+    const int32_t *rp = mats[k].rp, *ci = mats[k].ci;
+    const int64_t nz = nnz[k];
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0 && (rp[0] != 0 || (int64_t)rp[n] != nnz)) atomicCAS(flag, 0, SAM_ERR_BAD_CSR);
+    if (i == 0 && (rp[0] != 0 || (int64_t)rp[n] != nz)) atomicCAS(flag, 0, SAM_ERR_BAD_CSR);
     if (i >= n) return;
     int b = rp[i], e = rp[i + 1];
-    if (e < b || b < 0 || (int64_t)e > nnz) {
+    if (e < b || b < 0 || (int64_t)e > nz) {
         atomicCAS(flag, 0, SAM_ERR_BAD_CSR);
         return;
     }
@@ -168,12 +171,43 @@ __global__ void validate_csr_kernel(int n, int64_t nnz, const int32_t *rp, const
         prev = c;
     }
 }
+
+__global__ void concat_rows_kernel(int K, int n, const CsrPtrs *mats, const int64_t *nnz_off, int32_t *rp) {
+    const int k = blockIdx.y;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) rp[(int64_t)k * n + i] = mats[k].rp[i] + (int32_t)nnz_off[k];
+    if (k == K - 1 && i == n) rp[(int64_t)K * n] = (int32_t)nnz_off[K];
+}
+
+__global__ void concat_entries_kernel(int n, const CsrPtrs *mats, const int64_t *nnz_off, int32_t *ci, double *v) {
+    const int k = blockIdx.y;
+    const int64_t off = nnz_off[k], nz = nnz_off[k + 1] - off;
+    const int32_t *src = mats[k].ci;
+    const double *sv = mats[k].v;
+    const int32_t shift = (int32_t)((int64_t)k * n);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nz; e += (int64_t)gridDim.x * blockDim.x) {
+        ci[off + e] = src[e] + shift;
+        if (v) v[off + e] = sv[e];
+    }
+}
+
 }  // namespace
 
-cudaError_t validate_csr(sam_handle h, int n, int64_t nnz, const int32_t *rp, const int32_t *ci, int32_t *flag) {
-    int blocks = (n + 255) / 256;
-    validate_csr_kernel<<<blocks > 0 ? blocks : 1, 256, 0, handle_stream(h)>>>(n, nnz, rp, ci, flag);
+cudaError_t validate_csr_batch(sam_handle h, int K, int n, const CsrPtrs *mats, const int64_t *nnz, int32_t *flag) {
+    dim3 grid((unsigned)((n + 1 + 255) / 256), (unsigned)K);
+    validate_batch_kernel<<<grid, 256, 0, handle_stream(h)>>>(n, mats, nnz, flag);
     count_launch(h);
+    return cudaGetLastError();
+}
+
+cudaError_t concat_block_diag(sam_handle h, int K, int n, const CsrPtrs *mats, const int64_t *nnz_off, int32_t *rp,
+                              int32_t *ci, double *v) {
+    cudaStream_t st = handle_stream(h);
+    dim3 g1((unsigned)((n + 1 + 255) / 256), (unsigned)K);
+    concat_rows_kernel<<<g1, 256, 0, st>>>(K, n, mats, nnz_off, rp);
+    dim3 g2((unsigned)(handle_sms(h) * 4 / K + 1), (unsigned)K);
+    concat_entries_kernel<<<g2, 256, 0, st>>>(n, mats, nnz_off, ci, v);
+    count_launch(h, 2);
     return cudaGetLastError();
 }
 
@@ -186,26 +220,58 @@ __global__ void count_cols_kernel(int64_t nnz, const int32_t *ci, int32_t *cnt) 
         atomicAdd(&cnt[ci[e]], 1);
 }
 
-// one warp per row; positions claimed with atomics, ordered afterwards
+// positions claimed with atomics (8 lanes per row), ordered afterwards
 __global__ void fill_cols_kernel(int n, const int32_t *rp, const int32_t *ci, const double *val, int32_t *cursor,
                                  int32_t *ri, double *cv, int32_t *perm) {
-    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (w >= n) return;
-    int row = (int)w;
-    for (int e = rp[row] + lane; e < rp[row + 1]; e += 32) {
+    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    int sub = threadIdx.x & 7;
+    if (row >= n) return;
+    for (int e = rp[row] + sub; e < rp[row + 1]; e += 8) {
         int p = atomicAdd(&cursor[ci[e]], 1);
-        ri[p] = row;
+        ri[p] = (int)row;
         if (cv) cv[p] = val[e];
         if (perm) perm[p] = e;
     }
 }
 
-// insertion sort of each column segment by row index (rows are unique)
+// one warp per column: bitonic sort of the (row, value, perm) triples of a
+// segment of up to 32 entries in registers; longer segments fall back to an
+// insertion sort by lane 0
 __global__ void sort_cols_kernel(int n, const int32_t *cp, int32_t *ri, double *cv, int32_t *perm) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (c >= n) return;
-    int b = cp[c], e = cp[c + 1];
+    const int b = cp[c], e = cp[c + 1], len = e - b;
+    if (len <= 1) return;
+    if (len <= 32) {
+        int key = (lane < len) ? ri[b + lane] : INT_MAX;
+        double v = (cv && lane < len) ? cv[b + lane] : 0.0;
+        int p = (perm && lane < len) ? perm[b + lane] : 0;
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const int ok = __shfl_xor_sync(0xffffffffu, key, j);
+                const double ov = __shfl_xor_sync(0xffffffffu, v, j);
+                const int op = __shfl_xor_sync(0xffffffffu, p, j);
+                const bool up = (lane & k) == 0;
+                const bool low = (lane & j) == 0;
+                const bool take = low ? (up ? ok < key : ok > key) : (up ? ok > key : ok < key);
+                if (take) {
+                    key = ok;
+                    v = ov;
+                    p = op;
+                }
+            }
+        }
+        if (lane < len) {
+            ri[b + lane] = key;
+            if (cv) cv[b + lane] = v;
+            if (perm) perm[b + lane] = p;
+        }
+        return;
+    }
+    if (lane != 0) return;
     for (int t = b + 1; t < e; ++t) {
         int key = ri[t];
         double kv = cv ? cv[t] : 0.0;
@@ -234,7 +300,7 @@ cudaError_t csr_to_csc(sam_handle h, int n, int64_t nnz, const int32_t *rp, cons
     if (err != cudaSuccess) return err;
     if (nnz > 0) {
         int64_t blocks = (nnz + 255) / 256;
-        if (blocks > 65535 * 4) blocks = 65535 * 4;
+        if (blocks > (int64_t)handle_sms(h) * 32) blocks = (int64_t)handle_sms(h) * 32;
         count_cols_kernel<<<(unsigned)blocks, 256, 0, st>>>(nnz, ci, cnt);
         count_launch(h);
     }
@@ -243,60 +309,27 @@ cudaError_t csr_to_csc(sam_handle h, int n, int64_t nnz, const int32_t *rp, cons
     err = cudaMemcpyAsync(cnt, cp, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
     if (err != cudaSuccess) return err;
     if (n > 0) {
-        int64_t threads = (int64_t)n * 32;
+        int64_t threads = (int64_t)n * 8;
         fill_cols_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(n, rp, ci, val, cnt, ri, cv, perm);
-        count_launch(h);
-        sort_cols_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, cp, ri, val ? cv : nullptr, perm);
-        count_launch(h);
+        int64_t wthreads = (int64_t)n * 32;
+        sort_cols_kernel<<<(unsigned)((wthreads + 255) / 256), 256, 0, st>>>(n, cp, ri, val ? cv : nullptr, perm);
+        count_launch(h, 2);
     }
     pool_free(h, cnt);
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------- level patterns
+// ----------------------------------------------------------- column unions
 
 namespace {
 
-// Level 0/1 columns: J_j = {j} (level 0) or rows of A(:, j) plus j (level 1).
-__global__ void level01_count(int n, const int32_t *kcp, const int32_t *kri, int level, int32_t *cnt) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    if (level == 0) {
-        cnt[j] = 1;
-        return;
-    }
-    int b = kcp[j], e = kcp[j + 1], has = 0;
-    for (int t = b; t < e; ++t) has |= (kri[t] == j);
-    cnt[j] = e - b + (has ? 0 : 1);
-}
-
-__global__ void level01_fill(int n, const int32_t *kcp, const int32_t *kri, int level, const int32_t *jcp,
-                             int32_t *jri) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    int o = jcp[j];
-    if (level == 0) {
-        jri[o] = j;
-        return;
-    }
-    int b = kcp[j], e = kcp[j + 1];
-    bool placed = false;
-    for (int t = b; t < e; ++t) {
-        int r = kri[t];
-        if (!placed && r >= j) {
-            if (r != j) jri[o++] = j;
-            placed = true;
-        }
-        jri[o++] = r;
-    }
-    if (!placed) jri[o++] = j;
-}
-
 constexpr int kMergeWarps = 4;
-constexpr int kMergeBuf = 2048;  // candidate capacity per column (ints)
+constexpr int kBitWords = 2048;  // bitmap window of 65536 indices per warp
+constexpr int kMergeBuf = 2048;  // fallback candidate buffer (shares the storage)
 
-// Warp-cooperative sort + unique of buf[0..cnt), cnt <= kMergeBuf.  Returns
-// the number of distinct values, left ascending in buf[0..u).
+// Warp-cooperative sort + unique of buf[0..cnt), cnt <= kMergeBuf (fallback
+// path for wide windows).  Returns the number of distinct values, left
+// ascending in buf[0..u).
 __device__ int warp_sort_unique(int *buf, int cnt) {
     const int lane = threadIdx.x & 31;
     int p2 = 32;
@@ -336,19 +369,87 @@ __device__ int warp_sort_unique(int *buf, int cnt) {
     return u;
 }
 
-// Gather the candidate rows of column j: the concatenation of X(:, l) for l
-// in Y(:, j).  Returns the candidate count (may exceed kMergeBuf, in which
-// case the buffer content is incomplete).
-__device__ int gather_candidates(int j, const int32_t *xcp, const int32_t *xri, const int32_t *ycp,
-                                 const int32_t *yri, int *buf) {
+struct UnionResult {
+    int count;  // distinct entries (-1: too many candidates for the fallback)
+    int total;  // candidates, i.e. the sum of the list lengths
+};
+
+// Union of the sorted lists X(:, l), l in Y(:, j).  The distinct values are
+// written ascending to out[0..min(count, cap)) when out != nullptr.  Every
+// lane returns the same result.
+__device__ UnionResult warp_union(int j, const int32_t *xcp, const int32_t *xri, const int32_t *ycp,
+                                  const int32_t *yri, unsigned *bm, int32_t *out, int cap) {
     const int lane = threadIdx.x & 31;
-    int yb = ycp[j], ye = ycp[j + 1];
-    int total = 0;
+    const int yb = ycp[j], ye = ycp[j + 1];
+    int lo = INT_MAX, hi = INT_MIN, total = 0;
+    for (int t = yb + lane; t < ye; t += 32) {
+        const int l = yri[t];
+        const int b = xcp[l], e = xcp[l + 1];
+        if (e > b) {
+            lo = min(lo, xri[b]);
+            hi = max(hi, xri[e - 1]);
+            total += e - b;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        total += __shfl_xor_sync(0xffffffffu, total, o);
+    }
+    UnionResult res{0, total};
+    if (total == 0) return res;
+    const int64_t span = (int64_t)hi - lo + 1;
+    if (span <= (int64_t)kBitWords * 32) {
+        const int words = (int)((span + 31) >> 5);
+        for (int w = lane; w < words; w += 32) bm[w] = 0u;
+        __syncwarp();
+        for (int t = yb + lane; t < ye; t += 32) {
+            const int l = yri[t];
+            const int e = xcp[l + 1];
+            for (int q = xcp[l]; q < e; ++q) {
+                const int x = xri[q] - lo;
+                atomicOr(&bm[x >> 5], 1u << (x & 31));
+            }
+        }
+        __syncwarp();
+        const int wpl = (words + 31) >> 5;
+        const int w0 = lane * wpl, w1 = min(words, w0 + wpl);
+        int cnt = 0;
+        for (int w = w0; w < w1; ++w) cnt += __popc(bm[w]);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        res.count = __shfl_sync(0xffffffffu, incl, 31);
+        if (out) {
+            int pos = incl - cnt;
+            for (int w = w0; w < w1 && pos < cap; ++w) {
+                unsigned bits = bm[w];
+                while (bits && pos < cap) {
+                    const int bit = __ffs(bits) - 1;
+                    out[pos++] = lo + (w << 5) + bit;
+                    bits &= bits - 1u;
+                }
+            }
+        }
+        __syncwarp();
+        return res;
+    }
+    // wide window: concatenate the candidates and sort
+    if (total > kMergeBuf) {
+        res.count = -1;
+        return res;
+    }
+    int *buf = (int *)bm;
+    int off = 0;
     for (int base = yb; base < ye; base += 32) {
-        int t = base + lane;
+        const int t = base + lane;
         int xb = 0, len = 0;
         if (t < ye) {
-            int l = yri[t];
+            const int l = yri[t];
             xb = xcp[l];
             len = xcp[l + 1] - xb;
         }
@@ -358,151 +459,82 @@ __device__ int gather_candidates(int j, const int32_t *xcp, const int32_t *xri, 
             int y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        int off = total + incl - len;
-        int chunk = __shfl_sync(0xffffffffu, incl, 31);
-        if (off + len <= kMergeBuf)
-            for (int q = 0; q < len; ++q) buf[off + q] = xri[xb + q];
-        total += chunk;
+        for (int q = 0; q < len; ++q) buf[off + incl - len + q] = xri[xb + q];
+        off += __shfl_sync(0xffffffffu, incl, 31);
     }
     __syncwarp();
-    return total;
+    const int u = warp_sort_unique(buf, total);
+    res.count = u;
+    if (out)
+        for (int i = lane; i < u && i < cap; i += 32) out[i] = buf[i];
+    __syncwarp();
+    return res;
 }
 
-// mode 0: count distinct rows -> cnt[j] (-1 if the candidates overflow)
-// mode 1: write the distinct rows to out[optr[j] ...]
+// Level 0/1 columns: J_j = {j} (level 0) or rows of A(:, j) plus j (level 1).
+__global__ void level01_count(int n, const int32_t *kcp, const int32_t *kri, int level, int32_t *cnt) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    if (level == 0) {
+        cnt[j] = 1;
+        return;
+    }
+    int b = kcp[j], e = kcp[j + 1], has = 0;
+    for (int t = b; t < e; ++t) has |= (kri[t] == j);
+    cnt[j] = e - b + (has ? 0 : 1);
+}
+
+__global__ void level01_fill(int n, const int32_t *kcp, const int32_t *kri, int level, const int32_t *jcp,
+                             int32_t *jri) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int o = jcp[j];
+    if (level == 0) {
+        jri[o] = j;
+        return;
+    }
+    int b = kcp[j], e = kcp[j + 1];
+    bool placed = false;
+    for (int t = b; t < e; ++t) {
+        int r = kri[t];
+        if (!placed && r >= j) {
+            if (r != j) jri[o++] = j;
+            placed = true;
+        }
+        jri[o++] = r;
+    }
+    if (!placed) jri[o++] = j;
+}
+
+// mode 0: count distinct rows -> cnt[j]; mode 1: write them to out + optr[j]
 __global__ void __launch_bounds__(kMergeWarps * 32) product_pattern_kernel(
     int n, const int32_t *xcp, const int32_t *xri, const int32_t *ycp, const int32_t *yri, int mode,
     int32_t *cnt, const int32_t *optr, int32_t *out, int32_t *flag) {
-    __shared__ int bufs[kMergeWarps][kMergeBuf];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *buf = bufs[warp];
+    __shared__ unsigned bms[kMergeWarps][kBitWords];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned *bm = bms[warp];
     for (int64_t j = (int64_t)blockIdx.x * kMergeWarps + warp; j < n; j += (int64_t)gridDim.x * kMergeWarps) {
-        int total = gather_candidates((int)j, xcp, xri, ycp, yri, buf);
-        if (total > kMergeBuf) {
-            if (lane == 0) {
+        int32_t *dst = (mode == 1) ? out + optr[j] : nullptr;
+        UnionResult r = warp_union((int)j, xcp, xri, ycp, yri, bm, dst, INT_MAX);
+        if (lane == 0) {
+            if (r.count < 0) {
                 if (mode == 0) cnt[j] = 0;
                 atomicCAS(flag, 0, SAM_ERR_UNSUPPORTED);
+            } else if (mode == 0) {
+                cnt[j] = r.count;
             }
-            continue;
         }
-        int u = warp_sort_unique(buf, total);
-        if (mode == 0) {
-            if (lane == 0) cnt[j] = u;
-        } else {
-            int o = optr[j];
-            for (int i = lane; i < u; i += 32) out[o + i] = buf[i];
-        }
-        __syncwarp();
     }
 }
 
 int merge_grid(sam_handle h, int n) {
     int blocks = (n + kMergeWarps - 1) / kMergeWarps;
-    int cap = handle_sms(h) * 16;
+    int cap = handle_sms(h) * 12;
     return blocks < cap ? (blocks > 0 ? blocks : 1) : cap;
 }
 
-}  // namespace
-
-// Patterns for K structures at once; all count passes run before the single
-// synchronisation that sizes the outputs.
-sam_status level_pattern_batched(sam_handle h, int K, int n, const int32_t *const *kcp, const int32_t *const *kri,
-                                 int level, int32_t **jcp, int32_t **jri, int64_t *nnz_out) {
-    cudaStream_t st = handle_stream(h);
-    int32_t *flag = handle_flag(h);
-    int blocks = (n + 255) / 256;
-    if (blocks < 1) blocks = 1;
-    // level-1 (or 0) patterns of every map: sizes are bounded by nnz + n, so
-    // they need no synchronisation
-    std::vector<int32_t *> l1cp(K, nullptr), l1ri(K, nullptr), cnt(K, nullptr);
-    for (int k = 0; k < K; ++k) {
-        int lv = level == 0 ? 0 : 1;
-        l1cp[k] = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)n + 1));
-        cnt[k] = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)n + 1));
-        if (!l1cp[k] || !cnt[k]) return SAM_ERR_OOM;
-        level01_count<<<blocks, 256, 0, st>>>(n, kcp[k], kri[k], lv, cnt[k]);
-        count_launch(h);
-        if (exclusive_scan_i32(h, cnt[k], l1cp[k], n) != cudaSuccess) return SAM_ERR_CUDA;
-    }
-    // the level-1 total is needed for its allocation: read all K at once
-    std::vector<int32_t> tot(K);
-    int32_t *tot_dev = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)K);
-    if (!tot_dev) return SAM_ERR_OOM;
-    for (int k = 0; k < K; ++k)
-        cudaMemcpyAsync(tot_dev + k, l1cp[k] + n, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
-    if (cudaMemcpyAsync(tot.data(), tot_dev, sizeof(int32_t) * (size_t)K, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-        return SAM_ERR_CUDA;
-    for (int k = 0; k < K; ++k) {
-        l1ri[k] = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)tot[k] + 1));
-        if (!l1ri[k]) return SAM_ERR_OOM;
-        level01_fill<<<blocks, 256, 0, st>>>(n, kcp[k], kri[k], level == 0 ? 0 : 1, l1cp[k], l1ri[k]);
-        count_launch(h);
-    }
-    if (level <= 1) {
-        for (int k = 0; k < K; ++k) {
-            jcp[k] = l1cp[k];
-            jri[k] = l1ri[k];
-            nnz_out[k] = tot[k];
-            pool_free(h, cnt[k]);
-        }
-        pool_free(h, tot_dev);
-        return cudaGetLastError() == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
-    }
-    // level L+1 = union of level-1 columns over the level-L column
-    std::vector<int32_t *> curcp = l1cp, curri = l1ri;
-    for (int lv = 2; lv <= level; ++lv) {
-        std::vector<int32_t *> nxcp(K), nxri(K);
-        for (int k = 0; k < K; ++k) {
-            nxcp[k] = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)n + 1));
-            if (!nxcp[k]) return SAM_ERR_OOM;
-            product_pattern_kernel<<<merge_grid(h, n), kMergeWarps * 32, 0, st>>>(
-                n, l1cp[k], l1ri[k], curcp[k], curri[k], 0, cnt[k], nullptr, nullptr, flag);
-            count_launch(h);
-            if (exclusive_scan_i32(h, cnt[k], nxcp[k], n) != cudaSuccess) return SAM_ERR_CUDA;
-            cudaMemcpyAsync(tot_dev + k, nxcp[k] + n, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
-        }
-        if (cudaMemcpyAsync(tot.data(), tot_dev, sizeof(int32_t) * (size_t)K, cudaMemcpyDeviceToHost, st) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            return SAM_ERR_CUDA;
-        for (int k = 0; k < K; ++k) {
-            nxri[k] = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)tot[k] + 1));
-            if (!nxri[k]) return SAM_ERR_OOM;
-            product_pattern_kernel<<<merge_grid(h, n), kMergeWarps * 32, 0, st>>>(
-                n, l1cp[k], l1ri[k], curcp[k], curri[k], 1, nullptr, nxcp[k], nxri[k], flag);
-            count_launch(h);
-            if (curcp[k] != l1cp[k]) {
-                pool_free(h, curcp[k]);
-                pool_free(h, curri[k]);
-            }
-        }
-        curcp = nxcp;
-        curri = nxri;
-    }
-    for (int k = 0; k < K; ++k) {
-        pool_free(h, l1cp[k]);
-        pool_free(h, l1ri[k]);
-        pool_free(h, cnt[k]);
-        jcp[k] = curcp[k];
-        jri[k] = curri[k];
-        nnz_out[k] = tot[k];
-    }
-    pool_free(h, tot_dev);
-    return cudaGetLastError() == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
-}
-
-sam_status level_pattern(sam_handle h, int n, const int32_t *kcp, const int32_t *kri, int level, int32_t **jcp,
-                         int32_t **jri, int64_t *nnz_out) {
-    return level_pattern_batched(h, 1, n, &kcp, &kri, level, jcp, jri, nnz_out);
-}
-
-// ------------------------------------------------------- shadows and bins
-
-namespace {
-
-// Size classes shared by both precisions: |I| <= bin_maxi, |J| <= bin_maxj,
-// nnz(B) <= 8 * bin_maxi.  Must match the tile table in lsq.cu.
+// Size classes: |I| <= bin_maxi, |J| <= bin_maxj, nnz(B) <= 8 * bin_maxi.
+// Must match the tile table in lsq.cu.
 __constant__ int c_bin_maxi[kNumBins] = {14, 26, 40, 52, 64};
 __constant__ int c_bin_maxj[kNumBins] = {5, 9, 23, 27, 27};
 
@@ -510,45 +542,39 @@ __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const i
                                                                   const int32_t *jcp, const int32_t *jri,
                                                                   int32_t *ish, int32_t *icnt, uint8_t *bin,
                                                                   int32_t *colstat) {
-    __shared__ int bufs[kMergeWarps][kMergeBuf];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *buf = bufs[warp];
+    __shared__ unsigned bms[kMergeWarps][kBitWords];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned *bm = bms[warp];
     for (int64_t j = (int64_t)blockIdx.x * kMergeWarps + warp; j < n; j += (int64_t)gridDim.x * kMergeWarps) {
-        int total = gather_candidates((int)j, kcp, kri, jcp, jri, buf);
-        int nj = jcp[j + 1] - jcp[j];
-        int u = -1;
-        if (total <= kMergeBuf) u = warp_sort_unique(buf, total);
-        int b = kBinNone;
-        if (u >= nj && u >= 0) {
-            for (int q = 0; q < kNumBins; ++q)
-                if (u <= c_bin_maxi[q] && nj <= c_bin_maxj[q] && total <= 8 * c_bin_maxi[q]) {
-                    b = q;
-                    break;
-                }
-        }
-        int uc = (u < 0) ? 0 : (u > kICap ? kICap : u);
-        for (int i = lane; i < uc; i += 32) ish[j * kICap + i] = buf[i];
+        UnionResult r = warp_union((int)j, kcp, kri, jcp, jri, bm, ish + j * kICap, kICap);
         if (lane == 0) {
-            icnt[j] = (u < 0) ? -1 : u;
+            const int nj = jcp[j + 1] - jcp[j];
+            const int u = r.count;
+            int b = kBinNone;
+            if (u >= nj && u >= 0)
+                for (int q = 0; q < kNumBins; ++q)
+                    if (u <= c_bin_maxi[q] && nj <= c_bin_maxj[q] && r.total <= 8 * c_bin_maxi[q]) {
+                        b = q;
+                        break;
+                    }
+            icnt[j] = u;
             bin[j] = (uint8_t)b;
             // fewer shadow rows than unknowns means a zero column: rank deficient
             colstat[j] = (b != kBinNone) ? kStOk : ((u >= 0 && u < nj) ? kStRank : kStUnsupported);
         }
-        __syncwarp();
     }
 }
 
 __global__ void bin_count_kernel(int n, const uint8_t *bin, int32_t *counts /* [kNumBins] */) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     int b = (j < n) ? bin[j] : kBinNone;
-    // warp-aggregated increments
     for (int q = 0; q < kNumBins; ++q) {
         unsigned m = __ballot_sync(0xffffffffu, b == q);
         if (m && (threadIdx.x & 31) == (__ffs(m) - 1)) atomicAdd(&counts[q], __popc(m));
     }
 }
 
-__global__ void bin_scatter_kernel(int n, int map, const uint8_t *bin, int32_t *cursor, int2 *work) {
+__global__ void bin_scatter_kernel(int n, const uint8_t *bin, int32_t *cursor, int32_t *work) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     int b = (j < n) ? bin[j] : kBinNone;
     int lane = threadIdx.x & 31;
@@ -559,7 +585,7 @@ __global__ void bin_scatter_kernel(int n, int map, const uint8_t *bin, int32_t *
         int base = 0;
         if (lane == leader) base = atomicAdd(&cursor[q], __popc(m));
         base = __shfl_sync(0xffffffffu, base, leader);
-        if (b == q) work[base + __popc(m & ((1u << lane) - 1u))] = make_int2(map, j);
+        if (b == q) work[base + __popc(m & ((1u << lane) - 1u))] = j;
     }
 }
 
@@ -577,31 +603,111 @@ __global__ void bin_offsets_kernel(const int32_t *counts, int32_t *off, int32_t 
 
 }  // namespace
 
-cudaError_t shadow_and_bins(sam_handle h, int n, const int32_t *kcp, const int32_t *kri, const int32_t *jcp,
-                            const int32_t *jri, int precision, int32_t *ish, int32_t *icnt, uint8_t *bin,
-                            int32_t *colstat) {
-    (void)precision;
-    shadow_kernel<<<merge_grid(h, n), kMergeWarps * 32, 0, handle_stream(h)>>>(n, kcp, kri, jcp, jri, ish, icnt,
-                                                                              bin, colstat);
+sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t *kri, int64_t nnz, int level,
+                         int32_t **jcp_out, int32_t **jri_out, int64_t *nnz_out) {
+    cudaStream_t st = handle_stream(h);
+    int32_t *flag = handle_flag(h);
+    const int blocks = (N + 255) / 256 > 0 ? (N + 255) / 256 : 1;
+    const int lv1 = level == 0 ? 0 : 1;
+    // level 1 (or 0): size bounded by nnz + N, no synchronisation needed
+    int32_t *cnt = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)N + 1));
+    int32_t *l1cp = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)N + 1));
+    int32_t *l1ri = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)(nnz + N + 1));
+    if (!cnt || !l1cp || !l1ri) return SAM_ERR_OOM;
+    level01_count<<<blocks, 256, 0, st>>>(N, kcp, kri, lv1, cnt);
+    count_launch(h);
+    if (exclusive_scan_i32(h, cnt, l1cp, N) != cudaSuccess) return SAM_ERR_CUDA;
+    level01_fill<<<blocks, 256, 0, st>>>(N, kcp, kri, lv1, l1cp, l1ri);
+    count_launch(h);
+    int32_t *curcp = l1cp, *curri = l1ri;
+    for (int lv = 2; lv <= level; ++lv) {
+        int32_t *nxcp = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)N + 1));
+        if (!nxcp) return SAM_ERR_OOM;
+        product_pattern_kernel<<<merge_grid(h, N), kMergeWarps * 32, 0, st>>>(N, l1cp, l1ri, curcp, curri, 0, cnt,
+                                                                              nullptr, nullptr, flag);
+        count_launch(h);
+        if (exclusive_scan_i32(h, cnt, nxcp, N) != cudaSuccess) return SAM_ERR_CUDA;
+        int32_t tot = 0;
+        if (cudaMemcpyAsync(&tot, nxcp + N, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return SAM_ERR_CUDA;
+        int32_t *nxri = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)tot + 1));
+        if (!nxri) return SAM_ERR_OOM;
+        product_pattern_kernel<<<merge_grid(h, N), kMergeWarps * 32, 0, st>>>(N, l1cp, l1ri, curcp, curri, 1, nullptr,
+                                                                              nxcp, nxri, flag);
+        count_launch(h);
+        if (curcp != l1cp) {
+            pool_free(h, curcp);
+            pool_free(h, curri);
+        }
+        curcp = nxcp;
+        curri = nxri;
+    }
+    int32_t tot = 0;
+    if (cudaMemcpyAsync(&tot, curcp + N, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    if (curcp != l1cp) {
+        pool_free(h, l1cp);
+        pool_free(h, l1ri);
+    }
+    pool_free(h, cnt);
+    *jcp_out = curcp;
+    *jri_out = curri;
+    *nnz_out = tot;
+    return cudaGetLastError() == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
+}
+
+cudaError_t shadow_and_bins(sam_handle h, int N, const int32_t *kcp, const int32_t *kri, const int32_t *jcp,
+                            const int32_t *jri, int32_t *ish, int32_t *icnt, uint8_t *bin, int32_t *colstat) {
+    shadow_kernel<<<merge_grid(h, N), kMergeWarps * 32, 0, handle_stream(h)>>>(N, kcp, kri, jcp, jri, ish, icnt, bin,
+                                                                              colstat);
     count_launch(h);
     return cudaGetLastError();
 }
 
-cudaError_t build_work_lists(sam_handle h, int K, int n, const uint8_t *const *bins, int2 *work, int32_t *bin_off) {
+cudaError_t build_work_list(sam_handle h, int N, const uint8_t *bin, int32_t *work, int32_t *bin_off) {
     cudaStream_t st = handle_stream(h);
     int32_t *tmp = (int32_t *)pool_alloc(h, sizeof(int32_t) * 2 * kNumBins);
     if (!tmp) return cudaErrorMemoryAllocation;
     int32_t *counts = tmp, *cursor = tmp + kNumBins;
     cudaMemsetAsync(counts, 0, sizeof(int32_t) * kNumBins, st);
-    int blocks = (n + 255) / 256;
-    if (blocks < 1) blocks = 1;
-    for (int k = 0; k < K; ++k) bin_count_kernel<<<blocks, 256, 0, st>>>(n, bins[k], counts);
-    count_launch(h, K);
+    const int blocks = (N + 255) / 256 > 0 ? (N + 255) / 256 : 1;
+    bin_count_kernel<<<blocks, 256, 0, st>>>(N, bin, counts);
     bin_offsets_kernel<<<1, 32, 0, st>>>(counts, bin_off, cursor);
-    count_launch(h);
-    for (int k = 0; k < K; ++k) bin_scatter_kernel<<<blocks, 256, 0, st>>>(n, k, bins[k], cursor, work);
-    count_launch(h, K);
+    bin_scatter_kernel<<<blocks, 256, 0, st>>>(N, bin, cursor, work);
+    count_launch(h, 3);
     pool_free(h, tmp);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------- per-map map structure
+
+namespace {
+__global__ void split_rows_kernel(int K, int n, const int32_t *mrp, int32_t *rp_out) {
+    const int k = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    rp_out[(int64_t)k * (n + 1) + i] = mrp[(int64_t)k * n + i] - mrp[(int64_t)k * n];
+}
+
+__global__ void split_cols_kernel(int n, int64_t N, const int32_t *mrp, const int32_t *mci, int32_t *ci_out) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int sub = threadIdx.x & 7;
+    if (row >= N) return;
+    const int32_t shift = (int32_t)((row / n) * n);
+    for (int e = mrp[row] + sub; e < mrp[row + 1]; e += 8) ci_out[e] = mci[e] - shift;
+}
+}  // namespace
+
+cudaError_t split_map_structure(sam_handle h, int K, int n, const int32_t *mrp_big, const int32_t *mci_big,
+                                int32_t *rp_out, int32_t *ci_out) {
+    cudaStream_t st = handle_stream(h);
+    dim3 g1((unsigned)((n + 1 + 255) / 256), (unsigned)K);
+    split_rows_kernel<<<g1, 256, 0, st>>>(K, n, mrp_big, rp_out);
+    const int64_t N = (int64_t)K * n;
+    if (N > 0) split_cols_kernel<<<(unsigned)((N * 8 + 255) / 256), 256, 0, st>>>(n, N, mrp_big, mci_big, ci_out);
+    count_launch(h, 2);
     return cudaGetLastError();
 }
 

@@ -79,7 +79,8 @@ _SIGS = [
      [_vp, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), _f64p, _f64p]),
     ("sam_apply", ctypes.c_int32, [_vp, ctypes.POINTER(sam_csr), _vp, _vp]),
     ("sam_build_backward", ctypes.c_int32,
-     [_vp, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]),
+     [_vp, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), _vp, ctypes.c_int, ctypes.c_int, _vp, _vp,
+      ctypes.c_double, _vp, _vp, _vp]),
     ("sam_tune", ctypes.c_int32,
      [_vp, ctypes.c_int, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(_vp), ctypes.c_int,
       ctypes.c_int, ctypes.c_char_p]),
@@ -349,8 +350,11 @@ class Handle:
         _check(load().sam_apply(self.ptr, ctypes.byref(m), _addr(x), _addr(y)), "sam_apply")
         return y
 
-    def sam_build_backward(self, A_k: Csr, A_0: Csr, S: Pattern, M_val, dM_val, precision="fp32r",
-                           refine_steps: int = 1, dA_k_val=None, dA_0_val=None):
+    def sam_build_backward(self, A_k: Csr, A_0: Csr, S: Pattern, M_val, dM_val=None, precision="fp32r",
+                           refine_steps: int = 1, resid_weight: float = 0.0, dA_k_val=None, dA_0_val=None,
+                           dM_resid=None):
+        """Gradients of <dM, M> + resid_weight ||A_k M - A_0||_F^2 with respect
+        to the values of A_k and A_0 (CSR orders); see include/sam.h."""
         import torch
 
         prec = PRECISIONS.get(precision, precision)
@@ -360,8 +364,8 @@ class Handle:
             dA_0_val = torch.empty(A_0.nnz, dtype=torch.float64, device="cuda")
         a, z = A_k.c(), A_0.c()
         _check(load().sam_build_backward(self.ptr, ctypes.byref(a), ctypes.byref(z), S.ptr, int(prec),
-                                         int(refine_steps), _addr(M_val), _addr(dM_val), _addr(dA_k_val),
-                                         _addr(dA_0_val)), "sam_build_backward")
+                                         int(refine_steps), _addr(M_val), _addr(dM_val), float(resid_weight),
+                                         _addr(dA_k_val), _addr(dA_0_val), _addr(dM_resid)), "sam_build_backward")
         return dA_k_val, dA_0_val
 
     def sam_profile(self, enable: bool):
