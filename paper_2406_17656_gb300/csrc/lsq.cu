@@ -36,8 +36,9 @@
 // ~u_32 kappa^2 ||r||/(||B|| ||m||) for problems with a nonzero residual, as
 // SAM columns have).  The FP64 products use the sparse B straight from
 // A_k's CSC values in a fixed order, so results are deterministic.  After
-// the last step the residual is ||r - B d||^2 = ||r||^2 - d.g (since
-// B^T B d = g), so no further FP64 pass over B is needed.  FP64->FP32
+// the last step the residual follows from the exact identity
+// ||r - B d||^2 = ||r||^2 - 2 d.g + ||B d||^2 with ||B d||^2 (a second-order
+// term) evaluated in FP32, so no further FP64 pass over B is needed.  FP64->FP32
 // conversions of the factorisation inputs truncate with integer operations,
 // leaving GB300's narrow FP64 pipe to the residual arithmetic.
 #include <cfloat>
@@ -271,7 +272,8 @@ struct SolveUpper {  // R x = y, k from high to low
 #pragma unroll
                 for (int q = 0; q <= Q; ++q) {
                     const int i = ll + q * P;
-                    if (i < k) x[q] = fma(-R[i * TL::RSTR + k], xk, x[q]);
+                    // rows of R at k >= n were never written: do not touch them
+                    if (i < k && k < n) x[q] = fma(-R[i * TL::RSTR + k], xk, x[q]);
                 }
             }
             SolveUpper<TL, Q - 1>::run(R, dinv, x, n, ll, gbase);
@@ -561,11 +563,29 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) lsq_kernel(LsqArgs args, 
                         dg = fma(d, g[q], dg);
                         mq[q] += d;
                         S.m[c] = mq[q];
+                        S.u.s.y[c] = x[q];
                     }
                 }
                 dg = group_sum<P>(dg);
                 __syncwarp();
-                r2 = rr - dg;  // ||r - B d||^2 with B^T B d = g
+                // ||B d||^2 in FP32 from the truncated entries (relative error
+                // ~1e-7 of a term that is already second order)
+                float bd2 = 0.f;
+#pragma unroll
+                for (int q = 0; q < TL::IQ; ++q) {
+                    const int i = ll + q * P;
+                    if (i < nI) {
+                        float v = 0.f;
+                        const int pe = S.u.s.rowstart[i + 1];
+                        for (int p = S.u.s.rowstart[i]; p < pe; ++p)
+                            v = fmaf(narrow_trunc(kcv[S.u.s.rowent[p]]), (float)S.u.s.y[S.u.s.rowcol[p]], v);
+                        bd2 = fmaf(v, v, bd2);
+                    }
+                }
+                bd2 = group_sum<P>(bd2);
+                __syncwarp();
+                // exact identity ||r - B d||^2 = ||r||^2 - 2 d.(B^T r) + ||B d||^2
+                r2 = rr - 2.0 * dg + to_f64<float>(bd2);
                 need_final = false;
             }
         }
