@@ -61,6 +61,8 @@ def _load():
                                      _i32p, _i32p, ctypes.c_int, _f64p, _f64p, _f64p]
             lib.so_build_cols.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p,
                                           _i32p, _i32p, ctypes.c_int, _i32p, ctypes.c_int, _f64p, _f64p, _f64p]
+            lib.so_adjoint.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p, _i32p, _i32p,
+                                       _f64p, _f64p, ctypes.c_double, _f64p, _f64p, _f64p]
             lib.so_residual.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p,
                                         _i32p, _i32p, _f64p, _f64p, _f64p]
             _lib = lib
@@ -180,6 +182,25 @@ def residual(Ak, colptr, rowidx, mval, A0):
     _check(st, "residual")
     fro = float(np.sqrt(fro2.value))
     return fro, fro / float(np.sqrt(a02.value))
+
+
+def adjoint(Ak, A0, colptr, rowidx, mval, gbar=None, rho=0.0, want_dmres=False):
+    """Gradients of sum(gbar * N) + rho ||A_k N - A_0||_F^2 with respect to
+    the stored values of A_k and A_0 (CSR orders), N the SAM on the pattern
+    with values mval (CSC order); gbar in CSC order or None.  Returns
+    (dA_k, dA_0[, dmres])."""
+    lib = _load()
+    n = int(Ak.n)
+    a = [_i32(Ak.indptr), _i32(Ak.indices), _f64(Ak.data), _i32(A0.indptr), _i32(A0.indices), _f64(A0.data),
+         _i32(colptr), _i32(rowidx), _f64(mval)]
+    g = _f64(gbar) if gbar is not None else (None, None)
+    dak = np.zeros(len(Ak.data), dtype=np.float64)
+    da0 = np.zeros(len(A0.data), dtype=np.float64)
+    dm = np.zeros(int(colptr[-1]), dtype=np.float64) if want_dmres else None
+    st = lib.so_adjoint(n, *(x[1] for x in a), g[1], float(rho), dak.ctypes.data_as(_f64p),
+                        da0.ctypes.data_as(_f64p), dm.ctypes.data_as(_f64p) if dm is not None else None)
+    _check(st, "adjoint")
+    return (dak, da0, dm) if want_dmres else (dak, da0)
 
 
 def apply(indptr, indices, data, x):

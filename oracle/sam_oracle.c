@@ -453,3 +453,136 @@ int so_residual(int n, const int *krp, const int *kci, const double *kv,
     *a02 = a0;
     return 0;
 }
+
+/*
+ * Adjoint of the SAM build on a fixed pattern (reverse-mode derivative of
+ * the column least-squares solutions of Sec. 2).  With the loss
+ *     L = sum over pattern entries of gbar * N  +  rho * ||A_k N - A_0||_F^2,
+ * and, per column j, B = A_k(I_j, J_j), c = A_0(I_j, j), m = N(J_j, j),
+ * r = c - B m, g = gbar(J_j, j), lambda = (B^T B)^{-1} g:
+ *     dL/dB = r lambda^T - (B lambda) m^T - 2 rho r m^T,
+ *     dL/dc = B lambda + 2 rho r,
+ *     dL/dA_0(i, j) = 2 rho A_0(i, j) for stored rows i outside I_j,
+ * summed over the columns into the stored entries of A_k and A_0 (in CSR
+ * order, as the inputs).  lambda is solved with the R factor of B's
+ * Householder QR: R^T z = g, R lambda = z.  dmres (nullable, pattern CSC
+ * order) receives the direct residual part of dL/dN: -2 rho B^T r.
+ * mval and gbar are in the pattern's CSC order; gbar may be NULL (zero).
+ * Columns are visited in order and accumulated one after the other.
+ */
+int so_adjoint(int n, const int *krp, const int *kci, const double *kv,
+               const int *zrp, const int *zci, const double *zv,
+               const int *jcp, const int *jri, const double *mval, const double *gbar,
+               double rho, double *dak, double *da0, double *dmres) {
+    if (so_check_csr(n, krp, kci) || so_check_csr(n, zrp, zci)) return 2;
+    int *kcp, *kcr, *zcp, *zcr;
+    double *kcv, *zcv;
+    if (transpose(n, krp, kci, kv, &kcp, &kcr, &kcv)) return 1;
+    if (transpose(n, zrp, zci, zv, &zcp, &zcr, &zcv)) {
+        free(kcp); free(kcr); free(kcv);
+        return 1;
+    }
+    /* CSR index of every CSC entry (to return gradients in CSR order) */
+    int *kperm = (int *)malloc(sizeof(int) * (size_t)(krp[n] > 0 ? krp[n] : 1));
+    int *zperm = (int *)malloc(sizeof(int) * (size_t)(zrp[n] > 0 ? zrp[n] : 1));
+    int *fill = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    double *dk = (double *)calloc((size_t)(krp[n] > 0 ? krp[n] : 1), sizeof(double));
+    double *dz = (double *)calloc((size_t)(zrp[n] > 0 ? zrp[n] : 1), sizeof(double));
+    int *icp, *iri;
+    int st = so_shadow(n, krp, kci, jcp, jri, &icp, &iri);
+    if (st || !kperm || !zperm || !fill || !dk || !dz) {
+        free(kcp); free(kcr); free(kcv); free(zcp); free(zcr); free(zcv);
+        free(kperm); free(zperm); free(fill); free(dk); free(dz);
+        if (!st) { free(icp); free(iri); }
+        return st ? st : 1;
+    }
+    for (int i = 0; i < n; ++i) fill[i] = kcp[i];
+    for (int i = 0; i < n; ++i)
+        for (int e = krp[i]; e < krp[i + 1]; ++e) kperm[fill[kci[e]]++] = e;
+    for (int i = 0; i < n; ++i) fill[i] = zcp[i];
+    for (int i = 0; i < n; ++i)
+        for (int e = zrp[i]; e < zrp[i + 1]; ++e) zperm[fill[zci[e]]++] = e;
+    int maxm = 1, maxn = 1;
+    for (int j = 0; j < n; ++j) {
+        if (icp[j + 1] - icp[j] > maxm) maxm = icp[j + 1] - icp[j];
+        if (jcp[j + 1] - jcp[j] > maxn) maxn = jcp[j + 1] - jcp[j];
+    }
+    double *B = (double *)malloc(sizeof(double) * (size_t)maxm * (size_t)maxn);
+    double *X = (double *)malloc(sizeof(double) * (size_t)maxm * (size_t)(maxn + 1));
+    double *v = (double *)malloc(sizeof(double) * (size_t)maxm);
+    double *c = (double *)malloc(sizeof(double) * (size_t)maxm);
+    double *r = (double *)malloc(sizeof(double) * (size_t)maxm);
+    double *w = (double *)malloc(sizeof(double) * (size_t)maxm);
+    double *lam = (double *)malloc(sizeof(double) * (size_t)maxn);
+    int status = 0;
+    if (!B || !X || !v || !c || !r || !w || !lam) status = 1;
+    for (int j = 0; j < n && !status; ++j) {
+        const int *I = iri + icp[j];
+        const int *J = jri + jcp[j];
+        const int mi = icp[j + 1] - icp[j], nj = jcp[j + 1] - jcp[j];
+        const double *m = mval + jcp[j];
+        if (mi < nj) { status = 3; break; }
+        memset(B, 0, sizeof(double) * (size_t)mi * (size_t)nj);
+        for (int q = 0; q < nj; ++q)
+            for (int e = kcp[J[q]]; e < kcp[J[q] + 1]; ++e)
+                B[(size_t)q * mi + find_sorted(I, mi, kcr[e])] = kcv[e];
+        memset(c, 0, sizeof(double) * (size_t)mi);
+        for (int e = zcp[j]; e < zcp[j + 1]; ++e) {
+            int p = find_sorted(I, mi, zcr[e]);
+            if (p >= 0) c[p] = zcv[e];
+            else dz[e] += 2.0 * rho * zcv[e];
+        }
+        /* r = c - B m */
+        for (int i = 0; i < mi; ++i) {
+            double s2 = c[i];
+            for (int q = 0; q < nj; ++q) s2 -= B[(size_t)q * mi + i] * m[q];
+            r[i] = s2;
+        }
+        /* lambda = (B^T B)^{-1} g through R of B = QR */
+        for (int q = 0; q < nj; ++q) lam[q] = gbar ? gbar[jcp[j] + q] : 0.0;
+        memcpy(X, B, sizeof(double) * (size_t)mi * (size_t)nj);
+        memset(X + (size_t)nj * mi, 0, sizeof(double) * (size_t)mi);
+        if (householder_qr(mi, nj, X, v)) { status = 3; break; }
+        for (int q = 0; q < nj; ++q) {  /* R^T z = g */
+            double s2 = lam[q];
+            for (int p = 0; p < q; ++p) s2 -= X[(size_t)q * mi + p] * lam[p];
+            lam[q] = s2 / X[(size_t)q * mi + q];
+        }
+        for (int q = nj - 1; q >= 0; --q) {  /* R lambda = z */
+            double s2 = lam[q];
+            for (int p = q + 1; p < nj; ++p) s2 -= X[(size_t)p * mi + q] * lam[p];
+            lam[q] = s2 / X[(size_t)q * mi + q];
+        }
+        /* w = B lambda */
+        for (int i = 0; i < mi; ++i) {
+            double s2 = 0.0;
+            for (int q = 0; q < nj; ++q) s2 += B[(size_t)q * mi + i] * lam[q];
+            w[i] = s2;
+        }
+        /* dL/dB on the stored entries of A_k(:, J) */
+        for (int q = 0; q < nj; ++q)
+            for (int e = kcp[J[q]]; e < kcp[J[q] + 1]; ++e) {
+                int i = find_sorted(I, mi, kcr[e]);
+                dk[e] += r[i] * lam[q] - w[i] * m[q] - 2.0 * rho * r[i] * m[q];
+            }
+        /* dL/dc on the stored entries of A_0(I, j) */
+        for (int e = zcp[j]; e < zcp[j + 1]; ++e) {
+            int p = find_sorted(I, mi, zcr[e]);
+            if (p >= 0) dz[e] += w[p] + 2.0 * rho * r[p];
+        }
+        if (dmres)
+            for (int q = 0; q < nj; ++q) {
+                double s2 = 0.0;
+                for (int i = 0; i < mi; ++i) s2 += B[(size_t)q * mi + i] * r[i];
+                dmres[jcp[j] + q] = -2.0 * rho * s2;
+            }
+    }
+    if (!status) {
+        for (int p = 0; p < krp[n]; ++p) dak[kperm[p]] = dk[p];
+        for (int p = 0; p < zrp[n]; ++p) da0[zperm[p]] = dz[p];
+    }
+    free(B); free(X); free(v); free(c); free(r); free(w); free(lam);
+    free(kcp); free(kcr); free(kcv); free(zcp); free(zcr); free(zcv);
+    free(kperm); free(zperm); free(fill); free(dk); free(dz); free(icp); free(iri);
+    return status;
+}
