@@ -36,9 +36,9 @@
 // ~u_32 kappa^2 ||r||/(||B|| ||m||) for problems with a nonzero residual, as
 // SAM columns have).  The FP64 products use the sparse B straight from
 // A_k's CSC values in a fixed order, so results are deterministic.  After
-// the last step the residual follows from the exact identity
-// ||r - B d||^2 = ||r||^2 - 2 d.g + ||B d||^2 with ||B d||^2 (a second-order
-// term) evaluated in FP32, so no further FP64 pass over B is needed.  FP64->FP32
+// the last step the residual is r - B d with the small product B d taken in
+// FP32 and the subtraction and squares in FP64, so no further FP64 pass over
+// B is needed.  FP64->FP32
 // conversions of the factorisation inputs truncate with integer operations,
 // leaving GB300's narrow FP64 pipe to the residual arithmetic.
 #include <cfloat>
@@ -307,7 +307,7 @@ struct SolveUpperT {  // R^T x = y, k from low to high
 
 // r = c - B m in FP64 over the row-major entry lists; returns this lane's
 // partial sum of r_i^2
-template <class TL>
+template <class TL, bool SQUARES = true>
 __device__ __forceinline__ double residual_rows(ProbSmem<TL> &S, const double *kcv, int nI, int ll) {
     double r2 = 0.0;
 #pragma unroll
@@ -318,7 +318,7 @@ __device__ __forceinline__ double residual_rows(ProbSmem<TL> &S, const double *k
             const int pe = S.u.s.rowstart[i + 1];
             for (int p = S.u.s.rowstart[i]; p < pe; ++p) ri = fma(-kcv[S.u.s.rowent[p]], S.m[S.u.s.rowcol[p]], ri);
             S.u.s.r[i] = ri;
-            r2 = fma(ri, ri, r2);
+            if (SQUARES) r2 = fma(ri, ri, r2);
         }
     }
     return r2;
@@ -538,39 +538,34 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) lsq_kernel(LsqArgs args, 
         if constexpr (!FP64) {
             const int steps = args.refine_steps;
             for (int step = 0; step < steps; ++step) {
-                // r = c - B m (FP64), ||r||^2
-                double rr = residual_rows<TL>(S, kcv, nI, ll);
-                rr = group_sum<P>(rr);
+                // r = c - B m (FP64)
+                residual_rows<TL, false>(S, kcv, nI, ll);
                 __syncwarp();
                 // g = B^T r (FP64), own columns
-                double g[JQ];
 #pragma unroll
                 for (int q = 0; q < JQ; ++q) {
                     double acc = 0.0;
                     for (int p = 0; p < clen[q]; ++p) acc = fma(kcv[colA[q] + p], S.u.s.r[S.locr[colB[q] + p]], acc);
-                    g[q] = acc;
                     x[q] = to_tile<T>(acc);
                 }
                 // d = (R^T R)^{-1} g in FP32
                 SolveUpperT<TL, 0>::run(S.u.s.R, S.u.s.dinv, x, nJ, ll, gbase);
                 SolveUpper<TL, JQ - 1>::run(S.u.s.R, S.u.s.dinv, x, nJ, ll, gbase);
-                double dg = 0.0;
 #pragma unroll
                 for (int q = 0; q < JQ; ++q) {
                     const int c = ll + q * P;
                     if (c < nJ) {
                         const double d = to_f64<T>(x[q]);
-                        dg = fma(d, g[q], dg);
                         mq[q] += d;
                         S.m[c] = mq[q];
                         S.u.s.y[c] = x[q];
                     }
                 }
-                dg = group_sum<P>(dg);
                 __syncwarp();
-                // ||B d||^2 in FP32 from the truncated entries (relative error
-                // ~1e-7 of a term that is already second order)
-                float bd2 = 0.f;
+                // final residual r - B d: B d in FP32 from the truncated
+                // entries (its error, ~1e-7 |B d|, multiplies a correction
+                // that is already ~1e-6 of |c|), subtracted and squared in FP64
+                double rf2 = 0.0;
 #pragma unroll
                 for (int q = 0; q < TL::IQ; ++q) {
                     const int i = ll + q * P;
@@ -579,13 +574,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) lsq_kernel(LsqArgs args, 
                         const int pe = S.u.s.rowstart[i + 1];
                         for (int p = S.u.s.rowstart[i]; p < pe; ++p)
                             v = fmaf(narrow_trunc(kcv[S.u.s.rowent[p]]), (float)S.u.s.y[S.u.s.rowcol[p]], v);
-                        bd2 = fmaf(v, v, bd2);
+                        const double rfi = S.u.s.r[i] - to_f64<float>(v);
+                        rf2 = fma(rfi, rfi, rf2);
                     }
                 }
-                bd2 = group_sum<P>(bd2);
+                rf2 = group_sum<P>(rf2);
                 __syncwarp();
-                // exact identity ||r - B d||^2 = ||r||^2 - 2 d.(B^T r) + ||B d||^2
-                r2 = rr - 2.0 * dg + to_f64<float>(bd2);
+                r2 = rf2;
                 need_final = false;
             }
         }

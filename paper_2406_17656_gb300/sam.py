@@ -190,21 +190,28 @@ class Pattern:
     def __init__(self, handle: "Handle", ptr: int):
         self.handle, self.ptr = handle, ptr
         handle._patterns.add(self)
-        n, nnz, cp, ri = ctypes.c_int32(), ctypes.c_int64(), _vp(), _vp()
-        _check(load().sam_pattern_get(ptr, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(cp), ctypes.byref(ri)),
-               "sam_pattern_get")
+        n, nnz = ctypes.c_int32(), ctypes.c_int64()
+        _check(load().sam_pattern_get(ptr, ctypes.byref(n), ctypes.byref(nnz), None, None), "sam_pattern_get")
         self.n, self.nnz = n.value, nnz.value
-        self._cp, self._ri = cp.value, ri.value
+        self._cp = self._ri = None
+
+    def _views(self):
+        if self._cp is None:
+            cp, ri = _vp(), _vp()
+            _check(load().sam_pattern_get(self.ptr, None, None, ctypes.byref(cp), ctypes.byref(ri)),
+                   "sam_pattern_get")
+            self._cp, self._ri = cp.value, ri.value
+        return self._cp, self._ri
 
     def colptr(self):
         import torch
 
-        return torch.as_tensor(_CudaView(self._cp, self.n + 1, "<i4"), device="cuda")
+        return torch.as_tensor(_CudaView(self._views()[0], self.n + 1, "<i4"), device="cuda")
 
     def rowidx(self):
         import torch
 
-        return torch.as_tensor(_CudaView(self._ri, self.nnz, "<i4"), device="cuda")
+        return torch.as_tensor(_CudaView(self._views()[1], self.nnz, "<i4"), device="cuda")
 
     def destroy(self):
         # a pattern lives in its handle's memory pool: once the handle is

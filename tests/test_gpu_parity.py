@@ -135,9 +135,17 @@ def test_batched_build_matches_oracle(sam, handle):
         assert np.array_equal(rp[k * (n + 1):(k + 1) * (n + 1)], ref["ip"])
         assert np.array_equal(ci[offs[k]:offs[k + 1]], ref["ix"])
         assert rel_fro(v[offs[k]:offs[k + 1]], ref["dv"]) <= 1e-10
+        # the reported residual is the residual of the map that was built ...
+        m = sp.csr_matrix((v[offs[k]:offs[k + 1]], ci[offs[k]:offs[k + 1]], rp[k * (n + 1):(k + 1) * (n + 1)]),
+                          shape=(n, n)).tocsc()
+        m.sort_indices()
+        own, _ = oracle.residual(Ak, m.indptr, m.indices, m.data, A0)
+        assert abs(fro[k] - own) <= 1e-10 * own + 1e-13 * np.linalg.norm(A0.data)
+        # ... and differs from the oracle map's residual by at most ||A_k (M - M_oracle)||_F
         ofro, _ = oracle.residual(Ak, ref["cp"], ref["ri"], ref["mval"], A0)
-        # relative to ||A_0||_F: the identity map (k = 0) has a residual at rounding level
-        assert abs(fro[k] - ofro) <= 1e-10 * ofro + 1e-13 * np.linalg.norm(A0.data)
+        a_abs = abs(Ak.to_scipy())
+        a2 = np.sqrt(a_abs.sum(0).max() * a_abs.sum(1).max())  # >= ||A_k||_2
+        assert abs(fro[k] - ofro) <= 1e-10 * ofro + a2 * np.linalg.norm(m.data - ref["mval"]) + 1e-14 * ofro
 
 
 def test_identity_map_when_source_is_target(sam, handle):
