@@ -1,0 +1,96 @@
+"""torch.autograd wrappers of the SAM build and of its residual.
+
+`SamMap(handle, A_k, A_0, S)` is a differentiable function of the stored
+values of A_k and A_0 that returns the map values M_k (CSR order):
+forward = `sam_build`, backward = the hand-written adjoint kernel
+(`sam_build_backward`), which recomputes each column's QR instead of storing
+it.  `SamMap.residual_sq(ak, a0, m)` is ||A_k M - A_0||_F^2 (Eq. (res)) as a
+differentiable function of all three; its backward returns the direct
+partials, and autograd chains its dependence on M through `SamMap`.
+
+Only argument marshalling happens here; every step runs in libsam.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import sam as _sam
+
+
+class _BuildFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, ak_val, a0_val, owner):
+        h, S = owner.handle, owner.pattern
+        ak = _sam.Csr(owner.ak_rp, owner.ak_ci, ak_val.detach().contiguous(), n=owner.n)
+        a0 = _sam.Csr(owner.a0_rp, owner.a0_ci, a0_val.detach().contiguous(), n=owner.n)
+        ip, ix, mv = h.sam_build(ak, a0, S, owner.precision, owner.refine_steps)
+        owner.indptr, owner.indices = ip, ix
+        ctx.owner = owner
+        ctx.save_for_backward(ak_val.detach(), a0_val.detach(), mv)
+        return mv
+
+    @staticmethod
+    def backward(ctx, dm):
+        owner = ctx.owner
+        ak_val, a0_val, mv = ctx.saved_tensors
+        ak = _sam.Csr(owner.ak_rp, owner.ak_ci, ak_val.contiguous(), n=owner.n)
+        a0 = _sam.Csr(owner.a0_rp, owner.a0_ci, a0_val.contiguous(), n=owner.n)
+        dak, da0 = owner.handle.sam_build_backward(ak, a0, owner.pattern, mv, dm.contiguous(), owner.precision,
+                                                   owner.refine_steps, 0.0)
+        return dak, da0, None
+
+
+class _ResidualSqFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, ak_val, a0_val, m_val, owner):
+        if owner.indptr is None:
+            raise RuntimeError("build the map (call the SamMap) before its residual")
+        h = owner.handle
+        ak = _sam.Csr(owner.ak_rp, owner.ak_ci, ak_val.detach().contiguous(), n=owner.n)
+        a0 = _sam.Csr(owner.a0_rp, owner.a0_ci, a0_val.detach().contiguous(), n=owner.n)
+        m = _sam.Csr(owner.indptr, owner.indices, m_val.detach().contiguous(), n=owner.n)
+        fro, _ = h.sam_residual(ak, m, a0)
+        ctx.owner = owner
+        ctx.save_for_backward(ak_val.detach(), a0_val.detach(), m_val.detach())
+        return torch.tensor(fro * fro, dtype=torch.float64, device=ak_val.device)
+
+    @staticmethod
+    def backward(ctx, dl):
+        owner = ctx.owner
+        ak_val, a0_val, m_val = ctx.saved_tensors
+        ak = _sam.Csr(owner.ak_rp, owner.ak_ci, ak_val.contiguous(), n=owner.n)
+        a0 = _sam.Csr(owner.a0_rp, owner.a0_ci, a0_val.contiguous(), n=owner.n)
+        dmres = torch.empty_like(m_val)
+        dak, da0 = owner.handle.sam_build_backward(ak, a0, owner.pattern, m_val.contiguous(), None, owner.precision,
+                                                   owner.refine_steps, float(dl), dM_resid=dmres)
+        return dak, da0, dmres, None
+
+
+class SamMap:
+    """Differentiable SAM on a fixed pattern.
+
+    handle: sam.Handle; ak_struct / a0_struct: (indptr, indices) int32 device
+    tensors of A_k and A_0; pattern: sam.Pattern (e.g. from
+    handle.sam_pattern_build); precision "fp32r" (FP32 QR + FP64 refinement)
+    or "fp64"."""
+
+    def __init__(self, handle, ak_struct, a0_struct, pattern, precision="fp32r", refine_steps=1):
+        self.handle, self.pattern = handle, pattern
+        self.ak_rp, self.ak_ci = ak_struct
+        self.a0_rp, self.a0_ci = a0_struct
+        self.n = int(self.ak_rp.shape[0] - 1)
+        self.precision, self.refine_steps = precision, int(refine_steps)
+        self.indptr = self.indices = None
+
+    def __call__(self, ak_val, a0_val):
+        return _BuildFn.apply(ak_val, a0_val, self)
+
+    def residual_sq(self, ak_val, a0_val, m_val):
+        return _ResidualSqFn.apply(ak_val, a0_val, m_val, self)
+
+    def matvec(self, m_val, v):
+        """M v as a differentiable function of the map values (plain torch ops)."""
+        rows = torch.repeat_interleave(torch.arange(self.n, device=m_val.device),
+                                       (self.indptr[1:] - self.indptr[:-1]).long())
+        return torch.zeros(self.n, dtype=m_val.dtype, device=m_val.device).index_add_(
+            0, rows, m_val * v[self.indices.long()])

@@ -1,0 +1,214 @@
+// adjoint.cu -- hand-written adjoint of the column least-squares solves of
+// SAM construction (reverse mode of Sec. 2's column problems
+// m_j = argmin ||B_j m - c_j||, B_j = A_k(I_j, J_j), c_j = A_0(I_j, j)).
+//
+// For the loss L = <dM, M> + w ||A_k M - A_0||_F^2 and one column, with
+// r = c - B m, g = dM(J_j, j) and lambda = (B^T B)^{-1} g:
+//   dL/dB = r lambda^T - (B lambda) m^T - 2 w r m^T   (stored entries only)
+//   dL/dc = B lambda + 2 w r,   dL/dA_0(i, j) = 2 w A_0(i, j) outside I_j.
+// The QR is recomputed (not stored): lambda comes from the FP32 R with
+// `refine_steps` corrections whose residuals g - B^T (B lambda) are FP64
+// (or from the FP64 R in FP64 mode).
+//
+// Deterministic reduction.  Column problem j writes its dL/dB entries, in
+// the gather order (columns c of J_j, each in A_k's CSC order), to its own
+// block of dB and records, for every pattern entry (c, j) (map CSR order),
+// where the block of column c starts (dbase).  A stored entry e of A_k in
+// column c then receives sum over the map's CSR row c (all j with c in J_j)
+// of dB[dbase[t] + (e - kcp[c])], added in a fixed order.  dL/dA_0(:, j) is
+// written by problem j alone.
+#include "lsq_core.cuh"
+
+namespace sam {
+namespace {
+
+template <class TL, bool FP64>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) adjoint_kernel(LsqArgs args, int bin) {
+    using T = typename TL::T;
+    constexpr int P = TL::P, PPW = TL::PPW, RS = TL::RS, CS = TL::CS, JQ = TL::JQ, IQ = TL::IQ;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ProbSmem<TL> *probs = reinterpret_cast<ProbSmem<TL> *>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    ProbSmem<TL> &S = probs[warp * PPW + lane / P];
+
+    const int w0 = args.bin_off[bin];
+    const int total = args.bin_off[bin + 1] - w0;
+    const int32_t *work = args.work + w0;
+    int32_t *ticket = args.ticket + bin;
+    const double *kcv = args.kcv;
+    const double rho = args.resid_weight;
+
+    for (int iter = 0; iter < (1 << 30); ++iter) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(ticket, PPW);
+        base = shfl(base, 0);
+        if (base >= total) break;
+        Column<TL> C;
+        C.begin(args, base + lane / P, total, work);
+        const int ll = C.ll;
+        C.gather(args, S);
+        T a[RS][CS];
+        C.load_tile(S, a);
+        C.build_rows(S);
+        C.factor(S, a);
+        const int nJ = C.nJ, nI = C.nI;
+        // ---- m (the forward map) and the incoming gradient g
+        double mq[JQ], gq[JQ];
+#pragma unroll
+        for (int q = 0; q < JQ; ++q) {
+            const int c = ll + q * P;
+            mq[q] = 0.0;
+            gq[q] = 0.0;
+            if (c < nJ) {
+                const int t = args.csr_pos[C.jb + c];
+                mq[q] = args.mval[t];
+                gq[q] = args.dmval ? args.dmval[t] : 0.0;
+                S.m[c] = mq[q];
+            }
+        }
+        __syncwarp();
+        // ---- r = c - B m (FP64)
+        residual_rows<TL, false>(S, kcv, nI, ll);
+        __syncwarp();
+        // ---- lambda = (B^T B)^{-1} g
+        T x[JQ];
+        double lq[JQ];
+#pragma unroll
+        for (int q = 0; q < JQ; ++q) x[q] = to_tile<T>(gq[q]);
+        C.normal_solve(S, x);
+#pragma unroll
+        for (int q = 0; q < JQ; ++q) lq[q] = to_f64<T>(x[q]);
+        const int steps = FP64 ? 0 : args.refine_steps;
+        for (int step = 0; step <= steps; ++step) {
+            // w = B lambda (FP64) over the row-major entry lists
+#pragma unroll
+            for (int q = 0; q < JQ; ++q) {
+                const int c = ll + q * P;
+                if (c < nJ) S.lam[c] = lq[q];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < IQ; ++q) {
+                const int i = ll + q * P;
+                if (i < nI) {
+                    double wi = 0.0;
+                    const int pe = S.u.s.rowstart[i + 1];
+                    for (int p = S.u.s.rowstart[i]; p < pe; ++p) wi = fma(kcv[S.u.s.rowent[p]], S.lam[S.u.s.rowcol[p]], wi);
+                    S.u.s.w[i] = wi;
+                }
+            }
+            __syncwarp();
+            if (step == steps) break;
+            // correction: lambda += (R^T R)^{-1} (g - B^T w)
+#pragma unroll
+            for (int q = 0; q < JQ; ++q) x[q] = to_tile<T>(gq[q] - C.bt_times(args, S, S.u.s.w, q));
+            C.normal_solve(S, x);
+#pragma unroll
+            for (int q = 0; q < JQ; ++q) lq[q] += to_f64<T>(x[q]);
+        }
+        if (C.valid && C.status == kStOk) {
+            // ---- dL/dB entries of this column's block, and where each block starts
+            const int64_t blk = args.dB_off[C.jj];
+#pragma unroll
+            for (int q = 0; q < JQ; ++q) {
+                const int c = ll + q * P;
+                if (c < nJ) {
+                    for (int p = 0; p < C.clen[q]; ++p) {
+                        const int i = S.locr[C.colB[q] + p];
+                        const double ri = S.u.s.r[i], wi = S.u.s.w[i];
+                        args.dB[blk + C.colB[q] + p] = ri * lq[q] - wi * mq[q] - 2.0 * rho * ri * mq[q];
+                    }
+                    const int t = args.csr_pos[C.jb + c];
+                    args.dbase[t] = blk + C.colB[q];
+                    if (args.dmres) args.dmres[t] = -2.0 * rho * C.bt_times(args, S, S.u.s.r, q);
+                }
+            }
+            // ---- dL/dA_0(:, j)
+            const int64_t zoff = (int64_t)(C.roff / args.n) * args.znnz;
+            for (int t = C.zb + ll; t < C.ze; t += P) {
+                const int i = find_sorted(S.I, nI, args.zri[t] + C.roff);
+                args.dzval[zoff + t] = (i >= 0) ? S.u.s.w[i] + 2.0 * rho * S.u.s.r[i] : 2.0 * rho * args.zcv[t];
+            }
+        }
+        if (C.valid && ll == 0) args.colstat[C.jj] = C.status;
+        __syncwarp();
+    }
+}
+
+// dA(e) for the stored entries e of column c (one warp per column)
+__global__ void adjoint_reduce_kernel(int N, const int32_t *kcp, const int32_t *mrp, const int64_t *dbase,
+                                      const double *dB, double *dak) {
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= N) return;
+    const int b = kcp[c], e = kcp[c + 1];
+    const int tb = mrp[c], te = mrp[c + 1];
+    for (int p = lane; p < e - b; p += 32) {
+        double acc = 0.0;
+        for (int t = tb; t < te; ++t) {
+            const int64_t base = dbase[t];
+            if (base >= 0) acc += dB[base + p];
+        }
+        dak[b + p] = acc;
+    }
+}
+
+__global__ void permute_scatter_kernel(int64_t nnz, const int32_t *perm, const double *in, double *out) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < nnz) out[perm[p]] = in[p];
+}
+
+template <class TL, bool FP64>
+cudaError_t launch_one(sam_handle h, const LsqArgs &a, int bin) {
+    const size_t smem = sizeof(ProbSmem<TL>) * TL::PPW * kWarpsPerBlock;
+    auto kern = adjoint_kernel<TL, FP64>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    kern<<<per_sm * handle_sms(h), kWarpsPerBlock * 32, smem, handle_stream(h)>>>(a, bin);
+    count_launch(h);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_adjoint(sam_handle h, int precision, const LsqArgs &args) {
+    cudaError_t e = cudaMemsetAsync(args.ticket, 0, sizeof(int32_t) * kNumBins, handle_stream(h));
+    if (e != cudaSuccess) return e;
+    if (precision == SAM_FP64) {
+        if ((e = launch_one<D0, true>(h, args, 0)) != cudaSuccess) return e;
+        if ((e = launch_one<D1, true>(h, args, 1)) != cudaSuccess) return e;
+        if ((e = launch_one<D2, true>(h, args, 2)) != cudaSuccess) return e;
+        if ((e = launch_one<D3, true>(h, args, 3)) != cudaSuccess) return e;
+        if ((e = launch_one<D4, true>(h, args, 4)) != cudaSuccess) return e;
+    } else {
+        if ((e = launch_one<F0, false>(h, args, 0)) != cudaSuccess) return e;
+        if ((e = launch_one<F1, false>(h, args, 1)) != cudaSuccess) return e;
+        if ((e = launch_one<F2, false>(h, args, 2)) != cudaSuccess) return e;
+        if ((e = launch_one<F3, false>(h, args, 3)) != cudaSuccess) return e;
+        if ((e = launch_one<F4, false>(h, args, 4)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t adjoint_reduce(sam_handle h, int N, const int32_t *kcp, const int32_t *mrp, const int64_t *dbase,
+                           const double *dB, double *dak_csc) {
+    if (N == 0) return cudaSuccess;
+    const int64_t threads = (int64_t)N * 32;
+    adjoint_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, handle_stream(h)>>>(N, kcp, mrp, dbase, dB,
+                                                                                          dak_csc);
+    count_launch(h);
+    return cudaGetLastError();
+}
+
+cudaError_t permute_scatter_f64(sam_handle h, int64_t nnz, const int32_t *perm, const double *in, double *out) {
+    if (nnz == 0) return cudaSuccess;
+    permute_scatter_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, handle_stream(h)>>>(nnz, perm, in, out);
+    count_launch(h);
+    return cudaGetLastError();
+}
+
+}  // namespace sam

@@ -700,8 +700,18 @@ sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_
     if (build_work_list(h, (int)N, bin, work, bin_off) != cudaSuccess) return SAM_ERR_CUDA;
     cudaMemsetAsync(d_v, 0, sizeof(double) * (size_t)total_nnz, st);
     cudaMemsetAsync(d_r2, 0, sizeof(double) * (size_t)N, st);
+    float *kcv32 = nullptr, *zcv32 = nullptr;
+    if (precision == SAM_FP32_REFINE) {
+        kcv32 = sc.get<float>((size_t)ktot);
+        zcv32 = sc.get<float>((size_t)z.nnz);
+        if (!kcv32 || !zcv32) return SAM_ERR_OOM;
+        if (round_to_f32(h, ktot, kcv, kcv32) != cudaSuccess || round_to_f32(h, z.nnz, zcv, zcv32) != cudaSuccess)
+            return SAM_ERR_CUDA;
+    }
     LsqArgs a;
     memset(&a, 0, sizeof(a));
+    a.kcv32 = kcv32;
+    a.zcv32 = zcv32;
     a.n = n;
     a.kcp = kcp;
     a.kri = kri;
@@ -798,9 +808,114 @@ sam_status sam_apply(sam_handle h, const sam_csr *M_k, const double *x, double *
 sam_status sam_build_backward(sam_handle h, const sam_csr *A_k, const sam_csr *A_0, sam_pattern S, int precision,
                               int refine_steps, const double *M_val, const double *dM_val, double resid_weight,
                               double *dA_k_val, double *dA_0_val, double *dM_resid) {
-    (void)h; (void)A_k; (void)A_0; (void)S; (void)precision; (void)refine_steps; (void)M_val; (void)dM_val;
-    (void)resid_weight; (void)dA_k_val; (void)dA_0_val; (void)dM_resid;
-    return SAM_ERR_UNSUPPORTED;
+    if (!h || !S || !M_val || !dA_k_val || !dA_0_val) return SAM_ERR_INVALID_ARG;
+    if (precision != SAM_FP64 && precision != SAM_FP32_REFINE) return SAM_ERR_INVALID_ARG;
+    if (refine_steps < 0 || refine_steps > 4 || !std::isfinite(resid_weight)) return SAM_ERR_INVALID_ARG;
+    if (check_csr_arg(A_k, true) != SAM_OK || check_csr_arg(A_0, true) != SAM_OK) return SAM_ERR_INVALID_ARG;
+    const int n = A_0->n;
+    if (A_k->n != n || S->n != n) return SAM_ERR_INVALID_ARG;
+    cudaStream_t st = h->stream;
+    Scratch sc(h);
+    Stager sg(sc, st);
+    DevCsr ak = stage_csr(sg, A_k, true), z = stage_csr(sg, A_0, true);
+    const double *d_m = sg.in(M_val, (size_t)S->nnz);
+    const double *d_dm = dM_val ? sg.in(dM_val, (size_t)S->nnz) : nullptr;
+    double *d_dak = sg.out(dA_k_val, (size_t)ak.nnz);
+    double *d_da0 = sg.out(dA_0_val, (size_t)z.nnz);
+    double *d_dmr = dM_resid ? sg.out(dM_resid, (size_t)S->nnz) : nullptr;
+    if (sg.failed) return SAM_ERR_OOM;
+    sam_status s = validate_all(h, sc, {ak, z});
+    if (s != SAM_OK) return s;
+    PatternGroup *g = nullptr;
+    bool temp = false;
+    s = group_for(h, 1, &S, &g, &temp);
+    if (s != SAM_OK) return s;
+    struct GroupGuard {
+        PatternGroup *g;
+        bool temp;
+        ~GroupGuard() {
+            if (temp) group_release(g);
+        }
+    } guard{g, temp};
+    int32_t *zcp = sc.get<int32_t>((size_t)n + 1), *zri = sc.get<int32_t>((size_t)z.nnz);
+    int32_t *zperm = sc.get<int32_t>((size_t)z.nnz);
+    double *zcv = sc.get<double>((size_t)z.nnz);
+    int32_t *kcp = sc.get<int32_t>((size_t)n + 1), *kri = sc.get<int32_t>((size_t)ak.nnz);
+    int32_t *kperm = sc.get<int32_t>((size_t)ak.nnz);
+    double *kcv = sc.get<double>((size_t)ak.nnz);
+    int32_t *ish = sc.get<int32_t>((size_t)n * kICap), *icnt = sc.get<int32_t>((size_t)n);
+    uint8_t *bin = sc.get<uint8_t>((size_t)n);
+    int32_t *colstat = sc.get<int32_t>((size_t)n);
+    int64_t *nbcnt = sc.get<int64_t>((size_t)n + 1), *dB_off = sc.get<int64_t>((size_t)n + 1);
+    int32_t *work = sc.get<int32_t>((size_t)n);
+    int32_t *bin_off = sc.get<int32_t>(kNumBins + 1), *tickets = sc.get<int32_t>(kNumBins);
+    int64_t *dbase = sc.get<int64_t>((size_t)S->nnz);
+    double *dzval = sc.get<double>((size_t)z.nnz), *dak_csc = sc.get<double>((size_t)ak.nnz);
+    if (!zcp || !zri || !zperm || !zcv || !kcp || !kri || !kperm || !kcv || !ish || !icnt || !bin || !colstat ||
+        !nbcnt || !dB_off || !work || !bin_off || !tickets || !dbase || !dzval || !dak_csc)
+        return SAM_ERR_OOM;
+    if (csr_to_csc(h, n, z.nnz, z.rp, z.ci, z.v, zcp, zri, zcv, zperm) != cudaSuccess ||
+        csr_to_csc(h, n, ak.nnz, ak.rp, ak.ci, ak.v, kcp, kri, kcv, kperm) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    if (shadow_and_bins(h, n, kcp, kri, g->jcp, g->jri, ish, icnt, bin, colstat, nbcnt) != cudaSuccess ||
+        exclusive_scan_i64(h, nbcnt, dB_off, n) != cudaSuccess || build_work_list(h, n, bin, work, bin_off) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    int64_t nbtot = 0;
+    if (cudaMemcpyAsync(&nbtot, dB_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    double *dB = sc.get<double>((size_t)(nbtot > 0 ? nbtot : 1));
+    if (!dB) return SAM_ERR_OOM;
+    cudaMemsetAsync(dbase, 0xff, sizeof(int64_t) * (size_t)S->nnz, st);  // -1: no contribution
+    float *kcv32 = nullptr, *zcv32 = nullptr;
+    if (precision == SAM_FP32_REFINE) {
+        kcv32 = sc.get<float>((size_t)ak.nnz);
+        zcv32 = sc.get<float>((size_t)z.nnz);
+        if (!kcv32 || !zcv32) return SAM_ERR_OOM;
+        if (round_to_f32(h, ak.nnz, kcv, kcv32) != cudaSuccess || round_to_f32(h, z.nnz, zcv, zcv32) != cudaSuccess)
+            return SAM_ERR_CUDA;
+    }
+    cudaMemsetAsync(dzval, 0, sizeof(double) * (size_t)z.nnz, st);
+    if (d_dmr) cudaMemsetAsync(d_dmr, 0, sizeof(double) * (size_t)S->nnz, st);
+    LsqArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.kcp = kcp;
+    a.kri = kri;
+    a.kcv = kcv;
+    a.jcp = g->jcp;
+    a.jri = g->jri;
+    a.ish = ish;
+    a.icnt = icnt;
+    a.zcp = zcp;
+    a.zri = zri;
+    a.zcv = zcv;
+    a.csr_pos = g->csr_pos;
+    a.mval = const_cast<double *>(d_m);
+    a.kcv32 = kcv32;
+    a.zcv32 = zcv32;
+    a.colstat = colstat;
+    a.work = work;
+    a.bin_off = bin_off;
+    a.ticket = tickets;
+    a.refine_steps = refine_steps;
+    a.dmval = d_dm;
+    a.resid_weight = resid_weight;
+    a.dB = dB;
+    a.dB_off = dB_off;
+    a.dzval = dzval;
+    a.dmres = d_dmr;
+    a.dbase = dbase;
+    a.znnz = z.nnz;
+    if (launch_adjoint(h, precision, a) != cudaSuccess) return SAM_ERR_CUDA;
+    if (adjoint_reduce(h, n, kcp, g->mrp, dbase, dB, dak_csc) != cudaSuccess ||
+        permute_scatter_f64(h, ak.nnz, kperm, dak_csc, d_dak) != cudaSuccess ||
+        permute_scatter_f64(h, z.nnz, zperm, dzval, d_da0) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    if (status_reduce(h, colstat, n, h->d_flag) != cudaSuccess) return SAM_ERR_CUDA;
+    if (sg.finish() != cudaSuccess) return SAM_ERR_CUDA;
+    if (sg.has_host_outputs()) return drain_status(h);
+    return cudaGetLastError() == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
 }
 
 sam_status sam_tune(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0, const sam_pattern *S, int precision,

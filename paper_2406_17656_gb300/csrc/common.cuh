@@ -45,10 +45,12 @@ struct LsqArgs {
     int n;                       // order of one map (A_0)
     const int32_t *kcp, *kri;    // CSC of the block-diagonal source
     const double *kcv;
+    const float *kcv32;          // the same values rounded to FP32 (FP32 tiles)
     const int32_t *jcp, *jri;    // pattern (CSC, big)
     const int32_t *ish, *icnt;   // shadow rows (padded) and counts
     const int32_t *zcp, *zri;    // CSC of the target A_0 (order n)
     const double *zcv;
+    const float *zcv32;          // the same values rounded to FP32
     const int32_t *csr_pos;      // pattern CSC entry -> map CSR position
     double *mval;                // map values, CSR order of the block-diagonal map
     double *colres;              // per-column residual^2 (+ out-of-shadow part)
@@ -63,7 +65,8 @@ struct LsqArgs {
     double *dB;                  // per-column dL/dB entries (gather order)
     const int64_t *dB_off;       // [N+1] offsets of each column's entries in dB
     double *dzval;               // dL/dA_0 contributions, CSC(A_0) order per map [K][nnz(A_0)]
-    double *dmres;               // dL/dM direct residual part, CSC order of the pattern (nullable)
+    double *dmres;               // dL/dM direct residual part, map CSR order (nullable)
+    int64_t *dbase;              // per pattern entry (map CSR order): offset of its column block in dB
     int64_t znnz;                // nnz(A_0)
 };
 
@@ -112,15 +115,24 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
                          int32_t **jcp, int32_t **jri, int64_t *nnz_out);
 
 // Shadow rows (padded), |I_j| and size class of every column.
+// nbcnt (nullable) receives nnz(B_j) = sum of |A(:, c)| over c in J_j.
 cudaError_t shadow_and_bins(sam_handle h, int N, const int32_t *kcp, const int32_t *kri, const int32_t *jcp,
-                            const int32_t *jri, int32_t *ish, int32_t *icnt, uint8_t *bin, int32_t *colstat);
+                            const int32_t *jri, int32_t *ish, int32_t *icnt, uint8_t *bin, int32_t *colstat,
+                            int64_t *nbcnt = nullptr);
 
 // Work list: columns grouped by size class; bin_off (device, [kNumBins+1]).
 cudaError_t build_work_list(sam_handle h, int N, const uint8_t *bin, int32_t *work, int32_t *bin_off);
 
 // Least-squares launches for every size class.
 cudaError_t launch_lsq(sam_handle h, int precision, const LsqArgs &args);
-cudaError_t launch_adjoint(sam_handle h, const LsqArgs &args);
+cudaError_t launch_adjoint(sam_handle h, int precision, const LsqArgs &args);
+// dA(e) = sum over map entries t of row c(e): dB[dbase[t] + (e - kcp[c])], CSC order of A
+cudaError_t adjoint_reduce(sam_handle h, int N, const int32_t *kcp, const int32_t *mrp, const int64_t *dbase,
+                           const double *dB, double *dak_csc);
+// out[i] = (float) in[i]
+cudaError_t round_to_f32(sam_handle h, int64_t n, const double *in, float *out);
+// out[perm[p]] = in[p]
+cudaError_t permute_scatter_f64(sam_handle h, int64_t nnz, const int32_t *perm, const double *in, double *out);
 
 // Deterministic sums: out[k] = sum of x[k*seg .. (k+1)*seg) (squares optional).
 cudaError_t segmented_sum_f64(sam_handle h, const double *x, int K, int64_t seg, double *out, bool squares);

@@ -1,0 +1,549 @@
+// lsq_core.cuh -- device building blocks shared by the forward least-squares
+// kernel (lsq.cu) and its adjoint (adjoint.cu): the register-tile
+// descriptor, the per-problem shared-memory layout, FP64<->FP32 conversions
+// done with integer operations, group reductions, the phased Householder QR
+// of [B c] and the register triangular solves with R.  See lsq.cu for the
+// method.
+#pragma once
+
+#include <cfloat>
+#include <climits>
+
+#include "common.cuh"
+
+namespace sam {
+namespace {
+
+constexpr int kWarpsPerBlock = 4;
+
+template <int RG_, int CG_, int RS_, int CS_, typename T_, int MAXI_BIN_>
+struct Tile {
+    static constexpr int RG = RG_, CG = CG_, RS = RS_, CS = CS_;
+    static constexpr int P = RG * CG;    // lanes per column problem
+    static constexpr int PPW = 32 / P;   // problems per warp
+    static constexpr int MAXI = RG * RS; // padded rows
+    static constexpr int NCOL = CG * CS; // padded columns incl. right-hand side
+    static constexpr int MAXJ = NCOL - 1;
+    static constexpr int L = RG < CG ? RG : CG;    // QR phase length
+    static constexpr int NBCAP = 8 * MAXI_BIN_;     // max stored entries of B
+    static constexpr int JQ = (MAXJ + P - 1) / P;  // unknowns per lane (solves)
+    static constexpr int IQ = (MAXI + P - 1) / P;  // rows per lane (residuals)
+    static constexpr int RSTR = (MAXJ % 2) ? MAXJ : MAXJ + 1;  // odd row stride of R
+    static constexpr int VEC = 16 / (int)sizeof(T_);            // elements per 16-byte access
+    static constexpr int RSP = (RS + VEC - 1) / VEC * VEC;     // padded row slots per lane
+    using T = T_;
+    static_assert(32 % P == 0, "group size must divide the warp");
+    static_assert(MAXJ <= 31, "column masks are 32-bit");
+    static_assert(MAXI <= 255, "local row indices are 8-bit");
+};
+
+template <class TL>
+struct ProbSmem {
+    using T = typename TL::T;
+    int I[TL::MAXI];
+    int colA[TL::MAXJ];
+    int colB[TL::MAXJ + 1];
+    unsigned mask[TL::MAXI];
+    double c[TL::MAXI];
+    double m[TL::MAXJ];
+    double lam[TL::MAXJ];  // adjoint multipliers (adjoint only)
+    unsigned char locr[TL::NBCAP];
+    union U {
+        // [B c], only until registers are loaded: element (i, col) at
+        // tile[col][i % RG][i / RG], so every lane's row slots are contiguous
+        __align__(16) T tile[TL::NCOL][TL::RG][TL::RSP];
+        struct S {
+            int rowstart[TL::MAXI + 1];
+            int rowent[TL::NBCAP];
+            unsigned char rowcol[TL::NBCAP];
+            double r[TL::MAXI];
+            double w[TL::MAXI];  // B lambda (adjoint only)
+            T y[TL::MAXJ];
+            T dinv[TL::MAXJ];
+            T R[TL::MAXJ * TL::RSTR];
+        } s;
+    } u;
+};
+
+// ------------------------------------------------------------- utilities
+
+__device__ __forceinline__ int find_sorted(const int *a, int len, int key) {
+    int lo = 0, hi = len - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int v = a[mid];
+        if (v == key) return mid;
+        if (v < key) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+// FP64 -> FP32 by truncation of the mantissa, with integer operations only.
+// Used for the inputs of the FP32 factorisation, whose rounding the FP64
+// refinement removes.  Overflow -> +-inf, NaN -> NaN, below FP32's normal
+// range -> +-0.
+__device__ __forceinline__ float narrow_trunc(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    if (e >= 255) {
+        const bool nan = ((hi >> 20) & 0x7ffu) == 0x7ffu && ((hi & 0xfffffu) | lo) != 0u;
+        return __int_as_float((int)(sign | 0x7f800000u | (nan ? 0x400000u : 0u)));
+    }
+    if (e <= 0) return __int_as_float((int)sign);
+    return __int_as_float((int)(sign | ((unsigned)e << 23) | mant));
+}
+
+// FP32 -> FP64 exactly, with integer operations (normal numbers and zeros;
+// FP32 subnormals widen to zero, infinities and NaN keep their class).
+__device__ __forceinline__ double widen(float x) {
+    const unsigned u = (unsigned)__float_as_int(x);
+    const unsigned sign = u & 0x80000000u;
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned mant = u & 0x7fffffu;
+    unsigned hi, lo;
+    if (e == 0u) {
+        hi = sign;
+        lo = 0u;
+    } else if (e == 0xffu) {
+        hi = sign | 0x7ff00000u | (mant >> 3);
+        lo = mant << 29;
+    } else {
+        hi = sign | ((e + 896u) << 20) | (mant >> 3);
+        lo = mant << 29;
+    }
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+
+template <typename T>
+__device__ __forceinline__ T to_tile(double x);
+template <>
+__device__ __forceinline__ float to_tile<float>(double x) { return narrow_trunc(x); }
+template <>
+__device__ __forceinline__ double to_tile<double>(double x) { return x; }
+
+template <typename T>
+__device__ __forceinline__ double to_f64(T x);
+template <>
+__device__ __forceinline__ double to_f64<float>(float x) { return widen(x); }
+template <>
+__device__ __forceinline__ double to_f64<double>(double x) { return x; }
+
+// value e of a source array as a tile element: the pre-rounded FP32 copy for
+// FP32 tiles, the FP64 value itself for FP64 tiles
+template <typename T>
+__device__ __forceinline__ T tile_value(const double *v64, const float *v32, int64_t e);
+template <>
+__device__ __forceinline__ float tile_value<float>(const double *, const float *v32, int64_t e) { return v32[e]; }
+template <>
+__device__ __forceinline__ double tile_value<double>(const double *v64, const float *, int64_t e) { return v64[e]; }
+
+// reflector arithmetic: hardware approximations suffice for the FP32
+// factorisation (its rounding is removed by the FP64 refinement); FP64
+// tiles keep correctly rounded sqrt and division
+__device__ __forceinline__ float refl_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ double refl_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float refl_neg_rcp(float x) { return -__frcp_rn(x); }
+__device__ __forceinline__ double refl_neg_rcp(double x) { return -1.0 / x; }
+
+__device__ __forceinline__ bool finite64(double x) {
+    return ((unsigned)(__double_as_longlong(x) >> 52) & 0x7ffu) != 0x7ffu;
+}
+
+// sum over the P lanes of a group (xor tree inside the aligned group)
+template <int P, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int o = 1; o < P; o <<= 1) v += shfl_xor(v, o);
+    return v;
+}
+
+// exclusive prefix over the P lanes of a group; *total gets the group sum
+template <int P>
+__device__ __forceinline__ int group_excl_scan(int v, int ll, int *total) {
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < P; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (ll >= o) incl += y;
+    }
+    *total = __shfl_sync(0xffffffffu, incl, (int)(threadIdx.x & 31) | (P - 1));
+    return incl - v;
+}
+
+// ---------------------------------------------------------- Householder QR
+
+template <class TL, int PH>
+struct QRPhase {
+    using T = typename TL::T;
+    static constexpr int RG = TL::RG, CG = TL::CG, RS = TL::RS, CS = TL::CS, L = TL::L;
+    static constexpr int K0 = PH * L;
+    static constexpr int SK = K0 / RG;  // row slot of this phase's pivots
+    static constexpr int TK = K0 / CG;  // column slot of this phase's pivots
+    static constexpr int NPH = (TL::MAXJ + L - 1) / L;
+
+    static __device__ __forceinline__ void run(T (&a)[RS][CS], int rg, int cg, int gbase, int nJ, int kmax) {
+        if constexpr (PH < NPH) {
+            if (K0 >= kmax) return;
+            const int kend = (K0 + L < kmax) ? K0 + L : kmax;
+            for (int k = K0; k < kend; ++k) {
+                const int ck = k - TK * CG;  // column group owning column k
+                const int rk = k - SK * RG;  // row group of row k inside slot SK
+                const bool active = k < nJ;
+                // squared norm of column k below the diagonal (two chains)
+                T sig0 = T(0), sig1 = T(0);
+#pragma unroll
+                for (int s = SK; s < RS; ++s) {
+                    T x = a[s][TK];
+                    if (s == SK) x = (rg > rk) ? x : T(0);
+                    if ((s - SK) & 1) sig1 = fma(x, x, sig1); else sig0 = fma(x, x, sig0);
+                }
+                T sig = sig0 + sig1;
+#pragma unroll
+                for (int o = 1; o < RG; o <<= 1) sig += shfl_xor(sig, o);
+                const T alpha = shfl(a[SK][TK], gbase + ck * RG + rk);
+                const T sigma = shfl(sig, gbase + ck * RG);
+                // reflector H = I - taup u u^T, u = x with u_k = alpha - beta
+                const T nrm = refl_sqrt(fma(alpha, alpha, sigma));
+                const T beta = (sigma == T(0)) ? alpha : ((alpha >= T(0)) ? -nrm : nrm);
+                const T uk = alpha - beta;
+                const T taup = (sigma == T(0) || !active) ? T(0) : refl_neg_rcp(beta * uk);
+                T u[RS - SK];
+#pragma unroll
+                for (int s = SK; s < RS; ++s) {
+                    T x = shfl(a[s][TK], gbase + ck * RG + rg);
+                    if (s == SK) x = (rg > rk) ? x : ((rg == rk) ? uk : T(0));
+                    u[s - SK] = x;
+                }
+#pragma unroll
+                for (int t = TK; t < CS; ++t) {
+                    T w0 = T(0), w1 = T(0);
+#pragma unroll
+                    for (int s = SK; s < RS; ++s) {
+                        if ((s - SK) & 1) w1 = fma(u[s - SK], a[s][t], w1); else w0 = fma(u[s - SK], a[s][t], w0);
+                    }
+                    T w = w0 + w1;
+#pragma unroll
+                    for (int o = 1; o < RG; o <<= 1) w += shfl_xor(w, o);
+                    // columns of slots after TK are all > k (L divides CG)
+                    const T coef = (t > TK || t * CG + cg > k) ? taup * w : T(0);
+#pragma unroll
+                    for (int s = SK; s < RS; ++s) a[s][t] = fma(-coef, u[s - SK], a[s][t]);
+                }
+                if (active && cg == ck && rg == rk) a[SK][TK] = beta;
+            }
+            QRPhase<TL, PH + 1>::run(a, rg, cg, gbase, nJ, kmax);
+        }
+    }
+};
+
+// ----------------------------------------------------- triangular solves
+// x[q] holds entry c = ll + P*q of the right-hand side (and the solution on
+// return).  Steps run in phases of P with the owning register slot fixed at
+// compile time; each step costs one shuffle.  Entries c >= n are untouched.
+
+template <class TL, int Q>
+struct SolveUpper {  // R x = y, k from high to low
+    using T = typename TL::T;
+    static __device__ __forceinline__ void run(const T *R, const T *dinv, T (&x)[TL::JQ], int n, int ll, int gbase) {
+        if constexpr (Q >= 0) {
+            constexpr int P = TL::P;
+            constexpr int KHI = (Q * P + P < TL::MAXJ) ? Q * P + P : TL::MAXJ;
+            for (int k = KHI - 1; k >= Q * P; --k) {
+                const int owner = k - Q * P;
+                T xk = x[Q] * dinv[k];
+                xk = shfl(xk, gbase + owner);
+                if (k >= n) xk = T(0);
+                if (ll == owner && k < n) x[Q] = xk;
+#pragma unroll
+                for (int q = 0; q <= Q; ++q) {
+                    const int i = ll + q * P;
+                    // rows of R at k >= n were never written: do not touch them
+                    if (i < k && k < n) x[q] = fma(-R[i * TL::RSTR + k], xk, x[q]);
+                }
+            }
+            SolveUpper<TL, Q - 1>::run(R, dinv, x, n, ll, gbase);
+        }
+    }
+};
+
+template <class TL, int Q>
+struct SolveUpperT {  // R^T x = y, k from low to high
+    using T = typename TL::T;
+    static __device__ __forceinline__ void run(const T *R, const T *dinv, T (&x)[TL::JQ], int n, int ll, int gbase) {
+        if constexpr (Q < TL::JQ) {
+            constexpr int P = TL::P;
+            constexpr int KHI = (Q * P + P < TL::MAXJ) ? Q * P + P : TL::MAXJ;
+            for (int k = Q * P; k < KHI; ++k) {
+                const int owner = k - Q * P;
+                T xk = x[Q] * dinv[k];
+                xk = shfl(xk, gbase + owner);
+                if (k >= n) xk = T(0);
+                if (ll == owner && k < n) x[Q] = xk;
+#pragma unroll
+                for (int q = Q; q < TL::JQ; ++q) {
+                    const int i = ll + q * P;
+                    if (i > k && i < n) x[q] = fma(-R[k * TL::RSTR + i], xk, x[q]);
+                }
+            }
+            SolveUpperT<TL, Q + 1>::run(R, dinv, x, n, ll, gbase);
+        }
+    }
+};
+
+// r = c - B m in FP64 over the row-major entry lists; returns this lane's
+// partial sum of r_i^2
+template <class TL, bool SQUARES = true>
+__device__ __forceinline__ double residual_rows(ProbSmem<TL> &S, const double *kcv, int nI, int ll) {
+    double r2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < TL::IQ; ++q) {
+        const int i = ll + q * TL::P;
+        if (i < nI) {
+            double ri = S.c[i];
+            const int pe = S.u.s.rowstart[i + 1];
+            for (int p = S.u.s.rowstart[i]; p < pe; ++p) ri = fma(-kcv[S.u.s.rowent[p]], S.m[S.u.s.rowcol[p]], ri);
+            S.u.s.r[i] = ri;
+            if (SQUARES) r2 = fma(ri, ri, r2);
+        }
+    }
+    return r2;
+}
+
+
+// --------------------------------------------------- size-class tile table
+// FP32 tiles per size class (bins: |I| <= 14/26/40/52/64, |J| <= 5/9/23/27/27)
+using F0 = Tile<2, 2, 7, 3, float, 14>;
+using F1 = Tile<2, 2, 13, 5, float, 26>;
+using F2 = Tile<4, 4, 10, 6, float, 40>;
+using F3 = Tile<4, 4, 13, 7, float, 52>;
+using F4 = Tile<4, 4, 16, 7, float, 64>;
+// FP64 tiles
+using D0 = Tile<2, 2, 7, 3, double, 14>;
+using D1 = Tile<2, 4, 13, 3, double, 26>;
+using D2 = Tile<4, 8, 10, 3, double, 40>;
+using D3 = Tile<4, 8, 13, 4, double, 52>;
+using D4 = Tile<4, 8, 16, 4, double, 64>;
+
+static_assert(F0::MAXI >= 14 && F0::MAXJ >= 5, "bin 0");
+static_assert(F1::MAXI >= 26 && F1::MAXJ >= 9, "bin 1");
+static_assert(F2::MAXI >= 40 && F2::MAXJ >= 23, "bin 2");
+static_assert(F3::MAXI >= 52 && F3::MAXJ >= 27, "bin 3");
+static_assert(F4::MAXI >= 64 && F4::MAXJ >= 27, "bin 4");
+static_assert(D1::MAXJ >= 9 && D2::MAXJ >= 23 && D3::MAXJ >= 27 && D4::MAXJ >= 27, "fp64 bins");
+
+// ----------------------------------------------------- one column problem
+// Per-lane state of the column problem owned by this lane's group, and the
+// stages shared by the forward build and its adjoint: gather of
+// A_k(I_j, J_j) and A_0(I_j, j) into the dense tile, the register tile, the
+// row-major entry lists, and the QR with its pivot checks.
+template <class TL>
+struct Column {
+    using T = typename TL::T;
+    static constexpr int P = TL::P, RG = TL::RG, CG = TL::CG, RS = TL::RS, CS = TL::CS;
+    static constexpr int MAXI = TL::MAXI, NCOL = TL::NCOL, MAXJ = TL::MAXJ, JQ = TL::JQ;
+    static constexpr int RPL = (MAXI + P - 1) / P;  // contiguous rows per lane (row prefix sums)
+
+    int ll, rg, cg, gbase;
+    bool valid;
+    int jj, jl, roff, jb, nJ, nI, zb, ze, nB, kmax;
+    int status;
+    int colA[JQ], clen[JQ], colB[JQ];
+    double out2;
+
+    __device__ __forceinline__ void begin(const LsqArgs &args, int item, int total, const int32_t *work) {
+        const int lane = threadIdx.x & 31;
+        ll = lane % P;
+        gbase = lane - ll;
+        rg = ll % RG;
+        cg = ll / RG;
+        valid = item < total;
+        jj = valid ? work[item] : 0;  // column of the block-diagonal batch
+        const int kmap = jj / args.n;
+        jl = jj - kmap * args.n;  // column of A_0
+        roff = kmap * args.n;     // row offset of this map
+        jb = nJ = nI = zb = ze = 0;
+        if (valid) {
+            jb = args.jcp[jj];
+            nJ = args.jcp[jj + 1] - jb;
+            nI = args.icnt[jj];
+            zb = args.zcp[jl];
+            ze = args.zcp[jl + 1];
+        }
+        status = kStOk;
+    }
+
+    // J columns, shadow rows, zeroed tile, gathered B and c (tile + FP64 c),
+    // column masks, local rows of every entry, out-of-shadow ||A_0||^2
+    __device__ __forceinline__ void gather(const LsqArgs &args, ProbSmem<TL> &S) {
+#pragma unroll
+        for (int q = 0; q < JQ; ++q) {
+            const int c = ll + q * P;
+            colA[q] = 0;
+            clen[q] = 0;
+            if (c < nJ) {
+                const int col = args.jri[jb + c];
+                colA[q] = args.kcp[col];
+                clen[q] = args.kcp[col + 1] - colA[q];
+            }
+        }
+        nB = 0;
+#pragma unroll
+        for (int q = 0; q < JQ; ++q) {
+            int tot;
+            colB[q] = nB + group_excl_scan<P>(clen[q], ll, &tot);
+            nB += tot;
+        }
+        for (int i = ll; i < MAXI; i += P) {
+            S.I[i] = (i < nI) ? args.ish[(int64_t)jj * kICap + i] : INT_MAX;
+            S.mask[i] = 0u;
+            S.c[i] = 0.0;
+        }
+        {
+            uint4 *tl = reinterpret_cast<uint4 *>(&S.u.tile[0][0][0]);
+            constexpr int NV = (int)(sizeof(S.u.tile) / sizeof(uint4));
+            for (int e = ll; e < NV; e += P) tl[e] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        __syncwarp();
+        const int32_t *kri = args.kri;
+#pragma unroll
+        for (int q = 0; q < JQ; ++q) {
+            const int c = ll + q * P;
+            const int len = clen[q];
+            for (int p0 = 0; p0 < len; p0 += 4) {
+                int rows[4];
+                T vals[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    rows[u] = (p0 + u < len) ? kri[colA[q] + p0 + u] : -1;
+                    vals[u] = (p0 + u < len) ? tile_value<T>(args.kcv, args.kcv32, colA[q] + p0 + u) : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (rows[u] < 0) continue;
+                    int i = find_sorted(S.I, nI, rows[u]);
+                    if (i < 0) {  // impossible for a consistent shadow: never write out of bounds
+                        status = kStUnsupported;
+                        i = 0;
+                    }
+                    S.locr[colB[q] + p0 + u] = (unsigned char)i;
+                    S.u.tile[c][i % RG][i / RG] = vals[u];
+                    atomicOr(&S.mask[i], 1u << c);
+                }
+            }
+        }
+        out2 = 0.0;
+        for (int t = zb + ll; t < ze; t += P) {
+            const int i = find_sorted(S.I, nI, args.zri[t] + roff);
+            const double v = args.zcv[t];
+            if (i >= 0) {
+                S.c[i] = v;
+                S.u.tile[NCOL - 1][i % RG][i / RG] = tile_value<T>(args.zcv, args.zcv32, t);
+            } else {
+                out2 = fma(v, v, out2);
+            }
+        }
+        out2 = group_sum<P>(out2);
+        __syncwarp();
+    }
+
+    __device__ __forceinline__ void load_tile(ProbSmem<TL> &S, T (&a)[RS][CS]) {
+        constexpr int VEC = TL::VEC;
+#pragma unroll
+        for (int t = 0; t < CS; ++t) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(&S.u.tile[t * CG + cg][rg][0]);
+#pragma unroll
+            for (int v = 0; v < TL::RSP / VEC; ++v) {
+                union {
+                    uint4 u;
+                    T e[VEC];
+                } w;
+                w.u = src[v];
+#pragma unroll
+                for (int q = 0; q < VEC; ++q)
+                    if (v * VEC + q < RS) a[v * VEC + q][t] = w.e[q];
+            }
+        }
+        __syncwarp();
+    }
+
+    // row-major entry lists (rowstart / rowent / rowcol) for products B x
+    __device__ __forceinline__ void build_rows(ProbSmem<TL> &S) {
+        int cnt = 0;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int i = ll * RPL + r;
+            if (i < nI) cnt += __popc(S.mask[i]);
+        }
+        int tot;
+        int run = group_excl_scan<P>(cnt, ll, &tot);
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int i = ll * RPL + r;
+            if (i < nI) {
+                S.u.s.rowstart[i] = run;
+                run += __popc(S.mask[i]);
+            }
+        }
+        if (ll == 0) S.u.s.rowstart[nI] = tot;
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < JQ; ++q) {
+            const int c = ll + q * P;
+            for (int p = 0; p < clen[q]; ++p) {
+                const int i = S.locr[colB[q] + p];
+                const int pos = S.u.s.rowstart[i] + __popc(S.mask[i] & ((1u << c) - 1u));
+                S.u.s.rowent[pos] = colA[q] + p;
+                S.u.s.rowcol[pos] = (unsigned char)c;
+            }
+        }
+    }
+
+    // QR of [B c]; R (odd stride), 1/R_kk and Q^T c to shared memory; a zero
+    // or non-finite pivot sets the status and clears nJ (no further work)
+    __device__ __forceinline__ void factor(ProbSmem<TL> &S, T (&a)[RS][CS]) {
+        kmax = nJ;
+#pragma unroll
+        for (int o = P; o < 32; o <<= 1) kmax = max(kmax, shfl_xor(kmax, o));
+        QRPhase<TL, 0>::run(a, rg, cg, gbase, nJ, kmax);
+#pragma unroll
+        for (int s = 0; s < RS; ++s)
+#pragma unroll
+            for (int t = 0; t < CS; ++t) {
+                const int i = s * RG + rg, col = t * CG + cg;
+                if (col < MAXJ && i <= col && col < nJ) S.u.s.R[i * TL::RSTR + col] = a[s][t];
+                if (col == NCOL - 1 && i < nJ) S.u.s.y[i] = a[s][t];
+            }
+        __syncwarp();
+        int st = kStOk;
+        for (int k = ll; k < nJ; k += P) {
+            const T rkk = S.u.s.R[k * TL::RSTR + k];
+            const double d = to_f64<T>(rkk);
+            if (!finite64(d)) st = max(st, (int)kStNonfinite);
+            else if (d == 0.0) st = max(st, (int)kStRank);
+            S.u.s.dinv[k] = T(1) / rkk;
+        }
+        status = max(status, st);
+#pragma unroll
+        for (int o = 1; o < P; o <<= 1) status = max(status, shfl_xor(status, o));
+        if (status != kStOk) nJ = 0;
+    }
+
+    // (R^T R)^{-1} applied in place to x (layout c = ll + P q)
+    __device__ __forceinline__ void normal_solve(ProbSmem<TL> &S, T (&x)[JQ]) {
+        SolveUpperT<TL, 0>::run(S.u.s.R, S.u.s.dinv, x, nJ, ll, gbase);
+        SolveUpper<TL, JQ - 1>::run(S.u.s.R, S.u.s.dinv, x, nJ, ll, gbase);
+    }
+
+    // (B^T v)_c in FP64 for the lane's own columns; v indexed by local row
+    __device__ __forceinline__ double bt_times(const LsqArgs &args, ProbSmem<TL> &S, const double *v, int q) {
+        double acc = 0.0;
+        for (int p = 0; p < clen[q]; ++p) acc = fma(args.kcv[colA[q] + p], v[S.locr[colB[q] + p]], acc);
+        return acc;
+    }
+};
+
+}  // namespace
+}  // namespace sam

@@ -176,6 +176,11 @@ __global__ void __launch_bounds__(kResWarps * 32) residual_rows_kernel(
     }
 }
 
+__global__ void round_f32_kernel(int64_t n, const double *in, float *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
 __global__ void status_max_kernel(const int32_t *st, int64_t n, int32_t *flag) {
     int m = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -279,6 +284,15 @@ cudaError_t residual_rows(sam_handle h, int n, const int32_t *krp, const int32_t
     if (blocks > cap) blocks = cap;
     residual_rows_kernel<<<blocks, kResWarps * 32, 0, handle_stream(h)>>>(n, krp, kci, kv, mrp, mci, mv, zrp, zci,
                                                                           zv, row_r2, flag);
+    count_launch(h);
+    return cudaGetLastError();
+}
+
+cudaError_t round_to_f32(sam_handle h, int64_t n, const double *in, float *out) {
+    if (n == 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)handle_sms(h) * 16) blocks = (int64_t)handle_sms(h) * 16;
+    round_f32_kernel<<<(unsigned)blocks, 256, 0, handle_stream(h)>>>(n, in, out);
     count_launch(h);
     return cudaGetLastError();
 }

@@ -541,7 +541,7 @@ __constant__ int c_bin_maxj[kNumBins] = {5, 9, 23, 27, 27};
 __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const int32_t *kcp, const int32_t *kri,
                                                                   const int32_t *jcp, const int32_t *jri,
                                                                   int32_t *ish, int32_t *icnt, uint8_t *bin,
-                                                                  int32_t *colstat) {
+                                                                  int32_t *colstat, int64_t *nbcnt) {
     __shared__ unsigned bms[kMergeWarps][kBitWords];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned *bm = bms[warp];
@@ -559,6 +559,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const i
                     }
             icnt[j] = u;
             bin[j] = (uint8_t)b;
+            if (nbcnt) nbcnt[j] = r.total;
             // fewer shadow rows than unknowns means a zero column: rank deficient
             colstat[j] = (b != kBinNone) ? kStOk : ((u >= 0 && u < nj) ? kStRank : kStUnsupported);
         }
@@ -659,9 +660,10 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
 }
 
 cudaError_t shadow_and_bins(sam_handle h, int N, const int32_t *kcp, const int32_t *kri, const int32_t *jcp,
-                            const int32_t *jri, int32_t *ish, int32_t *icnt, uint8_t *bin, int32_t *colstat) {
+                            const int32_t *jri, int32_t *ish, int32_t *icnt, uint8_t *bin, int32_t *colstat,
+                            int64_t *nbcnt) {
     shadow_kernel<<<merge_grid(h, N), kMergeWarps * 32, 0, handle_stream(h)>>>(N, kcp, kri, jcp, jri, ish, icnt, bin,
-                                                                              colstat);
+                                                                              colstat, nbcnt);
     count_launch(h);
     return cudaGetLastError();
 }
