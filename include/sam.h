@@ -235,6 +235,43 @@ sam_status sam_profile_read(sam_handle h, int64_t *launches, double *lsq_ms, int
  */
 sam_status sam_peak_flops(sam_handle h, double ms, double *fp32_flops, double *fp64_flops);
 
+/*
+ * sam_residual_static -- the same two numbers as sam_residual,
+ * ||A_k M_k - A_0||_F and ||A_k M_k - A_0||_F / ||A_0||_F, for callers that
+ * cannot allocate device memory.  The paper has no counterpart: this is an
+ * interface choice of the library.
+ *
+ * Who needs it: code that may not call cudaMalloc or any allocating routine
+ * -- a step running while the device memory budget is already handed out,
+ * a caller whose memory belongs to another framework's caching allocator,
+ * or an environment that only lends the library device buffers.
+ * sam_residual allocates its workspace from a handle's memory pool; this
+ * entry point takes no handle and allocates nothing.  Its workspace is one
+ * file-scope device array of fixed size (about 4.2 MB: one double per row
+ * for up to SAM_STATIC_MAX_ROWS rows, plus reduction partials and a status
+ * word) that every GPU which loads the library holds until the process
+ * exits.
+ *
+ * Arguments: cuda_stream (a cudaStream_t, NULL for the legacy stream); A_k,
+ * M_k, A_0 square CSR matrices of the same order n <= SAM_STATIC_MAX_ROWS;
+ * out (device, 2 doubles) receives ||R||_F and ||R||_F / ||A_0||_F; status
+ * (device, nullable) receives 0 or a sam_status detected on the device
+ * (SAM_ERR_BAD_CSR for a malformed structure, SAM_ERR_UNSUPPORTED for a row
+ * of R with more than 1024 candidate entries), in which case out holds zeros.
+ * Every array must be device or managed memory: host arrays are rejected
+ * (SAM_ERR_INVALID_ARG), as are orders above SAM_STATIC_MAX_ROWS.
+ * The call is asynchronous on cuda_stream.  Its first call on a device looks
+ * up the workspace's device address (cudaGetSymbolAddress) and caches it;
+ * make that first call before capturing the stream into a CUDA graph.
+ * Every call reuses the same workspace and clears what must start at zero,
+ * so a call never depends on an earlier one; calls whose work overlaps on
+ * the GPU (other streams or host threads) race on the workspace and must be
+ * serialised by the caller.
+ */
+#define SAM_STATIC_MAX_ROWS (1 << 19)
+sam_status sam_residual_static(void *cuda_stream, const sam_csr *A_k, const sam_csr *M_k, const sam_csr *A_0,
+                               double *out, int32_t *status);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,6 +32,7 @@ SAM_ERR_UNSUPPORTED = 8
 SAM_FP64 = 0
 SAM_FP32_REFINE = 1
 SAM_FLAG_TRUSTED = 1
+SAM_STATIC_MAX_ROWS = 1 << 19  # largest order sam_residual_static accepts
 
 PRECISIONS = {"fp64": SAM_FP64, "fp32r": SAM_FP32_REFINE}
 
@@ -87,6 +88,8 @@ _SIGS = [
     ("sam_profile", ctypes.c_int32, [_vp, ctypes.c_int]),
     ("sam_profile_read", ctypes.c_int32, [_vp, _i64p, ctypes.POINTER(ctypes.c_double), _i64p]),
     ("sam_peak_flops", ctypes.c_int32, [_vp, ctypes.c_double, _f64p, _f64p]),
+    ("sam_residual_static", ctypes.c_int32,
+     [_vp, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), _vp, _vp]),
 ]
 
 
@@ -148,6 +151,21 @@ def _addr(x) -> int:
             raise ValueError("array must be contiguous")
         return int(x.ctypes.data)
     raise TypeError("expected a torch tensor or numpy array, got %r" % type(x))
+
+
+def sam_residual_static(A_k: "Csr", M_k: "Csr", A_0: "Csr", out, status=None, stream=None):
+    """||A_k M_k - A_0||_F and its ratio to ||A_0||_F into the device array
+    `out` (2 float64) without allocating device memory (see include/sam.h);
+    all arrays must be on the device.  Asynchronous on `stream` (default:
+    torch's current stream)."""
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    a, m, z = A_k.c(), M_k.c(), A_0.c()
+    _check(load().sam_residual_static(_vp(int(stream.cuda_stream)), ctypes.byref(a), ctypes.byref(m), ctypes.byref(z),
+                                      _addr(out), _addr(status)), "sam_residual_static")
+    return out
 
 
 class Csr:
