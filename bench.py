@@ -107,6 +107,17 @@ def algorithmic_flops(I, J, nB, precision, steps):
     return f32, f64
 
 
+def kernel_hash() -> str:
+    """sha256 over the sources of the least-squares kernel (a recorded ncu
+    traffic figure is only reported while these are unchanged)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("lsq.cu", "lsq_core.cuh", "common.cuh"):
+        h.update(open(os.path.join(HERE, "paper_2406_17656_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 # ------------------------------------------------------------------ clocks
 
 
@@ -360,9 +371,10 @@ def main():
             import hashlib
 
             rec = json.load(open(tf))
-            src = open(os.path.join(HERE, "paper_2406_17656_gb300", "csrc", "lsq.cu"), "rb").read()
-            if rec.get("lsq_sha256") == hashlib.sha256(src).hexdigest() and str(dom) in rec.get("bytes_per_launch", {}):
-                traffic = rec["bytes_per_launch"][str(dom)]
+            if rec.get("kernel_sha256") == kernel_hash() and str(dom) in rec.get("bytes_per_column", {}):
+                # traffic per column from the capture, times this launch's columns
+                ncols = sum(int(np.sum(bin_of(I, J, nB) == dom)) for (I, J, nB) in sizes)
+                traffic = rec["bytes_per_column"][str(dom)] * ncols
         except Exception:
             traffic = None
     roofline = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",

@@ -695,7 +695,9 @@ sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_
     if (concat_block_diag(h, K, n, dtab, doff, brp, bci, bv) != cudaSuccess) return SAM_ERR_CUDA;
     if (csr_to_csc(h, (int)N, ktot, brp, bci, bv, kcp, kri, kcv, nullptr) != cudaSuccess) return SAM_ERR_CUDA;
     // shadow rows, size classes, work list
-    if (shadow_and_bins(h, (int)N, kcp, kri, g->jcp, g->jri, ish, icnt, bin, d_st) != cudaSuccess)
+    uint8_t *lrow = sc.get<uint8_t>((size_t)N * kLCap);
+    if (!lrow) return SAM_ERR_OOM;
+    if (shadow_and_bins(h, (int)N, kcp, kri, g->jcp, g->jri, ish, icnt, bin, d_st, nullptr, lrow) != cudaSuccess)
         return SAM_ERR_CUDA;
     if (build_work_list(h, (int)N, bin, work, bin_off) != cudaSuccess) return SAM_ERR_CUDA;
     cudaMemsetAsync(d_v, 0, sizeof(double) * (size_t)total_nnz, st);
@@ -720,6 +722,7 @@ sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_
     a.jri = g->jri;
     a.ish = ish;
     a.icnt = icnt;
+    a.lrow = lrow;
     a.zcp = zcp;
     a.zri = zri;
     a.zcv = zcv;
@@ -857,7 +860,9 @@ sam_status sam_build_backward(sam_handle h, const sam_csr *A_k, const sam_csr *A
     if (csr_to_csc(h, n, z.nnz, z.rp, z.ci, z.v, zcp, zri, zcv, zperm) != cudaSuccess ||
         csr_to_csc(h, n, ak.nnz, ak.rp, ak.ci, ak.v, kcp, kri, kcv, kperm) != cudaSuccess)
         return SAM_ERR_CUDA;
-    if (shadow_and_bins(h, n, kcp, kri, g->jcp, g->jri, ish, icnt, bin, colstat, nbcnt) != cudaSuccess ||
+    uint8_t *lrow = sc.get<uint8_t>((size_t)n * kLCap);
+    if (!lrow) return SAM_ERR_OOM;
+    if (shadow_and_bins(h, n, kcp, kri, g->jcp, g->jri, ish, icnt, bin, colstat, nbcnt, lrow) != cudaSuccess ||
         exclusive_scan_i64(h, nbcnt, dB_off, n) != cudaSuccess || build_work_list(h, n, bin, work, bin_off) != cudaSuccess)
         return SAM_ERR_CUDA;
     int64_t nbtot = 0;
@@ -887,6 +892,7 @@ sam_status sam_build_backward(sam_handle h, const sam_csr *A_k, const sam_csr *A
     a.jri = g->jri;
     a.ish = ish;
     a.icnt = icnt;
+    a.lrow = lrow;
     a.zcp = zcp;
     a.zri = zri;
     a.zcv = zcv;

@@ -24,6 +24,7 @@ namespace sam {
 constexpr int kICap = 64;    // max |I_j| (shadow rows) of one column problem
 constexpr int kJCap = 27;    // max |J_j| (unknowns) of one column problem
 constexpr int kNumBins = 5;  // size classes (see lsq.cu)
+constexpr int kLCap = 512;   // max stored entries of one column's B (8 per shadow row)
 constexpr int kBinNone = 255;
 
 // Per-column status codes written by the kernels (0 = ok); equal to the
@@ -48,6 +49,7 @@ struct LsqArgs {
     const float *kcv32;          // the same values rounded to FP32 (FP32 tiles)
     const int32_t *jcp, *jri;    // pattern (CSC, big)
     const int32_t *ish, *icnt;   // shadow rows (padded) and counts
+    const uint8_t *lrow;         // local shadow row of every gathered entry (padded [N][kLCap])
     const int32_t *zcp, *zri;    // CSC of the target A_0 (order n)
     const double *zcv;
     const float *zcv32;          // the same values rounded to FP32
@@ -115,10 +117,12 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
                          int32_t **jcp, int32_t **jri, int64_t *nnz_out);
 
 // Shadow rows (padded), |I_j| and size class of every column.
-// nbcnt (nullable) receives nnz(B_j) = sum of |A(:, c)| over c in J_j.
+// nbcnt (nullable) receives nnz(B_j) = sum of |A(:, c)| over c in J_j;
+// lrow (nullable, padded [N][kLCap]) the local shadow row of every entry of
+// A(:, J_j) in gather order, for the columns that have a size class.
 cudaError_t shadow_and_bins(sam_handle h, int N, const int32_t *kcp, const int32_t *kri, const int32_t *jcp,
                             const int32_t *jri, int32_t *ish, int32_t *icnt, uint8_t *bin, int32_t *colstat,
-                            int64_t *nbcnt = nullptr);
+                            int64_t *nbcnt = nullptr, uint8_t *lrow = nullptr);
 
 // Work list: columns grouped by size class; bin_off (device, [kNumBins+1]).
 cudaError_t build_work_list(sam_handle h, int N, const uint8_t *bin, int32_t *work, int32_t *bin_off);

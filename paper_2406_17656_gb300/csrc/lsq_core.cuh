@@ -29,8 +29,11 @@ struct Tile {
     static constexpr int JQ = (MAXJ + P - 1) / P;  // unknowns per lane (solves)
     static constexpr int IQ = (MAXI + P - 1) / P;  // rows per lane (residuals)
     static constexpr int RSTR = (MAXJ % 2) ? MAXJ : MAXJ + 1;  // odd row stride of R
-    static constexpr int VEC = 16 / (int)sizeof(T_);            // elements per 16-byte access
-    static constexpr int RSP = (RS + VEC - 1) / VEC * VEC;     // padded row slots per lane
+    static constexpr int VEC = 16 / (int)sizeof(T_);            // elements per 16-byte chunk
+    static constexpr int NCH0 = (RS + VEC - 1) / VEC;
+    static constexpr int NCH = NCH0 <= 1 ? 1 : NCH0 <= 2 ? 2 : NCH0 <= 4 ? 4 : NCH0 <= 8 ? 8 : 16;  // chunks per lane row
+    static constexpr int RSP = NCH * VEC;                      // padded row slots per lane
+    static constexpr int SWZ = (NCH < 4 ? NCH : 4) - 1;        // chunk swizzle mask
     using T = T_;
     static_assert(32 % P == 0, "group size must divide the warp");
     static_assert(MAXJ <= 31, "column masks are 32-bit");
@@ -49,9 +52,8 @@ struct ProbSmem {
     double lam[TL::MAXJ];  // adjoint multipliers (adjoint only)
     unsigned char locr[TL::NBCAP];
     union U {
-        // [B c], only until registers are loaded: element (i, col) at
-        // tile[col][i % RG][i / RG], so every lane's row slots are contiguous
-        __align__(16) T tile[TL::NCOL][TL::RG][TL::RSP];
+        // [B c], only until registers are loaded (see tile_pos)
+        __align__(16) T tile[TL::NCOL * TL::RG * TL::RSP];
         struct S {
             int rowstart[TL::MAXI + 1];
             int rowent[TL::NBCAP];
@@ -66,6 +68,19 @@ struct ProbSmem {
 };
 
 // ------------------------------------------------------------- utilities
+
+// Position of element (i, col) of [B c] in the shared tile.  The lane that
+// owns it (rg = i % RG, cg = col % CG) reads all its row slots of a column
+// as one contiguous "lane row" r = col RG + rg of RSP elements, in 16-byte
+// chunks; the chunk index is XOR-swizzled with (r >> 1) so that the eight
+// lanes of a quarter-warp hit eight different bank groups.
+template <class TL>
+__device__ __forceinline__ int tile_pos(int i, int col) {
+    const int r = col * TL::RG + (i % TL::RG);
+    const int s = i / TL::RG;
+    const int v = s / TL::VEC, q = s % TL::VEC;
+    return r * TL::RSP + (v ^ ((r >> 1) & TL::SWZ)) * TL::VEC + q;
+}
 
 __device__ __forceinline__ int find_sorted(const int *a, int len, int key) {
     int lo = 0, hi = len - 1;
@@ -402,34 +417,34 @@ struct Column {
             S.c[i] = 0.0;
         }
         {
-            uint4 *tl = reinterpret_cast<uint4 *>(&S.u.tile[0][0][0]);
+            uint4 *tl = reinterpret_cast<uint4 *>(&S.u.tile[0]);
             constexpr int NV = (int)(sizeof(S.u.tile) / sizeof(uint4));
             for (int e = ll; e < NV; e += P) tl[e] = make_uint4(0u, 0u, 0u, 0u);
         }
         __syncwarp();
-        const int32_t *kri = args.kri;
 #pragma unroll
         for (int q = 0; q < JQ; ++q) {
             const int c = ll + q * P;
             const int len = clen[q];
+            const uint8_t *lr = args.lrow + (int64_t)jj * kLCap + colB[q];
             for (int p0 = 0; p0 < len; p0 += 4) {
                 int rows[4];
                 T vals[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    rows[u] = (p0 + u < len) ? kri[colA[q] + p0 + u] : -1;
+                    rows[u] = (p0 + u < len) ? (int)lr[p0 + u] : -1;
                     vals[u] = (p0 + u < len) ? tile_value<T>(args.kcv, args.kcv32, colA[q] + p0 + u) : T(0);
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (rows[u] < 0) continue;
-                    int i = find_sorted(S.I, nI, rows[u]);
-                    if (i < 0) {  // impossible for a consistent shadow: never write out of bounds
+                    int i = rows[u];
+                    if (i >= nI) {  // impossible for a consistent shadow: never write out of bounds
                         status = kStUnsupported;
                         i = 0;
                     }
                     S.locr[colB[q] + p0 + u] = (unsigned char)i;
-                    S.u.tile[c][i % RG][i / RG] = vals[u];
+                    S.u.tile[tile_pos<TL>(i, c)] = vals[u];
                     atomicOr(&S.mask[i], 1u << c);
                 }
             }
@@ -440,7 +455,7 @@ struct Column {
             const double v = args.zcv[t];
             if (i >= 0) {
                 S.c[i] = v;
-                S.u.tile[NCOL - 1][i % RG][i / RG] = tile_value<T>(args.zcv, args.zcv32, t);
+                S.u.tile[tile_pos<TL>(i, NCOL - 1)] = tile_value<T>(args.zcv, args.zcv32, t);
             } else {
                 out2 = fma(v, v, out2);
             }
@@ -453,14 +468,17 @@ struct Column {
         constexpr int VEC = TL::VEC;
 #pragma unroll
         for (int t = 0; t < CS; ++t) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(&S.u.tile[t * CG + cg][rg][0]);
+            const int r = (t * CG + cg) * RG + rg;
+            const uint4 *row = reinterpret_cast<const uint4 *>(&S.u.tile[r * TL::RSP]);
+            const int swz = (r >> 1) & TL::SWZ;
 #pragma unroll
-            for (int v = 0; v < TL::RSP / VEC; ++v) {
+            for (int v = 0; v < TL::NCH; ++v) {
+                if (v * VEC >= RS) break;
                 union {
                     uint4 u;
                     T e[VEC];
                 } w;
-                w.u = src[v];
+                w.u = row[v ^ swz];
 #pragma unroll
                 for (int q = 0; q < VEC; ++q)
                     if (v * VEC + q < RS) a[v * VEC + q][t] = w.e[q];

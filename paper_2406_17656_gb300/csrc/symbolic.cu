@@ -372,13 +372,16 @@ __device__ int warp_sort_unique(int *buf, int cnt) {
 struct UnionResult {
     int count;  // distinct entries (-1: too many candidates for the fallback)
     int total;  // candidates, i.e. the sum of the list lengths
+    int mode;   // 0: bitmap over [lo, ...] left in shared memory, 1: sorted buffer
+    int lo;
 };
 
 // Union of the sorted lists X(:, l), l in Y(:, j).  The distinct values are
 // written ascending to out[0..min(count, cap)) when out != nullptr.  Every
 // lane returns the same result.
 __device__ UnionResult warp_union(int j, const int32_t *xcp, const int32_t *xri, const int32_t *ycp,
-                                  const int32_t *yri, unsigned *bm, int32_t *out, int cap) {
+                                  const int32_t *yri, unsigned *bm, int32_t *out, int cap,
+                                  unsigned char *wpre = nullptr) {
     const int lane = threadIdx.x & 31;
     const int yb = ycp[j], ye = ycp[j + 1];
     int lo = INT_MAX, hi = INT_MIN, total = 0;
@@ -397,7 +400,7 @@ __device__ UnionResult warp_union(int j, const int32_t *xcp, const int32_t *xri,
         hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
         total += __shfl_xor_sync(0xffffffffu, total, o);
     }
-    UnionResult res{0, total};
+    UnionResult res{0, total, 0, lo};
     if (total == 0) return res;
     const int64_t span = (int64_t)hi - lo + 1;
     if (span <= (int64_t)kBitWords * 32) {
@@ -424,6 +427,13 @@ __device__ UnionResult warp_union(int j, const int32_t *xcp, const int32_t *xri,
             if (lane >= o) incl += y;
         }
         res.count = __shfl_sync(0xffffffffu, incl, 31);
+        if (wpre) {  // rank of the first index of every word (saturating at 255)
+            int run = incl - cnt;
+            for (int w = w0; w < w1; ++w) {
+                wpre[w] = (unsigned char)(run < 255 ? run : 255);
+                run += __popc(bm[w]);
+            }
+        }
         if (out) {
             int pos = incl - cnt;
             for (int w = w0; w < w1 && pos < cap; ++w) {
@@ -465,6 +475,7 @@ __device__ UnionResult warp_union(int j, const int32_t *xcp, const int32_t *xri,
     __syncwarp();
     const int u = warp_sort_unique(buf, total);
     res.count = u;
+    res.mode = 1;
     if (out)
         for (int i = lane; i < u && i < cap; i += 32) out[i] = buf[i];
     __syncwarp();
@@ -541,22 +552,65 @@ __constant__ int c_bin_maxj[kNumBins] = {5, 9, 23, 27, 27};
 __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const int32_t *kcp, const int32_t *kri,
                                                                   const int32_t *jcp, const int32_t *jri,
                                                                   int32_t *ish, int32_t *icnt, uint8_t *bin,
-                                                                  int32_t *colstat, int64_t *nbcnt) {
+                                                                  int32_t *colstat, int64_t *nbcnt, uint8_t *lrow) {
     __shared__ unsigned bms[kMergeWarps][kBitWords];
+    __shared__ unsigned char pres[kMergeWarps][kBitWords];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned *bm = bms[warp];
+    unsigned char *wpre = pres[warp];
     for (int64_t j = (int64_t)blockIdx.x * kMergeWarps + warp; j < n; j += (int64_t)gridDim.x * kMergeWarps) {
-        UnionResult r = warp_union((int)j, kcp, kri, jcp, jri, bm, ish + j * kICap, kICap);
-        if (lane == 0) {
-            const int nj = jcp[j + 1] - jcp[j];
-            const int u = r.count;
-            int b = kBinNone;
-            if (u >= nj && u >= 0)
-                for (int q = 0; q < kNumBins; ++q)
-                    if (u <= c_bin_maxi[q] && nj <= c_bin_maxj[q] && r.total <= 8 * c_bin_maxi[q]) {
-                        b = q;
-                        break;
+        UnionResult r = warp_union((int)j, kcp, kri, jcp, jri, bm, ish + j * kICap, kICap, wpre);
+        const int nj = jcp[j + 1] - jcp[j];
+        const int u = r.count;
+        int b = kBinNone;
+        if (u >= nj && u >= 0)
+            for (int q = 0; q < kNumBins; ++q)
+                if (u <= c_bin_maxi[q] && nj <= c_bin_maxj[q] && r.total <= 8 * c_bin_maxi[q]) {
+                    b = q;
+                    break;
+                }
+        // local shadow row of every entry of A(:, J_j), in gather order (the
+        // columns of J_j in order, each in CSC order): its rank in I_j
+        if (lrow && b != kBinNone) {
+            const int yb = jcp[j], ye = jcp[j + 1];
+            int off = 0;
+            for (int base = yb; base < ye; base += 32) {
+                const int t = base + lane;
+                int xb = 0, len = 0;
+                if (t < ye) {
+                    const int l = jri[t];
+                    xb = kcp[l];
+                    len = kcp[l + 1] - xb;
+                }
+                int incl = len;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                uint8_t *dst = lrow + j * kLCap + off + incl - len;
+                for (int q = 0; q < len; ++q) {
+                    const int x = kri[xb + q];
+                    int rank;
+                    if (r.mode == 0) {
+                        const int d = x - r.lo;
+                        rank = wpre[d >> 5] + __popc(bm[d >> 5] & ((1u << (d & 31)) - 1u));
+                    } else {
+                        const int *srt = (const int *)bm;
+                        int lo = 0, hi = u - 1;
+                        rank = 0;
+                        while (lo <= hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (srt[mid] < x) lo = mid + 1; else if (srt[mid] > x) hi = mid - 1; else { rank = mid; break; }
+                        }
                     }
+                    dst[q] = (uint8_t)rank;
+                }
+                off += __shfl_sync(0xffffffffu, incl, 31);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
             icnt[j] = u;
             bin[j] = (uint8_t)b;
             if (nbcnt) nbcnt[j] = r.total;
@@ -661,9 +715,9 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
 
 cudaError_t shadow_and_bins(sam_handle h, int N, const int32_t *kcp, const int32_t *kri, const int32_t *jcp,
                             const int32_t *jri, int32_t *ish, int32_t *icnt, uint8_t *bin, int32_t *colstat,
-                            int64_t *nbcnt) {
+                            int64_t *nbcnt, uint8_t *lrow) {
     shadow_kernel<<<merge_grid(h, N), kMergeWarps * 32, 0, handle_stream(h)>>>(N, kcp, kri, jcp, jri, ish, icnt, bin,
-                                                                              colstat, nbcnt);
+                                                                              colstat, nbcnt, lrow);
     count_launch(h);
     return cudaGetLastError();
 }
