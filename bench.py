@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--level", type=int, default=2)
     ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--no-tune", action="store_true", help="default tile shapes instead of sam_tune's choice")
     return ap.parse_args()
 
 
@@ -319,6 +320,14 @@ def main():
             dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
         return float(ms_t.item()) / nsteps, fro, prof, (offs, out)
 
+    # ---- one-time tuning of the FP32 tile shapes on this workload (untimed)
+    variants = [0] * 5
+    if not args.no_tune:
+        pats = h.sam_pattern_build_batched(aks, args.level)
+        variants = h.sam_tune(aks, a0, pats, "fp32r", args.refine)
+        for p in pats:
+            p.destroy()
+
     # ---- headline: FP32 QR + FP64 refinement, level 2
     with ClockSampler(local) as clk:
         ms, fro, prof, (offs, out) = timed(args.level, "fp32r", args.refine, args.steps, args.warmup, profile=True)
@@ -449,7 +458,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": seq.name + "_seq%d_level%d" % (K, args.level), "n": n, "maps": K,
                            "level": args.level, "precision": "fp32 Householder QR + %d FP64 CSNE step(s)" % args.refine,
-                           "columns_per_step": cols_per_step, "parallelism": "replicas" if world > 1 else "single",
+                           "columns_per_step": cols_per_step, "tile_variants": variants, "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed between steps (256 MiB write outside the timed interval)"},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks, "cpu_baseline": cpu}

@@ -209,13 +209,34 @@ sam_status sam_build_backward(sam_handle h, const sam_csr *A_k, const sam_csr *A
                               double *dA_0_val, double *dM_resid);
 
 /*
- * sam_tune -- time the least-squares kernels' launch shapes on the columns of
- * the given problems and keep the fastest per size class in the handle (and
- * in the text file cache_path when it is not NULL).  Optional: the defaults
- * are used until it is called.
+ * sam_tune -- autotuner (no counterpart in the paper, which fixes one kernel
+ * shape).  For SAM_FP32_REFINE each size class has more than one register
+ * tile shape (variant 0: the default; variant 1: one problem per 8 or 32
+ * lanes with fewer register slots per lane).  The call runs the complete
+ * batched build of the given problems (as sam_build_batched, outputs to
+ * workspace it frees) once per variant plus one warm-up each, times every
+ * size class's least-squares launch with CUDA events, and keeps the fastest
+ * variant per size class in the handle; later builds on the handle use it.
+ * Results of every variant satisfy the same accuracy bounds (they differ
+ * only in rounding order).  cache_path (nullable): a text file with one line
+ * per tuned family, keyed by device name, SM count, K, n, total nnz(S),
+ * precision and refine_steps; a matching line is used without timing, and a
+ * new choice is appended.  SAM_FP64 has one shape per class: returns SAM_OK
+ * at once.  Synchronises the handle's stream.  Tracing counters of the
+ * handle are left as they were.  Errors: those of sam_build_batched;
+ * SAM_ERR_INVALID_ARG if cache_path cannot be opened for appending.
  */
 sam_status sam_tune(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0, const sam_pattern *S,
                     int precision, int refine_steps, const char *cache_path);
+
+/*
+ * sam_set_tile_variants / sam_get_tile_variants -- set or read the tile
+ * variant per size class (count must be 5; variant 0 for every class is the
+ * default of a new handle; class 0 has only variant 0).  Set: returns
+ * SAM_ERR_INVALID_ARG, changing nothing, if a value is out of range.
+ */
+sam_status sam_set_tile_variants(sam_handle h, const int *variants, int count);
+sam_status sam_get_tile_variants(sam_handle h, int *variants, int count);
 
 /*
  * sam_profile -- tracing.  enable != 0 starts timing every least-squares

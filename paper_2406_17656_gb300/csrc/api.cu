@@ -12,7 +12,9 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -35,6 +37,8 @@ struct sam_handle_t {
     std::vector<Ev> pending;
     double lsq_ms[sam::kNumBins] = {0};
     int64_t lsq_n[sam::kNumBins] = {0};
+    // FP32 tile shape per size class (sam_tune / sam_set_tile_variants)
+    int variant[sam::kNumBins] = {0};
 };
 
 namespace {
@@ -76,6 +80,7 @@ cudaStream_t handle_stream(sam_handle h) { return h->stream; }
 int handle_sms(sam_handle h) { return h->sms; }
 int32_t *handle_flag(sam_handle h) { return h->d_flag; }
 void count_launch(sam_handle h, int n) { h->launches += n; }
+int handle_variant(sam_handle h, int bin) { return h->variant[bin]; }
 
 void profile_begin(sam_handle h, int bin) {
     if (!h->profiling) return;
@@ -387,6 +392,42 @@ sam_status group_for(sam_handle h, int K, const sam_pattern *S, PatternGroup **g
     return group_finish(h, K, n, jcp, jri, tot, g_out);
 }
 
+}  // namespace
+
+namespace {
+// one line per tuned problem family:
+//   <device name with '_' for blanks> <SMs> <K> <n> <nnz(S) total> <precision> <steps> v0 .. v4
+std::string tune_key(sam_handle h, int K, int n, int64_t nnz, int precision, int steps) {
+    cudaDeviceProp p;
+    std::string name = "unknown";
+    if (cudaGetDeviceProperties(&p, h->device) == cudaSuccess) name = p.name;
+    cudaGetLastError();
+    for (char &c : name)
+        if (c == ' ' || c == '\t') c = '_';
+    char buf[160];
+    snprintf(buf, sizeof(buf), " %d %d %d %lld %d %d", h->sms, K, n, (long long)nnz, precision, steps);
+    return name + buf;
+}
+
+bool tune_lookup(const char *path, const std::string &key, int *v) {
+    FILE *f = path ? fopen(path, "r") : nullptr;
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (fgets(line, sizeof(line), f)) {
+        const size_t kl = key.size();
+        if (strncmp(line, key.c_str(), kl) != 0 || line[kl] != ' ') continue;
+        int t[kNumBins];
+        if (sscanf(line + kl, "%d %d %d %d %d", &t[0], &t[1], &t[2], &t[3], &t[4]) != kNumBins) continue;
+        bool ok = true;
+        for (int b = 0; b < kNumBins; ++b) ok = ok && t[b] >= 0 && t[b] < kTileVariants[b];
+        if (!ok) continue;
+        for (int b = 0; b < kNumBins; ++b) v[b] = t[b];
+        found = true;  // the last matching line wins
+    }
+    fclose(f);
+    return found;
+}
 }  // namespace
 
 extern "C" {
@@ -924,10 +965,105 @@ sam_status sam_build_backward(sam_handle h, const sam_csr *A_k, const sam_csr *A
     return cudaGetLastError() == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
 }
 
+sam_status sam_set_tile_variants(sam_handle h, const int *variants, int count) {
+    if (!h || !variants || count != kNumBins) return SAM_ERR_INVALID_ARG;
+    for (int b = 0; b < kNumBins; ++b)
+        if (variants[b] < 0 || variants[b] >= kTileVariants[b]) return SAM_ERR_INVALID_ARG;
+    for (int b = 0; b < kNumBins; ++b) h->variant[b] = variants[b];
+    return SAM_OK;
+}
+
+sam_status sam_get_tile_variants(sam_handle h, int *variants, int count) {
+    if (!h || !variants || count != kNumBins) return SAM_ERR_INVALID_ARG;
+    for (int b = 0; b < kNumBins; ++b) variants[b] = h->variant[b];
+    return SAM_OK;
+}
+
+
 sam_status sam_tune(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0, const sam_pattern *S, int precision,
                     int refine_steps, const char *cache_path) {
-    (void)h; (void)K; (void)A_k; (void)A_0; (void)S; (void)precision; (void)refine_steps; (void)cache_path;
-    return SAM_ERR_UNSUPPORTED;
+    if (!h || K < 1 || !A_k || !A_0 || !S) return SAM_ERR_INVALID_ARG;
+    if (precision != SAM_FP64 && precision != SAM_FP32_REFINE) return SAM_ERR_INVALID_ARG;
+    for (int k = 0; k < K; ++k)
+        if (!S[k]) return SAM_ERR_INVALID_ARG;
+    if (precision == SAM_FP64) return SAM_OK;  // one shape per size class: nothing to choose
+    std::vector<int64_t> off(K + 1, 0);
+    for (int k = 0; k < K; ++k) off[k + 1] = off[k] + S[k]->nnz;
+    const int n = A_0->n;
+    const std::string key = tune_key(h, K, n, off[K], precision, refine_steps);
+    int chosen[kNumBins];
+    if (tune_lookup(cache_path, key, chosen)) {
+        for (int b = 0; b < kNumBins; ++b) h->variant[b] = chosen[b];
+        return SAM_OK;
+    }
+    // outputs of the trial builds: device workspace of this call
+    Scratch sc(h);
+    int32_t *rp = sc.get<int32_t>((size_t)K * ((size_t)n + 1));
+    int32_t *ci = sc.get<int32_t>((size_t)off[K]);
+    double *v = sc.get<double>((size_t)off[K]);
+    if (!rp || !ci || !v) return SAM_ERR_OOM;
+    // the trial builds are timed with the tracing events; keep the caller's
+    profile_resolve(h);
+    const bool prof = h->profiling;
+    const int64_t launches = h->launches;
+    double keep_ms[kNumBins];
+    int64_t keep_n[kNumBins];
+    int saved[kNumBins];
+    for (int b = 0; b < kNumBins; ++b) {
+        keep_ms[b] = h->lsq_ms[b];
+        keep_n[b] = h->lsq_n[b];
+        saved[b] = h->variant[b];
+    }
+    constexpr int kTrials = 3;
+    double best[kNumBins];
+    for (int b = 0; b < kNumBins; ++b) {
+        best[b] = 1e300;
+        chosen[b] = 0;
+    }
+    sam_status result = SAM_OK;
+    int max_var = 1;
+    for (int b = 0; b < kNumBins; ++b) max_var = std::max(max_var, kTileVariants[b]);
+    for (int var = 0; var < max_var && result == SAM_OK; ++var) {
+        // every size class tries its variant `var` (the last one if it has fewer)
+        for (int b = 0; b < kNumBins; ++b) h->variant[b] = std::min(var, kTileVariants[b] - 1);
+        h->profiling = false;
+        result = sam_build_batched(h, K, A_k, A_0, S, precision, refine_steps, off.data(), rp, ci, v, nullptr,
+                                   nullptr, nullptr);  // warm-up
+        if (result != SAM_OK) break;
+        for (int b = 0; b < kNumBins; ++b) {
+            h->lsq_ms[b] = 0.0;
+            h->lsq_n[b] = 0;
+        }
+        h->profiling = true;
+        for (int t = 0; t < kTrials && result == SAM_OK; ++t)
+            result = sam_build_batched(h, K, A_k, A_0, S, precision, refine_steps, off.data(), rp, ci, v, nullptr,
+                                       nullptr, nullptr);
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) result = SAM_ERR_CUDA;
+        profile_resolve(h);
+        for (int b = 0; b < kNumBins; ++b) {
+            if (h->variant[b] != var || h->lsq_n[b] == 0) continue;
+            const double ms = h->lsq_ms[b] / (double)h->lsq_n[b];
+            if (ms < best[b]) {
+                best[b] = ms;
+                chosen[b] = var;
+            }
+        }
+    }
+    h->profiling = prof;
+    h->launches = launches;
+    for (int b = 0; b < kNumBins; ++b) {
+        h->lsq_ms[b] = keep_ms[b];
+        h->lsq_n[b] = keep_n[b];
+        h->variant[b] = result == SAM_OK ? chosen[b] : saved[b];
+    }
+    if (result != SAM_OK) return result;
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (!f) return SAM_ERR_INVALID_ARG;
+        fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), chosen[0], chosen[1], chosen[2], chosen[3], chosen[4]);
+        fclose(f);
+    }
+    return SAM_OK;
 }
 
 sam_status sam_profile(sam_handle h, int enable) {

@@ -92,6 +92,11 @@ int32_t *handle_flag(sam_handle h);  // device int32 error word (sticky)
 void count_launch(sam_handle h, int n = 1);
 void profile_begin(sam_handle h, int bin);
 void profile_end(sam_handle h, int bin);
+// FP32 tile shape of a size class chosen by sam_tune (0: two problems per
+// warp where the tile allows, 1: the alternative shape)
+int handle_variant(sam_handle h, int bin);
+// number of FP32 tile shapes per size class
+constexpr int kTileVariants[kNumBins] = {1, 2, 2, 2, 2};
 
 // out[0..n] = exclusive scan of in[0..n), out[n] = total
 cudaError_t exclusive_scan_i32(sam_handle h, const int32_t *in, int32_t *out, int64_t n);

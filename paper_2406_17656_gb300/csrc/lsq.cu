@@ -194,14 +194,18 @@ cudaError_t launch_lsq(sam_handle h, int precision, const LsqArgs &args) {
         if ((e = launch_one<D2, true>(h, args, 2)) != cudaSuccess) return e;
         if ((e = launch_one<D3, true>(h, args, 3)) != cudaSuccess) return e;
         if ((e = launch_one<D4, true>(h, args, 4)) != cudaSuccess) return e;
-    } else {
-        if ((e = launch_one<F0, false>(h, args, 0)) != cudaSuccess) return e;
-        if ((e = launch_one<F1, false>(h, args, 1)) != cudaSuccess) return e;
-        if ((e = launch_one<F2, false>(h, args, 2)) != cudaSuccess) return e;
-        if ((e = launch_one<F3, false>(h, args, 3)) != cudaSuccess) return e;
-        if ((e = launch_one<F4, false>(h, args, 4)) != cudaSuccess) return e;
+        return cudaSuccess;
     }
-    return cudaSuccess;
+    // FP32 tiles: the shape of each size class comes from the handle (sam_tune)
+    if ((e = launch_one<F0, false>(h, args, 0)) != cudaSuccess) return e;
+    e = handle_variant(h, 1) ? launch_one<F1b, false>(h, args, 1) : launch_one<F1, false>(h, args, 1);
+    if (e != cudaSuccess) return e;
+    e = handle_variant(h, 2) ? launch_one<F2b, false>(h, args, 2) : launch_one<F2, false>(h, args, 2);
+    if (e != cudaSuccess) return e;
+    e = handle_variant(h, 3) ? launch_one<F3b, false>(h, args, 3) : launch_one<F3, false>(h, args, 3);
+    if (e != cudaSuccess) return e;
+    e = handle_variant(h, 4) ? launch_one<F4b, false>(h, args, 4) : launch_one<F4, false>(h, args, 4);
+    return e;
 }
 
 }  // namespace sam

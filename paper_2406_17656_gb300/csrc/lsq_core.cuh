@@ -342,7 +342,15 @@ using D2 = Tile<4, 8, 10, 3, double, 40>;
 using D3 = Tile<4, 8, 13, 4, double, 52>;
 using D4 = Tile<4, 8, 16, 4, double, 64>;
 
+// alternative shapes for the autotuner: one problem per 8 or 32 lanes
+using F1b = Tile<2, 4, 13, 3, float, 26>;
+using F2b = Tile<4, 8, 10, 3, float, 40>;
+using F3b = Tile<4, 8, 13, 4, float, 52>;
+using F4b = Tile<4, 8, 16, 4, float, 64>;
+
 static_assert(F0::MAXI >= 14 && F0::MAXJ >= 5, "bin 0");
+static_assert(F1b::MAXI >= 26 && F1b::MAXJ >= 9 && F2b::MAXI >= 40 && F2b::MAXJ >= 23, "variants");
+static_assert(F3b::MAXI >= 52 && F3b::MAXJ >= 27 && F4b::MAXI >= 64 && F4b::MAXJ >= 27, "variants");
 static_assert(F1::MAXI >= 26 && F1::MAXJ >= 9, "bin 1");
 static_assert(F2::MAXI >= 40 && F2::MAXJ >= 23, "bin 2");
 static_assert(F3::MAXI >= 52 && F3::MAXJ >= 27, "bin 3");
@@ -426,6 +434,9 @@ struct Column {
         for (int q = 0; q < JQ; ++q) {
             const int c = ll + q * P;
             const int len = clen[q];
+            // local shadow rows of the entries, computed with the shadow rows
+            // (read straight from global memory: staging them through shared
+            // memory first measured 2x slower in the FP64 kernel)
             const uint8_t *lr = args.lrow + (int64_t)jj * kLCap + colB[q];
             for (int p0 = 0; p0 < len; p0 += 4) {
                 int rows[4];

@@ -555,6 +555,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const i
                                                                   int32_t *colstat, int64_t *nbcnt, uint8_t *lrow) {
     __shared__ unsigned bms[kMergeWarps][kBitWords];
     __shared__ unsigned char pres[kMergeWarps][kBitWords];
+    __shared__ __align__(16) unsigned char stg[kMergeWarps][kLCap];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned *bm = bms[warp];
     unsigned char *wpre = pres[warp];
@@ -570,9 +571,11 @@ __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const i
                     break;
                 }
         // local shadow row of every entry of A(:, J_j), in gather order (the
-        // columns of J_j in order, each in CSC order): its rank in I_j
+        // columns of J_j in order, each in CSC order): its rank in I_j,
+        // staged in shared memory and written out as 32-bit words
         if (lrow && b != kBinNone) {
             const int yb = jcp[j], ye = jcp[j + 1];
+            unsigned char *stage = stg[warp];
             int off = 0;
             for (int base = yb; base < ye; base += 32) {
                 const int t = base + lane;
@@ -588,7 +591,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const i
                     const int y = __shfl_up_sync(0xffffffffu, incl, o);
                     if (lane >= o) incl += y;
                 }
-                uint8_t *dst = lrow + j * kLCap + off + incl - len;
+                unsigned char *dst = stage + off + incl - len;
                 for (int q = 0; q < len; ++q) {
                     const int x = kri[xb + q];
                     int rank;
@@ -604,10 +607,14 @@ __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const i
                             if (srt[mid] < x) lo = mid + 1; else if (srt[mid] > x) hi = mid - 1; else { rank = mid; break; }
                         }
                     }
-                    dst[q] = (uint8_t)rank;
+                    dst[q] = (unsigned char)rank;
                 }
                 off += __shfl_sync(0xffffffffu, incl, 31);
             }
+            __syncwarp();
+            const unsigned *src = reinterpret_cast<const unsigned *>(stage);
+            unsigned *out = reinterpret_cast<unsigned *>(lrow + j * kLCap);
+            for (int w = lane; w < (r.total + 3) / 4; w += 32) out[w] = src[w];
         }
         __syncwarp();
         if (lane == 0) {

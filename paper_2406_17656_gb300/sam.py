@@ -85,6 +85,8 @@ _SIGS = [
     ("sam_tune", ctypes.c_int32,
      [_vp, ctypes.c_int, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(_vp), ctypes.c_int,
       ctypes.c_int, ctypes.c_char_p]),
+    ("sam_set_tile_variants", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    ("sam_get_tile_variants", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("sam_profile", ctypes.c_int32, [_vp, ctypes.c_int]),
     ("sam_profile_read", ctypes.c_int32, [_vp, _i64p, ctypes.POINTER(ctypes.c_double), _i64p]),
     ("sam_peak_flops", ctypes.c_int32, [_vp, ctypes.c_double, _f64p, _f64p]),
@@ -392,6 +394,29 @@ class Handle:
                                          int(refine_steps), _addr(M_val), _addr(dM_val), float(resid_weight),
                                          _addr(dA_k_val), _addr(dA_0_val), _addr(dM_resid)), "sam_build_backward")
         return dA_k_val, dA_0_val
+
+    # ---------------------------------------------------------------- tuning
+    def sam_tune(self, A_ks: list, A_0: Csr, Ss: list, precision="fp32r", refine_steps: int = 1,
+                 cache_path: str | None = None):
+        """Time the tile variants of every size class on these problems and
+        keep the fastest in the handle; returns the chosen variants."""
+        K = len(A_ks)
+        prec = PRECISIONS.get(precision, precision)
+        arr = (sam_csr * K)(*[a.c() for a in A_ks])
+        z = A_0.c()
+        pats = (_vp * K)(*[s.ptr for s in Ss])
+        _check(load().sam_tune(self.ptr, K, arr, ctypes.byref(z), pats, int(prec), int(refine_steps),
+                               cache_path.encode() if cache_path else None), "sam_tune")
+        return self.sam_get_tile_variants()
+
+    def sam_set_tile_variants(self, variants):
+        v = (ctypes.c_int * 5)(*[int(x) for x in variants])
+        _check(load().sam_set_tile_variants(self.ptr, v, len(variants)), "sam_set_tile_variants")
+
+    def sam_get_tile_variants(self):
+        v = (ctypes.c_int * 5)()
+        _check(load().sam_get_tile_variants(self.ptr, v, 5), "sam_get_tile_variants")
+        return list(v)
 
     def sam_profile(self, enable: bool):
         _check(load().sam_profile(self.ptr, int(bool(enable))), "sam_profile")
