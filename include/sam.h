@@ -164,6 +164,17 @@ sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_
                              double *M_val, int32_t *col_status, double *res2, double *fro);
 
 /*
+ * sam_build_multi -- as sam_build_batched, but map k has its own target:
+ * A_0[0..K-1] (all of order n), M_k = argmin ||A_k M - A_0[k]||_F on S[k].
+ * For batches of independent (A_0, A_1) pairs; fro[k] is the residual of
+ * map k against A_0[k].  Same outputs, errors and synchronisation.
+ */
+sam_status sam_build_multi(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0,
+                           const sam_pattern *S, int precision, int refine_steps,
+                           const int64_t *M_offsets, int32_t *M_row_ptr, int32_t *M_col_idx,
+                           double *M_val, int32_t *col_status, double *res2, double *fro);
+
+/*
  * sam_residual -- ||R_k||_F and ||R_k||_F / ||A_0||_F for R_k = A_k M_k - A_0
  * (Eq. (res); the relative form is the metric of Sec. 5), computed in FP64
  * column by column with a deterministic reduction.  fro and rel are host
@@ -207,6 +218,21 @@ sam_status sam_build_backward(sam_handle h, const sam_csr *A_k, const sam_csr *A
                               int precision, int refine_steps, const double *M_val,
                               const double *dM_val, double resid_weight, double *dA_k_val,
                               double *dA_0_val, double *dM_resid);
+
+/*
+ * sam_build_backward_batched -- sam_build_backward for K maps in one pass,
+ * map k built from A_k[k] against its own target A_0[k] on S[k] (pass the
+ * same A_0 K times for a shared target; its gradient is then returned per
+ * map).  M_offsets[K+1] (host): offsets of each map's values in M_val,
+ * dM_val and dM_resid (concatenated CSR orders, as sam_build_multi writes
+ * them).  dA_k_val: the K gradients concatenated in the order of A_k
+ * (sum of nnz(A_k[k]) values); dA_0_val: likewise for A_0.
+ */
+sam_status sam_build_backward_batched(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0,
+                                      const sam_pattern *S, int precision, int refine_steps,
+                                      const int64_t *M_offsets, const double *M_val,
+                                      const double *dM_val, double resid_weight, double *dA_k_val,
+                                      double *dA_0_val, double *dM_resid);
 
 /*
  * sam_tune -- autotuner (no counterpart in the paper, which fixes one kernel

@@ -653,16 +653,64 @@ sam_status sam_pattern_destroy(sam_pattern S) {
     return SAM_OK;
 }
 
-sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0, const sam_pattern *S,
-                             int precision, int refine_steps, const int64_t *M_offsets, int32_t *M_row_ptr,
-                             int32_t *M_col_idx, double *M_val, int32_t *col_status, double *res2, double *fro) {
+}  // extern "C"
+
+namespace {
+
+// K matrices of order n as one block-diagonal CSC of order K n (with the
+// CSC -> CSR permutation when perm != nullptr); K = 1 skips the copy.
+sam_status block_diag_csc(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms, int n, int32_t **cp,
+                          int32_t **ri, double **cv, int32_t **perm, int64_t *total) {
+    const int K = (int)ms.size();
+    const int64_t N = (int64_t)K * n;
+    int64_t tot = 0;
+    std::vector<CsrPtrs> tab(K);
+    std::vector<int64_t> off(K + 1, 0);
+    for (int k = 0; k < K; ++k) {
+        tab[k] = {ms[k].rp, ms[k].ci, ms[k].v};
+        off[k + 1] = off[k] + ms[k].nnz;
+    }
+    tot = off[K];
+    *total = tot;
+    *cp = sc.get<int32_t>((size_t)N + 1);
+    *ri = sc.get<int32_t>((size_t)tot);
+    *cv = sc.get<double>((size_t)tot);
+    if (perm) *perm = sc.get<int32_t>((size_t)tot);
+    if (!*cp || !*ri || !*cv || (perm && !*perm)) return SAM_ERR_OOM;
+    const int32_t *rp = ms[0].rp, *ci = ms[0].ci;
+    const double *v = ms[0].v;
+    if (K > 1) {
+        CsrPtrs *dtab = sc.get<CsrPtrs>(K);
+        int64_t *doff = sc.get<int64_t>(K + 1);
+        int32_t *brp = sc.get<int32_t>((size_t)N + 1), *bci = sc.get<int32_t>((size_t)tot);
+        double *bv = sc.get<double>((size_t)tot);
+        if (!dtab || !doff || !brp || !bci || !bv) return SAM_ERR_OOM;
+        cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * K, cudaMemcpyHostToDevice, h->stream);
+        cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, h->stream);
+        if (concat_block_diag(h, K, n, dtab, doff, brp, bci, bv) != cudaSuccess) return SAM_ERR_CUDA;
+        rp = brp;
+        ci = bci;
+        v = bv;
+    }
+    if (csr_to_csc(h, (int)N, tot, rp, ci, v, *cp, *ri, *cv, perm ? *perm : nullptr) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    return SAM_OK;
+}
+
+// K maps of order n against NT = 1 shared target or NT = K targets (one per map)
+sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0, int NT, const sam_pattern *S,
+                      int precision, int refine_steps, const int64_t *M_offsets, int32_t *M_row_ptr,
+                      int32_t *M_col_idx, double *M_val, int32_t *col_status, double *res2, double *fro) {
     if (!h || K < 1 || !A_k || !A_0 || !S || !M_offsets || !M_row_ptr || !M_col_idx || !M_val)
         return SAM_ERR_INVALID_ARG;
     if (precision != SAM_FP64 && precision != SAM_FP32_REFINE) return SAM_ERR_INVALID_ARG;
     if (refine_steps < 0 || refine_steps > 4) return SAM_ERR_INVALID_ARG;
-    if (check_csr_arg(A_0, true) != SAM_OK) return SAM_ERR_INVALID_ARG;
-    const int n = A_0->n;
-    int64_t ktot = 0;
+    const int n = A_0[0].n;
+    int64_t ktot = 0, ztot = 0;
+    for (int t = 0; t < NT; ++t) {
+        if (check_csr_arg(&A_0[t], true) != SAM_OK || A_0[t].n != n) return SAM_ERR_INVALID_ARG;
+        ztot += A_0[t].nnz;
+    }
     if (M_offsets[0] != 0) return SAM_ERR_INVALID_ARG;
     for (int k = 0; k < K; ++k) {
         if (check_csr_arg(&A_k[k], true) != SAM_OK || A_k[k].n != n || !S[k] || S[k]->n != n)
@@ -672,11 +720,13 @@ sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_
     }
     const int64_t N = (int64_t)K * n;
     const int64_t total_nnz = M_offsets[K];
-    if (N > INT32_MAX - 1 || ktot > INT32_MAX || total_nnz > INT32_MAX) return SAM_ERR_INVALID_ARG;
+    if (N > INT32_MAX - 1 || ktot > INT32_MAX || ztot > INT32_MAX || total_nnz > INT32_MAX)
+        return SAM_ERR_INVALID_ARG;
     cudaStream_t st = h->stream;
     Scratch sc(h);
     Stager sg(sc, st);
-    DevCsr z = stage_csr(sg, A_0, true);
+    std::vector<DevCsr> zs(NT);
+    for (int t = 0; t < NT; ++t) zs[t] = stage_csr(sg, &A_0[t], true);
     std::vector<DevCsr> ak(K);
     for (int k = 0; k < K; ++k) ak[k] = stage_csr(sg, &A_k[k], true);
     int32_t *d_rp = sg.out(M_row_ptr, (size_t)K * ((size_t)n + 1));
@@ -687,7 +737,7 @@ sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_
     if (sg.failed) return SAM_ERR_OOM;
     {
         std::vector<DevCsr> all(ak);
-        all.push_back(z);
+        all.insert(all.end(), zs.begin(), zs.end());
         sam_status s = validate_all(h, sc, all);
         if (s != SAM_OK) return s;
     }
@@ -704,40 +754,23 @@ sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_
             if (temp) group_release(g);
         }
     } guard{g, temp};
-    // target: CSC with values
-    int32_t *zcp = sc.get<int32_t>((size_t)n + 1), *zri = sc.get<int32_t>((size_t)z.nnz);
-    double *zcv = sc.get<double>((size_t)z.nnz);
-    if (!zcp || !zri || !zcv) return SAM_ERR_OOM;
-    if (csr_to_csc(h, n, z.nnz, z.rp, z.ci, z.v, zcp, zri, zcv, nullptr) != cudaSuccess) return SAM_ERR_CUDA;
-    // sources: block-diagonal CSR, then CSC with values
-    std::vector<CsrPtrs> tab(K);
-    std::vector<int64_t> off(K + 1, 0);
-    for (int k = 0; k < K; ++k) {
-        tab[k] = {ak[k].rp, ak[k].ci, ak[k].v};
-        off[k + 1] = off[k] + ak[k].nnz;
-    }
-    CsrPtrs *dtab = sc.get<CsrPtrs>(K);
-    int64_t *doff = sc.get<int64_t>(K + 1);
-    int32_t *brp = sc.get<int32_t>((size_t)N + 1), *bci = sc.get<int32_t>((size_t)ktot);
-    double *bv = sc.get<double>((size_t)ktot);
-    int32_t *kcp = sc.get<int32_t>((size_t)N + 1), *kri = sc.get<int32_t>((size_t)ktot);
-    double *kcv = sc.get<double>((size_t)ktot);
+    // target(s) and sources as CSC with values
+    int32_t *zcp = nullptr, *zri = nullptr, *kcp = nullptr, *kri = nullptr;
+    double *zcv = nullptr, *kcv = nullptr;
+    int64_t zn = 0, kn = 0;
+    sam_status s = block_diag_csc(h, sc, zs, n, &zcp, &zri, &zcv, nullptr, &zn);
+    if (s != SAM_OK) return s;
+    s = block_diag_csc(h, sc, ak, n, &kcp, &kri, &kcv, nullptr, &kn);
+    if (s != SAM_OK) return s;
     int32_t *ish = sc.get<int32_t>((size_t)N * kICap), *icnt = sc.get<int32_t>((size_t)N);
     uint8_t *bin = sc.get<uint8_t>((size_t)N);
     int32_t *work = sc.get<int32_t>((size_t)N);
     int32_t *bin_off = sc.get<int32_t>(kNumBins + 1), *tickets = sc.get<int32_t>(kNumBins);
     if (!d_st) d_st = sc.get<int32_t>((size_t)N);
     if (!d_r2) d_r2 = sc.get<double>((size_t)N);
-    if (!dtab || !doff || !brp || !bci || !bv || !kcp || !kri || !kcv || !ish || !icnt || !bin || !work ||
-        !bin_off || !tickets || !d_st || !d_r2)
-        return SAM_ERR_OOM;
-    cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * K, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, st);
-    if (concat_block_diag(h, K, n, dtab, doff, brp, bci, bv) != cudaSuccess) return SAM_ERR_CUDA;
-    if (csr_to_csc(h, (int)N, ktot, brp, bci, bv, kcp, kri, kcv, nullptr) != cudaSuccess) return SAM_ERR_CUDA;
-    // shadow rows, size classes, work list
     uint8_t *lrow = sc.get<uint8_t>((size_t)N * kLCap);
-    if (!lrow) return SAM_ERR_OOM;
+    if (!ish || !icnt || !bin || !work || !bin_off || !tickets || !d_st || !d_r2 || !lrow) return SAM_ERR_OOM;
+    // shadow rows, size classes, work list
     if (shadow_and_bins(h, (int)N, kcp, kri, g->jcp, g->jri, ish, icnt, bin, d_st, nullptr, lrow) != cudaSuccess)
         return SAM_ERR_CUDA;
     if (build_work_list(h, (int)N, bin, work, bin_off) != cudaSuccess) return SAM_ERR_CUDA;
@@ -745,10 +778,10 @@ sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_
     cudaMemsetAsync(d_r2, 0, sizeof(double) * (size_t)N, st);
     float *kcv32 = nullptr, *zcv32 = nullptr;
     if (precision == SAM_FP32_REFINE) {
-        kcv32 = sc.get<float>((size_t)ktot);
-        zcv32 = sc.get<float>((size_t)z.nnz);
+        kcv32 = sc.get<float>((size_t)kn);
+        zcv32 = sc.get<float>((size_t)zn);
         if (!kcv32 || !zcv32) return SAM_ERR_OOM;
-        if (round_to_f32(h, ktot, kcv, kcv32) != cudaSuccess || round_to_f32(h, z.nnz, zcv, zcv32) != cudaSuccess)
+        if (round_to_f32(h, kn, kcv, kcv32) != cudaSuccess || round_to_f32(h, zn, zcv, zcv32) != cudaSuccess)
             return SAM_ERR_CUDA;
     }
     LsqArgs a;
@@ -767,6 +800,7 @@ sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_
     a.zcp = zcp;
     a.zri = zri;
     a.zcv = zcv;
+    a.zbig = NT > 1 ? 1 : 0;
     a.csr_pos = g->csr_pos;
     a.mval = d_v;
     a.colres = d_r2;
@@ -790,12 +824,30 @@ sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_
         std::vector<double> f2(K);
         if (cudaMemcpyAsync(f2.data(), fro_dev, sizeof(double) * K, cudaMemcpyDeviceToHost, st) != cudaSuccess)
             return SAM_ERR_CUDA;
-        sam_status s = drain_status(h);
+        s = drain_status(h);
         for (int k = 0; k < K; ++k) fro[k] = sqrt(f2[k]);
         return s;
     }
     if (sg.has_host_outputs()) return drain_status(h);
     return cudaGetLastError() == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0, const sam_pattern *S,
+                             int precision, int refine_steps, const int64_t *M_offsets, int32_t *M_row_ptr,
+                             int32_t *M_col_idx, double *M_val, int32_t *col_status, double *res2, double *fro) {
+    return build_impl(h, K, A_k, A_0, 1, S, precision, refine_steps, M_offsets, M_row_ptr, M_col_idx, M_val,
+                      col_status, res2, fro);
+}
+
+sam_status sam_build_multi(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0, const sam_pattern *S,
+                           int precision, int refine_steps, const int64_t *M_offsets, int32_t *M_row_ptr,
+                           int32_t *M_col_idx, double *M_val, int32_t *col_status, double *res2, double *fro) {
+    return build_impl(h, K, A_k, A_0, K, S, precision, refine_steps, M_offsets, M_row_ptr, M_col_idx, M_val,
+                      col_status, res2, fro);
 }
 
 sam_status sam_build(sam_handle h, const sam_csr *A_k, const sam_csr *A_0, sam_pattern S, int precision,
@@ -849,30 +901,55 @@ sam_status sam_apply(sam_handle h, const sam_csr *M_k, const double *x, double *
     return SAM_OK;
 }
 
-sam_status sam_build_backward(sam_handle h, const sam_csr *A_k, const sam_csr *A_0, sam_pattern S, int precision,
-                              int refine_steps, const double *M_val, const double *dM_val, double resid_weight,
-                              double *dA_k_val, double *dA_0_val, double *dM_resid) {
-    if (!h || !S || !M_val || !dA_k_val || !dA_0_val) return SAM_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// adjoint of K maps, each against its own target
+sam_status backward_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0, const sam_pattern *S,
+                         int precision, int refine_steps, const int64_t *M_offsets, const double *M_val,
+                         const double *dM_val, double resid_weight, double *dA_k_val, double *dA_0_val,
+                         double *dM_resid) {
+    if (!h || K < 1 || !A_k || !A_0 || !S || !M_offsets || !M_val || !dA_k_val || !dA_0_val)
+        return SAM_ERR_INVALID_ARG;
     if (precision != SAM_FP64 && precision != SAM_FP32_REFINE) return SAM_ERR_INVALID_ARG;
     if (refine_steps < 0 || refine_steps > 4 || !std::isfinite(resid_weight)) return SAM_ERR_INVALID_ARG;
-    if (check_csr_arg(A_k, true) != SAM_OK || check_csr_arg(A_0, true) != SAM_OK) return SAM_ERR_INVALID_ARG;
-    const int n = A_0->n;
-    if (A_k->n != n || S->n != n) return SAM_ERR_INVALID_ARG;
+    const int n = A_0[0].n;
+    int64_t ktot = 0, ztot = 0;
+    if (M_offsets[0] != 0) return SAM_ERR_INVALID_ARG;
+    for (int k = 0; k < K; ++k) {
+        if (check_csr_arg(&A_k[k], true) != SAM_OK || check_csr_arg(&A_0[k], true) != SAM_OK) return SAM_ERR_INVALID_ARG;
+        if (A_k[k].n != n || A_0[k].n != n || !S[k] || S[k]->n != n) return SAM_ERR_INVALID_ARG;
+        if (M_offsets[k + 1] - M_offsets[k] != S[k]->nnz) return SAM_ERR_INVALID_ARG;
+        ktot += A_k[k].nnz;
+        ztot += A_0[k].nnz;
+    }
+    const int64_t N = (int64_t)K * n;
+    const int64_t mtot = M_offsets[K];
+    if (N > INT32_MAX - 1 || ktot > INT32_MAX || ztot > INT32_MAX || mtot > INT32_MAX) return SAM_ERR_INVALID_ARG;
     cudaStream_t st = h->stream;
     Scratch sc(h);
     Stager sg(sc, st);
-    DevCsr ak = stage_csr(sg, A_k, true), z = stage_csr(sg, A_0, true);
-    const double *d_m = sg.in(M_val, (size_t)S->nnz);
-    const double *d_dm = dM_val ? sg.in(dM_val, (size_t)S->nnz) : nullptr;
-    double *d_dak = sg.out(dA_k_val, (size_t)ak.nnz);
-    double *d_da0 = sg.out(dA_0_val, (size_t)z.nnz);
-    double *d_dmr = dM_resid ? sg.out(dM_resid, (size_t)S->nnz) : nullptr;
+    std::vector<DevCsr> ak(K), zs(K);
+    for (int k = 0; k < K; ++k) {
+        ak[k] = stage_csr(sg, &A_k[k], true);
+        zs[k] = stage_csr(sg, &A_0[k], true);
+    }
+    const double *d_m = sg.in(M_val, (size_t)mtot);
+    const double *d_dm = dM_val ? sg.in(dM_val, (size_t)mtot) : nullptr;
+    double *d_dak = sg.out(dA_k_val, (size_t)ktot);
+    double *d_da0 = sg.out(dA_0_val, (size_t)ztot);
+    double *d_dmr = dM_resid ? sg.out(dM_resid, (size_t)mtot) : nullptr;
     if (sg.failed) return SAM_ERR_OOM;
-    sam_status s = validate_all(h, sc, {ak, z});
-    if (s != SAM_OK) return s;
+    {
+        std::vector<DevCsr> all(ak);
+        all.insert(all.end(), zs.begin(), zs.end());
+        sam_status s = validate_all(h, sc, all);
+        if (s != SAM_OK) return s;
+    }
     PatternGroup *g = nullptr;
     bool temp = false;
-    s = group_for(h, 1, &S, &g, &temp);
+    sam_status s = group_for(h, K, S, &g, &temp);
     if (s != SAM_OK) return s;
     struct GroupGuard {
         PatternGroup *g;
@@ -881,48 +958,44 @@ sam_status sam_build_backward(sam_handle h, const sam_csr *A_k, const sam_csr *A
             if (temp) group_release(g);
         }
     } guard{g, temp};
-    int32_t *zcp = sc.get<int32_t>((size_t)n + 1), *zri = sc.get<int32_t>((size_t)z.nnz);
-    int32_t *zperm = sc.get<int32_t>((size_t)z.nnz);
-    double *zcv = sc.get<double>((size_t)z.nnz);
-    int32_t *kcp = sc.get<int32_t>((size_t)n + 1), *kri = sc.get<int32_t>((size_t)ak.nnz);
-    int32_t *kperm = sc.get<int32_t>((size_t)ak.nnz);
-    double *kcv = sc.get<double>((size_t)ak.nnz);
-    int32_t *ish = sc.get<int32_t>((size_t)n * kICap), *icnt = sc.get<int32_t>((size_t)n);
-    uint8_t *bin = sc.get<uint8_t>((size_t)n);
-    int32_t *colstat = sc.get<int32_t>((size_t)n);
-    int64_t *nbcnt = sc.get<int64_t>((size_t)n + 1), *dB_off = sc.get<int64_t>((size_t)n + 1);
-    int32_t *work = sc.get<int32_t>((size_t)n);
+    int32_t *zcp = nullptr, *zri = nullptr, *zperm = nullptr, *kcp = nullptr, *kri = nullptr, *kperm = nullptr;
+    double *zcv = nullptr, *kcv = nullptr;
+    int64_t zn = 0, kn = 0;
+    if ((s = block_diag_csc(h, sc, zs, n, &zcp, &zri, &zcv, &zperm, &zn)) != SAM_OK) return s;
+    if ((s = block_diag_csc(h, sc, ak, n, &kcp, &kri, &kcv, &kperm, &kn)) != SAM_OK) return s;
+    int32_t *ish = sc.get<int32_t>((size_t)N * kICap), *icnt = sc.get<int32_t>((size_t)N);
+    uint8_t *bin = sc.get<uint8_t>((size_t)N);
+    int32_t *colstat = sc.get<int32_t>((size_t)N);
+    int64_t *nbcnt = sc.get<int64_t>((size_t)N + 1), *dB_off = sc.get<int64_t>((size_t)N + 1);
+    int32_t *work = sc.get<int32_t>((size_t)N);
     int32_t *bin_off = sc.get<int32_t>(kNumBins + 1), *tickets = sc.get<int32_t>(kNumBins);
-    int64_t *dbase = sc.get<int64_t>((size_t)S->nnz);
-    double *dzval = sc.get<double>((size_t)z.nnz), *dak_csc = sc.get<double>((size_t)ak.nnz);
-    if (!zcp || !zri || !zperm || !zcv || !kcp || !kri || !kperm || !kcv || !ish || !icnt || !bin || !colstat ||
-        !nbcnt || !dB_off || !work || !bin_off || !tickets || !dbase || !dzval || !dak_csc)
+    int64_t *dbase = sc.get<int64_t>((size_t)mtot);
+    double *dzval = sc.get<double>((size_t)zn), *dak_csc = sc.get<double>((size_t)kn);
+    uint8_t *lrow = sc.get<uint8_t>((size_t)N * kLCap);
+    if (!ish || !icnt || !bin || !colstat || !nbcnt || !dB_off || !work || !bin_off || !tickets || !dbase || !dzval ||
+        !dak_csc || !lrow)
         return SAM_ERR_OOM;
-    if (csr_to_csc(h, n, z.nnz, z.rp, z.ci, z.v, zcp, zri, zcv, zperm) != cudaSuccess ||
-        csr_to_csc(h, n, ak.nnz, ak.rp, ak.ci, ak.v, kcp, kri, kcv, kperm) != cudaSuccess)
-        return SAM_ERR_CUDA;
-    uint8_t *lrow = sc.get<uint8_t>((size_t)n * kLCap);
-    if (!lrow) return SAM_ERR_OOM;
-    if (shadow_and_bins(h, n, kcp, kri, g->jcp, g->jri, ish, icnt, bin, colstat, nbcnt, lrow) != cudaSuccess ||
-        exclusive_scan_i64(h, nbcnt, dB_off, n) != cudaSuccess || build_work_list(h, n, bin, work, bin_off) != cudaSuccess)
+    if (shadow_and_bins(h, (int)N, kcp, kri, g->jcp, g->jri, ish, icnt, bin, colstat, nbcnt, lrow) != cudaSuccess ||
+        exclusive_scan_i64(h, nbcnt, dB_off, N) != cudaSuccess ||
+        build_work_list(h, (int)N, bin, work, bin_off) != cudaSuccess)
         return SAM_ERR_CUDA;
     int64_t nbtot = 0;
-    if (cudaMemcpyAsync(&nbtot, dB_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    if (cudaMemcpyAsync(&nbtot, dB_off + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return SAM_ERR_CUDA;
     double *dB = sc.get<double>((size_t)(nbtot > 0 ? nbtot : 1));
     if (!dB) return SAM_ERR_OOM;
-    cudaMemsetAsync(dbase, 0xff, sizeof(int64_t) * (size_t)S->nnz, st);  // -1: no contribution
+    cudaMemsetAsync(dbase, 0xff, sizeof(int64_t) * (size_t)mtot, st);  // -1: no contribution
     float *kcv32 = nullptr, *zcv32 = nullptr;
     if (precision == SAM_FP32_REFINE) {
-        kcv32 = sc.get<float>((size_t)ak.nnz);
-        zcv32 = sc.get<float>((size_t)z.nnz);
+        kcv32 = sc.get<float>((size_t)kn);
+        zcv32 = sc.get<float>((size_t)zn);
         if (!kcv32 || !zcv32) return SAM_ERR_OOM;
-        if (round_to_f32(h, ak.nnz, kcv, kcv32) != cudaSuccess || round_to_f32(h, z.nnz, zcv, zcv32) != cudaSuccess)
+        if (round_to_f32(h, kn, kcv, kcv32) != cudaSuccess || round_to_f32(h, zn, zcv, zcv32) != cudaSuccess)
             return SAM_ERR_CUDA;
     }
-    cudaMemsetAsync(dzval, 0, sizeof(double) * (size_t)z.nnz, st);
-    if (d_dmr) cudaMemsetAsync(d_dmr, 0, sizeof(double) * (size_t)S->nnz, st);
+    cudaMemsetAsync(dzval, 0, sizeof(double) * (size_t)zn, st);
+    if (d_dmr) cudaMemsetAsync(d_dmr, 0, sizeof(double) * (size_t)mtot, st);
     LsqArgs a;
     memset(&a, 0, sizeof(a));
     a.n = n;
@@ -937,6 +1010,7 @@ sam_status sam_build_backward(sam_handle h, const sam_csr *A_k, const sam_csr *A
     a.zcp = zcp;
     a.zri = zri;
     a.zcv = zcv;
+    a.zbig = 1;
     a.csr_pos = g->csr_pos;
     a.mval = const_cast<double *>(d_m);
     a.kcv32 = kcv32;
@@ -953,16 +1027,37 @@ sam_status sam_build_backward(sam_handle h, const sam_csr *A_k, const sam_csr *A
     a.dzval = dzval;
     a.dmres = d_dmr;
     a.dbase = dbase;
-    a.znnz = z.nnz;
+    a.znnz = zn;
     if (launch_adjoint(h, precision, a) != cudaSuccess) return SAM_ERR_CUDA;
-    if (adjoint_reduce(h, n, kcp, g->mrp, dbase, dB, dak_csc) != cudaSuccess ||
-        permute_scatter_f64(h, ak.nnz, kperm, dak_csc, d_dak) != cudaSuccess ||
-        permute_scatter_f64(h, z.nnz, zperm, dzval, d_da0) != cudaSuccess)
+    if (adjoint_reduce(h, (int)N, kcp, g->mrp, dbase, dB, dak_csc) != cudaSuccess ||
+        permute_scatter_f64(h, kn, kperm, dak_csc, d_dak) != cudaSuccess ||
+        permute_scatter_f64(h, zn, zperm, dzval, d_da0) != cudaSuccess)
         return SAM_ERR_CUDA;
-    if (status_reduce(h, colstat, n, h->d_flag) != cudaSuccess) return SAM_ERR_CUDA;
+    if (status_reduce(h, colstat, N, h->d_flag) != cudaSuccess) return SAM_ERR_CUDA;
     if (sg.finish() != cudaSuccess) return SAM_ERR_CUDA;
     if (sg.has_host_outputs()) return drain_status(h);
     return cudaGetLastError() == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+sam_status sam_build_backward(sam_handle h, const sam_csr *A_k, const sam_csr *A_0, sam_pattern S, int precision,
+                              int refine_steps, const double *M_val, const double *dM_val, double resid_weight,
+                              double *dA_k_val, double *dA_0_val, double *dM_resid) {
+    if (!S) return SAM_ERR_INVALID_ARG;
+    const int64_t off[2] = {0, S->nnz};
+    return backward_impl(h, 1, A_k, A_0, &S, precision, refine_steps, off, M_val, dM_val, resid_weight, dA_k_val,
+                         dA_0_val, dM_resid);
+}
+
+sam_status sam_build_backward_batched(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0,
+                                      const sam_pattern *S, int precision, int refine_steps,
+                                      const int64_t *M_offsets, const double *M_val, const double *dM_val,
+                                      double resid_weight, double *dA_k_val, double *dA_0_val, double *dM_resid) {
+    return backward_impl(h, K, A_k, A_0, S, precision, refine_steps, M_offsets, M_val, dM_val, resid_weight,
+                         dA_k_val, dA_0_val, dM_resid);
 }
 
 sam_status sam_set_tile_variants(sam_handle h, const int *variants, int count) {

@@ -50,7 +50,8 @@ struct LsqArgs {
     const int32_t *jcp, *jri;    // pattern (CSC, big)
     const int32_t *ish, *icnt;   // shadow rows (padded) and counts
     const uint8_t *lrow;         // local shadow row of every gathered entry (padded [N][kLCap])
-    const int32_t *zcp, *zri;    // CSC of the target A_0 (order n)
+    const int32_t *zcp, *zri;    // CSC of the target: A_0 (order n, shared by every map; zbig = 0)
+                                 // or the block-diagonal of one target per map (order N; zbig = 1)
     const double *zcv;
     const float *zcv32;          // the same values rounded to FP32
     const int32_t *csr_pos;      // pattern CSC entry -> map CSR position
@@ -61,12 +62,14 @@ struct LsqArgs {
     const int32_t *bin_off;      // [kNumBins+1] offsets into work
     int32_t *ticket;             // [kNumBins] persistent-loop counters (zeroed before launch)
     int refine_steps;
+    int zbig;                    // 1: one target per map, stored block-diagonally
     // adjoint
     const double *dmval;         // dL/dM, CSR order (nullable)
     double resid_weight;         // weight of ||A_k M - A_0||_F^2 in the loss
     double *dB;                  // per-column dL/dB entries (gather order)
     const int64_t *dB_off;       // [N+1] offsets of each column's entries in dB
-    double *dzval;               // dL/dA_0 contributions, CSC(A_0) order per map [K][nnz(A_0)]
+    double *dzval;               // dL/dA_0 contributions: CSC(A_0) order per map [K][nnz(A_0)] (zbig = 0)
+                                 // or the CSC order of the block-diagonal targets (zbig = 1)
     double *dmres;               // dL/dM direct residual part, map CSR order (nullable)
     int64_t *dbase;              // per pattern entry (map CSR order): offset of its column block in dB
     int64_t znnz;                // nnz(A_0)

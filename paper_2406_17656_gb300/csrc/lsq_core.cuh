@@ -371,7 +371,7 @@ struct Column {
 
     int ll, rg, cg, gbase;
     bool valid;
-    int jj, jl, roff, jb, nJ, nI, zb, ze, nB, kmax;
+    int jj, jl, roff, zro, jb, nJ, nI, zb, ze, nB, kmax;
     int status;
     int colA[JQ], clen[JQ], colB[JQ];
     double out2;
@@ -387,13 +387,17 @@ struct Column {
         const int kmap = jj / args.n;
         jl = jj - kmap * args.n;  // column of A_0
         roff = kmap * args.n;     // row offset of this map
+        // target column: A_0(:, jl) shifted by roff, or column jj of the
+        // block-diagonal targets (rows already global)
+        const int zc = args.zbig ? jj : jl;
+        zro = args.zbig ? 0 : roff;
         jb = nJ = nI = zb = ze = 0;
         if (valid) {
             jb = args.jcp[jj];
             nJ = args.jcp[jj + 1] - jb;
             nI = args.icnt[jj];
-            zb = args.zcp[jl];
-            ze = args.zcp[jl + 1];
+            zb = args.zcp[zc];
+            ze = args.zcp[zc + 1];
         }
         status = kStOk;
     }
@@ -462,7 +466,7 @@ struct Column {
         }
         out2 = 0.0;
         for (int t = zb + ll; t < ze; t += P) {
-            const int i = find_sorted(S.I, nI, args.zri[t] + roff);
+            const int i = find_sorted(S.I, nI, args.zri[t] + zro);
             const double v = args.zcv[t];
             if (i >= 0) {
                 S.c[i] = v;

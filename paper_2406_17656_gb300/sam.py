@@ -85,6 +85,12 @@ _SIGS = [
     ("sam_tune", ctypes.c_int32,
      [_vp, ctypes.c_int, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(_vp), ctypes.c_int,
       ctypes.c_int, ctypes.c_char_p]),
+    ("sam_build_multi", ctypes.c_int32,
+     [_vp, ctypes.c_int, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(_vp), ctypes.c_int,
+      ctypes.c_int, _i64p, _vp, _vp, _vp, _vp, _vp, _f64p]),
+    ("sam_build_backward_batched", ctypes.c_int32,
+     [_vp, ctypes.c_int, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(_vp), ctypes.c_int,
+      ctypes.c_int, _i64p, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     ("sam_set_tile_variants", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("sam_get_tile_variants", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("sam_profile", ctypes.c_int32, [_vp, ctypes.c_int]),
@@ -330,16 +336,21 @@ class Handle:
                "sam_build")
         return out
 
-    def sam_build_batched(self, A_ks: list, A_0: Csr, Ss: list, precision="fp32r", refine_steps: int = 1,
+    def sam_build_batched(self, A_ks: list, A_0, Ss: list, precision="fp32r", refine_steps: int = 1,
                           M_row_ptr=None, M_col_idx=None, M_val=None, col_status=None, res2=None,
                           want_fro: bool = False, offsets=None):
-        """K maps in one pass.  Output arrays are allocated on the device when
-        None.  Returns (offsets, M_row_ptr[K*(n+1)], M_col_idx, M_val, fro)."""
+        """K maps in one pass.  A_0 is the shared target (sam_build_batched)
+        or a list of K targets, one per map (sam_build_multi).  Output arrays
+        are allocated on the device when None.  Returns (offsets,
+        M_row_ptr[K*(n+1)], M_col_idx, M_val, fro)."""
         import torch
 
         K = len(A_ks)
         prec = PRECISIONS.get(precision, precision)
-        n = A_0.n
+        multi = isinstance(A_0, (list, tuple))
+        if multi and len(A_0) != K:
+            raise ValueError("one target per map")
+        n = (A_0[0] if multi else A_0).n
         if offsets is None:
             offsets = np.zeros(K + 1, dtype=np.int64)
             offsets[1:] = np.cumsum([s.nnz for s in Ss])
@@ -351,13 +362,17 @@ class Handle:
         if M_val is None:
             M_val = torch.empty(tot, dtype=torch.float64, device="cuda")
         arr = (sam_csr * K)(*[a.c() for a in A_ks])
-        z = A_0.c()
+        if multi:
+            z = (sam_csr * K)(*[a.c() for a in A_0])
+            zp, fn, name = z, load().sam_build_multi, "sam_build_multi"
+        else:
+            z = A_0.c()
+            zp, fn, name = ctypes.byref(z), load().sam_build_batched, "sam_build_batched"
         pats = (_vp * K)(*[s.ptr for s in Ss])
         fro = np.zeros(K, dtype=np.float64) if want_fro else None
-        _check(load().sam_build_batched(
-            self.ptr, K, arr, ctypes.byref(z), pats, int(prec), int(refine_steps),
-            offsets.ctypes.data_as(_i64p), _addr(M_row_ptr), _addr(M_col_idx), _addr(M_val), _addr(col_status),
-            _addr(res2), fro.ctypes.data_as(_f64p) if fro is not None else None), "sam_build_batched")
+        _check(fn(self.ptr, K, arr, zp, pats, int(prec), int(refine_steps), offsets.ctypes.data_as(_i64p),
+                  _addr(M_row_ptr), _addr(M_col_idx), _addr(M_val), _addr(col_status), _addr(res2),
+                  fro.ctypes.data_as(_f64p) if fro is not None else None), name)
         return offsets, M_row_ptr, M_col_idx, M_val, fro
 
     # -------------------------------------------------------------- residual
@@ -393,6 +408,31 @@ class Handle:
         _check(load().sam_build_backward(self.ptr, ctypes.byref(a), ctypes.byref(z), S.ptr, int(prec),
                                          int(refine_steps), _addr(M_val), _addr(dM_val), float(resid_weight),
                                          _addr(dA_k_val), _addr(dA_0_val), _addr(dM_resid)), "sam_build_backward")
+        return dA_k_val, dA_0_val
+
+    def sam_build_backward_batched(self, A_ks: list, A_0s: list, Ss: list, M_val, dM_val=None, precision="fp32r",
+                                   refine_steps: int = 1, resid_weight: float = 0.0, offsets=None, dA_k_val=None,
+                                   dA_0_val=None, dM_resid=None):
+        """K maps, map k against its own target A_0s[k]; values concatenated
+        in map order (see include/sam.h).  Returns (dA_k_val, dA_0_val)."""
+        import torch
+
+        K = len(A_ks)
+        prec = PRECISIONS.get(precision, precision)
+        if offsets is None:
+            offsets = np.zeros(K + 1, dtype=np.int64)
+            offsets[1:] = np.cumsum([s.nnz for s in Ss])
+        if dA_k_val is None:
+            dA_k_val = torch.empty(sum(a.nnz for a in A_ks), dtype=torch.float64, device="cuda")
+        if dA_0_val is None:
+            dA_0_val = torch.empty(sum(a.nnz for a in A_0s), dtype=torch.float64, device="cuda")
+        arr = (sam_csr * K)(*[a.c() for a in A_ks])
+        z = (sam_csr * K)(*[a.c() for a in A_0s])
+        pats = (_vp * K)(*[s.ptr for s in Ss])
+        _check(load().sam_build_backward_batched(self.ptr, K, arr, z, pats, int(prec), int(refine_steps),
+                                                 offsets.ctypes.data_as(_i64p), _addr(M_val), _addr(dM_val),
+                                                 float(resid_weight), _addr(dA_k_val), _addr(dA_0_val),
+                                                 _addr(dM_resid)), "sam_build_backward_batched")
         return dA_k_val, dA_0_val
 
     # ---------------------------------------------------------------- tuning

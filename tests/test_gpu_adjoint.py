@@ -144,3 +144,24 @@ def test_autograd_loss_matches_finite_differences_32x32(sam, handle):
         fd = (lp - lm) / (2 * h)
         ad = float(np.dot(gk, uk.cpu().numpy()) + np.dot(g0, u0.cpu().numpy()))
         assert abs(fd - ad) <= 1e-6 * abs(fd)
+
+
+def test_batched_adjoint_equals_single_calls(sam, handle):
+    """sam_build_backward_batched over several pairs gives, bit for bit, the
+    gradients of one sam_build_backward call per pair."""
+    import torch
+
+    pairs = [W.config5_pair(b, nx=16) for b in range(3)]
+    A0s = [sam.Csr.from_host(p[0]) for p in pairs]
+    A1s = [sam.Csr.from_host(p[1]) for p in pairs]
+    Ss = handle.sam_pattern_build_batched(A1s, 2)
+    offs, rp, ci, v, _ = handle.sam_build_batched(A1s, A0s, Ss, "fp32r", 1)
+    g = torch.randn(v.numel(), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    dk, d0 = handle.sam_build_backward_batched(A1s, A0s, Ss, v, g, "fp32r", 1, 0.4, offsets=offs)
+    ko = np.concatenate([[0], np.cumsum([a.nnz for a in A1s])])
+    zo = np.concatenate([[0], np.cumsum([a.nnz for a in A0s])])
+    for k in range(3):
+        sk, s0 = handle.sam_build_backward(A1s[k], A0s[k], Ss[k], v[offs[k]:offs[k + 1]], g[offs[k]:offs[k + 1]],
+                                           "fp32r", 1, 0.4)
+        assert torch.equal(sk, dk[ko[k]:ko[k + 1]])
+        assert torch.equal(s0, d0[zo[k]:zo[k + 1]])

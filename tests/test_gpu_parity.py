@@ -294,3 +294,21 @@ def test_full_size_q1_256_level2_sampled(sam, handle):
         assert np.array_equal(m.indptr, cp) and np.array_equal(m.indices, ri)
         idx = np.concatenate([np.arange(cp[j], cp[j + 1]) for j in cols])
         assert rel_fro(m.data[idx], ref["mval"][idx]) <= 1e-10
+
+
+def test_multi_target_batch_matches_per_pair_oracle(sam, handle):
+    """sam_build_multi: each map against its own target, small pairs."""
+    pairs = [W.config5_pair(b, nx=20) for b in range(3)]
+    A0s = [dev(sam, p[0]) for p in pairs]
+    A1s = [dev(sam, p[1]) for p in pairs]
+    for level in (1, 2):
+        Ss = handle.sam_pattern_build_batched(A1s, level)
+        offs, rp, ci, v, fro = handle.sam_build_batched(A1s, A0s, Ss, "fp32r", 1, want_fro=True)
+        n = pairs[0][0].n
+        rp, ci, v = rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy()
+        for k, (a0, a1) in enumerate(pairs):
+            ref = oracle_map(a1, a0, level)
+            assert np.array_equal(rp[k * (n + 1):(k + 1) * (n + 1)], ref["ip"])
+            assert np.array_equal(ci[offs[k]:offs[k + 1]], ref["ix"])
+            assert rel_fro(v[offs[k]:offs[k + 1]], ref["dv"]) <= 1e-10
+            assert abs(fro[k] ** 2 - ref["res2"].sum()) <= 1e-9 * ref["res2"].sum()
