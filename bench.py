@@ -98,13 +98,18 @@ def bin_of(I, J, nB):
 
 
 def algorithmic_flops(I, J, nB, precision, steps):
+    """Algorithmic work of one column (m = |I_j|, n = |J_j|, s refinement
+    steps): Householder QR with Q^T c and the back-solve,
+    2 n^2 (m - n/3) + 4 m n - 2 n^2 + n^2 flops, plus per step an FP32
+    correction solve 4 m n - n^2; FP64 per step the residual
+    r = c - B m, 2 nnz(B) + m.  The plain FP64 build does the QR part in
+    FP64.  Returns (FP32 flops, FP64 flops) per column."""
     m, n = I.astype(np.float64), J.astype(np.float64)
     qr = 2 * n * n * (m - n / 3) + (4 * m * n - 2 * n * n) + n * n
-    final_res = 2 * nB + 2 * m
     if precision == "fp64":
-        return 0.0 * qr, qr + final_res
-    f32 = qr + steps * 2 * n * n
-    f64 = steps * 4 * nB + final_res
+        return 0.0 * qr, qr
+    f32 = qr + steps * (4 * m * n - n * n)
+    f64 = steps * (2 * nB + m)
     return f32, f64
 
 
@@ -380,7 +385,8 @@ def main():
             import hashlib
 
             rec = json.load(open(tf))
-            if rec.get("kernel_sha256") == kernel_hash() and str(dom) in rec.get("bytes_per_column", {}):
+            if (rec.get("kernel_sha256") == kernel_hash() and str(dom) in rec.get("bytes_per_column", {})
+                    and rec.get("variant", {}).get(str(dom), 0) == variants[dom]):
                 # traffic per column from the capture, times this launch's columns
                 ncols = sum(int(np.sum(bin_of(I, J, nB) == dom)) for (I, J, nB) in sizes)
                 traffic = rec["bytes_per_column"][str(dom)] * ncols
