@@ -84,6 +84,7 @@ typedef struct {
 
 typedef struct sam_handle_t *sam_handle;   /* stream, device workspace, sticky status */
 typedef struct sam_pattern_t *sam_pattern; /* a map sparsity pattern S (device resident) */
+typedef struct sam_plan_t *sam_plan;       /* a captured numeric rebuild (sam_plan_create) */
 
 /* Largest column sizes the least-squares kernels accept:
  * |J_j| <= *max_cols and |I_j| <= *max_rows. */
@@ -173,6 +174,38 @@ sam_status sam_build_multi(sam_handle h, int K, const sam_csr *A_k, const sam_cs
                            const sam_pattern *S, int precision, int refine_steps,
                            const int64_t *M_offsets, int32_t *M_row_ptr, int32_t *M_col_idx,
                            double *M_val, int32_t *col_status, double *res2, double *fro);
+
+/*
+ * sam_plan_create -- the batched build (sam_build_batched when n_targets = 1,
+ * sam_build_multi when n_targets = K) split into its value-independent part,
+ * done here once, and its value-dependent part, captured once into a CUDA
+ * graph that sam_plan_execute replays.  For sequences whose sparsity stays
+ * fixed while the values change (the paper's setting of Sec. 2: a sequence
+ * A_k of one discretisation), every replay re-reads the values of the A_k
+ * and A_0 given here (the val pointers; structure arrays are read only here),
+ * gathers them, solves every column and writes M_val, col_status, res2 and
+ * fro2 -- the same results, bit for bit, as the corresponding direct call
+ * with the handle's tile variants at creation.
+ * Done at creation: validation, transposes, shadow rows, size classes, work
+ * lists and the map structure (M_row_ptr / M_col_idx are written here and
+ * not again).  All arrays must be device memory and stay allocated while
+ * the plan lives; the patterns may be destroyed after creation.
+ * fro2 (nullable, device double[K]): ||A_k M_k - A_0||_F^2 per map.
+ * Synchronises the handle's stream (creation only).  Errors: those of
+ * sam_build_batched; SAM_ERR_INVALID_ARG for host pointers.
+ */
+sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0, int n_targets,
+                           const sam_pattern *S, int precision, int refine_steps,
+                           const int64_t *M_offsets, int32_t *M_row_ptr, int32_t *M_col_idx,
+                           double *M_val, int32_t *col_status, double *res2, double *fro2,
+                           sam_plan *out);
+/* Replays the plan on the handle's current stream (asynchronous; a failed
+ * column raises the sticky status read by sam_sync). */
+sam_status sam_plan_execute(sam_plan p);
+/* Kernels one replay launches. */
+sam_status sam_plan_launches(sam_plan p, int64_t *launches);
+/* Synchronises the handle's stream and frees the plan. */
+sam_status sam_plan_destroy(sam_plan p);
 
 /*
  * sam_residual -- ||R_k||_F and ||R_k||_F / ||A_0||_F for R_k = A_k M_k - A_0

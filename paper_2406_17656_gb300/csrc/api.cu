@@ -54,6 +54,17 @@ struct PatternGroup {
 };
 }  // namespace
 
+// A captured numeric rebuild (see sam_plan_create in sam.h)
+struct sam_plan_t {
+    sam_handle h = nullptr;
+    PatternGroup *g = nullptr;     // holds one reference
+    std::vector<void *> mem;       // workspace from the handle's pool
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;          // kernels per replay
+};
+
+
 struct sam_pattern_t {
     PatternGroup *g = nullptr;
     int k = 0;
@@ -128,6 +139,12 @@ struct Scratch {
         void *p = pool_alloc(h, sizeof(T) * (count ? count : 1));
         if (p) ptrs.push_back(p);
         return (T *)p;
+    }
+    // hand the allocations to a longer-lived owner
+    std::vector<void *> release() {
+        std::vector<void *> out;
+        out.swap(ptrs);
+        return out;
     }
     ~Scratch() {
         for (void *p : ptrs) pool_free(h, p);
@@ -660,7 +677,8 @@ namespace {
 // K matrices of order n as one block-diagonal CSC of order K n (with the
 // CSC -> CSR permutation when perm != nullptr); K = 1 skips the copy.
 sam_status block_diag_csc(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms, int n, int32_t **cp,
-                          int32_t **ri, double **cv, int32_t **perm, int64_t *total) {
+                          int32_t **ri, double **cv, int32_t **perm, int64_t *total, Scratch *tmp_sc = nullptr) {
+    Scratch &tmp = tmp_sc ? *tmp_sc : sc;  // the concatenated copy lives only until the transpose
     const int K = (int)ms.size();
     const int64_t N = (int64_t)K * n;
     int64_t tot = 0;
@@ -680,10 +698,10 @@ sam_status block_diag_csc(sam_handle h, Scratch &sc, const std::vector<DevCsr> &
     const int32_t *rp = ms[0].rp, *ci = ms[0].ci;
     const double *v = ms[0].v;
     if (K > 1) {
-        CsrPtrs *dtab = sc.get<CsrPtrs>(K);
-        int64_t *doff = sc.get<int64_t>(K + 1);
-        int32_t *brp = sc.get<int32_t>((size_t)N + 1), *bci = sc.get<int32_t>((size_t)tot);
-        double *bv = sc.get<double>((size_t)tot);
+        CsrPtrs *dtab = tmp.get<CsrPtrs>(K);
+        int64_t *doff = tmp.get<int64_t>(K + 1);
+        int32_t *brp = tmp.get<int32_t>((size_t)N + 1), *bci = tmp.get<int32_t>((size_t)tot);
+        double *bv = tmp.get<double>((size_t)tot);
         if (!dtab || !doff || !brp || !bci || !bv) return SAM_ERR_OOM;
         cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * K, cudaMemcpyHostToDevice, h->stream);
         cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, h->stream);
@@ -1192,3 +1210,221 @@ sam_status sam_peak_flops(sam_handle h, double ms, double *fp32_flops, double *f
 }
 
 }  // extern "C"
+
+namespace {
+
+void plan_free(sam_plan p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (void *q : p->mem) pool_free(p->h, q);
+    if (p->g) group_release(p->g);
+    delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0, int n_targets,
+                           const sam_pattern *S, int precision, int refine_steps, const int64_t *M_offsets,
+                           int32_t *M_row_ptr, int32_t *M_col_idx, double *M_val, int32_t *col_status, double *res2,
+                           double *fro2, sam_plan *out) {
+    if (!out) return SAM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!h || K < 1 || !A_k || !A_0 || !S || !M_offsets || !M_row_ptr || !M_col_idx || !M_val)
+        return SAM_ERR_INVALID_ARG;
+    if (n_targets != 1 && n_targets != K) return SAM_ERR_INVALID_ARG;
+    if (precision != SAM_FP64 && precision != SAM_FP32_REFINE) return SAM_ERR_INVALID_ARG;
+    if (refine_steps < 0 || refine_steps > 4) return SAM_ERR_INVALID_ARG;
+    const int NT = n_targets;
+    const int n = A_0[0].n;
+    int64_t ktot = 0, ztot = 0;
+    auto dev_csr = [](const sam_csr &a) {
+        return is_device_ptr(a.row_ptr) && (a.nnz == 0 || (is_device_ptr(a.col_idx) && is_device_ptr(a.val)));
+    };
+    for (int t = 0; t < NT; ++t) {
+        if (check_csr_arg(&A_0[t], true) != SAM_OK || A_0[t].n != n || !dev_csr(A_0[t])) return SAM_ERR_INVALID_ARG;
+        ztot += A_0[t].nnz;
+    }
+    if (M_offsets[0] != 0) return SAM_ERR_INVALID_ARG;
+    for (int k = 0; k < K; ++k) {
+        if (check_csr_arg(&A_k[k], true) != SAM_OK || A_k[k].n != n || !S[k] || S[k]->n != n || !dev_csr(A_k[k]))
+            return SAM_ERR_INVALID_ARG;
+        if (M_offsets[k + 1] - M_offsets[k] != S[k]->nnz) return SAM_ERR_INVALID_ARG;
+        ktot += A_k[k].nnz;
+    }
+    const int64_t N = (int64_t)K * n;
+    const int64_t total_nnz = M_offsets[K];
+    if (N > INT32_MAX - 1 || ktot > INT32_MAX || ztot > INT32_MAX || total_nnz > INT32_MAX)
+        return SAM_ERR_INVALID_ARG;
+    if (!is_device_ptr(M_row_ptr) || (total_nnz > 0 && (!is_device_ptr(M_col_idx) || !is_device_ptr(M_val))) ||
+        (col_status && !is_device_ptr(col_status)) || (res2 && !is_device_ptr(res2)) || (fro2 && !is_device_ptr(fro2)))
+        return SAM_ERR_INVALID_ARG;
+    sam_plan p = new (std::nothrow) sam_plan_t;
+    if (!p) return SAM_ERR_OOM;
+    p->h = h;
+    struct Guard {
+        sam_plan p;
+        ~Guard() { plan_free(p); }
+    } guard{p};
+    cudaStream_t st = h->stream;
+    Scratch keep(h), tmp(h);
+    std::vector<DevCsr> zs(NT), ak(K);
+    for (int t = 0; t < NT; ++t) zs[t] = DevCsr{A_0[t].n, A_0[t].nnz, A_0[t].row_ptr, A_0[t].col_idx, A_0[t].val};
+    for (int k = 0; k < K; ++k) ak[k] = DevCsr{A_k[k].n, A_k[k].nnz, A_k[k].row_ptr, A_k[k].col_idx, A_k[k].val};
+    {
+        std::vector<DevCsr> all(ak);
+        all.insert(all.end(), zs.begin(), zs.end());
+        sam_status s = validate_all(h, tmp, all);
+        if (s != SAM_OK) return s;
+    }
+    {
+        bool temp = false;
+        sam_status s = group_for(h, K, S, &p->g, &temp);
+        if (s != SAM_OK) {
+            p->g = nullptr;
+            return s;
+        }
+        if (!temp) p->g->refs++;
+    }
+    PatternGroup *g = p->g;
+    // ---- value-independent work, done once
+    int32_t *zcp = nullptr, *zri = nullptr, *zperm = nullptr, *kcp = nullptr, *kri = nullptr, *kperm = nullptr;
+    double *zcv = nullptr, *kcv = nullptr;
+    int64_t zn = 0, kn = 0;
+    sam_status s = block_diag_csc(h, keep, zs, n, &zcp, &zri, &zcv, &zperm, &zn, &tmp);
+    if (s != SAM_OK) return s;
+    if ((s = block_diag_csc(h, keep, ak, n, &kcp, &kri, &kcv, &kperm, &kn, &tmp)) != SAM_OK) return s;
+    int32_t *ish = keep.get<int32_t>((size_t)N * kICap), *icnt = keep.get<int32_t>((size_t)N);
+    uint8_t *bin = tmp.get<uint8_t>((size_t)N);
+    int32_t *work = keep.get<int32_t>((size_t)N);
+    int32_t *bin_off = keep.get<int32_t>(kNumBins + 1), *tickets = keep.get<int32_t>(kNumBins);
+    int32_t *d_st = col_status ? col_status : keep.get<int32_t>((size_t)N);
+    double *d_r2 = res2 ? res2 : keep.get<double>((size_t)N);
+    uint8_t *lrow = keep.get<uint8_t>((size_t)N * kLCap);
+    float *kcv32 = nullptr, *zcv32 = nullptr;
+    if (precision == SAM_FP32_REFINE) {
+        kcv32 = keep.get<float>((size_t)kn);
+        zcv32 = keep.get<float>((size_t)zn);
+    }
+    double *seg_work = fro2 ? keep.get<double>(segmented_sum_workspace(K)) : nullptr;
+    // value sources: per-matrix pointers and CSC offsets
+    std::vector<const double *> kptr(K), zptr(NT);
+    std::vector<int64_t> koff(K + 1, 0), zoff(NT + 1, 0);
+    for (int k = 0; k < K; ++k) {
+        kptr[k] = A_k[k].val;
+        koff[k + 1] = koff[k] + A_k[k].nnz;
+    }
+    for (int t = 0; t < NT; ++t) {
+        zptr[t] = A_0[t].val;
+        zoff[t + 1] = zoff[t] + A_0[t].nnz;
+    }
+    const double **d_kptr = keep.get<const double *>(K), **d_zptr = keep.get<const double *>(NT);
+    int64_t *d_koff = keep.get<int64_t>(K + 1), *d_zoff = keep.get<int64_t>(NT + 1);
+    if (!ish || !icnt || !bin || !work || !bin_off || !tickets || !d_st || !d_r2 || !lrow ||
+        (precision == SAM_FP32_REFINE && (!kcv32 || !zcv32)) || (fro2 && !seg_work) || !d_kptr || !d_zptr ||
+        !d_koff || !d_zoff)
+        return SAM_ERR_OOM;
+    cudaMemcpyAsync(d_kptr, kptr.data(), sizeof(double *) * K, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_zptr, zptr.data(), sizeof(double *) * NT, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_koff, koff.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_zoff, zoff.data(), sizeof(int64_t) * (NT + 1), cudaMemcpyHostToDevice, st);
+    if (shadow_and_bins(h, (int)N, kcp, kri, g->jcp, g->jri, ish, icnt, bin, d_st, nullptr, lrow) != cudaSuccess ||
+        build_work_list(h, (int)N, bin, work, bin_off) != cudaSuccess ||
+        split_map_structure(h, K, n, g->mrp, g->mci, M_row_ptr, M_col_idx) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    // shadow failures (rank / unsupported) are structural: report them now
+    if (status_reduce(h, d_st, N, h->d_flag) != cudaSuccess) return SAM_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SAM_ERR_CUDA;
+    // ---- value-dependent steps, captured once on a private stream
+    LsqArgs a;
+    memset(&a, 0, sizeof(a));
+    a.kcv32 = kcv32;
+    a.zcv32 = zcv32;
+    a.n = n;
+    a.kcp = kcp;
+    a.kri = kri;
+    a.kcv = kcv;
+    a.jcp = g->jcp;
+    a.jri = g->jri;
+    a.ish = ish;
+    a.icnt = icnt;
+    a.lrow = lrow;
+    a.zcp = zcp;
+    a.zri = zri;
+    a.zcv = zcv;
+    a.zbig = NT > 1 ? 1 : 0;
+    a.csr_pos = g->csr_pos;
+    a.mval = M_val;
+    a.colres = d_r2;
+    a.colstat = d_st;
+    a.work = work;
+    a.bin_off = bin_off;
+    a.ticket = tickets;
+    a.refine_steps = refine_steps;
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return SAM_ERR_CUDA;
+    const bool prof = h->profiling;
+    const int64_t launches0 = h->launches;
+    h->profiling = false;
+    h->stream = cs;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        // the shadow status of each column is kept in d_st; the solve overwrites it per column
+        bool ok = gather_values(h, kn, K, d_koff, d_kptr, kperm, kcv, kcv32) == cudaSuccess &&
+                  gather_values(h, zn, NT, d_zoff, d_zptr, zperm, zcv, zcv32) == cudaSuccess &&
+                  cudaMemsetAsync(M_val, 0, sizeof(double) * (size_t)total_nnz, cs) == cudaSuccess &&
+                  cudaMemsetAsync(d_r2, 0, sizeof(double) * (size_t)N, cs) == cudaSuccess &&
+                  launch_lsq(h, precision, a) == cudaSuccess &&
+                  status_reduce(h, d_st, N, h->d_flag) == cudaSuccess &&
+                  (!fro2 || segmented_sum_f64(h, d_r2, K, n, fro2, false, seg_work) == cudaSuccess);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cs, &graph);
+        p->graph = graph;
+        if (!ok && e == cudaSuccess) e = cudaErrorUnknown;
+    }
+    h->stream = st;
+    h->profiling = prof;
+    p->launches = h->launches - launches0;
+    h->launches = launches0;
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess || !p->graph) {
+        cudaGetLastError();
+        return SAM_ERR_CUDA;
+    }
+    if (cudaGraphInstantiate(&p->exec, p->graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return SAM_ERR_CUDA;
+    }
+    p->mem = keep.release();
+    *out = p;
+    guard.p = nullptr;
+    return drain_status(h);
+}
+
+sam_status sam_plan_execute(sam_plan p) {
+    if (!p || !p->exec) return SAM_ERR_INVALID_ARG;
+    if (cudaGraphLaunch(p->exec, p->h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return SAM_ERR_CUDA;
+    }
+    p->h->launches += p->launches;
+    return SAM_OK;
+}
+
+sam_status sam_plan_launches(sam_plan p, int64_t *launches) {
+    if (!p || !launches) return SAM_ERR_INVALID_ARG;
+    *launches = p->launches;
+    return SAM_OK;
+}
+
+sam_status sam_plan_destroy(sam_plan p) {
+    if (!p) return SAM_ERR_INVALID_ARG;
+    cudaStreamSynchronize(p->h->stream);
+    plan_free(p);
+    return SAM_OK;
+}
+
+}  // extern "C"
+

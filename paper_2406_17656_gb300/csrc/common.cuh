@@ -147,7 +147,13 @@ cudaError_t round_to_f32(sam_handle h, int64_t n, const double *in, float *out);
 cudaError_t permute_scatter_f64(sam_handle h, int64_t nnz, const int32_t *perm, const double *in, double *out);
 
 // Deterministic sums: out[k] = sum of x[k*seg .. (k+1)*seg) (squares optional).
-cudaError_t segmented_sum_f64(sam_handle h, const double *x, int K, int64_t seg, double *out, bool squares);
+cudaError_t segmented_sum_f64(sam_handle h, const double *x, int K, int64_t seg, double *out, bool squares,
+                              double *work = nullptr);
+// doubles of workspace segmented_sum_f64 needs for K segments
+size_t segmented_sum_workspace(int K);
+// values of K matrices into the CSC order of their block-diagonal (+ FP32 copy)
+cudaError_t gather_values(sam_handle h, int64_t tot, int K, const int64_t *off, const double *const *vals,
+                          const int32_t *perm, double *v, float *v32);
 cudaError_t sum_f64(sam_handle h, const double *x, int64_t n, double *out_dev, bool squares);
 cudaError_t csr_spmv(sam_handle h, int n, const int32_t *rp, const int32_t *ci, const double *v, const double *x,
                      double *y);

@@ -255,14 +255,44 @@ cudaError_t sum_f64(sam_handle h, const double *x, int64_t n, double *out_dev, b
     return cudaGetLastError();
 }
 
-cudaError_t segmented_sum_f64(sam_handle h, const double *x, int K, int64_t seg, double *out, bool squares) {
+size_t segmented_sum_workspace(int K) { return (size_t)K * kSegBlocks; }
+
+cudaError_t segmented_sum_f64(sam_handle h, const double *x, int K, int64_t seg, double *out, bool squares,
+                              double *work) {
     cudaStream_t st = handle_stream(h);
-    double *part = (double *)pool_alloc(h, sizeof(double) * (size_t)K * kSegBlocks);
+    double *part = work ? work : (double *)pool_alloc(h, sizeof(double) * segmented_sum_workspace(K));
     if (!part) return cudaErrorMemoryAllocation;
     seg_partial_kernel<<<dim3(kSegBlocks, (unsigned)K), kSumThreads, 0, st>>>(x, seg, squares, part);
     seg_final_kernel<<<(K + 127) / 128, 128, 0, st>>>(part, K, out);
     count_launch(h, 2);
-    pool_free(h, part);
+    if (!work) pool_free(h, part);
+    return cudaGetLastError();
+}
+
+// values of K matrices gathered into the CSC order of their block-diagonal
+// (and rounded to FP32 when v32 != nullptr): entry p of the CSC belongs to
+// matrix k with off[k] <= p < off[k+1] and is entry perm[p] - off[k] of it
+__global__ void gather_values_kernel(int64_t tot, int K, const int64_t *off, const double *const *vals,
+                                     const int32_t *perm, double *v, float *v32) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < tot; p += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = K - 1;
+        while (lo < hi) {  // last k with off[k] <= p
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= p) lo = mid; else hi = mid - 1;
+        }
+        const double x = vals[lo][perm[p] - off[lo]];
+        v[p] = x;
+        if (v32) v32[p] = (float)x;
+    }
+}
+
+cudaError_t gather_values(sam_handle h, int64_t tot, int K, const int64_t *off, const double *const *vals,
+                          const int32_t *perm, double *v, float *v32) {
+    if (tot == 0) return cudaSuccess;
+    int64_t blocks = (tot + 255) / 256;
+    if (blocks > (int64_t)handle_sms(h) * 16) blocks = (int64_t)handle_sms(h) * 16;
+    gather_values_kernel<<<(unsigned)blocks, 256, 0, handle_stream(h)>>>(tot, K, off, vals, perm, v, v32);
+    count_launch(h);
     return cudaGetLastError();
 }
 

@@ -91,6 +91,12 @@ _SIGS = [
     ("sam_build_backward_batched", ctypes.c_int32,
      [_vp, ctypes.c_int, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(_vp), ctypes.c_int,
       ctypes.c_int, _i64p, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
+    ("sam_plan_create", ctypes.c_int32,
+     [_vp, ctypes.c_int, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.c_int, ctypes.POINTER(_vp),
+      ctypes.c_int, ctypes.c_int, _i64p, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    ("sam_plan_execute", ctypes.c_int32, [_vp]),
+    ("sam_plan_launches", ctypes.c_int32, [_vp, _i64p]),
+    ("sam_plan_destroy", ctypes.c_int32, [_vp]),
     ("sam_set_tile_variants", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("sam_get_tile_variants", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("sam_profile", ctypes.c_int32, [_vp, ctypes.c_int]),
@@ -244,6 +250,37 @@ class Pattern:
         # closed the pool has released it, and the pattern must not be touched
         if self.ptr and getattr(self.handle, "ptr", 0):
             load().sam_pattern_destroy(self.ptr)
+        self.ptr = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Plan:
+    """A captured numeric rebuild (sam_plan_create): `execute()` replays the
+    whole value-dependent build as one CUDA graph.  Keeps the arrays it was
+    made from alive."""
+
+    def __init__(self, handle: "Handle", ptr: int, keep: tuple, offsets, outputs):
+        self.handle, self.ptr, self._keep = handle, ptr, keep
+        self.offsets = offsets
+        self.M_row_ptr, self.M_col_idx, self.M_val, self.col_status, self.res2, self.fro2 = outputs
+        handle._patterns.add(self)
+
+    def execute(self):
+        _check(load().sam_plan_execute(self.ptr), "sam_plan_execute")
+
+    def launches(self) -> int:
+        n = ctypes.c_int64()
+        _check(load().sam_plan_launches(self.ptr, ctypes.byref(n)), "sam_plan_launches")
+        return n.value
+
+    def destroy(self):
+        if self.ptr and getattr(self.handle, "ptr", 0):
+            load().sam_plan_destroy(self.ptr)
         self.ptr = 0
 
     def __del__(self):
@@ -434,6 +471,38 @@ class Handle:
                                                  float(resid_weight), _addr(dA_k_val), _addr(dA_0_val),
                                                  _addr(dM_resid)), "sam_build_backward_batched")
         return dA_k_val, dA_0_val
+
+    # ------------------------------------------------------------------ plans
+    def sam_plan_create(self, A_ks: list, A_0, Ss: list, precision="fp32r", refine_steps: int = 1,
+                        want_status: bool = False, want_res2: bool = False, want_fro2: bool = True) -> Plan:
+        """Capture the batched build of these device matrices (A_0 shared, or
+        a list of one target per map) as a replayable plan; outputs are
+        allocated here and live on the returned Plan."""
+        import torch
+
+        K = len(A_ks)
+        prec = PRECISIONS.get(precision, precision)
+        multi = isinstance(A_0, (list, tuple))
+        tg = list(A_0) if multi else [A_0]
+        n = tg[0].n
+        offsets = np.zeros(K + 1, dtype=np.int64)
+        offsets[1:] = np.cumsum([s.nnz for s in Ss])
+        tot = int(offsets[-1])
+        dev = "cuda"
+        rp = torch.empty(K * (n + 1), dtype=torch.int32, device=dev)
+        ci = torch.empty(tot, dtype=torch.int32, device=dev)
+        v = torch.empty(tot, dtype=torch.float64, device=dev)
+        st = torch.empty(K * n, dtype=torch.int32, device=dev) if want_status else None
+        r2 = torch.empty(K * n, dtype=torch.float64, device=dev) if want_res2 else None
+        f2 = torch.empty(K, dtype=torch.float64, device=dev) if want_fro2 else None
+        arr = (sam_csr * K)(*[a.c() for a in A_ks])
+        z = (sam_csr * len(tg))(*[a.c() for a in tg])
+        pats = (_vp * K)(*[s.ptr for s in Ss])
+        out = _vp()
+        _check(load().sam_plan_create(self.ptr, K, arr, z, len(tg), pats, int(prec), int(refine_steps),
+                                      offsets.ctypes.data_as(_i64p), _addr(rp), _addr(ci), _addr(v), _addr(st),
+                                      _addr(r2), _addr(f2), ctypes.byref(out)), "sam_plan_create")
+        return Plan(self, out.value, (tuple(A_ks), tuple(tg)), offsets, (rp, ci, v, st, r2, f2))
 
     # ---------------------------------------------------------------- tuning
     def sam_tune(self, A_ks: list, A_0: Csr, Ss: list, precision="fp32r", refine_steps: int = 1,

@@ -75,13 +75,22 @@ def test_config3_upwind7_64cube_20maps_level2(sam, handle):
 
 def test_config4_p1_fem_512_16maps_level2(sam, handle):
     """Jittered P1 FEM with reaction on 512^2 cells, 16 matrices whose
-    pattern changes by edge flips (non-nested), level-2 patterns."""
+    pattern changes by edge flips (non-nested), level-2 patterns; direct
+    call and captured plan."""
+    import torch
+
     seq = W.config4()
     A0 = seq.mats[0]
     Aks = [sam.Csr.from_host(m) for m in seq.mats]
     a0 = sam.Csr.from_host(A0)
     Ss = handle.sam_pattern_build_batched(Aks, 2)
     offs, rp, ci, v, fro = handle.sam_build_batched(Aks, a0, Ss, "fp32r", 1, want_fro=True)
+    # the CUDA-graph-captured pipeline gives the same maps bit for bit
+    plan = handle.sam_plan_create(Aks, a0, Ss, "fp32r", 1)
+    plan.execute()
+    handle.sam_sync()
+    assert torch.equal(plan.M_val, v) and torch.equal(plan.M_col_idx, ci) and torch.equal(plan.M_row_ptr, rp)
+    plan.destroy()
     rp, ci, v = rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy()
     for k in (1, 8, 15):
         _check_map(k, seq.mats[k], A0, 2, Ss, offs, rp, ci, v, fro, 1200, 400 + k)
