@@ -64,6 +64,27 @@ def dist_env():
     return rank, world, local
 
 
+# --------------------------------------------------------------- ranks
+
+
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The largest x over all ranks (identity on one rank)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank_step: float, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank processes its own copy of the step's
+    units (weak scaling), timed by the slowest rank."""
+    return units_per_rank_step * world / (ms_per_step * 1e-3)
+
+
 # --------------------------------------------------------------- accounting
 
 
@@ -319,11 +340,9 @@ def main():
         prof = h.sam_profile_read() if profile else None
         if profile:
             h.sam_profile(False)
-        ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
         if world > 1:
             dist.barrier()
-            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        return float(ms_t.item()) / nsteps, fro, prof, (offs, out)
+        return max_over_ranks(ms, world, dev) / nsteps, fro, prof, (offs, out)
 
     # ---- one-time tuning of the FP32 tile shapes on this workload (untimed)
     variants = [0] * 5
@@ -338,7 +357,7 @@ def main():
         ms, fro, prof, (offs, out) = timed(args.level, "fp32r", args.refine, args.steps, args.warmup, profile=True)
     clocks = clk.summary()
     cols_per_step = K * n
-    value = cols_per_step * world / (ms * 1e-3)
+    value = job_value(cols_per_step, world, ms)
     launches_total, lsq_ms, lsq_n = prof
     gpu_launches = int(launches_total)
 
@@ -347,7 +366,7 @@ def main():
     v32 = out[2].clone()
     if not args.quick:
         ms64, fro64, _, (offs64, out64) = timed(args.level, "fp64", 0, max(2, args.steps // 3), 1)
-        extra["fp64_columns_per_s"] = cols_per_step * world / (ms64 * 1e-3)
+        extra["fp64_columns_per_s"] = job_value(cols_per_step, world, ms64)
         extra["fp64_ms_per_step"] = ms64
         extra["speedup_fp32r_vs_fp64"] = value / extra["fp64_columns_per_s"]
         errs = []
@@ -356,8 +375,34 @@ def main():
             errs.append(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)))
         extra["max_rel_fro_vs_fp64_gpu"] = max(errs)
         ms1, _, _, _ = timed(1, "fp32r", args.refine, max(2, args.steps // 2), 1)
-        extra["level1_columns_per_s"] = cols_per_step * world / (ms1 * 1e-3)
+        extra["level1_columns_per_s"] = job_value(cols_per_step, world, ms1)
         extra["rel_residual_per_map"] = [float(f) / float(np.linalg.norm(a0h.data)) for f in fro]
+
+    # ---- numeric rebuild replayed from a captured CUDA graph (patterns fixed,
+    #      values re-read from the same device buffers every replay)
+    if not args.quick:
+        pats = h.sam_pattern_build_batched(aks, args.level)
+        plan = h.sam_plan_create(aks, a0, pats, "fp32r", args.refine)
+        for p in pats:
+            p.destroy()
+        for _ in range(3):
+            plan.execute()
+        torch.cuda.synchronize()
+        tg = 0.0
+        ng = max(5, args.steps)
+        for _ in range(ng):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.execute()
+            e1.record(stream)
+            e1.synchronize()
+            tg += e0.elapsed_time(e1)
+        tg = max_over_ranks(tg / ng, world, dev)
+        extra["graph_replay_columns_per_s"] = job_value(cols_per_step, world, tg)
+        extra["graph_replay_ms"] = tg
+        extra["graph_replay_launches"] = plan.launches()
+        plan.destroy()
 
     # ---- roofline of the dominant kernel (largest least-squares size class)
     sizes = column_sizes(seq.mats, args.level)
@@ -431,10 +476,7 @@ def main():
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / ne
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = cols_per_step * world / float(e2e_t.item())
+    e2e_value = job_value(cols_per_step, world, max_over_ranks(e2e_s * 1e3, world, dev))
 
     # ---- CPU oracle baseline and sampled parity (rank 0, N = 1 only)
     cpu = None
