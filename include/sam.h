@@ -68,6 +68,18 @@ enum {
                             semi-normal-equation steps with FP64 residuals */
 };
 
+/*
+ * refine_steps = SAM_REFINE_AUTO (SAM_FP32_REFINE only): one or two steps per
+ * column, chosen by a stopping test, with an FP64 re-solve of the columns
+ * that miss the target.  Corrected semi-normal-equation steps contract the
+ * error by rho ~ u_32 kappa(B)^2 each.  After step 1 the predicted error
+ * 4 |d_1|^2 / |m| is compared with 1e-12 |m|; a warp takes step 2 if any of
+ * its columns misses.  After step 2 the predicted error |d_2|^2 / |d_1|
+ * (|d_2| alone when the correction grew) above 1e-10 |m| sends the column
+ * to the FP64 kernel.  sam_refine_stats counts the outcomes.
+ */
+#define SAM_REFINE_AUTO (-1)
+
 /* flag bits for sam_set_flags */
 enum {
     SAM_FLAG_TRUSTED = 1 /* skip CSR validation of inputs */
@@ -112,6 +124,8 @@ sam_status sam_sync(sam_handle h);
  * stored on the device in CSC form (= the CSC structure of the map) together
  * with the CSR structure of the map.  Synchronises once (to size the
  * output).  *out is library-owned: release with sam_pattern_destroy.
+ * Limit: a column whose merged candidate lists hold more than 1024 entries
+ * and span more than 32768 row indices is SAM_ERR_UNSUPPORTED.
  */
 sam_status sam_pattern_build(sam_handle h, const sam_csr *A_k, int level, sam_pattern *out);
 
@@ -137,8 +151,8 @@ sam_status sam_pattern_destroy(sam_pattern S);
  * problem per column, written as CSR:
  *   M_row_ptr[n+1], M_col_idx[nnz(S)], M_val[nnz(S)] (caller-allocated,
  *   nnz from sam_pattern_get).  Column indices ascend within each row.
- * precision: SAM_FP64 or SAM_FP32_REFINE; refine_steps (0..4) is used by
- * SAM_FP32_REFINE only.  col_status (nullable, int32[n]) receives 0 or a
+ * precision: SAM_FP64 or SAM_FP32_REFINE; refine_steps (0..4, or
+ * SAM_REFINE_AUTO) is used by SAM_FP32_REFINE only.  col_status (nullable, int32[n]) receives 0 or a
  * sam_status per column.  res2 (nullable, double[n]) receives per column
  * ||A_k(I_j,J_j) m_j - A_0(I_j,j)||^2 + sum of A_0(i,j)^2 over rows i
  * outside I_j, so that ||R_k||_F^2 = sum_j res2[j] (Eq. (res)).
@@ -296,6 +310,14 @@ sam_status sam_tune(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0,
  */
 sam_status sam_set_tile_variants(sam_handle h, const int *variants, int count);
 sam_status sam_get_tile_variants(sam_handle h, int *variants, int count);
+
+/*
+ * sam_refine_stats -- outcome counts of the last build on this handle that
+ * ran with refine_steps = SAM_REFINE_AUTO: counts[0] columns that stopped
+ * after one step, counts[1] after two, counts[2] re-solved in FP64 (count
+ * must be 3).  Synchronises the handle's stream.
+ */
+sam_status sam_refine_stats(sam_handle h, int64_t *counts, int count);
 
 /*
  * sam_profile -- tracing.  enable != 0 starts timing every least-squares

@@ -79,7 +79,7 @@ class SamMap:
         self.ak_rp, self.ak_ci = ak_struct
         self.a0_rp, self.a0_ci = a0_struct
         self.n = int(self.ak_rp.shape[0] - 1)
-        self.precision, self.refine_steps = precision, int(refine_steps)
+        self.precision, self.refine_steps = precision, refine_steps
         self.indptr = self.indices = None
 
     def __call__(self, ak_val, a0_val):

@@ -39,6 +39,8 @@ struct sam_handle_t {
     int64_t lsq_n[sam::kNumBins] = {0};
     // FP32 tile shape per size class (sam_tune / sam_set_tile_variants)
     int variant[sam::kNumBins] = {0};
+    // automatic refinement: columns of the last such build per outcome
+    int64_t *d_refine = nullptr;
 };
 
 namespace {
@@ -492,14 +494,17 @@ sam_status sam_create(sam_handle *out, void *cuda_stream) {
     uint64_t thr = UINT64_MAX;  // keep freed blocks for reuse
     cudaMemPoolSetAttribute(h->pool, cudaMemPoolAttrReleaseThreshold, &thr);
     if (cudaMalloc(&h->d_flag, sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&h->d_refine, sizeof(int64_t) * (kAutoSteps + 1)) != cudaSuccess ||
         cudaMallocHost(&h->h_flag, sizeof(int32_t)) != cudaSuccess) {
         cudaGetLastError();
         if (h->d_flag) cudaFree(h->d_flag);
+        if (h->d_refine) cudaFree(h->d_refine);
         cudaMemPoolDestroy(h->pool);
         delete h;
         return SAM_ERR_OOM;
     }
     cudaMemset(h->d_flag, 0, sizeof(int32_t));
+    cudaMemset(h->d_refine, 0, sizeof(int64_t) * (kAutoSteps + 1));
     *h->h_flag = 0;
     *out = h;
     return SAM_OK;
@@ -511,6 +516,7 @@ sam_status sam_destroy(sam_handle h) {
     h->profiling = false;
     profile_resolve(h);
     cudaFree(h->d_flag);
+    cudaFree(h->d_refine);
     cudaFreeHost(h->h_flag);
     cudaMemPoolDestroy(h->pool);
     delete h;
@@ -722,7 +728,7 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     if (!h || K < 1 || !A_k || !A_0 || !S || !M_offsets || !M_row_ptr || !M_col_idx || !M_val)
         return SAM_ERR_INVALID_ARG;
     if (precision != SAM_FP64 && precision != SAM_FP32_REFINE) return SAM_ERR_INVALID_ARG;
-    if (refine_steps < 0 || refine_steps > 4) return SAM_ERR_INVALID_ARG;
+    if (refine_steps < SAM_REFINE_AUTO || refine_steps > 4) return SAM_ERR_INVALID_ARG;
     const int n = A_0[0].n;
     int64_t ktot = 0, ztot = 0;
     for (int t = 0; t < NT; ++t) {
@@ -827,7 +833,20 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     a.bin_off = bin_off;
     a.ticket = tickets;
     a.refine_steps = refine_steps;
+    const bool autoref = precision == SAM_FP32_REFINE && refine_steps < 0;
+    uint8_t *bin2 = nullptr;
+    int32_t *work2 = nullptr, *bin_off2 = nullptr;
+    if (autoref) {
+        a.refine_used = sc.get<uint8_t>((size_t)N);
+        bin2 = sc.get<uint8_t>((size_t)N);
+        work2 = sc.get<int32_t>((size_t)N);
+        bin_off2 = sc.get<int32_t>(kNumBins + 1);
+        if (!a.refine_used || !bin2 || !work2 || !bin_off2) return SAM_ERR_OOM;
+        cudaMemsetAsync(a.refine_used, 0, (size_t)N, st);
+    }
     if (launch_lsq(h, precision, a) != cudaSuccess) return SAM_ERR_CUDA;
+    if (autoref && launch_refine_fallback(h, a, (int)N, bin, bin2, work2, bin_off2, nullptr, h->d_refine) != cudaSuccess)
+        return SAM_ERR_CUDA;
     // CSR structure of every map
     if (split_map_structure(h, K, n, g->mrp, g->mci, d_rp, d_ci) != cudaSuccess) return SAM_ERR_CUDA;
     if (status_reduce(h, d_st, N, h->d_flag) != cudaSuccess) return SAM_ERR_CUDA;
@@ -931,7 +950,8 @@ sam_status backward_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr 
     if (!h || K < 1 || !A_k || !A_0 || !S || !M_offsets || !M_val || !dA_k_val || !dA_0_val)
         return SAM_ERR_INVALID_ARG;
     if (precision != SAM_FP64 && precision != SAM_FP32_REFINE) return SAM_ERR_INVALID_ARG;
-    if (refine_steps < 0 || refine_steps > 4 || !std::isfinite(resid_weight)) return SAM_ERR_INVALID_ARG;
+    if (refine_steps < SAM_REFINE_AUTO || refine_steps > 4 || !std::isfinite(resid_weight)) return SAM_ERR_INVALID_ARG;
+    if (refine_steps < 0) refine_steps = kAutoSteps;  // lambda: the automatic mode's largest step count
     const int n = A_0[0].n;
     int64_t ktot = 0, ztot = 0;
     if (M_offsets[0] != 0) return SAM_ERR_INVALID_ARG;
@@ -1086,6 +1106,15 @@ sam_status sam_set_tile_variants(sam_handle h, const int *variants, int count) {
     return SAM_OK;
 }
 
+sam_status sam_refine_stats(sam_handle h, int64_t *counts, int count) {
+    if (!h || !counts || count != kAutoSteps + 1) return SAM_ERR_INVALID_ARG;
+    if (cudaMemcpyAsync(counts, h->d_refine, sizeof(int64_t) * (kAutoSteps + 1), cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    return SAM_OK;
+}
+
 sam_status sam_get_tile_variants(sam_handle h, int *variants, int count) {
     if (!h || !variants || count != kNumBins) return SAM_ERR_INVALID_ARG;
     for (int b = 0; b < kNumBins; ++b) variants[b] = h->variant[b];
@@ -1236,7 +1265,7 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
         return SAM_ERR_INVALID_ARG;
     if (n_targets != 1 && n_targets != K) return SAM_ERR_INVALID_ARG;
     if (precision != SAM_FP64 && precision != SAM_FP32_REFINE) return SAM_ERR_INVALID_ARG;
-    if (refine_steps < 0 || refine_steps > 4) return SAM_ERR_INVALID_ARG;
+    if (refine_steps < SAM_REFINE_AUTO || refine_steps > 4) return SAM_ERR_INVALID_ARG;
     const int NT = n_targets;
     const int n = A_0[0].n;
     int64_t ktot = 0, ztot = 0;
@@ -1309,6 +1338,14 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
         zcv32 = keep.get<float>((size_t)zn);
     }
     double *seg_work = fro2 ? keep.get<double>(segmented_sum_workspace(K)) : nullptr;
+    const bool autoref = precision == SAM_FP32_REFINE && refine_steps < 0;
+    uint8_t *refine_used = autoref ? keep.get<uint8_t>((size_t)N) : nullptr;
+    uint8_t *bin_keep = autoref ? keep.get<uint8_t>((size_t)N) : nullptr;
+    uint8_t *bin2 = autoref ? keep.get<uint8_t>((size_t)N) : nullptr;
+    int32_t *work2 = autoref ? keep.get<int32_t>((size_t)N) : nullptr;
+    int32_t *bin_off2 = autoref ? keep.get<int32_t>(kNumBins + 1) : nullptr;
+    int32_t *wl_ws = autoref ? keep.get<int32_t>(2 * kNumBins) : nullptr;
+    if (autoref && (!refine_used || !bin_keep || !bin2 || !work2 || !bin_off2 || !wl_ws)) return SAM_ERR_OOM;
     // value sources: per-matrix pointers and CSC offsets
     std::vector<const double *> kptr(K), zptr(NT);
     std::vector<int64_t> koff(K + 1, 0), zoff(NT + 1, 0);
@@ -1330,6 +1367,7 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
     cudaMemcpyAsync(d_zptr, zptr.data(), sizeof(double *) * NT, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_koff, koff.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_zoff, zoff.data(), sizeof(int64_t) * (NT + 1), cudaMemcpyHostToDevice, st);
+    if (autoref) bin = bin_keep;  // the fallback pass reads the size classes at every replay
     if (shadow_and_bins(h, (int)N, kcp, kri, g->jcp, g->jri, ish, icnt, bin, d_st, nullptr, lrow) != cudaSuccess ||
         build_work_list(h, (int)N, bin, work, bin_off) != cudaSuccess ||
         split_map_structure(h, K, n, g->mrp, g->mci, M_row_ptr, M_col_idx) != cudaSuccess)
@@ -1363,6 +1401,7 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
     a.bin_off = bin_off;
     a.ticket = tickets;
     a.refine_steps = refine_steps;
+    a.refine_used = refine_used;
     cudaStream_t cs = nullptr;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return SAM_ERR_CUDA;
     const bool prof = h->profiling;
@@ -1376,7 +1415,10 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
                   gather_values(h, zn, NT, d_zoff, d_zptr, zperm, zcv, zcv32) == cudaSuccess &&
                   cudaMemsetAsync(M_val, 0, sizeof(double) * (size_t)total_nnz, cs) == cudaSuccess &&
                   cudaMemsetAsync(d_r2, 0, sizeof(double) * (size_t)N, cs) == cudaSuccess &&
+                  (!autoref || cudaMemsetAsync(refine_used, 0, (size_t)N, cs) == cudaSuccess) &&
                   launch_lsq(h, precision, a) == cudaSuccess &&
+                  (!autoref || launch_refine_fallback(h, a, (int)N, bin, bin2, work2, bin_off2, wl_ws,
+                                                      h->d_refine) == cudaSuccess) &&
                   status_reduce(h, d_st, N, h->d_flag) == cudaSuccess &&
                   (!fro2 || segmented_sum_f64(h, d_r2, K, n, fro2, false, seg_work) == cudaSuccess);
         cudaGraph_t graph = nullptr;

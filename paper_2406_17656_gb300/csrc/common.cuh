@@ -33,6 +33,12 @@ constexpr int kStOk = SAM_OK;
 constexpr int kStRank = SAM_ERR_RANK_DEFICIENT;
 constexpr int kStNonfinite = SAM_ERR_NONFINITE;
 constexpr int kStUnsupported = SAM_ERR_UNSUPPORTED;
+// internal: the FP32 solve missed the accuracy target; the FP64 kernel
+// re-solves the column (never left in a status array)
+constexpr int kStRefine = 100;
+// automatic refinement (refine_steps = SAM_REFINE_AUTO)
+constexpr int kAutoSteps = 2;
+constexpr double kAutoC = 4.0, kAutoTol = 1e-12, kFallbackTol = 1e-10;
 
 // Source CSR of one map (device pointers) for the batch concatenation.
 struct CsrPtrs {
@@ -61,7 +67,8 @@ struct LsqArgs {
     const int32_t *work;         // columns grouped by size class
     const int32_t *bin_off;      // [kNumBins+1] offsets into work
     int32_t *ticket;             // [kNumBins] persistent-loop counters (zeroed before launch)
-    int refine_steps;
+    int refine_steps;            // < 0: automatic (up to kAutoSteps, FP64 fallback)
+    uint8_t *refine_used;        // automatic mode: steps taken per column, kAutoSteps+1 = FP64 fallback
     int zbig;                    // 1: one target per map, stored block-diagonally
     // adjoint
     const double *dmval;         // dL/dM, CSR order (nullable)
@@ -133,7 +140,15 @@ cudaError_t shadow_and_bins(sam_handle h, int N, const int32_t *kcp, const int32
                             int64_t *nbcnt = nullptr, uint8_t *lrow = nullptr);
 
 // Work list: columns grouped by size class; bin_off (device, [kNumBins+1]).
-cudaError_t build_work_list(sam_handle h, int N, const uint8_t *bin, int32_t *work, int32_t *bin_off);
+// work list of the columns grouped by size class; ws (nullable): int32[2 kNumBins] workspace
+cudaError_t build_work_list(sam_handle h, int N, const uint8_t *bin, int32_t *work, int32_t *bin_off,
+                            int32_t *ws = nullptr);
+// out[j] = bin[j] where colstat[j] == flag, else no size class
+cudaError_t flagged_bins(sam_handle h, int N, const uint8_t *bin, const int32_t *colstat, int32_t flag, uint8_t *out);
+// automatic refinement: FP64 re-solve of the columns the FP32 kernel flagged,
+// then the per-mode column counts (counts[kAutoSteps + 1], nullable)
+cudaError_t launch_refine_fallback(sam_handle h, const LsqArgs &args, int N, const uint8_t *bin, uint8_t *bin2,
+                                   int32_t *work2, int32_t *bin_off2, int32_t *ws, int64_t *counts);
 
 // Least-squares launches for every size class.
 cudaError_t launch_lsq(sam_handle h, int precision, const LsqArgs &args);

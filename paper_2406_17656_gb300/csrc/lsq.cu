@@ -93,8 +93,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) lsq_kernel(LsqArgs args, 
         __syncwarp();
         double r2 = 0.0;
         bool need_final = true;
+        bool fallback = false;
         if constexpr (!FP64) {
-            const int steps = args.refine_steps;
+            // fixed number of steps, or (refine_steps < 0) up to kAutoSteps
+            // with the stopping test below
+            const bool autoref = args.refine_steps < 0;
+            const int steps = autoref ? kAutoSteps : args.refine_steps;
+            double d1sq = 0.0;
+            int used = 0;
             for (int step = 0; step < steps; ++step) {
                 // r = c - B m (FP64), g = B^T r (FP64), d = (R^T R)^{-1} g (FP32)
                 residual_rows<TL, false>(S, kcv, nI, ll);
@@ -102,16 +108,41 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) lsq_kernel(LsqArgs args, 
 #pragma unroll
                 for (int q = 0; q < JQ; ++q) x[q] = to_tile<T>(C.bt_times(args, S, S.u.s.r, q));
                 C.normal_solve(S, x);
+                double dsq = 0.0, msq = 0.0;
 #pragma unroll
                 for (int q = 0; q < JQ; ++q) {
                     const int c = ll + q * P;
                     if (c < nJ) {
-                        mq[q] += to_f64<T>(x[q]);
+                        const double dq = to_f64<T>(x[q]);
+                        mq[q] += dq;
                         S.m[c] = mq[q];
                         S.u.s.y[c] = x[q];
+                        dsq = fma(dq, dq, dsq);
+                        msq = fma(mq[q], mq[q], msq);
                     }
                 }
                 __syncwarp();
+                used = step + 1;
+                if (autoref) {
+                    // CSNE contracts the error by a factor rho ~ u_32 kappa^2 per step.
+                    // After step 1 the error is ~ rho |d_1| with rho <~ kAutoC |d_1| / |m|:
+                    // stop when kAutoC |d_1|^2 <= kAutoTol |m|^2.  After step 2,
+                    // rho ~ |d_2| / |d_1|; a predicted error |d_2|^2 / |d_1| above
+                    // kFallbackTol |m| sends the column to the FP64 solve.
+                    dsq = group_sum<P>(dsq);
+                    msq = group_sum<P>(msq);
+                    bool more = false;
+                    if (step == 0) {
+                        more = kAutoC * dsq > kAutoTol * msq;
+                        d1sq = dsq;
+                    } else {
+                        // (max: a growing correction is judged by itself)
+                        fallback = dsq * dsq > kFallbackTol * kFallbackTol * msq * fmax(d1sq, dsq);
+                    }
+                    if (!__any_sync(0xffffffffu, more)) break;  // warp-uniform
+                }
+            }
+            if (used > 0) {
                 // final residual r - B d: B d in FP32 from the rounded
                 // entries (its error, ~1e-7 |B d|, multiplies a correction
                 // that is already ~1e-6 of |c|), subtracted and squared in FP64
@@ -133,6 +164,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) lsq_kernel(LsqArgs args, 
                 r2 = rf2;
                 need_final = false;
             }
+            if (autoref && C.valid && ll == 0 && args.refine_used)
+                args.refine_used[C.jj] = (uint8_t)((fallback && C.status == kStOk) ? kAutoSteps + 1 : used);
         }
         if (need_final) {
             r2 = residual_rows<TL>(S, kcv, nI, ll);
@@ -148,6 +181,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) lsq_kernel(LsqArgs args, 
         if (C.valid) {
             int status = C.status;
             if (status == kStOk && (nf || !finite64(r2))) status = kStNonfinite;
+            if (status == kStOk && fallback) status = kStRefine;  // re-solved by the FP64 kernel
             const int njo = args.jcp[C.jj + 1] - C.jb;
 #pragma unroll
             for (int q = 0; q < JQ; ++q) {
@@ -206,6 +240,43 @@ cudaError_t launch_lsq(sam_handle h, int precision, const LsqArgs &args) {
     if (e != cudaSuccess) return e;
     e = handle_variant(h, 4) ? launch_one<F4b, false>(h, args, 4) : launch_one<F4, false>(h, args, 4);
     return e;
+}
+
+namespace {
+// columns that took s = 1..kAutoSteps steps, and FP64 re-solves
+__global__ void refine_count_kernel(int64_t N, const uint8_t *used, unsigned long long *counts) {
+    __shared__ unsigned long long sh[kAutoSteps + 1];
+    if (threadIdx.x <= kAutoSteps) sh[threadIdx.x] = 0ull;
+    __syncthreads();
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        const int u = used[j];
+        if (u >= 1 && u <= kAutoSteps + 1) atomicAdd(&sh[u - 1], 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x <= kAutoSteps && sh[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sh[threadIdx.x]);
+}
+}  // namespace
+
+cudaError_t launch_refine_fallback(sam_handle h, const LsqArgs &args, int N, const uint8_t *bin, uint8_t *bin2,
+                                   int32_t *work2, int32_t *bin_off2, int32_t *ws, int64_t *counts) {
+    cudaError_t e = flagged_bins(h, N, bin, args.colstat, kStRefine, bin2);
+    if (e != cudaSuccess) return e;
+    if ((e = build_work_list(h, N, bin2, work2, bin_off2, ws)) != cudaSuccess) return e;
+    LsqArgs a = args;
+    a.work = work2;
+    a.bin_off = bin_off2;
+    if ((e = launch_lsq(h, SAM_FP64, a)) != cudaSuccess) return e;
+    if (counts) {
+        if ((e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * (kAutoSteps + 1), handle_stream(h))) != cudaSuccess)
+            return e;
+        int blocks = (N + 255) / 256;
+        if (blocks > handle_sms(h) * 4) blocks = handle_sms(h) * 4;
+        if (blocks < 1) blocks = 1;
+        refine_count_kernel<<<blocks, 256, 0, handle_stream(h)>>>(N, args.refine_used,
+                                                                  reinterpret_cast<unsigned long long *>(counts));
+        count_launch(h);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace sam

@@ -324,8 +324,8 @@ cudaError_t csr_to_csc(sam_handle h, int n, int64_t nnz, const int32_t *rp, cons
 namespace {
 
 constexpr int kMergeWarps = 4;
-constexpr int kBitWords = 2048;  // bitmap window of 65536 indices per warp
-constexpr int kMergeBuf = 2048;  // fallback candidate buffer (shares the storage)
+constexpr int kBitWords = 1024;  // bitmap window of 32768 indices per warp
+constexpr int kMergeBuf = 1024;  // fallback candidate buffer (shares the storage)
 
 // Warp-cooperative sort + unique of buf[0..cnt), cnt <= kMergeBuf (fallback
 // path for wide windows).  Returns the number of distinct values, left
@@ -517,6 +517,135 @@ __global__ void level01_fill(int n, const int32_t *kcp, const int32_t *kri, int 
     if (!placed) jri[o++] = j;
 }
 
+// Size classes: |I| <= bin_maxi, |J| <= bin_maxj, nnz(B) <= 8 * bin_maxi.
+// Must match the tile table in lsq.cu.
+__constant__ int c_bin_maxi[kNumBins] = {14, 26, 40, 52, 64};
+__constant__ int c_bin_maxj[kNumBins] = {5, 9, 23, 27, 27};
+
+__device__ __forceinline__ int size_class(int u, int nj, int total) {
+    int b = kBinNone;
+    if (u >= nj && u >= 0)
+        for (int q = 0; q < kNumBins; ++q)
+            if (u <= c_bin_maxi[q] && nj <= c_bin_maxj[q] && total <= 8 * c_bin_maxi[q]) {
+                b = q;
+                break;
+            }
+    return b;
+}
+
+constexpr int kRegRows = 16;  // stored entries per source column held in registers (fast path)
+
+// Fast path of the union of the lists X(:, l), l in Y(:, j), when Y(:, j)
+// has at most 32 entries and every list at most kRegRows (every stencil and
+// FEM matrix here): lane t holds list Y(:, j)[t] in registers, read in one
+// round of independent loads and reused for the bitmap union, the sorted
+// output (out[0..min(count, cap)), nullable) and, for the shadow (SHADOW),
+// the size class and the local ranks of all entries (lrow_j, nullable).
+// Returns false, having written nothing, when the column does not qualify
+// or its values span more than the bitmap window.
+template <bool SHADOW>
+__device__ bool union_fast(int j, const int32_t *kcp, const int32_t *kri, const int32_t *jcp, const int32_t *jri,
+                           unsigned *bm, unsigned char *wpre, unsigned char *stage, int32_t *ish_j, int cap,
+                           uint8_t *lrow_j, UnionResult &r, int &bsz) {
+    const int lane = threadIdx.x & 31;
+    const int yb = jcp[j], nj = jcp[j + 1] - yb;
+    if (nj > 32) return false;
+    int cb = 0, len = 0;
+    if (lane < nj) {
+        const int l = jri[yb + lane];
+        cb = kcp[l];
+        len = kcp[l + 1] - cb;
+    }
+    int mx = len;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (mx > kRegRows) return false;
+    int v[kRegRows];
+#pragma unroll
+    for (int u = 0; u < kRegRows; ++u) v[u] = (u < len) ? __ldg(kri + cb + u) : 0;
+    int lo = INT_MAX, hi = INT_MIN;
+#pragma unroll
+    for (int u = 0; u < kRegRows; ++u)
+        if (u < len) {
+            lo = min(lo, v[u]);
+            hi = max(hi, v[u]);
+        }
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int off = incl - len;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (total == 0) {
+        r = UnionResult{0, 0, 0, lo};
+        if (SHADOW) bsz = size_class(0, nj, 0);
+        return true;
+    }
+    const int64_t span = (int64_t)hi - lo + 1;
+    if (span > (int64_t)kBitWords * 32) return false;
+    const int words = (int)((span + 31) >> 5);
+    for (int w = lane; w < words; w += 32) bm[w] = 0u;
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < kRegRows; ++u)
+        if (u < len) {
+            const int x = v[u] - lo;
+            atomicOr(&bm[x >> 5], 1u << (x & 31));
+        }
+    __syncwarp();
+    const int wpl = (words + 31) >> 5;
+    const int w0 = lane * wpl, w1 = min(words, w0 + wpl);
+    int cnt = 0;
+    for (int w = w0; w < w1; ++w) cnt += __popc(bm[w]);
+    int winc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, winc, o);
+        if (lane >= o) winc += y;
+    }
+    const int count = __shfl_sync(0xffffffffu, winc, 31);
+    {
+        int run = winc - cnt;
+        int pos = run;
+        for (int w = w0; w < w1; ++w) {
+            if (SHADOW) wpre[w] = (unsigned char)(run < 255 ? run : 255);
+            unsigned bits = bm[w];
+            run += __popc(bits);
+            if (!ish_j) continue;
+            while (bits && pos < cap) {
+                const int bit = __ffs(bits) - 1;
+                ish_j[pos++] = lo + (w << 5) + bit;
+                bits &= bits - 1u;
+            }
+        }
+    }
+    __syncwarp();
+    if (SHADOW) bsz = size_class(count, nj, total);
+    if (SHADOW && lrow_j && bsz != kBinNone) {
+        // rank of every entry among the shadow rows, in gather order
+#pragma unroll
+        for (int u = 0; u < kRegRows; ++u)
+            if (u < len) {
+                const int d = v[u] - lo;
+                stage[off + u] = (unsigned char)(wpre[d >> 5] + __popc(bm[d >> 5] & ((1u << (d & 31)) - 1u)));
+            }
+        __syncwarp();
+        const unsigned *src = reinterpret_cast<const unsigned *>(stage);
+        unsigned *dst = reinterpret_cast<unsigned *>(lrow_j);
+        for (int w = lane; w < (total + 3) / 4; w += 32) dst[w] = src[w];
+    }
+    __syncwarp();
+    r = UnionResult{count, total, 0, lo};
+    return true;
+}
+
 // mode 0: count distinct rows -> cnt[j]; mode 1: write them to out + optr[j]
 __global__ void __launch_bounds__(kMergeWarps * 32) product_pattern_kernel(
     int n, const int32_t *xcp, const int32_t *xri, const int32_t *ycp, const int32_t *yri, int mode,
@@ -526,7 +655,10 @@ __global__ void __launch_bounds__(kMergeWarps * 32) product_pattern_kernel(
     unsigned *bm = bms[warp];
     for (int64_t j = (int64_t)blockIdx.x * kMergeWarps + warp; j < n; j += (int64_t)gridDim.x * kMergeWarps) {
         int32_t *dst = (mode == 1) ? out + optr[j] : nullptr;
-        UnionResult r = warp_union((int)j, xcp, xri, ycp, yri, bm, dst, INT_MAX);
+        UnionResult r;
+        int unused = 0;
+        if (!union_fast<false>((int)j, xcp, xri, ycp, yri, bm, nullptr, nullptr, dst, INT_MAX, nullptr, r, unused))
+            r = warp_union((int)j, xcp, xri, ycp, yri, bm, dst, INT_MAX);
         if (lane == 0) {
             if (r.count < 0) {
                 if (mode == 0) cnt[j] = 0;
@@ -544,10 +676,6 @@ int merge_grid(sam_handle h, int n) {
     return blocks < cap ? (blocks > 0 ? blocks : 1) : cap;
 }
 
-// Size classes: |I| <= bin_maxi, |J| <= bin_maxj, nnz(B) <= 8 * bin_maxi.
-// Must match the tile table in lsq.cu.
-__constant__ int c_bin_maxi[kNumBins] = {14, 26, 40, 52, 64};
-__constant__ int c_bin_maxj[kNumBins] = {5, 9, 23, 27, 27};
 
 __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const int32_t *kcp, const int32_t *kri,
                                                                   const int32_t *jcp, const int32_t *jri,
@@ -559,65 +687,65 @@ __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const i
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned *bm = bms[warp];
     unsigned char *wpre = pres[warp];
+    unsigned char *stage = stg[warp];
     for (int64_t j = (int64_t)blockIdx.x * kMergeWarps + warp; j < n; j += (int64_t)gridDim.x * kMergeWarps) {
-        UnionResult r = warp_union((int)j, kcp, kri, jcp, jri, bm, ish + j * kICap, kICap, wpre);
         const int nj = jcp[j + 1] - jcp[j];
-        const int u = r.count;
+        UnionResult r;
         int b = kBinNone;
-        if (u >= nj && u >= 0)
-            for (int q = 0; q < kNumBins; ++q)
-                if (u <= c_bin_maxi[q] && nj <= c_bin_maxj[q] && r.total <= 8 * c_bin_maxi[q]) {
-                    b = q;
-                    break;
-                }
-        // local shadow row of every entry of A(:, J_j), in gather order (the
-        // columns of J_j in order, each in CSC order): its rank in I_j,
-        // staged in shared memory and written out as 32-bit words
-        if (lrow && b != kBinNone) {
-            const int yb = jcp[j], ye = jcp[j + 1];
-            unsigned char *stage = stg[warp];
-            int off = 0;
-            for (int base = yb; base < ye; base += 32) {
-                const int t = base + lane;
-                int xb = 0, len = 0;
-                if (t < ye) {
-                    const int l = jri[t];
-                    xb = kcp[l];
-                    len = kcp[l + 1] - xb;
-                }
-                int incl = len;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                unsigned char *dst = stage + off + incl - len;
-                for (int q = 0; q < len; ++q) {
-                    const int x = kri[xb + q];
-                    int rank;
-                    if (r.mode == 0) {
-                        const int d = x - r.lo;
-                        rank = wpre[d >> 5] + __popc(bm[d >> 5] & ((1u << (d & 31)) - 1u));
-                    } else {
-                        const int *srt = (const int *)bm;
-                        int lo = 0, hi = u - 1;
-                        rank = 0;
-                        while (lo <= hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (srt[mid] < x) lo = mid + 1; else if (srt[mid] > x) hi = mid - 1; else { rank = mid; break; }
-                        }
+        if (!union_fast<true>((int)j, kcp, kri, jcp, jri, bm, wpre, stage, ish + j * kICap, kICap,
+                              lrow ? lrow + j * kLCap : nullptr, r, b)) {
+            r = warp_union((int)j, kcp, kri, jcp, jri, bm, ish + j * kICap, kICap, wpre);
+            b = size_class(r.count, nj, r.total);
+            // local shadow row of every entry of A(:, J_j), in gather order (the
+            // columns of J_j in order, each in CSC order): its rank in I_j,
+            // staged in shared memory and written out as 32-bit words
+            if (lrow && b != kBinNone) {
+                const int yb = jcp[j], ye = jcp[j + 1];
+                const int u = r.count;
+                int off = 0;
+                for (int base = yb; base < ye; base += 32) {
+                    const int t = base + lane;
+                    int xb = 0, len = 0;
+                    if (t < ye) {
+                        const int l = jri[t];
+                        xb = kcp[l];
+                        len = kcp[l + 1] - xb;
                     }
-                    dst[q] = (unsigned char)rank;
+                    int incl = len;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    unsigned char *dst = stage + off + incl - len;
+                    for (int q = 0; q < len; ++q) {
+                        const int x = kri[xb + q];
+                        int rank;
+                        if (r.mode == 0) {
+                            const int d = x - r.lo;
+                            rank = wpre[d >> 5] + __popc(bm[d >> 5] & ((1u << (d & 31)) - 1u));
+                        } else {
+                            const int *srt = (const int *)bm;
+                            int lo = 0, hi = u - 1;
+                            rank = 0;
+                            while (lo <= hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (srt[mid] < x) lo = mid + 1; else if (srt[mid] > x) hi = mid - 1; else { rank = mid; break; }
+                            }
+                        }
+                        dst[q] = (unsigned char)rank;
+                    }
+                    off += __shfl_sync(0xffffffffu, incl, 31);
                 }
-                off += __shfl_sync(0xffffffffu, incl, 31);
+                __syncwarp();
+                const unsigned *src = reinterpret_cast<const unsigned *>(stage);
+                unsigned *out = reinterpret_cast<unsigned *>(lrow + j * kLCap);
+                for (int w = lane; w < (r.total + 3) / 4; w += 32) out[w] = src[w];
             }
             __syncwarp();
-            const unsigned *src = reinterpret_cast<const unsigned *>(stage);
-            unsigned *out = reinterpret_cast<unsigned *>(lrow + j * kLCap);
-            for (int w = lane; w < (r.total + 3) / 4; w += 32) out[w] = src[w];
         }
-        __syncwarp();
         if (lane == 0) {
+            const int u = r.count;
             icnt[j] = u;
             bin[j] = (uint8_t)b;
             if (nbcnt) nbcnt[j] = r.total;
@@ -625,6 +753,11 @@ __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const i
             colstat[j] = (b != kBinNone) ? kStOk : ((u >= 0 && u < nj) ? kStRank : kStUnsupported);
         }
     }
+}
+
+__global__ void flagged_bins_kernel(int n, const uint8_t *bin, const int32_t *colstat, int32_t flag, uint8_t *out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[j] = (colstat[j] == flag) ? bin[j] : (uint8_t)kBinNone;
 }
 
 __global__ void bin_count_kernel(int n, const uint8_t *bin, int32_t *counts /* [kNumBins] */) {
@@ -729,9 +862,10 @@ cudaError_t shadow_and_bins(sam_handle h, int N, const int32_t *kcp, const int32
     return cudaGetLastError();
 }
 
-cudaError_t build_work_list(sam_handle h, int N, const uint8_t *bin, int32_t *work, int32_t *bin_off) {
+cudaError_t build_work_list(sam_handle h, int N, const uint8_t *bin, int32_t *work, int32_t *bin_off,
+                            int32_t *ws) {
     cudaStream_t st = handle_stream(h);
-    int32_t *tmp = (int32_t *)pool_alloc(h, sizeof(int32_t) * 2 * kNumBins);
+    int32_t *tmp = ws ? ws : (int32_t *)pool_alloc(h, sizeof(int32_t) * 2 * kNumBins);
     if (!tmp) return cudaErrorMemoryAllocation;
     int32_t *counts = tmp, *cursor = tmp + kNumBins;
     cudaMemsetAsync(counts, 0, sizeof(int32_t) * kNumBins, st);
@@ -740,7 +874,15 @@ cudaError_t build_work_list(sam_handle h, int N, const uint8_t *bin, int32_t *wo
     bin_offsets_kernel<<<1, 32, 0, st>>>(counts, bin_off, cursor);
     bin_scatter_kernel<<<blocks, 256, 0, st>>>(N, bin, cursor, work);
     count_launch(h, 3);
-    pool_free(h, tmp);
+    if (!ws) pool_free(h, tmp);
+    return cudaGetLastError();
+}
+
+cudaError_t flagged_bins(sam_handle h, int N, const uint8_t *bin, const int32_t *colstat, int32_t flag,
+                         uint8_t *out) {
+    if (N == 0) return cudaSuccess;
+    flagged_bins_kernel<<<(N + 255) / 256, 256, 0, handle_stream(h)>>>(N, bin, colstat, flag, out);
+    count_launch(h);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,12 @@ SAM_FLAG_TRUSTED = 1
 SAM_STATIC_MAX_ROWS = 1 << 19  # largest order sam_residual_static accepts
 
 PRECISIONS = {"fp64": SAM_FP64, "fp32r": SAM_FP32_REFINE}
+SAM_REFINE_AUTO = -1
+
+
+def _steps(refine_steps) -> int:
+    """refine_steps as an int; "auto" selects SAM_REFINE_AUTO."""
+    return SAM_REFINE_AUTO if refine_steps == "auto" else int(refine_steps)
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -97,6 +103,7 @@ _SIGS = [
     ("sam_plan_execute", ctypes.c_int32, [_vp]),
     ("sam_plan_launches", ctypes.c_int32, [_vp, _i64p]),
     ("sam_plan_destroy", ctypes.c_int32, [_vp]),
+    ("sam_refine_stats", ctypes.c_int32, [_vp, _i64p, ctypes.c_int]),
     ("sam_set_tile_variants", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("sam_get_tile_variants", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("sam_profile", ctypes.c_int32, [_vp, ctypes.c_int]),
@@ -368,7 +375,7 @@ class Handle:
                    torch.empty(S.nnz, dtype=torch.int32, device=dev),
                    torch.empty(S.nnz, dtype=torch.float64, device=dev))
         a, z = A_k.c(), A_0.c()
-        _check(load().sam_build(self.ptr, ctypes.byref(a), ctypes.byref(z), S.ptr, int(prec), int(refine_steps),
+        _check(load().sam_build(self.ptr, ctypes.byref(a), ctypes.byref(z), S.ptr, int(prec), _steps(refine_steps),
                                 _addr(out[0]), _addr(out[1]), _addr(out[2]), _addr(col_status), _addr(res2)),
                "sam_build")
         return out
@@ -407,7 +414,7 @@ class Handle:
             zp, fn, name = ctypes.byref(z), load().sam_build_batched, "sam_build_batched"
         pats = (_vp * K)(*[s.ptr for s in Ss])
         fro = np.zeros(K, dtype=np.float64) if want_fro else None
-        _check(fn(self.ptr, K, arr, zp, pats, int(prec), int(refine_steps), offsets.ctypes.data_as(_i64p),
+        _check(fn(self.ptr, K, arr, zp, pats, int(prec), _steps(refine_steps), offsets.ctypes.data_as(_i64p),
                   _addr(M_row_ptr), _addr(M_col_idx), _addr(M_val), _addr(col_status), _addr(res2),
                   fro.ctypes.data_as(_f64p) if fro is not None else None), name)
         return offsets, M_row_ptr, M_col_idx, M_val, fro
@@ -443,7 +450,7 @@ class Handle:
             dA_0_val = torch.empty(A_0.nnz, dtype=torch.float64, device="cuda")
         a, z = A_k.c(), A_0.c()
         _check(load().sam_build_backward(self.ptr, ctypes.byref(a), ctypes.byref(z), S.ptr, int(prec),
-                                         int(refine_steps), _addr(M_val), _addr(dM_val), float(resid_weight),
+                                         _steps(refine_steps), _addr(M_val), _addr(dM_val), float(resid_weight),
                                          _addr(dA_k_val), _addr(dA_0_val), _addr(dM_resid)), "sam_build_backward")
         return dA_k_val, dA_0_val
 
@@ -466,7 +473,7 @@ class Handle:
         arr = (sam_csr * K)(*[a.c() for a in A_ks])
         z = (sam_csr * K)(*[a.c() for a in A_0s])
         pats = (_vp * K)(*[s.ptr for s in Ss])
-        _check(load().sam_build_backward_batched(self.ptr, K, arr, z, pats, int(prec), int(refine_steps),
+        _check(load().sam_build_backward_batched(self.ptr, K, arr, z, pats, int(prec), _steps(refine_steps),
                                                  offsets.ctypes.data_as(_i64p), _addr(M_val), _addr(dM_val),
                                                  float(resid_weight), _addr(dA_k_val), _addr(dA_0_val),
                                                  _addr(dM_resid)), "sam_build_backward_batched")
@@ -499,7 +506,7 @@ class Handle:
         z = (sam_csr * len(tg))(*[a.c() for a in tg])
         pats = (_vp * K)(*[s.ptr for s in Ss])
         out = _vp()
-        _check(load().sam_plan_create(self.ptr, K, arr, z, len(tg), pats, int(prec), int(refine_steps),
+        _check(load().sam_plan_create(self.ptr, K, arr, z, len(tg), pats, int(prec), _steps(refine_steps),
                                       offsets.ctypes.data_as(_i64p), _addr(rp), _addr(ci), _addr(v), _addr(st),
                                       _addr(r2), _addr(f2), ctypes.byref(out)), "sam_plan_create")
         return Plan(self, out.value, (tuple(A_ks), tuple(tg)), offsets, (rp, ci, v, st, r2, f2))
@@ -514,13 +521,20 @@ class Handle:
         arr = (sam_csr * K)(*[a.c() for a in A_ks])
         z = A_0.c()
         pats = (_vp * K)(*[s.ptr for s in Ss])
-        _check(load().sam_tune(self.ptr, K, arr, ctypes.byref(z), pats, int(prec), int(refine_steps),
+        _check(load().sam_tune(self.ptr, K, arr, ctypes.byref(z), pats, int(prec), _steps(refine_steps),
                                cache_path.encode() if cache_path else None), "sam_tune")
         return self.sam_get_tile_variants()
 
     def sam_set_tile_variants(self, variants):
         v = (ctypes.c_int * 5)(*[int(x) for x in variants])
         _check(load().sam_set_tile_variants(self.ptr, v, len(variants)), "sam_set_tile_variants")
+
+    def sam_refine_stats(self):
+        """[one step, two steps, FP64 re-solve] column counts of the last
+        build with refine_steps="auto"."""
+        c = (ctypes.c_int64 * 3)()
+        _check(load().sam_refine_stats(self.ptr, c, 3), "sam_refine_stats")
+        return list(c)
 
     def sam_get_tile_variants(self):
         v = (ctypes.c_int * 5)()
