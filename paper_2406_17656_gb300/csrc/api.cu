@@ -53,6 +53,7 @@ struct PatternGroup {
     int32_t *mrp = nullptr, *mci = nullptr;  // CSR of the block-diagonal map
     int32_t *csr_pos = nullptr;              // CSC entry -> CSR position
     std::vector<int64_t> off;                // per-map nnz prefix [K+1]
+    bool symmetric = false;                  // every map's pattern is structurally symmetric
 };
 }  // namespace
 
@@ -243,7 +244,8 @@ sam_status drain_status(sam_handle h) {
 
 // Validates the CSR structures of equal-order matrices on the device;
 // synchronises once.  Nothing reads an unvalidated structure before this.
-sam_status validate_all(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms) {
+sam_status validate_all(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms, std::vector<char> *sym = nullptr) {
+    if (sym) sym->assign(ms.size(), 0);  // unknown (trusted inputs): treated as not symmetric
     if ((h->flags & SAM_FLAG_TRUSTED) || ms.empty()) return SAM_OK;
     const int K = (int)ms.size();
     std::vector<CsrPtrs> tab(K);
@@ -254,25 +256,28 @@ sam_status validate_all(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms
     }
     CsrPtrs *dtab = sc.get<CsrPtrs>(K);
     int64_t *dnz = sc.get<int64_t>(K);
-    int32_t *flag = sc.get<int32_t>(1);
+    int32_t *flag = sc.get<int32_t>((size_t)K + 1);  // [0] status, [1 + k] matrix k not symmetric
     if (!dtab || !dnz || !flag) return SAM_ERR_OOM;
     cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * K, cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(dnz, nz.data(), sizeof(int64_t) * K, cudaMemcpyHostToDevice, h->stream);
-    cudaMemsetAsync(flag, 0, sizeof(int32_t), h->stream);
+    cudaMemsetAsync(flag, 0, sizeof(int32_t) * ((size_t)K + 1), h->stream);
+    int32_t *asym = sym ? flag + 1 : nullptr;
     // matrices of different order (the residual call) are validated one by one
     bool same = true;
     for (auto &m : ms) same &= (m.n == ms[0].n);
     if (same) {
-        if (validate_csr_batch(h, K, ms[0].n, dtab, dnz, flag) != cudaSuccess) return SAM_ERR_CUDA;
+        if (validate_csr_batch(h, K, ms[0].n, dtab, dnz, flag, asym) != cudaSuccess) return SAM_ERR_CUDA;
     } else {
         for (int k = 0; k < K; ++k)
-            if (validate_csr_batch(h, 1, ms[k].n, dtab + k, dnz + k, flag) != cudaSuccess) return SAM_ERR_CUDA;
+            if (validate_csr_batch(h, 1, ms[k].n, dtab + k, dnz + k, flag, asym ? asym + k : nullptr) != cudaSuccess)
+                return SAM_ERR_CUDA;
     }
-    cudaMemcpyAsync(h->h_flag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+    std::vector<int32_t> hf((size_t)K + 1, 0);
+    cudaMemcpyAsync(hf.data(), flag, sizeof(int32_t) * (sym ? (size_t)K + 1 : 1), cudaMemcpyDeviceToHost, h->stream);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SAM_ERR_CUDA;
-    const int32_t hv = *h->h_flag;
-    *h->h_flag = 0;
-    return hv ? (sam_status)hv : SAM_OK;
+    if (sym && hf[0] == 0)
+        for (int k = 0; k < K; ++k) (*sym)[k] = hf[(size_t)k + 1] == 0;
+    return hf[0] ? (sam_status)hf[0] : SAM_OK;
 }
 
 __global__ void scatter_inverse_kernel(int64_t nnz, const int32_t *perm, int32_t *pos) {
@@ -299,7 +304,8 @@ void group_release(PatternGroup *g) {
 // Completes a group from its block-diagonal CSC pattern (takes ownership of
 // jcp / jri, which must come from the handle's pool): per-map offsets, the
 // CSR structure of the map and the CSC -> CSR positions.
-sam_status group_finish(sam_handle h, int K, int n, int32_t *jcp, int32_t *jri, int64_t nnz, PatternGroup **out) {
+sam_status group_finish(sam_handle h, int K, int n, int32_t *jcp, int32_t *jri, int64_t nnz, PatternGroup **out,
+                        bool symmetric = false) {
     PatternGroup *g = new (std::nothrow) PatternGroup;
     if (!g) return SAM_ERR_OOM;
     g->h = h;
@@ -321,13 +327,22 @@ sam_status group_finish(sam_handle h, int K, int n, int32_t *jcp, int32_t *jri, 
         return s;
     };
     if (!g->mrp || !g->mci || !g->csr_pos || !perm || !doff) return fail(SAM_ERR_OOM);
-    // the CSC of the map read as the CSR of its transpose; transposing it
-    // gives the CSR of the map, with perm[p] = CSC entry of CSR position p
-    if (csr_to_csc(h, (int)N, nnz, jcp, jri, nullptr, g->mrp, g->mci, nullptr, perm) != cudaSuccess)
-        return fail(SAM_ERR_CUDA);
-    if (nnz > 0) {
-        scatter_inverse_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, h->stream>>>(nnz, perm, g->csr_pos);
-        count_launch(h);
+    g->symmetric = symmetric;
+    if (symmetric) {
+        // a symmetric pattern is its own transpose: the map's CSR structure is
+        // the CSC structure, and CSC entry p sits at its mirror's position
+        if (csr_to_csc(h, (int)N, nnz, jcp, jri, nullptr, g->mrp, g->mci, nullptr, nullptr, true) != cudaSuccess ||
+            mirror_positions(h, (int)N, jcp, jri, g->csr_pos) != cudaSuccess)
+            return fail(SAM_ERR_CUDA);
+    } else {
+        // the CSC of the map read as the CSR of its transpose; transposing it
+        // gives the CSR of the map, with perm[p] = CSC entry of CSR position p
+        if (csr_to_csc(h, (int)N, nnz, jcp, jri, nullptr, g->mrp, g->mci, nullptr, perm) != cudaSuccess)
+            return fail(SAM_ERR_CUDA);
+        if (nnz > 0) {
+            scatter_inverse_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, h->stream>>>(nnz, perm, g->csr_pos);
+            count_launch(h);
+        }
     }
     gather_strided_kernel<<<(K + 1 + 127) / 128, 128, 0, h->stream>>>(K, n, jcp, doff);
     count_launch(h);
@@ -408,7 +423,9 @@ sam_status group_for(sam_handle h, int K, const sam_pattern *S, PatternGroup **g
         base += S[k]->nnz;
     }
     *temp = true;
-    return group_finish(h, K, n, jcp, jri, tot, g_out);
+    bool sym = true;
+    for (int k = 0; k < K; ++k) sym = sym && S[k]->g->symmetric;
+    return group_finish(h, K, n, jcp, jri, tot, g_out, sym);
 }
 
 }  // namespace
@@ -557,8 +574,11 @@ sam_status sam_pattern_build_batched(sam_handle h, int K, const sam_csr *A, int 
     std::vector<DevCsr> d(K);
     for (int k = 0; k < K; ++k) d[k] = stage_csr(sg, &A[k], false);
     if (sg.failed) return SAM_ERR_OOM;
-    sam_status s = validate_all(h, sc, d);
+    std::vector<char> symv;
+    sam_status s = validate_all(h, sc, d, &symv);
     if (s != SAM_OK) return s;
+    bool sym = true;
+    for (char c : symv) sym = sym && c;
     // block-diagonal structure of the batch, then its CSC
     std::vector<CsrPtrs> tab(K);
     std::vector<int64_t> off(K + 1, 0);
@@ -574,13 +594,15 @@ sam_status sam_pattern_build_batched(sam_handle h, int K, const sam_csr *A, int 
     cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * K, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, st);
     if (concat_block_diag(h, K, n, dtab, doff, brp, bci, nullptr) != cudaSuccess) return SAM_ERR_CUDA;
-    if (csr_to_csc(h, (int)N, tot, brp, bci, nullptr, kcp, kri, nullptr, nullptr) != cudaSuccess) return SAM_ERR_CUDA;
+    if (csr_to_csc(h, (int)N, tot, brp, bci, nullptr, kcp, kri, nullptr, nullptr, sym) != cudaSuccess)
+        return SAM_ERR_CUDA;
     int32_t *jcp = nullptr, *jri = nullptr;
     int64_t nnz = 0;
     s = level_pattern(h, (int)N, kcp, kri, tot, level, &jcp, &jri, &nnz);
     if (s != SAM_OK) return s;
     PatternGroup *g = nullptr;
-    s = group_finish(h, K, n, jcp, jri, nnz, &g);
+    // level-L patterns of a structurally symmetric matrix are symmetric
+    s = group_finish(h, K, n, jcp, jri, nnz, &g, sym);
     if (s != SAM_OK) return s;
     s = make_patterns(g, out);
     if (s != SAM_OK) {
@@ -612,6 +634,7 @@ sam_status sam_pattern_from_csc(sam_handle h, int32_t n, int64_t nnz, const int3
     // copy of the column pointers)
     std::vector<int32_t> hcp((size_t)n + 1);
     cudaMemcpyAsync(hcp.data(), jcp, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost, h->stream);
+    bool user_sym = false;
     {
         Scratch sc(h);
         DevCsr d;
@@ -621,8 +644,10 @@ sam_status sam_pattern_from_csc(sam_handle h, int32_t n, int64_t nnz, const int3
         d.ci = jri;
         uint32_t saved = h->flags;
         h->flags &= ~(uint32_t)SAM_FLAG_TRUSTED;  // a pattern is always validated
-        sam_status s = validate_all(h, sc, {d});
+        std::vector<char> symv;
+        sam_status s = validate_all(h, sc, {d}, &symv);
         h->flags = saved;
+        user_sym = s == SAM_OK && symv[0];
         bool nonempty = true;
         for (int j = 0; j < n && s == SAM_OK; ++j) nonempty &= hcp[(size_t)j + 1] > hcp[j];
         if (s == SAM_OK && !nonempty) s = SAM_ERR_BAD_CSR;
@@ -633,7 +658,7 @@ sam_status sam_pattern_from_csc(sam_handle h, int32_t n, int64_t nnz, const int3
         }
     }
     PatternGroup *g = nullptr;
-    sam_status s = group_finish(h, 1, n, jcp, jri, nnz, &g);
+    sam_status s = group_finish(h, 1, n, jcp, jri, nnz, &g, user_sym);
     if (s != SAM_OK) return s;
     return make_patterns(g, out);
 }
@@ -683,7 +708,8 @@ namespace {
 // K matrices of order n as one block-diagonal CSC of order K n (with the
 // CSC -> CSR permutation when perm != nullptr); K = 1 skips the copy.
 sam_status block_diag_csc(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms, int n, int32_t **cp,
-                          int32_t **ri, double **cv, int32_t **perm, int64_t *total, Scratch *tmp_sc = nullptr) {
+                          int32_t **ri, double **cv, int32_t **perm, int64_t *total, Scratch *tmp_sc = nullptr,
+                          bool symmetric = false) {
     Scratch &tmp = tmp_sc ? *tmp_sc : sc;  // the concatenated copy lives only until the transpose
     const int K = (int)ms.size();
     const int64_t N = (int64_t)K * n;
@@ -716,7 +742,7 @@ sam_status block_diag_csc(sam_handle h, Scratch &sc, const std::vector<DevCsr> &
         ci = bci;
         v = bv;
     }
-    if (csr_to_csc(h, (int)N, tot, rp, ci, v, *cp, *ri, *cv, perm ? *perm : nullptr) != cudaSuccess)
+    if (csr_to_csc(h, (int)N, tot, rp, ci, v, *cp, *ri, *cv, perm ? *perm : nullptr, symmetric) != cudaSuccess)
         return SAM_ERR_CUDA;
     return SAM_OK;
 }
@@ -759,11 +785,14 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     int32_t *d_st = col_status ? sg.out(col_status, (size_t)N) : nullptr;
     double *d_r2 = res2 ? sg.out(res2, (size_t)N) : nullptr;
     if (sg.failed) return SAM_ERR_OOM;
+    bool ksym = true, zsym = true;  // structurally symmetric sources / targets
     {
         std::vector<DevCsr> all(ak);
         all.insert(all.end(), zs.begin(), zs.end());
-        sam_status s = validate_all(h, sc, all);
+        std::vector<char> symv;
+        sam_status s = validate_all(h, sc, all, &symv);
         if (s != SAM_OK) return s;
+        for (size_t q = 0; q < symv.size(); ++q) (q < ak.size() ? ksym : zsym) &= symv[q] != 0;
     }
     PatternGroup *g = nullptr;
     bool temp = false;
@@ -782,9 +811,9 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     int32_t *zcp = nullptr, *zri = nullptr, *kcp = nullptr, *kri = nullptr;
     double *zcv = nullptr, *kcv = nullptr;
     int64_t zn = 0, kn = 0;
-    sam_status s = block_diag_csc(h, sc, zs, n, &zcp, &zri, &zcv, nullptr, &zn);
+    sam_status s = block_diag_csc(h, sc, zs, n, &zcp, &zri, &zcv, nullptr, &zn, nullptr, zsym);
     if (s != SAM_OK) return s;
-    s = block_diag_csc(h, sc, ak, n, &kcp, &kri, &kcv, nullptr, &kn);
+    s = block_diag_csc(h, sc, ak, n, &kcp, &kri, &kcv, nullptr, &kn, nullptr, ksym);
     if (s != SAM_OK) return s;
     int32_t *ish = sc.get<int32_t>((size_t)N * kICap), *icnt = sc.get<int32_t>((size_t)N);
     uint8_t *bin = sc.get<uint8_t>((size_t)N);
@@ -979,11 +1008,14 @@ sam_status backward_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr 
     double *d_da0 = sg.out(dA_0_val, (size_t)ztot);
     double *d_dmr = dM_resid ? sg.out(dM_resid, (size_t)mtot) : nullptr;
     if (sg.failed) return SAM_ERR_OOM;
+    bool ksym = true, zsym = true;  // structurally symmetric sources / targets
     {
         std::vector<DevCsr> all(ak);
         all.insert(all.end(), zs.begin(), zs.end());
-        sam_status s = validate_all(h, sc, all);
+        std::vector<char> symv;
+        sam_status s = validate_all(h, sc, all, &symv);
         if (s != SAM_OK) return s;
+        for (size_t q = 0; q < symv.size(); ++q) (q < ak.size() ? ksym : zsym) &= symv[q] != 0;
     }
     PatternGroup *g = nullptr;
     bool temp = false;
@@ -999,8 +1031,8 @@ sam_status backward_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr 
     int32_t *zcp = nullptr, *zri = nullptr, *zperm = nullptr, *kcp = nullptr, *kri = nullptr, *kperm = nullptr;
     double *zcv = nullptr, *kcv = nullptr;
     int64_t zn = 0, kn = 0;
-    if ((s = block_diag_csc(h, sc, zs, n, &zcp, &zri, &zcv, &zperm, &zn)) != SAM_OK) return s;
-    if ((s = block_diag_csc(h, sc, ak, n, &kcp, &kri, &kcv, &kperm, &kn)) != SAM_OK) return s;
+    if ((s = block_diag_csc(h, sc, zs, n, &zcp, &zri, &zcv, &zperm, &zn, nullptr, zsym)) != SAM_OK) return s;
+    if ((s = block_diag_csc(h, sc, ak, n, &kcp, &kri, &kcv, &kperm, &kn, nullptr, ksym)) != SAM_OK) return s;
     int32_t *ish = sc.get<int32_t>((size_t)N * kICap), *icnt = sc.get<int32_t>((size_t)N);
     uint8_t *bin = sc.get<uint8_t>((size_t)N);
     int32_t *colstat = sc.get<int32_t>((size_t)N);
@@ -1302,11 +1334,14 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
     std::vector<DevCsr> zs(NT), ak(K);
     for (int t = 0; t < NT; ++t) zs[t] = DevCsr{A_0[t].n, A_0[t].nnz, A_0[t].row_ptr, A_0[t].col_idx, A_0[t].val};
     for (int k = 0; k < K; ++k) ak[k] = DevCsr{A_k[k].n, A_k[k].nnz, A_k[k].row_ptr, A_k[k].col_idx, A_k[k].val};
+    bool ksym = true, zsym = true;  // structurally symmetric sources / targets
     {
         std::vector<DevCsr> all(ak);
         all.insert(all.end(), zs.begin(), zs.end());
-        sam_status s = validate_all(h, tmp, all);
+        std::vector<char> symv;
+        sam_status s = validate_all(h, tmp, all, &symv);
         if (s != SAM_OK) return s;
+        for (size_t q = 0; q < symv.size(); ++q) (q < ak.size() ? ksym : zsym) &= symv[q] != 0;
     }
     {
         bool temp = false;
@@ -1322,9 +1357,9 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
     int32_t *zcp = nullptr, *zri = nullptr, *zperm = nullptr, *kcp = nullptr, *kri = nullptr, *kperm = nullptr;
     double *zcv = nullptr, *kcv = nullptr;
     int64_t zn = 0, kn = 0;
-    sam_status s = block_diag_csc(h, keep, zs, n, &zcp, &zri, &zcv, &zperm, &zn, &tmp);
+    sam_status s = block_diag_csc(h, keep, zs, n, &zcp, &zri, &zcv, &zperm, &zn, &tmp, zsym);
     if (s != SAM_OK) return s;
-    if ((s = block_diag_csc(h, keep, ak, n, &kcp, &kri, &kcv, &kperm, &kn, &tmp)) != SAM_OK) return s;
+    if ((s = block_diag_csc(h, keep, ak, n, &kcp, &kri, &kcv, &kperm, &kn, &tmp, ksym)) != SAM_OK) return s;
     int32_t *ish = keep.get<int32_t>((size_t)N * kICap), *icnt = keep.get<int32_t>((size_t)N);
     uint8_t *bin = tmp.get<uint8_t>((size_t)N);
     int32_t *work = keep.get<int32_t>((size_t)N);

@@ -114,7 +114,8 @@ cudaError_t exclusive_scan_i64(sam_handle h, const int64_t *in, int64_t *out, in
 
 // CSR structure checks of K matrices of order n; sets *flag to SAM_ERR_BAD_CSR
 // on any violation.  mats/nnz are device arrays of K entries.
-cudaError_t validate_csr_batch(sam_handle h, int K, int n, const CsrPtrs *mats, const int64_t *nnz, int32_t *flag);
+cudaError_t validate_csr_batch(sam_handle h, int K, int n, const CsrPtrs *mats, const int64_t *nnz, int32_t *flag,
+                               int32_t *asym = nullptr);
 
 // Concatenate K CSR matrices of order n into the block-diagonal CSR of order
 // K n.  nnz_off (device, [K+1]) = prefix of the nnz; values optional.
@@ -122,9 +123,13 @@ cudaError_t concat_block_diag(sam_handle h, int K, int n, const CsrPtrs *mats, c
                               int32_t *rp, int32_t *ci, double *v);
 
 // CSR -> CSC transpose with sorted rows per column.  perm (nullable) gets the
-// CSR index of every CSC entry; val / cv may be null.
+// CSR index of every CSC entry; val / cv may be null.  symmetric: the
+// structure is known to be structurally symmetric (validated), so the CSC
+// structure is a copy and values / perm come from a mirror lookup (no
+// atomics, no sort).
 cudaError_t csr_to_csc(sam_handle h, int n, int64_t nnz, const int32_t *rp, const int32_t *ci,
-                       const double *val, int32_t *cp, int32_t *ri, double *cv, int32_t *perm);
+                       const double *val, int32_t *cp, int32_t *ri, double *cv, int32_t *perm,
+                       bool symmetric = false);
 
 // Level-L pattern (CSC) of the matrix with CSC structure (kcp, kri), order N.
 // Allocates *jcp / *jri from the pool; synchronises once to size the result.
@@ -164,6 +169,9 @@ cudaError_t permute_scatter_f64(sam_handle h, int64_t nnz, const int32_t *perm, 
 // Deterministic sums: out[k] = sum of x[k*seg .. (k+1)*seg) (squares optional).
 cudaError_t segmented_sum_f64(sam_handle h, const double *x, int K, int64_t seg, double *out, bool squares,
                               double *work = nullptr);
+// pos[q] = position of the mirror entry of CSR position q of a structurally
+// symmetric matrix (the CSR position of A(ci[q], row of q))
+cudaError_t mirror_positions(sam_handle h, int n, const int32_t *rp, const int32_t *ci, int32_t *pos);
 // doubles of workspace segmented_sum_f64 needs for K segments
 size_t segmented_sum_workspace(int K);
 // values of K matrices into the CSC order of their block-diagonal (+ FP32 copy)

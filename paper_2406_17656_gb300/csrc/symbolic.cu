@@ -149,7 +149,20 @@ cudaError_t exclusive_scan_i64(sam_handle h, const int64_t *in, int64_t *out, in
 
 namespace {
 
-__global__ void validate_batch_kernel(int n, const CsrPtrs *mats, const int64_t *nnz, int32_t *flag) {
+__device__ __forceinline__ int lower_bound_i32(const int32_t *a, int len, int key) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Structure checks of K CSR matrices of order n; asym[k] (nullable) is set
+// when matrix k is not structurally symmetric (some stored (i, c) without
+// a stored (c, i)).
+__global__ void validate_batch_kernel(int n, const CsrPtrs *mats, const int64_t *nnz, int32_t *flag,
+                                      int32_t *asym) {
     const int k = blockIdx.y;
     const int32_t *rp = mats[k].rp, *ci = mats[k].ci;
     const int64_t nz = nnz[k];
@@ -162,6 +175,7 @@ __global__ void validate_batch_kernel(int n, const CsrPtrs *mats, const int64_t 
         return;
     }
     int prev = -1;
+    bool sym = true;
     for (int t = b; t < e; ++t) {
         int c = ci[t];
         if (c <= prev || c >= n) {
@@ -169,7 +183,18 @@ __global__ void validate_batch_kernel(int n, const CsrPtrs *mats, const int64_t 
             return;
         }
         prev = c;
+        if (asym && sym) {
+            // the mirror (c, i) in row c, read only inside row c's valid range
+            const int cb = rp[c], ce = rp[c + 1];
+            if (cb < 0 || ce < cb || (int64_t)ce > nz) {
+                sym = false;
+            } else {
+                const int q = lower_bound_i32(ci + cb, ce - cb, (int)i);
+                sym = q < ce - cb && ci[cb + q] == (int)i;
+            }
+        }
     }
+    if (asym && !sym) asym[k] = 1;
 }
 
 __global__ void concat_rows_kernel(int K, int n, const CsrPtrs *mats, const int64_t *nnz_off, int32_t *rp) {
@@ -193,9 +218,10 @@ __global__ void concat_entries_kernel(int n, const CsrPtrs *mats, const int64_t 
 
 }  // namespace
 
-cudaError_t validate_csr_batch(sam_handle h, int K, int n, const CsrPtrs *mats, const int64_t *nnz, int32_t *flag) {
+cudaError_t validate_csr_batch(sam_handle h, int K, int n, const CsrPtrs *mats, const int64_t *nnz, int32_t *flag,
+                               int32_t *asym) {
     dim3 grid((unsigned)((n + 1 + 255) / 256), (unsigned)K);
-    validate_batch_kernel<<<grid, 256, 0, handle_stream(h)>>>(n, mats, nnz, flag);
+    validate_batch_kernel<<<grid, 256, 0, handle_stream(h)>>>(n, mats, nnz, flag, asym);
     count_launch(h);
     return cudaGetLastError();
 }
@@ -289,11 +315,51 @@ __global__ void sort_cols_kernel(int n, const int32_t *cp, int32_t *ri, double *
     }
 }
 
+// Transpose of a structurally symmetric CSR matrix: the CSC structure is the
+// CSR structure, and the entry at position q of row c (column r = ci[q]) of
+// the CSC is A(r, c), stored at position mirror(q) of row r.  Eight threads
+// per row; no atomics, no sort.
+__global__ void mirror_lookup_kernel(int n, const int32_t *rp, const int32_t *ci, const double *val, double *cv,
+                                     int32_t *perm) {
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int sub = threadIdx.x & 7;
+    if (c >= n) return;
+    for (int q = rp[c] + sub; q < rp[c + 1]; q += 8) {
+        const int r = ci[q];
+        const int rb = rp[r];
+        const int e = rb + lower_bound_i32(ci + rb, rp[r + 1] - rb, (int)c);
+        if (cv) cv[q] = val[e];
+        if (perm) perm[q] = e;
+    }
+}
+
 }  // namespace
 
+cudaError_t mirror_positions(sam_handle h, int n, const int32_t *rp, const int32_t *ci, int32_t *pos) {
+    if (n == 0) return cudaSuccess;
+    const int64_t threads = (int64_t)n * 8;
+    mirror_lookup_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, handle_stream(h)>>>(n, rp, ci, nullptr,
+                                                                                         nullptr, pos);
+    count_launch(h);
+    return cudaGetLastError();
+}
+
 cudaError_t csr_to_csc(sam_handle h, int n, int64_t nnz, const int32_t *rp, const int32_t *ci, const double *val,
-                       int32_t *cp, int32_t *ri, double *cv, int32_t *perm) {
+                       int32_t *cp, int32_t *ri, double *cv, int32_t *perm, bool symmetric) {
     cudaStream_t st = handle_stream(h);
+    if (symmetric) {
+        cudaError_t err = cudaMemcpyAsync(cp, rp, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, st);
+        if (err == cudaSuccess && nnz > 0)
+            err = cudaMemcpyAsync(ri, ci, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToDevice, st);
+        if (err != cudaSuccess) return err;
+        if (n > 0 && ((val && cv) || perm)) {
+            const int64_t threads = (int64_t)n * 8;
+            mirror_lookup_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(n, rp, ci, val, val ? cv : nullptr,
+                                                                                    perm);
+            count_launch(h);
+        }
+        return cudaGetLastError();
+    }
     int32_t *cnt = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)n + 1));
     if (!cnt) return cudaErrorMemoryAllocation;
     cudaError_t err = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)n + 1), st);

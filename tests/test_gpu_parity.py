@@ -312,3 +312,59 @@ def test_multi_target_batch_matches_per_pair_oracle(sam, handle):
             assert np.array_equal(ci[offs[k]:offs[k + 1]], ref["ix"])
             assert rel_fro(v[offs[k]:offs[k + 1]], ref["dv"]) <= 1e-10
             assert abs(fro[k] ** 2 - ref["res2"].sum()) <= 1e-9 * ref["res2"].sum()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+def _banded_nonsymmetric(seed, offsets, n=400):
+    """Diagonally dominant matrix with a few nonsymmetric off-diagonals,
+    each entry kept with probability 0.8."""
+    rng = np.random.default_rng(seed)
+    a = np.zeros((n, n))
+    for o in offsets:
+        i = np.arange(max(0, -o), min(n, n - o))
+        keep = rng.random(len(i)) < 0.8
+        a[i[keep], i[keep] + o] = rng.uniform(-1.0, 1.0, keep.sum())
+    a[np.arange(n), np.arange(n)] = 4.0 + rng.random(n)
+    return W.CSR.from_dense(a)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+def test_nonsymmetric_structure_takes_the_general_transpose(sam, handle, precision):
+    """Structurally nonsymmetric source and target go through the
+    atomic-fill + sort transposes (symmetric ones through the mirror
+    lookup); against the oracle."""
+    import torch
+
+    A1 = _banded_nonsymmetric(31, (1, -2, 4, -7))
+    A0 = _banded_nonsymmetric(32, (1, -1, 3))
+    s1 = abs(A1.to_scipy())
+    assert (s1 != s1.T).nnz > 0
+    for level in (1, 2):
+        ref = oracle_map(A1, A0, level)
+        S = handle.sam_pattern_build(dev(sam, A1), level)
+        st = torch.empty(A1.n, dtype=torch.int32, device="cuda")
+        ip, ix, dv = handle.sam_build(dev(sam, A1), dev(sam, A0), S, precision, refine_steps=1, col_status=st)
+        handle.sam_sync()
+        assert int(st.abs().max()) == 0
+        assert np.array_equal(ip.cpu().numpy(), ref["ip"]) and np.array_equal(ix.cpu().numpy(), ref["ix"])
+        assert rel_fro(dv.cpu().numpy(), ref["dv"]) <= TOL[precision]
+
+
+def test_trusted_inputs_give_the_same_maps(sam):
+    """A trusted handle skips validation (and so the symmetry detection):
+    its general transposes give the validated handle's maps bit for bit."""
+    import torch
+
+    seq = W.config4(ncell=24, nmat=3, flip_frac=0.1)
+    outs = []
+    for trusted in (False, True):
+        h = sam.Handle(trusted=trusted)
+        try:
+            Aks = [dev(sam, m) for m in seq.mats]
+            Ss = h.sam_pattern_build_batched(Aks, 2)
+            offs, rp, ci, v, _ = h.sam_build_batched(Aks, dev(sam, seq.mats[0]), Ss, "fp32r", 1)
+            outs.append((rp, ci, v))
+        finally:
+            h.close()
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
