@@ -46,8 +46,17 @@
 namespace sam {
 namespace {
 
+// blocks per SM that the shared memory of a tile allows (1..4): the
+// register budget is held to the same count
+template <class TL>
+struct MinBlocks {
+    static constexpr int bytes = (int)sizeof(ProbSmem<TL>) * TL::PPW * kWarpsPerBlock + 1024;
+    static constexpr int raw = 233472 / bytes;
+    static constexpr int value = raw < 1 ? 1 : (raw > 4 ? 4 : raw);
+};
+
 template <class TL, bool FP64>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) lsq_kernel(LsqArgs args, int bin) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq_kernel(LsqArgs args, int bin) {
     using T = typename TL::T;
     constexpr int P = TL::P, PPW = TL::PPW, RS = TL::RS, CS = TL::CS, JQ = TL::JQ;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -15,6 +15,7 @@ namespace sam {
 namespace {
 
 constexpr int kWarpsPerBlock = 4;
+constexpr int kGatherRegs = 12;  // entries per source column gathered with one round of loads
 
 template <int RG_, int CG_, int RS_, int CS_, typename T_, int MAXI_BIN_>
 struct Tile {
@@ -442,7 +443,29 @@ struct Column {
             // (read straight from global memory: staging them through shared
             // memory first measured 2x slower in the FP64 kernel)
             const uint8_t *lr = args.lrow + (int64_t)jj * kLCap + colB[q];
-            for (int p0 = 0; p0 < len; p0 += 4) {
+            // the first kGatherRegs entries: all loads issued before any use
+            {
+                int rows[kGatherRegs];
+                T vals[kGatherRegs];
+#pragma unroll
+                for (int u = 0; u < kGatherRegs; ++u) {
+                    rows[u] = (u < len) ? (int)lr[u] : -1;
+                    vals[u] = (u < len) ? tile_value<T>(args.kcv, args.kcv32, colA[q] + u) : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < kGatherRegs; ++u) {
+                    if (rows[u] < 0) continue;
+                    int i = rows[u];
+                    if (i >= nI) {  // impossible for a consistent shadow: never write out of bounds
+                        status = kStUnsupported;
+                        i = 0;
+                    }
+                    S.locr[colB[q] + u] = (unsigned char)i;
+                    S.u.tile[tile_pos<TL>(i, c)] = vals[u];
+                    atomicOr(&S.mask[i], 1u << c);
+                }
+            }
+            for (int p0 = kGatherRegs; p0 < len; p0 += 4) {
                 int rows[4];
                 T vals[4];
 #pragma unroll
