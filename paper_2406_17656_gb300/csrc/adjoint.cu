@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) adjoint_kernel(LsqArgs ar
             // ---- dL/dA_0(:, j)
             const int64_t zoff = args.zbig ? 0 : (int64_t)(C.roff / args.n) * args.znnz;
             for (int t = C.zb + ll; t < C.ze; t += P) {
-                const int i = find_sorted(S.I, nI, args.zri[t] + C.zro);
+                const int i = C.target_row(args, S, t - C.zb, t);
                 args.dzval[zoff + t] = (i >= 0) ? S.u.s.w[i] + 2.0 * rho * S.u.s.r[i] : 2.0 * rho * args.zcv[t];
             }
         }

@@ -822,9 +822,17 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     if (!d_st) d_st = sc.get<int32_t>((size_t)N);
     if (!d_r2) d_r2 = sc.get<double>((size_t)N);
     uint8_t *lrow = sc.get<uint8_t>((size_t)N * kLCap);
-    if (!ish || !icnt || !bin || !work || !bin_off || !tickets || !d_st || !d_r2 || !lrow) return SAM_ERR_OOM;
+    uint8_t *zloc = sc.get<uint8_t>((size_t)N * kZCap);
+    if (!ish || !icnt || !bin || !work || !bin_off || !tickets || !d_st || !d_r2 || !lrow || !zloc)
+        return SAM_ERR_OOM;
     // shadow rows, size classes, work list
-    if (shadow_and_bins(h, (int)N, kcp, kri, g->jcp, g->jri, ish, icnt, bin, d_st, nullptr, lrow) != cudaSuccess)
+    ShadowTarget tg;
+    tg.zcp = zcp;
+    tg.zri = zri;
+    tg.zbig = NT > 1 ? 1 : 0;
+    tg.n = n;
+    tg.zloc = zloc;
+    if (shadow_and_bins(h, (int)N, kcp, kri, g->jcp, g->jri, ish, icnt, bin, d_st, nullptr, lrow, tg) != cudaSuccess)
         return SAM_ERR_CUDA;
     if (build_work_list(h, (int)N, bin, work, bin_off) != cudaSuccess) return SAM_ERR_CUDA;
     cudaMemsetAsync(d_v, 0, sizeof(double) * (size_t)total_nnz, st);
@@ -854,6 +862,7 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     a.zri = zri;
     a.zcv = zcv;
     a.zbig = NT > 1 ? 1 : 0;
+    a.zloc = zloc;
     a.csr_pos = g->csr_pos;
     a.mval = d_v;
     a.colres = d_r2;
@@ -1042,10 +1051,17 @@ sam_status backward_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr 
     int64_t *dbase = sc.get<int64_t>((size_t)mtot);
     double *dzval = sc.get<double>((size_t)zn), *dak_csc = sc.get<double>((size_t)kn);
     uint8_t *lrow = sc.get<uint8_t>((size_t)N * kLCap);
+    uint8_t *zloc = sc.get<uint8_t>((size_t)N * kZCap);
     if (!ish || !icnt || !bin || !colstat || !nbcnt || !dB_off || !work || !bin_off || !tickets || !dbase || !dzval ||
-        !dak_csc || !lrow)
+        !dak_csc || !lrow || !zloc)
         return SAM_ERR_OOM;
-    if (shadow_and_bins(h, (int)N, kcp, kri, g->jcp, g->jri, ish, icnt, bin, colstat, nbcnt, lrow) != cudaSuccess ||
+    ShadowTarget tg;
+    tg.zcp = zcp;
+    tg.zri = zri;
+    tg.zbig = 1;
+    tg.n = n;
+    tg.zloc = zloc;
+    if (shadow_and_bins(h, (int)N, kcp, kri, g->jcp, g->jri, ish, icnt, bin, colstat, nbcnt, lrow, tg) != cudaSuccess ||
         exclusive_scan_i64(h, nbcnt, dB_off, N) != cudaSuccess ||
         build_work_list(h, (int)N, bin, work, bin_off) != cudaSuccess)
         return SAM_ERR_CUDA;
@@ -1081,6 +1097,7 @@ sam_status backward_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr 
     a.zri = zri;
     a.zcv = zcv;
     a.zbig = 1;
+    a.zloc = zloc;
     a.csr_pos = g->csr_pos;
     a.mval = const_cast<double *>(d_m);
     a.kcv32 = kcv32;
@@ -1367,6 +1384,8 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
     int32_t *d_st = col_status ? col_status : keep.get<int32_t>((size_t)N);
     double *d_r2 = res2 ? res2 : keep.get<double>((size_t)N);
     uint8_t *lrow = keep.get<uint8_t>((size_t)N * kLCap);
+    uint8_t *zloc = keep.get<uint8_t>((size_t)N * kZCap);
+    if (!zloc) return SAM_ERR_OOM;
     float *kcv32 = nullptr, *zcv32 = nullptr;
     if (precision == SAM_FP32_REFINE) {
         kcv32 = keep.get<float>((size_t)kn);
@@ -1403,7 +1422,13 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
     cudaMemcpyAsync(d_koff, koff.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_zoff, zoff.data(), sizeof(int64_t) * (NT + 1), cudaMemcpyHostToDevice, st);
     if (autoref) bin = bin_keep;  // the fallback pass reads the size classes at every replay
-    if (shadow_and_bins(h, (int)N, kcp, kri, g->jcp, g->jri, ish, icnt, bin, d_st, nullptr, lrow) != cudaSuccess ||
+    ShadowTarget tg;
+    tg.zcp = zcp;
+    tg.zri = zri;
+    tg.zbig = NT > 1 ? 1 : 0;
+    tg.n = n;
+    tg.zloc = zloc;
+    if (shadow_and_bins(h, (int)N, kcp, kri, g->jcp, g->jri, ish, icnt, bin, d_st, nullptr, lrow, tg) != cudaSuccess ||
         build_work_list(h, (int)N, bin, work, bin_off) != cudaSuccess ||
         split_map_structure(h, K, n, g->mrp, g->mci, M_row_ptr, M_col_idx) != cudaSuccess)
         return SAM_ERR_CUDA;
@@ -1428,6 +1453,7 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
     a.zri = zri;
     a.zcv = zcv;
     a.zbig = NT > 1 ? 1 : 0;
+    a.zloc = zloc;
     a.csr_pos = g->csr_pos;
     a.mval = M_val;
     a.colres = d_r2;

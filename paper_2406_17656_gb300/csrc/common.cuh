@@ -25,6 +25,8 @@ constexpr int kICap = 64;    // max |I_j| (shadow rows) of one column problem
 constexpr int kJCap = 27;    // max |J_j| (unknowns) of one column problem
 constexpr int kNumBins = 5;  // size classes (see lsq.cu)
 constexpr int kLCap = 512;   // max stored entries of one column's B (8 per shadow row)
+constexpr int kZCap = 32;    // target entries per column with a precomputed local row (zloc)
+constexpr int kZOutside = 255;  // zloc value of a target entry outside the shadow rows
 constexpr int kBinNone = 255;
 
 // Per-column status codes written by the kernels (0 = ok); equal to the
@@ -56,6 +58,9 @@ struct LsqArgs {
     const int32_t *jcp, *jri;    // pattern (CSC, big)
     const int32_t *ish, *icnt;   // shadow rows (padded) and counts
     const uint8_t *lrow;         // local shadow row of every gathered entry (padded [N][kLCap])
+    const uint8_t *zloc;         // local shadow row of the first kZCap entries of each column's target
+                                 // column ([N][kZCap], kZOutside = not a shadow row); the shadow rows
+                                 // (ish) are stored only for columns with more target entries
     const int32_t *zcp, *zri;    // CSC of the target: A_0 (order n, shared by every map; zbig = 0)
                                  // or the block-diagonal of one target per map (order N; zbig = 1)
     const double *zcv;
@@ -136,16 +141,25 @@ cudaError_t csr_to_csc(sam_handle h, int n, int64_t nnz, const int32_t *rp, cons
 sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t *kri, int64_t nnz, int level,
                          int32_t **jcp, int32_t **jri, int64_t *nnz_out);
 
+// The target of a shadow pass: zloc (nullable) receives the local row of
+// every target entry (see LsqArgs::zloc)
+struct ShadowTarget {
+    const int32_t *zcp = nullptr, *zri = nullptr;
+    int zbig = 0, n = 1;
+    uint8_t *zloc = nullptr;
+};
 // Shadow rows (padded), |I_j| and size class of every column.
 // nbcnt (nullable) receives nnz(B_j) = sum of |A(:, c)| over c in J_j;
 // lrow (nullable, padded [N][kLCap]) the local shadow row of every entry of
 // A(:, J_j) in gather order, for the columns that have a size class.
+// With a target (tg.zloc), ish is written only for the columns whose target
+// column has more than kZCap entries.
 cudaError_t shadow_and_bins(sam_handle h, int N, const int32_t *kcp, const int32_t *kri, const int32_t *jcp,
                             const int32_t *jri, int32_t *ish, int32_t *icnt, uint8_t *bin, int32_t *colstat,
-                            int64_t *nbcnt = nullptr, uint8_t *lrow = nullptr);
+                            int64_t *nbcnt = nullptr, uint8_t *lrow = nullptr, ShadowTarget tg = ShadowTarget());
 
-// Work list: columns grouped by size class; bin_off (device, [kNumBins+1]).
-// work list of the columns grouped by size class; ws (nullable): int32[2 kNumBins] workspace
+// Work list: columns grouped by size class; bin_off (device, [kNumBins+1]);
+// ws (nullable): int32[2 kNumBins] workspace
 cudaError_t build_work_list(sam_handle h, int N, const uint8_t *bin, int32_t *work, int32_t *bin_off,
                             int32_t *ws = nullptr);
 // out[j] = bin[j] where colstat[j] == flag, else no size class

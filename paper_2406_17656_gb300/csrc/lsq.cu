@@ -47,7 +47,8 @@ namespace sam {
 namespace {
 
 // blocks per SM that the shared memory of a tile allows (1..4): the
-// register budget is held to the same count
+// register budget is held to the same count, so registers never lower the
+// occupancy that shared memory permits
 template <class TL>
 struct MinBlocks {
     static constexpr int bytes = (int)sizeof(ProbSmem<TL>) * TL::PPW * kWarpsPerBlock + 1024;

@@ -424,8 +424,11 @@ struct Column {
             colB[q] = nB + group_excl_scan<P>(clen[q], ll, &tot);
             nB += tot;
         }
+        // the sorted shadow rows are needed only for target entries beyond
+        // the precomputed local rows
+        const bool need_I = !args.zloc || ze - zb > kZCap;
         for (int i = ll; i < MAXI; i += P) {
-            S.I[i] = (i < nI) ? args.ish[(int64_t)jj * kICap + i] : INT_MAX;
+            if (need_I) S.I[i] = (i < nI) ? args.ish[(int64_t)jj * kICap + i] : INT_MAX;
             S.mask[i] = 0u;
             S.c[i] = 0.0;
         }
@@ -489,7 +492,7 @@ struct Column {
         }
         out2 = 0.0;
         for (int t = zb + ll; t < ze; t += P) {
-            const int i = find_sorted(S.I, nI, args.zri[t] + zro);
+            const int i = target_row(args, S, t - zb, t);
             const double v = args.zcv[t];
             if (i >= 0) {
                 S.c[i] = v;
@@ -500,6 +503,21 @@ struct Column {
         }
         out2 = group_sum<P>(out2);
         __syncwarp();
+    }
+
+    // local shadow row of entry t (offset tz in the column) of the target
+    // column, -1 outside the shadow
+    __device__ __forceinline__ int target_row(const LsqArgs &args, const ProbSmem<TL> &S, int tz, int t) {
+        if (args.zloc && tz < kZCap) {
+            const int z = args.zloc[(int64_t)jj * kZCap + tz];
+            if (z == kZOutside) return -1;
+            if (z >= nI) {  // impossible for a consistent shadow: never index out of bounds
+                status = kStUnsupported;
+                return -1;
+            }
+            return z;
+        }
+        return find_sorted(S.I, nI, args.zri[t] + zro);
     }
 
     __device__ __forceinline__ void load_tile(ProbSmem<TL> &S, T (&a)[RS][CS]) {

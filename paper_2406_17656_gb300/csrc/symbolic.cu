@@ -438,9 +438,32 @@ __device__ int warp_sort_unique(int *buf, int cnt) {
 struct UnionResult {
     int count;  // distinct entries (-1: too many candidates for the fallback)
     int total;  // candidates, i.e. the sum of the list lengths
-    int mode;   // 0: bitmap over [lo, ...] left in shared memory, 1: sorted buffer
+    int mode;   // 0: bitmap over [lo, lo + 32 words) left in shared memory, 1: sorted buffer
     int lo;
+    int words;
 };
+
+// Rank of x among the union left in shared memory by warp_union / union_fast
+// (bitmap with word prefixes wpre, or sorted buffer), -1 when absent.
+__device__ __forceinline__ int union_rank(int x, const UnionResult &r, const unsigned *bm, const unsigned char *wpre) {
+    if (r.count <= 0) return -1;
+    if (r.mode == 0) {
+        const int64_t d = (int64_t)x - r.lo;
+        if (d < 0 || d >= (int64_t)r.words * 32) return -1;
+        const unsigned w = bm[d >> 5], bit = 1u << (d & 31);
+        if (!(w & bit)) return -1;
+        return wpre[d >> 5] + __popc(w & (bit - 1u));
+    }
+    const int *srt = reinterpret_cast<const int *>(bm);
+    int lo = 0, hi = r.count - 1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int v = srt[mid];
+        if (v == x) return mid;
+        if (v < x) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
 
 // Union of the sorted lists X(:, l), l in Y(:, j).  The distinct values are
 // written ascending to out[0..min(count, cap)) when out != nullptr.  Every
@@ -466,11 +489,12 @@ __device__ UnionResult warp_union(int j, const int32_t *xcp, const int32_t *xri,
         hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
         total += __shfl_xor_sync(0xffffffffu, total, o);
     }
-    UnionResult res{0, total, 0, lo};
+    UnionResult res{0, total, 0, lo, 0};
     if (total == 0) return res;
     const int64_t span = (int64_t)hi - lo + 1;
     if (span <= (int64_t)kBitWords * 32) {
         const int words = (int)((span + 31) >> 5);
+        res.words = words;
         for (int w = lane; w < words; w += 32) bm[w] = 0u;
         __syncwarp();
         for (int t = yb + lane; t < ye; t += 32) {
@@ -650,7 +674,7 @@ __device__ bool union_fast(int j, const int32_t *kcp, const int32_t *kri, const 
         hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
     if (total == 0) {
-        r = UnionResult{0, 0, 0, lo};
+        r = UnionResult{0, 0, 0, lo, 0};
         if (SHADOW) bsz = size_class(0, nj, 0);
         return true;
     }
@@ -708,7 +732,7 @@ __device__ bool union_fast(int j, const int32_t *kcp, const int32_t *kri, const 
         for (int w = lane; w < (total + 3) / 4; w += 32) dst[w] = src[w];
     }
     __syncwarp();
-    r = UnionResult{count, total, 0, lo};
+    r = UnionResult{count, total, 0, lo, words};
     return true;
 }
 
@@ -746,7 +770,8 @@ int merge_grid(sam_handle h, int n) {
 __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const int32_t *kcp, const int32_t *kri,
                                                                   const int32_t *jcp, const int32_t *jri,
                                                                   int32_t *ish, int32_t *icnt, uint8_t *bin,
-                                                                  int32_t *colstat, int64_t *nbcnt, uint8_t *lrow) {
+                                                                  int32_t *colstat, int64_t *nbcnt, uint8_t *lrow,
+                                                                  ShadowTarget tg) {
     __shared__ unsigned bms[kMergeWarps][kBitWords];
     __shared__ unsigned char pres[kMergeWarps][kBitWords];
     __shared__ __align__(16) unsigned char stg[kMergeWarps][kLCap];
@@ -756,11 +781,23 @@ __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const i
     unsigned char *stage = stg[warp];
     for (int64_t j = (int64_t)blockIdx.x * kMergeWarps + warp; j < n; j += (int64_t)gridDim.x * kMergeWarps) {
         const int nj = jcp[j + 1] - jcp[j];
+        // the target column of this map column: local rows go to zloc; the
+        // sorted shadow rows themselves are only stored when some target
+        // entries lie beyond zloc's capacity (or no target is given)
+        int zb = 0, zlen = 0, zro = 0;
+        if (tg.zloc) {
+            const int kmap = (int)(j / tg.n);
+            const int zc = tg.zbig ? (int)j : (int)(j - (int64_t)kmap * tg.n);
+            zro = tg.zbig ? 0 : kmap * tg.n;
+            zb = tg.zcp[zc];
+            zlen = tg.zcp[zc + 1] - zb;
+        }
+        int32_t *ish_j = (!tg.zloc || zlen > kZCap) ? ish + j * kICap : nullptr;
         UnionResult r;
         int b = kBinNone;
-        if (!union_fast<true>((int)j, kcp, kri, jcp, jri, bm, wpre, stage, ish + j * kICap, kICap,
+        if (!union_fast<true>((int)j, kcp, kri, jcp, jri, bm, wpre, stage, ish_j, kICap,
                               lrow ? lrow + j * kLCap : nullptr, r, b)) {
-            r = warp_union((int)j, kcp, kri, jcp, jri, bm, ish + j * kICap, kICap, wpre);
+            r = warp_union((int)j, kcp, kri, jcp, jri, bm, ish_j, kICap, wpre);
             b = size_class(r.count, nj, r.total);
             // local shadow row of every entry of A(:, J_j), in gather order (the
             // columns of J_j in order, each in CSC order): its rank in I_j,
@@ -810,6 +847,14 @@ __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const i
             }
             __syncwarp();
         }
+        if (tg.zloc && b != kBinNone) {
+            uint8_t *zl = tg.zloc + j * kZCap;
+            for (int t = lane; t < zlen && t < kZCap; t += 32) {
+                const int rk = union_rank(tg.zri[zb + t] + zro, r, bm, wpre);
+                zl[t] = (uint8_t)(rk < 0 ? kZOutside : rk);
+            }
+        }
+        __syncwarp();
         if (lane == 0) {
             const int u = r.count;
             icnt[j] = u;
@@ -921,9 +966,9 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
 
 cudaError_t shadow_and_bins(sam_handle h, int N, const int32_t *kcp, const int32_t *kri, const int32_t *jcp,
                             const int32_t *jri, int32_t *ish, int32_t *icnt, uint8_t *bin, int32_t *colstat,
-                            int64_t *nbcnt, uint8_t *lrow) {
+                            int64_t *nbcnt, uint8_t *lrow, ShadowTarget tg) {
     shadow_kernel<<<merge_grid(h, N), kMergeWarps * 32, 0, handle_stream(h)>>>(N, kcp, kri, jcp, jri, ish, icnt, bin,
-                                                                              colstat, nbcnt, lrow);
+                                                                              colstat, nbcnt, lrow, tg);
     count_launch(h);
     return cudaGetLastError();
 }

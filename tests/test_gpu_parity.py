@@ -368,3 +368,24 @@ def test_trusted_inputs_give_the_same_maps(sam):
             h.close()
     for a, b in zip(*outs):
         assert torch.equal(a, b)
+
+
+def test_dense_target_columns_use_the_shadow_row_search(sam, handle):
+    """Target columns with more stored entries than the precomputed local-row
+    capacity (32), inside and outside the shadow rows, against the oracle."""
+    seq = W.config2(nx=24, nmat=2)
+    a0, a1 = seq.mats
+    d = a0.dense()
+    rng = np.random.default_rng(12)
+    for j in rng.choice(a0.n, 12, replace=False):
+        rows = rng.choice(a0.n, 45, replace=False)
+        d[rows, j] += rng.uniform(-0.5, 0.5, 45)
+    A0 = W.CSR.from_dense(d)
+    assert np.diff(A0.to_scipy().tocsc().indptr).max() > 32
+    for precision in ("fp64", "fp32r"):
+        ref = oracle_map(a1, A0, 2)
+        S = handle.sam_pattern_build(dev(sam, a1), 2)
+        r2 = __import__("torch").empty(a1.n, dtype=__import__("torch").float64, device="cuda")
+        ip, ix, dv = handle.sam_build(dev(sam, a1), dev(sam, A0), S, precision, refine_steps=1, res2=r2)
+        assert rel_fro(dv.cpu().numpy(), ref["dv"]) <= TOL[precision]
+        assert abs(r2.cpu().numpy().sum() - ref["res2"].sum()) <= 1e-10 * ref["res2"].sum()
