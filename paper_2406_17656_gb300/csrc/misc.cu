@@ -290,7 +290,7 @@ cudaError_t gather_values(sam_handle h, int64_t tot, int K, const int64_t *off, 
                           const int32_t *perm, double *v, float *v32) {
     if (tot == 0) return cudaSuccess;
     int64_t blocks = (tot + 255) / 256;
-    if (blocks > (int64_t)handle_sms(h) * 16) blocks = (int64_t)handle_sms(h) * 16;
+    if (blocks > (int64_t)handle_sms(h) * 8) blocks = (int64_t)handle_sms(h) * 8;  // one resident wave
     gather_values_kernel<<<(unsigned)blocks, 256, 0, handle_stream(h)>>>(tot, K, off, vals, perm, v, v32);
     count_launch(h);
     return cudaGetLastError();
@@ -321,7 +321,7 @@ cudaError_t residual_rows(sam_handle h, int n, const int32_t *krp, const int32_t
 cudaError_t round_to_f32(sam_handle h, int64_t n, const double *in, float *out) {
     if (n == 0) return cudaSuccess;
     int64_t blocks = (n + 255) / 256;
-    if (blocks > (int64_t)handle_sms(h) * 16) blocks = (int64_t)handle_sms(h) * 16;
+    if (blocks > (int64_t)handle_sms(h) * 8) blocks = (int64_t)handle_sms(h) * 8;  // one resident wave
     round_f32_kernel<<<(unsigned)blocks, 256, 0, handle_stream(h)>>>(n, in, out);
     count_launch(h);
     return cudaGetLastError();

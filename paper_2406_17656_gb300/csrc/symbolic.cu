@@ -760,9 +760,18 @@ __global__ void __launch_bounds__(kMergeWarps * 32) product_pattern_kernel(
     }
 }
 
-int merge_grid(sam_handle h, int n) {
-    int blocks = (n + kMergeWarps - 1) / kMergeWarps;
-    int cap = handle_sms(h) * 12;
+// One resident wave of a grid-stride union kernel: blocks beyond what the
+// SMs hold at once would run as a second wave with the same per-block work.
+template <typename Kernel>
+int merge_grid(sam_handle h, int n, Kernel kernel) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kMergeWarps * 32, 0) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const int blocks = (n + kMergeWarps - 1) / kMergeWarps;
+    const int cap = handle_sms(h) * per_sm;
     return blocks < cap ? (blocks > 0 ? blocks : 1) : cap;
 }
 
@@ -929,7 +938,7 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
     for (int lv = 2; lv <= level; ++lv) {
         int32_t *nxcp = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)N + 1));
         if (!nxcp) return SAM_ERR_OOM;
-        product_pattern_kernel<<<merge_grid(h, N), kMergeWarps * 32, 0, st>>>(N, l1cp, l1ri, curcp, curri, 0, cnt,
+        product_pattern_kernel<<<merge_grid(h, N, product_pattern_kernel), kMergeWarps * 32, 0, st>>>(N, l1cp, l1ri, curcp, curri, 0, cnt,
                                                                               nullptr, nullptr, flag);
         count_launch(h);
         if (exclusive_scan_i32(h, cnt, nxcp, N) != cudaSuccess) return SAM_ERR_CUDA;
@@ -939,7 +948,7 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
             return SAM_ERR_CUDA;
         int32_t *nxri = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)tot + 1));
         if (!nxri) return SAM_ERR_OOM;
-        product_pattern_kernel<<<merge_grid(h, N), kMergeWarps * 32, 0, st>>>(N, l1cp, l1ri, curcp, curri, 1, nullptr,
+        product_pattern_kernel<<<merge_grid(h, N, product_pattern_kernel), kMergeWarps * 32, 0, st>>>(N, l1cp, l1ri, curcp, curri, 1, nullptr,
                                                                               nxcp, nxri, flag);
         count_launch(h);
         if (curcp != l1cp) {
@@ -967,7 +976,7 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
 cudaError_t shadow_and_bins(sam_handle h, int N, const int32_t *kcp, const int32_t *kri, const int32_t *jcp,
                             const int32_t *jri, int32_t *ish, int32_t *icnt, uint8_t *bin, int32_t *colstat,
                             int64_t *nbcnt, uint8_t *lrow, ShadowTarget tg) {
-    shadow_kernel<<<merge_grid(h, N), kMergeWarps * 32, 0, handle_stream(h)>>>(N, kcp, kri, jcp, jri, ish, icnt, bin,
+    shadow_kernel<<<merge_grid(h, N, shadow_kernel), kMergeWarps * 32, 0, handle_stream(h)>>>(N, kcp, kri, jcp, jri, ish, icnt, bin,
                                                                               colstat, nbcnt, lrow, tg);
     count_launch(h);
     return cudaGetLastError();
