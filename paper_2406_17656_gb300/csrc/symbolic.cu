@@ -652,14 +652,19 @@ __device__ bool union_fast(int j, const int32_t *kcp, const int32_t *kri, const 
     if (mx > kRegRows) return false;
     int v[kRegRows];
 #pragma unroll
-    for (int u = 0; u < kRegRows; ++u) v[u] = (u < len) ? __ldg(kri + cb + u) : 0;
+    for (int u = 0; u < kRegRows; ++u) {
+        if (u >= mx) break;  // warp-uniform: no predicated-off tail iterations
+        v[u] = (u < len) ? __ldg(kri + cb + u) : 0;
+    }
     int lo = INT_MAX, hi = INT_MIN;
 #pragma unroll
-    for (int u = 0; u < kRegRows; ++u)
+    for (int u = 0; u < kRegRows; ++u) {
+        if (u >= mx) break;
         if (u < len) {
             lo = min(lo, v[u]);
             hi = max(hi, v[u]);
         }
+    }
     int incl = len;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -684,11 +689,13 @@ __device__ bool union_fast(int j, const int32_t *kcp, const int32_t *kri, const 
     for (int w = lane; w < words; w += 32) bm[w] = 0u;
     __syncwarp();
 #pragma unroll
-    for (int u = 0; u < kRegRows; ++u)
+    for (int u = 0; u < kRegRows; ++u) {
+        if (u >= mx) break;
         if (u < len) {
             const int x = v[u] - lo;
             atomicOr(&bm[x >> 5], 1u << (x & 31));
         }
+    }
     __syncwarp();
     const int wpl = (words + 31) >> 5;
     const int w0 = lane * wpl, w1 = min(words, w0 + wpl);
@@ -721,11 +728,13 @@ __device__ bool union_fast(int j, const int32_t *kcp, const int32_t *kri, const 
     if (SHADOW && lrow_j && bsz != kBinNone) {
         // rank of every entry among the shadow rows, in gather order
 #pragma unroll
-        for (int u = 0; u < kRegRows; ++u)
+        for (int u = 0; u < kRegRows; ++u) {
+            if (u >= mx) break;
             if (u < len) {
                 const int d = v[u] - lo;
                 stage[off + u] = (unsigned char)(wpre[d >> 5] + __popc(bm[d >> 5] & ((1u << (d & 31)) - 1u)));
             }
+        }
         __syncwarp();
         const unsigned *src = reinterpret_cast<const unsigned *>(stage);
         unsigned *dst = reinterpret_cast<unsigned *>(lrow_j);
@@ -736,28 +745,54 @@ __device__ bool union_fast(int j, const int32_t *kcp, const int32_t *kri, const 
     return true;
 }
 
-// mode 0: count distinct rows -> cnt[j]; mode 1: write them to out + optr[j]
+// Distinct rows of the union of X(:, l), l in Y(:, j): cnt[j] receives their
+// number and, with out != nullptr, they are written ascending to
+// out + ooff[j] (ooff: room for every candidate of column j).
 __global__ void __launch_bounds__(kMergeWarps * 32) product_pattern_kernel(
-    int n, const int32_t *xcp, const int32_t *xri, const int32_t *ycp, const int32_t *yri, int mode,
-    int32_t *cnt, const int32_t *optr, int32_t *out, int32_t *flag) {
+    int n, const int32_t *xcp, const int32_t *xri, const int32_t *ycp, const int32_t *yri, int32_t *cnt,
+    const int64_t *ooff, int32_t *out, int32_t *flag) {
     __shared__ unsigned bms[kMergeWarps][kBitWords];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned *bm = bms[warp];
     for (int64_t j = (int64_t)blockIdx.x * kMergeWarps + warp; j < n; j += (int64_t)gridDim.x * kMergeWarps) {
-        int32_t *dst = (mode == 1) ? out + optr[j] : nullptr;
+        int32_t *dst = out ? out + ooff[j] : nullptr;
         UnionResult r;
         int unused = 0;
         if (!union_fast<false>((int)j, xcp, xri, ycp, yri, bm, nullptr, nullptr, dst, INT_MAX, nullptr, r, unused))
             r = warp_union((int)j, xcp, xri, ycp, yri, bm, dst, INT_MAX);
         if (lane == 0) {
             if (r.count < 0) {
-                if (mode == 0) cnt[j] = 0;
+                cnt[j] = 0;
                 atomicCAS(flag, 0, SAM_ERR_UNSUPPORTED);
-            } else if (mode == 0) {
+            } else {
                 cnt[j] = r.count;
             }
         }
     }
+}
+
+// candidates of column j: sum of |X(:, l)| over l in Y(:, j)
+__global__ void candidate_count_kernel(int n, const int32_t *xcp, const int32_t *ycp, const int32_t *yri,
+                                       int64_t *cand) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int64_t c = 0;
+    for (int t = ycp[j]; t < ycp[j + 1]; ++t) {
+        const int l = yri[t];
+        c += xcp[l + 1] - xcp[l];
+    }
+    cand[j] = c;
+}
+
+// column j of the union result: from its padded slot to its final place
+__global__ void compact_columns_kernel(int n, const int64_t *ooff, const int32_t *pad, const int32_t *cp,
+                                       int32_t *ri) {
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int sub = threadIdx.x & 7;
+    if (j >= n) return;
+    const int32_t *src = pad + ooff[j];
+    const int b = cp[j], len = cp[j + 1] - b;
+    for (int t = sub; t < len; t += 8) ri[b + t] = src[t];
 }
 
 // One resident wave of a grid-stride union kernel: blocks beyond what the
@@ -936,10 +971,23 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
     count_launch(h);
     int32_t *curcp = l1cp, *curri = l1ri;
     for (int lv = 2; lv <= level; ++lv) {
+        // one union pass: rows go to a slot per column sized by its candidate
+        // count, then are compacted once the counts are known
         int32_t *nxcp = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)N + 1));
-        if (!nxcp) return SAM_ERR_OOM;
-        product_pattern_kernel<<<merge_grid(h, N, product_pattern_kernel), kMergeWarps * 32, 0, st>>>(N, l1cp, l1ri, curcp, curri, 0, cnt,
-                                                                              nullptr, nullptr, flag);
+        int64_t *cand = (int64_t *)pool_alloc(h, sizeof(int64_t) * ((size_t)N + 1));
+        int64_t *coff = (int64_t *)pool_alloc(h, sizeof(int64_t) * ((size_t)N + 1));
+        if (!nxcp || !cand || !coff) return SAM_ERR_OOM;
+        candidate_count_kernel<<<blocks, 256, 0, st>>>(N, l1cp, curcp, curri, cand);
+        count_launch(h);
+        if (exclusive_scan_i64(h, cand, coff, N) != cudaSuccess) return SAM_ERR_CUDA;
+        int64_t ctot = 0;
+        if (cudaMemcpyAsync(&ctot, coff + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return SAM_ERR_CUDA;
+        int32_t *pad = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)ctot + 1));
+        if (!pad) return SAM_ERR_OOM;
+        product_pattern_kernel<<<merge_grid(h, N, product_pattern_kernel), kMergeWarps * 32, 0, st>>>(
+            N, l1cp, l1ri, curcp, curri, cnt, coff, pad, flag);
         count_launch(h);
         if (exclusive_scan_i32(h, cnt, nxcp, N) != cudaSuccess) return SAM_ERR_CUDA;
         int32_t tot = 0;
@@ -948,9 +996,12 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
             return SAM_ERR_CUDA;
         int32_t *nxri = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)tot + 1));
         if (!nxri) return SAM_ERR_OOM;
-        product_pattern_kernel<<<merge_grid(h, N, product_pattern_kernel), kMergeWarps * 32, 0, st>>>(N, l1cp, l1ri, curcp, curri, 1, nullptr,
-                                                                              nxcp, nxri, flag);
+        const int64_t cthreads = (int64_t)N * 8;
+        compact_columns_kernel<<<(unsigned)((cthreads + 255) / 256), 256, 0, st>>>(N, coff, pad, nxcp, nxri);
         count_launch(h);
+        pool_free(h, pad);
+        pool_free(h, cand);
+        pool_free(h, coff);
         if (curcp != l1cp) {
             pool_free(h, curcp);
             pool_free(h, curri);
