@@ -162,8 +162,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
                     const int i = ll + q * P;
                     if (i < nI) {
                         float v = 0.f;
-                        const int pe = S.u.s.rowstart[i + 1];
-                        for (int p = S.u.s.rowstart[i]; p < pe; ++p)
+                        const int pb = S.u.s.rowstart[i], pe = S.u.s.rowstart[i + 1];
+                        float bv[kRowRegs];
+#pragma unroll
+                        for (int u = 0; u < kRowRegs; ++u) bv[u] = (pb + u < pe) ? args.kcv32[S.u.s.rowent[pb + u]] : 0.f;
+#pragma unroll
+                        for (int u = 0; u < kRowRegs; ++u)
+                            if (pb + u < pe) v = fmaf(bv[u], (float)S.u.s.y[S.u.s.rowcol[pb + u]], v);
+                        for (int p = pb + kRowRegs; p < pe; ++p)
                             v = fmaf(args.kcv32[S.u.s.rowent[p]], (float)S.u.s.y[S.u.s.rowcol[p]], v);
                         const double rfi = S.u.s.r[i] - to_f64<float>(v);
                         rf2 = fma(rfi, rfi, rf2);

@@ -16,6 +16,7 @@ namespace {
 
 constexpr int kWarpsPerBlock = 4;
 constexpr int kGatherRegs = 12;  // entries per source column gathered with one round of loads
+constexpr int kRowRegs = 8;      // entries per row of B loaded with one round in the residual passes
 
 template <int RG_, int CG_, int RS_, int CS_, typename T_, int MAXI_BIN_>
 struct Tile {
@@ -319,8 +320,15 @@ __device__ __forceinline__ double residual_rows(ProbSmem<TL> &S, const double *k
         const int i = ll + q * TL::P;
         if (i < nI) {
             double ri = S.c[i];
-            const int pe = S.u.s.rowstart[i + 1];
-            for (int p = S.u.s.rowstart[i]; p < pe; ++p) ri = fma(-kcv[S.u.s.rowent[p]], S.m[S.u.s.rowcol[p]], ri);
+            const int pb = S.u.s.rowstart[i], pe = S.u.s.rowstart[i + 1];
+            // the row's first kRowRegs entries: all loads issued before use
+            double bv[kRowRegs];
+#pragma unroll
+            for (int u = 0; u < kRowRegs; ++u) bv[u] = (pb + u < pe) ? kcv[S.u.s.rowent[pb + u]] : 0.0;
+#pragma unroll
+            for (int u = 0; u < kRowRegs; ++u)
+                if (pb + u < pe) ri = fma(-bv[u], S.m[S.u.s.rowcol[pb + u]], ri);
+            for (int p = pb + kRowRegs; p < pe; ++p) ri = fma(-kcv[S.u.s.rowent[p]], S.m[S.u.s.rowcol[p]], ri);
             S.u.s.r[i] = ri;
             if (SQUARES) r2 = fma(ri, ri, r2);
         }
@@ -614,7 +622,14 @@ struct Column {
     // (B^T v)_c in FP64 for the lane's own columns; v indexed by local row
     __device__ __forceinline__ double bt_times(const LsqArgs &args, ProbSmem<TL> &S, const double *v, int q) {
         double acc = 0.0;
-        for (int p = 0; p < clen[q]; ++p) acc = fma(args.kcv[colA[q] + p], v[S.locr[colB[q] + p]], acc);
+        const int len = clen[q];
+        double bv[kGatherRegs];
+#pragma unroll
+        for (int u = 0; u < kGatherRegs; ++u) bv[u] = (u < len) ? args.kcv[colA[q] + u] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kGatherRegs; ++u)
+            if (u < len) acc = fma(bv[u], v[S.locr[colB[q] + u]], acc);
+        for (int p = kGatherRegs; p < len; ++p) acc = fma(args.kcv[colA[q] + p], v[S.locr[colB[q] + p]], acc);
         return acc;
     }
 };
