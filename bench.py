@@ -404,6 +404,31 @@ def main():
         extra["graph_replay_launches"] = plan.launches()
         plan.destroy()
 
+    # ---- adjoint of the same batched build (dL/dM random, residual term on)
+    if not args.quick:
+        pats = h.sam_pattern_build_batched(aks, args.level)
+        offs_a, _, _, mv, _ = h.sam_build_batched(aks, a0, pats, "fp32r", args.refine)
+        gbar = torch.randn(mv.numel(), dtype=torch.float64, device=dev,
+                           generator=torch.Generator(device=dev).manual_seed(3))
+        targets = [a0] * K
+        for _ in range(2):
+            h.sam_build_backward_batched(aks, targets, pats, mv, gbar, "fp32r", args.refine, 1.0, offsets=offs_a)
+        torch.cuda.synchronize()
+        ta = 0.0
+        na = 3
+        for _ in range(na):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.sam_build_backward_batched(aks, targets, pats, mv, gbar, "fp32r", args.refine, 1.0, offsets=offs_a)
+            e1.record(stream)
+            e1.synchronize()
+            ta += e0.elapsed_time(e1)
+        ta = max_over_ranks(ta / na, world, dev)
+        extra["adjoint_columns_per_s"] = job_value(cols_per_step, world, ta)
+        extra["adjoint_ms"] = ta
+        for p in pats:
+            p.destroy()
+
     # ---- roofline of the dominant kernel (largest least-squares size class)
     sizes = column_sizes(seq.mats, args.level)
     dom = int(np.argmax(lsq_ms))
