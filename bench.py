@@ -134,6 +134,14 @@ def algorithmic_flops(I, J, nB, precision, steps):
     return f32, f64
 
 
+def measured_hbm_gbs() -> float:
+    """Measured copy bandwidth of the GB300s, else the fallback figure."""
+    try:
+        return float(json.load(open(os.path.join(HERE, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
 def kernel_hash() -> str:
     """sha256 over the sources of the least-squares kernel (a recorded ncu
     traffic figure is only reported while these are unchanged)."""
@@ -160,7 +168,7 @@ class ClockSampler:
             self.path = "/tmp/sam_clocks_%d.csv" % os.getpid()
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -432,19 +440,27 @@ def main():
     # ---- roofline of the dominant kernel (largest least-squares size class)
     sizes = column_sizes(seq.mats, args.level)
     dom = int(np.argmax(lsq_ms))
-    f32 = f64 = 0.0
+    f32 = f64 = gathered = 0.0
     for (I, J, nB) in sizes:
         sel = bin_of(I, J, nB) == dom
         a, b = algorithmic_flops(I[sel], J[sel], nB[sel], "fp32r", args.refine)
         f32 += float(np.sum(a))
         f64 += float(np.sum(b))
+        # gathered bytes: every entry of B_j (FP64 value + int32 row) once per column
+        gathered += 12.0 * float(np.sum(nB[sel]))
     t_launch = lsq_ms[dom] / max(lsq_n[dom], 1) * 1e-3
     nsteps_prof = args.steps
     f32_l, f64_l = f32, f64  # per launch: one launch per size class covers all maps of a step
-    t_roof = max(f32_l / PEAK_FP32, f64_l / PEAK_FP64)
+    hbm_gbs = measured_hbm_gbs()
+    t_hbm = gathered / (hbm_gbs * 1e9)
+    t_roof = max(f32_l / PEAK_FP32, f64_l / PEAK_FP64, t_hbm)
     fp32_frac = f32_l / t_launch / PEAK_FP32
     fp64_frac = f64_l / t_launch / PEAK_FP64
-    if f32_l / PEAK_FP32 >= f64_l / PEAK_FP64:
+    bound, unit = "alu", "TFLOP/s"
+    if t_hbm >= max(f32_l / PEAK_FP32, f64_l / PEAK_FP64):
+        bound, unit = "hbm", "GB/s"
+        ach, peak = gathered / t_launch / 1e-3, hbm_gbs * 1e9 / 1e-3  # scaled by 1e12 below -> GB/s
+    elif f32_l / PEAK_FP32 >= f64_l / PEAK_FP64:
         ach, peak = f32_l / t_launch, PEAK_FP32
     else:
         ach, peak = f64_l / t_launch, PEAK_FP64
@@ -462,11 +478,12 @@ def main():
                 traffic = rec["bytes_per_column"][str(dom)] * ncols
         except Exception:
             traffic = None
-    roofline = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+    roofline = {"bound": bound, "achieved": ach / 1e12, "peak": peak / 1e12, "unit": unit,
                 "frac": t_roof / t_launch, "traffic": traffic,
                 "kernel": "lsq_kernel size class %d (|I|<=%d, |J|<=%d)" % (dom, BIN_MAXI[dom], BIN_MAXJ[dom]),
                 "launch_ms": t_launch * 1e3, "fp32_flops_per_launch": f32_l, "fp64_flops_per_launch": f64_l,
                 "fp32_frac": fp32_frac, "fp64_frac": fp64_frac,
+                "gathered_bytes_per_launch": gathered, "t_hbm_ms": t_hbm * 1e3, "hbm_gbs_measured": hbm_gbs,
                 "peak_source": "nominal: 152 SMs x 2070 MHz; FP32 128 lanes x 2, FP64 1.25 TFLOP/s (2 FMA/SM/clk)"}
     if not args.quick:
         p32, p64 = h.sam_peak_flops(100.0)
@@ -534,7 +551,8 @@ def main():
                            "columns_per_step": cols_per_step, "tile_variants": variants, "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed between steps (256 MiB write outside the timed interval)"},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-                "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks, "cpu_baseline": cpu}
+                "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks, "cpu_baseline": cpu,
+                "maps_per_s": job_value(K, world, ms)}
         line.update(extra)
         print(json.dumps(line), flush=True)
     h.close()
