@@ -65,6 +65,7 @@ def _load():
                                        _f64p, _f64p, ctypes.c_double, _f64p, _f64p, _f64p]
             lib.so_residual.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p,
                                         _i32p, _i32p, _f64p, _f64p, _f64p]
+            lib.so_sparsify.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, ctypes.c_int, ctypes.c_double, _i32p]
             _lib = lib
     return _lib
 
@@ -209,3 +210,26 @@ def apply(indptr, indices, data, x):
 
     n = len(indptr) - 1
     return sp.csr_matrix((data, indices, indptr), shape=(n, n)) @ np.asarray(x, np.float64)
+
+
+SPARSIFY_MODES = {"global": 0, "tau": 1, "lfil": 2}
+
+
+def sparsify(A, mode: str, param: float):
+    """Sparsified A~ of Sec. 4 (mode "global" thresh, "tau" column threshold,
+    "lfil" entries per column; readings in sam_oracle.c).  Returns a CSR
+    triple (indptr, indices, data) of the kept entries, rows ascending."""
+    lib = _load()
+    n = int(A.n)
+    rp, rpp = _i32(A.indptr)
+    ci, cip = _i32(A.indices)
+    v, vp = _f64(A.data)
+    keep = np.zeros(max(len(ci), 1), dtype=np.int32)
+    _check(lib.so_sparsify(n, rpp, cip, vp, int(SPARSIFY_MODES[mode]), ctypes.c_double(float(param)),
+                           keep.ctypes.data_as(_i32p)), "sparsify")
+    keep = keep[: len(ci)].astype(bool)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    kept_rows = rows[keep]
+    indptr = np.zeros(n + 1, dtype=np.int32)
+    np.add.at(indptr, kept_rows + 1, 1)
+    return np.cumsum(indptr).astype(np.int32), ci[keep].copy(), v[keep].copy()

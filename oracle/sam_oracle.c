@@ -18,6 +18,9 @@
  *     enter the residual only.
  *   - Eq. (res): R_k = A_k N_k - A_0 and the relative residual
  *     ||R_k||_F / ||A_0||_F used in Sec. 5.
+ *   - Sec. 4: the three sparsifications of A_k whose level-L patterns the
+ *     paper compares (global threshold on the diagonally scaled matrix,
+ *     column threshold tau, fixed count lfil per column).
  *
  * Each least-squares problem is solved with textbook Householder QR
  * (Golub & Van Loan, Matrix Computations, Sec. 5.1.2 "house" and Sec. 5.2.1
@@ -585,4 +588,79 @@ int so_adjoint(int n, const int *krp, const int *kci, const double *kv,
     free(kcp); free(kcr); free(kcv); free(zcp); free(zcr); free(zcv);
     free(kperm); free(zperm); free(fill); free(dk); free(dz); free(icp); free(iri);
     return status;
+}
+
+/*
+ * Sec. 4 sparsifications of A (CSR): keep[e] = 1 for every stored entry e
+ * that the sparsified matrix keeps, 0 otherwise.  The diagonal is always
+ * kept.  Readings of the printed formulas:
+ *   mode 0, global threshold `param`: keep (i, j) when
+ *           |A_ij| / sqrt(D_ii D_jj) > param, with D_ii = |A_ii| when that is
+ *           stored and nonzero, else 1 (the printed D^{1/2} A D^{1/2} read as
+ *           the usual symmetric scaling D^{-1/2} A D^{-1/2});
+ *   mode 1, column threshold tau = `param` in [0, 1]: keep (i, j) when
+ *           |A_ij| > (1 - tau) max_i |A_ij|, the maximum over the stored
+ *           entries of column j, as printed;
+ *   mode 2, lfil = (int)`param` >= 0: keep the lfil entries of column j of
+ *           largest |A_ij| (equal magnitudes: the lower row index first).
+ * Plain loops over the columns of the transpose.
+ */
+int so_sparsify(int n, const int *rp, const int *ci, const double *v, int mode, double param, int *keep) {
+    if (n < 0 || !rp || !keep || (rp[n] > 0 && (!ci || !v))) return 2;
+    if (mode < 0 || mode > 2) return 2;
+    const int nnz = rp[n];
+    for (int e = 0; e < nnz; ++e) keep[e] = 0;
+    if (mode == 0) {
+        double *d = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        if (!d) return 1;
+        for (int i = 0; i < n; ++i) {
+            d[i] = 1.0;
+            for (int e = rp[i]; e < rp[i + 1]; ++e)
+                if (ci[e] == i && fabs(v[e]) > 0.0) d[i] = fabs(v[e]);
+        }
+        for (int i = 0; i < n; ++i)
+            for (int e = rp[i]; e < rp[i + 1]; ++e) {
+                const int j = ci[e];
+                keep[e] = (i == j) || (fabs(v[e]) / sqrt(d[i] * d[j]) > param);
+            }
+        free(d);
+        return 0;
+    }
+    /* column criteria: walk the columns through the transpose, remembering
+     * where each CSC entry sits in the CSR arrays */
+    int *tp = NULL, *ti = NULL;
+    double *tv = NULL;
+    if (transpose(n, rp, ci, v, &tp, &ti, &tv)) return 1;
+    int *pos = (int *)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+    int *fill = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    if (!pos || !fill) {
+        free(tp); free(ti); free(tv); free(pos); free(fill);
+        return 1;
+    }
+    for (int j = 0; j < n; ++j) fill[j] = tp[j];
+    for (int i = 0; i < n; ++i)
+        for (int e = rp[i]; e < rp[i + 1]; ++e) pos[fill[ci[e]]++] = e;
+    for (int j = 0; j < n; ++j) {
+        const int b = tp[j], en = tp[j + 1];
+        if (mode == 1) {
+            double mx = 0.0;
+            for (int p = b; p < en; ++p) mx = fabs(tv[p]) > mx ? fabs(tv[p]) : mx;
+            for (int p = b; p < en; ++p) keep[pos[p]] = (ti[p] == j) || (fabs(tv[p]) > (1.0 - param) * mx);
+        } else {
+            const int lfil = (int)param;
+            for (int p = b; p < en; ++p) {
+                /* rank = entries of the column that come before p in the
+                 * order (larger magnitude, then lower row) */
+                int rank = 0;
+                for (int q = b; q < en; ++q) {
+                    if (q == p) continue;
+                    const double aq = fabs(tv[q]), ap = fabs(tv[p]);
+                    if (aq > ap || (aq == ap && ti[q] < ti[p])) ++rank;
+                }
+                keep[pos[p]] = (ti[p] == j) || (rank < lfil);
+            }
+        }
+    }
+    free(tp); free(ti); free(tv); free(pos); free(fill);
+    return 0;
 }

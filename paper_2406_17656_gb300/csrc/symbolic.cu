@@ -970,6 +970,7 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
     level01_fill<<<blocks, 256, 0, st>>>(N, kcp, kri, lv1, l1cp, l1ri);
     count_launch(h);
     int32_t *curcp = l1cp, *curri = l1ri;
+    int32_t tot = -1;  // entries of the current pattern, once read back
     for (int lv = 2; lv <= level; ++lv) {
         // one union pass: rows go to a slot per column sized by its candidate
         // count, then are compacted once the counts are known
@@ -990,7 +991,6 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
             N, l1cp, l1ri, curcp, curri, cnt, coff, pad, flag);
         count_launch(h);
         if (exclusive_scan_i32(h, cnt, nxcp, N) != cudaSuccess) return SAM_ERR_CUDA;
-        int32_t tot = 0;
         if (cudaMemcpyAsync(&tot, nxcp + N, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return SAM_ERR_CUDA;
@@ -1009,9 +1009,8 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
         curcp = nxcp;
         curri = nxri;
     }
-    int32_t tot = 0;
-    if (cudaMemcpyAsync(&tot, curcp + N, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
+    if (tot < 0 && (cudaMemcpyAsync(&tot, curcp + N, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess))
         return SAM_ERR_CUDA;
     if (curcp != l1cp) {
         pool_free(h, l1cp);

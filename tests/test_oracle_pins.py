@@ -308,3 +308,77 @@ def test_apply_is_the_sparse_product():
     y = oracle.apply(ip, ix, dv, x)
     m = _map_dense(a.n, cp, ri, out["mval"])
     assert np.allclose(y, m @ x, rtol=1e-14, atol=1e-14)
+
+
+# ------------------------------------------------------- sparsification
+
+
+@pytest.mark.parametrize("line", _golden_rows("cd2d_sparsified_nnz.txt"))
+def test_sparsified_pattern_counts_printed_in_paper(line):
+    """Sec. 4 sparsifications of the 5-point stencil (off-diagonal |A_ij| = 1/4
+    of the diagonal: inside 1 - 0.8 of the column maximum, outside 1 - 0.7),
+    then the printed power of the pattern."""
+    side, mode, param, power, nnz = line.split()
+    a = W.poisson5(int(side))
+    ip, ix, dv = oracle.sparsify(a, mode, float(param))
+    cp, ri = oracle.pattern(W.CSR(a.n, ip, ix, dv), int(power))
+    assert int(cp[-1]) == int(nnz)
+
+
+def _brute_sparsify(d, mode, param):
+    """Dense restatement of the Sec. 4 criteria on a small matrix."""
+    n = d.shape[0]
+    keep = np.zeros_like(d, dtype=bool)
+    stored = d != 0
+    if mode == "global":
+        diag = np.where(np.abs(np.diag(d)) > 0, np.abs(np.diag(d)), 1.0)
+        for i in range(n):
+            for j in range(n):
+                if stored[i, j]:
+                    keep[i, j] = i == j or abs(d[i, j]) / np.sqrt(diag[i] * diag[j]) > param
+    else:
+        for j in range(n):
+            rows = np.nonzero(stored[:, j])[0]
+            mags = np.abs(d[rows, j])
+            if mode == "tau":
+                for r, m in zip(rows, mags):
+                    keep[r, j] = r == j or m > (1.0 - param) * mags.max()
+            else:  # lfil: sort by magnitude descending, then row ascending
+                order = sorted(range(len(rows)), key=lambda t: (-mags[t], rows[t]))
+                for rank, t in enumerate(order):
+                    keep[rows[t], j] = rows[t] == j or rank < int(param)
+    return keep
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("mode,param", [("global", 0.05), ("global", 0.3), ("tau", 0.3), ("tau", 0.75),
+                                        ("lfil", 1), ("lfil", 3)])
+def test_sparsify_brute_force(seed, mode, param):
+    rng = np.random.default_rng(700 + seed)
+    n = 40
+    p = rng.random((n, n)) < 0.15
+    d = np.where(p, rng.uniform(-1.0, 1.0, (n, n)), 0.0)
+    # ties: a few equal magnitudes inside columns
+    d[p & (rng.random((n, n)) < 0.2)] = 0.5
+    np.fill_diagonal(d, np.where(rng.random(n) < 0.8, 2.0 + rng.random(n), 0.0))
+    a = W.CSR.from_dense(d)
+    ip, ix, dv = oracle.sparsify(a, mode, param)
+    got = np.zeros((n, n), dtype=bool)
+    rows = np.repeat(np.arange(n), np.diff(ip))
+    got[rows, ix] = True
+    assert np.array_equal(got, _brute_sparsify(d, mode, param))
+    # kept values are the source values
+    assert np.array_equal(dv, d[rows, ix])
+
+
+def test_sparsify_extremes():
+    """tau = 1 and lfil >= column length keep every entry; tau = 0 and
+    lfil = 0 keep the diagonal and, for tau, nothing but it."""
+    a = W.config2(nx=12, nmat=1).mats[0]
+    for mode, param in (("tau", 1.0), ("lfil", 100)):
+        ip, ix, _ = oracle.sparsify(a, mode, param)
+        assert np.array_equal(ip, a.indptr) and np.array_equal(ix, a.indices)
+    for mode, param in (("tau", 0.0), ("lfil", 0)):
+        ip, ix, _ = oracle.sparsify(a, mode, param)
+        rows = np.repeat(np.arange(a.n), np.diff(ip))
+        assert np.array_equal(rows, ix)
