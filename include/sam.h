@@ -146,6 +146,28 @@ sam_status sam_pattern_get(sam_pattern S, int32_t *n, int64_t *nnz, const int32_
 sam_status sam_pattern_destroy(sam_pattern S);
 
 /*
+ * sam_sparsify -- the sparsified source A~ of Sec. 4, whose level-L pattern
+ * (sam_pattern_build on A~) the paper compares as the map's pattern.  The
+ * diagonal is kept whenever it is stored; other stored entries by `mode`:
+ *   SAM_SPARSIFY_GLOBAL  |A_ij| / sqrt(D_ii D_jj) > param (the global
+ *                        threshold `thresh`), D_ii = |A_ii| if stored and
+ *                        nonzero, else 1 (the printed D^{1/2} A D^{1/2} is
+ *                        read as the symmetric scaling D^{-1/2} A D^{-1/2});
+ *   SAM_SPARSIFY_TAU     |A_ij| > (1 - param) max_i |A_ij| (column threshold
+ *                        tau = param in [0, 1], as printed);
+ *   SAM_SPARSIFY_LFIL    the (int)param entries of largest |A_ij| in each
+ *                        column (equal magnitudes: lower row index first).
+ * Outputs (caller-allocated, device or host): S_row_ptr[n+1],
+ * S_col_idx[nnz(A)] and S_val[nnz(A)] (nullable) receive the kept entries in
+ * CSR order; *S_nnz (host) their number.  Synchronises the handle's stream.
+ * Errors: SAM_ERR_INVALID_ARG (bad mode / parameter / pointers),
+ * SAM_ERR_BAD_CSR.
+ */
+enum { SAM_SPARSIFY_GLOBAL = 0, SAM_SPARSIFY_TAU = 1, SAM_SPARSIFY_LFIL = 2 };
+sam_status sam_sparsify(sam_handle h, const sam_csr *A, int mode, double param, int32_t *S_row_ptr,
+                        int32_t *S_col_idx, double *S_val, int64_t *S_nnz);
+
+/*
  * sam_build -- the SAM M_k = argmin ||A_k M - A_0||_F on the pattern S
  * (Eq. (approx_map), column decomposition of Sec. 2), one least-squares
  * problem per column, written as CSR:

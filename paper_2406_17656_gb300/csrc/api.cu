@@ -934,6 +934,39 @@ sam_status sam_build(sam_handle h, const sam_csr *A_k, const sam_csr *A_0, sam_p
                              col_status, res2, nullptr);
 }
 
+sam_status sam_sparsify(sam_handle h, const sam_csr *A, int mode, double param, int32_t *S_row_ptr,
+                        int32_t *S_col_idx, double *S_val, int64_t *S_nnz) {
+    if (!h || !A || !S_row_ptr || !S_col_idx || !S_nnz) return SAM_ERR_INVALID_ARG;
+    if (check_csr_arg(A, true) != SAM_OK) return SAM_ERR_INVALID_ARG;
+    if (mode < SAM_SPARSIFY_GLOBAL || mode > SAM_SPARSIFY_LFIL || !std::isfinite(param)) return SAM_ERR_INVALID_ARG;
+    if (mode == SAM_SPARSIFY_TAU && (param < 0.0 || param > 1.0)) return SAM_ERR_INVALID_ARG;
+    if (mode == SAM_SPARSIFY_LFIL && param < 0.0) return SAM_ERR_INVALID_ARG;
+    const int n = A->n;
+    cudaStream_t st = h->stream;
+    Scratch sc(h);
+    Stager sg(sc, st);
+    DevCsr a = stage_csr(sg, A, true);
+    int32_t *d_rp = sg.out(S_row_ptr, (size_t)n + 1);
+    int32_t *d_ci = sg.out(S_col_idx, (size_t)a.nnz);
+    double *d_v = S_val ? sg.out(S_val, (size_t)a.nnz) : nullptr;
+    if (sg.failed) return SAM_ERR_OOM;
+    sam_status s = validate_all(h, sc, {a});
+    if (s != SAM_OK) return s;
+    uint8_t *keep = sc.get<uint8_t>((size_t)a.nnz);
+    int32_t *cnt = sc.get<int32_t>((size_t)n + 1);
+    if (!keep || !cnt) return SAM_ERR_OOM;
+    if (sparsify_keep(h, n, a.nnz, a.rp, a.ci, a.v, mode, param, keep) != cudaSuccess ||
+        compact_kept(h, n, a.rp, a.ci, a.v, keep, cnt, d_rp, d_ci, d_v) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    int32_t kept = 0;
+    if (cudaMemcpyAsync(&kept, d_rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    if (sg.finish() != cudaSuccess) return SAM_ERR_CUDA;
+    s = drain_status(h);
+    *S_nnz = kept;
+    return s;
+}
+
 sam_status sam_residual(sam_handle h, const sam_csr *A_k, const sam_csr *M_k, const sam_csr *A_0, double *fro,
                         double *rel) {
     if (!h || check_csr_arg(A_k, true) || check_csr_arg(M_k, true) || check_csr_arg(A_0, true))

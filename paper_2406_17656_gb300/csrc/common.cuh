@@ -186,6 +186,13 @@ cudaError_t segmented_sum_f64(sam_handle h, const double *x, int K, int64_t seg,
 // pos[q] = position of the mirror entry of CSR position q of a structurally
 // symmetric matrix (the CSR position of A(ci[q], row of q))
 cudaError_t mirror_positions(sam_handle h, int n, const int32_t *rp, const int32_t *ci, int32_t *pos);
+// Sec. 4 sparsification: keep[e] (one byte per stored entry) for mode 0
+// (global threshold), 1 (column tau), 2 (lfil); then the kept entries in CSR
+// (cnt: int32[n] workspace)
+cudaError_t sparsify_keep(sam_handle h, int n, int64_t nnz, const int32_t *rp, const int32_t *ci, const double *v,
+                          int mode, double param, uint8_t *keep);
+cudaError_t compact_kept(sam_handle h, int n, const int32_t *rp, const int32_t *ci, const double *v,
+                         const uint8_t *keep, int32_t *cnt, int32_t *orp, int32_t *oci, double *ov);
 // doubles of workspace segmented_sum_f64 needs for K segments
 size_t segmented_sum_workspace(int K);
 // values of K matrices into the CSC order of their block-diagonal (+ FP32 copy)

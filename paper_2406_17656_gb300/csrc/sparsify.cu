@@ -1,0 +1,176 @@
+// sparsify.cu -- the sparsifications of A_k of arXiv 2406.17656 Sec. 4 that
+// produce the matrix A~_k whose level-L pattern serves as the map's pattern:
+//   global threshold  keep (i, j) if i = j or |A_ij| / sqrt(D_ii D_jj) > thresh,
+//                     D_ii = |A_ii| when stored and nonzero, else 1 (the
+//                     printed D^{1/2} A D^{1/2} read as the symmetric scaling
+//                     D^{-1/2} A D^{-1/2});
+//   column tau        keep (i, j) if i = j or |A_ij| > (1 - tau) max_i |A_ij|;
+//   lfil              keep the lfil entries of each column with the largest
+//                     |A_ij| (equal magnitudes: lower row first), and i = j.
+// Every decision is one FP64 comparison of the same expression on the same
+// inputs, so the kept structure is bit-exact.  The kept entries are written
+// compactly in CSR order.
+#include "common.cuh"
+
+namespace sam {
+namespace {
+
+__device__ __forceinline__ int lower_bound_row(const int32_t *a, int len, int key) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// D_ii: |A_ii| when the diagonal is stored and nonzero, else 1
+__global__ void diag_scale_kernel(int n, const int32_t *rp, const int32_t *ci, const double *v, double *d) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = rp[i], len = rp[i + 1] - b;
+    const int q = lower_bound_row(ci + b, len, i);
+    double di = 1.0;
+    if (q < len && ci[b + q] == i && fabs(v[b + q]) > 0.0) di = fabs(v[b + q]);
+    d[i] = di;
+}
+
+// eight threads per row
+__global__ void keep_global_kernel(int n, const int32_t *rp, const int32_t *ci, const double *v, const double *d,
+                                   double thresh, uint8_t *keep) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int sub = threadIdx.x & 7;
+    if (i >= n) return;
+    const double di = d[i];
+    for (int e = rp[i] + sub; e < rp[i + 1]; e += 8) {
+        const int j = ci[e];
+        keep[e] = (uint8_t)((j == (int)i) || (fabs(v[e]) / sqrt(di * d[j]) > thresh));
+    }
+}
+
+// column maxima of |A| as the bit patterns of non-negative doubles (which
+// order like the numbers)
+__global__ void col_max_kernel(int64_t nnz, const int32_t *ci, const double *v, unsigned long long *cmax) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        atomicMax(&cmax[ci[e]], (unsigned long long)__double_as_longlong(fabs(v[e])));
+}
+
+__global__ void keep_tau_kernel(int n, const int32_t *rp, const int32_t *ci, const double *v,
+                                const unsigned long long *cmax, double tau, uint8_t *keep) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int sub = threadIdx.x & 7;
+    if (i >= n) return;
+    for (int e = rp[i] + sub; e < rp[i + 1]; e += 8) {
+        const int j = ci[e];
+        const double mx = __longlong_as_double((long long)cmax[j]);
+        keep[e] = (uint8_t)((j == (int)i) || (fabs(v[e]) > (1.0 - tau) * mx));
+    }
+}
+
+// one warp per column of the CSC (cp, ri, cv): the rank of an entry is the
+// number of entries before it in the order (larger |value|, then lower row)
+__global__ void keep_lfil_kernel(int n, const int32_t *cp, const int32_t *ri, const double *cv, const int32_t *perm,
+                                 int lfil, uint8_t *keep) {
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= n) return;
+    const int b = cp[j], len = cp[j + 1] - b;
+    for (int p = lane; p < len; p += 32) {
+        const double a = fabs(cv[b + p]);
+        const int r = ri[b + p];
+        int rank = 0;
+        for (int q = 0; q < len && rank < lfil; ++q) {
+            const double aq = fabs(cv[b + q]);
+            rank += (aq > a || (aq == a && ri[b + q] < r)) ? 1 : 0;
+        }
+        keep[perm[b + p]] = (uint8_t)((r == (int)j) || rank < lfil);
+    }
+}
+
+__global__ void count_kept_kernel(int n, const int32_t *rp, const uint8_t *keep, int32_t *cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = 0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) c += keep[e];
+    cnt[i] = c;
+}
+
+__global__ void fill_kept_kernel(int n, const int32_t *rp, const int32_t *ci, const double *v, const uint8_t *keep,
+                                 const int32_t *orp, int32_t *oci, double *ov) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int o = orp[i];
+    for (int e = rp[i]; e < rp[i + 1]; ++e)
+        if (keep[e]) {
+            oci[o] = ci[e];
+            if (ov) ov[o] = v[e];
+            ++o;
+        }
+}
+
+}  // namespace
+
+cudaError_t sparsify_keep(sam_handle h, int n, int64_t nnz, const int32_t *rp, const int32_t *ci, const double *v,
+                          int mode, double param, uint8_t *keep) {
+    cudaStream_t st = handle_stream(h);
+    if (n == 0 || nnz == 0) return cudaSuccess;
+    const int rows8 = (int)(((int64_t)n * 8 + 255) / 256);
+    if (mode == 0) {
+        double *d = (double *)pool_alloc(h, sizeof(double) * (size_t)n);
+        if (!d) return cudaErrorMemoryAllocation;
+        diag_scale_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, rp, ci, v, d);
+        keep_global_kernel<<<rows8, 256, 0, st>>>(n, rp, ci, v, d, param, keep);
+        count_launch(h, 2);
+        pool_free(h, d);
+        return cudaGetLastError();
+    }
+    if (mode == 1) {
+        unsigned long long *cmax = (unsigned long long *)pool_alloc(h, sizeof(unsigned long long) * (size_t)n);
+        if (!cmax) return cudaErrorMemoryAllocation;
+        cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(unsigned long long) * (size_t)n, st);
+        if (e != cudaSuccess) return e;
+        int64_t blocks = (nnz + 255) / 256;
+        if (blocks > (int64_t)handle_sms(h) * 8) blocks = (int64_t)handle_sms(h) * 8;
+        col_max_kernel<<<(unsigned)blocks, 256, 0, st>>>(nnz, ci, v, cmax);
+        keep_tau_kernel<<<rows8, 256, 0, st>>>(n, rp, ci, v, cmax, param, keep);
+        count_launch(h, 2);
+        pool_free(h, cmax);
+        return cudaGetLastError();
+    }
+    // lfil: rank within the columns of the transpose
+    int32_t *cp = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)n + 1));
+    int32_t *ri = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)nnz);
+    double *cv = (double *)pool_alloc(h, sizeof(double) * (size_t)nnz);
+    int32_t *perm = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)nnz);
+    cudaError_t e = cudaErrorMemoryAllocation;
+    if (cp && ri && cv && perm) {
+        e = csr_to_csc(h, n, nnz, rp, ci, v, cp, ri, cv, perm);
+        if (e == cudaSuccess) {
+            const int64_t threads = (int64_t)n * 32;
+            const int lfil = param < 0.0 ? 0 : (param > 1e9 ? 1000000000 : (int)param);
+            keep_lfil_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(n, cp, ri, cv, perm, lfil, keep);
+            count_launch(h);
+            e = cudaGetLastError();
+        }
+    }
+    pool_free(h, cp);
+    pool_free(h, ri);
+    pool_free(h, cv);
+    pool_free(h, perm);
+    return e;
+}
+
+cudaError_t compact_kept(sam_handle h, int n, const int32_t *rp, const int32_t *ci, const double *v,
+                         const uint8_t *keep, int32_t *cnt, int32_t *orp, int32_t *oci, double *ov) {
+    cudaStream_t st = handle_stream(h);
+    if (n == 0) return cudaMemsetAsync(orp, 0, sizeof(int32_t), st);
+    count_kept_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, rp, keep, cnt);
+    count_launch(h);
+    cudaError_t e = exclusive_scan_i32(h, cnt, orp, n);
+    if (e != cudaSuccess) return e;
+    fill_kept_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, rp, ci, v, keep, orp, oci, ov);
+    count_launch(h);
+    return cudaGetLastError();
+}
+
+}  // namespace sam

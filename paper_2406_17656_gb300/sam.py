@@ -35,6 +35,7 @@ SAM_FLAG_TRUSTED = 1
 SAM_STATIC_MAX_ROWS = 1 << 19  # largest order sam_residual_static accepts
 
 PRECISIONS = {"fp64": SAM_FP64, "fp32r": SAM_FP32_REFINE}
+SPARSIFY_MODES = {"global": 0, "tau": 1, "lfil": 2}
 SAM_REFINE_AUTO = -1
 
 
@@ -104,6 +105,8 @@ _SIGS = [
     ("sam_plan_launches", ctypes.c_int32, [_vp, _i64p]),
     ("sam_plan_destroy", ctypes.c_int32, [_vp]),
     ("sam_refine_stats", ctypes.c_int32, [_vp, _i64p, ctypes.c_int]),
+    ("sam_sparsify", ctypes.c_int32,
+     [_vp, ctypes.POINTER(sam_csr), ctypes.c_int, ctypes.c_double, _vp, _vp, _vp, _i64p]),
     ("sam_set_tile_variants", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("sam_get_tile_variants", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("sam_profile", ctypes.c_int32, [_vp, ctypes.c_int]),
@@ -418,6 +421,22 @@ class Handle:
                   _addr(M_row_ptr), _addr(M_col_idx), _addr(M_val), _addr(col_status), _addr(res2),
                   fro.ctypes.data_as(_f64p) if fro is not None else None), name)
         return offsets, M_row_ptr, M_col_idx, M_val, fro
+
+    # ----------------------------------------------------------- sparsify
+    def sam_sparsify(self, A: Csr, mode: str, param: float) -> Csr:
+        """Sparsified A~ of Sec. 4 (mode "global", "tau" or "lfil"), as a
+        device Csr holding only the kept entries."""
+        import torch
+
+        rp = torch.empty(A.n + 1, dtype=torch.int32, device="cuda")
+        ci = torch.empty(max(A.nnz, 1), dtype=torch.int32, device="cuda")
+        v = torch.empty(max(A.nnz, 1), dtype=torch.float64, device="cuda")
+        nnz = ctypes.c_int64()
+        a = A.c()
+        _check(load().sam_sparsify(self.ptr, ctypes.byref(a), SPARSIFY_MODES[mode], float(param), _addr(rp),
+                                   _addr(ci), _addr(v), ctypes.byref(nnz)), "sam_sparsify")
+        k = int(nnz.value)
+        return Csr(rp, ci[:k], v[:k], n=A.n)
 
     # -------------------------------------------------------------- residual
     def sam_residual(self, A_k: Csr, M_k: Csr, A_0: Csr):
