@@ -233,3 +233,78 @@ def sparsify(A, mode: str, param: float):
     indptr = np.zeros(n + 1, dtype=np.int32)
     np.add.at(indptr, kept_rows + 1, 1)
     return np.cumsum(indptr).astype(np.int32), ci[keep].copy(), v[keep].copy()
+
+
+def gmres(A, b, x0=None, M=None, p0=None, restart: int = 30, maxiter: int = 1000, rtol: float = 1e-8):
+    """Restarted GMRES with right preconditioning for A x = b, as a Krylov
+    solve with a SAM would run it: the preconditioner is z = M (p0 * v), M a
+    map (CSR object, None = identity) and p0 the diagonal of P_0 (None =
+    identity).  Textbook steps (Saad, "Iterative Methods for Sparse Linear
+    Systems", right-preconditioned GMRES with modified Gram-Schmidt Arnoldi
+    and Givens rotations), FP64, scipy sparse products as the only library
+    primitive.  Stops when the least-squares residual estimate |g_{j+1}|
+    falls to rtol ||b|| or after maxiter Arnoldi steps.
+    Returns x, the number of Arnoldi steps, and the estimate after each step
+    divided by ||b||."""
+    import scipy.sparse as sp
+
+    n = int(A.n)
+    As = sp.csr_matrix((A.data, A.indices, A.indptr), shape=(n, n))
+    Ms = None if M is None else sp.csr_matrix((M.data, M.indices, M.indptr), shape=(n, n))
+    d = None if p0 is None else np.asarray(p0, np.float64)
+
+    def prec(v):
+        u = v if d is None else d * v
+        return u if Ms is None else Ms @ u
+
+    b = np.asarray(b, np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, np.float64)
+    bnorm = float(np.linalg.norm(b))
+    if bnorm == 0.0:
+        return np.zeros(n), 0, []
+    its, hist = 0, []
+    m = int(restart)
+    while its < maxiter:
+        r = b - As @ x
+        beta = float(np.linalg.norm(r))
+        if beta <= rtol * bnorm:
+            break
+        V = np.zeros((m + 1, n))
+        H = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        k = 0
+        done = False
+        for j in range(m):
+            w = As @ prec(V[j])
+            for i in range(j + 1):
+                H[i, j] = float(V[i] @ w)
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = float(np.linalg.norm(w))
+            if H[j + 1, j] > 0.0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):  # previous rotations on the new column
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = float(np.hypot(H[j, j], H[j + 1, j]))
+            cs[j], sn[j] = (1.0, 0.0) if den == 0.0 else (H[j, j] / den, H[j + 1, j] / den)
+            H[j, j] = cs[j] * H[j, j] + sn[j] * H[j + 1, j]
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            its += 1
+            k = j + 1
+            hist.append(abs(g[j + 1]) / bnorm)
+            if hist[-1] <= rtol or its >= maxiter:
+                done = True
+                break
+        y = np.zeros(k)
+        for i in range(k - 1, -1, -1):  # back substitution with the rotated H
+            y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+        x = x + prec(V[:k].T @ y)
+        if done:
+            break
+    return x, its, hist

@@ -382,3 +382,69 @@ def test_sparsify_extremes():
         ip, ix, _ = oracle.sparsify(a, mode, param)
         rows = np.repeat(np.arange(a.n), np.diff(ip))
         assert np.array_equal(rows, ix)
+
+
+# ------------------------------------------------------------- Krylov
+
+
+def _small_nonsym(seed, n=60):
+    rng = np.random.default_rng(seed)
+    p = (rng.random((n, n)) < 0.1) | np.eye(n, dtype=bool)
+    a = np.where(p, rng.uniform(-1.0, 1.0, (n, n)), 0.0)
+    a[np.arange(n), np.arange(n)] = 3.0 + rng.random(n)
+    return a
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_gmres_solves_small_systems(seed):
+    """The exact solution within the error bound: ||x - A^-1 b|| <=
+    kappa(A) rtol ||x||, and the true residual meets the tolerance."""
+    d = _small_nonsym(seed)
+    A = W.CSR.from_dense(d)
+    b = np.random.default_rng(seed + 10).standard_normal(d.shape[0])
+    x, its, hist = oracle.gmres(A, b, restart=20, rtol=1e-10)
+    exact = np.linalg.solve(d, b)
+    kappa = np.linalg.cond(d)
+    assert np.linalg.norm(x - exact) <= kappa * 2e-10 * np.linalg.norm(exact)
+    assert np.linalg.norm(b - d @ x) <= 2e-10 * np.linalg.norm(b)
+    # GMRES minimises the residual over growing spaces: the estimates do not
+    # increase inside a cycle
+    assert all(hist[i + 1] <= hist[i] * (1 + 1e-12) for i in range(min(19, len(hist) - 1)))
+
+
+def test_gmres_exact_preconditioner_converges_in_one_step():
+    d = _small_nonsym(5, n=40)
+    A = W.CSR.from_dense(d)
+    M = W.CSR.from_dense(np.linalg.inv(d))
+    b = np.ones(40)
+    x, its, hist = oracle.gmres(A, b, M=M, restart=10, rtol=1e-10)
+    assert its == 1 and np.allclose(d @ x, b, atol=1e-10)
+
+
+def test_gmres_diagonal_preconditioner_equals_scaled_system():
+    """P_0 = diag(p0): GMRES on A diag(p0) u = b, x = diag(p0) u, written out
+    with an explicitly scaled matrix and no preconditioner."""
+    d = _small_nonsym(7, n=50)
+    p0 = 1.0 / np.diag(d)
+    b = np.random.default_rng(3).standard_normal(50)
+    x1, it1, h1 = oracle.gmres(W.CSR.from_dense(d), b, p0=p0, restart=15, rtol=1e-9)
+    u, it2, h2 = oracle.gmres(W.CSR.from_dense(d * p0[None, :]), b, restart=15, rtol=1e-9)
+    assert it1 == it2
+    assert np.allclose(x1, p0 * u, rtol=1e-10, atol=1e-14)
+
+
+def test_gmres_iterations_match_scipy():
+    """A library special case: unpreconditioned restarted GMRES in scipy
+    stops after as many Arnoldi steps (same criterion ||r|| <= rtol ||b||),
+    give or take one at a restart boundary."""
+    import scipy.sparse.linalg as spla
+
+    a = W.config2(nx=16, nmat=1).mats[0]
+    b = np.random.default_rng(4).standard_normal(a.n)
+    x, its, hist = oracle.gmres(a, b, restart=25, rtol=1e-8, maxiter=2000)
+    count = [0]
+    xs, info = spla.gmres(a.to_scipy(), b, restart=25, rtol=1e-8, atol=0.0, maxiter=200,
+                          callback=lambda r: count.__setitem__(0, count[0] + 1), callback_type="pr_norm")
+    assert info == 0
+    assert abs(count[0] - its) <= 1
+    assert np.linalg.norm(x - xs) <= 1e-6 * np.linalg.norm(xs)
