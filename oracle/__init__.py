@@ -235,11 +235,11 @@ def sparsify(A, mode: str, param: float):
     return np.cumsum(indptr).astype(np.int32), ci[keep].copy(), v[keep].copy()
 
 
-def gmres(A, b, x0=None, M=None, p0=None, restart: int = 30, maxiter: int = 1000, rtol: float = 1e-8):
+def gmres(A, b, x0=None, M=None, p0=None, restart: int = 30, maxiter: int = 1000, rtol: float = 1e-8, P0=None):
     """Restarted GMRES with right preconditioning for A x = b, as a Krylov
-    solve with a SAM would run it: the preconditioner is z = M (p0 * v), M a
-    map (CSR object, None = identity) and p0 the diagonal of P_0 (None =
-    identity).  Textbook steps (Saad, "Iterative Methods for Sparse Linear
+    solve with a SAM would run it: the preconditioner is z = M (P_0 v), M a
+    map (CSR object, None = identity) and P_0 either the diagonal p0 or a
+    sparse operator P0 (CSR object; None for both = identity).  Textbook steps (Saad, "Iterative Methods for Sparse Linear
     Systems", right-preconditioned GMRES with modified Gram-Schmidt Arnoldi
     and Givens rotations), FP64, scipy sparse products as the only library
     primitive.  Stops when the least-squares residual estimate |g_{j+1}|
@@ -252,9 +252,11 @@ def gmres(A, b, x0=None, M=None, p0=None, restart: int = 30, maxiter: int = 1000
     As = sp.csr_matrix((A.data, A.indices, A.indptr), shape=(n, n))
     Ms = None if M is None else sp.csr_matrix((M.data, M.indices, M.indptr), shape=(n, n))
     d = None if p0 is None else np.asarray(p0, np.float64)
+    Ps = None if P0 is None else sp.csr_matrix((P0.data, P0.indices, P0.indptr), shape=(n, n))
 
     def prec(v):
         u = v if d is None else d * v
+        u = u if Ps is None else Ps @ u
         return u if Ms is None else Ms @ u
 
     b = np.asarray(b, np.float64)

@@ -448,3 +448,20 @@ def test_gmres_iterations_match_scipy():
     assert info == 0
     assert abs(count[0] - its) <= 1
     assert np.linalg.norm(x - xs) <= 1e-6 * np.linalg.norm(xs)
+
+
+def test_gmres_sparse_p0_operator():
+    """P_0 given as a sparse operator: a diagonal one reproduces the diagonal
+    p0 bit for bit (each product has one term), and an exact inverse of A
+    converges in one step, alone or composed with M = I."""
+    d = _small_nonsym(11, n=45)
+    A = W.CSR.from_dense(d)
+    p0 = 1.0 / np.diag(d)
+    b = np.random.default_rng(12).standard_normal(45)
+    x1, it1, h1 = oracle.gmres(A, b, p0=p0, restart=12, rtol=1e-10)
+    x2, it2, h2 = oracle.gmres(A, b, P0=W.CSR.from_dense(np.diag(p0)), restart=12, rtol=1e-10)
+    assert it1 == it2 and np.array_equal(x1, x2) and h1 == h2
+    inv = W.CSR.from_dense(np.linalg.inv(d))
+    for M in (None, W.CSR.from_dense(np.eye(45))):
+        x, its, _ = oracle.gmres(A, b, M=M, P0=inv, restart=12, rtol=1e-10)
+        assert its == 1 and np.allclose(d @ x, b, atol=1e-10)
