@@ -268,6 +268,78 @@ def cpu_baseline(seq, level, budget_s=12.0):
                 maps, len(seq.mats), cores, t_tot)}, seq.mats[:maps]
 
 
+# ------------------------------------------------------------------ krylov
+
+
+def krylov_bytes(n, nnz_ops, nnz_a, restart, its):
+    """Algorithmic bytes of `its` Arnoldi steps of GMRES(restart): per step,
+    each CSR product reads its values and column indices (12 B per entry),
+    its row pointers and the input vector and writes the output vector; the
+    Gram-Schmidt step j reads the j+1 basis vectors twice (projection and
+    update) and reads/writes w; per cycle, the update reads the k basis
+    vectors and x, the products of the preconditioner run once more, and
+    b - A x and its norm read A, x and b."""
+    def prod(nnz):
+        return 12.0 * nnz + 4.0 * (n + 1) + 16.0 * n
+
+    step_ops = sum(prod(z) for z in nnz_ops) + prod(nnz_a)
+    total, done = 0.0, 0
+    while done < its:
+        k = min(restart, its - done)
+        total += k * step_ops + sum(8.0 * n * (2 * (j + 1) + 3) for j in range(k))
+        total += 8.0 * n * (k + 2) + sum(prod(z) for z in nnz_ops) + prod(nnz_a) + 16.0 * n
+        done += k
+    return total
+
+
+def krylov_measurement(h, sam, torch, dev, stream, aks, a0, offs, mrp, mci, mval, n, K, world, rank):
+    k = K - 1
+    ident = sam.Csr(torch.arange(n + 1, dtype=torch.int32, device=dev), torch.arange(n, dtype=torch.int32, device=dev),
+                    torch.ones(n, dtype=torch.float64, device=dev), n=n)
+    p2 = h.sam_pattern_build(a0, 2)
+    P = sam.Csr(*h.sam_build(a0, ident, p2, "fp64"), n=n)
+    p2.destroy()
+    M = sam.Csr(mrp[k * (n + 1):(k + 1) * (n + 1)].contiguous(), mci[offs[k]:offs[k + 1]],
+                mval[offs[k]:offs[k + 1]], n=n)
+    A = aks[k]
+    b = torch.from_numpy(np.random.default_rng(9).standard_normal(n)).to(dev)
+    kw = dict(restart=30, maxiter=5000, rtol=1e-8)
+    res = {}
+    for name, MM in (("p0", None), ("map", M)):
+        h.sam_gmres(A, b, M=MM, P_0=P, **kw)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, its, rel = h.sam_gmres(A, b, M=MM, P_0=P, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        r = b - h.sam_apply(A, x)
+        res[name] = (its, rel, float(torch.linalg.norm(r) / torch.linalg.norm(b)), ms)
+    its, rel, true_rel, ms = res["map"]
+    ms = max_over_ranks(ms, world, dev)
+    moved = krylov_bytes(n, (P.nnz, M.nnz), A.nnz, kw["restart"], its)
+    gbs = moved / (ms * 1e-3) / 1e9
+    out = {"gmres": {"workload": "A_%d x = b, n = %d, GMRES(%d), rtol %g, right preconditioner M_%d (P_0 v), "
+                                 "P_0 = level-2 SPAI of A_0" % (k, n, kw["restart"], kw["rtol"], k),
+                     "steps_with_map": its, "steps_p0_only": res["p0"][0], "relres_estimate": rel,
+                     "true_relres": true_rel, "ms": ms, "us_per_step": ms * 1e3 / max(its, 1),
+                     "steps_per_s": job_value(its, world, ms), "ms_p0_only": res["p0"][3],
+                     "algorithmic_bytes": moved, "achieved_gbs": gbs, "hbm_frac": gbs / measured_hbm_gbs(),
+                     "working_set_mb": (12.0 * (A.nnz + M.nnz + P.nnz) + 8.0 * n * (kw["restart"] + 6)) / 1e6}}
+    if rank == 0 and world == 1:
+        # the oracle's textbook GMRES on the same system, 60 steps (two cycles)
+        import oracle
+
+        from paper_2406_17656_gb300 import workloads as W
+
+        host = lambda c: W.CSR(n, c.indptr.cpu().numpy(), c.indices.cpu().numpy(), c.data.cpu().numpy())
+        t = time.perf_counter()
+        oracle.gmres(host(A), b.cpu().numpy(), M=host(M), P0=host(P), restart=30, maxiter=60, rtol=1e-30)
+        out["gmres"]["oracle_us_per_step"] = (time.perf_counter() - t) * 1e6 / 60
+    return out
+
+
 # ------------------------------------------------------------------- ours
 
 
@@ -456,6 +528,13 @@ def main():
         extra["sparsify_ms_per_map"] = ts / K
         extra["sparsify_gbs"] = moved / (ts * 1e-3) / 1e9
         extra["sparsify_hbm_frac"] = extra["sparsify_gbs"] / measured_hbm_gbs()
+
+    # ---- the map in use (Sec. 1-2): restarted GMRES(30) on A_{K-1} x = b with
+    #      the right preconditioner M_{K-1} (P_0 v), P_0 a level-2 sparse
+    #      approximate inverse of A_0 (the map of A_0 onto I), against P_0 alone
+    if not args.quick:
+        extra.update(krylov_measurement(h, sam, torch, dev, stream, aks, a0, offs, out[0], out[1], v32, n, K,
+                                        world, rank))
 
     # ---- roofline of the dominant kernel (largest least-squares size class)
     sizes = column_sizes(seq.mats, args.level)

@@ -261,6 +261,42 @@ sam_status sam_residual(sam_handle h, const sam_csr *A_k, const sam_csr *M_k, co
 sam_status sam_apply(sam_handle h, const sam_csr *M_k, const double *x, double *y);
 
 /*
+ * sam_gmres -- restarted GMRES(restart) for A x = b with the right
+ * preconditioner z = M (P_0 v), the use of a map stated in Sec. 1-2: P_0 is
+ * a preconditioner built once for A_0, M = M_k the map of A_k, so that
+ * A_k M_k P_0 ~ A_0 P_0 ~ I (the paper builds the maps but does not run
+ * this solve).  FP64 throughout; orthogonalisation by classical
+ * Gram-Schmidt applied twice, Givens rotations on the Hessenberg matrix.
+ *   A       system matrix (values required).
+ *   M       nullable: the map M_k (identity when NULL).
+ *   P_0     nullable: a preconditioner of A_0 given as a sparse operator
+ *           (e.g. a diagonal, or a sparse approximate inverse of A_0 such as
+ *           sam_build(A_0, I, S) returns); applied by a product; identity
+ *           when NULL.
+ *   b[n]    right-hand side; x[n] the initial guess on entry, the solution
+ *           on return (x = x0 + M P_0 V y after every cycle).
+ *   restart Arnoldi steps per cycle, 1..SAM_GMRES_MAX_RESTART; maxiter the
+ *           total number of Arnoldi steps allowed (0: x is left as given).
+ *   rtol    stop when the least-squares residual estimate |g_{k+1}| falls
+ *           to rtol ||b||, or when the true residual ||b - A x|| computed at
+ *           the start of a cycle does.
+ *   iters   (host, nullable) Arnoldi steps taken; relres (host, nullable)
+ *           the last residual estimate (or cycle-start residual) / ||b||;
+ *           history (nullable, device or host double[maxiter]) the estimate
+ *           after each step (entries past *iters are left untouched).
+ * b = 0 gives x = 0 and 0 steps.  Not converging within maxiter is not an
+ * error (check relres).  Arrays may be host or device memory; the call
+ * synchronises once per restart cycle and returns when done.  Errors:
+ * SAM_ERR_INVALID_ARG, SAM_ERR_BAD_CSR (validated operators),
+ * SAM_ERR_NONFINITE (NaN/Inf in b or in the iteration), SAM_ERR_OOM.
+ * Workspace (handle's pool): (restart + 3) n + O(restart^2 + n restart / 256)
+ * doubles.
+ */
+#define SAM_GMRES_MAX_RESTART 128
+sam_status sam_gmres(sam_handle h, const sam_csr *A, const sam_csr *M, const sam_csr *P_0, const double *b, double *x,
+                     int restart, int maxiter, double rtol, int32_t *iters, double *relres, double *history);
+
+/*
  * sam_build_backward -- adjoint of sam_build on a fixed pattern: gradients
  * with respect to the stored values of A_k and A_0 of
  *     L = <dM, M_k>  +  resid_weight * ||A_k M_k - A_0||_F^2,

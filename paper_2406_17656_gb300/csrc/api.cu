@@ -198,6 +198,18 @@ struct Stager {
         outs.push_back({(void *)p, (const void *)d, sizeof(T) * count});
         return d;
     }
+    // an array read and written by the call (staged both ways if on the host)
+    template <typename T>
+    T *inout(T *p, size_t count) {
+        if (!p || count == 0 || is_device_ptr(p)) return p;
+        T *d = sc.get<T>(count);
+        if (!d || cudaMemcpyAsync(d, p, sizeof(T) * count, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            failed = true;
+            return nullptr;
+        }
+        outs.push_back({(void *)p, (const void *)d, sizeof(T) * count});
+        return d;
+    }
     bool has_host_outputs() const { return !outs.empty(); }
     cudaError_t finish() {
         for (auto &o : outs) {
@@ -1007,6 +1019,43 @@ sam_status sam_apply(sam_handle h, const sam_csr *M_k, const double *x, double *
     if (sg.finish() != cudaSuccess) return SAM_ERR_CUDA;
     if (sg.has_host_outputs()) return drain_status(h);
     return SAM_OK;
+}
+
+sam_status sam_gmres(sam_handle h, const sam_csr *A, const sam_csr *M, const sam_csr *P_0, const double *b, double *x,
+                     int restart, int maxiter, double rtol, int32_t *iters, double *relres, double *history) {
+    if (!h || check_csr_arg(A, true) || !b || !x) return SAM_ERR_INVALID_ARG;
+    if (restart < 1 || restart > SAM_GMRES_MAX_RESTART || maxiter < 0 || !std::isfinite(rtol) || rtol < 0.0)
+        return SAM_ERR_INVALID_ARG;
+    const int n = A->n;
+    if ((M && (check_csr_arg(M, true) || M->n != n)) || (P_0 && (check_csr_arg(P_0, true) || P_0->n != n)))
+        return SAM_ERR_INVALID_ARG;
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    if (n == 0) return SAM_OK;
+    Scratch sc(h);
+    Stager sg(sc, h->stream);
+    std::vector<DevCsr> all;
+    all.push_back(stage_csr(sg, A, true));
+    DevCsr dm, dp;
+    if (M) all.push_back(dm = stage_csr(sg, M, true));
+    if (P_0) all.push_back(dp = stage_csr(sg, P_0, true));
+    const double *db = sg.in(b, (size_t)n);
+    double *dx = sg.inout(x, (size_t)n);
+    double *dh = (history && maxiter > 0) ? sg.out(history, (size_t)maxiter) : nullptr;
+    if (sg.failed) return SAM_ERR_OOM;
+    sam_status s = validate_all(h, sc, all);
+    if (s != SAM_OK) return s;
+    KryOp a{all[0].nnz, all[0].rp, all[0].ci, all[0].v}, m, p;
+    if (M) m = KryOp{dm.nnz, dm.rp, dm.ci, dm.v};
+    if (P_0) p = KryOp{dp.nnz, dp.rp, dp.ci, dp.v};
+    int32_t its = 0;
+    double rel = 0.0;
+    s = gmres_solve(h, n, a, m, p, db, dx, restart, maxiter, rtol, dh, &its, &rel, nullptr);
+    if (iters) *iters = its;
+    if (relres) *relres = rel;
+    if (s != SAM_OK) return s;
+    if (sg.finish() != cudaSuccess) return SAM_ERR_CUDA;
+    return drain_status(h);
 }
 
 }  // extern "C"

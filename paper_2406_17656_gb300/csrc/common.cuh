@@ -207,6 +207,20 @@ cudaError_t residual_rows(sam_handle h, int n, const int32_t *krp, const int32_t
 cudaError_t status_reduce(sam_handle h, const int32_t *colstat, int64_t n, int32_t *flag);
 cudaError_t peak_fma(sam_handle h, double ms, double *f32, double *f64);
 
+// A CSR operator of a Krylov solve (device pointers; rp == nullptr: identity)
+struct KryOp {
+    int64_t nnz = 0;
+    const int32_t *rp = nullptr, *ci = nullptr;
+    const double *v = nullptr;
+};
+// Restarted GMRES(restart) for A x = b with the right preconditioner
+// z = M (P v) (krylov.cu).  x holds x0 on entry.  hist_dev (nullable,
+// device double[maxiter]) receives the residual estimate / ||b|| of every
+// step.  Synchronises once per restart cycle.
+sam_status gmres_solve(sam_handle h, int n, const KryOp &A, const KryOp &M, const KryOp &P, const double *b,
+                       double *x, int restart, int maxiter, double rtol, double *hist_dev, int32_t *its_out,
+                       double *rel_out, int64_t *launches_out);
+
 // Split the block-diagonal map CSR into per-map CSR arrays (row pointers
 // rebased to each map's offset, column indices shifted back by k n).
 cudaError_t split_map_structure(sam_handle h, int K, int n, const int32_t *mrp_big, const int32_t *mci_big,

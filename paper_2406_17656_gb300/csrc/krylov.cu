@@ -1,0 +1,527 @@
+// krylov.cu -- restarted GMRES(m) with the right preconditioner z = M (P_0 v)
+// (the use of a map named in Sec. 1-2: since A_k M_k ~ A_0 and P_0 is a
+// preconditioner of A_0, A_k M_k P_0 ~ A_0 P_0 ~ I).  FP64 throughout.
+//
+// Everything stays on the device.  One Arnoldi step is at most six launches:
+//   [P_0 product] -> [M product] -> A product (w written into V_{j+1})
+//   -> orth pass 0 (h = V^T w) -> pass 1 (w -= V h; h' = V^T w)
+//   -> pass 2 (w -= V h'; ||w||, Givens rotations, convergence test).
+// Orthogonalisation is classical Gram-Schmidt applied twice ("twice is
+// enough", Giraud, Langou and Rozloznik 2005), which is as stable as the
+// textbook modified Gram-Schmidt and reads the basis once per pass instead
+// of once per vector.  Basis vectors are stored unnormalised with a scale
+// s_l (the normalised vector is s_l V_l), which saves a normalisation pass.
+// Multi-block reductions write per-block partials in a fixed order; the
+// last block to finish (atomic ticket, no waiting) sums them in a fixed
+// order, so every result is bit-reproducible.
+//
+// Control lives in a device struct (KryCtl): every kernel of a step returns
+// at once when the iteration has stopped, so a whole restart cycle is
+// captured once into a CUDA graph and replayed, and the host reads the
+// control word once per cycle.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace sam {
+
+namespace {
+
+constexpr int kKryThreads = 256;
+constexpr int kMaxRestart = SAM_GMRES_MAX_RESTART;
+
+struct KryCtl {
+    int run;          // Arnoldi steps may execute
+    int k;            // steps taken in the current cycle
+    int its;          // steps taken in total
+    int maxiter;
+    unsigned ticket;  // last-block-done counter (0 between kernels)
+    int pad;
+    double rtol, bnorm, rel;
+};
+
+struct KryArgs {
+    int n, m, nblk;
+    KryCtl *ctl;
+    double *V;     // (m+1) x n, vector l at V + l n (unnormalised)
+    double *H;     // (m+1) x m column-major, rotated in place
+    double *cs, *sn;
+    double *g;     // (m+1) rotated right-hand side
+    double *s;     // (m+1) scales: the basis vector l is s[l] V_l
+    double *h;     // (m+1) this pass's projections / the cycle's y
+    double *coef;  // (m+1) coefficients of the next subtraction / combination
+    double *hist;  // [maxiter] residual estimates / ||b||
+    double *part;  // [nblk][m+1] block partials
+};
+
+// gates of the launches of a cycle
+enum { kGateAlways = 0, kGateRun = 1, kGateCycle = 2 };
+
+__device__ __forceinline__ bool gate_open(const KryCtl *c, int gate) {
+    if (gate == kGateRun) return c->run != 0;
+    if (gate == kGateCycle) return c->k > 0;
+    return true;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Each block has written its partials; returns true in the one block that
+// finishes last, after which all partials are visible to it.  No block waits.
+__device__ bool last_block(KryCtl *c, int nblk) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = atomicAdd(&c->ticket, 1u);
+        last = (t == (unsigned)nblk - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        if (threadIdx.x == 0) c->ticket = 0;
+    }
+    return last;
+}
+
+// Fixed-order sum over blocks of part[b][l] for l < cnt (called by the last
+// block): out[l] = total.  Warp w sums the vectors l = w, w + 8, ...; its
+// lanes read the blocks' partials in one round of independent loads.
+__device__ void reduce_partials(const double *part, int nblk, int stride, int cnt, double *out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int l = warp; l < cnt; l += kKryThreads / 32) {
+        double a = 0.0;
+        for (int b = lane; b < nblk; b += 32) a += __ldcg(part + (size_t)b * stride + l);
+        a = warp_sum(a);
+        if (lane == 0) out[l] = a;
+    }
+    __syncthreads();
+}
+
+// y = s (Op x), y = b - Op x, or y += Op x for a CSR operator, L lanes per
+// row.  s (nullable) is a device scalar.
+template <int L>
+__global__ void __launch_bounds__(kKryThreads) kry_spmv_kernel(const KryCtl *ctl, int gate, int n, const int32_t *rp,
+                                                               const int32_t *ci, const double *v, const double *x,
+                                                               const double *s, const double *b, double *y,
+                                                               int mode) {
+    if (!gate_open(ctl, gate)) return;
+    const int lane = threadIdx.x % L;
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
+    const bool live = row < n;  // every lane reaches the shuffles below
+    double acc = 0.0;
+    if (live) {
+        const int e1 = rp[row + 1];
+        for (int e = rp[row] + lane; e < e1; e += L) acc = fma(v[e], __ldg(x + ci[e]), acc);
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
+    if (live && lane == 0) {
+        if (mode == 0)
+            y[row] = s ? acc * *s : acc;
+        else if (mode == 1)
+            y[row] = b[row] - acc;
+        else
+            y[row] += acc;
+    }
+}
+
+// ||x||^2 over blocks; the last block stores ||b|| (what = 0) or starts a
+// cycle from the residual in V_0 (what = 1 between cycles, skipped once the
+// iteration has stopped; what = 2 for the first cycle, always: beta, g_0,
+// s_0, k = 0, and the stopping tests beta <= rtol ||b|| and its >= maxiter).
+__global__ void __launch_bounds__(kKryThreads) kry_norm_kernel(KryArgs a, const double *x, int what) {
+    __shared__ double red[kKryThreads / 32];
+    __shared__ double tot;
+    KryCtl *c = a.ctl;
+    if (what == 1 && !c->run) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) c->k = 0;
+        return;
+    }
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double t = 0.0;
+    if (i < a.n) t = x[i] * x[i];
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int w = 0; w < kKryThreads / 32; ++w) u += red[w];
+        a.part[(size_t)blockIdx.x * (a.m + 1)] = u;
+    }
+    if (!last_block(c, a.nblk)) return;
+    reduce_partials(a.part, a.nblk, a.m + 1, 1, &tot);
+    if (threadIdx.x == 0) {
+        const double nrm = sqrt(tot);
+        if (what == 0) {
+            c->bnorm = nrm;
+        } else {
+            c->k = 0;
+            a.g[0] = nrm;
+            a.s[0] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+            c->rel = c->bnorm > 0.0 ? nrm / c->bnorm : 0.0;
+            if (nrm <= c->rtol * c->bnorm || c->its >= c->maxiter) c->run = 0;
+        }
+    }
+}
+
+// One classical Gram-Schmidt pass on w = V_{j+1} against V_0..V_j.
+//   pass 0: h = V^T w (normalised basis);                 H(:, j)  = h
+//   pass 1: w -= sum coef_l V_l; h = V^T w;                H(:, j) += h
+//   pass 2: w -= sum coef_l V_l; ||w||, Givens rotations, residual estimate,
+//           stopping test.
+// A block owns 256 consecutive rows.  The subtraction takes one row per
+// thread; the projections take one vector per warp at a time, each lane
+// reading 8 of the block's rows of it (independent loads) against w staged
+// in shared memory.
+__global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j, int pass) {
+    __shared__ double ws[kKryThreads];
+    __shared__ double cf[kMaxRestart + 1];
+    __shared__ double red[kKryThreads / 32];
+    __shared__ double tot;
+    KryCtl *c = a.ctl;
+    if (!c->run) return;
+    const int n = a.n;
+    const int nv = j + 1;
+    double *w = a.V + (size_t)(j + 1) * n;
+    const int64_t row0 = (int64_t)blockIdx.x * kKryThreads;
+    const int64_t i = row0 + threadIdx.x;
+    const bool in = i < n;
+    if (pass > 0)
+        for (int l = threadIdx.x; l < nv; l += blockDim.x) cf[l] = a.coef[l];
+    __syncthreads();
+    double wi = in ? w[i] : 0.0;
+    if (pass > 0 && in) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int l = 0;
+        for (; l + 4 <= nv; l += 4) {
+            s0 = fma(cf[l], __ldg(a.V + (size_t)l * n + i), s0);
+            s1 = fma(cf[l + 1], __ldg(a.V + (size_t)(l + 1) * n + i), s1);
+            s2 = fma(cf[l + 2], __ldg(a.V + (size_t)(l + 2) * n + i), s2);
+            s3 = fma(cf[l + 3], __ldg(a.V + (size_t)(l + 3) * n + i), s3);
+        }
+        for (; l < nv; ++l) s0 = fma(cf[l], __ldg(a.V + (size_t)l * n + i), s0);
+        wi -= (s0 + s1) + (s2 + s3);
+        w[i] = wi;
+    }
+    ws[threadIdx.x] = wi;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int stride = a.m + 1;
+    if (pass < 2) {
+        for (int q = warp; q < nv; q += kKryThreads / 32) {
+            const double *vq = a.V + (size_t)q * n + row0;
+            double d = 0.0;
+#pragma unroll
+            for (int t = 0; t < kKryThreads / 32; ++t) {
+                const int r = lane + 32 * t;
+                if (row0 + r < n) d = fma(__ldg(vq + r), ws[r], d);
+            }
+            d = warp_sum(d);
+            if (lane == 0) a.part[(size_t)blockIdx.x * stride + q] = d;
+        }
+    } else {
+        double d = warp_sum(wi * wi);
+        if (lane == 0) red[warp] = d;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int ww = 0; ww < kKryThreads / 32; ++ww) t += red[ww];
+            a.part[(size_t)blockIdx.x * stride] = t;
+        }
+    }
+    if (!last_block(c, a.nblk)) return;
+    const int m = a.m;
+    double *Hj = a.H + (size_t)j * (m + 1);
+    if (pass < 2) {
+        reduce_partials(a.part, a.nblk, stride, nv, a.h);
+        for (int l = threadIdx.x; l < nv; l += blockDim.x) {
+            const double hl = a.s[l] * a.h[l];  // projection on the normalised s_l V_l
+            Hj[l] = pass == 0 ? hl : Hj[l] + hl;
+            a.coef[l] = hl * a.s[l];            // subtract hl (s_l V_l)
+        }
+        return;
+    }
+    reduce_partials(a.part, a.nblk, stride, 1, &tot);
+    if (threadIdx.x != 0) return;
+    const double hn = sqrt(tot);
+    Hj[j + 1] = hn;
+    a.s[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+    // earlier rotations on the new column, then the one that zeroes H(j+1, j)
+    for (int l = 0; l < j; ++l) {
+        const double t = a.cs[l] * Hj[l] + a.sn[l] * Hj[l + 1];
+        Hj[l + 1] = -a.sn[l] * Hj[l] + a.cs[l] * Hj[l + 1];
+        Hj[l] = t;
+    }
+    const double den = hypot(Hj[j], Hj[j + 1]);
+    const double cj = den == 0.0 ? 1.0 : Hj[j] / den, sj = den == 0.0 ? 0.0 : Hj[j + 1] / den;
+    a.cs[j] = cj;
+    a.sn[j] = sj;
+    Hj[j] = cj * Hj[j] + sj * Hj[j + 1];
+    Hj[j + 1] = 0.0;
+    a.g[j + 1] = -sj * a.g[j];
+    a.g[j] = cj * a.g[j];
+    c->its += 1;
+    c->k = j + 1;
+    const double est = fabs(a.g[j + 1]) / c->bnorm;
+    a.hist[c->its - 1] = est;
+    c->rel = est;
+    if (est <= c->rtol || c->its >= c->maxiter) c->run = 0;
+}
+
+// End of a cycle: y = R^{-1} g (back substitution on the rotated H), then
+// coef_l = y_l s_l so that the update is sum coef_l V_l.
+__global__ void kry_backsolve_kernel(KryArgs a) {
+    KryCtl *c = a.ctl;
+    if (c->k <= 0 || threadIdx.x != 0) return;
+    const int k = c->k, m = a.m;
+    for (int i = k - 1; i >= 0; --i) {
+        double t = a.g[i];
+        for (int l = i + 1; l < k; ++l) t -= a.H[(size_t)l * (m + 1) + i] * a.h[l];
+        a.h[i] = t / a.H[(size_t)i * (m + 1) + i];
+    }
+    for (int i = 0; i < k; ++i) a.coef[i] = a.h[i] * a.s[i];
+}
+
+// t = sum_{l<k} coef_l V_l (accumulate = 1: t += that sum)
+__global__ void __launch_bounds__(kKryThreads) kry_combine_kernel(KryArgs a, double *t, int accumulate) {
+    __shared__ double cf[kMaxRestart + 1];
+    KryCtl *c = a.ctl;
+    const int k = c->k;
+    if (k <= 0) return;
+    for (int l = threadIdx.x; l < k; l += blockDim.x) cf[l] = a.coef[l];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    double u0 = 0.0, u1 = 0.0;
+    int l = 0;
+    for (; l + 2 <= k; l += 2) {
+        u0 = fma(cf[l], __ldg(a.V + (size_t)l * a.n + i), u0);
+        u1 = fma(cf[l + 1], __ldg(a.V + (size_t)(l + 1) * a.n + i), u1);
+    }
+    if (l < k) u0 = fma(cf[l], __ldg(a.V + (size_t)l * a.n + i), u0);
+    const double u = u0 + u1;
+    if (accumulate)
+        t[i] += u;
+    else
+        t[i] = u;
+}
+
+__global__ void kry_init_kernel(KryCtl *c, int maxiter, double rtol) {
+    c->run = maxiter > 0;
+    c->k = 0;
+    c->its = 0;
+    c->maxiter = maxiter;
+    c->ticket = 0;
+    c->rtol = rtol;
+    c->bnorm = 0.0;
+    c->rel = 0.0;
+}
+
+// lanes per row: the power of two at or above the mean row length, 2..32
+int lanes_for(int n, int64_t nnz) {
+    const double mean = n > 0 ? (double)nnz / n : 0.0;
+    int L = 2;
+    while (L < 32 && L < mean) L *= 2;
+    return L;
+}
+
+cudaError_t spmv(cudaStream_t st, const KryArgs &a, int gate, const KryOp &op, const double *x, const double *s,
+                 const double *b, double *y, int mode) {
+    const int n = a.n;
+    const int L = lanes_for(n, op.nnz);
+    const int64_t threads = (int64_t)n * L;
+    const unsigned blocks = (unsigned)((threads + kKryThreads - 1) / kKryThreads);
+#define SAM_KRY_SPMV(LL)                                                                                      \
+    kry_spmv_kernel<LL><<<blocks, kKryThreads, 0, st>>>(a.ctl, gate, n, op.rp, op.ci, op.v, x, s, b, y, mode); \
+    break;
+    switch (L) {
+        case 2: SAM_KRY_SPMV(2)
+        case 4: SAM_KRY_SPMV(4)
+        case 8: SAM_KRY_SPMV(8)
+        case 16: SAM_KRY_SPMV(16)
+        default: SAM_KRY_SPMV(32)
+    }
+#undef SAM_KRY_SPMV
+    return cudaGetLastError();
+}
+
+// The launches of one restart cycle (all gated on the control word):
+// m Arnoldi steps, the update of x, and the residual of the next cycle.
+// Returns the number of kernels enqueued, or -1 on a launch error.
+int enqueue_cycle(cudaStream_t st, const KryArgs &a, const KryOp &A, const KryOp &M, const KryOp &P,
+                  const double *b, double *x, double *t, double *u) {
+    int launches = 0;
+    const unsigned nb = (unsigned)a.nblk;
+    auto ok = [&](cudaError_t e) { return e == cudaSuccess; };
+    for (int j = 0; j < a.m; ++j) {
+        // z = M (P_0 (s_j V_j)), the identity where an operator is absent
+        const double *z = a.V + (size_t)j * a.n;
+        const double *zs = a.s + j;
+        if (P.rp) {
+            if (!ok(spmv(st, a, kGateRun, P, z, zs, nullptr, t, 0))) return -1;
+            ++launches;
+            z = t;
+            zs = nullptr;
+        }
+        if (M.rp) {
+            if (!ok(spmv(st, a, kGateRun, M, z, zs, nullptr, u, 0))) return -1;
+            ++launches;
+            z = u;
+            zs = nullptr;
+        }
+        if (!ok(spmv(st, a, kGateRun, A, z, zs, nullptr, a.V + (size_t)(j + 1) * a.n, 0))) return -1;
+        ++launches;
+        for (int pass = 0; pass < 3; ++pass) {
+            kry_orth_kernel<<<nb, kKryThreads, 0, st>>>(a, j, pass);
+            if (!ok(cudaGetLastError())) return -1;
+            ++launches;
+        }
+    }
+    // x += M (P_0 (sum_l y_l s_l V_l))
+    kry_backsolve_kernel<<<1, 32, 0, st>>>(a);
+    ++launches;
+    if (!P.rp && !M.rp) {
+        kry_combine_kernel<<<nb, kKryThreads, 0, st>>>(a, x, 1);
+        ++launches;
+    } else {
+        // the sum goes to the temporary the first operator does not write
+        double *sum = P.rp ? u : t;
+        kry_combine_kernel<<<nb, kKryThreads, 0, st>>>(a, sum, 0);
+        ++launches;
+        const double *cur = sum;
+        if (P.rp && M.rp) {
+            if (!ok(spmv(st, a, kGateCycle, P, cur, nullptr, nullptr, t, 0))) return -1;
+            ++launches;
+            cur = t;
+        }
+        const KryOp &last = M.rp ? M : P;
+        if (!ok(spmv(st, a, kGateCycle, last, cur, nullptr, nullptr, x, 2))) return -1;
+        ++launches;
+    }
+    if (!ok(cudaGetLastError())) return -1;
+    // next cycle: V_0 = b - A x, beta, stopping test
+    if (!ok(spmv(st, a, kGateRun, A, x, nullptr, b, a.V, 1))) return -1;
+    kry_norm_kernel<<<nb, kKryThreads, 0, st>>>(a, a.V, 1);
+    launches += 2;
+    if (!ok(cudaGetLastError())) return -1;
+    return launches;
+}
+
+}  // namespace
+
+sam_status gmres_solve(sam_handle h, int n, const KryOp &A, const KryOp &M, const KryOp &P, const double *b,
+                       double *x, int restart, int maxiter, double rtol, double *hist_dev, int32_t *its_out,
+                       double *rel_out, int64_t *launches_out) {
+    cudaStream_t st = handle_stream(h);
+    const int m = restart;
+    const int nblk = (int)((n + kKryThreads - 1) / kKryThreads);
+    const size_t vec = (size_t)n;
+    std::vector<void *> mem;
+    bool oom = false;
+    auto get = [&](size_t bytes) {
+        void *p = pool_alloc(h, bytes);
+        if (p)
+            mem.push_back(p);
+        else
+            oom = true;
+        return p;
+    };
+    auto release = [&](sam_status s) {
+        for (void *p : mem) pool_free(h, p);
+        return s;
+    };
+    KryArgs a;
+    a.n = n;
+    a.m = m;
+    a.nblk = nblk;
+    a.ctl = (KryCtl *)get(sizeof(KryCtl));
+    a.V = (double *)get(sizeof(double) * vec * (m + 1));
+    a.H = (double *)get(sizeof(double) * (size_t)(m + 1) * m);
+    a.cs = (double *)get(sizeof(double) * (m + 1));
+    a.sn = (double *)get(sizeof(double) * (m + 1));
+    a.g = (double *)get(sizeof(double) * (m + 1));
+    a.s = (double *)get(sizeof(double) * (m + 1));
+    a.h = (double *)get(sizeof(double) * (m + 1));
+    a.coef = (double *)get(sizeof(double) * (m + 1));
+    a.hist = hist_dev ? hist_dev : (double *)get(sizeof(double) * (size_t)(maxiter > 0 ? maxiter : 1));
+    a.part = (double *)get(sizeof(double) * (size_t)nblk * (m + 1));
+    double *t = (double *)get(sizeof(double) * vec);
+    double *u = (double *)get(sizeof(double) * vec);
+    if (oom) return release(SAM_ERR_OOM);
+    int64_t launches = 0;
+    KryCtl hc;
+    // ||b||, then the first residual (b - A x0) and its norm
+    kry_init_kernel<<<1, 1, 0, st>>>(a.ctl, maxiter, rtol);
+    kry_norm_kernel<<<nblk, kKryThreads, 0, st>>>(a, b, 0);
+    launches += 2;
+    if (cudaMemcpyAsync(&hc, a.ctl, sizeof(KryCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return release(SAM_ERR_CUDA);
+    if (!std::isfinite(hc.bnorm)) return release(SAM_ERR_NONFINITE);
+    if (hc.bnorm == 0.0) {  // b = 0: x = 0, no steps
+        cudaMemsetAsync(x, 0, sizeof(double) * vec, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return release(SAM_ERR_CUDA);
+        if (its_out) *its_out = 0;
+        if (rel_out) *rel_out = 0.0;
+        if (launches_out) *launches_out = launches;
+        count_launch(h, (int)launches);
+        return release(SAM_OK);
+    }
+    if (spmv(st, a, kGateAlways, A, x, nullptr, b, a.V, 1) != cudaSuccess) return release(SAM_ERR_CUDA);
+    kry_norm_kernel<<<nblk, kKryThreads, 0, st>>>(a, a.V, 2);
+    launches += 2;
+    // one restart cycle, captured once and replayed while the iteration runs
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto drop_graph = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+    };
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return release(SAM_ERR_CUDA);
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        drop_graph();
+        return release(SAM_ERR_CUDA);
+    }
+    const int per_cycle = enqueue_cycle(cap, a, A, M, P, b, x, t, u);
+    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    if (per_cycle < 0 || ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        drop_graph();
+        return release(SAM_ERR_CUDA);
+    }
+    sam_status status = SAM_OK;
+    for (;;) {
+        if (cudaMemcpyAsync(&hc, a.ctl, sizeof(KryCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            status = SAM_ERR_CUDA;
+            break;
+        }
+        if (!std::isfinite(hc.rel)) {
+            status = SAM_ERR_NONFINITE;
+            break;
+        }
+        if (!hc.run) break;
+        if (cudaGraphLaunch(exec, st) != cudaSuccess) {
+            status = SAM_ERR_CUDA;
+            break;
+        }
+        launches += per_cycle;
+    }
+    drop_graph();
+    count_launch(h, (int)launches);
+    if (its_out) *its_out = hc.its;
+    if (rel_out) *rel_out = hc.rel;
+    if (launches_out) *launches_out = launches;
+    return release(status);
+}
+
+}  // namespace sam

@@ -112,6 +112,9 @@ _SIGS = [
     ("sam_profile", ctypes.c_int32, [_vp, ctypes.c_int]),
     ("sam_profile_read", ctypes.c_int32, [_vp, _i64p, ctypes.POINTER(ctypes.c_double), _i64p]),
     ("sam_peak_flops", ctypes.c_int32, [_vp, ctypes.c_double, _f64p, _f64p]),
+    ("sam_gmres", ctypes.c_int32,
+     [_vp, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), _vp, _vp, ctypes.c_int,
+      ctypes.c_int, ctypes.c_double, _i32p, _f64p, _vp]),
     ("sam_residual_static", ctypes.c_int32,
      [_vp, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), _vp, _vp]),
 ]
@@ -454,6 +457,27 @@ class Handle:
         m = M_k.c()
         _check(load().sam_apply(self.ptr, ctypes.byref(m), _addr(x), _addr(y)), "sam_apply")
         return y
+
+    def sam_gmres(self, A: Csr, b, x=None, M: Csr | None = None, P_0: Csr | None = None, restart: int = 30,
+                  maxiter: int = 1000, rtol: float = 1e-8, history=None):
+        """Restarted GMRES for A x = b with the right preconditioner
+        z = M (P_0 v) (either operator may be None = identity).  x holds the
+        initial guess (zeros if None) and receives the solution.  history
+        (nullable, float64[maxiter], device or host) gets the residual
+        estimate / ||b|| after every step.  Returns (x, iterations, relres)."""
+        import torch
+
+        if x is None:
+            x = torch.zeros_like(b) if hasattr(b, "data_ptr") else np.zeros_like(b)
+        its, rel = ctypes.c_int32(), ctypes.c_double()
+        a = A.c()
+        m = M.c() if M is not None else None
+        p = P_0.c() if P_0 is not None else None
+        _check(load().sam_gmres(self.ptr, ctypes.byref(a), ctypes.byref(m) if m is not None else None,
+                                ctypes.byref(p) if p is not None else None, _addr(b), _addr(x), int(restart),
+                                int(maxiter), float(rtol), ctypes.byref(its), ctypes.byref(rel), _addr(history)),
+               "sam_gmres")
+        return x, its.value, rel.value
 
     def sam_build_backward(self, A_k: Csr, A_0: Csr, S: Pattern, M_val, dM_val=None, precision="fp32r",
                            refine_steps: int = 1, resid_weight: float = 0.0, dA_k_val=None, dA_0_val=None,
