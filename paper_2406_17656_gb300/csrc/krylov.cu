@@ -105,7 +105,11 @@ __device__ void reduce_partials(const double *part, int nblk, int stride, int cn
 }
 
 // y = s (Op x), y = b - Op x, or y += Op x for a CSR operator, L lanes per
-// row.  s (nullable) is a device scalar.
+// row.  s (nullable) is a device scalar.  GB300 runs FP64 at 1/64 of the
+// FP32 rate, and the product is bound by FP64 warp instructions rather than
+// by memory, so a lane takes a dozen entries of its row: one FMA per entry
+// (two accumulators, loads issued four entries ahead) and log2(L)
+// shuffle-adds per row, instead of padding lanes and reduction trees.
 template <int L>
 __global__ void __launch_bounds__(kKryThreads) kry_spmv_kernel(const KryCtl *ctl, int gate, int n, const int32_t *rp,
                                                                const int32_t *ci, const double *v, const double *x,
@@ -115,11 +119,22 @@ __global__ void __launch_bounds__(kKryThreads) kry_spmv_kernel(const KryCtl *ctl
     const int lane = threadIdx.x % L;
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
     const bool live = row < n;  // every lane reaches the shuffles below
-    double acc = 0.0;
+    double a0 = 0.0, a1 = 0.0;
     if (live) {
         const int e1 = rp[row + 1];
-        for (int e = rp[row] + lane; e < e1; e += L) acc = fma(v[e], __ldg(x + ci[e]), acc);
+        int e = rp[row] + lane;
+        for (; e + 3 * L < e1; e += 4 * L) {
+            const int c0 = ci[e], c1 = ci[e + L], c2 = ci[e + 2 * L], c3 = ci[e + 3 * L];
+            const double v0 = v[e], v1 = v[e + L], v2 = v[e + 2 * L], v3 = v[e + 3 * L];
+            const double x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+            a0 = fma(v0, x0, a0);
+            a1 = fma(v1, x1, a1);
+            a0 = fma(v2, x2, a0);
+            a1 = fma(v3, x3, a1);
+        }
+        for (; e < e1; e += L) a0 = fma(v[e], __ldg(x + ci[e]), a0);
     }
+    double acc = a0 + a1;
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
     if (live && lane == 0) {
@@ -176,12 +191,16 @@ __global__ void __launch_bounds__(kKryThreads) kry_norm_kernel(KryArgs a, const 
 //   pass 1: w -= sum coef_l V_l; h = V^T w;                H(:, j) += h
 //   pass 2: w -= sum coef_l V_l; ||w||, Givens rotations, residual estimate,
 //           stopping test.
-// A block owns 256 consecutive rows.  The subtraction takes one row per
-// thread; the projections take one vector per warp at a time, each lane
-// reading 8 of the block's rows of it (independent loads) against w staged
-// in shared memory.
-__global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j, int pass) {
-    __shared__ double ws[kKryThreads];
+// A block owns 256 consecutive rows.  In pass 0, op (when given) computes
+// w = s (Op z) itself, one row per thread (rows short enough for one lane),
+// which fuses the product with A into the first pass.  The subtraction
+// takes one row per thread and loads 32 basis values before its FMAs; the
+// projections take four vectors per warp at a time, each lane reading 8 of
+// the block's rows of each (32 independent loads), against w staged in
+// shared memory, with the four shuffle reductions interleaved.
+__global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j, int pass, KryOp op, const double *z,
+                                                               const double *zs) {
+    __shared__ double ws[2 * (kMaxRestart + 2) > kKryThreads ? 2 * (kMaxRestart + 2) : kKryThreads];
     __shared__ double cf[kMaxRestart + 1];
     __shared__ double red[kKryThreads / 32];
     __shared__ double tot;
@@ -196,35 +215,103 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
     if (pass > 0)
         for (int l = threadIdx.x; l < nv; l += blockDim.x) cf[l] = a.coef[l];
     __syncthreads();
-    double wi = in ? w[i] : 0.0;
-    if (pass > 0 && in) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int l = 0;
-        for (; l + 4 <= nv; l += 4) {
-            s0 = fma(cf[l], __ldg(a.V + (size_t)l * n + i), s0);
-            s1 = fma(cf[l + 1], __ldg(a.V + (size_t)(l + 1) * n + i), s1);
-            s2 = fma(cf[l + 2], __ldg(a.V + (size_t)(l + 2) * n + i), s2);
-            s3 = fma(cf[l + 3], __ldg(a.V + (size_t)(l + 3) * n + i), s3);
+    double wi = 0.0;
+    if (in) {
+        if (pass == 0 && op.rp) {
+            double a0 = 0.0, a1 = 0.0;
+            const int e1 = op.rp[i + 1];
+            int e = op.rp[i];
+            for (; e + 3 < e1; e += 4) {
+                const int c0 = op.ci[e], c1 = op.ci[e + 1], c2 = op.ci[e + 2], c3 = op.ci[e + 3];
+                const double v0 = op.v[e], v1 = op.v[e + 1], v2 = op.v[e + 2], v3 = op.v[e + 3];
+                const double x0 = __ldg(z + c0), x1 = __ldg(z + c1), x2 = __ldg(z + c2), x3 = __ldg(z + c3);
+                a0 = fma(v0, x0, a0);
+                a1 = fma(v1, x1, a1);
+                a0 = fma(v2, x2, a0);
+                a1 = fma(v3, x3, a1);
+            }
+            for (; e < e1; ++e) a0 = fma(op.v[e], __ldg(z + op.ci[e]), a0);
+            wi = a0 + a1;
+            if (zs) wi *= *zs;
+            w[i] = wi;
+        } else {
+            wi = w[i];
         }
-        for (; l < nv; ++l) s0 = fma(cf[l], __ldg(a.V + (size_t)l * n + i), s0);
-        wi -= (s0 + s1) + (s2 + s3);
+    }
+    if (pass > 0 && in) {
+        // full chunks of 8 basis values: the next chunk's loads are issued
+        // before this chunk's FMAs; no FP64 instruction is issued for absent
+        // vectors (GB300's narrow FP64 pipe is the bound here)
+        const double *vi = a.V + i;
+        double s0 = 0.0, s1 = 0.0;
+        const int full = nv & ~7;
+        double cur[8], nxt[8];
+        if (full > 0) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) cur[t] = __ldg(vi + (size_t)t * n);
+        }
+        for (int l0 = 0; l0 < full; l0 += 8) {
+            if (l0 + 8 < full) {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) nxt[t] = __ldg(vi + (size_t)(l0 + 8 + t) * n);
+            }
+#pragma unroll
+            for (int t = 0; t < 8; t += 2) {
+                s0 = fma(cf[l0 + t], cur[t], s0);
+                s1 = fma(cf[l0 + t + 1], cur[t + 1], s1);
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) cur[t] = nxt[t];
+        }
+        for (int l = full; l < nv; ++l) s0 = fma(cf[l], __ldg(vi + (size_t)l * n), s0);
+        wi -= s0 + s1;
         w[i] = wi;
     }
     ws[threadIdx.x] = wi;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int stride = a.m + 1;
+    constexpr int W8 = kKryThreads / 32;
     if (pass < 2) {
-        for (int q = warp; q < nv; q += kKryThreads / 32) {
-            const double *vq = a.V + (size_t)q * n + row0;
-            double d = 0.0;
+        double wl[W8];
 #pragma unroll
-            for (int t = 0; t < kKryThreads / 32; ++t) {
-                const int r = lane + 32 * t;
-                if (row0 + r < n) d = fma(__ldg(vq + r), ws[r], d);
+        for (int t = 0; t < W8; ++t) wl[t] = ws[lane + 32 * t];  // rows past n hold 0
+        for (int q0 = warp; q0 < nv; q0 += 4 * W8) {
+            if (q0 + 3 * W8 < nv) {
+                // four vectors: 32 independent loads, interleaved reductions
+                double d[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const double *vq = a.V + (size_t)(q0 + u * W8) * n + row0;
+                    d[u] = 0.0;
+#pragma unroll
+                    for (int t = 0; t < W8; ++t) {
+                        const int r = lane + 32 * t;
+                        if (row0 + r < n) d[u] = fma(__ldg(vq + r), wl[t], d[u]);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) d[u] += __shfl_xor_sync(0xffffffffu, d[u], o);
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) a.part[(size_t)blockIdx.x * stride + q0 + u * W8] = d[u];
+                }
+            } else {
+                for (int q = q0; q < nv; q += W8) {
+                    const double *vq = a.V + (size_t)q * n + row0;
+                    double d = 0.0;
+#pragma unroll
+                    for (int t = 0; t < W8; ++t) {
+                        const int r = lane + 32 * t;
+                        if (row0 + r < n) d = fma(__ldg(vq + r), wl[t], d);
+                    }
+                    d = warp_sum(d);
+                    if (lane == 0) a.part[(size_t)blockIdx.x * stride + q] = d;
+                }
             }
-            d = warp_sum(d);
-            if (lane == 0) a.part[(size_t)blockIdx.x * stride + q] = d;
         }
     } else {
         double d = warp_sum(wi * wi);
@@ -232,7 +319,7 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
-            for (int ww = 0; ww < kKryThreads / 32; ++ww) t += red[ww];
+            for (int ww = 0; ww < W8; ++ww) t += red[ww];
             a.part[(size_t)blockIdx.x * stride] = t;
         }
     }
@@ -248,25 +335,35 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
         }
         return;
     }
+    // stage the new column and the earlier rotations in shared memory (one
+    // round of loads); the rotations are a serial chain
+    double *col = ws, *rc = ws + kMaxRestart + 2, *rs = cf;
+    for (int l = threadIdx.x; l <= j; l += blockDim.x) {
+        col[l] = Hj[l];
+        rc[l] = a.cs[l];
+        rs[l] = a.sn[l];
+    }
     reduce_partials(a.part, a.nblk, stride, 1, &tot);
     if (threadIdx.x != 0) return;
     const double hn = sqrt(tot);
-    Hj[j + 1] = hn;
+    col[j + 1] = hn;
     a.s[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
     // earlier rotations on the new column, then the one that zeroes H(j+1, j)
     for (int l = 0; l < j; ++l) {
-        const double t = a.cs[l] * Hj[l] + a.sn[l] * Hj[l + 1];
-        Hj[l + 1] = -a.sn[l] * Hj[l] + a.cs[l] * Hj[l + 1];
-        Hj[l] = t;
+        const double t = rc[l] * col[l] + rs[l] * col[l + 1];
+        col[l + 1] = -rs[l] * col[l] + rc[l] * col[l + 1];
+        col[l] = t;
     }
-    const double den = hypot(Hj[j], Hj[j + 1]);
-    const double cj = den == 0.0 ? 1.0 : Hj[j] / den, sj = den == 0.0 ? 0.0 : Hj[j + 1] / den;
+    const double den = hypot(col[j], col[j + 1]);
+    const double cj = den == 0.0 ? 1.0 : col[j] / den, sj = den == 0.0 ? 0.0 : col[j + 1] / den;
     a.cs[j] = cj;
     a.sn[j] = sj;
-    Hj[j] = cj * Hj[j] + sj * Hj[j + 1];
+    col[j] = cj * col[j] + sj * col[j + 1];
+    for (int l = 0; l <= j; ++l) Hj[l] = col[l];
     Hj[j + 1] = 0.0;
-    a.g[j + 1] = -sj * a.g[j];
-    a.g[j] = cj * a.g[j];
+    const double gj = a.g[j];
+    a.g[j + 1] = -sj * gj;
+    a.g[j] = cj * gj;
     c->its += 1;
     c->k = j + 1;
     const double est = fabs(a.g[j + 1]) / c->bnorm;
@@ -276,17 +373,37 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
 }
 
 // End of a cycle: y = R^{-1} g (back substitution on the rotated H), then
-// coef_l = y_l s_l so that the update is sum coef_l V_l.
-__global__ void kry_backsolve_kernel(KryArgs a) {
+// coef_l = y_l s_l so that the update is sum coef_l V_l.  One block: R and g
+// are staged in shared memory, and each column step updates the remaining
+// right-hand side in parallel (column-oriented back substitution).
+__global__ void __launch_bounds__(kKryThreads) kry_backsolve_kernel(KryArgs a) {
+    __shared__ double R[kMaxRestart * (kMaxRestart + 1) / 2 > 0 ? 64 * 65 : 1];
+    __shared__ double rhs[kMaxRestart + 1];
     KryCtl *c = a.ctl;
-    if (c->k <= 0 || threadIdx.x != 0) return;
     const int k = c->k, m = a.m;
-    for (int i = k - 1; i >= 0; --i) {
-        double t = a.g[i];
-        for (int l = i + 1; l < k; ++l) t -= a.H[(size_t)l * (m + 1) + i] * a.h[l];
-        a.h[i] = t / a.H[(size_t)i * (m + 1) + i];
+    if (k <= 0) return;
+    // R(i, l) for i <= l < k; columns of up to 64 rows fit the tile, longer
+    // cycles read R from global memory
+    const bool staged = k <= 64;
+    for (int e = threadIdx.x; e < k * k && staged; e += blockDim.x) {
+        const int i = e % k, l = e / k;
+        R[i * 65 + l] = i <= l ? a.H[(size_t)l * (m + 1) + i] : 0.0;
     }
-    for (int i = 0; i < k; ++i) a.coef[i] = a.h[i] * a.s[i];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = a.g[i];
+    __syncthreads();
+    for (int i = k - 1; i >= 0; --i) {
+        const double rii = staged ? R[i * 65 + i] : a.H[(size_t)i * (m + 1) + i];
+        const double yi = rhs[i] / rii;  // every thread reads the finished rhs[i]
+        __syncthreads();
+        if (threadIdx.x == 0) rhs[i] = yi;
+        for (int l = threadIdx.x; l < i; l += blockDim.x)
+            rhs[l] -= (staged ? R[l * 65 + i] : a.H[(size_t)i * (m + 1) + l]) * yi;
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        a.h[i] = rhs[i];
+        a.coef[i] = rhs[i] * a.s[i];
+    }
 }
 
 // t = sum_{l<k} coef_l V_l (accumulate = 1: t += that sum)
@@ -324,11 +441,12 @@ __global__ void kry_init_kernel(KryCtl *c, int maxiter, double rtol) {
     c->rel = 0.0;
 }
 
-// lanes per row: the power of two at or above the mean row length, 2..32
+// lanes per row: the smallest power of two (1..32) that leaves a lane at
+// most 13 entries of an average row
 int lanes_for(int n, int64_t nnz) {
     const double mean = n > 0 ? (double)nnz / n : 0.0;
-    int L = 2;
-    while (L < 32 && L < mean) L *= 2;
+    int L = 1;
+    while (L < 32 && 13 * L < mean) L *= 2;
     return L;
 }
 
@@ -342,6 +460,7 @@ cudaError_t spmv(cudaStream_t st, const KryArgs &a, int gate, const KryOp &op, c
     kry_spmv_kernel<LL><<<blocks, kKryThreads, 0, st>>>(a.ctl, gate, n, op.rp, op.ci, op.v, x, s, b, y, mode); \
     break;
     switch (L) {
+        case 1: SAM_KRY_SPMV(1)
         case 2: SAM_KRY_SPMV(2)
         case 4: SAM_KRY_SPMV(4)
         case 8: SAM_KRY_SPMV(8)
@@ -376,16 +495,24 @@ int enqueue_cycle(cudaStream_t st, const KryArgs &a, const KryOp &A, const KryOp
             z = u;
             zs = nullptr;
         }
-        if (!ok(spmv(st, a, kGateRun, A, z, zs, nullptr, a.V + (size_t)(j + 1) * a.n, 0))) return -1;
-        ++launches;
+        // w = A z: fused into the first Gram-Schmidt pass when a row of A
+        // fits one lane, a separate product otherwise
+        const bool fuse = lanes_for(a.n, A.nnz) == 1;
+        if (!fuse) {
+            if (!ok(spmv(st, a, kGateRun, A, z, zs, nullptr, a.V + (size_t)(j + 1) * a.n, 0))) return -1;
+            ++launches;
+        }
         for (int pass = 0; pass < 3; ++pass) {
-            kry_orth_kernel<<<nb, kKryThreads, 0, st>>>(a, j, pass);
+            if (pass == 0 && fuse)
+                kry_orth_kernel<<<nb, kKryThreads, 0, st>>>(a, j, pass, A, z, zs);
+            else
+                kry_orth_kernel<<<nb, kKryThreads, 0, st>>>(a, j, pass, KryOp(), nullptr, nullptr);
             if (!ok(cudaGetLastError())) return -1;
             ++launches;
         }
     }
     // x += M (P_0 (sum_l y_l s_l V_l))
-    kry_backsolve_kernel<<<1, 32, 0, st>>>(a);
+    kry_backsolve_kernel<<<1, kKryThreads, 0, st>>>(a);
     ++launches;
     if (!P.rp && !M.rp) {
         kry_combine_kernel<<<nb, kKryThreads, 0, st>>>(a, x, 1);
