@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-tune", action="store_true", help="default tile shapes instead of sam_tune's choice")
+    ap.add_argument("--profile-gmres", type=int, default=0, metavar="STEPS",
+                    help="profiling aid: run one GMRES solve of STEPS Arnoldi steps on the benchmark's last map "
+                         "and exit (no JSON line)")
     return ap.parse_args()
 
 
@@ -292,6 +295,22 @@ def krylov_bytes(n, nnz_ops, nnz_a, restart, its):
     return total
 
 
+def krylov_flops(n, nnz_ops, nnz_a, restart, its):
+    """Algorithmic FP64 flops of `its` Arnoldi steps of GMRES(restart) with
+    one Gram-Schmidt sweep (the textbook algorithm): per step 2 nnz for
+    each CSR product, 4 n (j+1) for the projections and the update, 3 n
+    for the norm and the scaling; per cycle the update 2 n k, the
+    preconditioner products, b - A x and its norm."""
+    step_ops = 2.0 * (sum(nnz_ops) + nnz_a)
+    total, done = 0.0, 0
+    while done < its:
+        k = min(restart, its - done)
+        total += k * (step_ops + 3.0 * n) + sum(4.0 * n * (j + 1) for j in range(k))
+        total += 2.0 * n * k + 2.0 * sum(nnz_ops) + 2.0 * nnz_a + 3.0 * n
+        done += k
+    return total
+
+
 def krylov_measurement(h, sam, torch, dev, stream, aks, a0, offs, mrp, mci, mval, n, K, world, rank):
     k = K - 1
     ident = sam.Csr(torch.arange(n + 1, dtype=torch.int32, device=dev), torch.arange(n, dtype=torch.int32, device=dev),
@@ -320,11 +339,17 @@ def krylov_measurement(h, sam, torch, dev, stream, aks, a0, offs, mrp, mci, mval
     ms = max_over_ranks(ms, world, dev)
     moved = krylov_bytes(n, (P.nnz, M.nnz), A.nnz, kw["restart"], its)
     gbs = moved / (ms * 1e-3) / 1e9
+    flops = krylov_flops(n, (P.nnz, M.nnz), A.nnz, kw["restart"], its)
     out = {"gmres": {"workload": "A_%d x = b, n = %d, GMRES(%d), rtol %g, right preconditioner M_%d (P_0 v), "
                                  "P_0 = level-2 SPAI of A_0" % (k, n, kw["restart"], kw["rtol"], k),
                      "steps_with_map": its, "steps_p0_only": res["p0"][0], "relres_estimate": rel,
                      "true_relres": true_rel, "ms": ms, "us_per_step": ms * 1e3 / max(its, 1),
                      "steps_per_s": job_value(its, world, ms), "ms_p0_only": res["p0"][3],
+                     "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": flops / (ms * 1e-3) / 1e12,
+                                  "peak": PEAK_FP64 / 1e12, "frac": flops / (ms * 1e-3) / PEAK_FP64,
+                                  "fp64_flops": flops,
+                                  "note": "FP64-instruction bound on GB300 (FP64 at 1/64 of FP32); the "
+                                          "working set is L2-resident"},
                      "algorithmic_bytes": moved, "achieved_gbs": gbs, "hbm_frac": gbs / measured_hbm_gbs(),
                      "working_set_mb": (12.0 * (A.nnz + M.nnz + P.nnz) + 8.0 * n * (kw["restart"] + 6)) / 1e6}}
     if rank == 0 and world == 1:
@@ -338,6 +363,23 @@ def krylov_measurement(h, sam, torch, dev, stream, aks, a0, offs, mrp, mci, mval
         oracle.gmres(host(A), b.cpu().numpy(), M=host(M), P0=host(P), restart=30, maxiter=60, rtol=1e-30)
         out["gmres"]["oracle_us_per_step"] = (time.perf_counter() - t) * 1e6 / 60
     return out
+
+
+def profile_gmres(h, sam, torch, dev, aks, a0, n, level, steps):
+    """One GMRES solve of `steps` Arnoldi steps on the last map of the
+    sequence (the system of the benchmark's Krylov figure), for ncu."""
+    ident = sam.Csr(torch.arange(n + 1, dtype=torch.int32, device=dev), torch.arange(n, dtype=torch.int32, device=dev),
+                    torch.ones(n, dtype=torch.float64, device=dev), n=n)
+    p2 = h.sam_pattern_build(a0, 2)
+    P = sam.Csr(*h.sam_build(a0, ident, p2, "fp64"), n=n)
+    sk = h.sam_pattern_build(aks[-1], level)
+    M = sam.Csr(*h.sam_build(aks[-1], a0, sk, "fp32r", 1), n=n)
+    b = torch.from_numpy(np.random.default_rng(9).standard_normal(n)).to(dev)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    _, its, rel = h.sam_gmres(aks[-1], b, M=M, P_0=P, restart=30, maxiter=steps, rtol=1e-30)
+    torch.cuda.synchronize()
+    print("gmres: %d steps, estimate %.3e, %.1f us per step" % (its, rel, (time.perf_counter() - t) * 1e6 / its))
 
 
 # ------------------------------------------------------------------- ours
@@ -376,6 +418,10 @@ def main():
     h = sam.Handle(stream=stream)
     aks = [sam.Csr.from_host(m, dev) for m in seq.mats]
     a0 = sam.Csr.from_host(a0h, dev)
+    if args.profile_gmres > 0:
+        profile_gmres(h, sam, torch, dev, aks, a0, n, args.level, args.profile_gmres)
+        h.close()
+        return
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def make_outputs(level):
