@@ -284,3 +284,83 @@ def random_nested_pair(n: int, density: float, seed: int, extra: float = 0.5):
         np.fill_diagonal(a, 0.0)
         np.fill_diagonal(a, np.abs(a).sum(1) + 1.0)
     return CSR.from_dense(a0), CSR.from_dense(a1)
+
+
+# ------------------------------------------------------------ CD2D stand-in
+
+
+def _cd2d_residual_jacobian(u: np.ndarray, nx: int, gamma: float, eta: float = 0.1, r: float = 1.0,
+                            s: float = 1.0):
+    """F(u) and its Jacobian for -div((eta + gamma u^2) grad u) + r u_x + s u_y = 0
+    on the unit square, second-order central differences on the nx-by-nx
+    interior grid (h = 1/(nx+1)), face coefficients k((u_P + u_Q)/2),
+    Dirichlet data u(0, y) = 0.2 + y (1 - y^2) and u = 0 on the other sides
+    (Sec. 5.1, Eq. (convDif), t = f = 0).  Unknowns in lexicographic order
+    (x fastest)."""
+    h = 1.0 / (nx + 1)
+    t = np.arange(nx + 2) * h
+    U = np.zeros((nx + 2, nx + 2))  # U[j, i] = u(x_i, y_j)
+    U[:, 0] = 0.2 + t * (1.0 - t * t)
+    U[1:-1, 1:-1] = u.reshape(nx, nx)
+    C = U[1:-1, 1:-1]
+    nb = {"E": U[1:-1, 2:], "W": U[1:-1, :-2], "N": U[2:, 1:-1], "S": U[:-2, 1:-1]}
+    kf = {d: eta + gamma * ((C + v) / 2) ** 2 for d, v in nb.items()}
+    dkf = {d: gamma * (C + v) / 2 for d, v in nb.items()}  # d k(face) / d u_P = d k / d u_Q
+    F = (-(kf["E"] * (nb["E"] - C) - kf["W"] * (C - nb["W"])) - (kf["N"] * (nb["N"] - C) - kf["S"] * (C - nb["S"]))) / h**2 \
+        + r * (nb["E"] - nb["W"]) / (2 * h) + s * (nb["N"] - nb["S"]) / (2 * h)
+    diag = (kf["E"] + kf["W"] + kf["N"] + kf["S"] - dkf["E"] * (nb["E"] - C) + dkf["W"] * (C - nb["W"])
+            - dkf["N"] * (nb["N"] - C) + dkf["S"] * (C - nb["S"])) / h**2
+    off = {"E": (-kf["E"] - dkf["E"] * (nb["E"] - C)) / h**2 + r / (2 * h),
+           "W": (-kf["W"] + dkf["W"] * (C - nb["W"])) / h**2 - r / (2 * h),
+           "N": (-kf["N"] - dkf["N"] * (nb["N"] - C)) / h**2 + s / (2 * h),
+           "S": (-kf["S"] + dkf["S"] * (C - nb["S"])) / h**2 - s / (2 * h)}
+    idx = np.arange(nx * nx).reshape(nx, nx)
+    jj, ii = np.meshgrid(np.arange(nx), np.arange(nx), indexing="ij")
+    rows, cols, vals = [idx.ravel()], [idx.ravel()], [diag.ravel()]
+    for d, (dj, di) in (("E", (0, 1)), ("W", (0, -1)), ("N", (1, 0)), ("S", (-1, 0))):
+        tj, ti = jj + dj, ii + di
+        ok = (tj >= 0) & (tj < nx) & (ti >= 0) & (ti < nx)
+        rows.append(idx[jj[ok], ii[ok]])
+        cols.append(idx[tj[ok], ti[ok]])
+        vals.append(off[d][ok])
+    J = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(nx * nx, nx * nx))
+    return F.ravel(), J
+
+
+def cd2d(nx: int = 64, nmat: int = 66, stages: int = 24) -> Sequence:
+    """Stand-in for the paper's CD2D sequence (Sec. 5.1): the Jacobians met
+    by Newton's method with a backtracking line search on the nonlinear
+    convection-diffusion problem of `_cd2d_residual_jacobian` (eta = 0.1,
+    r = s = 1), n = nx^2 = 4096 at nx = 64.  The paper takes 66 Jacobians
+    without saying how they arise (Newton from u = 0 converges in six
+    steps), so the nonlinearity is raised by natural-parameter
+    continuation: gamma = g / stages for g = 1..stages, each stage solved by
+    Newton (Armijo line search, halving) from the previous solution to
+    ||F|| <= 1e-9 ||F_stage start||; the first `nmat` Jacobians form the
+    sequence.  Every matrix has the 5-point pattern (the subset property
+    holds) and off-diagonal magnitudes between 20% and 30% of the diagonal,
+    as the paper's Sec. 5.1 reads its Table 1."""
+    import scipy.sparse.linalg as spla
+
+    u = np.zeros(nx * nx)
+    mats = []
+    for g in range(1, stages + 1):
+        gamma = g / stages
+        F, J = _cd2d_residual_jacobian(u, nx, gamma)
+        f0 = np.linalg.norm(F)
+        for _ in range(50):
+            if np.linalg.norm(F) <= 1e-9 * f0 or len(mats) >= nmat:
+                break
+            mats.append(CSR.from_scipy(J))
+            d = spla.spsolve(J.tocsc(), F)
+            nf, a = np.linalg.norm(F), 1.0
+            while a > 1e-4:
+                Ft, _ = _cd2d_residual_jacobian(u - a * d, nx, gamma)
+                if np.linalg.norm(Ft) <= (1.0 - 1e-4 * a) * nf:
+                    break
+                a /= 2
+            u = u - a * d
+            F, J = _cd2d_residual_jacobian(u, nx, gamma)
+        if len(mats) >= nmat:
+            break
+    return Sequence("cd2d_%dx%d" % (nx, nx), mats[:nmat], level=1, meta={"nx": nx, "stages": stages})
