@@ -168,6 +168,20 @@ sam_status sam_sparsify(sam_handle h, const sam_csr *A, int mode, double param, 
                         int32_t *S_col_idx, double *S_val, int64_t *S_nnz);
 
 /*
+ * sam_sparsify_batched -- sam_sparsify of K matrices of the same order n in
+ * one pass (one validation, one set of launches, one synchronisation; the
+ * sparsifications of Sec. 4 act within one matrix, so the batch is
+ * sparsified as its block-diagonal concatenation).  Outputs
+ * (caller-allocated, device or host): S_row_ptr[K][n+1], map k's row
+ * pointers relative to its own first entry; S_col_idx / S_val (nullable)
+ * with room for the sum of nnz(A_k) entries, map k's kept entries at
+ * S_offsets[k] .. S_offsets[k+1]; S_offsets (host, int64[K+1]).
+ * Synchronises the handle's stream.  Errors: those of sam_sparsify.
+ */
+sam_status sam_sparsify_batched(sam_handle h, int K, const sam_csr *A, int mode, double param, int32_t *S_row_ptr,
+                                int32_t *S_col_idx, double *S_val, int64_t *S_offsets);
+
+/*
  * sam_build -- the SAM M_k = argmin ||A_k M - A_0||_F on the pattern S
  * (Eq. (approx_map), column decomposition of Sec. 2), one least-squares
  * problem per column, written as CSR:

@@ -979,6 +979,68 @@ sam_status sam_sparsify(sam_handle h, const sam_csr *A, int mode, double param, 
     return s;
 }
 
+sam_status sam_sparsify_batched(sam_handle h, int K, const sam_csr *A, int mode, double param, int32_t *S_row_ptr,
+                                int32_t *S_col_idx, double *S_val, int64_t *S_offsets) {
+    if (!h || K < 1 || !A || !S_row_ptr || !S_col_idx || !S_offsets) return SAM_ERR_INVALID_ARG;
+    if (mode < SAM_SPARSIFY_GLOBAL || mode > SAM_SPARSIFY_LFIL || !std::isfinite(param)) return SAM_ERR_INVALID_ARG;
+    if (mode == SAM_SPARSIFY_TAU && (param < 0.0 || param > 1.0)) return SAM_ERR_INVALID_ARG;
+    if (mode == SAM_SPARSIFY_LFIL && param < 0.0) return SAM_ERR_INVALID_ARG;
+    int64_t tot = 0;
+    for (int k = 0; k < K; ++k) {
+        if (check_csr_arg(&A[k], true) != SAM_OK || A[k].n != A[0].n) return SAM_ERR_INVALID_ARG;
+        tot += A[k].nnz;
+    }
+    const int n = A[0].n;
+    const int64_t N = (int64_t)K * n;
+    if (N > INT32_MAX - 1 || tot > INT32_MAX) return SAM_ERR_INVALID_ARG;
+    cudaStream_t st = h->stream;
+    Scratch sc(h);
+    Stager sg(sc, st);
+    std::vector<DevCsr> d(K);
+    for (int k = 0; k < K; ++k) d[k] = stage_csr(sg, &A[k], true);
+    int32_t *d_rp = sg.out(S_row_ptr, (size_t)K * (n + 1));
+    int32_t *d_ci = sg.out(S_col_idx, (size_t)tot);
+    double *d_v = S_val ? sg.out(S_val, (size_t)tot) : nullptr;
+    if (sg.failed) return SAM_ERR_OOM;
+    sam_status s = validate_all(h, sc, d);
+    if (s != SAM_OK) return s;
+    // the sparsifications act within a column, a row, or on a pair of
+    // diagonal entries of the same matrix, so the block-diagonal
+    // concatenation of the batch sparsifies map by map in one pass
+    std::vector<CsrPtrs> tab(K);
+    std::vector<int64_t> off(K + 1, 0);
+    for (int k = 0; k < K; ++k) {
+        tab[k] = {d[k].rp, d[k].ci, d[k].v};
+        off[k + 1] = off[k] + d[k].nnz;
+    }
+    CsrPtrs *dtab = sc.get<CsrPtrs>(K);
+    int64_t *doff = sc.get<int64_t>(K + 1);
+    int32_t *brp = sc.get<int32_t>((size_t)N + 1), *bci = sc.get<int32_t>((size_t)tot);
+    double *bv = sc.get<double>((size_t)tot);
+    uint8_t *keep = sc.get<uint8_t>((size_t)tot);
+    int32_t *cnt = sc.get<int32_t>((size_t)N + 1);
+    int32_t *orp = sc.get<int32_t>((size_t)N + 1), *oci = sc.get<int32_t>((size_t)tot);
+    int64_t *koff = sc.get<int64_t>((size_t)K + 1);
+    if (!dtab || !doff || !brp || !bci || !bv || !keep || !cnt || !orp || !oci || !koff) return SAM_ERR_OOM;
+    cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * K, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, st);
+    if (concat_block_diag(h, K, n, dtab, doff, brp, bci, bv) != cudaSuccess ||
+        sparsify_keep(h, (int)N, tot, brp, bci, bv, mode, param, keep) != cudaSuccess ||
+        compact_kept(h, (int)N, brp, bci, bv, keep, cnt, orp, oci, d_v) != cudaSuccess ||
+        split_map_structure(h, K, n, orp, oci, d_rp, d_ci) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    gather_strided_kernel<<<(K + 1 + 127) / 128, 128, 0, st>>>(K, n, orp, koff);
+    count_launch(h);
+    if (cudaGetLastError() != cudaSuccess) return SAM_ERR_CUDA;
+    std::vector<int64_t> hoff((size_t)K + 1, 0);
+    if (cudaMemcpyAsync(hoff.data(), koff, sizeof(int64_t) * (K + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    if (sg.finish() != cudaSuccess) return SAM_ERR_CUDA;
+    s = drain_status(h);
+    for (int k = 0; k <= K; ++k) S_offsets[k] = hoff[k];
+    return s;
+}
+
 sam_status sam_residual(sam_handle h, const sam_csr *A_k, const sam_csr *M_k, const sam_csr *A_0, double *fro,
                         double *rel) {
     if (!h || check_csr_arg(A_k, true) || check_csr_arg(M_k, true) || check_csr_arg(A_0, true))

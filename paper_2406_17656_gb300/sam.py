@@ -107,6 +107,8 @@ _SIGS = [
     ("sam_refine_stats", ctypes.c_int32, [_vp, _i64p, ctypes.c_int]),
     ("sam_sparsify", ctypes.c_int32,
      [_vp, ctypes.POINTER(sam_csr), ctypes.c_int, ctypes.c_double, _vp, _vp, _vp, _i64p]),
+    ("sam_sparsify_batched", ctypes.c_int32,
+     [_vp, ctypes.c_int, ctypes.POINTER(sam_csr), ctypes.c_int, ctypes.c_double, _vp, _vp, _vp, _i64p]),
     ("sam_set_tile_variants", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("sam_get_tile_variants", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("sam_profile", ctypes.c_int32, [_vp, ctypes.c_int]),
@@ -440,6 +442,24 @@ class Handle:
                                    _addr(ci), _addr(v), ctypes.byref(nnz)), "sam_sparsify")
         k = int(nnz.value)
         return Csr(rp, ci[:k], v[:k], n=A.n)
+
+    def sam_sparsify_batched(self, As: list, mode: str, param: float) -> list:
+        """sam_sparsify of K matrices of one order in a single pass; returns
+        K device Csr views of the kept entries."""
+        import torch
+
+        K = len(As)
+        n = As[0].n
+        tot = sum(a.nnz for a in As)
+        rp = torch.empty(K * (n + 1), dtype=torch.int32, device="cuda")
+        ci = torch.empty(max(tot, 1), dtype=torch.int32, device="cuda")
+        v = torch.empty(max(tot, 1), dtype=torch.float64, device="cuda")
+        off = np.zeros(K + 1, dtype=np.int64)
+        arr = (sam_csr * K)(*[a.c() for a in As])
+        _check(load().sam_sparsify_batched(self.ptr, K, arr, SPARSIFY_MODES[mode], float(param), _addr(rp), _addr(ci),
+                                           _addr(v), off.ctypes.data_as(_i64p)), "sam_sparsify_batched")
+        return [Csr(rp[k * (n + 1):(k + 1) * (n + 1)], ci[off[k]:off[k + 1]], v[off[k]:off[k + 1]], n=n)
+                for k in range(K)]
 
     # -------------------------------------------------------------- residual
     def sam_residual(self, A_k: Csr, M_k: Csr, A_0: Csr):

@@ -99,3 +99,18 @@ def test_bad_parameters_are_rejected(sam, handle):
     for mode, param in (("tau", 1.5), ("tau", -0.1), ("lfil", -1), ("global", float("nan"))):
         with pytest.raises(sam.SamError):
             handle.sam_sparsify(A, mode, param)
+
+
+@pytest.mark.parametrize("mode,param", [("global", 0.01), ("tau", 0.8), ("lfil", 3)])
+def test_batched_sparsify_equals_per_matrix(sam, handle, mode, param):
+    """K matrices sparsified in one call: map k's kept entries, row pointers
+    and values equal, bit for bit, the single call's and the oracle's."""
+    mats = W.config2(nx=24, nmat=3).mats  # three matrices of order 576
+    out = handle.sam_sparsify_batched([sam.Csr.from_host(a) for a in mats], mode, param)
+    for a, got in zip(mats, out):
+        ip, ix, dv = oracle.sparsify(a, mode, param)
+        assert np.array_equal(got.indptr.cpu().numpy(), ip)
+        assert np.array_equal(got.indices.cpu().numpy(), ix)
+        assert np.array_equal(got.data.cpu().numpy(), dv)
+        one = handle.sam_sparsify(sam.Csr.from_host(a), mode, param)
+        assert np.array_equal(one.data.cpu().numpy(), got.data.cpu().numpy())
