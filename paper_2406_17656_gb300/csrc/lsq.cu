@@ -115,8 +115,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
                 // r = c - B m (FP64), g = B^T r (FP64), d = (R^T R)^{-1} g (FP32)
                 residual_rows<TL, false>(S, kcv, nI, ll);
                 __syncwarp();
+                {
+                    double g[JQ];
+                    C.bt_times_all(args, S, S.u.s.r, g);
 #pragma unroll
-                for (int q = 0; q < JQ; ++q) x[q] = to_tile<T>(C.bt_times(args, S, S.u.s.r, q));
+                    for (int q = 0; q < JQ; ++q) x[q] = to_tile<T>(g[q]);
+                }
                 C.normal_solve(S, x);
                 double dsq = 0.0, msq = 0.0;
 #pragma unroll
@@ -156,23 +160,38 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
                 // final residual r - B d: B d in FP32 from the rounded
                 // entries (its error, ~1e-7 |B d|, multiplies a correction
                 // that is already ~1e-6 of |c|), subtracted and squared in FP64
+                // (rows in groups of up to four, all loads of a group first)
                 double rf2 = 0.0;
+                constexpr int IQ = TL::IQ, QMAX = P >= 16 ? 4 : 2, QG = IQ < QMAX ? IQ : QMAX;
 #pragma unroll
-                for (int q = 0; q < TL::IQ; ++q) {
-                    const int i = ll + q * P;
-                    if (i < nI) {
-                        float v = 0.f;
-                        const int pb = S.u.s.rowstart[i], pe = S.u.s.rowstart[i + 1];
-                        float bv[kRowRegs];
+                for (int q0 = 0; q0 < IQ; q0 += QG) {
+                    int pb[QG], len[QG];
 #pragma unroll
-                        for (int u = 0; u < kRowRegs; ++u) bv[u] = (pb + u < pe) ? args.kcv32[S.u.s.rowent[pb + u]] : 0.f;
+                    for (int g = 0; g < QG; ++g) {
+                        const int i = ll + (q0 + g) * P;
+                        const bool live = q0 + g < IQ && i < nI;
+                        pb[g] = live ? S.u.s.rowstart[i] : 0;
+                        len[g] = live ? S.u.s.rowstart[i + 1] - pb[g] : 0;
+                    }
+                    float bv[QG][kRowRegs];
+#pragma unroll
+                    for (int g = 0; g < QG; ++g)
 #pragma unroll
                         for (int u = 0; u < kRowRegs; ++u)
-                            if (pb + u < pe) v = fmaf(bv[u], (float)S.u.s.y[S.u.s.rowcol[pb + u]], v);
-                        for (int p = pb + kRowRegs; p < pe; ++p)
-                            v = fmaf(args.kcv32[S.u.s.rowent[p]], (float)S.u.s.y[S.u.s.rowcol[p]], v);
-                        const double rfi = S.u.s.r[i] - to_f64<float>(v);
-                        rf2 = fma(rfi, rfi, rf2);
+                            bv[g][u] = (u < len[g]) ? args.kcv32[S.u.s.rowent[pb[g] + u]] : 0.f;
+#pragma unroll
+                    for (int g = 0; g < QG; ++g) {
+                        const int i = ll + (q0 + g) * P;
+                        if (q0 + g < IQ && i < nI) {
+                            float v = 0.f;
+#pragma unroll
+                            for (int u = 0; u < kRowRegs; ++u)
+                                if (u < len[g]) v = fmaf(bv[g][u], (float)S.u.s.y[S.u.s.rowcol[pb[g] + u]], v);
+                            for (int p = kRowRegs; p < len[g]; ++p)
+                                v = fmaf(args.kcv32[S.u.s.rowent[pb[g] + p]], (float)S.u.s.y[S.u.s.rowcol[pb[g] + p]], v);
+                            const double rfi = S.u.s.r[i] - to_f64<float>(v);
+                            rf2 = fma(rfi, rfi, rf2);
+                        }
                     }
                 }
                 rf2 = group_sum<P>(rf2);

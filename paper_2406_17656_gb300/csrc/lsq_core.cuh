@@ -311,26 +311,43 @@ struct SolveUpperT {  // R^T x = y, k from low to high
 };
 
 // r = c - B m in FP64 over the row-major entry lists; returns this lane's
-// partial sum of r_i^2
+// partial sum of r_i^2.  The lane's rows are taken in groups of up to four:
+// every load of a group (the first kRowRegs entries of each row) is issued
+// before the first FMA, so a group costs one round of L2 latency, not one
+// per row (the registers of the QR tile are free by now).  The FMAs of a
+// row run in the same order as a row-at-a-time loop.
 template <class TL, bool SQUARES = true>
 __device__ __forceinline__ double residual_rows(ProbSmem<TL> &S, const double *kcv, int nI, int ll) {
+    constexpr int IQ = TL::IQ, QMAX = TL::P >= 16 ? 4 : 2, QG = IQ < QMAX ? IQ : QMAX;
     double r2 = 0.0;
 #pragma unroll
-    for (int q = 0; q < TL::IQ; ++q) {
-        const int i = ll + q * TL::P;
-        if (i < nI) {
-            double ri = S.c[i];
-            const int pb = S.u.s.rowstart[i], pe = S.u.s.rowstart[i + 1];
-            // the row's first kRowRegs entries: all loads issued before use
-            double bv[kRowRegs];
+    for (int q0 = 0; q0 < IQ; q0 += QG) {
+        int pb[QG], len[QG];
 #pragma unroll
-            for (int u = 0; u < kRowRegs; ++u) bv[u] = (pb + u < pe) ? kcv[S.u.s.rowent[pb + u]] : 0.0;
+        for (int g = 0; g < QG; ++g) {
+            const int i = ll + (q0 + g) * TL::P;
+            const bool live = q0 + g < IQ && i < nI;
+            pb[g] = live ? S.u.s.rowstart[i] : 0;
+            len[g] = live ? S.u.s.rowstart[i + 1] - pb[g] : 0;
+        }
+        double bv[QG][kRowRegs];
 #pragma unroll
-            for (int u = 0; u < kRowRegs; ++u)
-                if (pb + u < pe) ri = fma(-bv[u], S.m[S.u.s.rowcol[pb + u]], ri);
-            for (int p = pb + kRowRegs; p < pe; ++p) ri = fma(-kcv[S.u.s.rowent[p]], S.m[S.u.s.rowcol[p]], ri);
-            S.u.s.r[i] = ri;
-            if (SQUARES) r2 = fma(ri, ri, r2);
+        for (int g = 0; g < QG; ++g)
+#pragma unroll
+            for (int u = 0; u < kRowRegs; ++u) bv[g][u] = (u < len[g]) ? kcv[S.u.s.rowent[pb[g] + u]] : 0.0;
+#pragma unroll
+        for (int g = 0; g < QG; ++g) {
+            const int i = ll + (q0 + g) * TL::P;
+            if (q0 + g < IQ && i < nI) {
+                double ri = S.c[i];
+#pragma unroll
+                for (int u = 0; u < kRowRegs; ++u)
+                    if (u < len[g]) ri = fma(-bv[g][u], S.m[S.u.s.rowcol[pb[g] + u]], ri);
+                for (int p = kRowRegs; p < len[g]; ++p)
+                    ri = fma(-kcv[S.u.s.rowent[pb[g] + p]], S.m[S.u.s.rowcol[pb[g] + p]], ri);
+                S.u.s.r[i] = ri;
+                if (SQUARES) r2 = fma(ri, ri, r2);
+            }
         }
     }
     return r2;
@@ -617,6 +634,37 @@ struct Column {
     __device__ __forceinline__ void normal_solve(ProbSmem<TL> &S, T (&x)[JQ]) {
         SolveUpperT<TL, 0>::run(S.u.s.R, S.u.s.dinv, x, nJ, ll, gbase);
         SolveUpper<TL, JQ - 1>::run(S.u.s.R, S.u.s.dinv, x, nJ, ll, gbase);
+    }
+
+    // (B^T v)_c in FP64 for all of the lane's columns, two at a time with
+    // every load of the pair issued before the first FMA (same FMA order as
+    // bt_times)
+    __device__ __forceinline__ void bt_times_all(const LsqArgs &args, ProbSmem<TL> &S, const double *v,
+                                                 double (&out)[JQ]) {
+        constexpr int JG = JQ < 2 ? JQ : 2;
+#pragma unroll
+        for (int q0 = 0; q0 < JQ; q0 += JG) {
+            double bv[JG][kGatherRegs];
+#pragma unroll
+            for (int g = 0; g < JG; ++g) {
+                const int q = q0 + g < JQ ? q0 + g : JQ - 1;
+                const int len = q0 + g < JQ ? clen[q] : 0;
+#pragma unroll
+                for (int u = 0; u < kGatherRegs; ++u) bv[g][u] = (u < len) ? args.kcv[colA[q] + u] : 0.0;
+            }
+#pragma unroll
+            for (int g = 0; g < JG; ++g) {
+                if (q0 + g < JQ) {
+                    const int q = q0 + g, len = clen[q];
+                    double acc = 0.0;
+#pragma unroll
+                    for (int u = 0; u < kGatherRegs; ++u)
+                        if (u < len) acc = fma(bv[g][u], v[S.locr[colB[q] + u]], acc);
+                    for (int p = kGatherRegs; p < len; ++p) acc = fma(args.kcv[colA[q] + p], v[S.locr[colB[q] + p]], acc);
+                    out[q] = acc;
+                }
+            }
+        }
     }
 
     // (B^T v)_c in FP64 for the lane's own columns; v indexed by local row
