@@ -5,8 +5,9 @@
 // A batch of K maps is one block-diagonal problem: source matrices, patterns
 // and shadow rows of map k occupy rows/columns [k n, (k+1) n) of "big"
 // arrays, so one launch per size class covers every map.  A persistent grid
-// pulls column indices from the size class's work list with an atomic
-// ticket (a bounded loop that ends when the ticket passes the item count).
+// (one resident wave) walks the size class's work list round-robin, each
+// warp loading its next column index one iteration ahead (a bounded loop
+// that ends past the item count).
 //
 // Register-tiled Householder QR.  A column problem is owned by a group of
 // P = RG x CG lanes (several groups per warp).  The dense augmented matrix
@@ -68,16 +69,23 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
     const int w0 = args.bin_off[bin];
     const int total = args.bin_off[bin + 1] - w0;
     const int32_t *work = args.work + w0;
-    int32_t *ticket = args.ticket + bin;
     const double *kcv = args.kcv;
 
+    // static round-robin over the resident warps (columns of a size class
+    // cost about the same): the next work item is known, and its column
+    // index is loaded one iteration ahead, so no atomic ticket and no work
+    // lookup sit at the head of an iteration's dependent loads
+    const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock * PPW;
+    int64_t base = ((int64_t)blockIdx.x * kWarpsPerBlock + warp) * PPW;
+    int jj_next = (base + lane / P < total) ? work[base + lane / P] : 0;
     for (int iter = 0; iter < (1 << 30); ++iter) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(ticket, PPW);
-        base = shfl(base, 0);
         if (base >= total) break;
+        const int item = (int)(base + lane / P);
+        const int jj_cur = jj_next;
+        base += stride;
+        jj_next = (base + lane / P < total) ? work[base + lane / P] : 0;
         Column<TL> C;
-        C.begin(args, base + lane / P, total, work);
+        C.begin_at(args, item, total, jj_cur);
         const int ll = C.ll;
         C.gather(args, S);
         T a[RS][CS];

@@ -403,13 +403,18 @@ struct Column {
     double out2;
 
     __device__ __forceinline__ void begin(const LsqArgs &args, int item, int total, const int32_t *work) {
+        begin_at(args, item, total, item < total ? work[item] : 0);
+    }
+
+    // as begin, with the work item's column (jj_item) already loaded
+    __device__ __forceinline__ void begin_at(const LsqArgs &args, int item, int total, int jj_item) {
         const int lane = threadIdx.x & 31;
         ll = lane % P;
         gbase = lane - ll;
         rg = ll % RG;
         cg = ll / RG;
         valid = item < total;
-        jj = valid ? work[item] : 0;  // column of the block-diagonal batch
+        jj = valid ? jj_item : 0;  // column of the block-diagonal batch
         const int kmap = jj / args.n;
         jl = jj - kmap * args.n;  // column of A_0
         roff = kmap * args.n;     // row offset of this map
