@@ -34,17 +34,22 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) adjoint_kernel(LsqArgs ar
     const int w0 = args.bin_off[bin];
     const int total = args.bin_off[bin + 1] - w0;
     const int32_t *work = args.work + w0;
-    int32_t *ticket = args.ticket + bin;
     const double *kcv = args.kcv;
     const double rho = args.resid_weight;
 
+    // static round-robin over the resident warps, next column index loaded
+    // one iteration ahead (as in the forward kernel)
+    const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock * PPW;
+    int64_t base = ((int64_t)blockIdx.x * kWarpsPerBlock + warp) * PPW;
+    int jj_next = (base + lane / P < total) ? work[base + lane / P] : 0;
     for (int iter = 0; iter < (1 << 30); ++iter) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(ticket, PPW);
-        base = shfl(base, 0);
         if (base >= total) break;
+        const int item = (int)(base + lane / P);
+        const int jj_cur = jj_next;
+        base += stride;
+        jj_next = (base + lane / P < total) ? work[base + lane / P] : 0;
         Column<TL> C;
-        C.begin(args, base + lane / P, total, work);
+        C.begin_at(args, item, total, jj_cur);
         const int ll = C.ll;
         C.gather(args, S);
         T a[RS][CS];
@@ -176,8 +181,7 @@ cudaError_t launch_one(sam_handle h, const LsqArgs &a, int bin) {
 }  // namespace
 
 cudaError_t launch_adjoint(sam_handle h, int precision, const LsqArgs &args) {
-    cudaError_t e = cudaMemsetAsync(args.ticket, 0, sizeof(int32_t) * kNumBins, handle_stream(h));
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     if (precision == SAM_FP64) {
         if ((e = launch_one<D0, true>(h, args, 0)) != cudaSuccess) return e;
         if ((e = launch_one<D1, true>(h, args, 1)) != cudaSuccess) return e;

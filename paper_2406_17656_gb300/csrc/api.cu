@@ -830,12 +830,12 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     int32_t *ish = sc.get<int32_t>((size_t)N * kICap), *icnt = sc.get<int32_t>((size_t)N);
     uint8_t *bin = sc.get<uint8_t>((size_t)N);
     int32_t *work = sc.get<int32_t>((size_t)N);
-    int32_t *bin_off = sc.get<int32_t>(kNumBins + 1), *tickets = sc.get<int32_t>(kNumBins);
+    int32_t *bin_off = sc.get<int32_t>(kNumBins + 1);
     if (!d_st) d_st = sc.get<int32_t>((size_t)N);
     if (!d_r2) d_r2 = sc.get<double>((size_t)N);
     uint8_t *lrow = sc.get<uint8_t>((size_t)N * kLCap);
     uint8_t *zloc = sc.get<uint8_t>((size_t)N * kZCap);
-    if (!ish || !icnt || !bin || !work || !bin_off || !tickets || !d_st || !d_r2 || !lrow || !zloc)
+    if (!ish || !icnt || !bin || !work || !bin_off || !d_st || !d_r2 || !lrow || !zloc)
         return SAM_ERR_OOM;
     // shadow rows, size classes, work list
     ShadowTarget tg;
@@ -881,7 +881,6 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     a.colstat = d_st;
     a.work = work;
     a.bin_off = bin_off;
-    a.ticket = tickets;
     a.refine_steps = refine_steps;
     const bool autoref = precision == SAM_FP32_REFINE && refine_steps < 0;
     uint8_t *bin2 = nullptr;
@@ -1191,12 +1190,12 @@ sam_status backward_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr 
     int32_t *colstat = sc.get<int32_t>((size_t)N);
     int64_t *nbcnt = sc.get<int64_t>((size_t)N + 1), *dB_off = sc.get<int64_t>((size_t)N + 1);
     int32_t *work = sc.get<int32_t>((size_t)N);
-    int32_t *bin_off = sc.get<int32_t>(kNumBins + 1), *tickets = sc.get<int32_t>(kNumBins);
+    int32_t *bin_off = sc.get<int32_t>(kNumBins + 1);
     int64_t *dbase = sc.get<int64_t>((size_t)mtot);
     double *dzval = sc.get<double>((size_t)zn), *dak_csc = sc.get<double>((size_t)kn);
     uint8_t *lrow = sc.get<uint8_t>((size_t)N * kLCap);
     uint8_t *zloc = sc.get<uint8_t>((size_t)N * kZCap);
-    if (!ish || !icnt || !bin || !colstat || !nbcnt || !dB_off || !work || !bin_off || !tickets || !dbase || !dzval ||
+    if (!ish || !icnt || !bin || !colstat || !nbcnt || !dB_off || !work || !bin_off || !dbase || !dzval ||
         !dak_csc || !lrow || !zloc)
         return SAM_ERR_OOM;
     ShadowTarget tg;
@@ -1249,7 +1248,6 @@ sam_status backward_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr 
     a.colstat = colstat;
     a.work = work;
     a.bin_off = bin_off;
-    a.ticket = tickets;
     a.refine_steps = refine_steps;
     a.dmval = d_dm;
     a.resid_weight = resid_weight;
@@ -1524,7 +1522,7 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
     int32_t *ish = keep.get<int32_t>((size_t)N * kICap), *icnt = keep.get<int32_t>((size_t)N);
     uint8_t *bin = tmp.get<uint8_t>((size_t)N);
     int32_t *work = keep.get<int32_t>((size_t)N);
-    int32_t *bin_off = keep.get<int32_t>(kNumBins + 1), *tickets = keep.get<int32_t>(kNumBins);
+    int32_t *bin_off = keep.get<int32_t>(kNumBins + 1);
     int32_t *d_st = col_status ? col_status : keep.get<int32_t>((size_t)N);
     double *d_r2 = res2 ? res2 : keep.get<double>((size_t)N);
     uint8_t *lrow = keep.get<uint8_t>((size_t)N * kLCap);
@@ -1557,7 +1555,7 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
     }
     const double **d_kptr = keep.get<const double *>(K), **d_zptr = keep.get<const double *>(NT);
     int64_t *d_koff = keep.get<int64_t>(K + 1), *d_zoff = keep.get<int64_t>(NT + 1);
-    if (!ish || !icnt || !bin || !work || !bin_off || !tickets || !d_st || !d_r2 || !lrow ||
+    if (!ish || !icnt || !bin || !work || !bin_off || !d_st || !d_r2 || !lrow ||
         (precision == SAM_FP32_REFINE && (!kcv32 || !zcv32)) || (fro2 && !seg_work) || !d_kptr || !d_zptr ||
         !d_koff || !d_zoff)
         return SAM_ERR_OOM;
@@ -1604,7 +1602,6 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
     a.colstat = d_st;
     a.work = work;
     a.bin_off = bin_off;
-    a.ticket = tickets;
     a.refine_steps = refine_steps;
     a.refine_used = refine_used;
     cudaStream_t cs = nullptr;

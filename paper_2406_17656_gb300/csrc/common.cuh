@@ -71,7 +71,6 @@ struct LsqArgs {
     int32_t *colstat;            // per-column status
     const int32_t *work;         // columns grouped by size class
     const int32_t *bin_off;      // [kNumBins+1] offsets into work
-    int32_t *ticket;             // [kNumBins] persistent-loop counters (zeroed before launch)
     int refine_steps;            // < 0: automatic (up to kAutoSteps, FP64 fallback)
     uint8_t *refine_used;        // automatic mode: steps taken per column, kAutoSteps+1 = FP64 fallback
     int zbig;                    // 1: one target per map, stored block-diagonally

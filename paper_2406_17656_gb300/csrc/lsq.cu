@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
 
     // static round-robin over the resident warps (columns of a size class
     // cost about the same): the next work item is known, and its column
-    // index is loaded one iteration ahead, so no atomic ticket and no work
+    // index is loaded one iteration ahead, so no atomic counter and no work
     // lookup sit at the head of an iteration's dependent loads
     const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock * PPW;
     int64_t base = ((int64_t)blockIdx.x * kWarpsPerBlock + warp) * PPW;
@@ -263,8 +263,7 @@ cudaError_t launch_one(sam_handle h, const LsqArgs &a, int bin) {
 }  // namespace
 
 cudaError_t launch_lsq(sam_handle h, int precision, const LsqArgs &args) {
-    cudaError_t e = cudaMemsetAsync(args.ticket, 0, sizeof(int32_t) * kNumBins, handle_stream(h));
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     if (precision == SAM_FP64) {
         if ((e = launch_one<D0, true>(h, args, 0)) != cudaSuccess) return e;
         if ((e = launch_one<D1, true>(h, args, 1)) != cudaSuccess) return e;
