@@ -54,6 +54,7 @@ struct PatternGroup {
     int32_t *csr_pos = nullptr;              // CSC entry -> CSR position
     std::vector<int64_t> off;                // per-map nnz prefix [K+1]
     bool symmetric = false;                  // every map's pattern is structurally symmetric
+    bool shared = false;                     // every map has the same pattern (built once, replicated)
 };
 }  // namespace
 
@@ -254,10 +255,71 @@ sam_status drain_status(sam_handle h) {
     return s;
 }
 
+// flag[0] = 1 when some matrix k in [1, K) has a structure (row pointers,
+// column indices) different from matrix 0's; nnz equal (checked on the host)
+__global__ void structure_differs_kernel(int n, const CsrPtrs *mats, int64_t nnz, int32_t *flag) {
+    const int k = blockIdx.y + 1;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const CsrPtrs a = mats[0], b = mats[k];
+    bool diff = false;
+    if (t <= n) diff = a.rp[t] != b.rp[t];
+    if (t < nnz) diff = diff || a.ci[t] != b.ci[t];
+    if (diff) *flag = 1;
+}
+
+// Whether every matrix of each range [b, e) of ms has the same structure as
+// the range's first (exact comparison on the device).  Launched into
+// flags[r] (device, zeroed by the caller); ranges whose nnz differ on the
+// host are marked at once in *differ_host.
+cudaError_t launch_structure_checks(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms,
+                                    const std::vector<std::pair<int, int>> &ranges, int32_t *flags,
+                                    std::vector<char> *differ_host) {
+    differ_host->assign(ranges.size(), 0);
+    for (size_t r = 0; r < ranges.size(); ++r) {
+        const int b = ranges[r].first, e = ranges[r].second;
+        if (e - b < 2) continue;
+        bool eq = true;
+        for (int k = b + 1; k < e; ++k) eq = eq && ms[k].n == ms[b].n && ms[k].nnz == ms[b].nnz;
+        if (!eq) {
+            (*differ_host)[r] = 1;
+            continue;
+        }
+        std::vector<CsrPtrs> tab;
+        for (int k = b; k < e; ++k) tab.push_back({ms[k].rp, ms[k].ci, nullptr});
+        CsrPtrs *dtab = sc.get<CsrPtrs>(tab.size());
+        if (!dtab) return cudaErrorMemoryAllocation;
+        cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * tab.size(), cudaMemcpyHostToDevice, h->stream);
+        const int64_t cnt = std::max<int64_t>((int64_t)ms[b].n + 1, ms[b].nnz);
+        dim3 grid((unsigned)((cnt + 255) / 256), (unsigned)(e - b - 1));
+        structure_differs_kernel<<<grid, 256, 0, h->stream>>>(ms[b].n, dtab, ms[b].nnz, flags + r);
+        count_launch(h);
+    }
+    return cudaGetLastError();
+}
+
 // Validates the CSR structures of equal-order matrices on the device;
 // synchronises once.  Nothing reads an unvalidated structure before this.
-sam_status validate_all(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms, std::vector<char> *sym = nullptr) {
+// same (nullable): for each range [b, e) of ms in same_ranges, whether all
+// its matrices share one structure, found in the same synchronisation (with
+// trusted inputs: one synchronisation for that alone).
+sam_status validate_all(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms, std::vector<char> *sym = nullptr,
+                        const std::vector<std::pair<int, int>> *same_ranges = nullptr,
+                        std::vector<char> *same = nullptr) {
     if (sym) sym->assign(ms.size(), 0);  // unknown (trusted inputs): treated as not symmetric
+    const size_t R = (same_ranges && same) ? same_ranges->size() : 0;
+    if (same) same->assign(R, 0);
+    if (((h->flags & SAM_FLAG_TRUSTED) || ms.empty()) && R > 0) {
+        int32_t *flags = sc.get<int32_t>(R);
+        if (!flags) return SAM_ERR_OOM;
+        cudaMemsetAsync(flags, 0, sizeof(int32_t) * R, h->stream);
+        std::vector<char> differ;
+        if (launch_structure_checks(h, sc, ms, *same_ranges, flags, &differ) != cudaSuccess) return SAM_ERR_CUDA;
+        std::vector<int32_t> hf(R, 0);
+        cudaMemcpyAsync(hf.data(), flags, sizeof(int32_t) * R, cudaMemcpyDeviceToHost, h->stream);
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SAM_ERR_CUDA;
+        for (size_t r = 0; r < R; ++r) (*same)[r] = !differ[r] && !hf[r];
+        return SAM_OK;
+    }
     if ((h->flags & SAM_FLAG_TRUSTED) || ms.empty()) return SAM_OK;
     const int K = (int)ms.size();
     std::vector<CsrPtrs> tab(K);
@@ -268,27 +330,37 @@ sam_status validate_all(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms
     }
     CsrPtrs *dtab = sc.get<CsrPtrs>(K);
     int64_t *dnz = sc.get<int64_t>(K);
-    int32_t *flag = sc.get<int32_t>((size_t)K + 1);  // [0] status, [1 + k] matrix k not symmetric
+    // [0] status, [1 + k] matrix k not symmetric, [1 + K + r] range r not of one structure
+    int32_t *flag = sc.get<int32_t>((size_t)K + 1 + R);
     if (!dtab || !dnz || !flag) return SAM_ERR_OOM;
     cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * K, cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(dnz, nz.data(), sizeof(int64_t) * K, cudaMemcpyHostToDevice, h->stream);
-    cudaMemsetAsync(flag, 0, sizeof(int32_t) * ((size_t)K + 1), h->stream);
+    cudaMemsetAsync(flag, 0, sizeof(int32_t) * ((size_t)K + 1 + R), h->stream);
     int32_t *asym = sym ? flag + 1 : nullptr;
     // matrices of different order (the residual call) are validated one by one
-    bool same = true;
-    for (auto &m : ms) same &= (m.n == ms[0].n);
-    if (same) {
+    bool same_order = true;
+    for (auto &m : ms) same_order &= (m.n == ms[0].n);
+    if (same_order) {
         if (validate_csr_batch(h, K, ms[0].n, dtab, dnz, flag, asym) != cudaSuccess) return SAM_ERR_CUDA;
     } else {
         for (int k = 0; k < K; ++k)
             if (validate_csr_batch(h, 1, ms[k].n, dtab + k, dnz + k, flag, asym ? asym + k : nullptr) != cudaSuccess)
                 return SAM_ERR_CUDA;
     }
-    std::vector<int32_t> hf((size_t)K + 1, 0);
-    cudaMemcpyAsync(hf.data(), flag, sizeof(int32_t) * (sym ? (size_t)K + 1 : 1), cudaMemcpyDeviceToHost, h->stream);
+    // the comparison reads rp[0..n] and ci[0..nnz) of each matrix, inside
+    // the sizes the caller declared (nothing it reads is used as an index),
+    // so it shares the synchronisation; its result counts only when the
+    // validation passed
+    std::vector<char> differ;
+    if (R > 0 && launch_structure_checks(h, sc, ms, *same_ranges, flag + 1 + K, &differ) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    std::vector<int32_t> hf((size_t)K + 1 + R, 0);
+    cudaMemcpyAsync(hf.data(), flag, sizeof(int32_t) * ((size_t)K + 1 + R), cudaMemcpyDeviceToHost, h->stream);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SAM_ERR_CUDA;
     if (sym && hf[0] == 0)
         for (int k = 0; k < K; ++k) (*sym)[k] = hf[(size_t)k + 1] == 0;
+    if (hf[0] == 0)
+        for (size_t r = 0; r < R; ++r) (*same)[r] = !differ[r] && !hf[(size_t)K + 1 + r];
     return hf[0] ? (sam_status)hf[0] : SAM_OK;
 }
 
@@ -365,6 +437,85 @@ sam_status group_finish(sam_handle h, int K, int n, int32_t *jcp, int32_t *jri, 
         return fail(SAM_ERR_CUDA);
     pool_free(h, perm);
     pool_free(h, doff);
+    *out = g;
+    return cudaGetLastError() == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
+}
+
+// dst[k n + t] = src[t] + k step for t < n, k < K; dst[K n] = K step
+__global__ void replicate_offsets_kernel(int K, int n, const int32_t *src, int32_t step, int32_t *dst) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (t < n) dst[(int64_t)k * n + t] = src[t] + k * step;
+    if (k == K - 1 && t == 0) dst[(int64_t)K * n] = K * step;
+}
+
+// dst[k m + e] = src[e] + k shift for e < m, k < K
+__global__ void replicate_shifted_kernel(int64_t m, const int32_t *src, int32_t shift, int32_t *dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (e < m) dst[(int64_t)k * m + e] = src[e] + k * shift;
+}
+
+// a[k n + t] = a[t] for 1 <= k < K (the per-column results of map 0)
+template <typename T>
+__global__ void replicate_cols_kernel(int64_t n, T *a) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y + 1;
+    if (t < n) a[(int64_t)k * n + t] = a[t];
+}
+
+template <typename T>
+cudaError_t replicate_cols(sam_handle h, int K, int64_t n, T *a) {
+    if (K < 2 || n == 0 || !a) return cudaSuccess;
+    dim3 grid((unsigned)((n + 255) / 256), (unsigned)(K - 1));
+    replicate_cols_kernel<T><<<grid, 256, 0, h->stream>>>(n, a);
+    count_launch(h);
+    return cudaGetLastError();
+}
+
+// A group of K maps that all have the pattern of g1 (a one-map group): its
+// CSC pattern, map CSR structure and CSC -> CSR positions replicated with
+// each map's offsets.  g1 is released.
+sam_status group_replicate(sam_handle h, PatternGroup *g1, int K, PatternGroup **out) {
+    const int n = g1->n;
+    const int64_t m = g1->off[1];
+    const int64_t N = (int64_t)K * n, tot = (int64_t)K * m;
+    if (N > INT32_MAX - 1 || tot > INT32_MAX) {
+        group_release(g1);
+        return SAM_ERR_INVALID_ARG;
+    }
+    PatternGroup *g = new (std::nothrow) PatternGroup;
+    if (!g) {
+        group_release(g1);
+        return SAM_ERR_OOM;
+    }
+    g->h = h;
+    g->refs = 1;
+    g->K = K;
+    g->n = n;
+    g->symmetric = g1->symmetric;
+    g->shared = true;
+    g->jcp = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)N + 1));
+    g->jri = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)(tot ? tot : 1));
+    g->mrp = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)N + 1));
+    g->mci = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)(tot ? tot : 1));
+    g->csr_pos = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)(tot ? tot : 1));
+    if (!g->jcp || !g->jri || !g->mrp || !g->mci || !g->csr_pos) {
+        group_release(g);
+        group_release(g1);
+        return SAM_ERR_OOM;
+    }
+    const dim3 gn((unsigned)((n + 255) / 256 > 0 ? (n + 255) / 256 : 1), (unsigned)K);
+    const dim3 gm((unsigned)((m + 255) / 256 > 0 ? (m + 255) / 256 : 1), (unsigned)K);
+    replicate_offsets_kernel<<<gn, 256, 0, h->stream>>>(K, n, g1->jcp, (int32_t)m, g->jcp);
+    replicate_offsets_kernel<<<gn, 256, 0, h->stream>>>(K, n, g1->mrp, (int32_t)m, g->mrp);
+    replicate_shifted_kernel<<<gm, 256, 0, h->stream>>>(m, g1->jri, n, g->jri);
+    replicate_shifted_kernel<<<gm, 256, 0, h->stream>>>(m, g1->mci, n, g->mci);
+    replicate_shifted_kernel<<<gm, 256, 0, h->stream>>>(m, g1->csr_pos, (int32_t)m, g->csr_pos);
+    count_launch(h, 5);
+    g->off.resize((size_t)K + 1);
+    for (int k = 0; k <= K; ++k) g->off[k] = (int64_t)k * m;
+    group_release(g1);  // stream-ordered frees: the copies above read g1 first
     *out = g;
     return cudaGetLastError() == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
 }
@@ -586,11 +737,35 @@ sam_status sam_pattern_build_batched(sam_handle h, int K, const sam_csr *A, int 
     std::vector<DevCsr> d(K);
     for (int k = 0; k < K; ++k) d[k] = stage_csr(sg, &A[k], false);
     if (sg.failed) return SAM_ERR_OOM;
-    std::vector<char> symv;
-    sam_status s = validate_all(h, sc, d, &symv);
+    std::vector<char> symv, same;
+    const std::vector<std::pair<int, int>> whole{{0, K}};
+    sam_status s = validate_all(h, sc, d, &symv, K > 1 ? &whole : nullptr, &same);
     if (s != SAM_OK) return s;
     bool sym = true;
     for (char c : symv) sym = sym && c;
+    if (K > 1 && same[0]) {
+        // one structure for the whole sequence (the paper's setting, Sec. 2):
+        // the pattern of map 0, replicated for every map
+        int32_t *kcp = sc.get<int32_t>((size_t)n + 1), *kri = sc.get<int32_t>((size_t)d[0].nnz);
+        if (!kcp || !kri) return SAM_ERR_OOM;
+        if (csr_to_csc(h, n, d[0].nnz, d[0].rp, d[0].ci, nullptr, kcp, kri, nullptr, nullptr, sym) != cudaSuccess)
+            return SAM_ERR_CUDA;
+        int32_t *jcp = nullptr, *jri = nullptr;
+        int64_t nnz = 0;
+        s = level_pattern(h, n, kcp, kri, d[0].nnz, level, &jcp, &jri, &nnz);
+        if (s != SAM_OK) return s;
+        PatternGroup *g1 = nullptr, *g = nullptr;
+        s = group_finish(h, 1, n, jcp, jri, nnz, &g1, sym);
+        if (s != SAM_OK) return s;
+        s = group_replicate(h, g1, K, &g);
+        if (s != SAM_OK) return s;
+        s = make_patterns(g, out);
+        if (s != SAM_OK) {
+            group_release(g);
+            return s;
+        }
+        return drain_status(h);
+    }
     // block-diagonal structure of the batch, then its CSC
     std::vector<CsrPtrs> tab(K);
     std::vector<int64_t> off(K + 1, 0);
@@ -798,13 +973,16 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     double *d_r2 = res2 ? sg.out(res2, (size_t)N) : nullptr;
     if (sg.failed) return SAM_ERR_OOM;
     bool ksym = true, zsym = true;  // structurally symmetric sources / targets
+    bool one_structure = false;     // every source, every target: one structure each
     {
         std::vector<DevCsr> all(ak);
         all.insert(all.end(), zs.begin(), zs.end());
-        std::vector<char> symv;
-        sam_status s = validate_all(h, sc, all, &symv);
+        std::vector<char> symv, same;
+        const std::vector<std::pair<int, int>> ranges{{0, K}, {K, K + NT}};
+        sam_status s = validate_all(h, sc, all, &symv, K > 1 ? &ranges : nullptr, &same);
         if (s != SAM_OK) return s;
         for (size_t q = 0; q < symv.size(); ++q) (q < ak.size() ? ksym : zsym) &= symv[q] != 0;
+        one_structure = K > 1 && same[0] && same[1];
     }
     PatternGroup *g = nullptr;
     bool temp = false;
@@ -819,6 +997,11 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
             if (temp) group_release(g);
         }
     } guard{g, temp};
+    // shadow rows, local rows and size classes depend on the structures
+    // alone: with one source structure, one target structure and one
+    // pattern for all maps, map 0's are computed and shared
+    const bool shared = one_structure && g->shared;
+    const int NS = shared ? n : (int)N;  // columns whose shadow data is computed
     // target(s) and sources as CSC with values
     int32_t *zcp = nullptr, *zri = nullptr, *kcp = nullptr, *kri = nullptr;
     double *zcv = nullptr, *kcv = nullptr;
@@ -844,7 +1027,10 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     tg.zbig = NT > 1 ? 1 : 0;
     tg.n = n;
     tg.zloc = zloc;
-    if (shadow_and_bins(h, (int)N, kcp, kri, g->jcp, g->jri, ish, icnt, bin, d_st, nullptr, lrow, tg) != cudaSuccess)
+    if (shadow_and_bins(h, NS, kcp, kri, g->jcp, g->jri, ish, icnt, bin, d_st, nullptr, lrow, tg) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    if (shared && (replicate_cols(h, K, n, icnt) != cudaSuccess || replicate_cols(h, K, n, bin) != cudaSuccess ||
+                   replicate_cols(h, K, n, d_st) != cudaSuccess))
         return SAM_ERR_CUDA;
     if (build_work_list(h, (int)N, bin, work, bin_off) != cudaSuccess) return SAM_ERR_CUDA;
     cudaMemsetAsync(d_v, 0, sizeof(double) * (size_t)total_nnz, st);
@@ -875,6 +1061,7 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     a.zcv = zcv;
     a.zbig = NT > 1 ? 1 : 0;
     a.zloc = zloc;
+    a.shadow_shared = shared ? 1 : 0;
     a.csr_pos = g->csr_pos;
     a.mval = d_v;
     a.colres = d_r2;
@@ -1161,13 +1348,16 @@ sam_status backward_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr 
     double *d_dmr = dM_resid ? sg.out(dM_resid, (size_t)mtot) : nullptr;
     if (sg.failed) return SAM_ERR_OOM;
     bool ksym = true, zsym = true;  // structurally symmetric sources / targets
+    bool one_structure = false;     // every source, every target: one structure each
     {
         std::vector<DevCsr> all(ak);
         all.insert(all.end(), zs.begin(), zs.end());
-        std::vector<char> symv;
-        sam_status s = validate_all(h, sc, all, &symv);
+        std::vector<char> symv, same;
+        const std::vector<std::pair<int, int>> ranges{{0, K}, {K, 2 * K}};
+        sam_status s = validate_all(h, sc, all, &symv, K > 1 ? &ranges : nullptr, &same);
         if (s != SAM_OK) return s;
         for (size_t q = 0; q < symv.size(); ++q) (q < ak.size() ? ksym : zsym) &= symv[q] != 0;
+        one_structure = K > 1 && same[0] && same[1];
     }
     PatternGroup *g = nullptr;
     bool temp = false;
@@ -1180,6 +1370,9 @@ sam_status backward_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr 
             if (temp) group_release(g);
         }
     } guard{g, temp};
+    // map 0's shadow data serves every map when all structures agree
+    const bool shared = one_structure && g->shared;
+    const int NS = shared ? n : (int)N;
     int32_t *zcp = nullptr, *zri = nullptr, *zperm = nullptr, *kcp = nullptr, *kri = nullptr, *kperm = nullptr;
     double *zcv = nullptr, *kcv = nullptr;
     int64_t zn = 0, kn = 0;
@@ -1204,8 +1397,12 @@ sam_status backward_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr 
     tg.zbig = 1;
     tg.n = n;
     tg.zloc = zloc;
-    if (shadow_and_bins(h, (int)N, kcp, kri, g->jcp, g->jri, ish, icnt, bin, colstat, nbcnt, lrow, tg) != cudaSuccess ||
-        exclusive_scan_i64(h, nbcnt, dB_off, N) != cudaSuccess ||
+    if (shadow_and_bins(h, NS, kcp, kri, g->jcp, g->jri, ish, icnt, bin, colstat, nbcnt, lrow, tg) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    if (shared && (replicate_cols(h, K, n, icnt) != cudaSuccess || replicate_cols(h, K, n, bin) != cudaSuccess ||
+                   replicate_cols(h, K, n, colstat) != cudaSuccess || replicate_cols(h, K, n, nbcnt) != cudaSuccess))
+        return SAM_ERR_CUDA;
+    if (exclusive_scan_i64(h, nbcnt, dB_off, N) != cudaSuccess ||
         build_work_list(h, (int)N, bin, work, bin_off) != cudaSuccess)
         return SAM_ERR_CUDA;
     int64_t nbtot = 0;
@@ -1241,6 +1438,7 @@ sam_status backward_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr 
     a.zcv = zcv;
     a.zbig = 1;
     a.zloc = zloc;
+    a.shadow_shared = shared ? 1 : 0;
     a.csr_pos = g->csr_pos;
     a.mval = const_cast<double *>(d_m);
     a.kcv32 = kcv32;

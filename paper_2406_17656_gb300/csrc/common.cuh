@@ -65,6 +65,9 @@ struct LsqArgs {
                                  // or the block-diagonal of one target per map (order N; zbig = 1)
     const double *zcv;
     const float *zcv32;          // the same values rounded to FP32
+    int shadow_shared;           // 1: every map has the same source, target and pattern structure, and
+                                 // ish / lrow / zloc hold map 0's columns only (indexed by the column
+                                 // within its map); 0: one entry per column of the batch
     const int32_t *csr_pos;      // pattern CSC entry -> map CSR position
     double *mval;                // map values, CSR order of the block-diagonal map
     double *colres;              // per-column residual^2 (+ out-of-shadow part)

@@ -397,7 +397,7 @@ struct Column {
 
     int ll, rg, cg, gbase;
     bool valid;
-    int jj, jl, roff, zro, jb, nJ, nI, zb, ze, nB, kmax;
+    int jj, jl, js, roff, zro, jb, nJ, nI, zb, ze, nB, kmax;  // js: column of the shadow data
     int status;
     int colA[JQ], clen[JQ], colB[JQ];
     double out2;
@@ -417,6 +417,7 @@ struct Column {
         jj = valid ? jj_item : 0;  // column of the block-diagonal batch
         const int kmap = jj / args.n;
         jl = jj - kmap * args.n;  // column of A_0
+        js = args.shadow_shared ? jl : jj;
         roff = kmap * args.n;     // row offset of this map
         // target column: A_0(:, jl) shifted by roff, or column jj of the
         // block-diagonal targets (rows already global)
@@ -458,7 +459,7 @@ struct Column {
         // the precomputed local rows
         const bool need_I = !args.zloc || ze - zb > kZCap;
         for (int i = ll; i < MAXI; i += P) {
-            if (need_I) S.I[i] = (i < nI) ? args.ish[(int64_t)jj * kICap + i] : INT_MAX;
+            if (need_I) S.I[i] = (i < nI) ? args.ish[(int64_t)js * kICap + i] : INT_MAX;
             S.mask[i] = 0u;
             S.c[i] = 0.0;
         }
@@ -475,7 +476,7 @@ struct Column {
             // local shadow rows of the entries, computed with the shadow rows
             // (read straight from global memory: staging them through shared
             // memory first measured 2x slower in the FP64 kernel)
-            const uint8_t *lr = args.lrow + (int64_t)jj * kLCap + colB[q];
+            const uint8_t *lr = args.lrow + (int64_t)js * kLCap + colB[q];
             // the first kGatherRegs entries: all loads issued before any use
             {
                 int rows[kGatherRegs];
@@ -539,7 +540,7 @@ struct Column {
     // column, -1 outside the shadow
     __device__ __forceinline__ int target_row(const LsqArgs &args, const ProbSmem<TL> &S, int tz, int t) {
         if (args.zloc && tz < kZCap) {
-            const int z = args.zloc[(int64_t)jj * kZCap + tz];
+            const int z = args.zloc[(int64_t)js * kZCap + tz];
             if (z == kZOutside) return -1;
             if (z >= nI) {  // impossible for a consistent shadow: never index out of bounds
                 status = kStUnsupported;

@@ -56,3 +56,59 @@ def test_one_pattern_serves_a_fixed_sparsity_sequence(sam, case):
         assert np.array_equal(ci2[o2[k]:o2[k + 1]].cpu().numpy(), ix)
         got = v2[o2[k]:o2[k + 1]].cpu().numpy()
         assert np.linalg.norm(got - dv) <= 1e-10 * np.linalg.norm(dv)
+
+
+def _drop_pair(a, i, j):
+    """a with the entries (i, j) and (j, i) removed (structure changes, the
+    matrix stays structurally symmetric)."""
+    d = a.dense()
+    d[i, j] = d[j, i] = 0.0
+    return W.CSR.from_dense(d)
+
+
+@pytest.mark.parametrize("level", [1, 2])
+def test_one_differing_structure_disables_sharing(sam, level):
+    """Structure work is shared only when every matrix of the batch has the
+    same structure: one matrix with two entries fewer gets its own pattern,
+    shadow rows and map, each equal to the oracle's."""
+    seq = W.config2(nx=20, nmat=3)
+    mats = list(seq.mats)
+    mats[1] = _drop_pair(mats[1], 45, 46)
+    n = mats[0].n
+    with sam.Handle() as h:
+        aks = [sam.Csr.from_host(m) for m in mats]
+        pats = h.sam_pattern_build_batched(aks, level)
+        offs, rp, ci, v, fro = h.sam_build_batched(aks, aks[0], pats, "fp32r", 1, want_fro=True)
+        for k, m in enumerate(mats):
+            cp, ri = oracle.pattern(m, level)
+            assert pats[k].nnz == int(cp[-1])
+            assert np.array_equal(pats[k].colptr().cpu().numpy(), cp)
+            assert np.array_equal(pats[k].rowidx().cpu().numpy(), ri)
+            ref = oracle.build(m, mats[0], cp, ri)
+            ip, ix, dv = oracle.to_csr(n, cp, ri, ref["mval"])
+            assert np.array_equal(rp[k * (n + 1):(k + 1) * (n + 1)].cpu().numpy(), ip)
+            assert np.array_equal(ci[offs[k]:offs[k + 1]].cpu().numpy(), ix)
+            got = v[offs[k]:offs[k + 1]].cpu().numpy()
+            assert np.linalg.norm(got - dv) <= 1e-10 * np.linalg.norm(dv)
+
+
+def test_shared_and_per_column_shadow_agree_in_the_adjoint(sam):
+    """The adjoint of a batch of one structure (shadow data shared) equals,
+    bit for bit, the adjoint computed one map at a time."""
+    seq = W.config2(nx=24, nmat=3)
+    with sam.Handle() as h:
+        aks = [sam.Csr.from_host(m) for m in seq.mats]
+        a0 = aks[0]
+        pats = h.sam_pattern_build_batched(aks, 2)
+        offs, rp, ci, mv, _ = h.sam_build_batched(aks, a0, pats, "fp32r", 1)
+        import torch
+
+        g = torch.randn(mv.numel(), dtype=torch.float64, device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+        dak, da0 = h.sam_build_backward_batched(aks, [a0] * len(aks), pats, mv, g, "fp32r", 1, 1.0, offsets=offs)
+        koff = np.cumsum([0] + [a.nnz for a in aks])
+        for k in range(len(aks)):
+            one = h.sam_pattern_build(aks[k], 2)
+            dk, d0 = h.sam_build_backward(aks[k], a0, one, mv[offs[k]:offs[k + 1]], g[offs[k]:offs[k + 1]], "fp32r", 1,
+                                          1.0)
+            assert bool((dk == dak[koff[k]:koff[k + 1]]).all())
+            assert bool((d0 == da0[k * a0.nnz:(k + 1) * a0.nnz]).all())
