@@ -54,7 +54,7 @@ struct KryArgs {
     double *h;     // (m+1) this pass's projections / the cycle's y
     double *coef;  // (m+1) coefficients of the next subtraction / combination
     double *hist;  // [maxiter] residual estimates / ||b||
-    double *part;  // [nblk][m+1] block partials
+    double *part;  // [m+1][nblk] block partials (vector-major)
 };
 
 // gates of the launches of a cycle
@@ -90,14 +90,15 @@ __device__ bool last_block(KryCtl *c, int nblk) {
     return last;
 }
 
-// Fixed-order sum over blocks of part[b][l] for l < cnt (called by the last
+// Fixed-order sum over blocks of part[l][b] for l < cnt (called by the last
 // block): out[l] = total.  Warp w sums the vectors l = w, w + 8, ...; its
-// lanes read the blocks' partials in one round of independent loads.
-__device__ void reduce_partials(const double *part, int nblk, int stride, int cnt, double *out) {
+// lanes read the blocks' partials of a vector, stored contiguously, in one
+// round of independent coalesced loads.
+__device__ void reduce_partials(const double *part, int nblk, int cnt, double *out) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int l = warp; l < cnt; l += kKryThreads / 32) {
         double a = 0.0;
-        for (int b = lane; b < nblk; b += 32) a += __ldcg(part + (size_t)b * stride + l);
+        for (int b = lane; b < nblk; b += 32) a += __ldcg(part + (size_t)l * nblk + b);
         a = warp_sum(a);
         if (lane == 0) out[l] = a;
     }
@@ -168,10 +169,10 @@ __global__ void __launch_bounds__(kKryThreads) kry_norm_kernel(KryArgs a, const 
     if (threadIdx.x == 0) {
         double u = 0.0;
         for (int w = 0; w < kKryThreads / 32; ++w) u += red[w];
-        a.part[(size_t)blockIdx.x * (a.m + 1)] = u;
+        a.part[blockIdx.x] = u;
     }
     if (!last_block(c, a.nblk)) return;
-    reduce_partials(a.part, a.nblk, a.m + 1, 1, &tot);
+    reduce_partials(a.part, a.nblk, 1, &tot);
     if (threadIdx.x == 0) {
         const double nrm = sqrt(tot);
         if (what == 0) {
@@ -270,7 +271,6 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
     ws[threadIdx.x] = wi;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int stride = a.m + 1;
     constexpr int W8 = kKryThreads / 32;
     if (pass < 2) {
         double wl[W8];
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
                 }
                 if (lane == 0) {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) a.part[(size_t)blockIdx.x * stride + q0 + u * W8] = d[u];
+                    for (int u = 0; u < 4; ++u) a.part[(size_t)(q0 + u * W8) * a.nblk + blockIdx.x] = d[u];
                 }
             } else {
                 for (int q = q0; q < nv; q += W8) {
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
                         if (row0 + r < n) d = fma(__ldg(vq + r), wl[t], d);
                     }
                     d = warp_sum(d);
-                    if (lane == 0) a.part[(size_t)blockIdx.x * stride + q] = d;
+                    if (lane == 0) a.part[(size_t)q * a.nblk + blockIdx.x] = d;
                 }
             }
         }
@@ -320,14 +320,14 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
         if (threadIdx.x == 0) {
             double t = 0.0;
             for (int ww = 0; ww < W8; ++ww) t += red[ww];
-            a.part[(size_t)blockIdx.x * stride] = t;
+            a.part[blockIdx.x] = t;
         }
     }
     if (!last_block(c, a.nblk)) return;
     const int m = a.m;
     double *Hj = a.H + (size_t)j * (m + 1);
     if (pass < 2) {
-        reduce_partials(a.part, a.nblk, stride, nv, a.h);
+        reduce_partials(a.part, a.nblk, nv, a.h);
         for (int l = threadIdx.x; l < nv; l += blockDim.x) {
             const double hl = a.s[l] * a.h[l];  // projection on the normalised s_l V_l
             Hj[l] = pass == 0 ? hl : Hj[l] + hl;
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
         rc[l] = a.cs[l];
         rs[l] = a.sn[l];
     }
-    reduce_partials(a.part, a.nblk, stride, 1, &tot);
+    reduce_partials(a.part, a.nblk, 1, &tot);
     if (threadIdx.x != 0) return;
     const double hn = sqrt(tot);
     col[j + 1] = hn;
