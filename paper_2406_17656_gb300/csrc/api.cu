@@ -256,14 +256,18 @@ sam_status drain_status(sam_handle h) {
 }
 
 // flag[0] = 1 when some matrix k in [1, K) has a structure (row pointers,
-// column indices) different from matrix 0's; nnz equal (checked on the host)
+// column indices) different from matrix 0's; nnz equal (checked on the host).
+// Thread t compares entries 4t .. 4t+3 of both arrays.
 __global__ void structure_differs_kernel(int n, const CsrPtrs *mats, int64_t nnz, int32_t *flag) {
     const int k = blockIdx.y + 1;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     const CsrPtrs a = mats[0], b = mats[k];
     bool diff = false;
-    if (t <= n) diff = a.rp[t] != b.rp[t];
-    if (t < nnz) diff = diff || a.ci[t] != b.ci[t];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        if (t + u <= n) diff = diff || a.rp[t + u] != b.rp[t + u];
+        if (t + u < nnz) diff = diff || a.ci[t + u] != b.ci[t + u];
+    }
     if (diff) *flag = 1;
 }
 
@@ -289,8 +293,8 @@ cudaError_t launch_structure_checks(sam_handle h, Scratch &sc, const std::vector
         CsrPtrs *dtab = sc.get<CsrPtrs>(tab.size());
         if (!dtab) return cudaErrorMemoryAllocation;
         cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * tab.size(), cudaMemcpyHostToDevice, h->stream);
-        const int64_t cnt = std::max<int64_t>((int64_t)ms[b].n + 1, ms[b].nnz);
-        dim3 grid((unsigned)((cnt + 255) / 256), (unsigned)(e - b - 1));
+        const int64_t cnt = (std::max<int64_t>((int64_t)ms[b].n + 1, ms[b].nnz) + 3) / 4;
+        dim3 grid((unsigned)((cnt + 255) / 256 > 0 ? (cnt + 255) / 256 : 1), (unsigned)(e - b - 1));
         structure_differs_kernel<<<grid, 256, 0, h->stream>>>(ms[b].n, dtab, ms[b].nnz, flags + r);
         count_launch(h);
     }
@@ -428,13 +432,18 @@ sam_status group_finish(sam_handle h, int K, int n, int32_t *jcp, int32_t *jri, 
             count_launch(h);
         }
     }
-    gather_strided_kernel<<<(K + 1 + 127) / 128, 128, 0, h->stream>>>(K, n, jcp, doff);
-    count_launch(h);
     g->off.resize((size_t)K + 1);
-    if (cudaMemcpyAsync(g->off.data(), doff, sizeof(int64_t) * ((size_t)K + 1), cudaMemcpyDeviceToHost, h->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(h->stream) != cudaSuccess)
-        return fail(SAM_ERR_CUDA);
+    if (K == 1) {  // one map: its offsets are known without a readback
+        g->off[0] = 0;
+        g->off[1] = nnz;
+    } else {
+        gather_strided_kernel<<<(K + 1 + 127) / 128, 128, 0, h->stream>>>(K, n, jcp, doff);
+        count_launch(h);
+        if (cudaMemcpyAsync(g->off.data(), doff, sizeof(int64_t) * ((size_t)K + 1), cudaMemcpyDeviceToHost,
+                            h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return fail(SAM_ERR_CUDA);
+    }
     pool_free(h, perm);
     pool_free(h, doff);
     *out = g;
@@ -454,6 +463,32 @@ __global__ void replicate_shifted_kernel(int64_t m, const int32_t *src, int32_t 
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int k = blockIdx.y;
     if (e < m) dst[(int64_t)k * m + e] = src[e] + k * shift;
+}
+
+// the same four entries per thread with 16-byte accesses (m a multiple of 4,
+// 16-byte aligned arrays)
+__global__ void replicate_shifted4_kernel(int64_t m4, const int4 *src, int32_t shift, int4 *dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (e < m4) {
+        int4 v = src[e];
+        const int32_t d = k * shift;
+        v.x += d;
+        v.y += d;
+        v.z += d;
+        v.w += d;
+        dst[(int64_t)k * m4 + e] = v;
+    }
+}
+
+void replicate_shifted(cudaStream_t st, int K, int64_t m, const int32_t *src, int32_t shift, int32_t *dst) {
+    const bool vec = m % 4 == 0 && ((uintptr_t)src % 16) == 0 && ((uintptr_t)dst % 16) == 0;
+    const int64_t cnt = vec ? m / 4 : m;
+    const dim3 grid((unsigned)((cnt + 255) / 256 > 0 ? (cnt + 255) / 256 : 1), (unsigned)K);
+    if (vec)
+        replicate_shifted4_kernel<<<grid, 256, 0, st>>>(cnt, (const int4 *)src, shift, (int4 *)dst);
+    else
+        replicate_shifted_kernel<<<grid, 256, 0, st>>>(m, src, shift, dst);
 }
 
 // a[k n + t] = a[t] for 1 <= k < K (the per-column results of map 0)
@@ -506,12 +541,11 @@ sam_status group_replicate(sam_handle h, PatternGroup *g1, int K, PatternGroup *
         return SAM_ERR_OOM;
     }
     const dim3 gn((unsigned)((n + 255) / 256 > 0 ? (n + 255) / 256 : 1), (unsigned)K);
-    const dim3 gm((unsigned)((m + 255) / 256 > 0 ? (m + 255) / 256 : 1), (unsigned)K);
     replicate_offsets_kernel<<<gn, 256, 0, h->stream>>>(K, n, g1->jcp, (int32_t)m, g->jcp);
     replicate_offsets_kernel<<<gn, 256, 0, h->stream>>>(K, n, g1->mrp, (int32_t)m, g->mrp);
-    replicate_shifted_kernel<<<gm, 256, 0, h->stream>>>(m, g1->jri, n, g->jri);
-    replicate_shifted_kernel<<<gm, 256, 0, h->stream>>>(m, g1->mci, n, g->mci);
-    replicate_shifted_kernel<<<gm, 256, 0, h->stream>>>(m, g1->csr_pos, (int32_t)m, g->csr_pos);
+    replicate_shifted(h->stream, K, m, g1->jri, n, g->jri);
+    replicate_shifted(h->stream, K, m, g1->mci, n, g->mci);
+    replicate_shifted(h->stream, K, m, g1->csr_pos, (int32_t)m, g->csr_pos);
     count_launch(h, 5);
     g->off.resize((size_t)K + 1);
     for (int k = 0; k <= K; ++k) g->off[k] = (int64_t)k * m;
