@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) adjoint_kernel(LsqArgs ar
             mq[q] = 0.0;
             gq[q] = 0.0;
             if (c < nJ) {
-                const int t = args.csr_pos[C.jb + c];
+                const int t = C.map_pos(args, c);
                 mq[q] = args.mval[t];
                 gq[q] = args.dmval ? args.dmval[t] : 0.0;
                 S.m[c] = mq[q];
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) adjoint_kernel(LsqArgs ar
                         const double ri = S.u.s.r[i], wi = S.u.s.w[i];
                         args.dB[blk + C.colB[q] + p] = ri * lq[q] - wi * mq[q] - 2.0 * rho * ri * mq[q];
                     }
-                    const int t = args.csr_pos[C.jb + c];
+                    const int t = C.map_pos(args, c);
                     args.dbase[t] = blk + C.colB[q];
                     if (args.dmres) args.dmres[t] = -2.0 * rho * C.bt_times(args, S, S.u.s.r, q);
                 }

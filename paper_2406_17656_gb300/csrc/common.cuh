@@ -68,6 +68,9 @@ struct LsqArgs {
     int shadow_shared;           // 1: every map has the same source, target and pattern structure, and
                                  // ish / lrow / zloc hold map 0's columns only (indexed by the column
                                  // within its map); 0: one entry per column of the batch
+    int64_t map_nnz_src;         // shadow_shared: stored entries of one source map and of one map
+    int64_t map_nnz_pat;         // pattern; map k's pattern and source metadata are map 0's, read
+                                 // at the same addresses for every map, plus k times these
     const int32_t *csr_pos;      // pattern CSC entry -> map CSR position
     double *mval;                // map values, CSR order of the block-diagonal map
     double *colres;              // per-column residual^2 (+ out-of-shadow part)

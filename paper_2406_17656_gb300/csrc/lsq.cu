@@ -225,11 +225,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
             int status = C.status;
             if (status == kStOk && (nf || !finite64(r2))) status = kStNonfinite;
             if (status == kStOk && fallback) status = kStRefine;  // re-solved by the FP64 kernel
-            const int njo = args.jcp[C.jj + 1] - C.jb;
+            const int njo = args.jcp[C.js + 1] - C.jb;
 #pragma unroll
             for (int q = 0; q < JQ; ++q) {
                 const int c = ll + q * P;
-                if (c < njo) args.mval[args.csr_pos[C.jb + c]] = (status == kStOk) ? mq[q] : 0.0;
+                if (c < njo) args.mval[C.map_pos(args, c)] = (status == kStOk) ? mq[q] : 0.0;
             }
             if (ll == 0) {
                 args.colres[C.jj] = (status == kStOk) ? (r2 > 0.0 ? r2 : 0.0) + C.out2 : 0.0;

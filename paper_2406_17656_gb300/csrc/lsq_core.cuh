@@ -398,6 +398,10 @@ struct Column {
     int ll, rg, cg, gbase;
     bool valid;
     int jj, jl, js, roff, zro, jb, nJ, nI, zb, ze, nB, kmax;  // js: column of the shadow data
+    // jb: start of the column in the pattern arrays, read at column js (map
+    // 0's copy when the batch shares one structure); aoff / poff: this map's
+    // offsets into the source values and the map positions
+    int64_t aoff, poff;
     int status;
     int colA[JQ], clen[JQ], colB[JQ];
     double out2;
@@ -418,6 +422,8 @@ struct Column {
         const int kmap = jj / args.n;
         jl = jj - kmap * args.n;  // column of A_0
         js = args.shadow_shared ? jl : jj;
+        aoff = args.shadow_shared ? (int64_t)kmap * args.map_nnz_src : 0;
+        poff = args.shadow_shared ? (int64_t)kmap * args.map_nnz_pat : 0;
         roff = kmap * args.n;     // row offset of this map
         // target column: A_0(:, jl) shifted by roff, or column jj of the
         // block-diagonal targets (rows already global)
@@ -425,9 +431,9 @@ struct Column {
         zro = args.zbig ? 0 : roff;
         jb = nJ = nI = zb = ze = 0;
         if (valid) {
-            jb = args.jcp[jj];
-            nJ = args.jcp[jj + 1] - jb;
-            nI = args.icnt[jj];
+            jb = args.jcp[js];
+            nJ = args.jcp[js + 1] - jb;
+            nI = args.icnt[js];
             zb = args.zcp[zc];
             ze = args.zcp[zc + 1];
         }
@@ -444,8 +450,9 @@ struct Column {
             clen[q] = 0;
             if (c < nJ) {
                 const int col = args.jri[jb + c];
-                colA[q] = args.kcp[col];
-                clen[q] = args.kcp[col + 1] - colA[q];
+                const int a0 = args.kcp[col];
+                clen[q] = args.kcp[col + 1] - a0;
+                colA[q] = (int)(a0 + aoff);
             }
         }
         nB = 0;
@@ -534,6 +541,11 @@ struct Column {
         }
         out2 = group_sum<P>(out2);
         __syncwarp();
+    }
+
+    // position in the map (CSR order of the batch) of pattern entry c
+    __device__ __forceinline__ int map_pos(const LsqArgs &args, int c) const {
+        return (int)(args.csr_pos[jb + c] + poff);
     }
 
     // local shadow row of entry t (offset tz in the column) of the target
