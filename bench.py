@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-tune", action="store_true", help="default tile shapes instead of sam_tune's choice")
+    ap.add_argument("--no-configs", action="store_true", help="skip the per-configuration throughput figures")
     ap.add_argument("--profile-gmres", type=int, default=0, metavar="STEPS",
                     help="profiling aid: run one GMRES solve of STEPS Arnoldi steps on the benchmark's last map "
                          "and exit (no JSON line)")
@@ -382,6 +383,104 @@ def profile_gmres(h, sam, torch, dev, aks, a0, n, level, steps):
     print("gmres: %d steps, estimate %.3e, %.1f us per step" % (its, rel, (time.perf_counter() - t) * 1e6 / its))
 
 
+# ------------------------------------------------------------ all configs
+
+
+def config_figures(h, sam, torch, dev, stream, nsteps=5):
+    """Throughput of the whole path (level-L patterns + batched maps, with
+    the per-map residuals) on the other synthetic workloads: CUDA events
+    around each step, mean of `nsteps` after one warm-up.  Returns a dict
+    keyed by workload."""
+    from paper_2406_17656_gb300 import workloads as W
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ms = 0.0
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        return ms / reps
+
+    def line(name, cols, maps, ms, extra=None):
+        d = {"columns_per_s": cols / (ms * 1e-3), "maps_per_s": maps / (ms * 1e-3), "ms_per_step": ms,
+             "columns_per_step": cols, "maps": maps}
+        d.update(extra or {})
+        out[name] = d
+
+    out = {}
+    # config 1: 5-point Poisson 32^2, A_1 = A_0 + diag, level 1, plain FP64 single build
+    seq = W.config1()
+    aks = [sam.Csr.from_host(m, dev) for m in seq.mats]
+
+    def c1():
+        ps = h.sam_pattern_build_batched(aks, 1)
+        h.sam_build_batched(aks, aks[0], ps, "fp64", 0, want_fro=True)
+        for p in ps:
+            p.destroy()
+
+    line("poisson5_32x32_seq2_level1_fp64", 2 * aks[0].n, 2, timed(c1, nsteps))
+    # config 3: 7-point upwind 64^3, 20 maps, level 2, FP32 QR + 1 FP64 step
+    seq = W.config3()
+    aks = [sam.Csr.from_host(m, dev) for m in seq.mats]
+
+    def c3():
+        ps = h.sam_pattern_build_batched(aks, 2)
+        h.sam_build_batched(aks, aks[0], ps, "fp32r", 1, want_fro=True)
+        for p in ps:
+            p.destroy()
+
+    line("upwind7_64cube_seq20_level2", len(aks) * aks[0].n, len(aks), timed(c3, nsteps))
+    del aks
+    # config 4: P1 FEM 512^2 cells, 16 maps whose pattern changes, level 2; direct and captured plan
+    seq = W.config4()
+    aks = [sam.Csr.from_host(m, dev) for m in seq.mats]
+
+    def c4():
+        ps = h.sam_pattern_build_batched(aks, 2)
+        h.sam_build_batched(aks, aks[0], ps, "fp32r", 1, want_fro=True)
+        for p in ps:
+            p.destroy()
+
+    ms4 = timed(c4, nsteps)
+    ps = h.sam_pattern_build_batched(aks, 2)
+    plan = h.sam_plan_create(aks, aks[0], ps, "fp32r", 1)
+    for p in ps:
+        p.destroy()
+    msp = timed(plan.execute, nsteps)
+    plan.destroy()
+    cols4 = len(aks) * aks[0].n
+    line("p1_fem_512x512_seq16_level2", cols4, len(aks), ms4,
+         {"graph_replay_columns_per_s": cols4 / (msp * 1e-3), "graph_replay_ms": msp})
+    del aks
+    # config 5: 32 independent (A_0, A_1) 512^2 pairs, level 1, forward (one target per map) and adjoint
+    pairs = [W.config5_pair(b) for b in range(32)]
+    a0s = [sam.Csr.from_host(p[0], dev) for p in pairs]
+    a1s = [sam.Csr.from_host(p[1], dev) for p in pairs]
+    n5 = a0s[0].n
+
+    def c5():
+        ps = h.sam_pattern_build_batched(a1s, 1)
+        h.sam_build_batched(a1s, a0s, ps, "fp32r", 2, want_fro=True)
+        for p in ps:
+            p.destroy()
+
+    ms5 = timed(c5, nsteps)
+    ps = h.sam_pattern_build_batched(a1s, 1)
+    offs, _, _, mv, _ = h.sam_build_batched(a1s, a0s, ps, "fp32r", 2)
+    gbar = torch.randn(mv.numel(), dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(5))
+    msb = timed(lambda: h.sam_build_backward_batched(a1s, a0s, ps, mv, gbar, "fp32r", 2, 1.0, offsets=offs), nsteps)
+    for p in ps:
+        p.destroy()
+    line("q1_pairs_512x512_x32_level1", 32 * n5, 32, ms5,
+         {"adjoint_columns_per_s": 32 * n5 / (msb * 1e-3), "adjoint_ms": msb, "refine_steps": 2})
+    return out
+
+
 # ------------------------------------------------------------------- ours
 
 
@@ -592,6 +691,10 @@ def main():
     if not args.quick:
         extra.update(krylov_measurement(h, sam, torch, dev, stream, aks, a0, offs, out[0], out[1], v32, n, K,
                                         world, rank))
+
+    # ---- the other workloads of the same path (patterns + batched maps per step)
+    if not args.quick and not args.no_configs and world == 1:
+        extra["configs"] = config_figures(h, sam, torch, dev, stream)
 
     # ---- roofline of the dominant kernel (largest least-squares size class)
     sizes = column_sizes(seq.mats, args.level)
