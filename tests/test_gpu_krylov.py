@@ -243,3 +243,18 @@ def test_full_size_q1_256_sequence(sam, handle):
     assert itg == ito == 300
     assert np.all(np.abs(hg - ho) <= 1e-6 * np.asarray(ho))
     assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("restart", [100, 128])
+def test_long_cycles(sam, handle, restart):
+    """Cycles longer than 64 steps (the back substitution reads R from global
+    memory instead of the shared-memory tile) up to the largest restart
+    length: 24^2 diffusion with a Jacobi P_0 takes about 150 steps."""
+    seq = W.config2(nx=24, nmat=4)
+    A0, Ak = seq.mats[0], seq.mats[3]
+    P = jacobi(A0)
+    b = rhs(Ak.n, 11)
+    kw = dict(restart=restart, maxiter=1000, rtol=1e-10)
+    gpu = run_gpu(sam, handle, Ak, b, P=P, **kw)
+    assert gpu[1] > 64
+    compare(Ak, b, gpu, oracle.gmres(Ak, b, P0=P, **kw), 1e-10, 1e-6)
