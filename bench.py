@@ -386,29 +386,51 @@ def profile_gmres(h, sam, torch, dev, aks, a0, n, level, steps):
 # ------------------------------------------------------------ all configs
 
 
-def config_figures(h, sam, torch, dev, stream, nsteps=5):
+def config_figures(h, sam, torch, dev, stream, nsteps=7):
     """Throughput of the whole path (level-L patterns + batched maps, with
     the per-map residuals) on the other synthetic workloads: CUDA events
-    around each step, mean of `nsteps` after one warm-up.  Returns a dict
+    around each step, median of `nsteps` after one warm-up.  Returns a dict
     keyed by workload."""
     from paper_2406_17656_gb300 import workloads as W
 
     def timed(fn, reps):
         fn()
         torch.cuda.synchronize()
-        ms = 0.0
+        ms = []
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             fn()
             e1.record(stream)
             e1.synchronize()
-            ms += e0.elapsed_time(e1)
-        return ms / reps
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
 
-    def line(name, cols, maps, ms, extra=None):
+    size_cache = {}
+
+    def step_roofline(mats, level, precision, steps, ms):
+        """Whole-step roofline: the slowest of the algorithmic FP32 flops at the
+        FP32 peak, the FP64 flops at the FP64 peak and the gathered bytes at
+        the measured HBM bandwidth, over the measured step time (column sizes
+        from the structures, computed once per distinct structure)."""
+        f32 = f64 = gathered = 0.0
+        for m in mats:
+            key = (m.indptr.tobytes(), m.indices.tobytes())
+            if key not in size_cache:
+                I, J, nB = column_sizes([m], level)[0]
+                a, b = algorithmic_flops(I, J, nB, precision, steps)
+                size_cache[key] = (float(np.sum(a)), float(np.sum(b)), 12.0 * float(np.sum(nB)))
+            a, b, g = size_cache[key]
+            f32, f64, gathered = f32 + a, f64 + b, gathered + g
+        t_roof = max(f32 / PEAK_FP32, f64 / PEAK_FP64, gathered / (measured_hbm_gbs() * 1e9))
+        return {"roofline_frac": t_roof / (ms * 1e-3), "fp32_flops": f32, "fp64_flops": f64,
+                "gathered_bytes": gathered}
+
+    def line(name, cols, maps, ms, extra=None, roof=None):
         d = {"columns_per_s": cols / (ms * 1e-3), "maps_per_s": maps / (ms * 1e-3), "ms_per_step": ms,
              "columns_per_step": cols, "maps": maps}
+        if roof is not None:
+            d.update(step_roofline(*roof, ms))
         d.update(extra or {})
         out[name] = d
 
@@ -423,7 +445,7 @@ def config_figures(h, sam, torch, dev, stream, nsteps=5):
         for p in ps:
             p.destroy()
 
-    line("poisson5_32x32_seq2_level1_fp64", 2 * aks[0].n, 2, timed(c1, nsteps))
+    line("poisson5_32x32_seq2_level1_fp64", 2 * aks[0].n, 2, timed(c1, nsteps), roof=(seq.mats, 1, "fp64", 0))
     # config 3: 7-point upwind 64^3, 20 maps, level 2, FP32 QR + 1 FP64 step
     seq = W.config3()
     aks = [sam.Csr.from_host(m, dev) for m in seq.mats]
@@ -434,7 +456,7 @@ def config_figures(h, sam, torch, dev, stream, nsteps=5):
         for p in ps:
             p.destroy()
 
-    line("upwind7_64cube_seq20_level2", len(aks) * aks[0].n, len(aks), timed(c3, nsteps))
+    line("upwind7_64cube_seq20_level2", len(aks) * aks[0].n, len(aks), timed(c3, nsteps), roof=(seq.mats, 2, "fp32r", 1))
     del aks
     # config 4: P1 FEM 512^2 cells, 16 maps whose pattern changes, level 2; direct and captured plan
     seq = W.config4()
@@ -455,7 +477,7 @@ def config_figures(h, sam, torch, dev, stream, nsteps=5):
     plan.destroy()
     cols4 = len(aks) * aks[0].n
     line("p1_fem_512x512_seq16_level2", cols4, len(aks), ms4,
-         {"graph_replay_columns_per_s": cols4 / (msp * 1e-3), "graph_replay_ms": msp})
+         {"graph_replay_columns_per_s": cols4 / (msp * 1e-3), "graph_replay_ms": msp}, roof=(seq.mats, 2, "fp32r", 1))
     del aks
     # config 5: 32 independent (A_0, A_1) 512^2 pairs, level 1, forward (one target per map) and adjoint
     pairs = [W.config5_pair(b) for b in range(32)]
@@ -477,7 +499,8 @@ def config_figures(h, sam, torch, dev, stream, nsteps=5):
     for p in ps:
         p.destroy()
     line("q1_pairs_512x512_x32_level1", 32 * n5, 32, ms5,
-         {"adjoint_columns_per_s": 32 * n5 / (msb * 1e-3), "adjoint_ms": msb, "refine_steps": 2})
+         {"adjoint_columns_per_s": 32 * n5 / (msb * 1e-3), "adjoint_ms": msb, "refine_steps": 2},
+         roof=([p[1] for p in pairs], 1, "fp32r", 2))
     return out
 
 
