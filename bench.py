@@ -353,6 +353,33 @@ def krylov_measurement(h, sam, torch, dev, stream, aks, a0, offs, mrp, mci, mval
                                           "working set is L2-resident"},
                      "algorithmic_bytes": moved, "achieved_gbs": gbs, "hbm_frac": gbs / measured_hbm_gbs(),
                      "working_set_mb": (12.0 * (A.nnz + M.nnz + P.nnz) + 8.0 * n * (kw["restart"] + 6)) / 1e6}}
+    # the whole sequence: A_k x = b for k = 1..K-1, each with its map M_k, solved
+    # together in one batched call and one by one
+    Ms = [sam.Csr(mrp[q * (n + 1):(q + 1) * (n + 1)].contiguous(), mci[offs[q]:offs[q + 1]], mval[offs[q]:offs[q + 1]],
+                  n=n) for q in range(1, K)]
+    As = aks[1:K]
+    bb = b.repeat(K - 1)
+    h.sam_gmres_batched(As, bb, Ms=Ms, P_0=P, **kw)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, its_b, _ = h.sam_gmres_batched(As, bb, Ms=Ms, P_0=P, **kw)
+    e1.record(stream)
+    e1.synchronize()
+    ms_batched = e0.elapsed_time(e1)
+    ms_single, its_single = 0.0, []
+    for A_q, M_q in zip(As, Ms):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, its_q, _ = h.sam_gmres(A_q, b, M=M_q, P_0=P, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        ms_single += e0.elapsed_time(e1)
+        its_single.append(its_q)
+    out["gmres"]["sequence"] = {"systems": K - 1, "steps": [int(v) for v in its_b],
+                                "steps_equal_single_solves": [int(v) for v in its_b] == its_single,
+                                "batched_ms": ms_batched, "one_by_one_ms": ms_single,
+                                "speedup": ms_single / ms_batched}
     if rank == 0 and world == 1:
         # the oracle's textbook GMRES on the same system, 60 steps (two cycles)
         import oracle

@@ -311,6 +311,23 @@ sam_status sam_gmres(sam_handle h, const sam_csr *A, const sam_csr *M, const sam
                      int restart, int maxiter, double rtol, int32_t *iters, double *relres, double *history);
 
 /*
+ * sam_gmres_batched -- K independent solves A_k x_k = b_k of one order n
+ * (a sequence of Sec. 2, each with its own map M_k and the one P_0 built for
+ * A_0), by sam_gmres's algorithm, in the same launches: every system keeps
+ * its own Krylov basis, Hessenberg matrix, step count and stopping test, and
+ * drops out when it stops; the launches of a restart cycle cover all
+ * systems.
+ *   A[K]       system matrices; M (nullable) K maps; P_0 (nullable) shared.
+ *   b, x       [K][n] (system k at k n); x holds x0_k on entry.
+ *   iters, relres (host, nullable) [K]; history (nullable, device or host)
+ *              [K][maxiter].
+ * Same arguments, errors and synchronisation as sam_gmres otherwise.
+ */
+sam_status sam_gmres_batched(sam_handle h, int K, const sam_csr *A, const sam_csr *M, const sam_csr *P_0,
+                             const double *b, double *x, int restart, int maxiter, double rtol, int32_t *iters,
+                             double *relres, double *history);
+
+/*
  * sam_build_backward -- adjoint of sam_build on a fixed pattern: gradients
  * with respect to the stored values of A_k and A_0 of
  *     L = <dM, M_k>  +  resid_weight * ||A_k M_k - A_0||_F^2,

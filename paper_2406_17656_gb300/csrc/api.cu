@@ -1362,9 +1362,64 @@ sam_status sam_gmres(sam_handle h, const sam_csr *A, const sam_csr *M, const sam
     if (P_0) p = KryOp{dp.nnz, dp.rp, dp.ci, dp.v};
     int32_t its = 0;
     double rel = 0.0;
-    s = gmres_solve(h, n, a, m, p, db, dx, restart, maxiter, rtol, dh, &its, &rel, nullptr);
+    s = gmres_solve(h, 1, n, &a, M ? &m : nullptr, p, db, dx, restart, maxiter, rtol, dh, &its, &rel, nullptr);
     if (iters) *iters = its;
     if (relres) *relres = rel;
+    if (s != SAM_OK) return s;
+    if (sg.finish() != cudaSuccess) return SAM_ERR_CUDA;
+    return drain_status(h);
+}
+
+sam_status sam_gmres_batched(sam_handle h, int K, const sam_csr *A, const sam_csr *M, const sam_csr *P_0,
+                             const double *b, double *x, int restart, int maxiter, double rtol, int32_t *iters,
+                             double *relres, double *history) {
+    if (!h || K < 1 || !A || !b || !x) return SAM_ERR_INVALID_ARG;
+    if (restart < 1 || restart > SAM_GMRES_MAX_RESTART || maxiter < 0 || !std::isfinite(rtol) || rtol < 0.0)
+        return SAM_ERR_INVALID_ARG;
+    const int n = A[0].n;
+    for (int k = 0; k < K; ++k) {
+        if (check_csr_arg(&A[k], true) || A[k].n != n) return SAM_ERR_INVALID_ARG;
+        if (M && (check_csr_arg(&M[k], true) || M[k].n != n)) return SAM_ERR_INVALID_ARG;
+    }
+    if (P_0 && (check_csr_arg(P_0, true) || P_0->n != n)) return SAM_ERR_INVALID_ARG;
+    const int64_t N = (int64_t)K * n;
+    if (N > INT32_MAX) return SAM_ERR_INVALID_ARG;
+    for (int k = 0; k < K; ++k) {
+        if (iters) iters[k] = 0;
+        if (relres) relres[k] = 0.0;
+    }
+    if (n == 0) return SAM_OK;
+    Scratch sc(h);
+    Stager sg(sc, h->stream);
+    std::vector<DevCsr> all;
+    for (int k = 0; k < K; ++k) all.push_back(stage_csr(sg, &A[k], true));
+    if (M)
+        for (int k = 0; k < K; ++k) all.push_back(stage_csr(sg, &M[k], true));
+    if (P_0) all.push_back(stage_csr(sg, P_0, true));
+    const double *db = sg.in(b, (size_t)N);
+    double *dx = sg.inout(x, (size_t)N);
+    double *dh = (history && maxiter > 0) ? sg.out(history, (size_t)K * maxiter) : nullptr;
+    if (sg.failed) return SAM_ERR_OOM;
+    sam_status s = validate_all(h, sc, all);
+    if (s != SAM_OK) return s;
+    std::vector<KryOp> a(K), m(M ? K : 0);
+    for (int k = 0; k < K; ++k) {
+        a[k] = KryOp{all[k].nnz, all[k].rp, all[k].ci, all[k].v};
+        if (M) m[k] = KryOp{all[K + k].nnz, all[K + k].rp, all[K + k].ci, all[K + k].v};
+    }
+    KryOp p;
+    if (P_0) {
+        const DevCsr &d = all.back();
+        p = KryOp{d.nnz, d.rp, d.ci, d.v};
+    }
+    std::vector<int32_t> its((size_t)K, 0);
+    std::vector<double> rel((size_t)K, 0.0);
+    s = gmres_solve(h, K, n, a.data(), M ? m.data() : nullptr, p, db, dx, restart, maxiter, rtol, dh, its.data(),
+                    rel.data(), nullptr);
+    for (int k = 0; k < K; ++k) {
+        if (iters) iters[k] = its[k];
+        if (relres) relres[k] = rel[k];
+    }
     if (s != SAM_OK) return s;
     if (sg.finish() != cudaSuccess) return SAM_ERR_CUDA;
     return drain_status(h);

@@ -218,11 +218,14 @@ struct KryOp {
     const int32_t *rp = nullptr, *ci = nullptr;
     const double *v = nullptr;
 };
-// Restarted GMRES(restart) for A x = b with the right preconditioner
-// z = M (P v) (krylov.cu).  x holds x0 on entry.  hist_dev (nullable,
-// device double[maxiter]) receives the residual estimate / ||b|| of every
-// step.  Synchronises once per restart cycle.
-sam_status gmres_solve(sam_handle h, int n, const KryOp &A, const KryOp &M, const KryOp &P, const double *b,
+// Restarted GMRES(restart) for K systems A_k x_k = b_k of order n with the
+// right preconditioners z = M_k (P v) (krylov.cu).  A[K], M[K] (nullable:
+// identity) host tables of device operators, P shared (P.rp nullptr:
+// identity); b, x device [K][n], x holding x0 on entry.  hist_dev
+// (nullable, device double[K][maxiter]) receives the residual estimate /
+// ||b_k|| of every step; its_out, rel_out host [K].  Synchronises once per
+// restart cycle.
+sam_status gmres_solve(sam_handle h, int K, int n, const KryOp *A, const KryOp *M, const KryOp &P, const double *b,
                        double *x, int restart, int maxiter, double rtol, double *hist_dev, int32_t *its_out,
                        double *rel_out, int64_t *launches_out);
 

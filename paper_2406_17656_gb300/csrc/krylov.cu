@@ -2,6 +2,11 @@
 // (the use of a map named in Sec. 1-2: since A_k M_k ~ A_0 and P_0 is a
 // preconditioner of A_0, A_k M_k P_0 ~ A_0 P_0 ~ I).  FP64 throughout.
 //
+// K independent systems A_k x_k = b_k (a sequence, each with its own map
+// M_k and the shared P_0) are solved in the same launches: the grid's y
+// index is the system, every system has its own control word, Hessenberg
+// matrix, rotations and reductions, and stops on its own.
+//
 // Everything stays on the device.  One Arnoldi step is at most six launches:
 //   [P_0 product] -> [M product] -> A product (w written into V_{j+1})
 //   -> orth pass 0 (h = V^T w) -> pass 1 (w -= V h; h' = V^T w)
@@ -44,18 +49,44 @@ struct KryCtl {
 };
 
 struct KryArgs {
-    int n, m, nblk;
-    KryCtl *ctl;
-    double *V;     // (m+1) x n, vector l at V + l n (unnormalised)
-    double *H;     // (m+1) x m column-major, rotated in place
+    int n, m, nblk, K;  // rows and blocks per system, restart length, systems
+    int64_t N;          // K n
+    int hstride;        // history entries per system (maxiter)
+    KryCtl *ctl;   // [K]
+    double *V;     // (m+1) vectors of K n: basis vector l of system k at V + l N + k n (unnormalised)
+    double *H;     // [K][(m+1) x m] column-major, rotated in place
     double *cs, *sn;
-    double *g;     // (m+1) rotated right-hand side
-    double *s;     // (m+1) scales: the basis vector l is s[l] V_l
-    double *h;     // (m+1) this pass's projections / the cycle's y
-    double *coef;  // (m+1) coefficients of the next subtraction / combination
-    double *hist;  // [maxiter] residual estimates / ||b||
-    double *part;  // [m+1][nblk] block partials (vector-major)
+    double *g;     // [K][m+1] rotated right-hand side
+    double *s;     // [K][m+1] scales: the basis vector l is s[l] V_l
+    double *h;     // [K][m+1] this pass's projections / the cycle's y
+    double *coef;  // [K][m+1] coefficients of the next subtraction / combination
+    double *hist;  // [K][hstride] residual estimates / ||b||
+    double *part;  // [K][m+1][nblk] block partials (vector-major)
 };
+
+// one system's slices of the arguments
+struct KrySys {
+    KryCtl *c;
+    double *H, *cs, *sn, *g, *s, *h, *coef, *hist, *part;
+    int64_t base;  // k n: offset of the system's rows in every vector
+};
+
+__device__ __forceinline__ KrySys kry_sys(const KryArgs &a, int k) {
+    const size_t m1 = (size_t)a.m + 1;
+    KrySys y;
+    y.c = a.ctl + k;
+    y.H = a.H + (size_t)k * m1 * a.m;
+    y.cs = a.cs + k * m1;
+    y.sn = a.sn + k * m1;
+    y.g = a.g + k * m1;
+    y.s = a.s + k * m1;
+    y.h = a.h + k * m1;
+    y.coef = a.coef + k * m1;
+    y.hist = a.hist + (size_t)k * a.hstride;
+    y.part = a.part + (size_t)k * m1 * a.nblk;
+    y.base = (int64_t)k * a.n;
+    return y;
+}
 
 // gates of the launches of a cycle
 enum { kGateAlways = 0, kGateRun = 1, kGateCycle = 2 };
@@ -111,12 +142,23 @@ __device__ void reduce_partials(const double *part, int nblk, int cnt, double *o
 // by memory, so a lane takes a dozen entries of its row: one FMA per entry
 // (two accumulators, loads issued four entries ahead) and log2(L)
 // shuffle-adds per row, instead of padding lanes and reduction trees.
+// System k = blockIdx.y uses ops[per_system ? k : 0]; x, b, y are [K][n]
+// and s (nullable) is s[k s_stride].
 template <int L>
-__global__ void __launch_bounds__(kKryThreads) kry_spmv_kernel(const KryCtl *ctl, int gate, int n, const int32_t *rp,
-                                                               const int32_t *ci, const double *v, const double *x,
-                                                               const double *s, const double *b, double *y,
-                                                               int mode) {
-    if (!gate_open(ctl, gate)) return;
+__global__ void __launch_bounds__(kKryThreads) kry_spmv_kernel(const KryCtl *ctls, int gate, int n,
+                                                               const KryOp *ops, int per_system, const double *x,
+                                                               const double *s, int s_stride, const double *b,
+                                                               double *y, int mode) {
+    const int k = blockIdx.y;
+    if (!gate_open(ctls + k, gate)) return;
+    const KryOp op = ops[per_system ? k : 0];
+    const int32_t *rp = op.rp, *ci = op.ci;
+    const double *v = op.v;
+    const int64_t base = (int64_t)k * n;
+    x += base;
+    y += base;
+    if (b) b += base;
+    if (s) s += (size_t)k * s_stride;
     const int lane = threadIdx.x % L;
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
     const bool live = row < n;  // every lane reaches the shuffles below
@@ -155,11 +197,13 @@ __global__ void __launch_bounds__(kKryThreads) kry_spmv_kernel(const KryCtl *ctl
 __global__ void __launch_bounds__(kKryThreads) kry_norm_kernel(KryArgs a, const double *x, int what) {
     __shared__ double red[kKryThreads / 32];
     __shared__ double tot;
-    KryCtl *c = a.ctl;
+    const KrySys S = kry_sys(a, blockIdx.y);
+    KryCtl *c = S.c;
     if (what == 1 && !c->run) {
         if (blockIdx.x == 0 && threadIdx.x == 0) c->k = 0;
         return;
     }
+    x += S.base;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double t = 0.0;
     if (i < a.n) t = x[i] * x[i];
@@ -169,18 +213,18 @@ __global__ void __launch_bounds__(kKryThreads) kry_norm_kernel(KryArgs a, const 
     if (threadIdx.x == 0) {
         double u = 0.0;
         for (int w = 0; w < kKryThreads / 32; ++w) u += red[w];
-        a.part[blockIdx.x] = u;
+        S.part[blockIdx.x] = u;
     }
     if (!last_block(c, a.nblk)) return;
-    reduce_partials(a.part, a.nblk, 1, &tot);
+    reduce_partials(S.part, a.nblk, 1, &tot);
     if (threadIdx.x == 0) {
         const double nrm = sqrt(tot);
         if (what == 0) {
             c->bnorm = nrm;
         } else {
             c->k = 0;
-            a.g[0] = nrm;
-            a.s[0] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+            S.g[0] = nrm;
+            S.s[0] = nrm > 0.0 ? 1.0 / nrm : 0.0;
             c->rel = c->bnorm > 0.0 ? nrm / c->bnorm : 0.0;
             if (nrm <= c->rtol * c->bnorm || c->its >= c->maxiter) c->run = 0;
         }
@@ -199,26 +243,35 @@ __global__ void __launch_bounds__(kKryThreads) kry_norm_kernel(KryArgs a, const 
 // projections take four vectors per warp at a time, each lane reading 8 of
 // the block's rows of each (32 independent loads), against w staged in
 // shared memory, with the four shuffle reductions interleaved.
-__global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j, int pass, KryOp op, const double *z,
-                                                               const double *zs) {
+__global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j, int pass, const KryOp *ops,
+                                                               const double *z, const double *zs, int zs_stride) {
     __shared__ double ws[2 * (kMaxRestart + 2) > kKryThreads ? 2 * (kMaxRestart + 2) : kKryThreads];
     __shared__ double cf[kMaxRestart + 1];
     __shared__ double red[kKryThreads / 32];
     __shared__ double tot;
-    KryCtl *c = a.ctl;
+    const KrySys S = kry_sys(a, blockIdx.y);
+    KryCtl *c = S.c;
     if (!c->run) return;
     const int n = a.n;
+    const int64_t N = a.N;
     const int nv = j + 1;
-    double *w = a.V + (size_t)(j + 1) * n;
+    double *w = a.V + (size_t)(j + 1) * N + S.base;
+    const double *V0 = a.V + S.base;  // this system's basis vector l at V0 + l N
     const int64_t row0 = (int64_t)blockIdx.x * kKryThreads;
     const int64_t i = row0 + threadIdx.x;
     const bool in = i < n;
     if (pass > 0)
-        for (int l = threadIdx.x; l < nv; l += blockDim.x) cf[l] = a.coef[l];
+        for (int l = threadIdx.x; l < nv; l += blockDim.x) cf[l] = S.coef[l];
     __syncthreads();
     double wi = 0.0;
+    KryOp op;
+    if (pass == 0 && ops) {
+        op = ops[blockIdx.y];
+        z += S.base;
+        if (zs) zs += (size_t)blockIdx.y * zs_stride;
+    }
     if (in) {
-        if (pass == 0 && op.rp) {
+        if (pass == 0 && ops) {
             double a0 = 0.0, a1 = 0.0;
             const int e1 = op.rp[i + 1];
             int e = op.rp[i];
@@ -243,18 +296,18 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
         // full chunks of 8 basis values: the next chunk's loads are issued
         // before this chunk's FMAs; no FP64 instruction is issued for absent
         // vectors (GB300's narrow FP64 pipe is the bound here)
-        const double *vi = a.V + i;
+        const double *vi = V0 + i;
         double s0 = 0.0, s1 = 0.0;
         const int full = nv & ~7;
         double cur[8], nxt[8];
         if (full > 0) {
 #pragma unroll
-            for (int t = 0; t < 8; ++t) cur[t] = __ldg(vi + (size_t)t * n);
+            for (int t = 0; t < 8; ++t) cur[t] = __ldg(vi + (size_t)t * N);
         }
         for (int l0 = 0; l0 < full; l0 += 8) {
             if (l0 + 8 < full) {
 #pragma unroll
-                for (int t = 0; t < 8; ++t) nxt[t] = __ldg(vi + (size_t)(l0 + 8 + t) * n);
+                for (int t = 0; t < 8; ++t) nxt[t] = __ldg(vi + (size_t)(l0 + 8 + t) * N);
             }
 #pragma unroll
             for (int t = 0; t < 8; t += 2) {
@@ -264,7 +317,7 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
 #pragma unroll
             for (int t = 0; t < 8; ++t) cur[t] = nxt[t];
         }
-        for (int l = full; l < nv; ++l) s0 = fma(cf[l], __ldg(vi + (size_t)l * n), s0);
+        for (int l = full; l < nv; ++l) s0 = fma(cf[l], __ldg(vi + (size_t)l * N), s0);
         wi -= s0 + s1;
         w[i] = wi;
     }
@@ -282,7 +335,7 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
                 double d[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const double *vq = a.V + (size_t)(q0 + u * W8) * n + row0;
+                    const double *vq = V0 + (size_t)(q0 + u * W8) * N + row0;
                     d[u] = 0.0;
 #pragma unroll
                     for (int t = 0; t < W8; ++t) {
@@ -297,11 +350,11 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
                 }
                 if (lane == 0) {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) a.part[(size_t)(q0 + u * W8) * a.nblk + blockIdx.x] = d[u];
+                    for (int u = 0; u < 4; ++u) S.part[(size_t)(q0 + u * W8) * a.nblk + blockIdx.x] = d[u];
                 }
             } else {
                 for (int q = q0; q < nv; q += W8) {
-                    const double *vq = a.V + (size_t)q * n + row0;
+                    const double *vq = V0 + (size_t)q * N + row0;
                     double d = 0.0;
 #pragma unroll
                     for (int t = 0; t < W8; ++t) {
@@ -309,7 +362,7 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
                         if (row0 + r < n) d = fma(__ldg(vq + r), wl[t], d);
                     }
                     d = warp_sum(d);
-                    if (lane == 0) a.part[(size_t)q * a.nblk + blockIdx.x] = d;
+                    if (lane == 0) S.part[(size_t)q * a.nblk + blockIdx.x] = d;
                 }
             }
         }
@@ -320,18 +373,18 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
         if (threadIdx.x == 0) {
             double t = 0.0;
             for (int ww = 0; ww < W8; ++ww) t += red[ww];
-            a.part[blockIdx.x] = t;
+            S.part[blockIdx.x] = t;
         }
     }
     if (!last_block(c, a.nblk)) return;
     const int m = a.m;
-    double *Hj = a.H + (size_t)j * (m + 1);
+    double *Hj = S.H + (size_t)j * (m + 1);
     if (pass < 2) {
-        reduce_partials(a.part, a.nblk, nv, a.h);
+        reduce_partials(S.part, a.nblk, nv, S.h);
         for (int l = threadIdx.x; l < nv; l += blockDim.x) {
-            const double hl = a.s[l] * a.h[l];  // projection on the normalised s_l V_l
+            const double hl = S.s[l] * S.h[l];  // projection on the normalised s_l V_l
             Hj[l] = pass == 0 ? hl : Hj[l] + hl;
-            a.coef[l] = hl * a.s[l];            // subtract hl (s_l V_l)
+            S.coef[l] = hl * S.s[l];            // subtract hl (s_l V_l)
         }
         return;
     }
@@ -340,14 +393,14 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
     double *col = ws, *rc = ws + kMaxRestart + 2, *rs = cf;
     for (int l = threadIdx.x; l <= j; l += blockDim.x) {
         col[l] = Hj[l];
-        rc[l] = a.cs[l];
-        rs[l] = a.sn[l];
+        rc[l] = S.cs[l];
+        rs[l] = S.sn[l];
     }
-    reduce_partials(a.part, a.nblk, 1, &tot);
+    reduce_partials(S.part, a.nblk, 1, &tot);
     if (threadIdx.x != 0) return;
     const double hn = sqrt(tot);
     col[j + 1] = hn;
-    a.s[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+    S.s[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
     // earlier rotations on the new column, then the one that zeroes H(j+1, j)
     for (int l = 0; l < j; ++l) {
         const double t = rc[l] * col[l] + rs[l] * col[l + 1];
@@ -356,18 +409,18 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
     }
     const double den = hypot(col[j], col[j + 1]);
     const double cj = den == 0.0 ? 1.0 : col[j] / den, sj = den == 0.0 ? 0.0 : col[j + 1] / den;
-    a.cs[j] = cj;
-    a.sn[j] = sj;
+    S.cs[j] = cj;
+    S.sn[j] = sj;
     col[j] = cj * col[j] + sj * col[j + 1];
     for (int l = 0; l <= j; ++l) Hj[l] = col[l];
     Hj[j + 1] = 0.0;
-    const double gj = a.g[j];
-    a.g[j + 1] = -sj * gj;
-    a.g[j] = cj * gj;
+    const double gj = S.g[j];
+    S.g[j + 1] = -sj * gj;
+    S.g[j] = cj * gj;
     c->its += 1;
     c->k = j + 1;
-    const double est = fabs(a.g[j + 1]) / c->bnorm;
-    a.hist[c->its - 1] = est;
+    const double est = fabs(S.g[j + 1]) / c->bnorm;
+    S.hist[c->its - 1] = est;
     c->rel = est;
     if (est <= c->rtol || c->its >= c->maxiter) c->run = 0;
 }
@@ -379,7 +432,8 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
 __global__ void __launch_bounds__(kKryThreads) kry_backsolve_kernel(KryArgs a) {
     __shared__ double R[kMaxRestart * (kMaxRestart + 1) / 2 > 0 ? 64 * 65 : 1];
     __shared__ double rhs[kMaxRestart + 1];
-    KryCtl *c = a.ctl;
+    const KrySys S = kry_sys(a, blockIdx.y);
+    KryCtl *c = S.c;
     const int k = c->k, m = a.m;
     if (k <= 0) return;
     // R(i, l) for i <= l < k; columns of up to 64 rows fit the tile, longer
@@ -387,42 +441,44 @@ __global__ void __launch_bounds__(kKryThreads) kry_backsolve_kernel(KryArgs a) {
     const bool staged = k <= 64;
     for (int e = threadIdx.x; e < k * k && staged; e += blockDim.x) {
         const int i = e % k, l = e / k;
-        R[i * 65 + l] = i <= l ? a.H[(size_t)l * (m + 1) + i] : 0.0;
+        R[i * 65 + l] = i <= l ? S.H[(size_t)l * (m + 1) + i] : 0.0;
     }
-    for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = a.g[i];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = S.g[i];
     __syncthreads();
     for (int i = k - 1; i >= 0; --i) {
-        const double rii = staged ? R[i * 65 + i] : a.H[(size_t)i * (m + 1) + i];
+        const double rii = staged ? R[i * 65 + i] : S.H[(size_t)i * (m + 1) + i];
         const double yi = rhs[i] / rii;  // every thread reads the finished rhs[i]
         __syncthreads();
         if (threadIdx.x == 0) rhs[i] = yi;
         for (int l = threadIdx.x; l < i; l += blockDim.x)
-            rhs[l] -= (staged ? R[l * 65 + i] : a.H[(size_t)i * (m + 1) + l]) * yi;
+            rhs[l] -= (staged ? R[l * 65 + i] : S.H[(size_t)i * (m + 1) + l]) * yi;
         __syncthreads();
     }
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        a.h[i] = rhs[i];
-        a.coef[i] = rhs[i] * a.s[i];
+        S.h[i] = rhs[i];
+        S.coef[i] = rhs[i] * S.s[i];
     }
 }
 
 // t = sum_{l<k} coef_l V_l (accumulate = 1: t += that sum)
 __global__ void __launch_bounds__(kKryThreads) kry_combine_kernel(KryArgs a, double *t, int accumulate) {
     __shared__ double cf[kMaxRestart + 1];
-    KryCtl *c = a.ctl;
-    const int k = c->k;
+    const KrySys S = kry_sys(a, blockIdx.y);
+    const int k = S.c->k;
     if (k <= 0) return;
-    for (int l = threadIdx.x; l < k; l += blockDim.x) cf[l] = a.coef[l];
+    for (int l = threadIdx.x; l < k; l += blockDim.x) cf[l] = S.coef[l];
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
+    const double *V0 = a.V + S.base + i;
+    t += S.base;
     double u0 = 0.0, u1 = 0.0;
     int l = 0;
     for (; l + 2 <= k; l += 2) {
-        u0 = fma(cf[l], __ldg(a.V + (size_t)l * a.n + i), u0);
-        u1 = fma(cf[l + 1], __ldg(a.V + (size_t)(l + 1) * a.n + i), u1);
+        u0 = fma(cf[l], __ldg(V0 + (size_t)l * a.N), u0);
+        u1 = fma(cf[l + 1], __ldg(V0 + (size_t)(l + 1) * a.N), u1);
     }
-    if (l < k) u0 = fma(cf[l], __ldg(a.V + (size_t)l * a.n + i), u0);
+    if (l < k) u0 = fma(cf[l], __ldg(V0 + (size_t)l * a.N), u0);
     const double u = u0 + u1;
     if (accumulate)
         t[i] += u;
@@ -430,7 +486,10 @@ __global__ void __launch_bounds__(kKryThreads) kry_combine_kernel(KryArgs a, dou
         t[i] = u;
 }
 
-__global__ void kry_init_kernel(KryCtl *c, int maxiter, double rtol) {
+__global__ void kry_init_kernel(KryCtl *ctls, int K, int maxiter, double rtol) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    KryCtl *c = ctls + k;
     c->run = maxiter > 0;
     c->k = 0;
     c->its = 0;
@@ -450,14 +509,22 @@ int lanes_for(int n, int64_t nnz) {
     return L;
 }
 
-cudaError_t spmv(cudaStream_t st, const KryArgs &a, int gate, const KryOp &op, const double *x, const double *s,
-                 const double *b, double *y, int mode) {
+// Operators of a solve: device tables (A and M one entry per system, P one
+// shared entry; M / P nullptr for the identity) and the largest row mean of
+// each (lanes per row).
+struct KryOps {
+    const KryOp *A = nullptr, *M = nullptr, *P = nullptr;
+    int64_t a_nnz = 0, m_nnz = 0, p_nnz = 0;  // largest nnz over the systems
+};
+
+cudaError_t spmv(cudaStream_t st, const KryArgs &a, int gate, const KryOp *ops, int per_system, int64_t nnz,
+                 const double *x, const double *s, int s_stride, const double *b, double *y, int mode) {
     const int n = a.n;
-    const int L = lanes_for(n, op.nnz);
+    const int L = lanes_for(n, nnz);
     const int64_t threads = (int64_t)n * L;
-    const unsigned blocks = (unsigned)((threads + kKryThreads - 1) / kKryThreads);
-#define SAM_KRY_SPMV(LL)                                                                                      \
-    kry_spmv_kernel<LL><<<blocks, kKryThreads, 0, st>>>(a.ctl, gate, n, op.rp, op.ci, op.v, x, s, b, y, mode); \
+    const dim3 grid((unsigned)((threads + kKryThreads - 1) / kKryThreads), (unsigned)a.K);
+#define SAM_KRY_SPMV(LL)                                                                                          \
+    kry_spmv_kernel<LL><<<grid, kKryThreads, 0, st>>>(a.ctl, gate, n, ops, per_system, x, s, s_stride, b, y, mode); \
     break;
     switch (L) {
         case 1: SAM_KRY_SPMV(1)
@@ -471,71 +538,75 @@ cudaError_t spmv(cudaStream_t st, const KryArgs &a, int gate, const KryOp &op, c
     return cudaGetLastError();
 }
 
-// The launches of one restart cycle (all gated on the control word):
-// m Arnoldi steps, the update of x, and the residual of the next cycle.
-// Returns the number of kernels enqueued, or -1 on a launch error.
-int enqueue_cycle(cudaStream_t st, const KryArgs &a, const KryOp &A, const KryOp &M, const KryOp &P,
-                  const double *b, double *x, double *t, double *u) {
+// The launches of one restart cycle (all gated on the systems' control
+// words): m Arnoldi steps, the update of x, and the residual of the next
+// cycle.  Returns the number of kernels enqueued, or -1 on a launch error.
+int enqueue_cycle(cudaStream_t st, const KryArgs &a, const KryOps &op, const double *b, double *x, double *t,
+                  double *u) {
     int launches = 0;
-    const unsigned nb = (unsigned)a.nblk;
+    const dim3 gb((unsigned)a.nblk, (unsigned)a.K);
+    const int ss = a.m + 1;  // stride of the per-system scales
     auto ok = [&](cudaError_t e) { return e == cudaSuccess; };
+    // w = A z fused into the first Gram-Schmidt pass when a row of A fits one
+    // lane, a separate product otherwise
+    const bool fuse = lanes_for(a.n, op.a_nnz) == 1;
     for (int j = 0; j < a.m; ++j) {
         // z = M (P_0 (s_j V_j)), the identity where an operator is absent
-        const double *z = a.V + (size_t)j * a.n;
+        const double *z = a.V + (size_t)j * a.N;
         const double *zs = a.s + j;
-        if (P.rp) {
-            if (!ok(spmv(st, a, kGateRun, P, z, zs, nullptr, t, 0))) return -1;
+        if (op.P) {
+            if (!ok(spmv(st, a, kGateRun, op.P, 0, op.p_nnz, z, zs, ss, nullptr, t, 0))) return -1;
             ++launches;
             z = t;
             zs = nullptr;
         }
-        if (M.rp) {
-            if (!ok(spmv(st, a, kGateRun, M, z, zs, nullptr, u, 0))) return -1;
+        if (op.M) {
+            if (!ok(spmv(st, a, kGateRun, op.M, 1, op.m_nnz, z, zs, ss, nullptr, u, 0))) return -1;
             ++launches;
             z = u;
             zs = nullptr;
         }
-        // w = A z: fused into the first Gram-Schmidt pass when a row of A
-        // fits one lane, a separate product otherwise
-        const bool fuse = lanes_for(a.n, A.nnz) == 1;
         if (!fuse) {
-            if (!ok(spmv(st, a, kGateRun, A, z, zs, nullptr, a.V + (size_t)(j + 1) * a.n, 0))) return -1;
+            if (!ok(spmv(st, a, kGateRun, op.A, 1, op.a_nnz, z, zs, ss, nullptr, a.V + (size_t)(j + 1) * a.N, 0)))
+                return -1;
             ++launches;
         }
         for (int pass = 0; pass < 3; ++pass) {
             if (pass == 0 && fuse)
-                kry_orth_kernel<<<nb, kKryThreads, 0, st>>>(a, j, pass, A, z, zs);
+                kry_orth_kernel<<<gb, kKryThreads, 0, st>>>(a, j, pass, op.A, z, zs, ss);
             else
-                kry_orth_kernel<<<nb, kKryThreads, 0, st>>>(a, j, pass, KryOp(), nullptr, nullptr);
+                kry_orth_kernel<<<gb, kKryThreads, 0, st>>>(a, j, pass, nullptr, nullptr, nullptr, 0);
             if (!ok(cudaGetLastError())) return -1;
             ++launches;
         }
     }
     // x += M (P_0 (sum_l y_l s_l V_l))
-    kry_backsolve_kernel<<<1, kKryThreads, 0, st>>>(a);
+    kry_backsolve_kernel<<<dim3(1, (unsigned)a.K), kKryThreads, 0, st>>>(a);
     ++launches;
-    if (!P.rp && !M.rp) {
-        kry_combine_kernel<<<nb, kKryThreads, 0, st>>>(a, x, 1);
+    if (!op.P && !op.M) {
+        kry_combine_kernel<<<gb, kKryThreads, 0, st>>>(a, x, 1);
         ++launches;
     } else {
         // the sum goes to the temporary the first operator does not write
-        double *sum = P.rp ? u : t;
-        kry_combine_kernel<<<nb, kKryThreads, 0, st>>>(a, sum, 0);
+        double *sum = op.P ? u : t;
+        kry_combine_kernel<<<gb, kKryThreads, 0, st>>>(a, sum, 0);
         ++launches;
         const double *cur = sum;
-        if (P.rp && M.rp) {
-            if (!ok(spmv(st, a, kGateCycle, P, cur, nullptr, nullptr, t, 0))) return -1;
+        if (op.P && op.M) {
+            if (!ok(spmv(st, a, kGateCycle, op.P, 0, op.p_nnz, cur, nullptr, 0, nullptr, t, 0))) return -1;
             ++launches;
             cur = t;
         }
-        const KryOp &last = M.rp ? M : P;
-        if (!ok(spmv(st, a, kGateCycle, last, cur, nullptr, nullptr, x, 2))) return -1;
+        const bool last_m = op.M != nullptr;
+        if (!ok(spmv(st, a, kGateCycle, last_m ? op.M : op.P, last_m ? 1 : 0, last_m ? op.m_nnz : op.p_nnz, cur,
+                     nullptr, 0, nullptr, x, 2)))
+            return -1;
         ++launches;
     }
     if (!ok(cudaGetLastError())) return -1;
     // next cycle: V_0 = b - A x, beta, stopping test
-    if (!ok(spmv(st, a, kGateRun, A, x, nullptr, b, a.V, 1))) return -1;
-    kry_norm_kernel<<<nb, kKryThreads, 0, st>>>(a, a.V, 1);
+    if (!ok(spmv(st, a, kGateRun, op.A, 1, op.a_nnz, x, nullptr, 0, b, a.V, 1))) return -1;
+    kry_norm_kernel<<<gb, kKryThreads, 0, st>>>(a, a.V, 1);
     launches += 2;
     if (!ok(cudaGetLastError())) return -1;
     return launches;
@@ -543,13 +614,14 @@ int enqueue_cycle(cudaStream_t st, const KryArgs &a, const KryOp &A, const KryOp
 
 }  // namespace
 
-sam_status gmres_solve(sam_handle h, int n, const KryOp &A, const KryOp &M, const KryOp &P, const double *b,
+sam_status gmres_solve(sam_handle h, int K, int n, const KryOp *A, const KryOp *M, const KryOp &P, const double *b,
                        double *x, int restart, int maxiter, double rtol, double *hist_dev, int32_t *its_out,
                        double *rel_out, int64_t *launches_out) {
     cudaStream_t st = handle_stream(h);
     const int m = restart;
     const int nblk = (int)((n + kKryThreads - 1) / kKryThreads);
-    const size_t vec = (size_t)n;
+    const int64_t N = (int64_t)K * n;
+    const size_t m1 = (size_t)m + 1;
     std::vector<void *> mem;
     bool oom = false;
     auto get = [&](size_t bytes) {
@@ -568,43 +640,68 @@ sam_status gmres_solve(sam_handle h, int n, const KryOp &A, const KryOp &M, cons
     a.n = n;
     a.m = m;
     a.nblk = nblk;
-    a.ctl = (KryCtl *)get(sizeof(KryCtl));
-    a.V = (double *)get(sizeof(double) * vec * (m + 1));
-    a.H = (double *)get(sizeof(double) * (size_t)(m + 1) * m);
-    a.cs = (double *)get(sizeof(double) * (m + 1));
-    a.sn = (double *)get(sizeof(double) * (m + 1));
-    a.g = (double *)get(sizeof(double) * (m + 1));
-    a.s = (double *)get(sizeof(double) * (m + 1));
-    a.h = (double *)get(sizeof(double) * (m + 1));
-    a.coef = (double *)get(sizeof(double) * (m + 1));
-    a.hist = hist_dev ? hist_dev : (double *)get(sizeof(double) * (size_t)(maxiter > 0 ? maxiter : 1));
-    a.part = (double *)get(sizeof(double) * (size_t)nblk * (m + 1));
-    double *t = (double *)get(sizeof(double) * vec);
-    double *u = (double *)get(sizeof(double) * vec);
+    a.K = K;
+    a.N = N;
+    a.hstride = maxiter > 0 ? maxiter : 1;
+    a.ctl = (KryCtl *)get(sizeof(KryCtl) * K);
+    a.V = (double *)get(sizeof(double) * (size_t)N * m1);
+    a.H = (double *)get(sizeof(double) * K * m1 * m);
+    a.cs = (double *)get(sizeof(double) * K * m1);
+    a.sn = (double *)get(sizeof(double) * K * m1);
+    a.g = (double *)get(sizeof(double) * K * m1);
+    a.s = (double *)get(sizeof(double) * K * m1);
+    a.h = (double *)get(sizeof(double) * K * m1);
+    a.coef = (double *)get(sizeof(double) * K * m1);
+    a.hist = hist_dev ? hist_dev : (double *)get(sizeof(double) * (size_t)K * a.hstride);
+    a.part = (double *)get(sizeof(double) * K * m1 * nblk);
+    double *t = (double *)get(sizeof(double) * (size_t)N);
+    double *u = (double *)get(sizeof(double) * (size_t)N);
+    // operator tables
+    KryOps op;
+    KryOp *dA = (KryOp *)get(sizeof(KryOp) * K);
+    KryOp *dM = M ? (KryOp *)get(sizeof(KryOp) * K) : nullptr;
+    KryOp *dP = P.rp ? (KryOp *)get(sizeof(KryOp)) : nullptr;
     if (oom) return release(SAM_ERR_OOM);
-    int64_t launches = 0;
-    KryCtl hc;
-    // ||b||, then the first residual (b - A x0) and its norm
-    kry_init_kernel<<<1, 1, 0, st>>>(a.ctl, maxiter, rtol);
-    kry_norm_kernel<<<nblk, kKryThreads, 0, st>>>(a, b, 0);
-    launches += 2;
-    if (cudaMemcpyAsync(&hc, a.ctl, sizeof(KryCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-        return release(SAM_ERR_CUDA);
-    if (!std::isfinite(hc.bnorm)) return release(SAM_ERR_NONFINITE);
-    if (hc.bnorm == 0.0) {  // b = 0: x = 0, no steps
-        cudaMemsetAsync(x, 0, sizeof(double) * vec, st);
-        if (cudaStreamSynchronize(st) != cudaSuccess) return release(SAM_ERR_CUDA);
-        if (its_out) *its_out = 0;
-        if (rel_out) *rel_out = 0.0;
-        if (launches_out) *launches_out = launches;
-        count_launch(h, (int)launches);
-        return release(SAM_OK);
+    cudaMemcpyAsync(dA, A, sizeof(KryOp) * K, cudaMemcpyHostToDevice, st);
+    if (dM) cudaMemcpyAsync(dM, M, sizeof(KryOp) * K, cudaMemcpyHostToDevice, st);
+    if (dP) cudaMemcpyAsync(dP, &P, sizeof(KryOp), cudaMemcpyHostToDevice, st);
+    op.A = dA;
+    op.M = dM;
+    op.P = dP;
+    for (int k = 0; k < K; ++k) {
+        op.a_nnz = std::max(op.a_nnz, A[k].nnz);
+        if (M) op.m_nnz = std::max(op.m_nnz, M[k].nnz);
     }
-    if (spmv(st, a, kGateAlways, A, x, nullptr, b, a.V, 1) != cudaSuccess) return release(SAM_ERR_CUDA);
-    kry_norm_kernel<<<nblk, kKryThreads, 0, st>>>(a, a.V, 2);
+    op.p_nnz = P.nnz;
+    const dim3 gb((unsigned)nblk, (unsigned)K);
+    int64_t launches = 0;
+    std::vector<KryCtl> hc((size_t)K);
+    auto read_ctl = [&]() {
+        return cudaMemcpyAsync(hc.data(), a.ctl, sizeof(KryCtl) * K, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+               cudaStreamSynchronize(st) == cudaSuccess;
+    };
+    // ||b_k||, then the first residuals (b_k - A_k x0_k) and their norms
+    kry_init_kernel<<<(K + 127) / 128, 128, 0, st>>>(a.ctl, K, maxiter, rtol);
+    kry_norm_kernel<<<gb, kKryThreads, 0, st>>>(a, b, 0);
     launches += 2;
-    // one restart cycle, captured once and replayed while the iteration runs
+    if (!read_ctl()) return release(SAM_ERR_CUDA);
+    bool any_zero = false;
+    for (int k = 0; k < K; ++k) {
+        if (!std::isfinite(hc[k].bnorm)) return release(SAM_ERR_NONFINITE);
+        any_zero = any_zero || hc[k].bnorm == 0.0;
+    }
+    if (any_zero) {
+        // b_k = 0: x_k = 0 and no steps for that system
+        for (int k = 0; k < K; ++k)
+            if (hc[k].bnorm == 0.0) {
+                cudaMemsetAsync(x + (size_t)k * n, 0, sizeof(double) * n, st);
+                cudaMemsetAsync(&a.ctl[k].run, 0, sizeof(int), st);
+            }
+    }
+    if (spmv(st, a, kGateRun, op.A, 1, op.a_nnz, x, nullptr, 0, b, a.V, 1) != cudaSuccess) return release(SAM_ERR_CUDA);
+    kry_norm_kernel<<<gb, kKryThreads, 0, st>>>(a, a.V, 2);
+    launches += 2;
+    // one restart cycle, captured once and replayed while any system runs
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -618,7 +715,7 @@ sam_status gmres_solve(sam_handle h, int n, const KryOp &A, const KryOp &M, cons
         drop_graph();
         return release(SAM_ERR_CUDA);
     }
-    const int per_cycle = enqueue_cycle(cap, a, A, M, P, b, x, t, u);
+    const int per_cycle = enqueue_cycle(cap, a, op, b, x, t, u);
     cudaError_t ce = cudaStreamEndCapture(cap, &graph);
     if (per_cycle < 0 || ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
         cudaGetLastError();
@@ -627,16 +724,20 @@ sam_status gmres_solve(sam_handle h, int n, const KryOp &A, const KryOp &M, cons
     }
     sam_status status = SAM_OK;
     for (;;) {
-        if (cudaMemcpyAsync(&hc, a.ctl, sizeof(KryCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) {
+        if (!read_ctl()) {
             status = SAM_ERR_CUDA;
             break;
         }
-        if (!std::isfinite(hc.rel)) {
+        bool any_run = false, bad = false;
+        for (int k = 0; k < K; ++k) {
+            any_run = any_run || hc[k].run;
+            bad = bad || !std::isfinite(hc[k].rel);
+        }
+        if (bad) {
             status = SAM_ERR_NONFINITE;
             break;
         }
-        if (!hc.run) break;
+        if (!any_run) break;
         if (cudaGraphLaunch(exec, st) != cudaSuccess) {
             status = SAM_ERR_CUDA;
             break;
@@ -645,8 +746,10 @@ sam_status gmres_solve(sam_handle h, int n, const KryOp &A, const KryOp &M, cons
     }
     drop_graph();
     count_launch(h, (int)launches);
-    if (its_out) *its_out = hc.its;
-    if (rel_out) *rel_out = hc.rel;
+    for (int k = 0; k < K; ++k) {
+        if (its_out) its_out[k] = hc[k].bnorm == 0.0 ? 0 : hc[k].its;
+        if (rel_out) rel_out[k] = hc[k].bnorm == 0.0 ? 0.0 : hc[k].rel;
+    }
     if (launches_out) *launches_out = launches;
     return release(status);
 }

@@ -117,6 +117,9 @@ _SIGS = [
     ("sam_gmres", ctypes.c_int32,
      [_vp, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), _vp, _vp, ctypes.c_int,
       ctypes.c_int, ctypes.c_double, _i32p, _f64p, _vp]),
+    ("sam_gmres_batched", ctypes.c_int32,
+     [_vp, ctypes.c_int, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), _vp, _vp,
+      ctypes.c_int, ctypes.c_int, ctypes.c_double, _i32p, _f64p, _vp]),
     ("sam_residual_static", ctypes.c_int32,
      [_vp, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), _vp, _vp]),
 ]
@@ -498,6 +501,27 @@ class Handle:
                                 int(maxiter), float(rtol), ctypes.byref(its), ctypes.byref(rel), _addr(history)),
                "sam_gmres")
         return x, its.value, rel.value
+
+    def sam_gmres_batched(self, As: list, b, x=None, Ms: list | None = None, P_0: Csr | None = None,
+                          restart: int = 30, maxiter: int = 1000, rtol: float = 1e-8, history=None):
+        """K independent restarted GMRES solves A_k x_k = b_k with the right
+        preconditioners M_k (P_0 v), in the same launches.  b, x: [K*n]
+        (system k at k*n).  Returns (x, iterations[K], relres[K])."""
+        import torch
+
+        K = len(As)
+        if x is None:
+            x = torch.zeros_like(b) if hasattr(b, "data_ptr") else np.zeros_like(b)
+        its = np.zeros(K, dtype=np.int32)
+        rel = np.zeros(K, dtype=np.float64)
+        a = (sam_csr * K)(*[m.c() for m in As])
+        m = (sam_csr * K)(*[q.c() for q in Ms]) if Ms is not None else None
+        p = P_0.c() if P_0 is not None else None
+        _check(load().sam_gmres_batched(self.ptr, K, a, m, ctypes.byref(p) if p is not None else None, _addr(b),
+                                        _addr(x), int(restart), int(maxiter), float(rtol),
+                                        its.ctypes.data_as(_i32p), rel.ctypes.data_as(_f64p), _addr(history)),
+               "sam_gmres_batched")
+        return x, its, rel
 
     def sam_build_backward(self, A_k: Csr, A_0: Csr, S: Pattern, M_val, dM_val=None, precision="fp32r",
                            refine_steps: int = 1, resid_weight: float = 0.0, dA_k_val=None, dA_0_val=None,

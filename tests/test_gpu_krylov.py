@@ -258,3 +258,52 @@ def test_long_cycles(sam, handle, restart):
     gpu = run_gpu(sam, handle, Ak, b, P=P, **kw)
     assert gpu[1] > 64
     compare(Ak, b, gpu, oracle.gmres(Ak, b, P0=P, **kw), 1e-10, 1e-6)
+
+
+def test_batched_equals_single_solves(sam, handle):
+    """K solves of a sequence (A_k with its map M_k, one P_0) in the same
+    launches: every system's steps, estimates and solution equal, bit for
+    bit, its own sam_gmres call, and the oracle's within rounding; systems
+    stop at different steps."""
+    import torch
+
+    seq = W.config2(nx=24, nmat=4)
+    A0 = seq.mats[0]
+    P = spai(A0)
+    Ms = [oracle_map_csr(seq.mats[k], A0, 2) for k in (1, 2, 3)]
+    As = [seq.mats[k] for k in (1, 2, 3)]
+    n = A0.n
+    bs = [rhs(n, 20 + k) for k in range(3)]
+    kw = dict(restart=20, maxiter=400, rtol=1e-10)
+    dA = [sam.Csr.from_host(a) for a in As]
+    dM = [sam.Csr.from_host(m) for m in Ms]
+    dP = sam.Csr.from_host(P)
+    b = torch.from_numpy(np.concatenate(bs)).cuda()
+    hist = torch.full((3 * kw["maxiter"],), -1.0, dtype=torch.float64, device="cuda")
+    x, its, rel = handle.sam_gmres_batched(dA, b, Ms=dM, P_0=dP, history=hist, **kw)
+    x, hist = x.cpu().numpy(), hist.cpu().numpy().reshape(3, -1)
+    for k in range(3):
+        xs, its1, rel1, h1 = run_gpu(sam, handle, As[k], bs[k], M=Ms[k], P=P, **kw)
+        assert its[k] == its1 and rel[k] == rel1
+        assert np.array_equal(x[k * n:(k + 1) * n], xs)
+        assert np.array_equal(hist[k, :its1], h1)
+        compare(As[k], bs[k], (x[k * n:(k + 1) * n], its[k], rel[k], hist[k, :its[k]]),
+                oracle.gmres(As[k], bs[k], M=Ms[k], P0=P, **kw), 1e-10, 1e-6)
+
+
+def test_batched_zero_rhs_and_host_arrays(sam, handle):
+    """A zero right-hand side in the batch gives x_k = 0 and no steps while
+    the others solve; numpy arrays go through the staging."""
+    seq = W.config3(nx=8, nmat=3)
+    As = seq.mats
+    n = As[0].n
+    b = np.concatenate([rhs(n, 1), np.zeros(n), rhs(n, 3)])
+    x = np.ones(3 * n)
+    kw = dict(restart=15, maxiter=300, rtol=1e-11)
+    x, its, rel = handle.sam_gmres_batched([sam.Csr.from_host(a) for a in As], b, x, P_0=sam.Csr.from_host(jacobi(As[0])),
+                                           **kw)
+    assert its[1] == 0 and np.all(x[n:2 * n] == 0.0)
+    for k in (0, 2):
+        xo, ito, ho = oracle.gmres(As[k], b[k * n:(k + 1) * n], x0=np.ones(n), P0=jacobi(As[0]), **kw)
+        assert abs(int(its[k]) - ito) <= 1
+        assert np.linalg.norm(x[k * n:(k + 1) * n] - xo) <= 1e-6 * np.linalg.norm(xo)
