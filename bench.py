@@ -531,6 +531,45 @@ def config_figures(h, sam, torch, dev, stream, nsteps=7):
     return out
 
 
+# ------------------------------------------------------------ CD2D study
+
+
+def cd2d_study(h, sam, torch, dev, stream):
+    """The paper's comparison (Sec. 5.1, Figs. 3-4, Tables 1-2) on the CD2D
+    stand-in, through the GPU path: for each pattern choice -- S(A_0), and
+    the square / cube of S(A~_k) for the column threshold and lfil
+    sparsifications -- all 66 maps N_k onto A_0 in one batched build, with
+    the pattern sizes and the relative residual ||A_k N_k - A_0||_F / ||A_0||_F
+    per map (min / mean / max over the sequence)."""
+    from paper_2406_17656_gb300 import workloads as W
+
+    seq = W.cd2d()
+    aks = [sam.Csr.from_host(m, dev) for m in seq.mats]
+    a0 = aks[0]
+    K = len(aks)
+    nrm0 = float(np.linalg.norm(seq.mats[0].data))
+    choices = [("S(A_0)", None, None, 1), ("tau 0.6, square", "tau", 0.6, 2), ("tau 0.7, square", "tau", 0.7, 2),
+               ("tau 0.8, square", "tau", 0.8, 2), ("lfil 3, square", "lfil", 3, 2), ("lfil 5, square", "lfil", 5, 2),
+               ("tau 0.8, cube", "tau", 0.8, 3), ("lfil 5, cube", "lfil", 5, 3)]
+    out = {"workload": "cd2d_64x64_seq66 (Newton-with-line-search Jacobians, n = 4096)", "maps": K}
+    torch.cuda.synchronize()
+    for name, mode, param, power in choices:
+        t0 = time.perf_counter()
+        if mode is None:
+            pats = [h.sam_pattern_build(a0, power)] * K
+        else:
+            pats = h.sam_pattern_build_batched(h.sam_sparsify_batched(aks, mode, param), power)
+        _, _, _, _, fro = h.sam_build_batched(aks, a0, pats, "fp32r", 1, want_fro=True)
+        torch.cuda.synchronize()
+        rel = np.asarray(fro) / nrm0
+        out[name] = {"nnz_per_map": sorted({int(p.nnz) for p in pats}), "rel_residual_min": float(rel[1:].min()),
+                     "rel_residual_mean": float(rel[1:].mean()), "rel_residual_max": float(rel[1:].max()),
+                     "ms": (time.perf_counter() - t0) * 1e3}
+        for p in set(pats):
+            p.destroy()
+    return out
+
+
 # ------------------------------------------------------------------- ours
 
 
@@ -745,6 +784,7 @@ def main():
     # ---- the other workloads of the same path (patterns + batched maps per step)
     if not args.quick and not args.no_configs and world == 1:
         extra["configs"] = config_figures(h, sam, torch, dev, stream)
+        extra["cd2d_study"] = cd2d_study(h, sam, torch, dev, stream)
 
     # ---- roofline of the dominant kernel (largest least-squares size class)
     sizes = column_sizes(seq.mats, args.level)
