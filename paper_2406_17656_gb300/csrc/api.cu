@@ -177,7 +177,47 @@ struct Stager {
     };
     std::vector<Out> outs;
     bool failed = false;
+    // host outputs copied early on a side stream (flush_early), joined back
+    // into st by finish() or, on an error path, by the destructor
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_ready = nullptr, ev_done = nullptr;
+    bool early_pending = false;
     Stager(Scratch &s, cudaStream_t stream) : sc(s), st(stream) {}
+    ~Stager() {
+        join();
+        if (ev_ready) cudaEventDestroy(ev_ready);
+        if (ev_done) cudaEventDestroy(ev_done);
+        if (side) cudaStreamDestroy(side);
+    }
+    // st waits for the early copies (before the workspace they read is freed)
+    void join() {
+        if (!early_pending) return;
+        cudaEventRecord(ev_done, side);
+        cudaStreamWaitEvent(st, ev_done, 0);
+        early_pending = false;
+    }
+    // The host output staged in dev is final once the work enqueued on st so
+    // far completes: copy it to the host on a side stream, overlapping what st
+    // does next.  Device outputs need nothing.
+    cudaError_t flush_early(const void *dev) {
+        for (size_t q = 0; q < outs.size(); ++q) {
+            if (outs[q].dev != dev) continue;
+            if (!side) {
+                if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming) != cudaSuccess)
+                    return cudaGetLastError();
+            }
+            cudaEventRecord(ev_ready, st);
+            cudaStreamWaitEvent(side, ev_ready, 0);
+            cudaError_t e = cudaMemcpyAsync(outs[q].host, outs[q].dev, outs[q].bytes, cudaMemcpyDeviceToHost, side);
+            if (e != cudaSuccess) return e;
+            early_pending = true;
+            outs.erase(outs.begin() + (std::ptrdiff_t)q);
+            return cudaSuccess;
+        }
+        return cudaSuccess;
+    }
     template <typename T>
     const T *in(const T *p, size_t count) {
         if (!p || count == 0 || is_device_ptr(p)) return p;
@@ -197,6 +237,7 @@ struct Stager {
             return nullptr;
         }
         outs.push_back({(void *)p, (const void *)d, sizeof(T) * count});
+        any_host = true;
         return d;
     }
     // an array read and written by the call (staged both ways if on the host)
@@ -209,15 +250,18 @@ struct Stager {
             return nullptr;
         }
         outs.push_back({(void *)p, (const void *)d, sizeof(T) * count});
+        any_host = true;
         return d;
     }
-    bool has_host_outputs() const { return !outs.empty(); }
+    bool any_host = false;  // some output is a host array (the call must synchronise)
+    bool has_host_outputs() const { return any_host; }
     cudaError_t finish() {
         for (auto &o : outs) {
             cudaError_t e = cudaMemcpyAsync(o.host, o.dev, o.bytes, cudaMemcpyDeviceToHost, st);
             if (e != cudaSuccess) return e;
         }
-        return cudaSuccess;
+        join();
+        return cudaGetLastError();
     }
 };
 
@@ -1144,11 +1188,14 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
         if (!a.refine_used || !bin2 || !work2 || !bin_off2) return SAM_ERR_OOM;
         cudaMemsetAsync(a.refine_used, 0, (size_t)N, st);
     }
+    // CSR structure of every map (it depends on the patterns alone): written
+    // before the solves, so that a copy to host outputs overlaps them
+    if (split_map_structure(h, K, n, g->mrp, g->mci, d_rp, d_ci) != cudaSuccess ||
+        sg.flush_early(d_rp) != cudaSuccess || sg.flush_early(d_ci) != cudaSuccess)
+        return SAM_ERR_CUDA;
     if (launch_lsq(h, precision, a) != cudaSuccess) return SAM_ERR_CUDA;
     if (autoref && launch_refine_fallback(h, a, (int)N, bin, bin2, work2, bin_off2, nullptr, h->d_refine) != cudaSuccess)
         return SAM_ERR_CUDA;
-    // CSR structure of every map
-    if (split_map_structure(h, K, n, g->mrp, g->mci, d_rp, d_ci) != cudaSuccess) return SAM_ERR_CUDA;
     if (status_reduce(h, d_st, N, h->d_flag) != cudaSuccess) return SAM_ERR_CUDA;
     double *fro_dev = nullptr;
     if (fro) {
