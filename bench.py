@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--profile-gmres", type=int, default=0, metavar="STEPS",
                     help="profiling aid: run one GMRES solve of STEPS Arnoldi steps on the benchmark's last map "
                          "and exit (no JSON line)")
+    ap.add_argument("--profile-fem", type=int, default=0, metavar="STEPS",
+                    help="profiling aid: run STEPS whole steps (level-2 patterns + batched maps + residuals) of "
+                         "the 16-map P1 FEM 512x512 sequence and exit (no JSON line)")
     return ap.parse_args()
 
 
@@ -422,6 +425,24 @@ def profile_gmres(h, sam, torch, dev, aks, a0, n, level, steps):
     print("gmres: %d steps, estimate %.3e, %.1f us per step" % (its, rel, (time.perf_counter() - t) * 1e6 / its))
 
 
+def profile_fem(h, sam, torch, dev, steps):
+    """`steps` whole steps of the P1 FEM sequence whose pattern changes from
+    map to map (the workload of the configuration figures), for ncu."""
+    from paper_2406_17656_gb300 import workloads as W
+
+    seq = W.config4()
+    aks = [sam.Csr.from_host(m, dev) for m in seq.mats]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(steps):
+        ps = h.sam_pattern_build_batched(aks, 2)
+        h.sam_build_batched(aks, aks[0], ps, "fp32r", 1, want_fro=True)
+        for p in ps:
+            p.destroy()
+    torch.cuda.synchronize()
+    print("fem: %d steps, %.2f ms per step" % (steps, (time.perf_counter() - t) * 1e3 / steps))
+
+
 # ------------------------------------------------------------ all configs
 
 
@@ -632,6 +653,11 @@ def main():
         dist.barrier()
     sam.load()
     dev = torch.device("cuda", torch.cuda.current_device())
+    if args.profile_fem > 0:
+        h = sam.Handle(stream=torch.cuda.current_stream())
+        profile_fem(h, sam, torch, dev, args.profile_fem)
+        h.close()
+        return
 
     seq = W.config2(nx=args.nx, nmat=args.maps, level=args.level)
     a0h = seq.mats[0]

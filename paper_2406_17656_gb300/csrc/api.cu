@@ -27,6 +27,7 @@ struct sam_handle_t {
     cudaMemPool_t pool = nullptr;
     int32_t *d_flag = nullptr;  // sticky device status word
     int32_t *h_flag = nullptr;  // pinned mirror
+    int32_t *h_bins = nullptr;  // pinned: one map's size-class offsets [kNumBins+1] (chunked builds)
     // tracing
     int64_t launches = 0;
     bool profiling = false;
@@ -44,6 +45,12 @@ struct sam_handle_t {
 };
 
 namespace {
+// Builds whose map values go to a host array: at most kMaxChunks chunks of
+// maps, each of about kChunkColumns columns or more (each chunk boundary
+// costs the tail of a persistent launch; the last chunk's copy is exposed)
+constexpr int64_t kMaxChunks = 8;
+constexpr int64_t kChunkColumns = 1 << 17;
+
 // K patterns of order n stored as one block-diagonal pattern
 struct PatternGroup {
     sam_handle h = nullptr;
@@ -174,6 +181,7 @@ struct Stager {
         void *host;
         const void *dev;
         size_t bytes;
+        size_t flushed;  // bytes already copied by flush_range
     };
     std::vector<Out> outs;
     bool failed = false;
@@ -218,6 +226,39 @@ struct Stager {
         }
         return cudaSuccess;
     }
+    // Bytes [off, off + bytes) of the host output staged in dev are final
+    // once the work enqueued on st so far completes: copy them on the side
+    // stream.  The output is dropped from the final copy once every byte has
+    // been flushed this way (the ranges must not overlap).
+    cudaError_t flush_range(const void *dev, size_t off, size_t bytes) {
+        for (size_t q = 0; q < outs.size(); ++q) {
+            if (outs[q].dev != dev) continue;
+            if (off + bytes > outs[q].bytes) return cudaErrorInvalidValue;
+            if (!side) {
+                if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming) != cudaSuccess)
+                    return cudaGetLastError();
+            }
+            if (bytes > 0) {
+                cudaEventRecord(ev_ready, st);
+                cudaStreamWaitEvent(side, ev_ready, 0);
+                cudaError_t e = cudaMemcpyAsync((char *)outs[q].host + off, (const char *)outs[q].dev + off, bytes,
+                                                cudaMemcpyDeviceToHost, side);
+                if (e != cudaSuccess) return e;
+                early_pending = true;
+            }
+            outs[q].flushed += bytes;
+            if (outs[q].flushed == outs[q].bytes) outs.erase(outs.begin() + (std::ptrdiff_t)q);
+            return cudaSuccess;
+        }
+        return cudaSuccess;
+    }
+    bool is_host_output(const void *dev) const {
+        for (const auto &o : outs)
+            if (o.dev == dev) return true;
+        return false;
+    }
     template <typename T>
     const T *in(const T *p, size_t count) {
         if (!p || count == 0 || is_device_ptr(p)) return p;
@@ -236,7 +277,7 @@ struct Stager {
             failed = true;
             return nullptr;
         }
-        outs.push_back({(void *)p, (const void *)d, sizeof(T) * count});
+        outs.push_back({(void *)p, (const void *)d, sizeof(T) * count, 0});
         any_host = true;
         return d;
     }
@@ -249,7 +290,7 @@ struct Stager {
             failed = true;
             return nullptr;
         }
-        outs.push_back({(void *)p, (const void *)d, sizeof(T) * count});
+        outs.push_back({(void *)p, (const void *)d, sizeof(T) * count, 0});
         any_host = true;
         return d;
     }
@@ -548,24 +589,33 @@ __global__ void replicate_cols_kernel(int64_t n, T *a) {
 // column, work[K t + k] = work0[t] + k n, off[c] = K off0[c], so that the
 // same column of every map is solved side by side (one block reads map 0's
 // metadata for all of them)
-__global__ void expand_work_kernel(int K, int n, const int32_t *work0, const int32_t *off0, int32_t *work,
+__global__ void expand_work_kernel(int K, int Kc, int n, const int32_t *work0, const int32_t *off0, int32_t *work,
                                    int32_t *off) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int k = blockIdx.y;
-    if (t < off0[kNumBins]) work[(int64_t)K * t + k] = work0[t] + k * n;
+    if (t < off0[kNumBins]) {
+        int b = 0;
+        while (t >= off0[b + 1]) ++b;
+        const int64_t c = off0[b + 1] - off0[b], tl = t - off0[b];
+        // maps in chunks of Kc: a chunk's items are contiguous within the
+        // class, its maps interleaved column by column
+        const int k0 = (k / Kc) * Kc, wq = min(Kc, K - k0);
+        work[(int64_t)K * off0[b] + (int64_t)k0 * c + wq * tl + (k - k0)] = work0[t] + k * n;
+    }
     if (t <= kNumBins && k == 0) off[t] = K * off0[t];
 }
 
 cudaError_t interleaved_work_list(sam_handle h, Scratch &sc, int K, int n, const uint8_t *bin, int32_t *work,
-                                  int32_t *bin_off) {
+                                  int32_t *bin_off, int Kc = 0, const int32_t **off0_out = nullptr) {
     int32_t *work0 = sc.get<int32_t>((size_t)n), *off0 = sc.get<int32_t>(kNumBins + 1);
     if (!work0 || !off0) return cudaErrorMemoryAllocation;
     cudaError_t e = build_work_list(h, n, bin, work0, off0);
     if (e != cudaSuccess) return e;
     const int64_t cnt = std::max<int64_t>(n, kNumBins + 1);
     dim3 grid((unsigned)((cnt + 255) / 256), (unsigned)K);
-    expand_work_kernel<<<grid, 256, 0, h->stream>>>(K, n, work0, off0, work, bin_off);
+    expand_work_kernel<<<grid, 256, 0, h->stream>>>(K, Kc > 0 && Kc < K ? Kc : K, n, work0, off0, work, bin_off);
     count_launch(h);
+    if (off0_out) *off0_out = off0;
     return cudaGetLastError();
 }
 
@@ -779,7 +829,7 @@ sam_status sam_create(sam_handle *out, void *cuda_stream) {
     cudaMemPoolSetAttribute(h->pool, cudaMemPoolAttrReleaseThreshold, &thr);
     if (cudaMalloc(&h->d_flag, sizeof(int32_t)) != cudaSuccess ||
         cudaMalloc(&h->d_refine, sizeof(int64_t) * (kAutoSteps + 1)) != cudaSuccess ||
-        cudaMallocHost(&h->h_flag, sizeof(int32_t)) != cudaSuccess) {
+        cudaMallocHost(&h->h_flag, sizeof(int32_t) * (2 + kNumBins)) != cudaSuccess) {
         cudaGetLastError();
         if (h->d_flag) cudaFree(h->d_flag);
         if (h->d_refine) cudaFree(h->d_refine);
@@ -790,6 +840,7 @@ sam_status sam_create(sam_handle *out, void *cuda_stream) {
     cudaMemset(h->d_flag, 0, sizeof(int32_t));
     cudaMemset(h->d_refine, 0, sizeof(int64_t) * (kAutoSteps + 1));
     *h->h_flag = 0;
+    h->h_bins = h->h_flag + 1;
     *out = h;
     return SAM_OK;
 }
@@ -1136,8 +1187,33 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     if (shared && (replicate_cols(h, K, n, icnt) != cudaSuccess || replicate_cols(h, K, n, bin) != cudaSuccess ||
                    replicate_cols(h, K, n, d_st) != cudaSuccess))
         return SAM_ERR_CUDA;
-    if ((shared ? interleaved_work_list(h, sc, K, n, bin, work, bin_off)
+    // Map values going to a host array: the solves of the large size classes
+    // run in chunks of maps, and each chunk's values are copied to the host
+    // while the next chunk is solved (one structure only, where every map has
+    // the same columns per class; the automatic mode re-solves columns after
+    // all chunks and is left whole)
+    const bool autoref = precision == SAM_FP32_REFINE && refine_steps < 0;
+    int Kc = K;
+    if (shared && !autoref && sg.is_host_output(d_v)) {
+        const int64_t chunks = std::min<int64_t>(std::min<int64_t>(K, kMaxChunks), std::max<int64_t>(1, N / kChunkColumns));
+        Kc = (int)((K + chunks - 1) / chunks);
+    }
+    const bool chunked = Kc < K;
+    cudaEvent_t ev_bins = nullptr;
+    struct EventGuard {
+        cudaEvent_t &e;
+        ~EventGuard() {
+            if (e) cudaEventDestroy(e);
+        }
+    } ev_guard{ev_bins};
+    const int32_t *off0 = nullptr;
+    if ((shared ? interleaved_work_list(h, sc, K, n, bin, work, bin_off, Kc, &off0)
                 : build_work_list(h, (int)N, bin, work, bin_off)) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    if (chunked && (cudaEventCreateWithFlags(&ev_bins, cudaEventDisableTiming) != cudaSuccess ||
+                    cudaMemcpyAsync(h->h_bins, off0, sizeof(int32_t) * (kNumBins + 1), cudaMemcpyDeviceToHost, st) !=
+                        cudaSuccess ||
+                    cudaEventRecord(ev_bins, st) != cudaSuccess))
         return SAM_ERR_CUDA;
     cudaMemsetAsync(d_v, 0, sizeof(double) * (size_t)total_nnz, st);
     cudaMemsetAsync(d_r2, 0, sizeof(double) * (size_t)N, st);
@@ -1177,7 +1253,6 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     a.work = work;
     a.bin_off = bin_off;
     a.refine_steps = refine_steps;
-    const bool autoref = precision == SAM_FP32_REFINE && refine_steps < 0;
     uint8_t *bin2 = nullptr;
     int32_t *work2 = nullptr, *bin_off2 = nullptr;
     if (autoref) {
@@ -1193,7 +1268,34 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     if (split_map_structure(h, K, n, g->mrp, g->mci, d_rp, d_ci) != cudaSuccess ||
         sg.flush_early(d_rp) != cudaSuccess || sg.flush_early(d_ci) != cudaSuccess)
         return SAM_ERR_CUDA;
-    if (launch_lsq(h, precision, a) != cudaSuccess) return SAM_ERR_CUDA;
+    if (!chunked) {
+        if (launch_lsq(h, precision, a) != cudaSuccess) return SAM_ERR_CUDA;
+    } else {
+        // one map's columns per class (the work list is read back while the
+        // launches above run); classes holding a quarter of the columns or
+        // more are chunked, the others go first over all maps
+        if (cudaEventSynchronize(ev_bins) != cudaSuccess) return SAM_ERR_CUDA;
+        int cnt[kNumBins];
+        bool big[kNumBins];
+        for (int b = 0; b < kNumBins; ++b) {
+            cnt[b] = h->h_bins[b + 1] - h->h_bins[b];
+            big[b] = (int64_t)cnt[b] * 4 >= n;
+            if (!big[b] && launch_lsq_bin(h, precision, a, b) != cudaSuccess) return SAM_ERR_CUDA;
+        }
+        for (int k0 = 0; k0 < K; k0 += Kc) {
+            const int k1 = std::min(K, k0 + Kc);
+            for (int b = 0; b < kNumBins; ++b) {
+                if (!big[b]) continue;
+                LsqArgs ac = a;
+                ac.item_lo = k0 * cnt[b];
+                ac.item_hi = k1 * cnt[b];
+                if (launch_lsq_bin(h, precision, ac, b) != cudaSuccess) return SAM_ERR_CUDA;
+            }
+            if (sg.flush_range(d_v, sizeof(double) * (size_t)M_offsets[k0],
+                               sizeof(double) * (size_t)(M_offsets[k1] - M_offsets[k0])) != cudaSuccess)
+                return SAM_ERR_CUDA;
+        }
+    }
     if (autoref && launch_refine_fallback(h, a, (int)N, bin, bin2, work2, bin_off2, nullptr, h->d_refine) != cudaSuccess)
         return SAM_ERR_CUDA;
     if (status_reduce(h, d_st, N, h->d_flag) != cudaSuccess) return SAM_ERR_CUDA;

@@ -77,6 +77,7 @@ struct LsqArgs {
     int32_t *colstat;            // per-column status
     const int32_t *work;         // columns grouped by size class
     const int32_t *bin_off;      // [kNumBins+1] offsets into work
+    int item_lo, item_hi;        // item_hi > 0: only items [item_lo, item_hi) of the launched class
     int refine_steps;            // < 0: automatic (up to kAutoSteps, FP64 fallback)
     uint8_t *refine_used;        // automatic mode: steps taken per column, kAutoSteps+1 = FP64 fallback
     int zbig;                    // 1: one target per map, stored block-diagonally
@@ -176,6 +177,8 @@ cudaError_t launch_refine_fallback(sam_handle h, const LsqArgs &args, int N, con
 
 // Least-squares launches for every size class.
 cudaError_t launch_lsq(sam_handle h, int precision, const LsqArgs &args);
+// one size class (the items args.item_lo/item_hi select, else all of it)
+cudaError_t launch_lsq_bin(sam_handle h, int precision, const LsqArgs &args, int bin);
 cudaError_t launch_adjoint(sam_handle h, int precision, const LsqArgs &args);
 // dA(e) = sum over map entries t of row c(e): dB[dbase[t] + (e - kcp[c])], CSC order of A
 cudaError_t adjoint_reduce(sam_handle h, int N, const int32_t *kcp, const int32_t *mrp, const int64_t *dbase,

@@ -66,8 +66,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ProbSmem<TL> &S = probs[warp * PPW + lane / P];
 
-    const int w0 = args.bin_off[bin];
-    const int total = args.bin_off[bin + 1] - w0;
+    const int w0 = args.bin_off[bin] + (args.item_hi > 0 ? args.item_lo : 0);
+    const int total = args.item_hi > 0 ? args.item_hi - args.item_lo : args.bin_off[bin + 1] - w0;
     const int32_t *work = args.work + w0;
     const double *kcv = args.kcv;
 
@@ -262,26 +262,33 @@ cudaError_t launch_one(sam_handle h, const LsqArgs &a, int bin) {
 
 }  // namespace
 
-cudaError_t launch_lsq(sam_handle h, int precision, const LsqArgs &args) {
-    cudaError_t e;
+cudaError_t launch_lsq_bin(sam_handle h, int precision, const LsqArgs &args, int bin) {
     if (precision == SAM_FP64) {
-        if ((e = launch_one<D0, true>(h, args, 0)) != cudaSuccess) return e;
-        if ((e = launch_one<D1, true>(h, args, 1)) != cudaSuccess) return e;
-        if ((e = launch_one<D2, true>(h, args, 2)) != cudaSuccess) return e;
-        if ((e = launch_one<D3, true>(h, args, 3)) != cudaSuccess) return e;
-        if ((e = launch_one<D4, true>(h, args, 4)) != cudaSuccess) return e;
-        return cudaSuccess;
+        switch (bin) {
+            case 0: return launch_one<D0, true>(h, args, 0);
+            case 1: return launch_one<D1, true>(h, args, 1);
+            case 2: return launch_one<D2, true>(h, args, 2);
+            case 3: return launch_one<D3, true>(h, args, 3);
+            default: return launch_one<D4, true>(h, args, 4);
+        }
     }
     // FP32 tiles: the shape of each size class comes from the handle (sam_tune)
-    if ((e = launch_one<F0, false>(h, args, 0)) != cudaSuccess) return e;
-    e = handle_variant(h, 1) ? launch_one<F1b, false>(h, args, 1) : launch_one<F1, false>(h, args, 1);
-    if (e != cudaSuccess) return e;
-    e = handle_variant(h, 2) ? launch_one<F2b, false>(h, args, 2) : launch_one<F2, false>(h, args, 2);
-    if (e != cudaSuccess) return e;
-    e = handle_variant(h, 3) ? launch_one<F3b, false>(h, args, 3) : launch_one<F3, false>(h, args, 3);
-    if (e != cudaSuccess) return e;
-    e = handle_variant(h, 4) ? launch_one<F4b, false>(h, args, 4) : launch_one<F4, false>(h, args, 4);
-    return e;
+    const bool b = handle_variant(h, bin) != 0;
+    switch (bin) {
+        case 0: return launch_one<F0, false>(h, args, 0);
+        case 1: return b ? launch_one<F1b, false>(h, args, 1) : launch_one<F1, false>(h, args, 1);
+        case 2: return b ? launch_one<F2b, false>(h, args, 2) : launch_one<F2, false>(h, args, 2);
+        case 3: return b ? launch_one<F3b, false>(h, args, 3) : launch_one<F3, false>(h, args, 3);
+        default: return b ? launch_one<F4b, false>(h, args, 4) : launch_one<F4, false>(h, args, 4);
+    }
+}
+
+cudaError_t launch_lsq(sam_handle h, int precision, const LsqArgs &args) {
+    for (int b = 0; b < kNumBins; ++b) {
+        cudaError_t e = launch_lsq_bin(h, precision, args, b);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 namespace {

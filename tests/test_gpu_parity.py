@@ -196,6 +196,39 @@ def test_host_buffers_give_the_device_result(sam, handle):
     assert np.array_equal(out[2], dvd.cpu().numpy())
 
 
+@pytest.mark.parametrize("nmat", [4, 5])
+def test_chunked_host_outputs_give_the_device_result(sam, handle, nmat):
+    """A one-structure sequence large enough (4 or 5 maps of 65536 columns)
+    that a build into host arrays solves its large size classes in chunks of
+    maps (2 + 2, or 3 + 2) and copies each chunk's values while the next is
+    solved: the same bits as the build into device arrays, residuals and
+    column status included."""
+    import torch
+
+    seq = W.config2(nx=256, nmat=nmat)
+    aks = [sam.Csr.from_host(m) for m in seq.mats]
+    ps = handle.sam_pattern_build_batched(aks, 2)
+    K, n = nmat, aks[0].n
+    st_d = torch.empty(K * n, dtype=torch.int32, device="cuda")
+    r2_d = torch.empty(K * n, dtype=torch.float64, device="cuda")
+    offs, rp_d, ci_d, mv_d, fro_d = handle.sam_build_batched(aks, aks[0], ps, "fp32r", 1, col_status=st_d,
+                                                             res2=r2_d, want_fro=True)
+    tot = int(offs[-1])
+    out = [torch.full((K * (n + 1),), -1, dtype=torch.int32).pin_memory(),
+           torch.full((tot,), -1, dtype=torch.int32).pin_memory(),
+           torch.full((tot,), np.nan, dtype=torch.float64).pin_memory(),
+           torch.full((K * n,), -1, dtype=torch.int32).pin_memory(),
+           torch.full((K * n,), np.nan, dtype=torch.float64).pin_memory()]
+    _, _, _, _, fro_h = handle.sam_build_batched(aks, aks[0], ps, "fp32r", 1, M_row_ptr=out[0], M_col_idx=out[1],
+                                                 M_val=out[2], col_status=out[3], res2=out[4], want_fro=True,
+                                                 offsets=offs)
+    for p in ps:
+        p.destroy()
+    for got, want in zip(out, (rp_d, ci_d, mv_d, st_d, r2_d)):
+        assert torch.equal(got, want.cpu())
+    assert np.array_equal(fro_h, fro_d)
+
+
 # ------------------------------------------------------------- edge cases
 
 
