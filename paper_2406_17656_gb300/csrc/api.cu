@@ -190,12 +190,58 @@ struct Stager {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_ready = nullptr, ev_done = nullptr;
     bool early_pending = false;
+    // host inputs copied on a second side stream (in_deferred), joined into
+    // st by join_inputs() before their first use
+    cudaStream_t side_in = nullptr;
+    cudaEvent_t ev_in_ready = nullptr, ev_in_done = nullptr;
+    bool in_pending = false;
     Stager(Scratch &s, cudaStream_t stream) : sc(s), st(stream) {}
     ~Stager() {
         join();
+        join_inputs();
         if (ev_ready) cudaEventDestroy(ev_ready);
         if (ev_done) cudaEventDestroy(ev_done);
         if (side) cudaStreamDestroy(side);
+        if (ev_in_ready) cudaEventDestroy(ev_in_ready);
+        if (ev_in_done) cudaEventDestroy(ev_in_done);
+        if (side_in) cudaStreamDestroy(side_in);
+    }
+    // st waits for the deferred input copies
+    void join_inputs() {
+        if (!in_pending) return;
+        cudaEventRecord(ev_in_done, side_in);
+        cudaStreamWaitEvent(st, ev_in_done, 0);
+        in_pending = false;
+    }
+    bool inputs_pending() const { return in_pending; }
+    // As in(), but a host array is copied on the input side stream, so that
+    // what st does next (work that does not read it) overlaps the copy; the
+    // caller calls join_inputs() before st first reads it.
+    template <typename T>
+    const T *in_deferred(const T *p, size_t count) {
+        if (!p || count == 0 || is_device_ptr(p)) return p;
+        T *d = sc.get<T>(count);
+        if (!d) {
+            failed = true;
+            return nullptr;
+        }
+        if (!side_in) {
+            if (cudaStreamCreateWithFlags(&side_in, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ev_in_ready, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ev_in_done, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                failed = true;
+                return nullptr;
+            }
+        }
+        // the buffer comes from st's stream-ordered pool: copy after it exists
+        if (cudaEventRecord(ev_in_ready, st) != cudaSuccess || cudaStreamWaitEvent(side_in, ev_in_ready, 0) != cudaSuccess ||
+            cudaMemcpyAsync(d, p, sizeof(T) * count, cudaMemcpyHostToDevice, side_in) != cudaSuccess) {
+            failed = true;
+            return nullptr;
+        }
+        in_pending = true;
+        return d;
     }
     // st waits for the early copies (before the workspace they read is freed)
     void join() {
@@ -320,13 +366,13 @@ sam_status check_csr_arg(const sam_csr *A, bool need_val) {
     return SAM_OK;
 }
 
-DevCsr stage_csr(Stager &sg, const sam_csr *A, bool with_val) {
+DevCsr stage_csr(Stager &sg, const sam_csr *A, bool with_val, bool defer_val = false) {
     DevCsr d;
     d.n = A->n;
     d.nnz = A->nnz;
     d.rp = sg.in(A->row_ptr, (size_t)A->n + 1);
     d.ci = sg.in(A->col_idx, (size_t)A->nnz);
-    d.v = with_val ? sg.in(A->val, (size_t)A->nnz) : nullptr;
+    d.v = with_val ? (defer_val ? sg.in_deferred(A->val, (size_t)A->nnz) : sg.in(A->val, (size_t)A->nnz)) : nullptr;
     return d;
 }
 
@@ -1051,7 +1097,7 @@ namespace {
 // CSC -> CSR permutation when perm != nullptr); K = 1 skips the copy.
 sam_status block_diag_csc(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms, int n, int32_t **cp,
                           int32_t **ri, double **cv, int32_t **perm, int64_t *total, Scratch *tmp_sc = nullptr,
-                          bool symmetric = false) {
+                          bool symmetric = false, bool values_later = false) {
     Scratch &tmp = tmp_sc ? *tmp_sc : sc;  // the concatenated copy lives only until the transpose
     const int K = (int)ms.size();
     const int64_t N = (int64_t)K * n;
@@ -1059,7 +1105,7 @@ sam_status block_diag_csc(sam_handle h, Scratch &sc, const std::vector<DevCsr> &
     std::vector<CsrPtrs> tab(K);
     std::vector<int64_t> off(K + 1, 0);
     for (int k = 0; k < K; ++k) {
-        tab[k] = {ms[k].rp, ms[k].ci, ms[k].v};
+        tab[k] = {ms[k].rp, ms[k].ci, values_later ? nullptr : ms[k].v};
         off[k + 1] = off[k] + ms[k].nnz;
     }
     tot = off[K];
@@ -1075,8 +1121,8 @@ sam_status block_diag_csc(sam_handle h, Scratch &sc, const std::vector<DevCsr> &
         CsrPtrs *dtab = tmp.get<CsrPtrs>(K);
         int64_t *doff = tmp.get<int64_t>(K + 1);
         int32_t *brp = tmp.get<int32_t>((size_t)N + 1), *bci = tmp.get<int32_t>((size_t)tot);
-        double *bv = tmp.get<double>((size_t)tot);
-        if (!dtab || !doff || !brp || !bci || !bv) return SAM_ERR_OOM;
+        double *bv = values_later ? nullptr : tmp.get<double>((size_t)tot);
+        if (!dtab || !doff || !brp || !bci || (!values_later && !bv)) return SAM_ERR_OOM;
         cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * K, cudaMemcpyHostToDevice, h->stream);
         cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, h->stream);
         if (concat_block_diag(h, K, n, dtab, doff, brp, bci, bv) != cudaSuccess) return SAM_ERR_CUDA;
@@ -1084,9 +1130,44 @@ sam_status block_diag_csc(sam_handle h, Scratch &sc, const std::vector<DevCsr> &
         ci = bci;
         v = bv;
     }
-    if (csr_to_csc(h, (int)N, tot, rp, ci, v, *cp, *ri, *cv, perm ? *perm : nullptr, symmetric) != cudaSuccess)
+    if (csr_to_csc(h, (int)N, tot, rp, ci, values_later ? nullptr : v, *cp, *ri, values_later ? nullptr : *cv,
+                   perm ? *perm : nullptr, symmetric) != cudaSuccess)
         return SAM_ERR_CUDA;
     return SAM_OK;
+}
+
+__global__ void block_values_kernel(const CsrPtrs *mats, const int64_t *off, const int32_t *perm, double *cv) {
+    const int k = blockIdx.y;
+    const int64_t b = off[k], e = off[k + 1];
+    const double *v = mats[k].v;
+    for (int64_t q = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < e; q += (int64_t)gridDim.x * blockDim.x)
+        cv[q] = v[perm[q] - b];
+}
+
+// The values of a block_diag_csc made with values_later (and its perm): map
+// k's columns hold exactly its own entries, positions [off_k, off_k+1) of
+// the CSC, and perm gives each one's position in the concatenated CSR.
+sam_status block_diag_values(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms, const int32_t *perm,
+                             double *cv) {
+    const int K = (int)ms.size();
+    std::vector<CsrPtrs> tab(K);
+    std::vector<int64_t> off(K + 1, 0);
+    for (int k = 0; k < K; ++k) {
+        tab[k] = {ms[k].rp, ms[k].ci, ms[k].v};
+        off[k + 1] = off[k] + ms[k].nnz;
+    }
+    if (off[K] == 0) return SAM_OK;
+    CsrPtrs *dtab = sc.get<CsrPtrs>(K);
+    int64_t *doff = sc.get<int64_t>(K + 1);
+    if (!dtab || !doff) return SAM_ERR_OOM;
+    cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * K, cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, h->stream);
+    const int64_t per = (off[K] + K - 1) / K;
+    int64_t bx = (per + 255) / 256;
+    if (bx > (int64_t)h->sms * 8) bx = (int64_t)h->sms * 8;
+    block_values_kernel<<<dim3((unsigned)bx, (unsigned)K), 256, 0, h->stream>>>(dtab, doff, perm, cv);
+    count_launch(h);
+    return cudaGetLastError() == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
 }
 
 // K maps of order n against NT = 1 shared target or NT = K targets (one per map)
@@ -1117,10 +1198,13 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     cudaStream_t st = h->stream;
     Scratch sc(h);
     Stager sg(sc, st);
+    // host values are copied on a side stream while the validation and the
+    // structure work (which read the structures alone) run on st
     std::vector<DevCsr> zs(NT);
-    for (int t = 0; t < NT; ++t) zs[t] = stage_csr(sg, &A_0[t], true);
+    for (int t = 0; t < NT; ++t) zs[t] = stage_csr(sg, &A_0[t], true, true);
     std::vector<DevCsr> ak(K);
-    for (int k = 0; k < K; ++k) ak[k] = stage_csr(sg, &A_k[k], true);
+    for (int k = 0; k < K; ++k) ak[k] = stage_csr(sg, &A_k[k], true, true);
+    const bool late = sg.inputs_pending();
     int32_t *d_rp = sg.out(M_row_ptr, (size_t)K * ((size_t)n + 1));
     int32_t *d_ci = sg.out(M_col_idx, (size_t)total_nnz);
     double *d_v = sg.out(M_val, (size_t)total_nnz);
@@ -1160,10 +1244,11 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     // target(s) and sources as CSC with values
     int32_t *zcp = nullptr, *zri = nullptr, *kcp = nullptr, *kri = nullptr;
     double *zcv = nullptr, *kcv = nullptr;
+    int32_t *zperm = nullptr, *kperm = nullptr;  // with late values: CSC -> CSR positions
     int64_t zn = 0, kn = 0;
-    sam_status s = block_diag_csc(h, sc, zs, n, &zcp, &zri, &zcv, nullptr, &zn, nullptr, zsym);
+    sam_status s = block_diag_csc(h, sc, zs, n, &zcp, &zri, &zcv, late ? &zperm : nullptr, &zn, nullptr, zsym, late);
     if (s != SAM_OK) return s;
-    s = block_diag_csc(h, sc, ak, n, &kcp, &kri, &kcv, nullptr, &kn, nullptr, ksym);
+    s = block_diag_csc(h, sc, ak, n, &kcp, &kri, &kcv, late ? &kperm : nullptr, &kn, nullptr, ksym, late);
     if (s != SAM_OK) return s;
     int32_t *ish = sc.get<int32_t>((size_t)N * kICap), *icnt = sc.get<int32_t>((size_t)N);
     uint8_t *bin = sc.get<uint8_t>((size_t)N);
@@ -1217,6 +1302,16 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
         return SAM_ERR_CUDA;
     cudaMemsetAsync(d_v, 0, sizeof(double) * (size_t)total_nnz, st);
     cudaMemsetAsync(d_r2, 0, sizeof(double) * (size_t)N, st);
+    // CSR structure of every map (it depends on the patterns alone): written
+    // before the solves, so that a copy to host outputs overlaps them
+    if (split_map_structure(h, K, n, g->mrp, g->mci, d_rp, d_ci) != cudaSuccess ||
+        sg.flush_early(d_rp) != cudaSuccess || sg.flush_early(d_ci) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    if (late) {
+        sg.join_inputs();
+        if ((s = block_diag_values(h, sc, zs, zperm, zcv)) != SAM_OK) return s;
+        if ((s = block_diag_values(h, sc, ak, kperm, kcv)) != SAM_OK) return s;
+    }
     float *kcv32 = nullptr, *zcv32 = nullptr;
     if (precision == SAM_FP32_REFINE) {
         kcv32 = sc.get<float>((size_t)kn);
@@ -1263,11 +1358,6 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
         if (!a.refine_used || !bin2 || !work2 || !bin_off2) return SAM_ERR_OOM;
         cudaMemsetAsync(a.refine_used, 0, (size_t)N, st);
     }
-    // CSR structure of every map (it depends on the patterns alone): written
-    // before the solves, so that a copy to host outputs overlaps them
-    if (split_map_structure(h, K, n, g->mrp, g->mci, d_rp, d_ci) != cudaSuccess ||
-        sg.flush_early(d_rp) != cudaSuccess || sg.flush_early(d_ci) != cudaSuccess)
-        return SAM_ERR_CUDA;
     if (!chunked) {
         if (launch_lsq(h, precision, a) != cudaSuccess) return SAM_ERR_CUDA;
     } else {
