@@ -60,7 +60,8 @@ def parse():
                          "and exit (no JSON line)")
     ap.add_argument("--profile-fem", type=int, default=0, metavar="STEPS",
                     help="profiling aid: run STEPS whole steps (level-2 patterns + batched maps + residuals) of "
-                         "the 16-map P1 FEM 512x512 sequence and exit (no JSON line)")
+                         "the P1 FEM 512x512 sequence and exit (no JSON line)")
+    ap.add_argument("--fem-maps", type=int, default=16, help="maps of the --profile-fem sequence")
     return ap.parse_args()
 
 
@@ -425,12 +426,12 @@ def profile_gmres(h, sam, torch, dev, aks, a0, n, level, steps):
     print("gmres: %d steps, estimate %.3e, %.1f us per step" % (its, rel, (time.perf_counter() - t) * 1e6 / its))
 
 
-def profile_fem(h, sam, torch, dev, steps):
+def profile_fem(h, sam, torch, dev, steps, nmat=16):
     """`steps` whole steps of the P1 FEM sequence whose pattern changes from
     map to map (the workload of the configuration figures), for ncu."""
     from paper_2406_17656_gb300 import workloads as W
 
-    seq = W.config4()
+    seq = W.config4(nmat=nmat)
     aks = [sam.Csr.from_host(m, dev) for m in seq.mats]
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -655,7 +656,7 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
     if args.profile_fem > 0:
         h = sam.Handle(stream=torch.cuda.current_stream())
-        profile_fem(h, sam, torch, dev, args.profile_fem)
+        profile_fem(h, sam, torch, dev, args.profile_fem, args.fem_maps)
         h.close()
         return
 

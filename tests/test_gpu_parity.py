@@ -196,12 +196,13 @@ def test_host_buffers_give_the_device_result(sam, handle):
     assert np.array_equal(out[2], dvd.cpu().numpy())
 
 
-@pytest.mark.parametrize("nmat", [4, 5])
-def test_chunked_host_outputs_give_the_device_result(sam, handle, nmat):
+@pytest.mark.parametrize("nmat,host_inputs", [(4, False), (5, True)])
+def test_chunked_host_outputs_give_the_device_result(sam, handle, nmat, host_inputs):
     """A one-structure sequence large enough (4 or 5 maps of 65536 columns)
     that a build into host arrays solves its large size classes in chunks of
     maps (2 + 2, or 3 + 2) and copies each chunk's values while the next is
-    solved: the same bits as the build into device arrays, residuals and
+    solved (with host inputs, their values are copied while the structure
+    work runs): the same bits as the build into device arrays, residuals and
     column status included."""
     import torch
 
@@ -219,13 +220,39 @@ def test_chunked_host_outputs_give_the_device_result(sam, handle, nmat):
            torch.full((tot,), np.nan, dtype=torch.float64).pin_memory(),
            torch.full((K * n,), -1, dtype=torch.int32).pin_memory(),
            torch.full((K * n,), np.nan, dtype=torch.float64).pin_memory()]
-    _, _, _, _, fro_h = handle.sam_build_batched(aks, aks[0], ps, "fp32r", 1, M_row_ptr=out[0], M_col_idx=out[1],
+    src = aks
+    if host_inputs:
+        pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+        src = [sam.Csr(pin(m.indptr), pin(m.indices), pin(m.data), n=n) for m in seq.mats]
+    _, _, _, _, fro_h = handle.sam_build_batched(src, src[0], ps, "fp32r", 1, M_row_ptr=out[0], M_col_idx=out[1],
                                                  M_val=out[2], col_status=out[3], res2=out[4], want_fro=True,
                                                  offsets=offs)
     for p in ps:
         p.destroy()
     for got, want in zip(out, (rp_d, ci_d, mv_d, st_d, r2_d)):
         assert torch.equal(got, want.cpu())
+    assert np.array_equal(fro_h, fro_d)
+
+
+def test_changing_structure_host_batch_gives_the_device_result(sam, handle):
+    """A batch whose sources change structure from map to map (P1 FEM with
+    flipped diagonals), with host inputs (values copied while the structure
+    work runs) and host outputs: the same bits as with device arrays."""
+    seq = W.config4(ncell=40, nmat=4, flip_frac=0.2)
+    aks = [sam.Csr.from_host(m) for m in seq.mats]
+    ps = handle.sam_pattern_build_batched(aks, 2)
+    offs, rp_d, ci_d, mv_d, fro_d = handle.sam_build_batched(aks, aks[0], ps, "fp32r", 1, want_fro=True)
+    n = aks[0].n
+    hk = [sam.Csr(m.indptr, m.indices, m.data, n=n) for m in seq.mats]
+    out = (np.full(4 * (n + 1), -1, np.int32), np.full(int(offs[-1]), -1, np.int32),
+           np.full(int(offs[-1]), np.nan))
+    _, _, _, _, fro_h = handle.sam_build_batched(hk, hk[0], ps, "fp32r", 1, M_row_ptr=out[0], M_col_idx=out[1],
+                                                 M_val=out[2], want_fro=True, offsets=offs)
+    for p in ps:
+        p.destroy()
+    assert np.array_equal(out[0], rp_d.cpu().numpy())
+    assert np.array_equal(out[1], ci_d.cpu().numpy())
+    assert np.array_equal(out[2], mv_d.cpu().numpy())
     assert np.array_equal(fro_h, fro_d)
 
 
