@@ -208,6 +208,13 @@ sam_status sam_build(sam_handle h, const sam_csr *A_k, const sam_csr *A_0, sam_p
  * offset).  col_status and res2 (nullable) are laid out as [K][n].
  * fro (nullable, host double[K]) receives ||A_k M_k - A_0||_F per map and
  * forces a synchronisation.
+ * With host arrays the copies overlap the work: input values travel on a
+ * library-owned side stream while the structure work runs, the maps' CSR
+ * structure is copied out while the solves run, and when every map has one
+ * structure the large size classes are solved in chunks of maps, each
+ * chunk's values copied out while the next is solved.  The side streams
+ * are joined into the handle's stream before the call returns; the results
+ * are the same bits as with device arrays.
  */
 sam_status sam_build_batched(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0,
                              const sam_pattern *S, int precision, int refine_steps,
