@@ -62,6 +62,9 @@ def parse():
                     help="profiling aid: run STEPS whole steps (level-2 patterns + batched maps + residuals) of "
                          "the P1 FEM 512x512 sequence and exit (no JSON line)")
     ap.add_argument("--fem-maps", type=int, default=16, help="maps of the --profile-fem sequence")
+    ap.add_argument("--profile-adjoint", type=int, default=0, metavar="STEPS",
+                    help="profiling aid: run STEPS adjoints of the benchmark's batched build (dL/dM random, "
+                         "residual term on) and exit (no JSON line)")
     return ap.parse_args()
 
 
@@ -669,6 +672,20 @@ def main():
     a0 = sam.Csr.from_host(a0h, dev)
     if args.profile_gmres > 0:
         profile_gmres(h, sam, torch, dev, aks, a0, n, args.level, args.profile_gmres)
+        h.close()
+        return
+    if args.profile_adjoint > 0:
+        pats = h.sam_pattern_build_batched(aks, args.level)
+        offs_a, _, _, mv, _ = h.sam_build_batched(aks, a0, pats, "fp32r", args.refine)
+        gbar = torch.randn(mv.numel(), dtype=torch.float64, device=dev,
+                           generator=torch.Generator(device=dev).manual_seed(3))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.profile_adjoint):
+            h.sam_build_backward_batched(aks, [a0] * K, pats, mv, gbar, "fp32r", args.refine, 1.0, offsets=offs_a)
+        torch.cuda.synchronize()
+        print("adjoint: %d steps, %.2f ms per step" % (args.profile_adjoint,
+                                                      (time.perf_counter() - t) * 1e3 / args.profile_adjoint))
         h.close()
         return
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)

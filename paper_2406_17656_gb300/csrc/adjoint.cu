@@ -140,21 +140,59 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) adjoint_kernel(LsqArgs ar
     }
 }
 
-// dA(e) for the stored entries e of column c (one warp per column)
-__global__ void adjoint_reduce_kernel(int N, const int32_t *kcp, const int32_t *mrp, const int64_t *dbase,
-                                      const double *dB, double *dak) {
+constexpr int kReduceThreads = 256;
+
+// dA(e) for the stored entries e of column c (one warp per column).  The
+// contributions come from the map columns whose patterns hold c (map CSR
+// row c: mrp[c] .. mrp[c+1]), each a block of the column's len entries in
+// dB at dbase[t] (< 0: none).  The warp splits into G = 32 / len lane
+// groups; group g sums blocks g, g + G, g + 2G, ... in that order, two loads
+// in flight, and the groups' sums are added in group order, so the result
+// is fixed by the inputs.
+__global__ void __launch_bounds__(kReduceThreads) adjoint_reduce_kernel(int N, const int32_t *kcp, const int32_t *mrp,
+                                                                       const int64_t *dbase, const double *dB,
+                                                                       double *dak) {
+    __shared__ double part[kReduceThreads / 32][32];
     const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (c >= N) return;
-    const int b = kcp[c], e = kcp[c + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (c >= N) return;  // whole warps
+    const int b = kcp[c], e = kcp[c + 1], len = e - b;
     const int tb = mrp[c], te = mrp[c + 1];
-    for (int p = lane; p < e - b; p += 32) {
-        double acc = 0.0;
-        for (int t = tb; t < te; ++t) {
-            const int64_t base = dbase[t];
-            if (base >= 0) acc += dB[base + p];
+    if (len <= 0) return;
+    if (len > 32) {
+        for (int p = lane; p < len; p += 32) {
+            double acc = 0.0;
+            for (int t = tb; t < te; ++t) {
+                const int64_t base = dbase[t];
+                if (base >= 0) acc += dB[base + p];
+            }
+            dak[b + p] = acc;
         }
-        dak[b + p] = acc;
+        return;
+    }
+    const int G = 32 / len;
+    const int g = lane / len, p = lane - g * len;
+    double acc = 0.0;
+    if (g < G) {
+        int t = tb + g;
+        for (; t + G < te; t += 2 * G) {
+            const int64_t b0 = dbase[t], b1 = dbase[t + G];
+            const double v0 = b0 >= 0 ? dB[b0 + p] : 0.0;
+            const double v1 = b1 >= 0 ? dB[b1 + p] : 0.0;
+            acc += v0;
+            acc += v1;
+        }
+        if (t < te) {
+            const int64_t b0 = dbase[t];
+            if (b0 >= 0) acc += dB[b0 + p];
+        }
+    }
+    part[warp][lane] = acc;
+    __syncwarp();
+    if (lane < len) {
+        double sum = part[warp][lane];
+        for (int q = 1; q < G; ++q) sum += part[warp][q * len + lane];
+        dak[b + lane] = sum;
     }
 }
 
@@ -202,8 +240,8 @@ cudaError_t adjoint_reduce(sam_handle h, int N, const int32_t *kcp, const int32_
                            const double *dB, double *dak_csc) {
     if (N == 0) return cudaSuccess;
     const int64_t threads = (int64_t)N * 32;
-    adjoint_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, handle_stream(h)>>>(N, kcp, mrp, dbase, dB,
-                                                                                          dak_csc);
+    adjoint_reduce_kernel<<<(unsigned)((threads + kReduceThreads - 1) / kReduceThreads), kReduceThreads, 0,
+                            handle_stream(h)>>>(N, kcp, mrp, dbase, dB, dak_csc);
     count_launch(h);
     return cudaGetLastError();
 }
