@@ -518,6 +518,17 @@ def config_figures(h, sam, torch, dev, stream, nsteps=7):
         out[name] = d
 
     out = {}
+    saved_variants = h.sam_get_tile_variants()
+
+    def tune(aks, a0, level, steps):
+        """sam_tune on this workload's own patterns (the tile shape per size
+        class is the handle's; restored when all configurations are done)."""
+        ps = h.sam_pattern_build_batched(aks, level)
+        v = h.sam_tune(aks, a0, ps, "fp32r", steps)
+        for p in ps:
+            p.destroy()
+        return {"tile_variants": list(v)}
+
     # config 1: 5-point Poisson 32^2, A_1 = A_0 + diag, level 1, plain FP64 single build
     seq = W.config1()
     aks = [sam.Csr.from_host(m, dev) for m in seq.mats]
@@ -540,7 +551,8 @@ def config_figures(h, sam, torch, dev, stream, nsteps=7):
         for p in ps:
             p.destroy()
 
-    line("upwind7_64cube_seq20_level2", len(aks) * aks[0].n, len(aks), timed(c3, nsteps), roof=(seq.mats, 2, "fp32r", 1),
+    tv = tune(aks, aks[0], 2, 1)
+    line("upwind7_64cube_seq20_level2", len(aks) * aks[0].n, len(aks), timed(c3, nsteps), tv, roof=(seq.mats, 2, "fp32r", 1),
          orc=(seq.mats[-1], seq.mats[0], 2))
     del aks
     # config 4: P1 FEM 512^2 cells, 16 maps whose pattern changes, level 2; direct and captured plan
@@ -553,6 +565,7 @@ def config_figures(h, sam, torch, dev, stream, nsteps=7):
         for p in ps:
             p.destroy()
 
+    tv = tune(aks, aks[0], 2, 1)
     ms4 = timed(c4, nsteps)
     ps = h.sam_pattern_build_batched(aks, 2)
     plan = h.sam_plan_create(aks, aks[0], ps, "fp32r", 1)
@@ -562,7 +575,7 @@ def config_figures(h, sam, torch, dev, stream, nsteps=7):
     plan.destroy()
     cols4 = len(aks) * aks[0].n
     line("p1_fem_512x512_seq16_level2", cols4, len(aks), ms4,
-         {"graph_replay_columns_per_s": cols4 / (msp * 1e-3), "graph_replay_ms": msp}, roof=(seq.mats, 2, "fp32r", 1),
+         {"graph_replay_columns_per_s": cols4 / (msp * 1e-3), "graph_replay_ms": msp, **tv}, roof=(seq.mats, 2, "fp32r", 1),
          orc=(seq.mats[-1], seq.mats[0], 2))
     del aks
     # config 5: 32 independent (A_0, A_1) 512^2 pairs, level 1, forward (one target per map) and adjoint
@@ -577,6 +590,7 @@ def config_figures(h, sam, torch, dev, stream, nsteps=7):
         for p in ps:
             p.destroy()
 
+    tv = tune(a1s, a0s[0], 1, 2)
     ms5 = timed(c5, nsteps)
     ps = h.sam_pattern_build_batched(a1s, 1)
     offs, _, _, mv, _ = h.sam_build_batched(a1s, a0s, ps, "fp32r", 2)
@@ -585,8 +599,9 @@ def config_figures(h, sam, torch, dev, stream, nsteps=7):
     for p in ps:
         p.destroy()
     line("q1_pairs_512x512_x32_level1", 32 * n5, 32, ms5,
-         {"adjoint_columns_per_s": 32 * n5 / (msb * 1e-3), "adjoint_ms": msb, "refine_steps": 2},
+         {"adjoint_columns_per_s": 32 * n5 / (msb * 1e-3), "adjoint_ms": msb, "refine_steps": 2, **tv},
          roof=([p[1] for p in pairs], 1, "fp32r", 2), orc=(pairs[0][1], pairs[0][0], 1))
+    h.sam_set_tile_variants(saved_variants)
     return out
 
 

@@ -196,14 +196,15 @@ def test_host_buffers_give_the_device_result(sam, handle):
     assert np.array_equal(out[2], dvd.cpu().numpy())
 
 
-@pytest.mark.parametrize("nmat,host_inputs", [(4, False), (5, True)])
-def test_chunked_host_outputs_give_the_device_result(sam, handle, nmat, host_inputs):
+@pytest.mark.parametrize("nmat,host_inputs,steps", [(4, False, 1), (5, True, 1), (4, True, "auto")])
+def test_chunked_host_outputs_give_the_device_result(sam, handle, nmat, host_inputs, steps):
     """A one-structure sequence large enough (4 or 5 maps of 65536 columns)
     that a build into host arrays solves its large size classes in chunks of
     maps (2 + 2, or 3 + 2) and copies each chunk's values while the next is
     solved (with host inputs, their values are copied while the structure
-    work runs): the same bits as the build into device arrays, residuals and
-    column status included."""
+    work runs; the automatic refinement mode re-solves columns after all the
+    solves and is not chunked): the same bits as the build into device
+    arrays, residuals and column status included."""
     import torch
 
     seq = W.config2(nx=256, nmat=nmat)
@@ -212,7 +213,7 @@ def test_chunked_host_outputs_give_the_device_result(sam, handle, nmat, host_inp
     K, n = nmat, aks[0].n
     st_d = torch.empty(K * n, dtype=torch.int32, device="cuda")
     r2_d = torch.empty(K * n, dtype=torch.float64, device="cuda")
-    offs, rp_d, ci_d, mv_d, fro_d = handle.sam_build_batched(aks, aks[0], ps, "fp32r", 1, col_status=st_d,
+    offs, rp_d, ci_d, mv_d, fro_d = handle.sam_build_batched(aks, aks[0], ps, "fp32r", steps, col_status=st_d,
                                                              res2=r2_d, want_fro=True)
     tot = int(offs[-1])
     out = [torch.full((K * (n + 1),), -1, dtype=torch.int32).pin_memory(),
@@ -224,7 +225,7 @@ def test_chunked_host_outputs_give_the_device_result(sam, handle, nmat, host_inp
     if host_inputs:
         pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
         src = [sam.Csr(pin(m.indptr), pin(m.indices), pin(m.data), n=n) for m in seq.mats]
-    _, _, _, _, fro_h = handle.sam_build_batched(src, src[0], ps, "fp32r", 1, M_row_ptr=out[0], M_col_idx=out[1],
+    _, _, _, _, fro_h = handle.sam_build_batched(src, src[0], ps, "fp32r", steps, M_row_ptr=out[0], M_col_idx=out[1],
                                                  M_val=out[2], col_status=out[3], res2=out[4], want_fro=True,
                                                  offsets=offs)
     for p in ps:
