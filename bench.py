@@ -154,13 +154,19 @@ def measured_hbm_gbs() -> float:
 
 
 def kernel_hash() -> str:
-    """sha256 over the sources of the least-squares kernel (a recorded ncu
-    traffic figure is only reported while these are unchanged)."""
+    """sha256 over the sources the least-squares kernel is compiled from: its
+    two files and the device part of common.cuh (constants, LsqArgs, device
+    helpers; the host-side declarations after them do not enter the kernel).
+    A recorded ncu traffic figure is only reported while these are unchanged."""
     import hashlib
 
+    csrc = os.path.join(HERE, "paper_2406_17656_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("lsq.cu", "lsq_core.cuh", "common.cuh"):
-        h.update(open(os.path.join(HERE, "paper_2406_17656_gb300", "csrc", f), "rb").read())
+    for f in ("lsq.cu", "lsq_core.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    common = open(os.path.join(csrc, "common.cuh"), "rb").read()
+    cut = common.find(b"// ------------------------------------------------------- host-side helpers")
+    h.update(common if cut < 0 else common[:cut])
     return h.hexdigest()
 
 

@@ -1136,12 +1136,17 @@ sam_status block_diag_csc(sam_handle h, Scratch &sc, const std::vector<DevCsr> &
     return SAM_OK;
 }
 
-__global__ void block_values_kernel(const CsrPtrs *mats, const int64_t *off, const int32_t *perm, double *cv) {
-    const int k = blockIdx.y;
-    const int64_t b = off[k], e = off[k + 1];
-    const double *v = mats[k].v;
-    for (int64_t q = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < e; q += (int64_t)gridDim.x * blockDim.x)
-        cv[q] = v[perm[q] - b];
+// Values of K sources of one structure in the CSC order of the first: map
+// k's go to positions k nnz + q through the first's CSC -> CSR positions.
+sam_status shared_csc_values(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms, const int32_t *perm,
+                             double *cv) {
+    const int K = (int)ms.size();
+    std::vector<const double *> vals(K);
+    for (int k = 0; k < K; ++k) vals[k] = ms[k].v;
+    const double **dvals = sc.get<const double *>(K);
+    if (!dvals) return SAM_ERR_OOM;
+    cudaMemcpyAsync(dvals, vals.data(), sizeof(const double *) * K, cudaMemcpyHostToDevice, h->stream);
+    return gather_values_shared(h, ms[0].nnz, K, dvals, perm, cv) == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
 }
 
 // The values of a block_diag_csc made with values_later (and its perm): map
@@ -1150,24 +1155,19 @@ __global__ void block_values_kernel(const CsrPtrs *mats, const int64_t *off, con
 sam_status block_diag_values(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms, const int32_t *perm,
                              double *cv) {
     const int K = (int)ms.size();
-    std::vector<CsrPtrs> tab(K);
+    std::vector<const double *> vals(K);
     std::vector<int64_t> off(K + 1, 0);
     for (int k = 0; k < K; ++k) {
-        tab[k] = {ms[k].rp, ms[k].ci, ms[k].v};
+        vals[k] = ms[k].v;
         off[k + 1] = off[k] + ms[k].nnz;
     }
     if (off[K] == 0) return SAM_OK;
-    CsrPtrs *dtab = sc.get<CsrPtrs>(K);
+    const double **dvals = sc.get<const double *>(K);
     int64_t *doff = sc.get<int64_t>(K + 1);
-    if (!dtab || !doff) return SAM_ERR_OOM;
-    cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * K, cudaMemcpyHostToDevice, h->stream);
+    if (!dvals || !doff) return SAM_ERR_OOM;
+    cudaMemcpyAsync(dvals, vals.data(), sizeof(const double *) * K, cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, h->stream);
-    const int64_t per = (off[K] + K - 1) / K;
-    int64_t bx = (per + 255) / 256;
-    if (bx > (int64_t)h->sms * 8) bx = (int64_t)h->sms * 8;
-    block_values_kernel<<<dim3((unsigned)bx, (unsigned)K), 256, 0, h->stream>>>(dtab, doff, perm, cv);
-    count_launch(h);
-    return cudaGetLastError() == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
+    return gather_values(h, off[K], K, doff, dvals, perm, cv, nullptr) == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
 }
 
 // K maps of order n against NT = 1 shared target or NT = K targets (one per map)
@@ -1248,8 +1248,24 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     int64_t zn = 0, kn = 0;
     sam_status s = block_diag_csc(h, sc, zs, n, &zcp, &zri, &zcv, late ? &zperm : nullptr, &zn, nullptr, zsym, late);
     if (s != SAM_OK) return s;
-    s = block_diag_csc(h, sc, ak, n, &kcp, &kri, &kcv, late ? &kperm : nullptr, &kn, nullptr, ksym, late);
-    if (s != SAM_OK) return s;
+    // one structure: the kernels read map 0's CSC structure for every map, so
+    // only map 0 is transposed and each map's values are gathered into map
+    // 0's CSC order through its CSC -> CSR positions (map k at k nnz_0)
+    const bool one_csc = shared && K > 1;
+    if (one_csc) {
+        const std::vector<DevCsr> first{ak[0]};
+        double *unused = nullptr;
+        int64_t kn0 = 0;
+        s = block_diag_csc(h, sc, first, n, &kcp, &kri, &unused, &kperm, &kn0, nullptr, ksym, true);
+        if (s != SAM_OK) return s;
+        kn = (int64_t)K * kn0;
+        kcv = sc.get<double>((size_t)kn);
+        if (!kcv) return SAM_ERR_OOM;
+        if (!late && (s = shared_csc_values(h, sc, ak, kperm, kcv)) != SAM_OK) return s;
+    } else {
+        s = block_diag_csc(h, sc, ak, n, &kcp, &kri, &kcv, late ? &kperm : nullptr, &kn, nullptr, ksym, late);
+        if (s != SAM_OK) return s;
+    }
     int32_t *ish = sc.get<int32_t>((size_t)N * kICap), *icnt = sc.get<int32_t>((size_t)N);
     uint8_t *bin = sc.get<uint8_t>((size_t)N);
     int32_t *work = sc.get<int32_t>((size_t)N);
@@ -1310,7 +1326,8 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     if (late) {
         sg.join_inputs();
         if ((s = block_diag_values(h, sc, zs, zperm, zcv)) != SAM_OK) return s;
-        if ((s = block_diag_values(h, sc, ak, kperm, kcv)) != SAM_OK) return s;
+        if ((s = one_csc ? shared_csc_values(h, sc, ak, kperm, kcv) : block_diag_values(h, sc, ak, kperm, kcv)) != SAM_OK)
+            return s;
     }
     float *kcv32 = nullptr, *zcv32 = nullptr;
     if (precision == SAM_FP32_REFINE) {

@@ -203,6 +203,10 @@ cudaError_t compact_kept(sam_handle h, int n, const int32_t *rp, const int32_t *
                          const uint8_t *keep, int32_t *cnt, int32_t *orp, int32_t *oci, double *ov);
 // doubles of workspace segmented_sum_f64 needs for K segments
 size_t segmented_sum_workspace(int K);
+// K matrices of one structure: out[k m + q] = vals[k][perm[q]] (vals: device
+// array of K value pointers; perm: the common CSC -> CSR positions)
+cudaError_t gather_values_shared(sam_handle h, int64_t m, int K, const double *const *vals, const int32_t *perm,
+                                 double *out);
 // values of K matrices into the CSC order of their block-diagonal (+ FP32 copy)
 cudaError_t gather_values(sam_handle h, int64_t tot, int K, const int64_t *off, const double *const *vals,
                           const int32_t *perm, double *v, float *v32);

@@ -286,6 +286,27 @@ __global__ void gather_values_kernel(int64_t tot, int K, const int64_t *off, con
     }
 }
 
+// K matrices of one structure: out[k m + q] = vals[k][perm[q]] (perm: the
+// common CSC -> CSR positions of m entries)
+__global__ void gather_values_shared_kernel(int64_t m, const double *const *vals, const int32_t *perm, double *out) {
+    const int k = blockIdx.y;
+    const double *v = vals[k];
+    double *o = out + (int64_t)k * m;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x)
+        o[q] = v[perm[q]];
+}
+
+cudaError_t gather_values_shared(sam_handle h, int64_t m, int K, const double *const *vals, const int32_t *perm,
+                                 double *out) {
+    if (m == 0 || K == 0) return cudaSuccess;
+    int64_t bx = (m + 255) / 256;
+    const int64_t cap = (int64_t)handle_sms(h) * 8 / K + 1;  // about one resident wave over all maps
+    if (bx > cap) bx = cap;
+    gather_values_shared_kernel<<<dim3((unsigned)bx, (unsigned)K), 256, 0, handle_stream(h)>>>(m, vals, perm, out);
+    count_launch(h);
+    return cudaGetLastError();
+}
+
 cudaError_t gather_values(sam_handle h, int64_t tot, int K, const int64_t *off, const double *const *vals,
                           const int32_t *perm, double *v, float *v32) {
     if (tot == 0) return cudaSuccess;
