@@ -957,16 +957,21 @@ def main():
         for p in pats:
             p.destroy()
 
-    for _ in range(2):
+    for _ in range(3):
         e2e_step()
     torch.cuda.synchronize()
-    ne = max(3, args.steps // 2)
-    t0 = time.perf_counter()
+    # every step ends synchronised (host outputs): wall time per step, median
+    # (host jitter), the mean beside it
+    ne = max(10, args.steps)
+    e2e_ms = []
     for _ in range(ne):
+        t0 = time.perf_counter()
         e2e_step()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / ne
-    e2e_value = job_value(cols_per_step, world, max_over_ranks(e2e_s * 1e3, world, dev))
+    e2e_med = max_over_ranks(statistics.median(e2e_ms), world, dev)
+    e2e_mean = max_over_ranks(statistics.fmean(e2e_ms), world, dev)
+    e2e_value = job_value(cols_per_step, world, e2e_med)
 
     # ---- CPU oracle baseline and sampled parity (rank 0, N = 1 only)
     cpu = None
@@ -998,7 +1003,9 @@ def main():
                            "level": args.level, "precision": "fp32 Householder QR + %d FP64 CSNE step(s)" % args.refine,
                            "columns_per_step": cols_per_step, "tile_variants": variants, "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed between steps (256 MiB write outside the timed interval)"},
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                        "ms_per_step_median": e2e_med, "ms_per_step_mean": e2e_mean, "steps": ne,
+                        "mean_value": job_value(cols_per_step, world, e2e_mean)},
                 "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks, "cpu_baseline": cpu,
                 "maps_per_s": job_value(K, world, ms)}
         line.update(extra)

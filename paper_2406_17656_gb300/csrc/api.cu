@@ -47,9 +47,37 @@ struct sam_handle_t {
 namespace {
 // Builds whose map values go to a host array: at most kMaxChunks chunks of
 // maps, each of about kChunkColumns columns or more (each chunk boundary
-// costs the tail of a persistent launch; the last chunk's copy is exposed)
-constexpr int64_t kMaxChunks = 8;
+// costs the tail of a persistent launch; the last chunk's copy is exposed,
+// so the last chunk is the smallest)
+constexpr int kMaxChunks = 8;
 constexpr int64_t kChunkColumns = 1 << 17;
+
+// Maps [start[q], start[q+1]) form chunk q, q < count
+struct MapChunks {
+    int count;
+    int start[kMaxChunks + 1];
+};
+
+// K maps of n columns in chunks: none (one chunk) unless the values go to
+// the host; else the last chunk holds about half a share (at least one
+// map) and the others split the rest evenly
+MapChunks plan_chunks(int K, int64_t n, bool host_values) {
+    MapChunks c;
+    c.count = 1;
+    c.start[0] = 0;
+    c.start[1] = K;
+    if (!host_values) return c;
+    const int64_t want = std::min<int64_t>(std::min<int64_t>(K, kMaxChunks), std::max<int64_t>(1, (int64_t)K * n / kChunkColumns));
+    if (want < 2) return c;
+    const int C = (int)want;
+    const int last = std::max(1, K / (2 * C));
+    const int rest = K - last;
+    c.count = C;
+    for (int q = 0; q < C - 1; ++q) c.start[q] = (int)((int64_t)rest * q / (C - 1));
+    c.start[C - 1] = rest;
+    c.start[C] = K;
+    return c;
+}
 
 // K patterns of order n stored as one block-diagonal pattern
 struct PatternGroup {
@@ -635,7 +663,7 @@ __global__ void replicate_cols_kernel(int64_t n, T *a) {
 // column, work[K t + k] = work0[t] + k n, off[c] = K off0[c], so that the
 // same column of every map is solved side by side (one block reads map 0's
 // metadata for all of them)
-__global__ void expand_work_kernel(int K, int Kc, int n, const int32_t *work0, const int32_t *off0, int32_t *work,
+__global__ void expand_work_kernel(int K, MapChunks ch, int n, const int32_t *work0, const int32_t *off0, int32_t *work,
                                    int32_t *off) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int k = blockIdx.y;
@@ -643,23 +671,27 @@ __global__ void expand_work_kernel(int K, int Kc, int n, const int32_t *work0, c
         int b = 0;
         while (t >= off0[b + 1]) ++b;
         const int64_t c = off0[b + 1] - off0[b], tl = t - off0[b];
-        // maps in chunks of Kc: a chunk's items are contiguous within the
+        // maps in chunks: a chunk's items are contiguous within the
         // class, its maps interleaved column by column
-        const int k0 = (k / Kc) * Kc, wq = min(Kc, K - k0);
+        int q = 0;
+        while (q + 1 < ch.count && k >= ch.start[q + 1]) ++q;
+        const int k0 = ch.start[q], wq = ch.start[q + 1] - k0;
         work[(int64_t)K * off0[b] + (int64_t)k0 * c + wq * tl + (k - k0)] = work0[t] + k * n;
     }
     if (t <= kNumBins && k == 0) off[t] = K * off0[t];
 }
 
 cudaError_t interleaved_work_list(sam_handle h, Scratch &sc, int K, int n, const uint8_t *bin, int32_t *work,
-                                  int32_t *bin_off, int Kc = 0, const int32_t **off0_out = nullptr) {
+                                  int32_t *bin_off, const MapChunks *chunks = nullptr,
+                                  const int32_t **off0_out = nullptr) {
     int32_t *work0 = sc.get<int32_t>((size_t)n), *off0 = sc.get<int32_t>(kNumBins + 1);
     if (!work0 || !off0) return cudaErrorMemoryAllocation;
     cudaError_t e = build_work_list(h, n, bin, work0, off0);
     if (e != cudaSuccess) return e;
     const int64_t cnt = std::max<int64_t>(n, kNumBins + 1);
     dim3 grid((unsigned)((cnt + 255) / 256), (unsigned)K);
-    expand_work_kernel<<<grid, 256, 0, h->stream>>>(K, Kc > 0 && Kc < K ? Kc : K, n, work0, off0, work, bin_off);
+    const MapChunks ch = chunks ? *chunks : plan_chunks(K, n, false);
+    expand_work_kernel<<<grid, 256, 0, h->stream>>>(K, ch, n, work0, off0, work, bin_off);
     count_launch(h);
     if (off0_out) *off0_out = off0;
     return cudaGetLastError();
@@ -1294,12 +1326,8 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     // the same columns per class; the automatic mode re-solves columns after
     // all chunks and is left whole)
     const bool autoref = precision == SAM_FP32_REFINE && refine_steps < 0;
-    int Kc = K;
-    if (shared && !autoref && sg.is_host_output(d_v)) {
-        const int64_t chunks = std::min<int64_t>(std::min<int64_t>(K, kMaxChunks), std::max<int64_t>(1, N / kChunkColumns));
-        Kc = (int)((K + chunks - 1) / chunks);
-    }
-    const bool chunked = Kc < K;
+    const MapChunks chunks = plan_chunks(K, n, shared && !autoref && sg.is_host_output(d_v));
+    const bool chunked = chunks.count > 1;
     cudaEvent_t ev_bins = nullptr;
     struct EventGuard {
         cudaEvent_t &e;
@@ -1308,7 +1336,7 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
         }
     } ev_guard{ev_bins};
     const int32_t *off0 = nullptr;
-    if ((shared ? interleaved_work_list(h, sc, K, n, bin, work, bin_off, Kc, &off0)
+    if ((shared ? interleaved_work_list(h, sc, K, n, bin, work, bin_off, &chunks, &off0)
                 : build_work_list(h, (int)N, bin, work, bin_off)) != cudaSuccess)
         return SAM_ERR_CUDA;
     if (chunked && (cudaEventCreateWithFlags(&ev_bins, cudaEventDisableTiming) != cudaSuccess ||
@@ -1389,8 +1417,8 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
             big[b] = (int64_t)cnt[b] * 4 >= n;
             if (!big[b] && launch_lsq_bin(h, precision, a, b) != cudaSuccess) return SAM_ERR_CUDA;
         }
-        for (int k0 = 0; k0 < K; k0 += Kc) {
-            const int k1 = std::min(K, k0 + Kc);
+        for (int q = 0; q < chunks.count; ++q) {
+            const int k0 = chunks.start[q], k1 = chunks.start[q + 1];
             for (int b = 0; b < kNumBins; ++b) {
                 if (!big[b]) continue;
                 LsqArgs ac = a;

@@ -200,11 +200,11 @@ def test_host_buffers_give_the_device_result(sam, handle):
 def test_chunked_host_outputs_give_the_device_result(sam, handle, nmat, host_inputs, steps):
     """A one-structure sequence large enough (4 or 5 maps of 65536 columns)
     that a build into host arrays solves its large size classes in chunks of
-    maps (2 + 2, or 3 + 2) and copies each chunk's values while the next is
-    solved (with host inputs, their values are copied while the structure
-    work runs; the automatic refinement mode re-solves columns after all the
-    solves and is not chunked): the same bits as the build into device
-    arrays, residuals and column status included."""
+    maps (3 + 1, or 4 + 1: the last chunk is the smallest) and copies each
+    chunk's values while the next is solved (with host inputs, their values
+    are copied while the structure work runs; the automatic refinement mode
+    re-solves columns after all the solves and is not chunked): the same bits
+    as the build into device arrays, residuals and column status included."""
     import torch
 
     seq = W.config2(nx=256, nmat=nmat)
