@@ -968,25 +968,59 @@ sam_status sam_pattern_build_batched(sam_handle h, int K, const sam_csr *A, int 
     Scratch sc(h);
     Stager sg(sc, st);
     std::vector<DevCsr> d(K);
-    for (int k = 0; k < K; ++k) d[k] = stage_csr(sg, &A[k], false);
+    // host structures: map 0's now, the others on the input side stream; a
+    // batch of one structure needs map 0's alone for its pattern, which is
+    // built while the others copy (and dropped if they turn out to differ)
+    d[0] = stage_csr(sg, &A[0], false);
+    for (int k = 1; k < K; ++k) {
+        d[k].n = A[k].n;
+        d[k].nnz = A[k].nnz;
+        d[k].rp = sg.in_deferred(A[k].row_ptr, (size_t)A[k].n + 1);
+        d[k].ci = sg.in_deferred(A[k].col_idx, (size_t)A[k].nnz);
+    }
     if (sg.failed) return SAM_ERR_OOM;
+    // map 0's pattern (level-L CSC), built once
+    struct Map0Pattern {
+        sam_handle h;
+        int32_t *jcp = nullptr, *jri = nullptr;
+        int64_t nnz = 0;
+        bool built = false;
+        ~Map0Pattern() {  // released unless handed to a pattern group
+            pool_free(h, jcp);
+            pool_free(h, jri);
+        }
+    } p0{h};
+    auto build_map0 = [&](bool sym0) -> sam_status {
+        int32_t *kcp = sc.get<int32_t>((size_t)n + 1), *kri = sc.get<int32_t>((size_t)d[0].nnz);
+        if (!kcp || !kri) return SAM_ERR_OOM;
+        if (csr_to_csc(h, n, d[0].nnz, d[0].rp, d[0].ci, nullptr, kcp, kri, nullptr, nullptr, sym0) != cudaSuccess)
+            return SAM_ERR_CUDA;
+        p0.built = true;
+        return level_pattern(h, n, kcp, kri, d[0].nnz, level, &p0.jcp, &p0.jri, &p0.nnz);
+    };
+    sam_status s;
+    bool sym0 = false;
+    if (sg.inputs_pending()) {
+        std::vector<char> sv0;
+        s = validate_all(h, sc, {d[0]}, &sv0);
+        if (s != SAM_OK) return s;
+        sym0 = sv0[0] != 0;
+        if ((s = build_map0(sym0)) != SAM_OK) return s;
+        sg.join_inputs();
+    }
     std::vector<char> symv, same;
     const std::vector<std::pair<int, int>> whole{{0, K}};
-    sam_status s = validate_all(h, sc, d, &symv, K > 1 ? &whole : nullptr, &same);
+    s = validate_all(h, sc, d, &symv, K > 1 ? &whole : nullptr, &same);
     if (s != SAM_OK) return s;
     bool sym = true;
     for (char c : symv) sym = sym && c;
     if (K > 1 && same[0]) {
         // one structure for the whole sequence (the paper's setting, Sec. 2):
         // the pattern of map 0, replicated for every map
-        int32_t *kcp = sc.get<int32_t>((size_t)n + 1), *kri = sc.get<int32_t>((size_t)d[0].nnz);
-        if (!kcp || !kri) return SAM_ERR_OOM;
-        if (csr_to_csc(h, n, d[0].nnz, d[0].rp, d[0].ci, nullptr, kcp, kri, nullptr, nullptr, sym) != cudaSuccess)
-            return SAM_ERR_CUDA;
-        int32_t *jcp = nullptr, *jri = nullptr;
-        int64_t nnz = 0;
-        s = level_pattern(h, n, kcp, kri, d[0].nnz, level, &jcp, &jri, &nnz);
-        if (s != SAM_OK) return s;
+        if (!p0.built && (s = build_map0(sym)) != SAM_OK) return s;
+        int32_t *jcp = p0.jcp, *jri = p0.jri;
+        const int64_t nnz = p0.nnz;
+        p0.jcp = p0.jri = nullptr;  // owned by the group from here
         PatternGroup *g1 = nullptr, *g = nullptr;
         s = group_finish(h, 1, n, jcp, jri, nnz, &g1, sym);
         if (s != SAM_OK) return s;

@@ -112,3 +112,43 @@ def test_shared_and_per_column_shadow_agree_in_the_adjoint(sam):
                                           1.0)
             assert bool((dk == dak[koff[k]:koff[k + 1]]).all())
             assert bool((d0 == da0[k * a0.nnz:(k + 1) * a0.nnz]).all())
+
+
+HOST_SEQS = {"q1_40_one_structure": lambda: W.config2(nx=40, nmat=5),
+             "fem_24_changing": lambda: W.config4(ncell=24, nmat=5, flip_frac=0.2)}
+
+
+@pytest.mark.parametrize("case", sorted(HOST_SEQS))
+@pytest.mark.parametrize("level", [1, 2])
+def test_host_batch_patterns_equal_device_ones(sam, case, level):
+    """Batched pattern builds from host arrays (map 0's structure first, the
+    others copied while map 0's pattern is built; that pattern is dropped
+    when the structures differ) give the device build's patterns, bit for
+    bit, for a sequence of one structure and one whose structure changes."""
+    seq = HOST_SEQS[case]()
+    with sam.Handle() as h:
+        dev = h.sam_pattern_build_batched([sam.Csr.from_host(m) for m in seq.mats], level)
+        host = h.sam_pattern_build_batched([sam.Csr(m.indptr, m.indices, m.data, n=m.n) for m in seq.mats], level)
+        for a, b in zip(dev, host):
+            assert a.nnz == b.nnz
+            assert bool((a.colptr() == b.colptr()).all()) and bool((a.rowidx() == b.rowidx()).all())
+
+
+def test_host_batch_with_a_bad_later_map_is_rejected(sam):
+    """A later map with unsorted column indices, given as host arrays, is
+    rejected after map 0's pattern was built speculatively; the handle stays
+    usable."""
+    seq = W.config2(nx=24, nmat=4)
+    bad = seq.mats[2]
+    ci = bad.indices.copy()
+    r = 5
+    b, e = bad.indptr[r], bad.indptr[r + 1]
+    ci[b:e] = ci[b:e][::-1]
+    mats = [sam.Csr(m.indptr, m.indices, m.data, n=m.n) for m in seq.mats]
+    mats[2] = sam.Csr(bad.indptr, ci, bad.data, n=bad.n)
+    with sam.Handle() as h:
+        with pytest.raises(sam.SamError) as err:
+            h.sam_pattern_build_batched(mats, 2)
+        assert err.value.status == sam.SAM_ERR_BAD_CSR
+        ok = h.sam_pattern_build_batched([sam.Csr.from_host(m) for m in seq.mats], 2)
+        assert len(ok) == 4 and all(p.nnz == ok[0].nnz for p in ok)
