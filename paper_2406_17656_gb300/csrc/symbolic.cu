@@ -830,7 +830,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const i
         // entries lie beyond zloc's capacity (or no target is given)
         int zb = 0, zlen = 0, zro = 0;
         if (tg.zloc) {
-            const int kmap = (int)(j / tg.n);
+            const int kmap = (int)((uint32_t)j / (uint32_t)tg.n);  // j < 2^31: 32-bit division
             const int zc = tg.zbig ? (int)j : (int)(j - (int64_t)kmap * tg.n);
             zro = tg.zbig ? 0 : kmap * tg.n;
             zb = tg.zcp[zc];
