@@ -62,6 +62,9 @@ def parse():
                     help="profiling aid: run STEPS whole steps (level-2 patterns + batched maps + residuals) of "
                          "the P1 FEM 512x512 sequence and exit (no JSON line)")
     ap.add_argument("--fem-maps", type=int, default=16, help="maps of the --profile-fem sequence")
+    ap.add_argument("--profile-sparsify", type=int, default=0, metavar="CALLS",
+                    help="profiling aid: run CALLS batched column-tau (0.8) sparsifications of the benchmark's maps "
+                         "and exit (no JSON line)")
     ap.add_argument("--profile-adjoint", type=int, default=0, metavar="STEPS",
                     help="profiling aid: run STEPS adjoints of the benchmark's batched build (dL/dM random, "
                          "residual term on) and exit (no JSON line)")
@@ -693,6 +696,18 @@ def main():
     a0 = sam.Csr.from_host(a0h, dev)
     if args.profile_gmres > 0:
         profile_gmres(h, sam, torch, dev, aks, a0, n, args.level, args.profile_gmres)
+        h.close()
+        return
+    if args.profile_sparsify > 0:
+        for _ in range(2):
+            h.sam_sparsify_batched(aks, "tau", 0.8)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.profile_sparsify):
+            h.sam_sparsify_batched(aks, "tau", 0.8)
+        torch.cuda.synchronize()
+        print("sparsify: %d batched calls, %.3f ms per call (%d maps)" % (
+            args.profile_sparsify, (time.perf_counter() - t) * 1e3 / args.profile_sparsify, K))
         h.close()
         return
     if args.profile_adjoint > 0:
