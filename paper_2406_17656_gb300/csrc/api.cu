@@ -1535,9 +1535,23 @@ sam_status sam_sparsify(sam_handle h, const sam_csr *A, int mode, double param, 
     uint8_t *keep = sc.get<uint8_t>((size_t)a.nnz);
     int32_t *cnt = sc.get<int32_t>((size_t)n + 1);
     if (!keep || !cnt) return SAM_ERR_OOM;
-    if (sparsify_keep(h, n, a.nnz, a.rp, a.ci, a.v, mode, param, keep) != cudaSuccess ||
-        compact_kept(h, n, a.rp, a.ci, a.v, keep, cnt, d_rp, d_ci, d_v) != cudaSuccess)
+    if (mode != SAM_SPARSIFY_LFIL && n > 0 && a.nnz > 0) {
+        // row-wise decisions: the table form, which fuses the counts
+        const CsrPtrs tab{a.rp, a.ci, a.v};
+        const int64_t off[2] = {0, a.nnz};
+        CsrPtrs *dtab = sc.get<CsrPtrs>(1);
+        int64_t *doff = sc.get<int64_t>(2), *koff = sc.get<int64_t>(2);
+        int32_t *orp = sc.get<int32_t>((size_t)n + 1);
+        if (!dtab || !doff || !koff || !orp) return SAM_ERR_OOM;
+        cudaMemcpyAsync(dtab, &tab, sizeof(CsrPtrs), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(doff, off, sizeof(off), cudaMemcpyHostToDevice, st);
+        if (sparsify_rows_batched(h, 1, n, dtab, doff, a.nnz, mode == SAM_SPARSIFY_GLOBAL ? 0 : 1, param, keep, cnt,
+                                  orp, d_rp, d_ci, d_v, koff) != cudaSuccess)
+            return SAM_ERR_CUDA;
+    } else if (sparsify_keep(h, n, a.nnz, a.rp, a.ci, a.v, mode, param, keep) != cudaSuccess ||
+               compact_kept(h, n, a.rp, a.ci, a.v, keep, cnt, d_rp, d_ci, d_v) != cudaSuccess) {
         return SAM_ERR_CUDA;
+    }
     int32_t kept = 0;
     if (cudaMemcpyAsync(&kept, d_rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return SAM_ERR_CUDA;
@@ -1583,6 +1597,25 @@ sam_status sam_sparsify_batched(sam_handle h, int K, const sam_csr *A, int mode,
     }
     CsrPtrs *dtab = sc.get<CsrPtrs>(K);
     int64_t *doff = sc.get<int64_t>(K + 1);
+    if (mode != SAM_SPARSIFY_LFIL && n > 0 && tot > 0) {
+        // row-wise decisions: every map read in place through the table
+        uint8_t *keep = sc.get<uint8_t>((size_t)tot);
+        int32_t *cnt = sc.get<int32_t>((size_t)N + 1), *orp = sc.get<int32_t>((size_t)N + 1);
+        int64_t *koff = sc.get<int64_t>((size_t)K + 1);
+        if (!dtab || !doff || !keep || !cnt || !orp || !koff) return SAM_ERR_OOM;
+        cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * K, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, st);
+        if (sparsify_rows_batched(h, K, n, dtab, doff, tot, mode == SAM_SPARSIFY_GLOBAL ? 0 : 1, param, keep, cnt,
+                                  orp, d_rp, d_ci, d_v, koff) != cudaSuccess)
+            return SAM_ERR_CUDA;
+        std::vector<int64_t> hoff((size_t)K + 1, 0);
+        if (cudaMemcpyAsync(hoff.data(), koff, sizeof(int64_t) * (K + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return SAM_ERR_CUDA;
+        if (sg.finish() != cudaSuccess) return SAM_ERR_CUDA;
+        s = drain_status(h);
+        for (int k = 0; k <= K; ++k) S_offsets[k] = hoff[k];
+        return s;
+    }
     int32_t *brp = sc.get<int32_t>((size_t)N + 1), *bci = sc.get<int32_t>((size_t)tot);
     double *bv = sc.get<double>((size_t)tot);
     uint8_t *keep = sc.get<uint8_t>((size_t)tot);

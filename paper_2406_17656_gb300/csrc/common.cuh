@@ -199,6 +199,15 @@ cudaError_t mirror_positions(sam_handle h, int n, const int32_t *rp, const int32
 // (cnt: int32[n] workspace)
 cudaError_t sparsify_keep(sam_handle h, int n, int64_t nnz, const int32_t *rp, const int32_t *ci, const double *v,
                           int mode, double param, uint8_t *keep);
+// Global threshold (mode 0) or column tau (mode 1) of K matrices of order n
+// given by a device table (map k's entries at off[k] .. of the batch), in one
+// pass without concatenating them: keep (tot flags), cnt and orp (K n + 1)
+// are workspace; the kept entries of map k go to out_ci / out_v (nullable)
+// at koff[k] in its own numbering, its row pointers to out_rp + k (n + 1)
+// relative to koff[k]; koff has K + 1 entries.
+cudaError_t sparsify_rows_batched(sam_handle h, int K, int n, const CsrPtrs *mats, const int64_t *off, int64_t tot,
+                                  int mode, double param, uint8_t *keep, int32_t *cnt, int32_t *orp,
+                                  int32_t *out_rp, int32_t *out_ci, double *out_v, int64_t *koff);
 cudaError_t compact_kept(sam_handle h, int n, const int32_t *rp, const int32_t *ci, const double *v,
                          const uint8_t *keep, int32_t *cnt, int32_t *orp, int32_t *oci, double *ov);
 // doubles of workspace segmented_sum_f64 needs for K segments

@@ -108,7 +108,143 @@ __global__ void fill_kept_kernel(int n, const int32_t *rp, const int32_t *ci, co
         }
 }
 
+// ---- row-wise sparsifications of K matrices of order n, read in place
+// through a table (map k's entries at offsets off[k] .. of the batch; its
+// rows and columns numbered within the map; per-map arrays [K][n])
+
+__global__ void diag_scale_batch_kernel(const CsrPtrs *mats, int n, double *d) {
+    const int k = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t *rp = mats[k].rp, *ci = mats[k].ci;
+    const double *v = mats[k].v;
+    const int b = rp[i], len = rp[i + 1] - b;
+    const int q = lower_bound_row(ci + b, len, i);
+    double di = 1.0;
+    if (q < len && ci[b + q] == i && fabs(v[b + q]) > 0.0) di = fabs(v[b + q]);
+    d[(int64_t)k * n + i] = di;
+}
+
+__global__ void col_max_batch_kernel(const CsrPtrs *mats, const int64_t *off, int n, unsigned long long *cmax) {
+    const int k = blockIdx.y;
+    const int64_t nnz = off[k + 1] - off[k];
+    const int32_t *ci = mats[k].ci;
+    const double *v = mats[k].v;
+    unsigned long long *cm = cmax + (int64_t)k * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        atomicMax(&cm[ci[e]], (unsigned long long)__double_as_longlong(fabs(v[e])));
+}
+
+// keep flags (the same expressions as keep_global_kernel / keep_tau_kernel)
+// and each row's kept count, eight lanes per row
+__global__ void keep_count_batch_kernel(const CsrPtrs *mats, const int64_t *off, int n, int mode, double param,
+                                        const double *d, const unsigned long long *cmax, uint8_t *keep,
+                                        int32_t *cnt) {
+    const int k = blockIdx.y;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int lane = threadIdx.x & 31, sub = lane & 7;
+    if (i >= n) return;  // whole groups of eight
+    const unsigned gmask = 0xffu << (lane & 24);
+    const int32_t *rp = mats[k].rp, *ci = mats[k].ci;
+    const double *v = mats[k].v;
+    const int64_t base = (int64_t)k * n;
+    uint8_t *kp = keep + off[k];
+    int c = 0;
+    if (mode == 0) {
+        const double di = d[base + i];
+        for (int e = rp[i] + sub; e < rp[i + 1]; e += 8) {
+            const int j = ci[e];
+            const uint8_t f = (uint8_t)((j == (int)i) || (fabs(v[e]) / sqrt(di * d[base + j]) > param));
+            kp[e] = f;
+            c += f;
+        }
+    } else {
+        for (int e = rp[i] + sub; e < rp[i + 1]; e += 8) {
+            const int j = ci[e];
+            const double mx = __longlong_as_double((long long)cmax[base + j]);
+            const uint8_t f = (uint8_t)((j == (int)i) || (fabs(v[e]) > (1.0 - param) * mx));
+            kp[e] = f;
+            c += f;
+        }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) c += __shfl_xor_sync(gmask, c, o, 8);
+    if (sub == 0) cnt[base + i] = c;
+}
+
+// the kept entries of row i of map k, in order, at orp[k n + i] of the
+// batch's output (column indices in the map's own numbering); rows are
+// short, so one thread walks a row
+__global__ void fill_kept_batch_kernel(const CsrPtrs *mats, const int64_t *off, int n, const uint8_t *keep,
+                                       const int32_t *orp, int32_t *oci, double *ov) {
+    const int k = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t *rp = mats[k].rp, *ci = mats[k].ci;
+    const double *v = mats[k].v;
+    const uint8_t *kp = keep + off[k];
+    int o = orp[(int64_t)k * n + i];
+    for (int e = rp[i]; e < rp[i + 1]; ++e)
+        if (kp[e]) {
+            oci[o] = ci[e];
+            if (ov) ov[o] = v[e];
+            ++o;
+        }
+}
+
+// map k's row pointers relative to its own offset, and the offsets
+__global__ void kept_rows_kernel(int K, int n, const int32_t *orp, int32_t *out_rp, int64_t *koff) {
+    const int k = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    const int64_t base = (int64_t)k * n;
+    const int32_t o0 = orp[base];
+    out_rp[(int64_t)k * (n + 1) + i] = orp[base + i] - o0;
+    if (i == 0) {
+        koff[k] = o0;
+        if (k == K - 1) koff[K] = orp[(int64_t)K * n];
+    }
+}
+
 }  // namespace
+
+cudaError_t sparsify_rows_batched(sam_handle h, int K, int n, const CsrPtrs *mats, const int64_t *off, int64_t tot,
+                                  int mode, double param, uint8_t *keep, int32_t *cnt, int32_t *orp,
+                                  int32_t *out_rp, int32_t *out_ci, double *out_v, int64_t *koff) {
+    cudaStream_t st = handle_stream(h);
+    const int64_t N = (int64_t)K * n;
+    if (K < 1 || n < 1) return cudaErrorInvalidValue;
+    double *d = nullptr;
+    unsigned long long *cmax = nullptr;
+    if (mode == 0) {
+        d = (double *)pool_alloc(h, sizeof(double) * (size_t)N);
+        if (!d) return cudaErrorMemoryAllocation;
+        diag_scale_batch_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)K), 256, 0, st>>>(mats, n, d);
+        count_launch(h);
+    } else {
+        cmax = (unsigned long long *)pool_alloc(h, sizeof(unsigned long long) * (size_t)N);
+        if (!cmax) return cudaErrorMemoryAllocation;
+        cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(unsigned long long) * (size_t)N, st);
+        if (e != cudaSuccess) return e;
+        int64_t bx = (tot / K + 255) / 256 + 1;
+        const int64_t cap = (int64_t)handle_sms(h) * 8 / K + 1;
+        if (bx > cap) bx = cap;
+        col_max_batch_kernel<<<dim3((unsigned)bx, (unsigned)K), 256, 0, st>>>(mats, off, n, cmax);
+        count_launch(h);
+    }
+    const unsigned rows8 = (unsigned)(((int64_t)n * 8 + 255) / 256);
+    keep_count_batch_kernel<<<dim3(rows8, (unsigned)K), 256, 0, st>>>(mats, off, n, mode, param, d, cmax, keep, cnt);
+    count_launch(h);
+    pool_free(h, d);
+    pool_free(h, cmax);
+    cudaError_t e = exclusive_scan_i32(h, cnt, orp, N);
+    if (e != cudaSuccess) return e;
+    fill_kept_batch_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)K), 256, 0, st>>>(mats, off, n, keep, orp,
+                                                                                           out_ci, out_v);
+    kept_rows_kernel<<<dim3((unsigned)((n + 1 + 255) / 256), (unsigned)K), 256, 0, st>>>(K, n, orp, out_rp, koff);
+    count_launch(h, 2);
+    return cudaGetLastError();
+}
 
 cudaError_t sparsify_keep(sam_handle h, int n, int64_t nnz, const int32_t *rp, const int32_t *ci, const double *v,
                           int mode, double param, uint8_t *keep) {
