@@ -136,15 +136,13 @@ __global__ void col_max_batch_kernel(const CsrPtrs *mats, const int64_t *off, in
 }
 
 // keep flags (the same expressions as keep_global_kernel / keep_tau_kernel)
-// and each row's kept count, eight lanes per row
+// and each row's kept count; rows are short, so one thread walks a row
 __global__ void keep_count_batch_kernel(const CsrPtrs *mats, const int64_t *off, int n, int mode, double param,
                                         const double *d, const unsigned long long *cmax, uint8_t *keep,
                                         int32_t *cnt) {
     const int k = blockIdx.y;
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-    const int lane = threadIdx.x & 31, sub = lane & 7;
-    if (i >= n) return;  // whole groups of eight
-    const unsigned gmask = 0xffu << (lane & 24);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
     const int32_t *rp = mats[k].rp, *ci = mats[k].ci;
     const double *v = mats[k].v;
     const int64_t base = (int64_t)k * n;
@@ -152,24 +150,22 @@ __global__ void keep_count_batch_kernel(const CsrPtrs *mats, const int64_t *off,
     int c = 0;
     if (mode == 0) {
         const double di = d[base + i];
-        for (int e = rp[i] + sub; e < rp[i + 1]; e += 8) {
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
             const int j = ci[e];
-            const uint8_t f = (uint8_t)((j == (int)i) || (fabs(v[e]) / sqrt(di * d[base + j]) > param));
+            const uint8_t f = (uint8_t)((j == i) || (fabs(v[e]) / sqrt(di * d[base + j]) > param));
             kp[e] = f;
             c += f;
         }
     } else {
-        for (int e = rp[i] + sub; e < rp[i + 1]; e += 8) {
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
             const int j = ci[e];
             const double mx = __longlong_as_double((long long)cmax[base + j]);
-            const uint8_t f = (uint8_t)((j == (int)i) || (fabs(v[e]) > (1.0 - param) * mx));
+            const uint8_t f = (uint8_t)((j == i) || (fabs(v[e]) > (1.0 - param) * mx));
             kp[e] = f;
             c += f;
         }
     }
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) c += __shfl_xor_sync(gmask, c, o, 8);
-    if (sub == 0) cnt[base + i] = c;
+    cnt[base + i] = c;
 }
 
 // the kept entries of row i of map k, in order, at orp[k n + i] of the
@@ -232,8 +228,8 @@ cudaError_t sparsify_rows_batched(sam_handle h, int K, int n, const CsrPtrs *mat
         col_max_batch_kernel<<<dim3((unsigned)bx, (unsigned)K), 256, 0, st>>>(mats, off, n, cmax);
         count_launch(h);
     }
-    const unsigned rows8 = (unsigned)(((int64_t)n * 8 + 255) / 256);
-    keep_count_batch_kernel<<<dim3(rows8, (unsigned)K), 256, 0, st>>>(mats, off, n, mode, param, d, cmax, keep, cnt);
+    const unsigned rows1 = (unsigned)((n + 255) / 256);
+    keep_count_batch_kernel<<<dim3(rows1, (unsigned)K), 256, 0, st>>>(mats, off, n, mode, param, d, cmax, keep, cnt);
     count_launch(h);
     pool_free(h, d);
     pool_free(h, cmax);
