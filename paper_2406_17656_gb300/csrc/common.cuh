@@ -194,9 +194,10 @@ cudaError_t segmented_sum_f64(sam_handle h, const double *x, int K, int64_t seg,
 // pos[q] = position of the mirror entry of CSR position q of a structurally
 // symmetric matrix (the CSR position of A(ci[q], row of q))
 cudaError_t mirror_positions(sam_handle h, int n, const int32_t *rp, const int32_t *ci, int32_t *pos);
-// Sec. 4 sparsification: keep[e] (one byte per stored entry) for mode 0
-// (global threshold), 1 (column tau), 2 (lfil); then the kept entries in CSR
-// (cnt: int32[n] workspace)
+// Sec. 4 sparsification by lfil (mode 2): keep[e] (one byte per stored
+// entry); then the kept entries in CSR (cnt: int32[n] workspace).  The
+// row-wise criteria (global threshold, column tau) are sparsify_rows_batched;
+// mode 0 or 1 here is cudaErrorInvalidValue unless there is nothing to do.
 cudaError_t sparsify_keep(sam_handle h, int n, int64_t nnz, const int32_t *rp, const int32_t *ci, const double *v,
                           int mode, double param, uint8_t *keep);
 // Global threshold (mode 0) or column tau (mode 1) of K matrices of order n

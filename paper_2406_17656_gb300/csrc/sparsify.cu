@@ -24,49 +24,6 @@ __device__ __forceinline__ int lower_bound_row(const int32_t *a, int len, int ke
     return lo;
 }
 
-// D_ii: |A_ii| when the diagonal is stored and nonzero, else 1
-__global__ void diag_scale_kernel(int n, const int32_t *rp, const int32_t *ci, const double *v, double *d) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int b = rp[i], len = rp[i + 1] - b;
-    const int q = lower_bound_row(ci + b, len, i);
-    double di = 1.0;
-    if (q < len && ci[b + q] == i && fabs(v[b + q]) > 0.0) di = fabs(v[b + q]);
-    d[i] = di;
-}
-
-// eight threads per row
-__global__ void keep_global_kernel(int n, const int32_t *rp, const int32_t *ci, const double *v, const double *d,
-                                   double thresh, uint8_t *keep) {
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-    const int sub = threadIdx.x & 7;
-    if (i >= n) return;
-    const double di = d[i];
-    for (int e = rp[i] + sub; e < rp[i + 1]; e += 8) {
-        const int j = ci[e];
-        keep[e] = (uint8_t)((j == (int)i) || (fabs(v[e]) / sqrt(di * d[j]) > thresh));
-    }
-}
-
-// column maxima of |A| as the bit patterns of non-negative doubles (which
-// order like the numbers)
-__global__ void col_max_kernel(int64_t nnz, const int32_t *ci, const double *v, unsigned long long *cmax) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
-        atomicMax(&cmax[ci[e]], (unsigned long long)__double_as_longlong(fabs(v[e])));
-}
-
-__global__ void keep_tau_kernel(int n, const int32_t *rp, const int32_t *ci, const double *v,
-                                const unsigned long long *cmax, double tau, uint8_t *keep) {
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-    const int sub = threadIdx.x & 7;
-    if (i >= n) return;
-    for (int e = rp[i] + sub; e < rp[i + 1]; e += 8) {
-        const int j = ci[e];
-        const double mx = __longlong_as_double((long long)cmax[j]);
-        keep[e] = (uint8_t)((j == (int)i) || (fabs(v[e]) > (1.0 - tau) * mx));
-    }
-}
-
 // one warp per column of the CSC (cp, ri, cv): the rank of an entry is the
 // number of entries before it in the order (larger |value|, then lower row)
 __global__ void keep_lfil_kernel(int n, const int32_t *cp, const int32_t *ri, const double *cv, const int32_t *perm,
@@ -112,6 +69,7 @@ __global__ void fill_kept_kernel(int n, const int32_t *rp, const int32_t *ci, co
 // through a table (map k's entries at offsets off[k] .. of the batch; its
 // rows and columns numbered within the map; per-map arrays [K][n])
 
+// D_ii: |A_ii| when the diagonal is stored and nonzero, else 1
 __global__ void diag_scale_batch_kernel(const CsrPtrs *mats, int n, double *d) {
     const int k = blockIdx.y;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -125,6 +83,8 @@ __global__ void diag_scale_batch_kernel(const CsrPtrs *mats, int n, double *d) {
     d[(int64_t)k * n + i] = di;
 }
 
+// column maxima of |A| as the bit patterns of non-negative doubles (which
+// order like the numbers)
 __global__ void col_max_batch_kernel(const CsrPtrs *mats, const int64_t *off, int n, unsigned long long *cmax) {
     const int k = blockIdx.y;
     const int64_t nnz = off[k + 1] - off[k];
@@ -135,8 +95,9 @@ __global__ void col_max_batch_kernel(const CsrPtrs *mats, const int64_t *off, in
         atomicMax(&cm[ci[e]], (unsigned long long)__double_as_longlong(fabs(v[e])));
 }
 
-// keep flags (the same expressions as keep_global_kernel / keep_tau_kernel)
-// and each row's kept count; rows are short, so one thread walks a row
+// keep flags (global threshold: i = j or |A_ij| / sqrt(D_ii D_jj) > thresh;
+// column tau: i = j or |A_ij| > (1 - tau) max_i |A_ij|) and each row's kept
+// count; rows are short, so one thread walks a row
 __global__ void keep_count_batch_kernel(const CsrPtrs *mats, const int64_t *off, int n, int mode, double param,
                                         const double *d, const unsigned long long *cmax, uint8_t *keep,
                                         int32_t *cnt) {
@@ -246,29 +207,7 @@ cudaError_t sparsify_keep(sam_handle h, int n, int64_t nnz, const int32_t *rp, c
                           int mode, double param, uint8_t *keep) {
     cudaStream_t st = handle_stream(h);
     if (n == 0 || nnz == 0) return cudaSuccess;
-    const int rows8 = (int)(((int64_t)n * 8 + 255) / 256);
-    if (mode == 0) {
-        double *d = (double *)pool_alloc(h, sizeof(double) * (size_t)n);
-        if (!d) return cudaErrorMemoryAllocation;
-        diag_scale_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, rp, ci, v, d);
-        keep_global_kernel<<<rows8, 256, 0, st>>>(n, rp, ci, v, d, param, keep);
-        count_launch(h, 2);
-        pool_free(h, d);
-        return cudaGetLastError();
-    }
-    if (mode == 1) {
-        unsigned long long *cmax = (unsigned long long *)pool_alloc(h, sizeof(unsigned long long) * (size_t)n);
-        if (!cmax) return cudaErrorMemoryAllocation;
-        cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(unsigned long long) * (size_t)n, st);
-        if (e != cudaSuccess) return e;
-        int64_t blocks = (nnz + 255) / 256;
-        if (blocks > (int64_t)handle_sms(h) * 8) blocks = (int64_t)handle_sms(h) * 8;
-        col_max_kernel<<<(unsigned)blocks, 256, 0, st>>>(nnz, ci, v, cmax);
-        keep_tau_kernel<<<rows8, 256, 0, st>>>(n, rp, ci, v, cmax, param, keep);
-        count_launch(h, 2);
-        pool_free(h, cmax);
-        return cudaGetLastError();
-    }
+    if (mode != 2) return cudaErrorInvalidValue;  // the row-wise criteria: sparsify_rows_batched
     // lfil: rank within the columns of the transpose
     int32_t *cp = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)n + 1));
     int32_t *ri = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)nnz);
