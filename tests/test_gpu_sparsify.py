@@ -114,3 +114,29 @@ def test_batched_sparsify_equals_per_matrix(sam, handle, mode, param):
         assert np.array_equal(got.data.cpu().numpy(), dv)
         one = handle.sam_sparsify(sam.Csr.from_host(a), mode, param)
         assert np.array_equal(one.data.cpu().numpy(), got.data.cpu().numpy())
+
+
+@pytest.mark.parametrize("mode,param", [("global", 0.05), ("tau", 0.7), ("lfil", 2)])
+def test_batched_sparsify_of_different_structures(sam, handle, mode, param):
+    """One call over three matrices of one order with different structures
+    and entry counts (each read through its own offsets): every map's kept
+    entries equal the oracle's and the single call's, bit for bit."""
+    import scipy.sparse as sp
+
+    a = W.config4(ncell=24, nmat=1).mats[0].to_scipy().tocoo()
+    n = a.shape[0]
+    drop = (a.row != a.col) & ((a.row + 2 * a.col) % 5 == 0)
+    b = sp.csr_matrix((a.data[~drop], (a.row[~drop], a.col[~drop])), shape=(n, n))
+    rng = np.random.default_rng(11)
+    extra = sp.random(n, n, density=3.0 / n, random_state=rng, format="csr")
+    c = (a.tocsr() + extra).tocsr()
+    mats = [W.CSR.from_scipy(m.tocsr()) for m in (a.tocsr(), b, c)]
+    assert len({m.indptr[-1] for m in mats}) == 3
+    out = handle.sam_sparsify_batched([sam.Csr.from_host(m) for m in mats], mode, param)
+    for m, got in zip(mats, out):
+        ip, ix, dv = oracle.sparsify(m, mode, param)
+        assert np.array_equal(got.indptr.cpu().numpy(), ip)
+        assert np.array_equal(got.indices.cpu().numpy(), ix)
+        assert np.array_equal(got.data.cpu().numpy(), dv)
+        one = handle.sam_sparsify(sam.Csr.from_host(m), mode, param)
+        assert np.array_equal(one.indices.cpu().numpy(), ix) and np.array_equal(one.data.cpu().numpy(), dv)
