@@ -91,6 +91,15 @@ __device__ __forceinline__ KrySys kry_sys(const KryArgs &a, int k) {
 // gates of the launches of a cycle
 enum { kGateAlways = 0, kGateRun = 1, kGateCycle = 2 };
 
+// The kernels of a cycle are launched with programmatic stream
+// serialisation, so that a kernel's launch is prepared while its predecessor
+// runs; each waits here (griddepcontrol.wait: until the predecessor grid has
+// completed and its memory is visible) before reading anything.  No early
+// trigger: the successor is released as the blocks exit (triggering at the
+// start let waiting successor blocks take scheduling slots, 56 -> 73 us per
+// Arnoldi step).  Without the launch attribute the wait returns at once.
+__device__ __forceinline__ void after_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ bool gate_open(const KryCtl *c, int gate) {
     if (gate == kGateRun) return c->run != 0;
     if (gate == kGateCycle) return c->k > 0;
@@ -149,6 +158,7 @@ __global__ void __launch_bounds__(kKryThreads) kry_spmv_kernel(const KryCtl *ctl
                                                                const KryOp *ops, int per_system, const double *x,
                                                                const double *s, int s_stride, const double *b,
                                                                double *y, int mode) {
+    after_predecessor();
     const int k = blockIdx.y;
     if (!gate_open(ctls + k, gate)) return;
     const KryOp op = ops[per_system ? k : 0];
@@ -195,6 +205,7 @@ __global__ void __launch_bounds__(kKryThreads) kry_spmv_kernel(const KryCtl *ctl
 // iteration has stopped; what = 2 for the first cycle, always: beta, g_0,
 // s_0, k = 0, and the stopping tests beta <= rtol ||b|| and its >= maxiter).
 __global__ void __launch_bounds__(kKryThreads) kry_norm_kernel(KryArgs a, const double *x, int what) {
+    after_predecessor();
     __shared__ double red[kKryThreads / 32];
     __shared__ double tot;
     const KrySys S = kry_sys(a, blockIdx.y);
@@ -245,6 +256,7 @@ __global__ void __launch_bounds__(kKryThreads) kry_norm_kernel(KryArgs a, const 
 // shared memory, with the four shuffle reductions interleaved.
 __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j, int pass, const KryOp *ops,
                                                                const double *z, const double *zs, int zs_stride) {
+    after_predecessor();
     __shared__ double ws[2 * (kMaxRestart + 2) > kKryThreads ? 2 * (kMaxRestart + 2) : kKryThreads];
     __shared__ double cf[kMaxRestart + 1];
     __shared__ double red[kKryThreads / 32];
@@ -430,6 +442,7 @@ __global__ void __launch_bounds__(kKryThreads) kry_orth_kernel(KryArgs a, int j,
 // are staged in shared memory, and each column step updates the remaining
 // right-hand side in parallel (column-oriented back substitution).
 __global__ void __launch_bounds__(kKryThreads) kry_backsolve_kernel(KryArgs a) {
+    after_predecessor();
     __shared__ double R[kMaxRestart * (kMaxRestart + 1) / 2 > 0 ? 64 * 65 : 1];
     __shared__ double rhs[kMaxRestart + 1];
     const KrySys S = kry_sys(a, blockIdx.y);
@@ -462,6 +475,7 @@ __global__ void __launch_bounds__(kKryThreads) kry_backsolve_kernel(KryArgs a) {
 
 // t = sum_{l<k} coef_l V_l (accumulate = 1: t += that sum)
 __global__ void __launch_bounds__(kKryThreads) kry_combine_kernel(KryArgs a, double *t, int accumulate) {
+    after_predecessor();
     __shared__ double cf[kMaxRestart + 1];
     const KrySys S = kry_sys(a, blockIdx.y);
     const int k = S.c->k;
@@ -517,15 +531,32 @@ struct KryOps {
     int64_t a_nnz = 0, m_nnz = 0, p_nnz = 0;  // largest nnz over the systems
 };
 
+// a cycle kernel, launched so that it may be scheduled while its
+// predecessor finishes (it waits for it on the device: after_predecessor)
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 cudaError_t spmv(cudaStream_t st, const KryArgs &a, int gate, const KryOp *ops, int per_system, int64_t nnz,
                  const double *x, const double *s, int s_stride, const double *b, double *y, int mode) {
     const int n = a.n;
     const int L = lanes_for(n, nnz);
     const int64_t threads = (int64_t)n * L;
     const dim3 grid((unsigned)((threads + kKryThreads - 1) / kKryThreads), (unsigned)a.K);
-#define SAM_KRY_SPMV(LL)                                                                                          \
-    kry_spmv_kernel<LL><<<grid, kKryThreads, 0, st>>>(a.ctl, gate, n, ops, per_system, x, s, s_stride, b, y, mode); \
-    break;
+#define SAM_KRY_SPMV(LL)                                                                                        \
+    return launch_dep(kry_spmv_kernel<LL>, grid, dim3(kKryThreads), st, a.ctl, gate, n, ops, per_system, x, s, \
+                      s_stride, b, y, mode);
     switch (L) {
         case 1: SAM_KRY_SPMV(1)
         case 2: SAM_KRY_SPMV(2)
@@ -572,24 +603,23 @@ int enqueue_cycle(cudaStream_t st, const KryArgs &a, const KryOps &op, const dou
             ++launches;
         }
         for (int pass = 0; pass < 3; ++pass) {
-            if (pass == 0 && fuse)
-                kry_orth_kernel<<<gb, kKryThreads, 0, st>>>(a, j, pass, op.A, z, zs, ss);
-            else
-                kry_orth_kernel<<<gb, kKryThreads, 0, st>>>(a, j, pass, nullptr, nullptr, nullptr, 0);
-            if (!ok(cudaGetLastError())) return -1;
+            const bool f0 = pass == 0 && fuse;
+            if (!ok(launch_dep(kry_orth_kernel, gb, dim3(kKryThreads), st, a, j, pass, f0 ? op.A : (const KryOp *)nullptr,
+                               f0 ? z : (const double *)nullptr, f0 ? zs : (const double *)nullptr, f0 ? ss : 0)))
+                return -1;
             ++launches;
         }
     }
     // x += M (P_0 (sum_l y_l s_l V_l))
-    kry_backsolve_kernel<<<dim3(1, (unsigned)a.K), kKryThreads, 0, st>>>(a);
+    if (!ok(launch_dep(kry_backsolve_kernel, dim3(1, (unsigned)a.K), dim3(kKryThreads), st, a))) return -1;
     ++launches;
     if (!op.P && !op.M) {
-        kry_combine_kernel<<<gb, kKryThreads, 0, st>>>(a, x, 1);
+        if (!ok(launch_dep(kry_combine_kernel, gb, dim3(kKryThreads), st, a, x, 1))) return -1;
         ++launches;
     } else {
         // the sum goes to the temporary the first operator does not write
         double *sum = op.P ? u : t;
-        kry_combine_kernel<<<gb, kKryThreads, 0, st>>>(a, sum, 0);
+        if (!ok(launch_dep(kry_combine_kernel, gb, dim3(kKryThreads), st, a, sum, 0))) return -1;
         ++launches;
         const double *cur = sum;
         if (op.P && op.M) {
@@ -606,7 +636,7 @@ int enqueue_cycle(cudaStream_t st, const KryArgs &a, const KryOps &op, const dou
     if (!ok(cudaGetLastError())) return -1;
     // next cycle: V_0 = b - A x, beta, stopping test
     if (!ok(spmv(st, a, kGateRun, op.A, 1, op.a_nnz, x, nullptr, 0, b, a.V, 1))) return -1;
-    kry_norm_kernel<<<gb, kKryThreads, 0, st>>>(a, a.V, 1);
+    if (!ok(launch_dep(kry_norm_kernel, gb, dim3(kKryThreads), st, a, (const double *)a.V, 1))) return -1;
     launches += 2;
     if (!ok(cudaGetLastError())) return -1;
     return launches;
