@@ -18,8 +18,9 @@
  * (the paper's N_k).
  *
  * Conventions common to every call
- *  - Indices are 0-based int32; a matrix is square, n <= 2^31-1 rows, at
- *    most 2^31-1 stored entries.  CSR rows list column indices in strictly
+ *  - Indices are 0-based int32; a matrix is square, 1 <= n <= 2^31-1 rows
+ *    (an empty matrix is rejected with SAM_ERR_INVALID_ARG), at most
+ *    2^31-1 stored entries.  CSR rows list column indices in strictly
  *    ascending order.  Values are IEEE double.
  *  - Pointers in `sam_csr` and the vector/array arguments may point to
  *    device memory (cudaMalloc, managed) or to host memory (pinned or

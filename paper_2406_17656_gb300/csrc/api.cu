@@ -387,8 +387,9 @@ struct DevCsr {
     const double *v = nullptr;
 };
 
+// (an empty matrix, n = 0, has no columns to build a map for: rejected)
 sam_status check_csr_arg(const sam_csr *A, bool need_val) {
-    if (!A || A->n < 0 || A->nnz < 0 || A->nnz > INT32_MAX || !A->row_ptr || (A->nnz > 0 && !A->col_idx) ||
+    if (!A || A->n < 1 || A->nnz < 0 || A->nnz > INT32_MAX || !A->row_ptr || (A->nnz > 0 && !A->col_idx) ||
         (need_val && A->nnz > 0 && !A->val))
         return SAM_ERR_INVALID_ARG;
     return SAM_OK;
@@ -1072,7 +1073,7 @@ sam_status sam_pattern_build(sam_handle h, const sam_csr *A_k, int level, sam_pa
 
 sam_status sam_pattern_from_csc(sam_handle h, int32_t n, int64_t nnz, const int32_t *colptr, const int32_t *rowidx,
                                 sam_pattern *out) {
-    if (!h || !out || n < 0 || nnz < n || nnz > INT32_MAX || !colptr || !rowidx) return SAM_ERR_INVALID_ARG;
+    if (!h || !out || n < 1 || nnz < n || nnz > INT32_MAX || !colptr || !rowidx) return SAM_ERR_INVALID_ARG;
     *out = nullptr;
     int32_t *jcp = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)n + 1));
     int32_t *jri = (int32_t *)pool_alloc(h, sizeof(int32_t) * (size_t)(nnz ? nnz : 1));

@@ -260,6 +260,23 @@ def test_changing_structure_host_batch_gives_the_device_result(sam, handle):
 # ------------------------------------------------------------- edge cases
 
 
+def test_empty_matrix_is_rejected(sam, handle):
+    """An empty matrix (n = 0) is an invalid argument wherever a matrix is
+    taken, and the handle stays usable."""
+    import torch
+
+    E = sam.Csr(torch.zeros(1, dtype=torch.int32, device="cuda"), torch.zeros(0, dtype=torch.int32, device="cuda"),
+                torch.zeros(0, dtype=torch.float64, device="cuda"), n=0)
+    for call in (lambda: handle.sam_pattern_build(E, 1), lambda: handle.sam_sparsify(E, "tau", 0.5),
+                 lambda: handle.sam_residual(E, E, E)):
+        with pytest.raises(sam.SamError) as err:
+            call()
+        assert err.value.status == sam.SAM_ERR_INVALID_ARG
+    A = W.config1().mats[1]
+    S = handle.sam_pattern_build(dev(sam, A), 1)
+    assert S.nnz > A.n
+
+
 def test_one_by_one(sam, handle):
     A = W.CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([4.0]))
     B = W.CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([3.0]))
