@@ -123,8 +123,10 @@ sam_status sam_sync(sam_handle h);
  * the diagonal, 2 the pattern of (A_k + I)^2, 3 of (A_k + I)^3.
  * Only the structure of A_k is read (A_k->val may be NULL).  The pattern is
  * stored on the device in CSC form (= the CSC structure of the map) together
- * with the CSR structure of the map.  Synchronises once (to size the
- * output).  *out is library-owned: release with sam_pattern_destroy.
+ * with the CSR structure of the map.  Synchronises to validate A_k and to
+ * size the output (for level >= 2 also to size the candidate lists; the
+ * status word is read with the size).  *out is library-owned: release with
+ * sam_pattern_destroy.
  * Limit: a column whose merged candidate lists hold more than 1024 entries
  * and span more than 32768 row indices is SAM_ERR_UNSUPPORTED.
  */

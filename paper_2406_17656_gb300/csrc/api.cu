@@ -1032,7 +1032,8 @@ sam_status sam_pattern_build_batched(sam_handle h, int K, const sam_csr *A, int 
             group_release(g);
             return s;
         }
-        return drain_status(h);
+        // the status word was read with the pattern's size (level_pattern)
+        return cudaGetLastError() == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
     }
     // block-diagonal structure of the batch, then its CSC
     std::vector<CsrPtrs> tab(K);
@@ -1064,7 +1065,8 @@ sam_status sam_pattern_build_batched(sam_handle h, int K, const sam_csr *A, int 
         group_release(g);
         return s;
     }
-    return drain_status(h);
+    // the status word was read with the pattern's size (level_pattern)
+    return cudaGetLastError() == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
 }
 
 sam_status sam_pattern_build(sam_handle h, const sam_csr *A_k, int level, sam_pattern *out) {

@@ -991,9 +991,18 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
             N, l1cp, l1ri, curcp, curri, cnt, coff, pad, flag);
         count_launch(h);
         if (exclusive_scan_i32(h, cnt, nxcp, N) != cudaSuccess) return SAM_ERR_CUDA;
+        // the size and the status word in one synchronisation (the union
+        // flags a column it cannot hold; the word is sticky, so an earlier
+        // asynchronous call's error is reported here too)
+        int32_t fl = 0;
         if (cudaMemcpyAsync(&tot, nxcp + N, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&fl, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return SAM_ERR_CUDA;
+        if (fl != SAM_OK) {
+            cudaMemsetAsync(flag, 0, sizeof(int32_t), st);
+            return (sam_status)fl;
+        }
         int32_t *nxri = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)tot + 1));
         if (!nxri) return SAM_ERR_OOM;
         const int64_t cthreads = (int64_t)N * 8;
@@ -1009,9 +1018,17 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
         curcp = nxcp;
         curri = nxri;
     }
-    if (tot < 0 && (cudaMemcpyAsync(&tot, curcp + N, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                    cudaStreamSynchronize(st) != cudaSuccess))
-        return SAM_ERR_CUDA;
+    if (tot < 0) {
+        int32_t fl = 0;
+        if (cudaMemcpyAsync(&tot, curcp + N, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&fl, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return SAM_ERR_CUDA;
+        if (fl != SAM_OK) {
+            cudaMemsetAsync(flag, 0, sizeof(int32_t), st);
+            return (sam_status)fl;
+        }
+    }
     if (curcp != l1cp) {
         pool_free(h, l1cp);
         pool_free(h, l1ri);
