@@ -468,8 +468,9 @@ cudaError_t launch_structure_checks(sam_handle h, Scratch &sc, const std::vector
 // trusted inputs: one synchronisation for that alone).
 sam_status validate_all(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms, std::vector<char> *sym = nullptr,
                         const std::vector<std::pair<int, int>> *same_ranges = nullptr,
-                        std::vector<char> *same = nullptr) {
+                        std::vector<char> *same = nullptr, std::vector<int32_t> *maxrow = nullptr) {
     if (sym) sym->assign(ms.size(), 0);  // unknown (trusted inputs): treated as not symmetric
+    if (maxrow) maxrow->assign(ms.size(), -1);  // unknown
     const size_t R = (same_ranges && same) ? same_ranges->size() : 0;
     if (same) same->assign(R, 0);
     if (((h->flags & SAM_FLAG_TRUSTED) || ms.empty()) && R > 0) {
@@ -494,21 +495,25 @@ sam_status validate_all(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms
     }
     CsrPtrs *dtab = sc.get<CsrPtrs>(K);
     int64_t *dnz = sc.get<int64_t>(K);
-    // [0] status, [1 + k] matrix k not symmetric, [1 + K + r] range r not of one structure
-    int32_t *flag = sc.get<int32_t>((size_t)K + 1 + R);
+    // [0] status, [1 + k] matrix k not symmetric, [1 + K + r] range r not of
+    // one structure, [1 + K + R + k] the longest row of matrix k
+    const size_t W = (size_t)K + 1 + R + (maxrow ? (size_t)K : 0);
+    int32_t *flag = sc.get<int32_t>(W);
     if (!dtab || !dnz || !flag) return SAM_ERR_OOM;
     cudaMemcpyAsync(dtab, tab.data(), sizeof(CsrPtrs) * K, cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(dnz, nz.data(), sizeof(int64_t) * K, cudaMemcpyHostToDevice, h->stream);
-    cudaMemsetAsync(flag, 0, sizeof(int32_t) * ((size_t)K + 1 + R), h->stream);
+    cudaMemsetAsync(flag, 0, sizeof(int32_t) * W, h->stream);
     int32_t *asym = sym ? flag + 1 : nullptr;
+    int32_t *mrow = maxrow ? flag + 1 + K + R : nullptr;
     // matrices of different order (the residual call) are validated one by one
     bool same_order = true;
     for (auto &m : ms) same_order &= (m.n == ms[0].n);
     if (same_order) {
-        if (validate_csr_batch(h, K, ms[0].n, dtab, dnz, flag, asym) != cudaSuccess) return SAM_ERR_CUDA;
+        if (validate_csr_batch(h, K, ms[0].n, dtab, dnz, flag, asym, mrow) != cudaSuccess) return SAM_ERR_CUDA;
     } else {
         for (int k = 0; k < K; ++k)
-            if (validate_csr_batch(h, 1, ms[k].n, dtab + k, dnz + k, flag, asym ? asym + k : nullptr) != cudaSuccess)
+            if (validate_csr_batch(h, 1, ms[k].n, dtab + k, dnz + k, flag, asym ? asym + k : nullptr,
+                                   mrow ? mrow + k : nullptr) != cudaSuccess)
                 return SAM_ERR_CUDA;
     }
     // the comparison reads rp[0..n] and ci[0..nnz) of each matrix, inside
@@ -518,11 +523,13 @@ sam_status validate_all(sam_handle h, Scratch &sc, const std::vector<DevCsr> &ms
     std::vector<char> differ;
     if (R > 0 && launch_structure_checks(h, sc, ms, *same_ranges, flag + 1 + K, &differ) != cudaSuccess)
         return SAM_ERR_CUDA;
-    std::vector<int32_t> hf((size_t)K + 1 + R, 0);
-    cudaMemcpyAsync(hf.data(), flag, sizeof(int32_t) * ((size_t)K + 1 + R), cudaMemcpyDeviceToHost, h->stream);
+    std::vector<int32_t> hf(W, 0);
+    cudaMemcpyAsync(hf.data(), flag, sizeof(int32_t) * W, cudaMemcpyDeviceToHost, h->stream);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SAM_ERR_CUDA;
     if (sym && hf[0] == 0)
         for (int k = 0; k < K; ++k) (*sym)[k] = hf[(size_t)k + 1] == 0;
+    if (maxrow && hf[0] == 0)
+        for (int k = 0; k < K; ++k) (*maxrow)[k] = hf[(size_t)K + 1 + R + k];
     if (hf[0] == 0)
         for (size_t r = 0; r < R; ++r) (*same)[r] = !differ[r] && !hf[(size_t)K + 1 + r];
     return hf[0] ? (sam_status)hf[0] : SAM_OK;
@@ -991,34 +998,40 @@ sam_status sam_pattern_build_batched(sam_handle h, int K, const sam_csr *A, int 
             pool_free(h, jri);
         }
     } p0{h};
-    auto build_map0 = [&](bool sym0) -> sam_status {
+    // (a structurally symmetric matrix's columns are as long as its rows, so
+    // its longest row bounds the pattern's candidate lists: maxcol)
+    auto build_map0 = [&](bool sym0, int maxcol) -> sam_status {
         int32_t *kcp = sc.get<int32_t>((size_t)n + 1), *kri = sc.get<int32_t>((size_t)d[0].nnz);
         if (!kcp || !kri) return SAM_ERR_OOM;
         if (csr_to_csc(h, n, d[0].nnz, d[0].rp, d[0].ci, nullptr, kcp, kri, nullptr, nullptr, sym0) != cudaSuccess)
             return SAM_ERR_CUDA;
         p0.built = true;
-        return level_pattern(h, n, kcp, kri, d[0].nnz, level, &p0.jcp, &p0.jri, &p0.nnz);
+        return level_pattern(h, n, kcp, kri, d[0].nnz, level, &p0.jcp, &p0.jri, &p0.nnz, sym0 ? maxcol : -1);
     };
     sam_status s;
     bool sym0 = false;
     if (sg.inputs_pending()) {
         std::vector<char> sv0;
-        s = validate_all(h, sc, {d[0]}, &sv0);
+        std::vector<int32_t> mr0;
+        s = validate_all(h, sc, {d[0]}, &sv0, nullptr, nullptr, &mr0);
         if (s != SAM_OK) return s;
         sym0 = sv0[0] != 0;
-        if ((s = build_map0(sym0)) != SAM_OK) return s;
+        if ((s = build_map0(sym0, mr0[0])) != SAM_OK) return s;
         sg.join_inputs();
     }
     std::vector<char> symv, same;
+    std::vector<int32_t> mrow;
     const std::vector<std::pair<int, int>> whole{{0, K}};
-    s = validate_all(h, sc, d, &symv, K > 1 ? &whole : nullptr, &same);
+    s = validate_all(h, sc, d, &symv, K > 1 ? &whole : nullptr, &same, &mrow);
     if (s != SAM_OK) return s;
     bool sym = true;
+    int maxrow = 0;
     for (char c : symv) sym = sym && c;
+    for (int32_t m : mrow) maxrow = m < 0 ? -1 : (maxrow < 0 ? -1 : std::max(maxrow, (int)m));
     if (K > 1 && same[0]) {
         // one structure for the whole sequence (the paper's setting, Sec. 2):
         // the pattern of map 0, replicated for every map
-        if (!p0.built && (s = build_map0(sym)) != SAM_OK) return s;
+        if (!p0.built && (s = build_map0(sym, mrow[0])) != SAM_OK) return s;
         int32_t *jcp = p0.jcp, *jri = p0.jri;
         const int64_t nnz = p0.nnz;
         p0.jcp = p0.jri = nullptr;  // owned by the group from here
@@ -1054,7 +1067,7 @@ sam_status sam_pattern_build_batched(sam_handle h, int K, const sam_csr *A, int 
         return SAM_ERR_CUDA;
     int32_t *jcp = nullptr, *jri = nullptr;
     int64_t nnz = 0;
-    s = level_pattern(h, (int)N, kcp, kri, tot, level, &jcp, &jri, &nnz);
+    s = level_pattern(h, (int)N, kcp, kri, tot, level, &jcp, &jri, &nnz, sym ? maxrow : -1);
     if (s != SAM_OK) return s;
     PatternGroup *g = nullptr;
     // level-L patterns of a structurally symmetric matrix are symmetric

@@ -124,9 +124,11 @@ cudaError_t exclusive_scan_i32(sam_handle h, const int32_t *in, int32_t *out, in
 cudaError_t exclusive_scan_i64(sam_handle h, const int64_t *in, int64_t *out, int64_t n);
 
 // CSR structure checks of K matrices of order n; sets *flag to SAM_ERR_BAD_CSR
-// on any violation.  mats/nnz are device arrays of K entries.
+// on any violation.  mats/nnz are device arrays of K entries; asym[k] and
+// maxrow[k] (nullable, zeroed by the caller) receive "not structurally
+// symmetric" and the longest row of matrix k.
 cudaError_t validate_csr_batch(sam_handle h, int K, int n, const CsrPtrs *mats, const int64_t *nnz, int32_t *flag,
-                               int32_t *asym = nullptr);
+                               int32_t *asym = nullptr, int32_t *maxrow = nullptr);
 
 // Concatenate K CSR matrices of order n into the block-diagonal CSR of order
 // K n.  nnz_off (device, [K+1]) = prefix of the nnz; values optional.
@@ -143,9 +145,12 @@ cudaError_t csr_to_csc(sam_handle h, int n, int64_t nnz, const int32_t *rp, cons
                        bool symmetric = false);
 
 // Level-L pattern (CSC) of the matrix with CSC structure (kcp, kri), order N.
-// Allocates *jcp / *jri from the pool; synchronises once to size the result.
+// Allocates *jcp / *jri from the pool; synchronises to size the result (and
+// reads the status word with it).  maxcol >= 0: no column of the matrix is
+// longer, which bounds the level-2 and level-3 candidate lists and saves the
+// synchronisation that sizes them.
 sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t *kri, int64_t nnz, int level,
-                         int32_t **jcp, int32_t **jri, int64_t *nnz_out);
+                         int32_t **jcp, int32_t **jri, int64_t *nnz_out, int maxcol = -1);
 
 // The target of a shadow pass: zloc (nullable) receives the local row of
 // every target entry (see LsqArgs::zloc)

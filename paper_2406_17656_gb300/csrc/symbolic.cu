@@ -158,32 +158,26 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int len, int ke
     return lo;
 }
 
-// Structure checks of K CSR matrices of order n; asym[k] (nullable) is set
-// when matrix k is not structurally symmetric (some stored (i, c) without
-// a stored (c, i)).
-__global__ void validate_batch_kernel(int n, const CsrPtrs *mats, const int64_t *nnz, int32_t *flag,
-                                      int32_t *asym) {
-    const int k = blockIdx.y;
-    const int32_t *rp = mats[k].rp, *ci = mats[k].ci;
-    const int64_t nz = nnz[k];
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0 && (rp[0] != 0 || (int64_t)rp[n] != nz)) atomicCAS(flag, 0, SAM_ERR_BAD_CSR);
-    if (i >= n) return;
-    int b = rp[i], e = rp[i + 1];
+// Row i of a CSR matrix: checks (row pointers inside [0, nz], columns
+// strictly ascending and inside [0, n)) and, with sym, whether every (i, c)
+// has a stored mirror (c, i).  Returns the row's length, or -1 after
+// flagging an error.
+__device__ __forceinline__ int check_row(int n, const int32_t *rp, const int32_t *ci, int64_t nz, int64_t i,
+                                         int32_t *flag, bool &sym) {
+    const int b = rp[i], e = rp[i + 1];
     if (e < b || b < 0 || (int64_t)e > nz) {
         atomicCAS(flag, 0, SAM_ERR_BAD_CSR);
-        return;
+        return -1;
     }
     int prev = -1;
-    bool sym = true;
     for (int t = b; t < e; ++t) {
-        int c = ci[t];
+        const int c = ci[t];
         if (c <= prev || c >= n) {
             atomicCAS(flag, 0, SAM_ERR_BAD_CSR);
-            return;
+            return -1;
         }
         prev = c;
-        if (asym && sym) {
+        if (sym) {
             // the mirror (c, i) in row c, read only inside row c's valid range
             const int cb = rp[c], ce = rp[c + 1];
             if (cb < 0 || ce < cb || (int64_t)ce > nz) {
@@ -194,7 +188,33 @@ __global__ void validate_batch_kernel(int n, const CsrPtrs *mats, const int64_t 
             }
         }
     }
-    if (asym && !sym) asym[k] = 1;
+    return e - b;
+}
+
+// Structure checks of K CSR matrices of order n; asym[k] (nullable) is set
+// when matrix k is not structurally symmetric (some stored (i, c) without
+// a stored (c, i)); maxrow[k] (nullable) receives its longest row.
+__global__ void validate_batch_kernel(int n, const CsrPtrs *mats, const int64_t *nnz, int32_t *flag,
+                                      int32_t *asym, int32_t *maxrow) {
+    __shared__ int smax;
+    if (threadIdx.x == 0) smax = 0;
+    const int k = blockIdx.y;
+    const int32_t *rp = mats[k].rp, *ci = mats[k].ci;
+    const int64_t nz = nnz[k];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && (rp[0] != 0 || (int64_t)rp[n] != nz)) atomicCAS(flag, 0, SAM_ERR_BAD_CSR);
+    int len = -1;
+    if (i < n) {
+        bool sym = asym != nullptr;
+        len = check_row(n, rp, ci, nz, i, flag, sym);
+        if (asym && len >= 0 && !sym) asym[k] = 1;
+    }
+    if (maxrow) {  // the same for every thread of the launch
+        __syncthreads();
+        if (len > 0) atomicMax(&smax, len);
+        __syncthreads();
+        if (threadIdx.x == 0 && smax > 0) atomicMax(&maxrow[k], smax);
+    }
 }
 
 __global__ void concat_rows_kernel(int K, int n, const CsrPtrs *mats, const int64_t *nnz_off, int32_t *rp) {
@@ -219,9 +239,9 @@ __global__ void concat_entries_kernel(int n, const CsrPtrs *mats, const int64_t 
 }  // namespace
 
 cudaError_t validate_csr_batch(sam_handle h, int K, int n, const CsrPtrs *mats, const int64_t *nnz, int32_t *flag,
-                               int32_t *asym) {
+                               int32_t *asym, int32_t *maxrow) {
     dim3 grid((unsigned)((n + 1 + 255) / 256), (unsigned)K);
-    validate_batch_kernel<<<grid, 256, 0, handle_stream(h)>>>(n, mats, nnz, flag, asym);
+    validate_batch_kernel<<<grid, 256, 0, handle_stream(h)>>>(n, mats, nnz, flag, asym, maxrow);
     count_launch(h);
     return cudaGetLastError();
 }
@@ -953,8 +973,12 @@ __global__ void bin_offsets_kernel(const int32_t *counts, int32_t *off, int32_t 
 
 }  // namespace
 
+// a known bound sizes the candidate buffer only up to 2^28 entries (1 GiB);
+// past that the exact total is read back
+constexpr int64_t kCandidateBoundCap = int64_t(1) << 28;
+
 sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t *kri, int64_t nnz, int level,
-                         int32_t **jcp_out, int32_t **jri_out, int64_t *nnz_out) {
+                         int32_t **jcp_out, int32_t **jri_out, int64_t *nnz_out, int maxcol) {
     cudaStream_t st = handle_stream(h);
     int32_t *flag = handle_flag(h);
     const int blocks = (N + 255) / 256 > 0 ? (N + 255) / 256 : 1;
@@ -981,9 +1005,17 @@ sam_status level_pattern(sam_handle h, int N, const int32_t *kcp, const int32_t 
         candidate_count_kernel<<<blocks, 256, 0, st>>>(N, l1cp, curcp, curri, cand);
         count_launch(h);
         if (exclusive_scan_i64(h, cand, coff, N) != cudaSuccess) return SAM_ERR_CUDA;
-        int64_t ctot = 0;
-        if (cudaMemcpyAsync(&ctot, coff + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
+        // candidates of column j: sum over l in the previous pattern's column j
+        // of |L1(l)| <= maxcol + 1, so in all at most (entries of the previous
+        // pattern) (maxcol + 1); entries: nnz + N for level 1, tot after that
+        int64_t ctot = -1;
+        if (maxcol >= 0) {
+            const int64_t prev = tot >= 0 ? (int64_t)tot : nnz + N;
+            const int64_t bound = prev * ((int64_t)maxcol + 1);
+            if (bound <= kCandidateBoundCap) ctot = bound;
+        }
+        if (ctot < 0 && (cudaMemcpyAsync(&ctot, coff + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                         cudaStreamSynchronize(st) != cudaSuccess))
             return SAM_ERR_CUDA;
         int32_t *pad = (int32_t *)pool_alloc(h, sizeof(int32_t) * ((size_t)ctot + 1));
         if (!pad) return SAM_ERR_OOM;
