@@ -1,0 +1,44 @@
+"""The column sizes behind the benchmark's roofline figures.
+
+bench.py derives |J_j| (pattern), |I_j| (shadow rows) and nnz(B_j) (stored
+entries of A_k(I_j, J_j)) from sparse matrix products; here they are checked
+against the oracle's explicit pattern and shadow sets, and the algorithmic
+FP32 flop count against the closed form of Householder QR + Q^T c + back
+solve + correction solves for a dense column problem."""
+import numpy as np
+import pytest
+
+import bench
+import oracle
+from paper_2406_17656_gb300 import workloads as W
+
+CASES = {"q1_20_L2": (lambda: W.config2(nx=20, nmat=2).mats[1], 2),
+         "poisson5_16_L3": (lambda: W.config1(nx=16).mats[1], 3),
+         "fem_12_L2": (lambda: W.config4(ncell=12, nmat=2, flip_frac=0.3).mats[1], 2),
+         "upwind_6_L1": (lambda: W.config3(nx=6, nmat=2).mats[1], 1)}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_column_sizes_match_the_oracle_sets(case):
+    make, level = CASES[case]
+    A = make()
+    I, J, nB = bench.column_sizes([A], level)[0]
+    cp, ri = oracle.pattern(A, level)
+    icp, iri = oracle.shadow(A, cp, ri)
+    assert np.array_equal(J, np.diff(cp))
+    assert np.array_equal(I, np.diff(icp))
+    # nnz(B_j): stored entries of A in the rows I_j and the columns J_j
+    csc = A.to_scipy().tocsc()
+    want = np.array([sum(csc.indptr[c + 1] - csc.indptr[c] for c in ri[cp[j]:cp[j + 1]]) for j in range(A.n)])
+    assert np.array_equal(nB, want)
+
+
+def test_algorithmic_flops_closed_form():
+    I, J, nB = np.array([49, 10]), np.array([25, 4]), np.array([222, 30])
+    f32, f64 = bench.algorithmic_flops(I, J, nB, "fp32r", 1)
+    m, n = I.astype(float), J.astype(float)
+    qr = 2 * n * n * (m - n / 3) + 4 * m * n - 2 * n * n + n * n
+    assert np.allclose(f32, qr + (4 * m * n - n * n))
+    assert np.allclose(f64, 2 * nB + m)
+    f32_0, f64_0 = bench.algorithmic_flops(I, J, nB, "fp64", 0)
+    assert np.allclose(f64_0, qr) and np.allclose(f32_0, 0)
