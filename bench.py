@@ -31,15 +31,48 @@ sys.path.insert(0, HERE)
 
 METRIC = "SAM columns/s (batched FP32+refine vs FP64, same GB300, <=1e-10 rel err); % roofline"
 UNIT = "columns/s"
-# size classes of the least-squares kernels: |I| <= maxi, |J| <= maxj, nnz(B) <= 8 maxi
-BIN_MAXI = [14, 26, 40, 52, 64]
-BIN_MAXJ = [5, 9, 23, 27, 27]
-# nominal ALU peaks of a GB300 at its maximum SM clock (2070 MHz), 152 SMs:
-# FP32: 128 lanes x 2 flops per SM per clock; FP64: 1.25 TFLOP/s nominal
-# (= 2 FMA per SM per clock)
-SM_COUNT, SM_MHZ = 152, 2070.0
-PEAK_FP32 = SM_COUNT * 128 * 2 * SM_MHZ * 1e6
-PEAK_FP64 = SM_COUNT * 2 * 2 * SM_MHZ * 1e6
+
+
+def alu_peaks(sms: int, mhz: float):
+    """Nominal ALU peaks (FLOP/s) of a Blackwell GPU with `sms` SMs at `mhz`:
+    FP32 128 lanes x 2 flops per SM per clock; FP64 2 FMA per SM per clock
+    (GB300: 1.25 TFLOP/s nominal at 152 SMs and 2070 MHz)."""
+    return sms * 128 * 2 * mhz * 1e6, sms * 2 * 2 * mhz * 1e6
+
+
+# ALU peaks of the GPU the benchmark runs on (set by set_peaks from its SM
+# count and maximum SM clock)
+PEAK_FP32 = PEAK_FP64 = None
+PEAK_SOURCE = ""
+
+
+def max_sm_mhz(index: int) -> float:
+    """Maximum SM clock of GPU `index` from nvidia-smi, else the driver's
+    measured record, else GB300's 2070 MHz."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        return float(out.stdout.strip().splitlines()[0])
+    except Exception:
+        pass
+    try:
+        return float(json.load(open(os.path.join(HERE, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except Exception:
+        return 2070.0
+
+
+def set_peaks(sms: int, mhz: float):
+    global PEAK_FP32, PEAK_FP64, PEAK_SOURCE
+    PEAK_FP32, PEAK_FP64 = alu_peaks(sms, mhz)
+    PEAK_SOURCE = ("nominal: %d SMs x %.0f MHz (device properties, nvidia-smi); FP32 128 lanes x 2, "
+                   "FP64 2 FMA per SM per clock" % (sms, mhz))
+
+
+def size_classes():
+    """The least-squares kernels' size classes, as the library reports them."""
+    from paper_2406_17656_gb300 import sam
+
+    return sam.size_classes()
 
 
 def parse():
@@ -124,10 +157,14 @@ def column_sizes(mats, level):
     return out
 
 
-def bin_of(I, J, nB):
+def bin_of(I, J, nB, classes=None):
+    """Size class of every column (the library's rule: the first class the
+    column fits), -1 where none fits."""
+    c = classes or size_classes()
     b = np.full(I.shape, -1)
-    for q in range(len(BIN_MAXI) - 1, -1, -1):
-        ok = (I <= BIN_MAXI[q]) & (J <= BIN_MAXJ[q]) & (nB <= 8 * BIN_MAXI[q]) & (I >= J)
+    for q in range(len(c["max_rows"]) - 1, -1, -1):
+        ok = ((I <= c["max_rows"][q]) & (J <= c["max_cols"][q]) & (nB <= c["max_entries"][q]) &
+              (I * (J + 1) <= c["max_tile"][q]) & (I >= J))
         b[ok] = q
     return b
 
@@ -691,6 +728,7 @@ def main():
         dist.barrier()
     sam.load()
     dev = torch.device("cuda", torch.cuda.current_device())
+    set_peaks(torch.cuda.get_device_properties(dev).multi_processor_count, max_sm_mhz(local))
     if args.profile_fem > 0:
         h = sam.Handle(stream=torch.cuda.current_stream())
         profile_fem(h, sam, torch, dev, args.profile_fem, args.fem_maps)
@@ -783,7 +821,7 @@ def main():
         return max_over_ranks(ms, world, dev) / nsteps, fro, prof, (offs, out)
 
     # ---- one-time tuning of the FP32 tile shapes on this workload (untimed)
-    variants = [0] * 5
+    variants = [0] * sam.SAM_NUM_SIZE_CLASSES
     if not args.no_tune:
         pats = h.sam_pattern_build_batched(aks, args.level)
         variants = h.sam_tune(aks, a0, pats, "fp32r", args.refine)
@@ -912,10 +950,11 @@ def main():
 
     # ---- roofline of the dominant kernel (largest least-squares size class)
     sizes = column_sizes(seq.mats, args.level)
+    classes = size_classes()
     dom = int(np.argmax(lsq_ms))
     f32 = f64 = gathered = 0.0
     for (I, J, nB) in sizes:
-        sel = bin_of(I, J, nB) == dom
+        sel = bin_of(I, J, nB, classes) == dom
         a, b = algorithmic_flops(I[sel], J[sel], nB[sel], "fp32r", args.refine)
         f32 += float(np.sum(a))
         f64 += float(np.sum(b))
@@ -947,17 +986,18 @@ def main():
             if (rec.get("kernel_sha256") == kernel_hash() and str(dom) in rec.get("bytes_per_column", {})
                     and rec.get("variant", {}).get(str(dom), 0) == variants[dom]):
                 # traffic per column from the capture, times this launch's columns
-                ncols = sum(int(np.sum(bin_of(I, J, nB) == dom)) for (I, J, nB) in sizes)
+                ncols = sum(int(np.sum(bin_of(I, J, nB, classes) == dom)) for (I, J, nB) in sizes)
                 traffic = rec["bytes_per_column"][str(dom)] * ncols
         except Exception:
             traffic = None
     roofline = {"bound": bound, "achieved": ach / 1e12, "peak": peak / 1e12, "unit": unit,
                 "frac": t_roof / t_launch, "traffic": traffic,
-                "kernel": "lsq_kernel size class %d (|I|<=%d, |J|<=%d)" % (dom, BIN_MAXI[dom], BIN_MAXJ[dom]),
+                "kernel": "lsq_kernel size class %d (|I|<=%d, |J|<=%d)" % (dom, classes["max_rows"][dom],
+                                                                           classes["max_cols"][dom]),
                 "launch_ms": t_launch * 1e3, "fp32_flops_per_launch": f32_l, "fp64_flops_per_launch": f64_l,
                 "fp32_frac": fp32_frac, "fp64_frac": fp64_frac,
                 "gathered_bytes_per_launch": gathered, "t_hbm_ms": t_hbm * 1e3, "hbm_gbs_measured": hbm_gbs,
-                "peak_source": "nominal: 152 SMs x 2070 MHz; FP32 128 lanes x 2, FP64 1.25 TFLOP/s (2 FMA/SM/clk)"}
+                "peak_source": PEAK_SOURCE}
     if not args.quick:
         p32, p64 = h.sam_peak_flops(100.0)
         roofline["probe_fp32_tflops"] = p32 / 1e12

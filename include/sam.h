@@ -78,6 +78,14 @@ enum {
  * its columns misses.  After step 2 the predicted error |d_2|^2 / |d_1|
  * (|d_2| alone when the correction grew) above 1e-10 |m| sends the column
  * to the FP64 kernel.  sam_refine_stats counts the outcomes.
+ *
+ * A fixed number of steps s >= 1 is guarded the same way: after the last
+ * step the predicted error rho |d_s| is compared with 1e-10 |m|, where
+ * rho = |d_s| / |d_{s-1}| for s >= 2 and, for s = 1, the larger of
+ * 4 |d_1| / |m| and u_32 kappa^2 with kappa estimated as
+ * max |R_kk| / min |R_kk|; columns above it are re-solved by the FP64
+ * kernel (their values are then those of the plain FP64 build).  s = 0 (the
+ * FP32 solve alone, about 1e-5 relative) is not guarded.
  */
 #define SAM_REFINE_AUTO (-1)
 
@@ -100,8 +108,28 @@ typedef struct sam_pattern_t *sam_pattern; /* a map sparsity pattern S (device r
 typedef struct sam_plan_t *sam_plan;       /* a captured numeric rebuild (sam_plan_create) */
 
 /* Largest column sizes the least-squares kernels accept:
- * |J_j| <= *max_cols and |I_j| <= *max_rows. */
+ * |J_j| <= *max_cols and |I_j| <= *max_rows (the large class's limits; it
+ * also needs |I_j| (|J_j| + 1) <= 23552 and nnz(B_j) <= 16384). */
 void sam_limits(int32_t *max_rows, int32_t *max_cols);
+
+/*
+ * Size classes of the column problems (the batching of Sec. 2's column
+ * solves by their uneven sizes; no counterpart in the paper).  A column
+ * with |I_j| >= |J_j| shadow rows, |J_j| unknowns and nnz(B_j) stored
+ * entries goes to the first class b with |I_j| <= max_rows[b],
+ * |J_j| <= max_cols[b], nnz(B_j) <= max_entries[b] and
+ * |I_j| (|J_j| + 1) <= max_tile[b]; a column that fits none is
+ * SAM_ERR_UNSUPPORTED.  Classes 0..4 are register tiles with
+ * FP32 or FP64 arithmetic; class 5 (SAM_NUM_SIZE_CLASSES - 1) is one thread
+ * block per column with an FP64 tile in shared memory, whatever the
+ * precision asked for, and no adjoint (sam_build_backward reports its
+ * columns as SAM_ERR_UNSUPPORTED).  variants[b]: tile shapes of class b
+ * (sam_tune, sam_set_tile_variants).  count must be SAM_NUM_SIZE_CLASSES;
+ * any output may be NULL.
+ */
+#define SAM_NUM_SIZE_CLASSES 6
+sam_status sam_size_classes(int32_t *max_rows, int32_t *max_cols, int32_t *max_entries, int32_t *max_tile,
+                            int32_t *variants, int count);
 
 /* Human-readable text of a status code (static storage). */
 const char *sam_status_string(sam_status s);
@@ -285,6 +313,18 @@ sam_status sam_residual(sam_handle h, const sam_csr *A_k, const sam_csr *M_k, co
 sam_status sam_apply(sam_handle h, const sam_csr *M_k, const double *x, double *y);
 
 /*
+ * sam_apply_grad -- the gradient of a loss through y = M_k x with respect to
+ * the stored values of M_k: dM_val[e] = dy[i] x[c] for every stored entry
+ * e = (i, c) of M_k (CSR order), given dy = dL/dy.  With sam_apply it makes
+ * a loss term such as ||M_k v||^2 differentiable in the map values, as in
+ * the sensitivity studies of the map (the paper builds the map for use in
+ * M_k (P_0 v), Sec. 1-2).  Only the structure of M_k is read (M_k->val may
+ * be NULL).  x[n], dy[n], dM_val[nnz(M_k)] device or host.  Errors:
+ * SAM_ERR_INVALID_ARG, SAM_ERR_BAD_CSR.
+ */
+sam_status sam_apply_grad(sam_handle h, const sam_csr *M_k, const double *x, const double *dy, double *dM_val);
+
+/*
  * sam_gmres -- restarted GMRES(restart) for A x = b with the right
  * preconditioner z = M (P_0 v), the use of a map stated in Sec. 1-2: P_0 is
  * a preconditioner built once for A_0, M = M_k the map of A_k, so that
@@ -403,18 +443,21 @@ sam_status sam_tune(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0,
 
 /*
  * sam_set_tile_variants / sam_get_tile_variants -- set or read the tile
- * variant per size class (count must be 5; variant 0 for every class is the
- * default of a new handle; class 0 has only variant 0).  Set: returns
+ * variant per size class (count must be SAM_NUM_SIZE_CLASSES; variant 0 for
+ * every class is the default of a new handle; classes 0 and 5 have only
+ * variant 0).  Set: returns
  * SAM_ERR_INVALID_ARG, changing nothing, if a value is out of range.
  */
 sam_status sam_set_tile_variants(sam_handle h, const int *variants, int count);
 sam_status sam_get_tile_variants(sam_handle h, int *variants, int count);
 
 /*
- * sam_refine_stats -- outcome counts of the last build on this handle that
- * ran with refine_steps = SAM_REFINE_AUTO: counts[0] columns that stopped
- * after one step, counts[1] after two, counts[2] re-solved in FP64 (count
- * must be 3).  Synchronises the handle's stream.
+ * sam_refine_stats -- outcome counts of the last guarded SAM_FP32_REFINE
+ * build on this handle (refine_steps = SAM_REFINE_AUTO or >= 1):
+ * counts[0] columns that kept their solution after one step, counts[1]
+ * after two or more, counts[2] solved in FP64 (re-solved after missing the
+ * target, or in the large size class) (count must be 3).
+ * Synchronises the handle's stream.
  */
 sam_status sam_refine_stats(sam_handle h, int64_t *counts, int count);
 
@@ -423,8 +466,9 @@ sam_status sam_refine_stats(sam_handle h, int64_t *counts, int count);
  * launch (one per size class and build call) with CUDA events recorded on
  * the handle's stream; any call resets the counters.
  * sam_profile_read -- launches: kernels this handle launched since the last
- * reset; lsq_ms[5] / lsq_launches[5] (nullable): accumulated event time and
- * launch count of the least-squares kernel of each size class.  Synchronises.
+ * reset; lsq_ms / lsq_launches (nullable, SAM_NUM_SIZE_CLASSES entries):
+ * accumulated event time and launch count of the least-squares kernel of
+ * each size class.  Synchronises.
  */
 sam_status sam_profile(sam_handle h, int enable);
 sam_status sam_profile_read(sam_handle h, int64_t *launches, double *lsq_ms, int64_t *lsq_launches);
@@ -454,16 +498,21 @@ sam_status sam_peak_flops(sam_handle h, double ms, double *fp32_flops, double *f
  * exits.
  *
  * Arguments: cuda_stream (a cudaStream_t, NULL for the legacy stream); A_k,
- * M_k, A_0 square CSR matrices of the same order n <= SAM_STATIC_MAX_ROWS;
+ * M_k, A_0 square CSR matrices of the same order n, 1 <= n <=
+ * SAM_STATIC_MAX_ROWS (n = 0 is SAM_ERR_INVALID_ARG, as for every call);
  * out (device, 2 doubles) receives ||R||_F and ||R||_F / ||A_0||_F; status
  * (device, nullable) receives 0 or a sam_status detected on the device
  * (SAM_ERR_BAD_CSR for a malformed structure, SAM_ERR_UNSUPPORTED for a row
- * of R with more than 1024 candidate entries), in which case out holds zeros.
- * Every array must be device or managed memory: host arrays are rejected
+ * of R with more than 1024 candidate entries), in which case both outputs
+ * are NaN.  Every array must be device memory of the current device, or
+ * managed memory: host arrays and arrays of another device are rejected
  * (SAM_ERR_INVALID_ARG), as are orders above SAM_STATIC_MAX_ROWS.
- * The call is asynchronous on cuda_stream.  Its first call on a device looks
- * up the workspace's device address (cudaGetSymbolAddress) and caches it;
- * make that first call before capturing the stream into a CUDA graph.
+ * The call is asynchronous on cuda_stream.  It looks up the workspace's
+ * device address (cudaGetSymbolAddress, which allocates nothing) on every
+ * call made while cuda_stream is not being captured, and reuses the
+ * address found last on that device while it is; so make the first call
+ * on a device before capturing a stream into a CUDA graph (a first call
+ * under capture returns SAM_ERR_CUDA).
  * Every call reuses the same workspace and clears what must start at zero,
  * so a call never depends on an earlier one; calls whose work overlaps on
  * the GPU (other streams or host threads) race on the workspace and must be

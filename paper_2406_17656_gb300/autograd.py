@@ -66,6 +66,26 @@ class _ResidualSqFn(torch.autograd.Function):
         return dak, da0, dmres, None
 
 
+class _ApplyFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, m_val, v, owner):
+        if owner.indptr is None:
+            raise RuntimeError("build the map (call the SamMap) before applying it")
+        m = _sam.Csr(owner.indptr, owner.indices, m_val.detach().contiguous(), n=owner.n)
+        vv = v.detach().contiguous()
+        y = owner.handle.sam_apply(m, vv)
+        ctx.owner = owner
+        ctx.save_for_backward(vv)
+        return y
+
+    @staticmethod
+    def backward(ctx, dy):
+        owner = ctx.owner
+        (vv,) = ctx.saved_tensors
+        m = _sam.Csr(owner.indptr, owner.indices, None, n=owner.n)
+        return owner.handle.sam_apply_grad(m, vv, dy.contiguous()), None, None
+
+
 class SamMap:
     """Differentiable SAM on a fixed pattern.
 
@@ -89,8 +109,6 @@ class SamMap:
         return _ResidualSqFn.apply(ak_val, a0_val, m_val, self)
 
     def matvec(self, m_val, v):
-        """M v as a differentiable function of the map values (plain torch ops)."""
-        rows = torch.repeat_interleave(torch.arange(self.n, device=m_val.device),
-                                       (self.indptr[1:] - self.indptr[:-1]).long())
-        return torch.zeros(self.n, dtype=m_val.dtype, device=m_val.device).index_add_(
-            0, rows, m_val * v[self.indices.long()])
+        """M v as a differentiable function of the map values (sam_apply
+        forward, sam_apply_grad backward; v is a constant)."""
+        return _ApplyFn.apply(m_val, v, self)

@@ -40,8 +40,10 @@ struct sam_handle_t {
     int64_t lsq_n[sam::kNumBins] = {0};
     // FP32 tile shape per size class (sam_tune / sam_set_tile_variants)
     int variant[sam::kNumBins] = {0};
-    // automatic refinement: columns of the last such build per outcome
+    // refinement outcomes of the last guarded build (automatic, or a fixed
+    // number of steps >= 1): columns per outcome, and a pinned mirror
     int64_t *d_refine = nullptr;
+    int64_t *h_refine = nullptr;
 };
 
 namespace {
@@ -857,8 +859,14 @@ bool tune_lookup(const char *path, const std::string &key, int *v) {
         const size_t kl = key.size();
         if (strncmp(line, key.c_str(), kl) != 0 || line[kl] != ' ') continue;
         int t[kNumBins];
-        if (sscanf(line + kl, "%d %d %d %d %d", &t[0], &t[1], &t[2], &t[3], &t[4]) != kNumBins) continue;
+        const char *q = line + kl;
         bool ok = true;
+        for (int b = 0; b < kNumBins && ok; ++b) {
+            int used = 0;
+            ok = sscanf(q, "%d%n", &t[b], &used) == 1;
+            q += used;
+        }
+        if (!ok) continue;
         for (int b = 0; b < kNumBins; ++b) ok = ok && t[b] >= 0 && t[b] < kTileVariants[b];
         if (!ok) continue;
         for (int b = 0; b < kNumBins; ++b) v[b] = t[b];
@@ -872,8 +880,24 @@ bool tune_lookup(const char *path, const std::string &key, int *v) {
 extern "C" {
 
 void sam_limits(int32_t *max_rows, int32_t *max_cols) {
-    if (max_rows) *max_rows = kICap;
-    if (max_cols) *max_cols = kJCap;
+    if (max_rows) *max_rows = kBigICap;
+    if (max_cols) *max_cols = kBigJCap;
+}
+
+sam_status sam_size_classes(int32_t *max_rows, int32_t *max_cols, int32_t *max_entries, int32_t *max_tile,
+                            int32_t *variants, int count) {
+    // the register tiles' capacities (lsq.cu, the shadow kernel's table) and the large class
+    static const int32_t rows[kNumBins] = {14, 26, 40, 52, 64, kBigICap};
+    static const int32_t cols[kNumBins] = {5, 9, 23, 27, 27, kBigJCap};
+    if (count != kNumBins) return SAM_ERR_INVALID_ARG;
+    for (int b = 0; b < kNumBins; ++b) {
+        if (max_rows) max_rows[b] = rows[b];
+        if (max_cols) max_cols[b] = cols[b];
+        if (max_entries) max_entries[b] = b == kBinBig ? kBigLCap : 8 * rows[b];
+        if (max_tile) max_tile[b] = b == kBinBig ? kBigTileDoubles : rows[b] * (cols[b] + 1);
+        if (variants) variants[b] = kTileVariants[b];
+    }
+    return SAM_OK;
 }
 
 const char *sam_status_string(sam_status s) {
@@ -915,10 +939,12 @@ sam_status sam_create(sam_handle *out, void *cuda_stream) {
     cudaMemPoolSetAttribute(h->pool, cudaMemPoolAttrReleaseThreshold, &thr);
     if (cudaMalloc(&h->d_flag, sizeof(int32_t)) != cudaSuccess ||
         cudaMalloc(&h->d_refine, sizeof(int64_t) * (kAutoSteps + 1)) != cudaSuccess ||
-        cudaMallocHost(&h->h_flag, sizeof(int32_t) * (2 + kNumBins)) != cudaSuccess) {
+        cudaMallocHost(&h->h_flag, sizeof(int32_t) * (2 + kNumBins)) != cudaSuccess ||
+        cudaMallocHost(&h->h_refine, sizeof(int64_t) * (kAutoSteps + 1)) != cudaSuccess) {
         cudaGetLastError();
         if (h->d_flag) cudaFree(h->d_flag);
         if (h->d_refine) cudaFree(h->d_refine);
+        if (h->h_flag) cudaFreeHost(h->h_flag);
         cudaMemPoolDestroy(h->pool);
         delete h;
         return SAM_ERR_OOM;
@@ -939,6 +965,7 @@ sam_status sam_destroy(sam_handle h) {
     cudaFree(h->d_flag);
     cudaFree(h->d_refine);
     cudaFreeHost(h->h_flag);
+    cudaFreeHost(h->h_refine);
     cudaMemPoolDestroy(h->pool);
     delete h;
     return SAM_OK;
@@ -1375,7 +1402,10 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     // while the next chunk is solved (one structure only, where every map has
     // the same columns per class; the automatic mode re-solves columns after
     // all chunks and is left whole)
+    // automatic refinement, or a fixed number of steps >= 1: columns that
+    // miss the accuracy target are re-solved in FP64 after the solves
     const bool autoref = precision == SAM_FP32_REFINE && refine_steps < 0;
+    const bool guarded = precision == SAM_FP32_REFINE && refine_steps != 0;
     const MapChunks chunks = plan_chunks(K, n, shared && !autoref && sg.is_host_output(d_v));
     const bool chunked = chunks.count > 1;
     cudaEvent_t ev_bins = nullptr;
@@ -1445,7 +1475,7 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     a.refine_steps = refine_steps;
     uint8_t *bin2 = nullptr;
     int32_t *work2 = nullptr, *bin_off2 = nullptr;
-    if (autoref) {
+    if (guarded) {
         a.refine_used = sc.get<uint8_t>((size_t)N);
         bin2 = sc.get<uint8_t>((size_t)N);
         work2 = sc.get<int32_t>((size_t)N);
@@ -1481,8 +1511,22 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
                 return SAM_ERR_CUDA;
         }
     }
-    if (autoref && launch_refine_fallback(h, a, (int)N, bin, bin2, work2, bin_off2, nullptr, h->d_refine) != cudaSuccess)
+    if (guarded && launch_refine_fallback(h, a, (int)N, bin, bin2, work2, bin_off2, nullptr, h->d_refine) != cudaSuccess)
         return SAM_ERR_CUDA;
+    // chunked host values were copied before the re-solves: their count comes
+    // back with the final synchronisation, and re-solved columns are copied again
+    if (chunked && guarded &&
+        cudaMemcpyAsync(h->h_refine, h->d_refine, sizeof(int64_t) * (kAutoSteps + 1), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess)
+        return SAM_ERR_CUDA;
+    auto recopy_values = [&]() -> sam_status {
+        if (!(chunked && guarded) || h->h_refine[kAutoSteps] == 0) return SAM_OK;
+        if (cudaMemcpyAsync(M_val, d_v, sizeof(double) * (size_t)total_nnz, cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return SAM_ERR_CUDA;
+        return SAM_OK;
+    };
     if (status_reduce(h, d_st, N, h->d_flag) != cudaSuccess) return SAM_ERR_CUDA;
     double *fro_dev = nullptr;
     if (fro) {
@@ -1497,9 +1541,14 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
             return SAM_ERR_CUDA;
         s = drain_status(h);
         for (int k = 0; k < K; ++k) fro[k] = sqrt(f2[k]);
-        return s;
+        const sam_status r = recopy_values();
+        return s != SAM_OK ? s : r;
     }
-    if (sg.has_host_outputs()) return drain_status(h);
+    if (sg.has_host_outputs()) {
+        s = drain_status(h);
+        const sam_status r = recopy_values();
+        return s != SAM_OK ? s : r;
+    }
     return cudaGetLastError() == cudaSuccess ? SAM_OK : SAM_ERR_CUDA;
 }
 
@@ -1695,6 +1744,24 @@ sam_status sam_apply(sam_handle h, const sam_csr *M_k, const double *x, double *
     sam_status s = validate_all(h, sc, {m});
     if (s != SAM_OK) return s;
     if (csr_spmv(h, n, m.rp, m.ci, m.v, dx, dy) != cudaSuccess) return SAM_ERR_CUDA;
+    if (sg.finish() != cudaSuccess) return SAM_ERR_CUDA;
+    if (sg.has_host_outputs()) return drain_status(h);
+    return SAM_OK;
+}
+
+sam_status sam_apply_grad(sam_handle h, const sam_csr *M_k, const double *x, const double *dy, double *dM_val) {
+    if (!h || check_csr_arg(M_k, false) || !x || !dy || !dM_val) return SAM_ERR_INVALID_ARG;
+    const int n = M_k->n;
+    Scratch sc(h);
+    Stager sg(sc, h->stream);
+    DevCsr m = stage_csr(sg, M_k, false);
+    const double *dx = sg.in(x, (size_t)n);
+    const double *ddy = sg.in(dy, (size_t)n);
+    double *dg = sg.out(dM_val, (size_t)M_k->nnz);
+    if (sg.failed) return SAM_ERR_OOM;
+    sam_status s = validate_all(h, sc, {m});
+    if (s != SAM_OK) return s;
+    if (csr_outer_on_pattern(h, n, m.rp, m.ci, ddy, dx, dg) != cudaSuccess) return SAM_ERR_CUDA;
     if (sg.finish() != cudaSuccess) return SAM_ERR_CUDA;
     if (sg.has_host_outputs()) return drain_status(h);
     return SAM_OK;
@@ -2082,7 +2149,9 @@ sam_status sam_tune(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0,
     if (cache_path) {
         FILE *f = fopen(cache_path, "a");
         if (!f) return SAM_ERR_INVALID_ARG;
-        fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), chosen[0], chosen[1], chosen[2], chosen[3], chosen[4]);
+        fprintf(f, "%s", key.c_str());
+        for (int b = 0; b < kNumBins; ++b) fprintf(f, " %d", chosen[b]);
+        fprintf(f, "\n");
         fclose(f);
     }
     return SAM_OK;
@@ -2230,7 +2299,9 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
         zcv32 = keep.get<float>((size_t)zn);
     }
     double *seg_work = fro2 ? keep.get<double>(segmented_sum_workspace(K)) : nullptr;
-    const bool autoref = precision == SAM_FP32_REFINE && refine_steps < 0;
+    // automatic refinement or a fixed number of steps >= 1: the FP64
+    // re-solve of the columns that miss the accuracy target is captured too
+    const bool autoref = precision == SAM_FP32_REFINE && refine_steps != 0;
     uint8_t *refine_used = autoref ? keep.get<uint8_t>((size_t)N) : nullptr;
     uint8_t *bin_keep = autoref ? keep.get<uint8_t>((size_t)N) : nullptr;
     uint8_t *bin2 = autoref ? keep.get<uint8_t>((size_t)N) : nullptr;

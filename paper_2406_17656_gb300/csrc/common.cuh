@@ -20,11 +20,19 @@
 
 namespace sam {
 
-// Hard limits of the least-squares kernels.
+// Limits of the register-tile least-squares kernels (size classes 0..4).
 constexpr int kICap = 64;    // max |I_j| (shadow rows) of one column problem
 constexpr int kJCap = 27;    // max |J_j| (unknowns) of one column problem
-constexpr int kNumBins = 5;  // size classes (see lsq.cu)
+constexpr int kRegBins = 5;  // register-tile size classes (see lsq.cu)
 constexpr int kLCap = 512;   // max stored entries of one column's B (8 per shadow row)
+// The large class (lsq_big.cu): one thread block per column, [B c] as a
+// dense FP64 tile in shared memory.
+constexpr int kBinBig = kRegBins;  // its size-class index
+constexpr int kNumBins = kRegBins + 1;
+constexpr int kBigJCap = 128;                  // max |J_j|
+constexpr int kBigICap = 1024;                 // max |I_j|
+constexpr int kBigLCap = 16384;                // max stored entries of B_j
+constexpr int kBigTileDoubles = 23 * 1024;     // max |I_j| (|J_j| + 1) (184 KB)
 constexpr int kZCap = 32;    // target entries per column with a precomputed local row (zloc)
 constexpr int kZOutside = 255;  // zloc value of a target entry outside the shadow rows
 constexpr int kBinNone = 255;
@@ -41,6 +49,7 @@ constexpr int kStRefine = 100;
 // automatic refinement (refine_steps = SAM_REFINE_AUTO)
 constexpr int kAutoSteps = 2;
 constexpr double kAutoC = 4.0, kAutoTol = 1e-12, kFallbackTol = 1e-10;
+constexpr double kU32 = 5.9604644775390625e-8;  // unit roundoff of FP32, 2^-24
 
 // Source CSR of one map (device pointers) for the batch concatenation.
 struct CsrPtrs {
@@ -117,7 +126,7 @@ void profile_end(sam_handle h, int bin);
 // warp where the tile allows, 1: the alternative shape)
 int handle_variant(sam_handle h, int bin);
 // number of FP32 tile shapes per size class
-constexpr int kTileVariants[kNumBins] = {1, 2, 2, 2, 2};
+constexpr int kTileVariants[kNumBins] = {1, 2, 2, 2, 2, 1};
 
 // out[0..n] = exclusive scan of in[0..n), out[n] = total
 cudaError_t exclusive_scan_i32(sam_handle h, const int32_t *in, int32_t *out, int64_t n);
@@ -182,6 +191,8 @@ cudaError_t launch_refine_fallback(sam_handle h, const LsqArgs &args, int N, con
 
 // Least-squares launches for every size class.
 cudaError_t launch_lsq(sam_handle h, int precision, const LsqArgs &args);
+// the large class (any precision: solved in FP64)
+cudaError_t launch_lsq_big(sam_handle h, const LsqArgs &args, int bin);
 // one size class (the items args.item_lo/item_hi select, else all of it)
 cudaError_t launch_lsq_bin(sam_handle h, int precision, const LsqArgs &args, int bin);
 cudaError_t launch_adjoint(sam_handle h, int precision, const LsqArgs &args);
@@ -228,6 +239,9 @@ cudaError_t gather_values(sam_handle h, int64_t tot, int K, const int64_t *off, 
 cudaError_t sum_f64(sam_handle h, const double *x, int64_t n, double *out_dev, bool squares);
 cudaError_t csr_spmv(sam_handle h, int n, const int32_t *rp, const int32_t *ci, const double *v, const double *x,
                      double *y);
+// g[e] = dy[i] x[c] for every stored entry e = (i, c) of the CSR structure
+cudaError_t csr_outer_on_pattern(sam_handle h, int n, const int32_t *rp, const int32_t *ci, const double *dy,
+                                 const double *x, double *g);
 cudaError_t residual_rows(sam_handle h, int n, const int32_t *krp, const int32_t *kci, const double *kv,
                           const int32_t *mrp, const int32_t *mci, const double *mv, const int32_t *zrp,
                           const int32_t *zci, const double *zv, double *row_r2, int32_t *flag);

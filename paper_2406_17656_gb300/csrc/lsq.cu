@@ -145,14 +145,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
                 }
                 __syncwarp();
                 used = step + 1;
+                dsq = group_sum<P>(dsq);
+                msq = group_sum<P>(msq);
                 if (autoref) {
                     // CSNE contracts the error by a factor rho ~ u_32 kappa^2 per step.
                     // After step 1 the error is ~ rho |d_1| with rho <~ kAutoC |d_1| / |m|:
                     // stop when kAutoC |d_1|^2 <= kAutoTol |m|^2.  After step 2,
                     // rho ~ |d_2| / |d_1|; a predicted error |d_2|^2 / |d_1| above
                     // kFallbackTol |m| sends the column to the FP64 solve.
-                    dsq = group_sum<P>(dsq);
-                    msq = group_sum<P>(msq);
                     bool more = false;
                     if (step == 0) {
                         more = kAutoC * dsq > kAutoTol * msq;
@@ -162,6 +162,23 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
                         fallback = dsq * dsq > kFallbackTol * kFallbackTol * msq * fmax(d1sq, dsq);
                     }
                     if (!__any_sync(0xffffffffu, more)) break;  // warp-uniform
+                } else if (step == steps - 1) {
+                    // the same accuracy guard after the last of a fixed number of
+                    // steps: the predicted error rho |d_s| above kFallbackTol |m|
+                    // sends the column to the FP64 solve.  After two or more steps
+                    // rho ~ |d_s| / |d_{s-1}|; after one, rho is the larger of
+                    // kAutoC |d_1| / |m| and u_32 kappa^2, with kappa estimated by
+                    // max |R_kk| / min |R_kk| (a lower bound on kappa(B))
+                    constexpr double kTol2 = kFallbackTol * kFallbackTol;
+                    if (steps >= 2) {
+                        fallback = dsq * dsq > kTol2 * msq * fmax(d1sq, dsq);
+                    } else {
+                        const double k2 = C.rkk_max2 / C.rkk_min2;  // kappa^2
+                        const double u2k4 = kU32 * kU32 * k2 * k2;  // (u_32 kappa^2)^2
+                        fallback = kAutoC * kAutoC * dsq * dsq > kTol2 * msq * msq || u2k4 * dsq > kTol2 * msq;
+                    }
+                } else {
+                    d1sq = dsq;
                 }
             }
             if (used > 0) {
@@ -207,8 +224,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
                 r2 = rf2;
                 need_final = false;
             }
-            if (autoref && C.valid && ll == 0 && args.refine_used)
-                args.refine_used[C.jj] = (uint8_t)((fallback && C.status == kStOk) ? kAutoSteps + 1 : used);
+            if (C.valid && ll == 0 && args.refine_used)
+                args.refine_used[C.jj] =
+                    (uint8_t)((fallback && C.status == kStOk) ? kAutoSteps + 1 : (used < kAutoSteps ? used : kAutoSteps));
         }
         if (need_final) {
             r2 = residual_rows<TL>(S, kcv, nI, ll);
@@ -263,6 +281,7 @@ cudaError_t launch_one(sam_handle h, const LsqArgs &a, int bin) {
 }  // namespace
 
 cudaError_t launch_lsq_bin(sam_handle h, int precision, const LsqArgs &args, int bin) {
+    if (bin == kBinBig) return launch_lsq_big(h, args, bin);
     if (precision == SAM_FP64) {
         switch (bin) {
             case 0: return launch_one<D0, true>(h, args, 0);

@@ -405,6 +405,7 @@ struct Column {
     int status;
     int colA[JQ], clen[JQ], colB[JQ];
     double out2;
+    double rkk_max2, rkk_min2;  // largest and smallest R_kk^2 (factor): a cheap lower bound on kappa(B)^2
 
     __device__ __forceinline__ void begin(const LsqArgs &args, int item, int total, const int32_t *work) {
         begin_at(args, item, total, item < total ? work[item] : 0);
@@ -428,7 +429,11 @@ struct Column {
         // target column: A_0(:, jl) shifted by roff, or column jj of the
         // block-diagonal targets (rows already global)
         const int zc = args.zbig ? jj : jl;
-        zro = args.zbig ? 0 : roff;
+        // shift of the target's row indices into the numbering of the source
+        // rows (and so of the shadow rows): the sources' rows are global, or
+        // map 0's when the shadow data is shared; the target's rows are
+        // A_0's own (one shared target), or global (one target per map)
+        zro = (args.shadow_shared ? 0 : roff) - (args.zbig ? roff : 0);
         jb = nJ = nI = zb = ze = 0;
         if (valid) {
             jb = args.jcp[js];
@@ -635,16 +640,25 @@ struct Column {
             }
         __syncwarp();
         int st = kStOk;
+        double rmax2 = 0.0, rmin2 = DBL_MAX;
         for (int k = ll; k < nJ; k += P) {
             const T rkk = S.u.s.R[k * TL::RSTR + k];
             const double d = to_f64<T>(rkk);
             if (!finite64(d)) st = max(st, (int)kStNonfinite);
             else if (d == 0.0) st = max(st, (int)kStRank);
+            rmax2 = fmax(rmax2, d * d);
+            rmin2 = fmin(rmin2, d * d);
             S.u.s.dinv[k] = T(1) / rkk;
         }
         status = max(status, st);
 #pragma unroll
-        for (int o = 1; o < P; o <<= 1) status = max(status, shfl_xor(status, o));
+        for (int o = 1; o < P; o <<= 1) {
+            status = max(status, shfl_xor(status, o));
+            rmax2 = fmax(rmax2, shfl_xor(rmax2, o));
+            rmin2 = fmin(rmin2, shfl_xor(rmin2, o));
+        }
+        rkk_max2 = rmax2;
+        rkk_min2 = rmin2;
         if (status != kStOk) nJ = 0;
     }
 

@@ -4,6 +4,7 @@
 #include <climits>
 
 #include "common.cuh"
+#include "residual_row.cuh"
 
 namespace sam {
 namespace {
@@ -84,95 +85,33 @@ __global__ void spmv_kernel(int n, const int32_t *rp, const int32_t *ci, const d
     if (lane == 0) y[w] = s;
 }
 
-// Row i of R = A_k M - A_0: products A_k(i, c) M(c, :) and -A_0(i, :) are
-// gathered as (column, value) pairs, sorted by column with a fixed bitonic
-// network, summed per column and squared.
+// g[e] = dy[i] x[c] for every stored entry e = (i, c) of M: the gradient of
+// <dy, M x> with respect to M's values, one warp per row
+__global__ void outer_on_pattern_kernel(int n, const int32_t *rp, const int32_t *ci, const double *dy,
+                                        const double *x, double *g) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n) return;
+    const double d = dy[w];
+    for (int e = rp[w] + lane; e < rp[w + 1]; e += 32) g[e] = d * x[ci[e]];
+}
+
+// Row i of R = A_k M - A_0 into row_r2[i] (residual_row_sq: products
+// gathered as (column, value) pairs, sorted by column, summed and squared).
 constexpr int kResWarps = 2;
-constexpr int kResBuf = 1024;
 
 __global__ void __launch_bounds__(kResWarps * 32) residual_rows_kernel(
     int n, const int32_t *krp, const int32_t *kci, const double *kv, const int32_t *mrp, const int32_t *mci,
     const double *mv, const int32_t *zrp, const int32_t *zci, const double *zv, double *row_r2, int32_t *flag) {
-    __shared__ int keys[kResWarps][kResBuf];
-    __shared__ double vals[kResWarps][kResBuf];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *K = keys[warp];
-    double *V = vals[warp];
+    __shared__ int keys[kResWarps][kResRowBuf];
+    __shared__ double vals[kResWarps][kResRowBuf];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int64_t i = (int64_t)blockIdx.x * kResWarps + warp; i < n; i += (int64_t)gridDim.x * kResWarps) {
-        // count candidates
-        int cnt = zrp[i + 1] - zrp[i];
-        int tot = 0;
-        for (int base = krp[i]; base < krp[i + 1]; base += 32) {
-            int e = base + lane;
-            int len = (e < krp[i + 1]) ? mrp[kci[e] + 1] - mrp[kci[e]] : 0;
-            for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(0xffffffffu, len, o);
-            tot += len;
+        const double r2 = residual_row_sq(i, lane, krp, kci, kv, mrp, mci, mv, zrp, zci, zv, keys[warp], vals[warp]);
+        if (lane == 0) {
+            row_r2[i] = r2 < 0.0 ? 0.0 : r2;
+            if (r2 < 0.0) atomicCAS(flag, 0, SAM_ERR_UNSUPPORTED);
         }
-        cnt += tot;
-        if (cnt > kResBuf) {
-            if (lane == 0) {
-                row_r2[i] = 0.0;
-                atomicCAS(flag, 0, SAM_ERR_UNSUPPORTED);
-            }
-            continue;
-        }
-        // fill: target entries first, then products (fixed order)
-        int off = 0;
-        int zb = zrp[i], ze = zrp[i + 1];
-        for (int t = zb + lane; t < ze; t += 32) {
-            K[t - zb] = zci[t];
-            V[t - zb] = -zv[t];
-        }
-        off = ze - zb;
-        for (int e = krp[i]; e < krp[i + 1]; ++e) {
-            int c = kci[e];
-            double a = kv[e];
-            int mb = mrp[c], me = mrp[c + 1];
-            for (int t = mb + lane; t < me; t += 32) {
-                K[off + t - mb] = mci[t];
-                V[off + t - mb] = a * mv[t];
-            }
-            off += me - mb;
-        }
-        __syncwarp();
-        int p2 = 32;
-        while (p2 < cnt) p2 <<= 1;
-        for (int t = cnt + lane; t < p2; t += 32) {
-            K[t] = INT_MAX;
-            V[t] = 0.0;
-        }
-        __syncwarp();
-        for (int k = 2; k <= p2; k <<= 1)
-            for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                for (int t = lane; t < p2; t += 32) {
-                    int u = t ^ jj;
-                    if (u > t) {
-                        bool up = (t & k) == 0;
-                        int a = K[t], b = K[u];
-                        if ((a > b) == up) {
-                            K[t] = b;
-                            K[u] = a;
-                            double va = V[t];
-                            V[t] = V[u];
-                            V[u] = va;
-                        }
-                    }
-                }
-                __syncwarp();
-            }
-        // segmented sums: the lane holding the first entry of a column sums it
-        double r2 = 0.0;
-        for (int t = lane; t < cnt; t += 32) {
-            if (t == 0 || K[t - 1] != K[t]) {
-                double s = 0.0;
-                for (int q = t; q < cnt && K[q] == K[t]; ++q) s += V[q];
-                r2 = fma(s, s, r2);
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-        if (lane == 0) row_r2[i] = r2;
-        __syncwarp();
     }
 }
 
@@ -322,6 +261,15 @@ cudaError_t csr_spmv(sam_handle h, int n, const int32_t *rp, const int32_t *ci, 
     if (n == 0) return cudaSuccess;
     int64_t threads = (int64_t)n * 32;
     spmv_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, handle_stream(h)>>>(n, rp, ci, v, x, y);
+    count_launch(h);
+    return cudaGetLastError();
+}
+
+cudaError_t csr_outer_on_pattern(sam_handle h, int n, const int32_t *rp, const int32_t *ci, const double *dy,
+                                 const double *x, double *g) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t threads = (int64_t)n * 32;
+    outer_on_pattern_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, handle_stream(h)>>>(n, rp, ci, dy, x, g);
     count_launch(h);
     return cudaGetLastError();
 }

@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "residual_row.cuh"
 
 namespace {
 
@@ -26,7 +27,6 @@ constexpr int kStaticMaxRows = SAM_STATIC_MAX_ROWS;
 constexpr int kBlocks = 256;  // fixed reduction grid: deterministic sums
 constexpr int kThreads = 256;
 constexpr int kWarps = 2;     // row kernel: warps per block
-constexpr int kBuf = 1024;    // candidate entries per row
 
 // [0, kStaticMaxRows): squared residual of every row
 // [kStaticMaxRows, +kBlocks): block partials of sum ||R(i,:)||^2
@@ -75,88 +75,23 @@ __global__ void static_validate_kernel(int n, const int32_t *rp0, const int32_t 
     }
 }
 
-// Row i of R = A_k M - A_0 into rows[i] = ||R(i, :)||^2: the products
-// A_k(i, c) M(c, :) and -A_0(i, :) as (column, value) pairs, sorted by column
-// with a fixed bitonic network, summed per column, squared.  Does nothing
-// when the validation kernel flagged an input.
+// Row i of R = A_k M - A_0 into rows[i] = ||R(i, :)||^2 (residual_row_sq,
+// the routine sam_residual uses).  Does nothing when the validation kernel
+// flagged an input.
 __global__ void __launch_bounds__(kWarps * 32) static_rows_kernel(
     int n, const int32_t *krp, const int32_t *kci, const double *kv, const int32_t *mrp, const int32_t *mci,
     const double *mv, const int32_t *zrp, const int32_t *zci, const double *zv, double *rows, int32_t *flag) {
-    __shared__ int keys[kWarps][kBuf];
-    __shared__ double vals[kWarps][kBuf];
+    __shared__ int keys[kWarps][sam::kResRowBuf];
+    __shared__ double vals[kWarps][sam::kResRowBuf];
     if (*((volatile int32_t *)flag) != 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *K = keys[warp];
-    double *V = vals[warp];
     for (int64_t i = (int64_t)blockIdx.x * kWarps + warp; i < n; i += (int64_t)gridDim.x * kWarps) {
-        int cnt = zrp[i + 1] - zrp[i];
-        for (int base = krp[i]; base < krp[i + 1]; base += 32) {
-            const int e = base + lane;
-            int len = (e < krp[i + 1]) ? mrp[kci[e] + 1] - mrp[kci[e]] : 0;
-            for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(0xffffffffu, len, o);
-            cnt += len;
+        const double r2 =
+            sam::residual_row_sq(i, lane, krp, kci, kv, mrp, mci, mv, zrp, zci, zv, keys[warp], vals[warp]);
+        if (lane == 0) {
+            rows[i] = r2 < 0.0 ? 0.0 : r2;
+            if (r2 < 0.0) atomicCAS(flag, 0, SAM_ERR_UNSUPPORTED);
         }
-        if (cnt > kBuf) {
-            if (lane == 0) {
-                rows[i] = 0.0;
-                atomicCAS(flag, 0, SAM_ERR_UNSUPPORTED);
-            }
-            continue;
-        }
-        const int zb = zrp[i], ze = zrp[i + 1];
-        for (int t = zb + lane; t < ze; t += 32) {
-            K[t - zb] = zci[t];
-            V[t - zb] = -zv[t];
-        }
-        int off = ze - zb;
-        for (int e = krp[i]; e < krp[i + 1]; ++e) {
-            const int c = kci[e];
-            const double a = kv[e];
-            const int mb = mrp[c], me = mrp[c + 1];
-            for (int t = mb + lane; t < me; t += 32) {
-                K[off + t - mb] = mci[t];
-                V[off + t - mb] = a * mv[t];
-            }
-            off += me - mb;
-        }
-        __syncwarp();
-        int p2 = 32;
-        while (p2 < cnt) p2 <<= 1;
-        for (int t = cnt + lane; t < p2; t += 32) {
-            K[t] = 0x7fffffff;
-            V[t] = 0.0;
-        }
-        __syncwarp();
-        for (int k = 2; k <= p2; k <<= 1)
-            for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                for (int t = lane; t < p2; t += 32) {
-                    const int u = t ^ jj;
-                    if (u > t) {
-                        const bool up = (t & k) == 0;
-                        const int a = K[t], b = K[u];
-                        if ((a > b) == up) {
-                            K[t] = b;
-                            K[u] = a;
-                            const double va = V[t];
-                            V[t] = V[u];
-                            V[u] = va;
-                        }
-                    }
-                }
-                __syncwarp();
-            }
-        double r2 = 0.0;
-        for (int t = lane; t < cnt; t += 32) {
-            if (t == 0 || K[t - 1] != K[t]) {
-                double s = 0.0;
-                for (int q = t; q < cnt && K[q] == K[t]; ++q) s += V[q];
-                r2 = fma(s, s, r2);
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-        if (lane == 0) rows[i] = r2;
-        __syncwarp();
     }
 }
 
@@ -183,7 +118,9 @@ __global__ void __launch_bounds__(kThreads) static_partial_kernel(const double *
     if (threadIdx.x == 0) (first ? part_r : part_a)[blockIdx.x] = sh[0];
 }
 
-// out[0] = ||R||_F, out[1] = ||R||_F / ||A_0||_F, *status = the flag
+// out[0] = ||R||_F, out[1] = ||R||_F / ||A_0||_F, *status = the flag; a
+// flagged input gives NaN in both outputs, so that a caller who passes no
+// status word cannot mistake the failure for an exact map
 __global__ void __launch_bounds__(kBlocks) static_final_kernel(const double *part_r, const double *part_a,
                                                                const int32_t *flag, double *out, int32_t *status) {
     __shared__ double sr[kBlocks], sa[kBlocks];
@@ -200,51 +137,67 @@ __global__ void __launch_bounds__(kBlocks) static_final_kernel(const double *par
     if (threadIdx.x == 0) {
         const int32_t st = *flag;
         const double fro = sqrt(sr[0]);
-        out[0] = st ? 0.0 : fro;
-        out[1] = (st || sa[0] <= 0.0) ? 0.0 : fro / sqrt(sa[0]);
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        out[0] = st ? nan : fro;
+        out[1] = st ? nan : (sa[0] <= 0.0 ? 0.0 : fro / sqrt(sa[0]));
         if (status) *status = st;
     }
 }
 
-// Device address of the static array, looked up once per device with that
-// device current.
+// Device address of the static array for the current device.  It is looked
+// up (cudaGetSymbolAddress, which allocates nothing) on every call made
+// while the stream is not being captured, so that a device reset or a new
+// primary context never leaves a stale address behind; a call made while
+// the stream is being captured uses the address its device's last
+// uncaptured call found (the first call on a device must therefore come
+// before any capture).
 constexpr int kMaxDevices = 64;
 std::mutex g_lock;
 double *g_addr[kMaxDevices] = {nullptr};
 
-cudaError_t scratch_address(double **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
+cudaError_t scratch_address(cudaStream_t st, int dev, double **out) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;  // unknown: do not call into the runtime's loader
+    }
     std::lock_guard<std::mutex> guard(g_lock);
-    if (!g_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
         g_addr[dev] = static_cast<double *>(p);
     }
+    if (!g_addr[dev]) return cudaErrorStreamCaptureUnsupported;  // first call made under capture
     *out = g_addr[dev];
     return cudaSuccess;
 }
 
+// A matrix of order n >= 1 (the library's convention: an empty matrix is
+// an invalid argument) with consistent sizes and pointers.
 bool bad_csr(const sam_csr *A) {
-    return !A || A->n < 0 || A->nnz < 0 || A->nnz > INT32_MAX || !A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->val));
+    return !A || A->n < 1 || A->nnz < 0 || A->nnz > INT32_MAX || !A->row_ptr ||
+           (A->nnz > 0 && (!A->col_idx || !A->val));
 }
 
-// Every array must already be reachable from the device: this entry point
-// cannot stage host memory (staging would need a device buffer).
-bool on_device(const void *p) {
+// Every array must already be reachable from the current device: this entry
+// point cannot stage host memory (staging would need a device buffer), and
+// memory of another device would be read by kernels launched on this one.
+bool on_device(const void *p, int dev) {
     if (!p) return true;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
-bool csr_on_device(const sam_csr *A) { return on_device(A->row_ptr) && on_device(A->col_idx) && on_device(A->val); }
+bool csr_on_device(const sam_csr *A, int dev) {
+    return on_device(A->row_ptr, dev) && on_device(A->col_idx, dev) && on_device(A->val, dev);
+}
 
 }  // namespace
 
@@ -254,24 +207,24 @@ extern "C" sam_status sam_residual_static(void *cuda_stream, const sam_csr *A_k,
     const int n = A_k->n;
     if (M_k->n != n || A_0->n != n) return SAM_ERR_INVALID_ARG;
     if (n > kStaticMaxRows) return SAM_ERR_INVALID_ARG;  // beyond the fixed workspace
-    if (!csr_on_device(A_k) || !csr_on_device(M_k) || !csr_on_device(A_0) || !on_device(out) || !on_device(status))
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SAM_ERR_CUDA;
+    if (!csr_on_device(A_k, dev) || !csr_on_device(M_k, dev) || !csr_on_device(A_0, dev) || !on_device(out, dev) ||
+        !on_device(status, dev))
         return SAM_ERR_INVALID_ARG;
-    double *base = nullptr;
-    if (scratch_address(&base) != cudaSuccess) return SAM_ERR_CUDA;
-    const Slots s = slots_of(base);
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    double *base = nullptr;
+    if (scratch_address(st, dev, &base) != cudaSuccess) return SAM_ERR_CUDA;
+    const Slots s = slots_of(base);
     if (cudaMemsetAsync(s.flag, 0, sizeof(int32_t), st) != cudaSuccess) return SAM_ERR_CUDA;
-    if (n > 0) {
-        dim3 vg((unsigned)((n + 1 + 255) / 256), 3);
-        static_validate_kernel<<<vg, 256, 0, st>>>(n, A_k->row_ptr, A_k->col_idx, A_k->nnz, M_k->row_ptr,
-                                                   M_k->col_idx, M_k->nnz, A_0->row_ptr, A_0->col_idx, A_0->nnz,
-                                                   s.flag);
-        int blocks = (n + kWarps - 1) / kWarps;
-        if (blocks > 4096) blocks = 4096;
-        static_rows_kernel<<<blocks, kWarps * 32, 0, st>>>(n, A_k->row_ptr, A_k->col_idx, A_k->val, M_k->row_ptr,
-                                                           M_k->col_idx, M_k->val, A_0->row_ptr, A_0->col_idx,
-                                                           A_0->val, s.rows, s.flag);
-    }
+    dim3 vg((unsigned)((n + 1 + 255) / 256), 3);
+    static_validate_kernel<<<vg, 256, 0, st>>>(n, A_k->row_ptr, A_k->col_idx, A_k->nnz, M_k->row_ptr, M_k->col_idx,
+                                               M_k->nnz, A_0->row_ptr, A_0->col_idx, A_0->nnz, s.flag);
+    int blocks = (n + kWarps - 1) / kWarps;
+    if (blocks > 4096) blocks = 4096;
+    static_rows_kernel<<<blocks, kWarps * 32, 0, st>>>(n, A_k->row_ptr, A_k->col_idx, A_k->val, M_k->row_ptr,
+                                                       M_k->col_idx, M_k->val, A_0->row_ptr, A_0->col_idx, A_0->val,
+                                                       s.rows, s.flag);
     static_partial_kernel<<<dim3(kBlocks, 2), kThreads, 0, st>>>(s.rows, n, A_0->val, A_0->nnz, s.part_r, s.part_a,
                                                                  s.flag);
     static_final_kernel<<<1, kBlocks, 0, st>>>(s.part_r, s.part_a, s.flag, out, status);

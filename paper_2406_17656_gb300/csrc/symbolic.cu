@@ -627,19 +627,24 @@ __global__ void level01_fill(int n, const int32_t *kcp, const int32_t *kri, int 
     if (!placed) jri[o++] = j;
 }
 
-// Size classes: |I| <= bin_maxi, |J| <= bin_maxj, nnz(B) <= 8 * bin_maxi.
-// Must match the tile table in lsq.cu.
-__constant__ int c_bin_maxi[kNumBins] = {14, 26, 40, 52, 64};
-__constant__ int c_bin_maxj[kNumBins] = {5, 9, 23, 27, 27};
+// Size classes: |I| <= bin_maxi, |J| <= bin_maxj, nnz(B) <= 8 * bin_maxi
+// (the register tiles of lsq.cu, whose table these must match); larger
+// columns within the large class's limits go to it (lsq_big.cu).
+__constant__ int c_bin_maxi[kRegBins] = {14, 26, 40, 52, 64};
+__constant__ int c_bin_maxj[kRegBins] = {5, 9, 23, 27, 27};
 
 __device__ __forceinline__ int size_class(int u, int nj, int total) {
     int b = kBinNone;
-    if (u >= nj && u >= 0)
-        for (int q = 0; q < kNumBins; ++q)
+    if (u >= nj && u >= 0) {
+        for (int q = 0; q < kRegBins; ++q)
             if (u <= c_bin_maxi[q] && nj <= c_bin_maxj[q] && total <= 8 * c_bin_maxi[q]) {
                 b = q;
                 break;
             }
+        if (b == kBinNone && nj <= kBigJCap && u <= kBigICap && total <= kBigLCap &&
+            (int64_t)u * (nj + 1) <= kBigTileDoubles)
+            b = kBinBig;
+    }
     return b;
 }
 
@@ -745,7 +750,7 @@ __device__ bool union_fast(int j, const int32_t *kcp, const int32_t *kri, const 
     }
     __syncwarp();
     if (SHADOW) bsz = size_class(count, nj, total);
-    if (SHADOW && lrow_j && bsz != kBinNone) {
+    if (SHADOW && lrow_j && bsz < kRegBins) {
         // rank of every entry among the shadow rows, in gather order
 #pragma unroll
         for (int u = 0; u < kRegRows; ++u) {
@@ -866,7 +871,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const i
             // local shadow row of every entry of A(:, J_j), in gather order (the
             // columns of J_j in order, each in CSC order): its rank in I_j,
             // staged in shared memory and written out as 32-bit words
-            if (lrow && b != kBinNone) {
+            if (lrow && b < kRegBins) {
                 const int yb = jcp[j], ye = jcp[j + 1];
                 const int u = r.count;
                 int off = 0;
@@ -911,7 +916,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const i
             }
             __syncwarp();
         }
-        if (tg.zloc && b != kBinNone) {
+        if (tg.zloc && b < kRegBins) {
             uint8_t *zl = tg.zloc + j * kZCap;
             for (int t = lane; t < zlen && t < kZCap; t += 32) {
                 const int rk = union_rank(tg.zri[zb + t] + zro, r, bm, wpre);

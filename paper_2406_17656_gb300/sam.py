@@ -33,6 +33,7 @@ SAM_FP64 = 0
 SAM_FP32_REFINE = 1
 SAM_FLAG_TRUSTED = 1
 SAM_STATIC_MAX_ROWS = 1 << 19  # largest order sam_residual_static accepts
+SAM_NUM_SIZE_CLASSES = 6
 
 PRECISIONS = {"fp64": SAM_FP64, "fp32r": SAM_FP32_REFINE}
 SPARSIFY_MODES = {"global": 0, "tau": 1, "lfil": 2}
@@ -65,6 +66,7 @@ _lock = threading.Lock()
 # (name, restype, argtypes)
 _SIGS = [
     ("sam_limits", None, [_i32p, _i32p]),
+    ("sam_size_classes", ctypes.c_int32, [_i32p, _i32p, _i32p, _i32p, _i32p, ctypes.c_int]),
     ("sam_status_string", ctypes.c_char_p, [ctypes.c_int32]),
     ("sam_create", ctypes.c_int32, [ctypes.POINTER(_vp), _vp]),
     ("sam_destroy", ctypes.c_int32, [_vp]),
@@ -86,6 +88,7 @@ _SIGS = [
     ("sam_residual", ctypes.c_int32,
      [_vp, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), _f64p, _f64p]),
     ("sam_apply", ctypes.c_int32, [_vp, ctypes.POINTER(sam_csr), _vp, _vp]),
+    ("sam_apply_grad", ctypes.c_int32, [_vp, ctypes.POINTER(sam_csr), _vp, _vp, _vp]),
     ("sam_build_backward", ctypes.c_int32,
      [_vp, ctypes.POINTER(sam_csr), ctypes.POINTER(sam_csr), _vp, ctypes.c_int, ctypes.c_int, _vp, _vp,
       ctypes.c_double, _vp, _vp, _vp]),
@@ -163,6 +166,17 @@ def limits() -> tuple[int, int]:
     r, c = ctypes.c_int32(), ctypes.c_int32()
     load().sam_limits(ctypes.byref(r), ctypes.byref(c))
     return r.value, c.value
+
+
+def size_classes() -> dict:
+    """The size classes of the column problems (include/sam.h): per class
+    the largest |I_j|, |J_j|, nnz(B_j), |I_j| (|J_j| + 1) and the number of
+    tile variants."""
+    C = SAM_NUM_SIZE_CLASSES
+    r, c, e, t, v = [(ctypes.c_int32 * C)() for _ in range(5)]
+    _check(load().sam_size_classes(r, c, e, t, v, C), "sam_size_classes")
+    return {"max_rows": list(r), "max_cols": list(c), "max_entries": list(e), "max_tile": list(t),
+            "variants": list(v)}
 
 
 def _check(st: int, what: str):
@@ -481,6 +495,18 @@ class Handle:
         _check(load().sam_apply(self.ptr, ctypes.byref(m), _addr(x), _addr(y)), "sam_apply")
         return y
 
+    def sam_apply_grad(self, M_k: Csr, x, dy, dM_val=None):
+        """dL/dM values of y = M_k x given dy = dL/dy: dM_val[e] = dy[i] x[c]."""
+        import torch
+
+        if dM_val is None:
+            dM_val = torch.empty(M_k.nnz, dtype=torch.float64, device=x.device) if hasattr(x, "data_ptr") else \
+                np.empty(M_k.nnz, dtype=np.float64)
+        m = M_k.c()
+        _check(load().sam_apply_grad(self.ptr, ctypes.byref(m), _addr(x), _addr(dy), _addr(dM_val)),
+               "sam_apply_grad")
+        return dM_val
+
     def sam_gmres(self, A: Csr, b, x=None, M: Csr | None = None, P_0: Csr | None = None, restart: int = 30,
                   maxiter: int = 1000, rtol: float = 1e-8, history=None):
         """Restarted GMRES for A x = b with the right preconditioner
@@ -613,7 +639,7 @@ class Handle:
         return self.sam_get_tile_variants()
 
     def sam_set_tile_variants(self, variants):
-        v = (ctypes.c_int * 5)(*[int(x) for x in variants])
+        v = (ctypes.c_int * SAM_NUM_SIZE_CLASSES)(*[int(x) for x in variants])
         _check(load().sam_set_tile_variants(self.ptr, v, len(variants)), "sam_set_tile_variants")
 
     def sam_refine_stats(self):
@@ -624,8 +650,8 @@ class Handle:
         return list(c)
 
     def sam_get_tile_variants(self):
-        v = (ctypes.c_int * 5)()
-        _check(load().sam_get_tile_variants(self.ptr, v, 5), "sam_get_tile_variants")
+        v = (ctypes.c_int * SAM_NUM_SIZE_CLASSES)()
+        _check(load().sam_get_tile_variants(self.ptr, v, SAM_NUM_SIZE_CLASSES), "sam_get_tile_variants")
         return list(v)
 
     def sam_profile(self, enable: bool):
@@ -634,8 +660,8 @@ class Handle:
     def sam_profile_read(self):
         """(kernel launches, per-size-class least-squares ms, per-class launches)."""
         n = ctypes.c_int64()
-        ms = (ctypes.c_double * 5)()
-        cnt = (ctypes.c_int64 * 5)()
+        ms = (ctypes.c_double * SAM_NUM_SIZE_CLASSES)()
+        cnt = (ctypes.c_int64 * SAM_NUM_SIZE_CLASSES)()
         _check(load().sam_profile_read(self.ptr, ctypes.byref(n), ms, cnt), "sam_profile_read")
         return n.value, list(ms), list(cnt)
 

@@ -270,6 +270,29 @@ def config5_vector(n: int) -> np.ndarray:
     return np.random.default_rng(5000).standard_normal(n)
 
 
+def wide_band(n: int = 500, half: int = 50, keep: float = 0.85, nmat: int = 3, seed: int = 7000) -> Sequence:
+    """A sequence of sources with about 85 stored entries per column, the
+    density of the paper's NWP matrices (Sec. 5.2: 646,471 entries at
+    n = 7700), for column problems past the register tiles at level 1: every
+    entry of the band |i - j| <= half is stored with probability `keep`
+    (one structure for the whole sequence, plus the diagonal), values
+    U(-1, 1) with a dominant diagonal; A_k = A_0 with its off-diagonal
+    values scaled by 1 + 0.05 k U(-1, 1)."""
+    rng = np.random.default_rng(seed)
+    i, j = np.nonzero(np.abs(np.arange(n)[:, None] - np.arange(n)[None, :]) <= half)
+    sel = (rng.random(len(i)) < keep) | (i == j)
+    i, j = i[sel], j[sel]
+    base = rng.uniform(-1.0, 1.0, len(i))
+    mats = []
+    for k in range(nmat):
+        v = base * (1.0 + 0.05 * k * rng.uniform(-1.0, 1.0, len(i)))
+        off = np.where(i == j, 0.0, v)
+        rowsum = np.bincount(i, weights=np.abs(off), minlength=n)
+        v = np.where(i == j, rowsum[i] + 1.0, v)
+        mats.append(CSR.from_scipy(sp.csr_matrix((v, (i, j)), shape=(n, n))))
+    return Sequence("wide_band_%d_h%d" % (n, half), mats, level=1, meta={"half": half, "keep": keep})
+
+
 def random_nested_pair(n: int, density: float, seed: int, extra: float = 0.5):
     """Small random diagonally dominant A_0, A_1 with S(A_0) subset of S(A_1)
     (the subset property of Sec. 3); used for brute-force checks."""

@@ -42,3 +42,26 @@ def test_algorithmic_flops_closed_form():
     assert np.allclose(f64, 2 * nB + m)
     f32_0, f64_0 = bench.algorithmic_flops(I, J, nB, "fp64", 0)
     assert np.allclose(f64_0, qr) and np.allclose(f32_0, 0)
+
+
+def test_bench_size_classes_are_the_librarys():
+    """bench.py's roofline selects the columns of a size class by the
+    library's own limits (no copy of the kernel's constants)."""
+    from paper_2406_17656_gb300 import build, sam
+
+    build.build()
+    c = sam.size_classes()
+    assert bench.size_classes() == c
+    assert len(c["max_rows"]) == sam.SAM_NUM_SIZE_CLASSES
+    # every class boundary: a column just inside goes to that class (or an
+    # earlier one), just outside to a later one
+    for q in range(sam.SAM_NUM_SIZE_CLASSES):
+        I = np.array([c["max_rows"][q]])
+        J = np.array([min(c["max_cols"][q], c["max_tile"][q] // c["max_rows"][q] - 1)])
+        nB = np.array([min(c["max_entries"][q], int(I[0]) * int(J[0]))])
+        assert 0 <= bench.bin_of(I, J, nB, c)[0] <= q
+    I, J = np.array([c["max_rows"][-1] + 1]), np.array([2])
+    assert bench.bin_of(I, J, np.array([8]), c)[0] == -1
+    rows, cols = np.zeros(1, np.int32), np.zeros(1, np.int32)
+    sam.load().sam_limits(rows.ctypes.data_as(sam._i32p), cols.ctypes.data_as(sam._i32p))
+    assert rows[0] == c["max_rows"][-1] and cols[0] == c["max_cols"][-1]

@@ -1,13 +1,16 @@
 """Full-size parity of the remaining workloads, each in its batched launch
 configuration: every map of a sequence (or every pair of the adjoint batch)
 in one call, then sampled maps compared with the oracle -- patterns and CSR
-structure bit-exact on whole maps, values on sampled columns within the
-relative Frobenius bar, the residual of each sampled map against the
-oracle's residual of the GPU's own map."""
+structure bit-exact on whole maps, values of every sampled column within
+the per-column bar (and the sample within the relative Frobenius bar), the
+squared residual of every sampled column against the oracle's (bar derived
+in colcheck.py), the residual of each sampled map against the oracle's
+residual of the GPU's own map."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
 
+import colcheck
 import oracle
 from paper_2406_17656_gb300 import workloads as W
 
@@ -36,7 +39,7 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def _check_map(k, Ak, A0, level, Ss, offs, rp, ci, v, fro, ncols, seed, tol=1e-10):
+def _check_map(k, Ak, A0, level, Ss, offs, rp, ci, v, fro, ncols, seed, tol=1e-10, r2=None):
     n = A0.n
     cp, ri = oracle.pattern(Ak, level)
     assert np.array_equal(Ss[k].colptr().cpu().numpy(), cp)
@@ -51,6 +54,11 @@ def _check_map(k, Ak, A0, level, Ss, offs, rp, ci, v, fro, ncols, seed, tol=1e-1
     idx = np.concatenate([np.arange(cp[j], cp[j + 1]) for j in cols])
     err = _rel(m.data[idx], ref["mval"][idx])
     assert err <= tol, (k, err)
+    colcheck.assert_columns(cp, m.data, ref["mval"], "fp32r", cols=cols, what="map %d" % k)
+    if r2 is not None:
+        got = r2[k * n:(k + 1) * n][cols]
+        want = (ref["res2"] + ref["out2"])[cols]
+        colcheck.assert_res2(got, want, colcheck.target_column_norms(A0)[cols], "fp32r", what="res2 of map %d" % k)
     own, _ = oracle.residual(Ak, m.indptr, m.indices, m.data, A0)
     assert abs(fro[k] - own) <= 1e-10 * own + 1e-13 * np.linalg.norm(A0.data)
     return err
@@ -65,10 +73,13 @@ def test_config3_upwind7_64cube_20maps_level2(sam, handle):
     a0 = sam.Csr.from_host(A0)
     Ss = handle.sam_pattern_build_batched(Aks, 2)
     handle.sam_tune(Aks, a0, Ss, "fp32r", 1)
-    offs, rp, ci, v, fro = handle.sam_build_batched(Aks, a0, Ss, "fp32r", 1, want_fro=True)
-    rp, ci, v = rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy()
+    import torch
+
+    r2 = torch.empty(len(Aks) * A0.n, dtype=torch.float64, device="cuda")
+    offs, rp, ci, v, fro = handle.sam_build_batched(Aks, a0, Ss, "fp32r", 1, want_fro=True, res2=r2)
+    rp, ci, v, r2 = rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy(), r2.cpu().numpy()
     for k in (0, 10, 19):
-        _check_map(k, seq.mats[k], A0, 2, Ss, offs, rp, ci, v, fro, 1200, 300 + k)
+        _check_map(k, seq.mats[k], A0, 2, Ss, offs, rp, ci, v, fro, 1200, 300 + k, r2=r2)
     # M_0 = I: the first map of a sequence is the identity
     assert fro[0] <= 1e-12 * np.linalg.norm(A0.data)
 
@@ -84,16 +95,17 @@ def test_config4_p1_fem_512_16maps_level2(sam, handle):
     Aks = [sam.Csr.from_host(m) for m in seq.mats]
     a0 = sam.Csr.from_host(A0)
     Ss = handle.sam_pattern_build_batched(Aks, 2)
-    offs, rp, ci, v, fro = handle.sam_build_batched(Aks, a0, Ss, "fp32r", 1, want_fro=True)
+    r2 = torch.empty(len(Aks) * A0.n, dtype=torch.float64, device="cuda")
+    offs, rp, ci, v, fro = handle.sam_build_batched(Aks, a0, Ss, "fp32r", 1, want_fro=True, res2=r2)
     # the CUDA-graph-captured pipeline gives the same maps bit for bit
     plan = handle.sam_plan_create(Aks, a0, Ss, "fp32r", 1)
     plan.execute()
     handle.sam_sync()
     assert torch.equal(plan.M_val, v) and torch.equal(plan.M_col_idx, ci) and torch.equal(plan.M_row_ptr, rp)
     plan.destroy()
-    rp, ci, v = rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy()
+    rp, ci, v, r2 = rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy(), r2.cpu().numpy()
     for k in (1, 8, 15):
-        _check_map(k, seq.mats[k], A0, 2, Ss, offs, rp, ci, v, fro, 1200, 400 + k)
+        _check_map(k, seq.mats[k], A0, 2, Ss, offs, rp, ci, v, fro, 1200, 400 + k, r2=r2)
 
 
 def test_config5_pairs_512_forward_and_adjoint(sam, handle):
@@ -109,10 +121,11 @@ def test_config5_pairs_512_forward_and_adjoint(sam, handle):
     A0s = [sam.Csr.from_host(p[0]) for p in pairs]
     A1s = [sam.Csr.from_host(p[1]) for p in pairs]
     Ss = handle.sam_pattern_build_batched(A1s, 1)
-    offs, rp, ci, v, fro = handle.sam_build_batched(A1s, A0s, Ss, "fp32r", 2, want_fro=True)
-    rph, cih, vh = rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy()
+    r2 = torch.empty(32 * n, dtype=torch.float64, device="cuda")
+    offs, rp, ci, v, fro = handle.sam_build_batched(A1s, A0s, Ss, "fp32r", 2, want_fro=True, res2=r2)
+    rph, cih, vh, r2h = rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy(), r2.cpu().numpy()
     for b in (0, 17, 31):
-        _check_map(b, pairs[b][1], pairs[b][0], 1, Ss, offs, rph, cih, vh, fro, 1500, 500 + b)
+        _check_map(b, pairs[b][1], pairs[b][0], 1, Ss, offs, rph, cih, vh, fro, 1500, 500 + b, r2=r2h)
     # gradient of the loss: dL/dM from the ||M v||^2 term, residual term direct
     vec = torch.from_numpy(W.config5_vector(n)).cuda()
     rows = torch.repeat_interleave(torch.arange(32 * n, device="cuda"),

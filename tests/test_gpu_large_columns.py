@@ -1,0 +1,122 @@
+"""Column problems past the register tiles (more than 64 shadow rows, 27
+unknowns or 512 stored entries): the large size class, one thread block per
+column with an FP64 tile in shared memory, against the oracle column by
+column.  Workloads: level-3 patterns of the 9-point and 7-point stencils
+(the paper's "level 2" of Sec. 5.1: 49 and 63 unknowns per interior column)
+and a banded source with about 85 entries per column at level 1 (the NWP
+density of Sec. 5.2: up to 96 unknowns and 201 shadow rows)."""
+import numpy as np
+import pytest
+
+import colcheck
+import oracle
+from paper_2406_17656_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sam():
+    import torch
+
+    from paper_2406_17656_gb300 import build, sam as S
+
+    build.build()
+    assert torch.cuda.is_available()
+    return S
+
+
+@pytest.fixture(scope="module")
+def handle(sam):
+    h = sam.Handle()
+    yield h
+    h.close()
+
+
+CASES = {
+    "q1_24_L3": lambda: (W.config2(nx=24, nmat=3), 3),
+    "upwind7_9_L3": lambda: (W.config3(nx=9, nmat=3), 3),
+    "wide_band_85_L1": lambda: (W.wide_band(), 1),
+    "fem_20_L3": lambda: (W.config4(ncell=20, nmat=3, flip_frac=0.1), 3),
+}
+
+
+def _sizes(A, level):
+    import bench
+
+    return bench.column_sizes([A], level)[0]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_large_columns_match_the_oracle(sam, handle, case, precision):
+    import torch
+
+    seq, level = CASES[case]()
+    A0 = seq.mats[0]
+    gamma = colcheck.target_column_norms(A0)
+    for Ak in seq.mats[1:]:
+        I, J, nB = _sizes(Ak, level)
+        assert (I > 64).any() or (J > 27).any() or (nB > 512).any()  # the large class is used
+        cp, ri = oracle.pattern(Ak, level)
+        ref = oracle.build(Ak, A0, cp, ri)
+        S = handle.sam_pattern_build(sam.Csr.from_host(Ak), level)
+        st = torch.full((Ak.n,), -1, dtype=torch.int32, device="cuda")
+        r2 = torch.empty(Ak.n, dtype=torch.float64, device="cuda")
+        ip, ix, dv = handle.sam_build(sam.Csr.from_host(Ak), sam.Csr.from_host(A0), S, precision, 1, col_status=st,
+                                      res2=r2)
+        handle.sam_sync()
+        assert int(st.abs().max()) == 0
+        eip, eix, _ = oracle.to_csr(Ak.n, cp, ri, ref["mval"])
+        assert np.array_equal(ip.cpu().numpy(), eip) and np.array_equal(ix.cpu().numpy(), eix)
+        got = colcheck.csr_to_csc_values(Ak.n, ip.cpu().numpy(), ix.cpu().numpy(), dv.cpu().numpy(), cp, ri)
+        colcheck.assert_columns(cp, got, ref["mval"], precision)
+        # the large class is solved in FP64 whatever the precision: its columns meet the FP64 bar
+        big = (I > 64) | (J > 27) | (nB > 512)
+        colcheck.assert_columns(cp, got, ref["mval"], "fp64", cols=np.flatnonzero(big), what="large class")
+        colcheck.assert_res2(r2.cpu().numpy(), ref["res2"] + ref["out2"], gamma, precision)
+
+
+def test_large_columns_in_a_shared_batch_multi_target_and_plan(sam, handle):
+    """A level-3 sequence of one structure (shadow data shared across maps),
+    the same maps against one target per map, and the captured plan: the
+    large class reads every map's values at its own offsets."""
+    import torch
+
+    seq = W.config2(nx=20, nmat=3)
+    aks = [sam.Csr.from_host(m) for m in seq.mats]
+    a0 = aks[0]
+    n = seq.mats[0].n
+    pats = handle.sam_pattern_build_batched(aks, 3)
+    offs, rp, ci, v, fro = handle.sam_build_batched(aks, a0, pats, "fp32r", 1, want_fro=True)
+    offs2, rp2, ci2, v2, fro2 = handle.sam_build_batched(aks, [a0] * 3, pats, "fp32r", 1, want_fro=True)
+    assert torch.equal(v, v2) and np.array_equal(fro, fro2)
+    plan = handle.sam_plan_create(aks, a0, pats, "fp32r", 1)
+    plan.execute()
+    handle.sam_sync()
+    assert torch.equal(plan.M_val, v)
+    plan.destroy()
+    rp, ci, v = rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy()
+    for k, Ak in enumerate(seq.mats):
+        cp, ri = oracle.pattern(Ak, 3)
+        ref = oracle.build(Ak, seq.mats[0], cp, ri)
+        got = colcheck.csr_to_csc_values(n, rp[k * (n + 1):(k + 1) * (n + 1)], ci[offs[k]:offs[k + 1]],
+                                         v[offs[k]:offs[k + 1]], cp, ri)
+        colcheck.assert_columns(cp, got, ref["mval"], "fp32r", what="map %d" % k)
+
+
+def test_adjoint_reports_large_columns_as_unsupported(sam, handle):
+    seq = W.config2(nx=16, nmat=2)
+    A1, A0 = sam.Csr.from_host(seq.mats[1]), sam.Csr.from_host(seq.mats[0])
+    S = handle.sam_pattern_build(A1, 3)
+    _, _, mv = handle.sam_build(A1, A0, S, "fp32r", 1)
+    handle.sam_sync()
+    with pytest.raises(sam.SamError) as e:
+        handle.sam_build_backward(A1, A0, S, mv, mv, "fp32r", 1, 0.0)
+        handle.sam_sync()
+    assert e.value.status == sam.SAM_ERR_UNSUPPORTED
+    # the handle stays usable
+    S2 = handle.sam_pattern_build(A1, 2)
+    _, _, mv2 = handle.sam_build(A1, A0, S2, "fp32r", 1)
+    handle.sam_build_backward(A1, A0, S2, mv2, mv2, "fp32r", 1, 0.0)
+    handle.sam_sync()

@@ -7,6 +7,7 @@ matches the oracle."""
 import numpy as np
 import pytest
 
+import colcheck
 import oracle
 from paper_2406_17656_gb300 import workloads as W
 
@@ -24,10 +25,13 @@ def sam():
     return S
 
 
-# level 3 of the 9-point stencil has 49 unknowns per column, past the
-# kernels' 27; the 5-point sequence has 25 (and 41 shadow rows) there
+# level 3 of the 5-point stencil has 25 unknowns per column (and 41 shadow
+# rows), within the register tiles; level 3 of the 9-point stencil has 49
+# and of the 7-point stencil 63, which the large class (one thread block
+# per column) serves
 SEQS = {"q1_36_L1": (lambda: W.config2(nx=36, nmat=4), 1), "q1_36_L2": (lambda: W.config2(nx=36, nmat=4), 2),
-        "poisson5_32_L3": (lambda: W.config1(nx=32), 3)}
+        "poisson5_32_L3": (lambda: W.config1(nx=32), 3), "q1_24_L3": (lambda: W.config2(nx=24, nmat=3), 3),
+        "upwind7_9_L3": (lambda: W.config3(nx=9, nmat=3), 3)}
 
 
 @pytest.mark.parametrize("case", sorted(SEQS))
@@ -56,6 +60,8 @@ def test_one_pattern_serves_a_fixed_sparsity_sequence(sam, case):
         assert np.array_equal(ci2[o2[k]:o2[k + 1]].cpu().numpy(), ix)
         got = v2[o2[k]:o2[k + 1]].cpu().numpy()
         assert np.linalg.norm(got - dv) <= 1e-10 * np.linalg.norm(dv)
+        csc = colcheck.csr_to_csc_values(n, ip, ix, got, cp, ri)
+        colcheck.assert_columns(cp, csc, ref["mval"], "fp32r")
 
 
 def _drop_pair(a, i, j):

@@ -1,10 +1,13 @@
-"""Automatic refinement (refine_steps = SAM_REFINE_AUTO): the stopping test
-keeps well-conditioned columns at one or two FP32+FP64 steps within the
-parity bar, and columns the FP32 factorisation cannot serve are re-solved by
-the FP64 kernel (bit for bit the plain FP64 build of those columns)."""
+"""Guarded refinement: in the automatic mode (refine_steps = SAM_REFINE_AUTO)
+the stopping test keeps well-conditioned columns at one or two FP32+FP64
+steps within the parity bar, and columns the FP32 factorisation cannot serve
+are re-solved by the FP64 kernel (bit for bit the plain FP64 build of those
+columns); a fixed number of steps >= 1 is guarded by the same kind of test
+after its last step."""
 import numpy as np
 import pytest
 
+import colcheck
 import oracle
 from paper_2406_17656_gb300 import workloads as W
 
@@ -41,22 +44,29 @@ def test_auto_meets_the_bar_without_fallback(sam, handle, case):
     A0 = seq.mats[0]
     Aks = [sam.Csr.from_host(m) for m in seq.mats]
     Ss = handle.sam_pattern_build_batched(Aks, 2)
-    offs, _, _, v, _ = handle.sam_build_batched(Aks, sam.Csr.from_host(A0), Ss, "fp32r", "auto")
+    offs, rp, ci, v, _ = handle.sam_build_batched(Aks, sam.Csr.from_host(A0), Ss, "fp32r", "auto")
     one, two, fb = handle.sam_refine_stats()
     assert one + two + fb == sum(a.n for a in Aks) and fb == 0
-    v = v.cpu().numpy()
+    v, rp, ci = v.cpu().numpy(), rp.cpu().numpy(), ci.cpu().numpy()
+    n = A0.n
     for k, Ak in enumerate(seq.mats):
         cp, ri = oracle.pattern(Ak, 2)
         ref = oracle.build(Ak, A0, cp, ri)
         _, _, dv = oracle.to_csr(A0.n, cp, ri, ref["mval"])
         assert _rel(v[offs[k]:offs[k + 1]], dv) <= 1e-10
+        got = colcheck.csr_to_csc_values(n, rp[k * (n + 1):(k + 1) * (n + 1)], ci[offs[k]:offs[k + 1]],
+                                         v[offs[k]:offs[k + 1]], cp, ri)
+        colcheck.assert_columns(cp, got, ref["mval"], "fp32r", what="map %d" % k)
 
 
-def test_badly_scaled_rows_fall_back_to_fp64(sam, handle):
+@pytest.mark.parametrize("steps", ["auto", 1, 2])
+def test_badly_scaled_rows_fall_back_to_fp64(sam, handle, steps):
     """D A_1 with row scales spread over 1e-3..1e3 (a weighted problem;
     Householder QR is not invariant under row scaling) makes kappa(B) up to
-    ~1e6 kappa: FP32 refinement cannot converge on many columns, the
-    stopping test flags them and the FP64 kernel re-solves them."""
+    ~1e6 kappa: FP32 refinement cannot converge on many columns.  The
+    automatic mode's stopping test, and the same guard after a fixed number
+    of steps, flag them and the FP64 kernel re-solves them: every column is
+    within the bar."""
     import torch
 
     a0, a1 = W.config2(nx=24, nmat=2).mats
@@ -66,14 +76,17 @@ def test_badly_scaled_rows_fall_back_to_fp64(sam, handle):
     a1s = W.CSR(a1.n, a1.indptr, a1.indices, a1.data * d[rows])
     A1, A0 = sam.Csr.from_host(a1s), sam.Csr.from_host(a0)
     S = handle.sam_pattern_build(A1, 2)
-    _, _, v64 = handle.sam_build(A1, A0, S, "fp64", 0)
-    _, _, v1 = handle.sam_build(A1, A0, S, "fp32r", 1)
-    _, _, va = handle.sam_build(A1, A0, S, "fp32r", "auto")
+    ip, ix, v64 = handle.sam_build(A1, A0, S, "fp64", 0)
+    _, _, v0 = handle.sam_build(A1, A0, S, "fp32r", 0)  # the unguarded FP32 solve alone
+    _, _, va = handle.sam_build(A1, A0, S, "fp32r", steps)
     one, two, fb = handle.sam_refine_stats()
     assert fb > 0 and one + two + fb == a1.n
-    # the fixed single step is far off; the automatic mode is within the bar
-    assert _rel(v1.cpu().numpy(), v64.cpu().numpy()) > 1e-6
+    assert _rel(v0.cpu().numpy(), v64.cpu().numpy()) > 1e-6
     assert _rel(va.cpu().numpy(), v64.cpu().numpy()) <= 1e-10
+    cp, ri = oracle.pattern(a1s, 2)
+    ref = oracle.build(a1s, a0, cp, ri)
+    got = colcheck.csr_to_csc_values(a1.n, ip.cpu().numpy(), ix.cpu().numpy(), va.cpu().numpy(), cp, ri)
+    colcheck.assert_columns(cp, got, ref["mval"], "fp32r")
     # re-solved columns are the FP64 build's values bit for bit: at least fb
     # columns' worth of entries agree exactly
     same = torch.eq(va, v64).sum().item()

@@ -33,7 +33,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("variants", [[0, 1, 1, 1, 1], [0, 1, 0, 1, 0], [0, 0, 1, 0, 1]])
+@pytest.mark.parametrize("variants", [[0, 1, 1, 1, 1, 0], [0, 1, 0, 1, 0, 0], [0, 0, 1, 0, 1, 0]])
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_every_variant_matches_oracle(sam, case, variants):
     seq, level = CASES[case]()
@@ -61,10 +61,10 @@ def test_every_variant_matches_oracle(sam, case, variants):
 def test_out_of_range_variants_are_rejected(sam):
     h = sam.Handle()
     try:
-        for bad in ([1, 0, 0, 0, 0], [0, 2, 0, 0, 0], [0, 0, 0, 0, -1]):
+        for bad in ([1, 0, 0, 0, 0, 0], [0, 2, 0, 0, 0, 0], [0, 0, 0, 0, -1, 0], [0, 0, 0, 0, 0, 1]):
             with pytest.raises(sam.SamError):
                 h.sam_set_tile_variants(bad)
-        assert h.sam_get_tile_variants() == [0, 0, 0, 0, 0]
+        assert h.sam_get_tile_variants() == [0] * 6
     finally:
         h.close()
 
@@ -82,9 +82,9 @@ def test_tune_chooses_valid_variants_and_caches_them(sam, tmp_path):
         assert chosen[0] == 0 and all(c in (0, 1) for c in chosen)
         # the tuner leaves the caller's tracing counters alone
         launches, _, per_bin = h.sam_profile_read()
-        assert launches == 0 and per_bin == [0] * 5
+        assert launches == 0 and per_bin == [0] * 6
         lines = open(cache).read().splitlines()
-        assert len(lines) == 1 and lines[0].split()[-5:] == [str(c) for c in chosen]
+        assert len(lines) == 1 and lines[0].split()[-6:] == [str(c) for c in chosen]
         # the build after tuning still meets the parity bar
         offs, _, _, v, _ = h.sam_build_batched(Aks, A0, Ss, "fp32r", 1)
         v = v.cpu().numpy()
@@ -101,7 +101,7 @@ def test_tune_chooses_valid_variants_and_caches_them(sam, tmp_path):
         assert h2.sam_tune(Aks, A0, Ss, "fp32r", 1, cache_path=cache) == chosen
         assert len(open(cache).read().splitlines()) == 1
         # FP64 has a single shape: nothing changes
-        h2.sam_set_tile_variants([0, 0, 0, 0, 0])
-        assert h2.sam_tune(Aks, A0, Ss, "fp64", 0) == [0, 0, 0, 0, 0]
+        h2.sam_set_tile_variants([0] * 6)
+        assert h2.sam_tune(Aks, A0, Ss, "fp64", 0) == [0] * 6
     finally:
         h2.close()
