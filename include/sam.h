@@ -72,20 +72,20 @@ enum {
 /*
  * refine_steps = SAM_REFINE_AUTO (SAM_FP32_REFINE only): one or two steps per
  * column, chosen by a stopping test, with an FP64 re-solve of the columns
- * that miss the target.  Corrected semi-normal-equation steps contract the
- * error by rho ~ u_32 kappa(B)^2 each.  After step 1 the predicted error
- * 4 |d_1|^2 / |m| is compared with 1e-12 |m|; a warp takes step 2 if any of
- * its columns misses.  After step 2 the predicted error |d_2|^2 / |d_1|
- * (|d_2| alone when the correction grew) above 1e-10 |m| sends the column
- * to the FP64 kernel.  sam_refine_stats counts the outcomes.
+ * that miss the target.  A fixed number of steps s >= 1 is guarded the same
+ * way; s = 0 (the FP32 solve alone, about 1e-5 relative) is not.
  *
- * A fixed number of steps s >= 1 is guarded the same way: after the last
- * step the predicted error rho |d_s| is compared with 1e-10 |m|, where
- * rho = |d_s| / |d_{s-1}| for s >= 2 and, for s = 1, the larger of
- * 4 |d_1| / |m| and u_32 kappa^2 with kappa estimated as
- * max |R_kk| / min |R_kk|; columns above it are re-solved by the FP64
- * kernel (their values are then those of the plain FP64 build).  s = 0 (the
- * FP32 solve alone, about 1e-5 relative) is not guarded.
+ * Corrected semi-normal-equation steps contract the error by
+ * rho ~ u_32 kappa(B)^2 each, so the error after step s is at most
+ * rho / (1 - rho) |d_s| for the correction d_s of that step.  rho is
+ * estimated as the larger of u_32 kappa^2, with kappa estimated as
+ * max |R_kk| / min |R_kk|, and 4 |d_1| / |m| after step 1 or
+ * |d_s| / |d_{s-1}| after later steps.  Automatic mode takes step 2 when
+ * 4 |d_1|^2 > 1e-12 |m|^2 or the prediction after step 1 misses; after the
+ * last step (2 in automatic mode, s otherwise) a predicted error above
+ * 1e-10 |m|, or rho >= 1/2, sends the column to an FP64 Householder
+ * re-solve (the large class's kernel).  sam_refine_stats counts the
+ * outcomes.
  */
 #define SAM_REFINE_AUTO (-1)
 

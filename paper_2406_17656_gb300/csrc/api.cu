@@ -1473,14 +1473,12 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     a.work = work;
     a.bin_off = bin_off;
     a.refine_steps = refine_steps;
-    uint8_t *bin2 = nullptr;
     int32_t *work2 = nullptr, *bin_off2 = nullptr;
     if (guarded) {
         a.refine_used = sc.get<uint8_t>((size_t)N);
-        bin2 = sc.get<uint8_t>((size_t)N);
         work2 = sc.get<int32_t>((size_t)N);
-        bin_off2 = sc.get<int32_t>(kNumBins + 1);
-        if (!a.refine_used || !bin2 || !work2 || !bin_off2) return SAM_ERR_OOM;
+        bin_off2 = sc.get<int32_t>(2);
+        if (!a.refine_used || !work2 || !bin_off2) return SAM_ERR_OOM;
         cudaMemsetAsync(a.refine_used, 0, (size_t)N, st);
     }
     if (!chunked) {
@@ -1511,7 +1509,7 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
                 return SAM_ERR_CUDA;
         }
     }
-    if (guarded && launch_refine_fallback(h, a, (int)N, bin, bin2, work2, bin_off2, nullptr, h->d_refine) != cudaSuccess)
+    if (guarded && launch_refine_fallback(h, a, (int)N, work2, bin_off2, h->d_refine) != cudaSuccess)
         return SAM_ERR_CUDA;
     // chunked host values were copied before the re-solves: their count comes
     // back with the final synchronisation, and re-solved columns are copied again
@@ -2303,12 +2301,9 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
     // re-solve of the columns that miss the accuracy target is captured too
     const bool autoref = precision == SAM_FP32_REFINE && refine_steps != 0;
     uint8_t *refine_used = autoref ? keep.get<uint8_t>((size_t)N) : nullptr;
-    uint8_t *bin_keep = autoref ? keep.get<uint8_t>((size_t)N) : nullptr;
-    uint8_t *bin2 = autoref ? keep.get<uint8_t>((size_t)N) : nullptr;
     int32_t *work2 = autoref ? keep.get<int32_t>((size_t)N) : nullptr;
     int32_t *bin_off2 = autoref ? keep.get<int32_t>(kNumBins + 1) : nullptr;
-    int32_t *wl_ws = autoref ? keep.get<int32_t>(2 * kNumBins) : nullptr;
-    if (autoref && (!refine_used || !bin_keep || !bin2 || !work2 || !bin_off2 || !wl_ws)) return SAM_ERR_OOM;
+    if (autoref && (!refine_used || !work2 || !bin_off2)) return SAM_ERR_OOM;
     // value sources: per-matrix pointers and CSC offsets
     std::vector<const double *> kptr(K), zptr(NT);
     std::vector<int64_t> koff(K + 1, 0), zoff(NT + 1, 0);
@@ -2330,7 +2325,6 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
     cudaMemcpyAsync(d_zptr, zptr.data(), sizeof(double *) * NT, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_koff, koff.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_zoff, zoff.data(), sizeof(int64_t) * (NT + 1), cudaMemcpyHostToDevice, st);
-    if (autoref) bin = bin_keep;  // the fallback pass reads the size classes at every replay
     ShadowTarget tg;
     tg.zcp = zcp;
     tg.zri = zri;
@@ -2394,8 +2388,7 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
                   cudaMemsetAsync(d_r2, 0, sizeof(double) * (size_t)N, cs) == cudaSuccess &&
                   (!autoref || cudaMemsetAsync(refine_used, 0, (size_t)N, cs) == cudaSuccess) &&
                   launch_lsq(h, precision, a) == cudaSuccess &&
-                  (!autoref || launch_refine_fallback(h, a, (int)N, bin, bin2, work2, bin_off2, wl_ws,
-                                                      h->d_refine) == cudaSuccess) &&
+                  (!autoref || launch_refine_fallback(h, a, (int)N, work2, bin_off2, h->d_refine) == cudaSuccess) &&
                   status_reduce(h, d_st, N, h->d_flag) == cudaSuccess &&
                   (!fro2 || segmented_sum_f64(h, d_r2, K, n, fro2, false, seg_work) == cudaSuccess);
         cudaGraph_t graph = nullptr;

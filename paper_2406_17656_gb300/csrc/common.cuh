@@ -50,6 +50,7 @@ constexpr int kStRefine = 100;
 constexpr int kAutoSteps = 2;
 constexpr double kAutoC = 4.0, kAutoTol = 1e-12, kFallbackTol = 1e-10;
 constexpr double kU32 = 5.9604644775390625e-8;  // unit roundoff of FP32, 2^-24
+constexpr double kNoise2 = 1e-28;  // |d|^2 / |m|^2 below which a correction is rounding noise of the FP64 residual
 
 // Source CSR of one map (device pointers) for the batch concatenation.
 struct CsrPtrs {
@@ -184,15 +185,17 @@ cudaError_t build_work_list(sam_handle h, int N, const uint8_t *bin, int32_t *wo
                             int32_t *ws = nullptr);
 // out[j] = bin[j] where colstat[j] == flag, else no size class
 cudaError_t flagged_bins(sam_handle h, int N, const uint8_t *bin, const int32_t *colstat, int32_t flag, uint8_t *out);
-// automatic refinement: FP64 re-solve of the columns the FP32 kernel flagged,
-// then the per-mode column counts (counts[kAutoSteps + 1], nullable)
-cudaError_t launch_refine_fallback(sam_handle h, const LsqArgs &args, int N, const uint8_t *bin, uint8_t *bin2,
-                                   int32_t *work2, int32_t *bin_off2, int32_t *ws, int64_t *counts);
+// guarded refinement: FP64 re-solve of the columns the FP32 kernel flagged
+// (list: int32[N] workspace, list_off: int32[2]), then the per-outcome
+// column counts (counts[kAutoSteps + 1], nullable)
+cudaError_t launch_refine_fallback(sam_handle h, const LsqArgs &args, int N, int32_t *list, int32_t *list_off,
+                                   int64_t *counts);
 
 // Least-squares launches for every size class.
 cudaError_t launch_lsq(sam_handle h, int precision, const LsqArgs &args);
-// the large class (any precision: solved in FP64)
-cudaError_t launch_lsq_big(sam_handle h, const LsqArgs &args, int bin);
+// the large class (any precision: solved in FP64); profile: time it as
+// size class `bin` with the handle's tracing events
+cudaError_t launch_lsq_big(sam_handle h, const LsqArgs &args, int bin, bool profile = true);
 // one size class (the items args.item_lo/item_hi select, else all of it)
 cudaError_t launch_lsq_bin(sam_handle h, int precision, const LsqArgs &args, int bin);
 cudaError_t launch_adjoint(sam_handle h, int precision, const LsqArgs &args);

@@ -108,6 +108,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
             mq[q] = to_f64<T>(x[q]);
             if (c < nJ) S.m[c] = mq[q];
         }
+        if constexpr (!FP64) {
+            // |m|^2 of the FP32 solution: the scale of the refinement's
+            // accuracy guard (kept in shared memory, not in a register)
+            float m2 = 0.f;
+#pragma unroll
+            for (int q = 0; q < JQ; ++q)
+                if (ll + q * P < nJ) m2 = fmaf(x[q], x[q], m2);
+            m2 = group_sum<P>(m2);
+            if (ll == 0) S.msq = m2;
+        }
         __syncwarp();
         double r2 = 0.0;
         bool need_final = true;
@@ -117,8 +127,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
             // with the stopping test below
             const bool autoref = args.refine_steps < 0;
             const int steps = autoref ? kAutoSteps : args.refine_steps;
-            double d1sq = 0.0;
-            int used = 0;
+            // automatic mode: this column takes the current step.  The loop
+            // is warp-uniform (the passes use shuffles), so a warp runs step
+            // 2 when any of its columns needs it, but a column that stopped
+            // after step 1 discards step 2's correction: its result does not
+            // depend on which columns share its warp
+            bool active = true;
             for (int step = 0; step < steps; ++step) {
                 // r = c - B m (FP64), g = B^T r (FP64), d = (R^T R)^{-1} g (FP32)
                 residual_rows<TL, false>(S, kcv, nI, ll);
@@ -130,58 +144,63 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
                     for (int q = 0; q < JQ; ++q) x[q] = to_tile<T>(g[q]);
                 }
                 C.normal_solve(S, x);
-                double dsq = 0.0, msq = 0.0;
+                float dsq = 0.f;
 #pragma unroll
                 for (int q = 0; q < JQ; ++q) {
                     const int c = ll + q * P;
                     if (c < nJ) {
-                        const double dq = to_f64<T>(x[q]);
-                        mq[q] += dq;
+                        const T xq = active ? x[q] : T(0);
+                        mq[q] += to_f64<T>(xq);
                         S.m[c] = mq[q];
-                        S.u.s.y[c] = x[q];
-                        dsq = fma(dq, dq, dsq);
-                        msq = fma(mq[q], mq[q], msq);
+                        S.u.s.y[c] = xq;  // (zero when the step is discarded: the final residual is r itself)
+                        dsq = fmaf(xq, xq, dsq);
                     }
                 }
                 __syncwarp();
-                used = step + 1;
                 dsq = group_sum<P>(dsq);
-                msq = group_sum<P>(msq);
+                const float msq = S.msq;
+                // Accuracy guard.  CSNE contracts the error e_s by a factor
+                // rho ~ u_32 kappa(B)^2 per step, so e_s <= rho / (1 - rho) |d_s|
+                // for rho < 1.  rho is estimated as the larger of u_32 kappa^2,
+                // with kappa estimated by max |R_kk| / min |R_kk| (a lower
+                // bound on kappa(B)), and, after step 1, kAutoC |d_1| / |m|
+                // (the correction itself is ~ u_32 kappa |m|), after later
+                // steps |d_s| / |d_{s-1}|.  A column whose predicted error is
+                // above kFallbackTol |m| (or whose rho is 1/2 or more) is
+                // re-solved in FP64.  The test is monotone in rho, so it is
+                // applied to each estimate in turn; it runs in FP32 on squared
+                // norms, with products only (estimates need no more, and FP64
+                // arithmetic costs GB300's narrow FP64 pipe dearly), |m| taken
+                // from the FP32 solution, and 1 - rho >= 1/2 used for the ratio
+                // estimates (conservative)
+                constexpr float kTol = (float)kFallbackTol, kTol2 = kTol * kTol, kC = (float)kAutoC;
+                const float rk = (float)kU32 * S.kap2;  // u_32 kappa^2
+                bool miss = !(rk < 0.5f) || rk * rk * dsq > kTol2 * (1.f - rk) * (1.f - rk) * msq;
+                if (step == 0) {  // rho = kAutoC |d_1| / |m|
+                    miss = miss || 4.f * kC * kC * dsq >= msq || 2.f * kC * dsq > kTol * msq;
+                } else if (dsq > (float)kNoise2 * msq) {
+                    // rho = |d_s| / |d_{s-1}|, unless the corrections are at the
+                    // rounding level of the FP64 residual (their ratio is noise)
+                    const float dprev2 = S.dprev2;
+                    miss = miss || 4.f * dsq >= dprev2 || 4.f * dsq * dsq > kTol2 * msq * dprev2;
+                }
+                __syncwarp();
+                if (C.ll == 0) S.dprev2 = dsq;  // (shared memory: no register across the next step)
                 if (autoref) {
-                    // CSNE contracts the error by a factor rho ~ u_32 kappa^2 per step.
-                    // After step 1 the error is ~ rho |d_1| with rho <~ kAutoC |d_1| / |m|:
-                    // stop when kAutoC |d_1|^2 <= kAutoTol |m|^2.  After step 2,
-                    // rho ~ |d_2| / |d_1|; a predicted error |d_2|^2 / |d_1| above
-                    // kFallbackTol |m| sends the column to the FP64 solve.
-                    bool more = false;
+                    // automatic: a second step when step 1 left the column above
+                    // kAutoTol (kAutoC |d_1|^2 > kAutoTol |m|^2) or predicted above
+                    // the target; after it, a miss falls back to FP64
                     if (step == 0) {
-                        more = kAutoC * dsq > kAutoTol * msq;
-                        d1sq = dsq;
+                        active = kC * dsq > (float)kAutoTol * msq || miss;
+                        if (!__any_sync(0xffffffffu, active)) break;  // warp-uniform
                     } else {
-                        // (max: a growing correction is judged by itself)
-                        fallback = dsq * dsq > kFallbackTol * kFallbackTol * msq * fmax(d1sq, dsq);
+                        fallback = active && miss;
                     }
-                    if (!__any_sync(0xffffffffu, more)) break;  // warp-uniform
                 } else if (step == steps - 1) {
-                    // the same accuracy guard after the last of a fixed number of
-                    // steps: the predicted error rho |d_s| above kFallbackTol |m|
-                    // sends the column to the FP64 solve.  After two or more steps
-                    // rho ~ |d_s| / |d_{s-1}|; after one, rho is the larger of
-                    // kAutoC |d_1| / |m| and u_32 kappa^2, with kappa estimated by
-                    // max |R_kk| / min |R_kk| (a lower bound on kappa(B))
-                    constexpr double kTol2 = kFallbackTol * kFallbackTol;
-                    if (steps >= 2) {
-                        fallback = dsq * dsq > kTol2 * msq * fmax(d1sq, dsq);
-                    } else {
-                        const double k2 = C.rkk_max2 / C.rkk_min2;  // kappa^2
-                        const double u2k4 = kU32 * kU32 * k2 * k2;  // (u_32 kappa^2)^2
-                        fallback = kAutoC * kAutoC * dsq * dsq > kTol2 * msq * msq || u2k4 * dsq > kTol2 * msq;
-                    }
-                } else {
-                    d1sq = dsq;
+                    fallback = miss;
                 }
             }
-            if (used > 0) {
+            if (steps > 0) {
                 // final residual r - B d: B d in FP32 from the rounded
                 // entries (its error, ~1e-7 |B d|, multiplies a correction
                 // that is already ~1e-6 of |c|), subtracted and squared in FP64
@@ -225,8 +244,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
                 need_final = false;
             }
             if (C.valid && ll == 0 && args.refine_used)
-                args.refine_used[C.jj] =
-                    (uint8_t)((fallback && C.status == kStOk) ? kAutoSteps + 1 : (used < kAutoSteps ? used : kAutoSteps));
+                args.refine_used[C.jj] = (uint8_t)((fallback && C.status == kStOk)
+                                                       ? kAutoSteps + 1
+                                                       : (autoref ? (active ? 2 : 1) : (steps < 2 ? steps : 2)));
         }
         if (need_final) {
             r2 = residual_rows<TL>(S, kcv, nI, ll);
@@ -311,37 +331,66 @@ cudaError_t launch_lsq(sam_handle h, int precision, const LsqArgs &args) {
 }
 
 namespace {
-// columns that took s = 1..kAutoSteps steps, and FP64 re-solves
+// columns that took s = 1..kAutoSteps steps, and FP64 re-solves: per-thread
+// counts, summed over the warp by shuffles, one shared atomic per warp
 __global__ void refine_count_kernel(int64_t N, const uint8_t *used, unsigned long long *counts) {
     __shared__ unsigned long long sh[kAutoSteps + 1];
     if (threadIdx.x <= kAutoSteps) sh[threadIdx.x] = 0ull;
     __syncthreads();
+    unsigned c[kAutoSteps + 1] = {};
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
         const int u = used[j];
-        if (u >= 1 && u <= kAutoSteps + 1) atomicAdd(&sh[u - 1], 1ull);
+#pragma unroll
+        for (int v = 0; v <= kAutoSteps; ++v) c[v] += (u == v + 1) ? 1u : 0u;
+    }
+#pragma unroll
+    for (int v = 0; v <= kAutoSteps; ++v) {
+        unsigned t = c[v];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0 && t) atomicAdd(&sh[v], (unsigned long long)t);
     }
     __syncthreads();
     if (threadIdx.x <= kAutoSteps && sh[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sh[threadIdx.x]);
 }
+
+// the columns flagged for the FP64 re-solve, in any order, into list;
+// off[1] receives their number (off[0] = 0: the list as a work-list range)
+__global__ void flag_list_kernel(int N, const int32_t *colstat, int32_t *list, int32_t *off) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool f = j < N && colstat[j] == kStRefine;
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&off[1], __popc(m));
+    base = __shfl_sync(m, base, leader);
+    if (f) list[base + __popc(m & ((1u << lane) - 1u))] = j;
+}
 }  // namespace
 
-cudaError_t launch_refine_fallback(sam_handle h, const LsqArgs &args, int N, const uint8_t *bin, uint8_t *bin2,
-                                   int32_t *work2, int32_t *bin_off2, int32_t *ws, int64_t *counts) {
-    cudaError_t e = flagged_bins(h, N, bin, args.colstat, kStRefine, bin2);
+cudaError_t launch_refine_fallback(sam_handle h, const LsqArgs &args, int N, int32_t *list, int32_t *list_off,
+                                   int64_t *counts) {
+    cudaStream_t st = handle_stream(h);
+    cudaError_t e = cudaMemsetAsync(list_off, 0, sizeof(int32_t) * 2, st);
     if (e != cudaSuccess) return e;
-    if ((e = build_work_list(h, N, bin2, work2, bin_off2, ws)) != cudaSuccess) return e;
+    if (N > 0) {
+        flag_list_kernel<<<(N + 255) / 256, 256, 0, st>>>(N, args.colstat, list, list_off);
+        count_launch(h);
+    }
+    // every flagged column, whatever its size class, by the FP64 kernel of
+    // the large class (results do not depend on the order of the list)
     LsqArgs a = args;
-    a.work = work2;
-    a.bin_off = bin_off2;
-    if ((e = launch_lsq(h, SAM_FP64, a)) != cudaSuccess) return e;
+    a.work = list;
+    a.bin_off = list_off;
+    a.item_lo = a.item_hi = 0;
+    if ((e = launch_lsq_big(h, a, 0, false)) != cudaSuccess) return e;
     if (counts) {
-        if ((e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * (kAutoSteps + 1), handle_stream(h))) != cudaSuccess)
-            return e;
+        if ((e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * (kAutoSteps + 1), st)) != cudaSuccess) return e;
         int blocks = (N + 255) / 256;
         if (blocks > handle_sms(h) * 4) blocks = handle_sms(h) * 4;
         if (blocks < 1) blocks = 1;
-        refine_count_kernel<<<blocks, 256, 0, handle_stream(h)>>>(N, args.refine_used,
-                                                                  reinterpret_cast<unsigned long long *>(counts));
+        refine_count_kernel<<<blocks, 256, 0, st>>>(N, args.refine_used, reinterpret_cast<unsigned long long *>(counts));
         count_launch(h);
     }
     return cudaGetLastError();

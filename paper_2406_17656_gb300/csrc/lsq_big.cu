@@ -318,14 +318,14 @@ __global__ void __launch_bounds__(kBigThreads, 1) lsq_big_kernel(LsqArgs args, i
 
 }  // namespace
 
-cudaError_t launch_lsq_big(sam_handle h, const LsqArgs &args, int bin) {
+cudaError_t launch_lsq_big(sam_handle h, const LsqArgs &args, int bin, bool profile) {
     const size_t smem = sizeof(BigHdr) + sizeof(double) * (size_t)kBigTileDoubles;
-    cudaError_t e = cudaFuncSetAttribute(lsq_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = cudaFuncSetAttribute(lsq_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    profile_begin(h, bin);
+    if (profile) profile_begin(h, bin);
     lsq_big_kernel<<<handle_sms(h), kBigThreads, smem, handle_stream(h)>>>(args, bin);
     count_launch(h);
-    profile_end(h, bin);
+    if (profile) profile_end(h, bin);
     return cudaGetLastError();
 }
 

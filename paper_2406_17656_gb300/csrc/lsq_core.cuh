@@ -52,6 +52,9 @@ struct ProbSmem {
     double c[TL::MAXI];
     double m[TL::MAXJ];
     double lam[TL::MAXJ];  // adjoint multipliers (adjoint only)
+    float kap2;            // max R_kk^2 / min R_kk^2 (Column::factor): a cheap lower bound on kappa(B)^2
+    float dprev2;          // |d|^2 of the previous refinement step (accuracy guard)
+    float msq;             // |m|^2 of the FP32 solution (accuracy guard)
     unsigned char locr[TL::NBCAP];
     union U {
         // [B c], only until registers are loaded (see tile_pos)
@@ -405,7 +408,6 @@ struct Column {
     int status;
     int colA[JQ], clen[JQ], colB[JQ];
     double out2;
-    double rkk_max2, rkk_min2;  // largest and smallest R_kk^2 (factor): a cheap lower bound on kappa(B)^2
 
     __device__ __forceinline__ void begin(const LsqArgs &args, int item, int total, const int32_t *work) {
         begin_at(args, item, total, item < total ? work[item] : 0);
@@ -640,25 +642,28 @@ struct Column {
             }
         __syncwarp();
         int st = kStOk;
-        double rmax2 = 0.0, rmin2 = DBL_MAX;
+        float rmax = 0.f, rmin = FLT_MAX;  // |R_kk| range, in FP32 (an estimate only)
         for (int k = ll; k < nJ; k += P) {
             const T rkk = S.u.s.R[k * TL::RSTR + k];
             const double d = to_f64<T>(rkk);
             if (!finite64(d)) st = max(st, (int)kStNonfinite);
             else if (d == 0.0) st = max(st, (int)kStRank);
-            rmax2 = fmax(rmax2, d * d);
-            rmin2 = fmin(rmin2, d * d);
+            const float a = fabsf((float)rkk);
+            rmax = fmaxf(rmax, a);
+            rmin = fminf(rmin, a);
             S.u.s.dinv[k] = T(1) / rkk;
         }
         status = max(status, st);
 #pragma unroll
         for (int o = 1; o < P; o <<= 1) {
             status = max(status, shfl_xor(status, o));
-            rmax2 = fmax(rmax2, shfl_xor(rmax2, o));
-            rmin2 = fmin(rmin2, shfl_xor(rmin2, o));
+            rmax = fmaxf(rmax, shfl_xor(rmax, o));
+            rmin = fminf(rmin, shfl_xor(rmin, o));
         }
-        rkk_max2 = rmax2;
-        rkk_min2 = rmin2;
+        if (ll == 0) {  // kept in shared memory: no register across the solves
+            const float kap = rmax / rmin;
+            S.kap2 = kap * kap;
+        }
         if (status != kStOk) nJ = 0;
     }
 
