@@ -55,7 +55,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) adjoint_kernel(LsqArgs ar
         T a[RS][CS];
         C.load_tile(S, a);
         C.build_rows(S);
+        C.park(S);
         C.factor(S, a);
+        C.unpark(S);
         const int nJ = C.nJ, nI = C.nI;
         // ---- m (the forward map) and the incoming gradient g
         double mq[JQ], gq[JQ];

@@ -69,18 +69,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
     const int w0 = args.bin_off[bin] + (args.item_hi > 0 ? args.item_lo : 0);
     const int total = args.item_hi > 0 ? args.item_hi - args.item_lo : args.bin_off[bin + 1] - w0;
     const int32_t *work = args.work + w0;
-    const double *kcv = args.kcv;
 
     // static round-robin over the resident warps (columns of a size class
     // cost about the same): the next work item is known, and its column
     // index is loaded one iteration ahead, so no atomic counter and no work
-    // lookup sit at the head of an iteration's dependent loads
-    const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock * PPW;
-    int64_t base = ((int64_t)blockIdx.x * kWarpsPerBlock + warp) * PPW;
+    // lookup sit at the head of an iteration's dependent loads (32-bit
+    // indices: a class holds fewer than 2^31 - one wave of items)
+    const int stride = gridDim.x * kWarpsPerBlock * PPW;
+    int base = (blockIdx.x * kWarpsPerBlock + warp) * PPW;
     int jj_next = (base + lane / P < total) ? work[base + lane / P] : 0;
     for (int iter = 0; iter < (1 << 30); ++iter) {
         if (base >= total) break;
-        const int item = (int)(base + lane / P);
+        const int item = base + lane / P;
         const int jj_cur = jj_next;
         base += stride;
         jj_next = (base + lane / P < total) ? work[base + lane / P] : 0;
@@ -91,7 +91,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
         T a[RS][CS];
         C.load_tile(S, a);
         C.build_rows(S);
+        C.park(S);
         C.factor(S, a);
+        C.unpark(S);
         const int nJ = C.nJ, nI = C.nI;
         // ---- m0 = R^{-1} (Q^T c)(1:nJ)
         T x[JQ];
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
             bool active = true;
             for (int step = 0; step < steps; ++step) {
                 // r = c - B m (FP64), g = B^T r (FP64), d = (R^T R)^{-1} g (FP32)
-                residual_rows<TL, false>(S, kcv, nI, ll);
+                residual_rows<TL, false>(S, args.kcv, nI, ll);
                 __syncwarp();
                 {
                     double g[JQ];
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
                                                        : (autoref ? (active ? 2 : 1) : (steps < 2 ? steps : 2)));
         }
         if (need_final) {
-            r2 = residual_rows<TL>(S, kcv, nI, ll);
+            r2 = residual_rows<TL>(S, args.kcv, nI, ll);
             r2 = group_sum<P>(r2);
         }
         // ---- outputs

@@ -46,8 +46,11 @@ template <class TL>
 struct ProbSmem {
     using T = typename TL::T;
     int I[TL::MAXI];
-    int colA[TL::MAXJ];
-    int colB[TL::MAXJ + 1];
+    // column state parked across the QR (Column::park): every lane's colA and
+    // (colB << 16 | clen), and the group's scalars
+    int park[2 * TL::P * TL::JQ];
+    int park_i[8];
+    long long park_l[2];
     unsigned mask[TL::MAXI];
     double c[TL::MAXI];
     double m[TL::MAXJ];
@@ -548,6 +551,48 @@ struct Column {
         }
         out2 = group_sum<P>(out2);
         __syncwarp();
+    }
+
+    // The column's state that the QR does not use, parked in shared memory
+    // while the QR tile holds the registers, and taken back after it.
+    __device__ __forceinline__ void park(ProbSmem<TL> &S) {
+#pragma unroll
+        for (int q = 0; q < JQ; ++q) {
+            S.park[ll + q * P] = colA[q];
+            S.park[P * JQ + ll + q * P] = (colB[q] << 16) | clen[q];
+        }
+        if (ll == 0) {
+            S.park_i[0] = jj;
+            S.park_i[1] = js;
+            S.park_i[2] = jb;
+            S.park_i[3] = nI;
+            S.park_i[4] = zb;
+            S.park_i[5] = ze;
+            S.park_i[6] = zro;
+            S.park_i[7] = roff;
+            S.park_l[0] = poff;
+            S.park_l[1] = __double_as_longlong(out2);
+        }
+    }
+    __device__ __forceinline__ void unpark(ProbSmem<TL> &S) {
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < JQ; ++q) {
+            colA[q] = S.park[ll + q * P];
+            const int w = S.park[P * JQ + ll + q * P];
+            colB[q] = w >> 16;
+            clen[q] = w & 0xffff;
+        }
+        jj = S.park_i[0];
+        js = S.park_i[1];
+        jb = S.park_i[2];
+        nI = S.park_i[3];
+        zb = S.park_i[4];
+        ze = S.park_i[5];
+        zro = S.park_i[6];
+        roff = S.park_i[7];
+        poff = S.park_l[0];
+        out2 = __longlong_as_double(S.park_l[1]);
     }
 
     // position in the map (CSR order of the batch) of pattern entry c
