@@ -87,43 +87,72 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) adjoint_kernel(LsqArgs ar
         for (int q = 0; q < JQ; ++q) lq[q] = to_f64<T>(x[q]);
         const int steps = FP64 ? 0 : args.refine_steps;
         for (int step = 0; step <= steps; ++step) {
-            // w = B lambda (FP64) over the row-major entry lists
+            if (step == 0 || step < steps) {
+                // w = B lambda (FP64) over the row-major entry lists
 #pragma unroll
-            for (int q = 0; q < JQ; ++q) {
-                const int c = ll + q * P;
-                if (c < nJ) S.lam[c] = lq[q];
-            }
-            __syncwarp();
-#pragma unroll
-            for (int q = 0; q < IQ; ++q) {
-                const int i = ll + q * P;
-                if (i < nI) {
-                    double wi = 0.0;
-                    const int pe = S.u.s.rowstart[i + 1];
-                    for (int p = S.u.s.rowstart[i]; p < pe; ++p) wi = fma(kcv[S.u.s.rowent[p]], S.lam[S.u.s.rowcol[p]], wi);
-                    S.u.s.w[i] = wi;
+                for (int q = 0; q < JQ; ++q) {
+                    const int c = ll + q * P;
+                    if (c < nJ) S.lam[c] = lq[q];
                 }
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < IQ; ++q) {
+                    const int i = ll + q * P;
+                    if (i < nI) {
+                        double wi = 0.0;
+                        const int pe = S.u.s.rowstart[i + 1];
+                        for (int p = S.u.s.rowstart[i]; p < pe; ++p)
+                            wi = fma(kcv[S.u.s.rowent[p]], S.lam[S.u.s.rowcol[p]], wi);
+                        S.u.s.w[i] = wi;
+                    }
+                }
+                __syncwarp();
+            } else if constexpr (!FP64) {
+                // after the last correction d: w += B d with the small product
+                // B d in FP32 from the rounded entries (its error, ~1e-7 |B d|,
+                // multiplies a correction already ~1e-6 of |lambda|), added in
+                // FP64, as the forward kernel forms its final residual
+#pragma unroll
+                for (int q = 0; q < IQ; ++q) {
+                    const int i = ll + q * P;
+                    if (i < nI) {
+                        float v = 0.f;
+                        const int pe = S.u.s.rowstart[i + 1];
+                        for (int p = S.u.s.rowstart[i]; p < pe; ++p)
+                            v = fmaf(args.kcv32[S.u.s.rowent[p]], (float)S.u.s.y[S.u.s.rowcol[p]], v);
+                        S.u.s.w[i] += to_f64<float>(v);
+                    }
+                }
+                __syncwarp();
             }
-            __syncwarp();
             if (step == steps) break;
-            // correction: lambda += (R^T R)^{-1} (g - B^T w)
+            // correction: lambda += d = (R^T R)^{-1} (g - B^T w)
 #pragma unroll
             for (int q = 0; q < JQ; ++q) x[q] = to_tile<T>(gq[q] - C.bt_times(args, S, S.u.s.w, q));
             C.normal_solve(S, x);
 #pragma unroll
-            for (int q = 0; q < JQ; ++q) lq[q] += to_f64<T>(x[q]);
+            for (int q = 0; q < JQ; ++q) {
+                const int c = ll + q * P;
+                lq[q] += to_f64<T>(x[q]);
+                if (c < nJ) S.u.s.y[c] = x[q];
+            }
+            __syncwarp();
         }
         if (C.valid && C.status == kStOk) {
             // ---- dL/dB entries of this column's block, and where each block starts
+            // dL/dB(i, c) = r_i lambda_c - w_i m_c - 2 rho r_i m_c
+            //            = r_i (lambda_c - 2 rho m_c) - w_i m_c: two FP64
+            // operations per entry, the column factor formed once
             const int64_t blk = args.dB_off[C.jj];
 #pragma unroll
             for (int q = 0; q < JQ; ++q) {
                 const int c = ll + q * P;
                 if (c < nJ) {
+                    const double ac = fma(-2.0 * rho, mq[q], lq[q]);
+                    const double nm = -mq[q];
                     for (int p = 0; p < C.clen[q]; ++p) {
                         const int i = S.locr[C.colB[q] + p];
-                        const double ri = S.u.s.r[i], wi = S.u.s.w[i];
-                        args.dB[blk + C.colB[q] + p] = ri * lq[q] - wi * mq[q] - 2.0 * rho * ri * mq[q];
+                        args.dB[blk + C.colB[q] + p] = fma(S.u.s.r[i], ac, S.u.s.w[i] * nm);
                     }
                     const int t = C.map_pos(args, c);
                     args.dbase[t] = blk + C.colB[q];
