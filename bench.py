@@ -157,15 +157,19 @@ def column_sizes(mats, level):
     return out
 
 
-def bin_of(I, J, nB, classes=None):
-    """Size class of every column (the library's rule: the first class the
-    column fits), -1 where none fits."""
+def bin_of(I, J, nB, classes=None, schedule=None):
+    """Size class that solves every column (the library's rule: the first
+    class the column fits, then the handle's bin schedule), -1 where none
+    fits."""
     c = classes or size_classes()
     b = np.full(I.shape, -1)
     for q in range(len(c["max_rows"]) - 1, -1, -1):
         ok = ((I <= c["max_rows"][q]) & (J <= c["max_cols"][q]) & (nB <= c["max_entries"][q]) &
               (I * (J + 1) <= c["max_tile"][q]) & (I >= J))
         b[ok] = q
+    if schedule is not None:
+        to = np.asarray(list(schedule) + [-1])
+        b = to[b]
     return b
 
 
@@ -183,6 +187,87 @@ def algorithmic_flops(I, J, nB, precision, steps):
     f32 = qr + steps * (4 * m * n - n * n)
     f64 = steps * (2 * nB + m)
     return f32, f64
+
+
+def adjoint_algorithmic_flops(I, J, nB, steps):
+    """Algorithmic work of the adjoint of one column (m = |I_j|, n = |J_j|,
+    b = nnz(B_j), s refinement steps), as the adjoint kernel computes it:
+    FP32 the recomputed QR of [B c] (the forward's formula) and s + 1
+    solves with R^T R (2 n^2 each) plus, after the last correction, its
+    product B d (2 b); FP64 the residual r = c - B m (2 b + m), the products
+    w = B lambda before each correction (2 b each, s of them, at least one),
+    B^T w per correction (2 b each), the dL/dB entries (3 b: a product and
+    an FMA per entry) and dL/dc (m).  Returns (FP32, FP64) flops per column."""
+    m, n, b = I.astype(np.float64), J.astype(np.float64), nB.astype(np.float64)
+    qr = 2 * n * n * (m - n / 3) + (4 * m * n - 2 * n * n) + n * n
+    f32 = qr + (steps + 1) * 2 * n * n + (2 * b if steps > 0 else 0.0)
+    f64 = (2 * b + m) + max(steps, 1) * 2 * b + steps * 2 * b + 3 * b + m
+    return f32, f64
+
+
+def adjoint_roofline(mats, level, steps, ms):
+    """Roofline of a whole adjoint call over the maps of `mats`: the slower of
+    its algorithmic FP32 flops at the FP32 peak and FP64 flops at the FP64
+    peak (adjoint_algorithmic_flops summed over every column), over the
+    measured call time."""
+    f32 = f64 = 0.0
+    seen = {}
+    for m in mats:
+        key = (m.indptr.tobytes(), m.indices.tobytes())
+        if key not in seen:
+            I, J, nB = column_sizes([m], level)[0]
+            a, b = adjoint_algorithmic_flops(I, J, nB, steps)
+            seen[key] = (float(np.sum(a)), float(np.sum(b)))
+        f32, f64 = f32 + seen[key][0], f64 + seen[key][1]
+    t32, t64 = f32 / PEAK_FP32, f64 / PEAK_FP64
+    bound = "fp64" if t64 >= t32 else "fp32"
+    t_roof = max(t32, t64)
+    ach = (f64 if bound == "fp64" else f32) / (ms * 1e-3)
+    return {"bound": "alu (%s pipe)" % bound, "achieved": ach / 1e12,
+            "peak": (PEAK_FP64 if bound == "fp64" else PEAK_FP32) / 1e12, "unit": "TFLOP/s",
+            "frac": t_roof / (ms * 1e-3), "fp32_flops": f32, "fp64_flops": f64, "ms": ms}
+
+
+def error_stats(torch, ci, offs, v, vref, n):
+    """v against vref (the same map structures, concatenated with offsets
+    offs; ci the column index of every entry): the largest whole-map relative
+    Frobenius error and the largest per-column relative error over all
+    columns of all maps.  Reduced on the device."""
+    max_fro = max_col = 0.0
+    for k in range(len(offs) - 1):
+        a, b = v[offs[k]:offs[k + 1]], vref[offs[k]:offs[k + 1]]
+        c = ci[offs[k]:offs[k + 1]].long()
+        d = (a - b) ** 2
+        max_fro = max(max_fro, float(torch.sqrt(d.sum() / (b * b).sum())))
+        d2 = torch.zeros(n, dtype=torch.float64, device=v.device).index_add_(0, c, d)
+        w2 = torch.zeros(n, dtype=torch.float64, device=v.device).index_add_(0, c, b * b)
+        col = torch.where(w2 > 0, torch.sqrt(d2 / w2.clamp_min(1e-300)), torch.sqrt(d2) * float("inf"))
+        col = torch.nan_to_num(col, nan=0.0)
+        max_col = max(max_col, float(col.max()))
+    return max_fro, max_col
+
+
+def oracle_column_sample(ak, a0, level, n, ip, ix, v, ncols, seed):
+    """Per-column relative errors of the GPU map (CSR ip, ix, v; host) against
+    the FP64 oracle on `ncols` sampled columns (plus the first and last):
+    (max per-column error, relative Frobenius error over the sample)."""
+    import scipy.sparse as sp
+
+    import oracle
+
+    cp, ri = oracle.pattern(ak, level)
+    rng = np.random.default_rng(seed)
+    cols = np.unique(np.concatenate([rng.choice(n, ncols, replace=False), [0, n - 1]])).astype(np.int32)
+    ref = oracle.build_cols(ak, a0, cp, ri, cols)
+    m = sp.csr_matrix((v, ix, ip), shape=(n, n)).tocsc()
+    m.sort_indices()
+    errs, num, den = [], 0.0, 0.0
+    for j in cols:
+        a, b = m.data[cp[j]:cp[j + 1]], ref["mval"][cp[j]:cp[j + 1]]
+        d2, w2 = float(np.sum((a - b) ** 2)), float(np.sum(b * b))
+        errs.append(np.sqrt(d2 / w2) if w2 > 0 else (0.0 if d2 == 0 else float("inf")))
+        num, den = num + d2, den + w2
+    return float(max(errs)), float(np.sqrt(num / den)), len(cols)
 
 
 def measured_hbm_gbs() -> float:
@@ -565,6 +650,7 @@ def config_figures(h, sam, torch, dev, stream, nsteps=7):
 
     out = {}
     saved_variants = h.sam_get_tile_variants()
+    saved_schedule = h.sam_get_bin_schedule()
 
     def tune(aks, a0, level, steps):
         """sam_tune on this workload's own patterns (the tile shape per size
@@ -573,7 +659,7 @@ def config_figures(h, sam, torch, dev, stream, nsteps=7):
         v = h.sam_tune(aks, a0, ps, "fp32r", steps)
         for p in ps:
             p.destroy()
-        return {"tile_variants": list(v)}
+        return {"tile_variants": list(v), "bin_schedule": h.sam_get_bin_schedule()}
 
     # config 1: 5-point Poisson 32^2, A_1 = A_0 + diag, level 1, plain FP64 single build
     seq = W.config1()
@@ -597,67 +683,104 @@ def config_figures(h, sam, torch, dev, stream, nsteps=7):
     line("poisson5_32x32_seq2_level1_fp64", 2 * aks[0].n, 2, ms1,
          {"graph_replay_columns_per_s": 2 * aks[0].n / (msp1 * 1e-3), "graph_replay_ms": msp1},
          roof=(seq.mats, 1, "fp64", 0), orc=(seq.mats[1], seq.mats[0], 1))
+    def build_step(aks, tgt, level, precision, steps):
+        """One step of the path: level-L patterns of every A_k and the batched
+        maps with the per-map residuals."""
+        def fn():
+            ps = h.sam_pattern_build_batched(aks, level)
+            h.sam_build_batched(aks, tgt, ps, precision, steps, want_fro=True)
+            for p in ps:
+                p.destroy()
+        return fn
+
+    def accuracy(aks, tgt, level, steps, n, ms32, host_pair, nsample=300, seed=0):
+        """The plain FP64 GPU build of the same maps (step time, speed-up of FP32
+        + refinement over it) and the FP32 + refinement maps' errors against it
+        (largest whole-map relative Frobenius error and largest per-column
+        relative error, all maps) and against the FP64 oracle (sampled columns
+        of the last map); the guard's outcome counts."""
+        ps = h.sam_pattern_build_batched(aks, level)
+        offs, rp, ci, v32, _ = h.sam_build_batched(aks, tgt, ps, "fp32r", steps)
+        one, two, fp64 = h.sam_refine_stats()
+        _, _, _, v64, _ = h.sam_build_batched(aks, tgt, ps, "fp64", 0, offsets=offs)
+        for p in ps:
+            p.destroy()
+        fro, col = error_stats(torch, ci, offs, v32, v64, n)
+        k = len(aks) - 1
+        ak_h, a0_h = host_pair
+        ocol, ofro, ncols = oracle_column_sample(ak_h, a0_h, level, n, rp[k * (n + 1):(k + 1) * (n + 1)].cpu().numpy(),
+                                                 ci[offs[k]:offs[k + 1]].cpu().numpy(),
+                                                 v32[offs[k]:offs[k + 1]].cpu().numpy(), nsample, seed)
+        del v32, v64, rp, ci
+        ms64 = timed(build_step(aks, tgt, level, "fp64", 0), 3)
+        return {"fp64_ms_per_step": ms64, "fp64_columns_per_s": len(aks) * n / (ms64 * 1e-3),
+                "speedup_fp32r_vs_fp64": ms64 / ms32, "max_rel_fro_vs_fp64_gpu": fro,
+                "max_col_rel_err_vs_fp64_gpu": col, "sample_max_col_rel_err_vs_oracle": ocol,
+                "sample_rel_fro_vs_oracle": ofro, "oracle_sample_columns": ncols,
+                "refine_outcomes": {"one_step": one, "two_steps": two, "fp64_solved": fp64}}
+
+    def plan_replay(aks, tgt, level, steps, nt):
+        """The numeric rebuild replayed from its captured CUDA graph
+        (patterns fixed; every replay re-reads the values)."""
+        ps = h.sam_pattern_build_batched(aks, level)
+        plan = h.sam_plan_create(aks, tgt, ps, "fp32r", steps)
+        for p in ps:
+            p.destroy()
+        ms = timed(plan.execute, nsteps)
+        launches = plan.launches()
+        plan.destroy()
+        return {"graph_replay_columns_per_s": nt / (ms * 1e-3), "graph_replay_ms": ms,
+                "graph_replay_launches": launches}
+
     # config 3: 7-point upwind 64^3, 20 maps, level 2, FP32 QR + 1 FP64 step
     seq = W.config3()
     aks = [sam.Csr.from_host(m, dev) for m in seq.mats]
-
-    def c3():
-        ps = h.sam_pattern_build_batched(aks, 2)
-        h.sam_build_batched(aks, aks[0], ps, "fp32r", 1, want_fro=True)
-        for p in ps:
-            p.destroy()
-
+    n3 = aks[0].n
     tv = tune(aks, aks[0], 2, 1)
-    line("upwind7_64cube_seq20_level2", len(aks) * aks[0].n, len(aks), timed(c3, nsteps), tv, roof=(seq.mats, 2, "fp32r", 1),
+    ms3 = timed(build_step(aks, aks[0], 2, "fp32r", 1), nsteps)
+    ms3a = timed(build_step(aks, aks[0], 2, "fp32r", "auto"), nsteps)
+    ex = {**tv, "auto_columns_per_s": len(aks) * n3 / (ms3a * 1e-3), "auto_ms_per_step": ms3a}
+    ex.update(plan_replay(aks, aks[0], 2, 1, len(aks) * n3))
+    ex.update(accuracy(aks, aks[0], 2, 1, n3, ms3, (seq.mats[-1], seq.mats[0]), seed=3))
+    line("upwind7_64cube_seq20_level2", len(aks) * n3, len(aks), ms3, ex, roof=(seq.mats, 2, "fp32r", 1),
          orc=(seq.mats[-1], seq.mats[0], 2))
     del aks
+    torch.cuda.empty_cache()
     # config 4: P1 FEM 512^2 cells, 16 maps whose pattern changes, level 2; direct and captured plan
     seq = W.config4()
     aks = [sam.Csr.from_host(m, dev) for m in seq.mats]
-
-    def c4():
-        ps = h.sam_pattern_build_batched(aks, 2)
-        h.sam_build_batched(aks, aks[0], ps, "fp32r", 1, want_fro=True)
-        for p in ps:
-            p.destroy()
-
+    n4 = aks[0].n
     tv = tune(aks, aks[0], 2, 1)
-    ms4 = timed(c4, nsteps)
-    ps = h.sam_pattern_build_batched(aks, 2)
-    plan = h.sam_plan_create(aks, aks[0], ps, "fp32r", 1)
-    for p in ps:
-        p.destroy()
-    msp = timed(plan.execute, nsteps)
-    plan.destroy()
-    cols4 = len(aks) * aks[0].n
-    line("p1_fem_512x512_seq16_level2", cols4, len(aks), ms4,
-         {"graph_replay_columns_per_s": cols4 / (msp * 1e-3), "graph_replay_ms": msp, **tv}, roof=(seq.mats, 2, "fp32r", 1),
+    ms4 = timed(build_step(aks, aks[0], 2, "fp32r", 1), nsteps)
+    cols4 = len(aks) * n4
+    ex = {**tv, **plan_replay(aks, aks[0], 2, 1, cols4)}
+    ex.update(accuracy(aks, aks[0], 2, 1, n4, ms4, (seq.mats[-1], seq.mats[0]), seed=4))
+    line("p1_fem_512x512_seq16_level2", cols4, len(aks), ms4, ex, roof=(seq.mats, 2, "fp32r", 1),
          orc=(seq.mats[-1], seq.mats[0], 2))
     del aks
+    torch.cuda.empty_cache()
     # config 5: 32 independent (A_0, A_1) 512^2 pairs, level 1, forward (one target per map) and adjoint
     pairs = [W.config5_pair(b) for b in range(32)]
     a0s = [sam.Csr.from_host(p[0], dev) for p in pairs]
     a1s = [sam.Csr.from_host(p[1], dev) for p in pairs]
     n5 = a0s[0].n
-
-    def c5():
-        ps = h.sam_pattern_build_batched(a1s, 1)
-        h.sam_build_batched(a1s, a0s, ps, "fp32r", 2, want_fro=True)
-        for p in ps:
-            p.destroy()
-
     tv = tune(a1s, a0s[0], 1, 2)
-    ms5 = timed(c5, nsteps)
+    ms5 = timed(build_step(a1s, a0s, 1, "fp32r", 2), nsteps)
     ps = h.sam_pattern_build_batched(a1s, 1)
     offs, _, _, mv, _ = h.sam_build_batched(a1s, a0s, ps, "fp32r", 2)
     gbar = torch.randn(mv.numel(), dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(5))
     msb = timed(lambda: h.sam_build_backward_batched(a1s, a0s, ps, mv, gbar, "fp32r", 2, 1.0, offsets=offs), nsteps)
     for p in ps:
         p.destroy()
-    line("q1_pairs_512x512_x32_level1", 32 * n5, 32, ms5,
-         {"adjoint_columns_per_s": 32 * n5 / (msb * 1e-3), "adjoint_ms": msb, "refine_steps": 2, **tv},
+    del mv, gbar
+    ex = {"adjoint_columns_per_s": 32 * n5 / (msb * 1e-3), "adjoint_ms": msb, "refine_steps": 2, **tv}
+    ex["adjoint_roofline"] = adjoint_roofline([p[1] for p in pairs], 1, 2, msb)
+    ex.update(plan_replay(a1s, a0s, 1, 2, 32 * n5))
+    ex.update(accuracy(a1s, a0s, 1, 2, n5, ms5, (pairs[-1][1], pairs[-1][0]), seed=5))
+    line("q1_pairs_512x512_x32_level1", 32 * n5, 32, ms5, ex,
          roof=([p[1] for p in pairs], 1, "fp32r", 2), orc=(pairs[0][1], pairs[0][0], 1))
     h.sam_set_tile_variants(saved_variants)
+    h.sam_set_bin_schedule(saved_schedule)
     return out
 
 
@@ -838,6 +961,10 @@ def main():
     gpu_launches = int(launches_total)
 
     extra = {}
+    # the refinement guard's outcomes on the headline build (columns that kept
+    # their solution after one step, re-solved in FP64)
+    one, two, fp64c = h.sam_refine_stats()
+    extra["refine_outcomes"] = {"one_step": one, "two_steps": two, "fp64_solved": fp64c}
     # accuracy: FP32+refine against the FP64 GPU build (all columns) and the oracle (a sample, below)
     v32 = out[2].clone()
     if not args.quick:
@@ -845,11 +972,16 @@ def main():
         extra["fp64_columns_per_s"] = job_value(cols_per_step, world, ms64)
         extra["fp64_ms_per_step"] = ms64
         extra["speedup_fp32r_vs_fp64"] = value / extra["fp64_columns_per_s"]
-        errs = []
-        for k in range(K):
-            a, b = v32[offs[k]:offs[k + 1]], out64[2][offs64[k]:offs64[k + 1]]
-            errs.append(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)))
-        extra["max_rel_fro_vs_fp64_gpu"] = max(errs)
+        fro_e, col_e = error_stats(torch, out[1], offs, v32, out64[2], n)
+        extra["max_rel_fro_vs_fp64_gpu"] = fro_e
+        extra["max_col_rel_err_vs_fp64_gpu"] = col_e
+        del out64
+        # the automatic refinement mode on the same workload
+        msa, _, _, _ = timed(args.level, "fp32r", "auto", max(2, args.steps // 2), 1)
+        extra["auto_columns_per_s"] = job_value(cols_per_step, world, msa)
+        extra["auto_ms_per_step"] = msa
+        a1, a2, a3 = h.sam_refine_stats()
+        extra["auto_refine_outcomes"] = {"one_step": a1, "two_steps": a2, "fp64_solved": a3}
         ms1, _, _, _ = timed(1, "fp32r", args.refine, max(2, args.steps // 2), 1)
         extra["level1_columns_per_s"] = job_value(cols_per_step, world, ms1)
         extra["rel_residual_per_map"] = [float(f) / float(np.linalg.norm(a0h.data)) for f in fro]
@@ -902,6 +1034,7 @@ def main():
         ta = max_over_ranks(ta / na, world, dev)
         extra["adjoint_columns_per_s"] = job_value(cols_per_step, world, ta)
         extra["adjoint_ms"] = ta
+        extra["adjoint_roofline"] = adjoint_roofline(seq.mats, args.level, args.refine, ta)
         for p in pats:
             p.destroy()
 
@@ -951,10 +1084,11 @@ def main():
     # ---- roofline of the dominant kernel (largest least-squares size class)
     sizes = column_sizes(seq.mats, args.level)
     classes = size_classes()
+    schedule = h.sam_get_bin_schedule()
     dom = int(np.argmax(lsq_ms))
     f32 = f64 = gathered = 0.0
     for (I, J, nB) in sizes:
-        sel = bin_of(I, J, nB, classes) == dom
+        sel = bin_of(I, J, nB, classes, schedule) == dom
         a, b = algorithmic_flops(I[sel], J[sel], nB[sel], "fp32r", args.refine)
         f32 += float(np.sum(a))
         f64 += float(np.sum(b))
@@ -986,7 +1120,7 @@ def main():
             if (rec.get("kernel_sha256") == kernel_hash() and str(dom) in rec.get("bytes_per_column", {})
                     and rec.get("variant", {}).get(str(dom), 0) == variants[dom]):
                 # traffic per column from the capture, times this launch's columns
-                ncols = sum(int(np.sum(bin_of(I, J, nB, classes) == dom)) for (I, J, nB) in sizes)
+                ncols = sum(int(np.sum(bin_of(I, J, nB, classes, schedule) == dom)) for (I, J, nB) in sizes)
                 traffic = rec["bytes_per_column"][str(dom)] * ncols
         except Exception:
             traffic = None
@@ -1059,14 +1193,20 @@ def main():
             idx = np.concatenate([np.arange(cp[j], cp[j + 1]) for j in cols])
             extra["sample_rel_fro_vs_oracle"] = float(np.linalg.norm(m.data[idx] - ref["mval"][idx]) /
                                                       np.linalg.norm(ref["mval"][idx]))
+            cerr = [np.linalg.norm(m.data[cp[j]:cp[j + 1]] - ref["mval"][cp[j]:cp[j + 1]]) /
+                    np.linalg.norm(ref["mval"][cp[j]:cp[j + 1]]) for j in cols]
+            extra["max_col_rel_err_vs_oracle"] = float(max(cerr))
+            extra["oracle_sample_columns"] = int(len(cols))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": seq.name + "_seq%d_level%d" % (K, args.level), "n": n, "maps": K,
-                           "level": args.level, "precision": "fp32 Householder QR + %d FP64 CSNE step(s)" % args.refine,
-                           "columns_per_step": cols_per_step, "tile_variants": variants, "parallelism": "replicas" if world > 1 else "single",
+                           "level": args.level, "precision": "fp32 Householder QR + %d FP64 CSNE step(s), guarded (columns predicted above "
+                                                       "1e-10 re-solved in FP64)" % args.refine,
+                           "columns_per_step": cols_per_step, "tile_variants": variants,
+                           "bin_schedule": schedule, "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed between steps (256 MiB write outside the timed interval)"},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                         "ms_per_step_median": e2e_med, "ms_per_step_mean": e2e_mean, "steps": ne,

@@ -78,8 +78,9 @@ enum {
  * Corrected semi-normal-equation steps contract the error by
  * rho ~ u_32 kappa(B)^2 each, so the error after step s is at most
  * rho / (1 - rho) |d_s| for the correction d_s of that step.  rho is
- * estimated as the larger of u_32 kappa^2, with kappa estimated as
- * max |R_kk| / min |R_kk|, and 4 |d_1| / |m| after step 1 or
+ * estimated as the larger of 8 u_32 kappa^2, with kappa estimated as
+ * max |R_kk| / min |R_kk| (a lower bound on kappa(B), hence the factor 8),
+ * and 4 |d_1| / |m| after step 1 or
  * |d_s| / |d_{s-1}| after later steps.  Automatic mode takes step 2 when
  * 4 |d_1|^2 > 1e-12 |m|^2 or the prediction after step 1 misses; after the
  * last step (2 in automatic mode, s otherwise) a predicted error above
@@ -422,21 +423,31 @@ sam_status sam_build_backward_batched(sam_handle h, int K, const sam_csr *A_k, c
 
 /*
  * sam_tune -- autotuner (no counterpart in the paper, which fixes one kernel
- * shape).  For SAM_FP32_REFINE each size class has more than one register
- * tile shape (variant 0: the default; variant 1: one problem per 8 or 32
- * lanes with fewer register slots per lane).  The call runs the complete
- * batched build of the given problems (as sam_build_batched, outputs to
- * workspace it frees) once per variant plus one warm-up each, times every
- * size class's least-squares launch with CUDA events, and keeps the fastest
- * variant per size class in the handle; later builds on the handle use it.
- * Results of every variant satisfy the same accuracy bounds (they differ
- * only in rounding order).  cache_path (nullable): a text file with one line
- * per tuned family, keyed by device name, SM count, K, n, total nnz(S),
- * precision and refine_steps; a matching line is used without timing, and a
- * new choice is appended.  SAM_FP64 has one shape per class: returns SAM_OK
- * at once.  Synchronises the handle's stream.  Tracing counters of the
- * handle are left as they were.  Errors: those of sam_build_batched;
- * SAM_ERR_INVALID_ARG if cache_path cannot be opened for appending.
+ * shape).  It chooses, for SAM_FP32_REFINE builds on this handle:
+ *  - the register tile shape of each size class (variant 0: the default;
+ *    variant 1: one problem per 8 or 32 lanes with fewer register slots per
+ *    lane), and
+ *  - the bin schedule: which size class solves the columns of each natural
+ *    class (sam_set_bin_schedule); a small class can hand its columns to the
+ *    next larger register class, saving its launch and filling the larger
+ *    class's persistent wave.
+ * The call runs the complete batched build of the given problems (as
+ * sam_build_batched, outputs to workspace it frees): once to count the
+ * columns of every natural size class, then per variant and per candidate
+ * schedule one warm-up and three builds, timing every size class's
+ * least-squares launches with CUDA events.  The fastest variant per class
+ * is kept; then, from the smallest class up, folding a class into the next
+ * is kept when the summed launch time drops by 1% or more.  Results of every
+ * choice satisfy the same accuracy bounds (they differ only in rounding).
+ * cache_path (nullable): a text file with one line per tuned family, keyed by
+ * device name, SM count, K, n, total nnz(S), precision, refine_steps and the
+ * histogram of natural size classes (two families of equal sizes but
+ * different column sizes get their own lines); a matching line is used
+ * without timing, and a new choice is appended.  SAM_FP64 has one shape per
+ * class: returns SAM_OK at once.  Synchronises the handle's stream.  Tracing
+ * counters of the handle are left as they were.  Errors: those of
+ * sam_build_batched; SAM_ERR_INVALID_ARG if cache_path cannot be opened for
+ * appending.
  */
 sam_status sam_tune(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0, const sam_pattern *S,
                     int precision, int refine_steps, const char *cache_path);
@@ -450,6 +461,19 @@ sam_status sam_tune(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0,
  */
 sam_status sam_set_tile_variants(sam_handle h, const int *variants, int count);
 sam_status sam_get_tile_variants(sam_handle h, int *variants, int count);
+
+/*
+ * sam_set_bin_schedule / sam_get_bin_schedule -- the size class that solves
+ * the columns of each natural size class b (the first class they fit, see
+ * sam_size_classes): to[b] in [b, 4] for the register classes b = 0..4
+ * (a larger register tile always holds a smaller class's columns), to[5] = 5
+ * (count must be SAM_NUM_SIZE_CLASSES).  A new handle has to[b] = b;
+ * sam_tune chooses one.  Applies to later builds, plans and adjoints on the
+ * handle.  Set: returns SAM_ERR_INVALID_ARG, changing nothing, if an entry is
+ * out of range.
+ */
+sam_status sam_set_bin_schedule(sam_handle h, const int *to, int count);
+sam_status sam_get_bin_schedule(sam_handle h, int *to, int count);
 
 /*
  * sam_refine_stats -- outcome counts of the last guarded SAM_FP32_REFINE

@@ -40,6 +40,11 @@ struct sam_handle_t {
     int64_t lsq_n[sam::kNumBins] = {0};
     // FP32 tile shape per size class (sam_tune / sam_set_tile_variants)
     int variant[sam::kNumBins] = {0};
+    // bin schedule (sam_tune / sam_set_bin_schedule): identity by default
+    sam::BinSchedule sched = {{0, 1, 2, 3, 4, 5}};
+    // the tuner's record of the last build's columns per size class
+    bool record_hist = false;
+    int32_t *h_hist = nullptr;  // pinned [kNumBins + 1] work-list offsets
     // refinement outcomes of the last guarded build (automatic, or a fixed
     // number of steps >= 1): columns per outcome, and a pinned mirror
     int64_t *d_refine = nullptr;
@@ -133,6 +138,7 @@ int handle_sms(sam_handle h) { return h->sms; }
 int32_t *handle_flag(sam_handle h) { return h->d_flag; }
 void count_launch(sam_handle h, int n) { h->launches += n; }
 int handle_variant(sam_handle h, int bin) { return h->variant[bin]; }
+BinSchedule handle_schedule(sam_handle h) { return h->sched; }
 
 void profile_begin(sam_handle h, int bin) {
     if (!h->profiling) return;
@@ -850,26 +856,35 @@ std::string tune_key(sam_handle h, int K, int n, int64_t nnz, int precision, int
     return name + buf;
 }
 
-bool tune_lookup(const char *path, const std::string &key, int *v) {
+// A cache line: the key, then kNumBins tile variants and kNumBins entries of
+// the bin schedule.
+bool tune_lookup(const char *path, const std::string &key, int *v, int *to) {
     FILE *f = path ? fopen(path, "r") : nullptr;
     if (!f) return false;
-    char line[512];
+    char line[1024];
     bool found = false;
     while (fgets(line, sizeof(line), f)) {
         const size_t kl = key.size();
         if (strncmp(line, key.c_str(), kl) != 0 || line[kl] != ' ') continue;
-        int t[kNumBins];
+        int t[2 * kNumBins];
         const char *q = line + kl;
         bool ok = true;
-        for (int b = 0; b < kNumBins && ok; ++b) {
+        for (int b = 0; b < 2 * kNumBins && ok; ++b) {
             int used = 0;
             ok = sscanf(q, "%d%n", &t[b], &used) == 1;
             q += used;
         }
         if (!ok) continue;
-        for (int b = 0; b < kNumBins; ++b) ok = ok && t[b] >= 0 && t[b] < kTileVariants[b];
+        for (int b = 0; b < kNumBins; ++b) {
+            ok = ok && t[b] >= 0 && t[b] < kTileVariants[b];
+            const int d = t[kNumBins + b];
+            ok = ok && (b == kBinBig ? d == kBinBig : (d >= b && d < kRegBins));
+        }
         if (!ok) continue;
-        for (int b = 0; b < kNumBins; ++b) v[b] = t[b];
+        for (int b = 0; b < kNumBins; ++b) {
+            v[b] = t[b];
+            to[b] = t[kNumBins + b];
+        }
         found = true;  // the last matching line wins
     }
     fclose(f);
@@ -940,11 +955,13 @@ sam_status sam_create(sam_handle *out, void *cuda_stream) {
     if (cudaMalloc(&h->d_flag, sizeof(int32_t)) != cudaSuccess ||
         cudaMalloc(&h->d_refine, sizeof(int64_t) * (kAutoSteps + 1)) != cudaSuccess ||
         cudaMallocHost(&h->h_flag, sizeof(int32_t) * (2 + kNumBins)) != cudaSuccess ||
-        cudaMallocHost(&h->h_refine, sizeof(int64_t) * (kAutoSteps + 1)) != cudaSuccess) {
+        cudaMallocHost(&h->h_refine, sizeof(int64_t) * (kAutoSteps + 1)) != cudaSuccess ||
+        cudaMallocHost(&h->h_hist, sizeof(int32_t) * (kNumBins + 1)) != cudaSuccess) {
         cudaGetLastError();
         if (h->d_flag) cudaFree(h->d_flag);
         if (h->d_refine) cudaFree(h->d_refine);
         if (h->h_flag) cudaFreeHost(h->h_flag);
+        if (h->h_refine) cudaFreeHost(h->h_refine);
         cudaMemPoolDestroy(h->pool);
         delete h;
         return SAM_ERR_OOM;
@@ -966,6 +983,7 @@ sam_status sam_destroy(sam_handle h) {
     cudaFree(h->d_refine);
     cudaFreeHost(h->h_flag);
     cudaFreeHost(h->h_refine);
+    cudaFreeHost(h->h_hist);
     cudaMemPoolDestroy(h->pool);
     delete h;
     return SAM_OK;
@@ -1418,6 +1436,9 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     const int32_t *off0 = nullptr;
     if ((shared ? interleaved_work_list(h, sc, K, n, bin, work, bin_off, &chunks, &off0)
                 : build_work_list(h, (int)N, bin, work, bin_off)) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    if (h->record_hist &&
+        cudaMemcpyAsync(h->h_hist, bin_off, sizeof(int32_t) * (kNumBins + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return SAM_ERR_CUDA;
     if (chunked && (cudaEventCreateWithFlags(&ev_bins, cudaEventDisableTiming) != cudaSuccess ||
                     cudaMemcpyAsync(h->h_bins, off0, sizeof(int32_t) * (kNumBins + 1), cudaMemcpyDeviceToHost, st) !=
@@ -2051,6 +2072,22 @@ sam_status sam_set_tile_variants(sam_handle h, const int *variants, int count) {
     return SAM_OK;
 }
 
+sam_status sam_set_bin_schedule(sam_handle h, const int *to, int count) {
+    if (!h || !to || count != kNumBins) return SAM_ERR_INVALID_ARG;
+    for (int b = 0; b < kNumBins; ++b) {
+        const bool ok = b == kBinBig ? to[b] == kBinBig : (to[b] >= b && to[b] < kRegBins);
+        if (!ok) return SAM_ERR_INVALID_ARG;
+    }
+    for (int b = 0; b < kNumBins; ++b) h->sched.to[b] = (uint8_t)to[b];
+    return SAM_OK;
+}
+
+sam_status sam_get_bin_schedule(sam_handle h, int *to, int count) {
+    if (!h || !to || count != kNumBins) return SAM_ERR_INVALID_ARG;
+    for (int b = 0; b < kNumBins; ++b) to[b] = h->sched.to[b];
+    return SAM_OK;
+}
+
 sam_status sam_refine_stats(sam_handle h, int64_t *counts, int count) {
     if (!h || !counts || count != kAutoSteps + 1) return SAM_ERR_INVALID_ARG;
     if (cudaMemcpyAsync(counts, h->d_refine, sizeof(int64_t) * (kAutoSteps + 1), cudaMemcpyDeviceToHost,
@@ -2077,12 +2114,6 @@ sam_status sam_tune(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0,
     std::vector<int64_t> off(K + 1, 0);
     for (int k = 0; k < K; ++k) off[k + 1] = off[k] + S[k]->nnz;
     const int n = A_0->n;
-    const std::string key = tune_key(h, K, n, off[K], precision, refine_steps);
-    int chosen[kNumBins];
-    if (tune_lookup(cache_path, key, chosen)) {
-        for (int b = 0; b < kNumBins; ++b) h->variant[b] = chosen[b];
-        return SAM_OK;
-    }
     // outputs of the trial builds: device workspace of this call
     Scratch sc(h);
     int32_t *rp = sc.get<int32_t>((size_t)K * ((size_t)n + 1));
@@ -2096,59 +2127,125 @@ sam_status sam_tune(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0,
     double keep_ms[kNumBins];
     int64_t keep_n[kNumBins];
     int saved[kNumBins];
+    const BinSchedule saved_sched = h->sched;
     for (int b = 0; b < kNumBins; ++b) {
         keep_ms[b] = h->lsq_ms[b];
         keep_n[b] = h->lsq_n[b];
         saved[b] = h->variant[b];
     }
-    constexpr int kTrials = 3;
-    double best[kNumBins];
-    for (int b = 0; b < kNumBins; ++b) {
-        best[b] = 1e300;
-        chosen[b] = 0;
+    BinSchedule ident;
+    for (int b = 0; b < kNumBins; ++b) ident.to[b] = (uint8_t)b;
+    auto restore = [&](sam_status result, const int *chosen, const BinSchedule &sched) {
+        h->profiling = prof;
+        h->launches = launches;
+        h->record_hist = false;
+        for (int b = 0; b < kNumBins; ++b) {
+            h->lsq_ms[b] = keep_ms[b];
+            h->lsq_n[b] = keep_n[b];
+            h->variant[b] = result == SAM_OK ? chosen[b] : saved[b];
+        }
+        h->sched = result == SAM_OK ? sched : saved_sched;
+        return result;
+    };
+    auto build = [&]() {
+        return sam_build_batched(h, K, A_k, A_0, S, precision, refine_steps, off.data(), rp, ci, v, nullptr, nullptr,
+                                 nullptr);
+    };
+    // the natural size classes' histogram (identity schedule): the family's key
+    int chosen[kNumBins];
+    for (int b = 0; b < kNumBins; ++b) chosen[b] = saved[b];
+    h->profiling = false;
+    h->sched = ident;
+    h->record_hist = true;
+    sam_status result = build();
+    h->record_hist = false;
+    if (result == SAM_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) result = SAM_ERR_CUDA;
+    if (result != SAM_OK) return restore(result, chosen, saved_sched);
+    int64_t hist[kNumBins];
+    for (int b = 0; b < kNumBins; ++b) hist[b] = h->h_hist[b + 1] - h->h_hist[b];
+    std::string key = tune_key(h, K, n, off[K], precision, refine_steps);
+    for (int b = 0; b < kNumBins; ++b) key += " h" + std::to_string((long long)hist[b]);
+    BinSchedule sched = ident;
+    {
+        int to[kNumBins];
+        if (tune_lookup(cache_path, key, chosen, to)) {
+            for (int b = 0; b < kNumBins; ++b) sched.to[b] = (uint8_t)to[b];
+            return restore(SAM_OK, chosen, sched);
+        }
     }
-    sam_status result = SAM_OK;
-    int max_var = 1;
-    for (int b = 0; b < kNumBins; ++b) max_var = std::max(max_var, kTileVariants[b]);
-    for (int var = 0; var < max_var && result == SAM_OK; ++var) {
-        // every size class tries its variant `var` (the last one if it has fewer)
-        for (int b = 0; b < kNumBins; ++b) h->variant[b] = std::min(var, kTileVariants[b] - 1);
+    constexpr int kTrials = 3;
+    // mean time per build of every size class's launches under the current
+    // variants and schedule (one warm-up, kTrials timed builds)
+    double cls_ms[kNumBins];
+    auto trial = [&]() -> sam_status {
         h->profiling = false;
-        result = sam_build_batched(h, K, A_k, A_0, S, precision, refine_steps, off.data(), rp, ci, v, nullptr,
-                                   nullptr, nullptr);  // warm-up
-        if (result != SAM_OK) break;
+        sam_status r = build();
+        if (r != SAM_OK) return r;
         for (int b = 0; b < kNumBins; ++b) {
             h->lsq_ms[b] = 0.0;
             h->lsq_n[b] = 0;
         }
         h->profiling = true;
-        for (int t = 0; t < kTrials && result == SAM_OK; ++t)
-            result = sam_build_batched(h, K, A_k, A_0, S, precision, refine_steps, off.data(), rp, ci, v, nullptr,
-                                       nullptr, nullptr);
-        if (cudaStreamSynchronize(h->stream) != cudaSuccess) result = SAM_ERR_CUDA;
+        for (int t = 0; t < kTrials && r == SAM_OK; ++t) r = build();
+        if (r == SAM_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) r = SAM_ERR_CUDA;
         profile_resolve(h);
-        for (int b = 0; b < kNumBins; ++b) {
-            if (h->variant[b] != var || h->lsq_n[b] == 0) continue;
-            const double ms = h->lsq_ms[b] / (double)h->lsq_n[b];
-            if (ms < best[b]) {
-                best[b] = ms;
+        h->profiling = false;
+        for (int b = 0; b < kNumBins; ++b) cls_ms[b] = h->lsq_ms[b] / kTrials;
+        return r;
+    };
+    // 1. tile shapes: every size class tries its variant `var` (the last one
+    //    if it has fewer); the fastest launch per class wins
+    double best[kNumBins];
+    for (int b = 0; b < kNumBins; ++b) {
+        best[b] = 1e300;
+        chosen[b] = 0;
+    }
+    int max_var = 1;
+    for (int b = 0; b < kNumBins; ++b) max_var = std::max(max_var, kTileVariants[b]);
+    for (int var = 0; var < max_var && result == SAM_OK; ++var) {
+        for (int b = 0; b < kNumBins; ++b) h->variant[b] = std::min(var, kTileVariants[b] - 1);
+        result = trial();
+        for (int b = 0; b < kNumBins && result == SAM_OK; ++b) {
+            if (h->variant[b] != var || hist[b] == 0) continue;
+            if (cls_ms[b] < best[b]) {
+                best[b] = cls_ms[b];
                 chosen[b] = var;
             }
         }
     }
-    h->profiling = prof;
-    h->launches = launches;
-    for (int b = 0; b < kNumBins; ++b) {
-        h->lsq_ms[b] = keep_ms[b];
-        h->lsq_n[b] = keep_n[b];
-        h->variant[b] = result == SAM_OK ? chosen[b] : saved[b];
+    // 2. bin schedule: fold each small register class into the next one that
+    //    still solves columns (fewer launches, fuller waves), greedily from
+    //    the smallest, kept when the summed launch time drops by 1% or more
+    if (result == SAM_OK) {
+        for (int b = 0; b < kNumBins; ++b) h->variant[b] = chosen[b];
+        result = trial();
+        double cur = 0.0;
+        for (int b = 0; b < kNumBins; ++b) cur += cls_ms[b];
+        for (int b = 0; b + 1 < kRegBins && result == SAM_OK; ++b) {
+            if (hist[b] == 0 || sched.to[b] != b) continue;
+            BinSchedule cand = sched;
+            const uint8_t next = cand.to[b + 1];
+            for (int c = 0; c < kRegBins; ++c)
+                if (cand.to[c] == b) cand.to[c] = next;
+            h->sched = cand;
+            result = trial();
+            double tot = 0.0;
+            for (int c = 0; c < kNumBins; ++c) tot += cls_ms[c];
+            if (result == SAM_OK && tot <= 0.99 * cur) {
+                sched = cand;
+                cur = tot;
+            }
+            h->sched = sched;
+        }
     }
-    if (result != SAM_OK) return result;
+    if (result != SAM_OK) return restore(result, chosen, saved_sched);
+    restore(SAM_OK, chosen, sched);
     if (cache_path) {
         FILE *f = fopen(cache_path, "a");
         if (!f) return SAM_ERR_INVALID_ARG;
         fprintf(f, "%s", key.c_str());
         for (int b = 0; b < kNumBins; ++b) fprintf(f, " %d", chosen[b]);
+        for (int b = 0; b < kNumBins; ++b) fprintf(f, " %d", (int)sched.to[b]);
         fprintf(f, "\n");
         fclose(f);
     }

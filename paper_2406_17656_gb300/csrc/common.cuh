@@ -50,6 +50,9 @@ constexpr int kStRefine = 100;
 constexpr int kAutoSteps = 2;
 constexpr double kAutoC = 4.0, kAutoTol = 1e-12, kFallbackTol = 1e-10;
 constexpr double kU32 = 5.9604644775390625e-8;  // unit roundoff of FP32, 2^-24
+// the refinement guard's factor on u_32 kappa^2, kappa estimated from the R
+// diagonal (which can fall short of kappa(B) several times on P1 FEM columns)
+constexpr double kRhoSafety = 8.0;
 constexpr double kNoise2 = 1e-28;  // |d|^2 / |m|^2 below which a correction is rounding noise of the FP64 residual
 
 // Source CSR of one map (device pointers) for the batch concatenation.
@@ -126,6 +129,13 @@ void profile_end(sam_handle h, int bin);
 // FP32 tile shape of a size class chosen by sam_tune (0: two problems per
 // warp where the tile allows, 1: the alternative shape)
 int handle_variant(sam_handle h, int bin);
+// Bin schedule: the size class that solves the columns of each natural size
+// class (the first class they fit); a class may hand its columns to a larger
+// register-tile class (to[b] in [b, kRegBins - 1]); the large class keeps its own
+struct BinSchedule {
+    uint8_t to[kNumBins];
+};
+BinSchedule handle_schedule(sam_handle h);
 // number of FP32 tile shapes per size class
 constexpr int kTileVariants[kNumBins] = {1, 2, 2, 2, 2, 1};
 

@@ -163,9 +163,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
                 const float msq = S.msq;
                 // Accuracy guard.  CSNE contracts the error e_s by a factor
                 // rho ~ u_32 kappa(B)^2 per step, so e_s <= rho / (1 - rho) |d_s|
-                // for rho < 1.  rho is estimated as the larger of u_32 kappa^2,
-                // with kappa estimated by max |R_kk| / min |R_kk| (a lower
-                // bound on kappa(B)), and, after step 1, kAutoC |d_1| / |m|
+                // for rho < 1.  rho is estimated as the larger of
+                // kRhoSafety u_32 kappa^2, with kappa estimated by
+                // max |R_kk| / min |R_kk| (a lower bound on kappa(B), hence the
+                // safety factor), and, after step 1, kAutoC |d_1| / |m|
                 // (the correction itself is ~ u_32 kappa |m|), after later
                 // steps |d_s| / |d_{s-1}|.  A column whose predicted error is
                 // above kFallbackTol |m| (or whose rho is 1/2 or more) is
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
                 // from the FP32 solution, and 1 - rho >= 1/2 used for the ratio
                 // estimates (conservative)
                 constexpr float kTol = (float)kFallbackTol, kTol2 = kTol * kTol, kC = (float)kAutoC;
-                const float rk = (float)kU32 * S.kap2;  // u_32 kappa^2
+                const float rk = (float)(kRhoSafety * kU32) * S.kap2;  // u_32 kappa^2, with a safety factor
                 bool miss = !(rk < 0.5f) || rk * rk * dsq > kTol2 * (1.f - rk) * (1.f - rk) * msq;
                 if (step == 0) {  // rho = kAutoC |d_1| / |m|
                     miss = miss || 4.f * kC * kC * dsq >= msq || 2.f * kC * dsq > kTol * msq;

@@ -840,7 +840,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const i
                                                                   const int32_t *jcp, const int32_t *jri,
                                                                   int32_t *ish, int32_t *icnt, uint8_t *bin,
                                                                   int32_t *colstat, int64_t *nbcnt, uint8_t *lrow,
-                                                                  ShadowTarget tg) {
+                                                                  ShadowTarget tg, BinSchedule sched) {
     __shared__ unsigned bms[kMergeWarps][kBitWords];
     __shared__ unsigned char pres[kMergeWarps][kBitWords];
     __shared__ __align__(16) unsigned char stg[kMergeWarps][kLCap];
@@ -927,7 +927,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) shadow_kernel(int n, const i
         if (lane == 0) {
             const int u = r.count;
             icnt[j] = u;
-            bin[j] = (uint8_t)b;
+            bin[j] = (uint8_t)(b != kBinNone ? sched.to[b] : b);  // the class that solves it
             if (nbcnt) nbcnt[j] = r.total;
             // fewer shadow rows than unknowns means a zero column: rank deficient
             colstat[j] = (b != kBinNone) ? kStOk : ((u >= 0 && u < nj) ? kStRank : kStUnsupported);
@@ -1081,7 +1081,7 @@ cudaError_t shadow_and_bins(sam_handle h, int N, const int32_t *kcp, const int32
                             const int32_t *jri, int32_t *ish, int32_t *icnt, uint8_t *bin, int32_t *colstat,
                             int64_t *nbcnt, uint8_t *lrow, ShadowTarget tg) {
     shadow_kernel<<<merge_grid(h, N, shadow_kernel), kMergeWarps * 32, 0, handle_stream(h)>>>(N, kcp, kri, jcp, jri, ish, icnt, bin,
-                                                                              colstat, nbcnt, lrow, tg);
+                                                                              colstat, nbcnt, lrow, tg, handle_schedule(h));
     count_launch(h);
     return cudaGetLastError();
 }

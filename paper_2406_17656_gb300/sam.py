@@ -114,6 +114,8 @@ _SIGS = [
      [_vp, ctypes.c_int, ctypes.POINTER(sam_csr), ctypes.c_int, ctypes.c_double, _vp, _vp, _vp, _i64p]),
     ("sam_set_tile_variants", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("sam_get_tile_variants", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    ("sam_set_bin_schedule", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    ("sam_get_bin_schedule", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("sam_profile", ctypes.c_int32, [_vp, ctypes.c_int]),
     ("sam_profile_read", ctypes.c_int32, [_vp, _i64p, ctypes.POINTER(ctypes.c_double), _i64p]),
     ("sam_peak_flops", ctypes.c_int32, [_vp, ctypes.c_double, _f64p, _f64p]),
@@ -627,8 +629,9 @@ class Handle:
     # ---------------------------------------------------------------- tuning
     def sam_tune(self, A_ks: list, A_0: Csr, Ss: list, precision="fp32r", refine_steps: int = 1,
                  cache_path: str | None = None):
-        """Time the tile variants of every size class on these problems and
-        keep the fastest in the handle; returns the chosen variants."""
+        """Choose the tile variant of every size class and the bin schedule
+        on these problems (kept in the handle); returns the chosen variants
+        (the schedule: sam_get_bin_schedule)."""
         K = len(A_ks)
         prec = PRECISIONS.get(precision, precision)
         arr = (sam_csr * K)(*[a.c() for a in A_ks])
@@ -641,6 +644,16 @@ class Handle:
     def sam_set_tile_variants(self, variants):
         v = (ctypes.c_int * SAM_NUM_SIZE_CLASSES)(*[int(x) for x in variants])
         _check(load().sam_set_tile_variants(self.ptr, v, len(variants)), "sam_set_tile_variants")
+
+    def sam_set_bin_schedule(self, to):
+        v = (ctypes.c_int * SAM_NUM_SIZE_CLASSES)(*[int(x) for x in to])
+        _check(load().sam_set_bin_schedule(self.ptr, v, len(to)), "sam_set_bin_schedule")
+
+    def sam_get_bin_schedule(self):
+        """The size class that solves each natural size class's columns."""
+        v = (ctypes.c_int * SAM_NUM_SIZE_CLASSES)()
+        _check(load().sam_get_bin_schedule(self.ptr, v, SAM_NUM_SIZE_CLASSES), "sam_get_bin_schedule")
+        return list(v)
 
     def sam_refine_stats(self):
         """[one step, two steps, FP64 re-solve] column counts of the last

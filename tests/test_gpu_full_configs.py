@@ -149,3 +149,30 @@ def test_config5_pairs_512_forward_and_adjoint(sam, handle):
     scale = max(np.abs(wk).max(), np.abs(w0).max())
     assert np.abs(dk[koff[b]:koff[b + 1]] - wk).max() <= 1e-9 * scale
     assert np.abs(d0[zoff[b]:zoff[b + 1]] - w0).max() <= 1e-9 * scale
+
+
+def test_config4_every_column_against_the_fp64_build(sam, handle):
+    """Every column of the full P1 FEM sequence (16 maps, level 2, the
+    workload with the worst-conditioned column problems): FP32 QR + one
+    guarded FP64 step against the plain FP64 GPU build, whose columns meet
+    the oracle to 1e-12 (the parity tests): the per-column bar, with the
+    FP64 build's own error as margin."""
+    import torch
+
+    seq = W.config4()
+    A0 = seq.mats[0]
+    Aks = [sam.Csr.from_host(m) for m in seq.mats]
+    a0 = sam.Csr.from_host(A0)
+    n = A0.n
+    Ss = handle.sam_pattern_build_batched(Aks, 2)
+    offs, rp, ci, v32, _ = handle.sam_build_batched(Aks, a0, Ss, "fp32r", 1)
+    _, _, _, v64, _ = handle.sam_build_batched(Aks, a0, Ss, "fp64", 0, offsets=offs)
+    worst = 0.0
+    for k in range(len(Aks)):
+        a, b = v32[offs[k]:offs[k + 1]], v64[offs[k]:offs[k + 1]]
+        c = ci[offs[k]:offs[k + 1]].long()
+        d2 = torch.zeros(n, dtype=torch.float64, device="cuda").index_add_(0, c, (a - b) ** 2)
+        w2 = torch.zeros(n, dtype=torch.float64, device="cuda").index_add_(0, c, b * b)
+        assert bool((w2 > 0).all())
+        worst = max(worst, float(torch.sqrt(d2 / w2).max()))
+    assert worst <= colcheck.EPS["fp32r"] + colcheck.EPS["fp64"], worst
