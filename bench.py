@@ -98,6 +98,8 @@ def parse():
     ap.add_argument("--profile-sparsify", type=int, default=0, metavar="CALLS",
                     help="profiling aid: run CALLS batched column-tau (0.8) sparsifications of the benchmark's maps "
                          "and exit (no JSON line)")
+    ap.add_argument("--tape", action="store_true",
+                    help="with --profile-adjoint: the build records a factor tape and the adjoints replay it")
     ap.add_argument("--profile-adjoint", type=int, default=0, metavar="STEPS",
                     help="profiling aid: run STEPS adjoints of the benchmark's batched build (dL/dM random, "
                          "residual term on) and exit (no JSON line)")
@@ -189,23 +191,24 @@ def algorithmic_flops(I, J, nB, precision, steps):
     return f32, f64
 
 
-def adjoint_algorithmic_flops(I, J, nB, steps):
+def adjoint_algorithmic_flops(I, J, nB, steps, tape=False):
     """Algorithmic work of the adjoint of one column (m = |I_j|, n = |J_j|,
     b = nnz(B_j), s refinement steps), as the adjoint kernel computes it:
-    FP32 the recomputed QR of [B c] (the forward's formula) and s + 1
-    solves with R^T R (2 n^2 each) plus, after the last correction, its
-    product B d (2 b); FP64 the residual r = c - B m (2 b + m), the products
-    w = B lambda before each correction (2 b each, s of them, at least one),
-    B^T w per correction (2 b each), the dL/dB entries (3 b: a product and
-    an FMA per entry) and dL/dc (m).  Returns (FP32, FP64) flops per column."""
+    FP32 the recomputed QR of [B c] (the forward's formula; none when R comes
+    from a factor tape) and s + 1 solves with R^T R (2 n^2 each) plus, after
+    the last correction, its product B d (2 b); FP64 the residual
+    r = c - B m (2 b + m), the products w = B lambda before each correction
+    (2 b each, s of them, at least one), B^T w per correction (2 b each),
+    the dL/dB entries (3 b: a product and an FMA per entry) and dL/dc (m).
+    Returns (FP32, FP64) flops per column."""
     m, n, b = I.astype(np.float64), J.astype(np.float64), nB.astype(np.float64)
-    qr = 2 * n * n * (m - n / 3) + (4 * m * n - 2 * n * n) + n * n
+    qr = 0.0 if tape else 2 * n * n * (m - n / 3) + (4 * m * n - 2 * n * n) + n * n
     f32 = qr + (steps + 1) * 2 * n * n + (2 * b if steps > 0 else 0.0)
     f64 = (2 * b + m) + max(steps, 1) * 2 * b + steps * 2 * b + 3 * b + m
     return f32, f64
 
 
-def adjoint_roofline(mats, level, steps, ms):
+def adjoint_roofline(mats, level, steps, ms, tape=False):
     """Roofline of a whole adjoint call over the maps of `mats`: the slower of
     its algorithmic FP32 flops at the FP32 peak and FP64 flops at the FP64
     peak (adjoint_algorithmic_flops summed over every column), over the
@@ -216,7 +219,7 @@ def adjoint_roofline(mats, level, steps, ms):
         key = (m.indptr.tobytes(), m.indices.tobytes())
         if key not in seen:
             I, J, nB = column_sizes([m], level)[0]
-            a, b = adjoint_algorithmic_flops(I, J, nB, steps)
+            a, b = adjoint_algorithmic_flops(I, J, nB, steps, tape)
             seen[key] = (float(np.sum(a)), float(np.sum(b)))
         f32, f64 = f32 + seen[key][0], f64 + seen[key][1]
     t32, t64 = f32 / PEAK_FP32, f64 / PEAK_FP64
@@ -769,12 +772,19 @@ def config_figures(h, sam, torch, dev, stream, nsteps=7):
     ps = h.sam_pattern_build_batched(a1s, 1)
     offs, _, _, mv, _ = h.sam_build_batched(a1s, a0s, ps, "fp32r", 2)
     gbar = torch.randn(mv.numel(), dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(5))
+    msb_re = timed(lambda: h.sam_build_backward_batched(a1s, a0s, ps, mv, gbar, "fp32r", 2, 1.0, offsets=offs), nsteps)
+    tape = torch.empty((h.sam_factor_tape_bytes(ps, "fp32r") + 15) // 16 * 2, dtype=torch.float64, device=dev)
+    h.sam_set_factor_tape(sam.SAM_TAPE_RECORD, tape)
+    h.sam_build_batched(a1s, a0s, ps, "fp32r", 2, M_val=mv)
+    h.sam_set_factor_tape(sam.SAM_TAPE_REPLAY, tape)
     msb = timed(lambda: h.sam_build_backward_batched(a1s, a0s, ps, mv, gbar, "fp32r", 2, 1.0, offsets=offs), nsteps)
+    h.sam_set_factor_tape(sam.SAM_TAPE_OFF)
     for p in ps:
         p.destroy()
-    del mv, gbar
-    ex = {"adjoint_columns_per_s": 32 * n5 / (msb * 1e-3), "adjoint_ms": msb, "refine_steps": 2, **tv}
-    ex["adjoint_roofline"] = adjoint_roofline([p[1] for p in pairs], 1, 2, msb)
+    del mv, gbar, tape
+    ex = {"adjoint_columns_per_s": 32 * n5 / (msb * 1e-3), "adjoint_ms": msb, "adjoint_recompute_ms": msb_re,
+          "refine_steps": 2, **tv}
+    ex["adjoint_roofline"] = adjoint_roofline([p[1] for p in pairs], 1, 2, msb, tape=True)
     ex.update(plan_replay(a1s, a0s, 1, 2, 32 * n5))
     ex.update(accuracy(a1s, a0s, 1, 2, n5, ms5, (pairs[-1][1], pairs[-1][0]), seed=5))
     line("q1_pairs_512x512_x32_level1", 32 * n5, 32, ms5, ex,
@@ -883,7 +893,14 @@ def main():
         return
     if args.profile_adjoint > 0:
         pats = h.sam_pattern_build_batched(aks, args.level)
+        tape = None
+        if args.tape:
+            tape = torch.empty((h.sam_factor_tape_bytes(pats, "fp32r") + 15) // 16 * 2, dtype=torch.float64,
+                               device=dev)
+            h.sam_set_factor_tape(sam.SAM_TAPE_RECORD, tape)
         offs_a, _, _, mv, _ = h.sam_build_batched(aks, a0, pats, "fp32r", args.refine)
+        if tape is not None:
+            h.sam_set_factor_tape(sam.SAM_TAPE_REPLAY, tape)
         gbar = torch.randn(mv.numel(), dtype=torch.float64, device=dev,
                            generator=torch.Generator(device=dev).manual_seed(3))
         torch.cuda.synchronize()
@@ -1019,22 +1036,43 @@ def main():
         gbar = torch.randn(mv.numel(), dtype=torch.float64, device=dev,
                            generator=torch.Generator(device=dev).manual_seed(3))
         targets = [a0] * K
-        for _ in range(2):
+
+        def event_ms(fn, reps=3, warm=2):
+            for _ in range(warm):
+                fn()
+            torch.cuda.synchronize()
+            t = 0.0
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                t += e0.elapsed_time(e1)
+            return max_over_ranks(t / reps, world, dev)
+
+        def backward():
             h.sam_build_backward_batched(aks, targets, pats, mv, gbar, "fp32r", args.refine, 1.0, offsets=offs_a)
-        torch.cuda.synchronize()
-        ta = 0.0
-        na = 3
-        for _ in range(na):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            h.sam_build_backward_batched(aks, targets, pats, mv, gbar, "fp32r", args.refine, 1.0, offsets=offs_a)
-            e1.record(stream)
-            e1.synchronize()
-            ta += e0.elapsed_time(e1)
-        ta = max_over_ranks(ta / na, world, dev)
+
+        ta_re = event_ms(backward)
+        # factor tape: the build records every column's R, the adjoint
+        # replays it instead of recomputing the QR
+        tape = torch.empty((h.sam_factor_tape_bytes(pats, "fp32r") + 15) // 16 * 2, dtype=torch.float64, device=dev)
+        h.sam_set_factor_tape(sam.SAM_TAPE_RECORD, tape)
+        tb_rec = event_ms(lambda: h.sam_build_batched(aks, a0, pats, "fp32r", args.refine, M_val=mv))
+        h.sam_set_factor_tape(sam.SAM_TAPE_REPLAY, tape)
+        ta = event_ms(backward)
+        h.sam_set_factor_tape(sam.SAM_TAPE_OFF)
         extra["adjoint_columns_per_s"] = job_value(cols_per_step, world, ta)
         extra["adjoint_ms"] = ta
-        extra["adjoint_roofline"] = adjoint_roofline(seq.mats, args.level, args.refine, ta)
+        extra["adjoint_note"] = ("adjoint_ms: the batched adjoint reading R from the build's factor tape "
+                                 "(sam_set_factor_tape); adjoint_recompute_ms: the same adjoint recomputing the "
+                                 "QR; build_with_tape_ms: the batched build recording the tape (no pattern build)")
+        extra["adjoint_recompute_ms"] = ta_re
+        extra["build_with_tape_ms"] = tb_rec
+        extra["factor_tape_bytes"] = int(tape.numel() * 8)
+        extra["adjoint_roofline"] = adjoint_roofline(seq.mats, args.level, args.refine, ta, tape=True)
+        del tape
         for p in pats:
             p.destroy()
 

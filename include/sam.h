@@ -394,7 +394,8 @@ sam_status sam_gmres_batched(sam_handle h, int K, const sam_csr *A, const sam_cs
  * Entries of dL/dB at positions not stored in A_k are dropped; every stored
  * A_k entry receives the sum of its contributions from all columns, added
  * in a fixed order (deterministic).  lambda uses the recomputed QR (FP32 R
- * plus `refine_steps` FP64-residual corrections for SAM_FP32_REFINE).
+ * plus `refine_steps` FP64-residual corrections for SAM_FP32_REFINE), or the
+ * forward build's R from a factor tape (sam_set_factor_tape).
  * dA_k_val[nnz(A_k)], dA_0_val[nnz(A_0)]: outputs in the CSR order of A_k
  * and A_0 (overwritten).  dM_resid (nullable, nnz(S), CSR order of the map):
  * receives w * d||A_k M - A_0||_F^2 / dM = -2 w A_k^T R on the pattern (zero
@@ -420,6 +421,52 @@ sam_status sam_build_backward_batched(sam_handle h, int K, const sam_csr *A_k, c
                                       const int64_t *M_offsets, const double *M_val,
                                       const double *dM_val, double resid_weight, double *dA_k_val,
                                       double *dA_0_val, double *dM_resid);
+
+/*
+ * Factor tape (no counterpart in the paper): the adjoint of a build needs
+ * the triangular factor R of every column problem, which it otherwise
+ * recomputes (gathering B_j into a tile and running the QR again, about a
+ * quarter of an adjoint's time).  A caller that runs the adjoint after the
+ * build (reverse-mode training) can keep the build's factors instead:
+ *
+ *   sam_factor_tape_bytes(h, K, S, precision, &bytes);   allocate bytes
+ *   sam_set_factor_tape(h, SAM_TAPE_RECORD, buf, bytes);
+ *   sam_build_batched(h, K, A_k, A_0, S, precision, ...);  (writes R)
+ *   sam_set_factor_tape(h, SAM_TAPE_REPLAY, buf, bytes);
+ *   sam_build_backward_batched(h, K, A_k, A_0s, S, precision, ...);
+ *   sam_set_factor_tape(h, SAM_TAPE_OFF, NULL, 0);
+ *
+ * The tape holds, per column j of the batch with |J_j| <= 27, the packed
+ * upper triangle of R in the build's arithmetic type (FP32 for
+ * SAM_FP32_REFINE, FP64 for SAM_FP64), rows in order, each from its
+ * diagonal, in a slot of |J_j| (|J_j| + 1) / 2 elements rounded up to a
+ * multiple of four; slots follow the columns of the batch in order (map k's
+ * columns after map k-1's).  Columns of the large class (sam_size_classes)
+ * write nothing and have no adjoint.
+ *
+ * sam_factor_tape_bytes -- bytes of the tape of the K maps on patterns S
+ * (one slot per column of each pattern) at `precision`.  Synchronises.
+ *
+ * sam_set_factor_tape -- mode SAM_TAPE_RECORD: later builds on the handle
+ * (sam_build, sam_build_batched, sam_build_multi; not captured plans, not
+ * sam_tune's trial builds) write their columns' R into buf;
+ * SAM_TAPE_REPLAY: later adjoints (sam_build_backward,
+ * sam_build_backward_batched) read R from buf instead of recomputing it;
+ * SAM_TAPE_OFF: neither (buf and bytes ignored).  buf: device memory of the
+ * handle's device, 16-byte aligned, owned by the caller and kept alive while
+ * the mode is set.  A replaying adjoint must see the same K, sources,
+ * patterns, precision and tile variants as the recording build (as M_val
+ * must be the build's map).  The adjoint recomputes R with the default tile
+ * shapes (variant 0); for a build with those shapes, replaying the tape
+ * gives the recomputing adjoint's results bit for bit, and otherwise
+ * results that differ in rounding only.  Errors: SAM_ERR_INVALID_ARG for a bad
+ * mode or buffer; a build or adjoint whose tape needs more than `bytes`
+ * returns SAM_ERR_INVALID_ARG before launching its solves (each of them
+ * synchronises once to size the tape).
+ */
+enum { SAM_TAPE_OFF = 0, SAM_TAPE_RECORD = 1, SAM_TAPE_REPLAY = 2 };
+sam_status sam_factor_tape_bytes(sam_handle h, int K, const sam_pattern *S, int precision, int64_t *bytes);
+sam_status sam_set_factor_tape(sam_handle h, int mode, void *buf, int64_t bytes);
 
 /*
  * sam_tune -- autotuner (no counterpart in the paper, which fixes one kernel

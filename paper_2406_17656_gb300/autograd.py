@@ -23,9 +23,19 @@ class _BuildFn(torch.autograd.Function):
         h, S = owner.handle, owner.pattern
         ak = _sam.Csr(owner.ak_rp, owner.ak_ci, ak_val.detach().contiguous(), n=owner.n)
         a0 = _sam.Csr(owner.a0_rp, owner.a0_ci, a0_val.detach().contiguous(), n=owner.n)
-        ip, ix, mv = h.sam_build(ak, a0, S, owner.precision, owner.refine_steps)
+        tape = None
+        if owner.keep_factors:
+            # the build's R factors, kept for the backward (sam_set_factor_tape)
+            tape = torch.empty((owner.tape_bytes() + 15) // 16 * 2, dtype=torch.float64, device=ak_val.device)
+            h.sam_set_factor_tape(_sam.SAM_TAPE_RECORD, tape)
+        try:
+            ip, ix, mv = h.sam_build(ak, a0, S, owner.precision, owner.refine_steps)
+        finally:
+            if tape is not None:
+                h.sam_set_factor_tape(_sam.SAM_TAPE_OFF)
         owner.indptr, owner.indices = ip, ix
         ctx.owner = owner
+        ctx.tape = tape
         ctx.save_for_backward(ak_val.detach(), a0_val.detach(), mv)
         return mv
 
@@ -35,8 +45,16 @@ class _BuildFn(torch.autograd.Function):
         ak_val, a0_val, mv = ctx.saved_tensors
         ak = _sam.Csr(owner.ak_rp, owner.ak_ci, ak_val.contiguous(), n=owner.n)
         a0 = _sam.Csr(owner.a0_rp, owner.a0_ci, a0_val.contiguous(), n=owner.n)
-        dak, da0 = owner.handle.sam_build_backward(ak, a0, owner.pattern, mv, dm.contiguous(), owner.precision,
-                                                   owner.refine_steps, 0.0)
+        h = owner.handle
+        if ctx.tape is not None:
+            h.sam_set_factor_tape(_sam.SAM_TAPE_REPLAY, ctx.tape)
+        try:
+            dak, da0 = h.sam_build_backward(ak, a0, owner.pattern, mv, dm.contiguous(), owner.precision,
+                                            owner.refine_steps, 0.0)
+        finally:
+            if ctx.tape is not None:
+                h.sam_set_factor_tape(_sam.SAM_TAPE_OFF)
+        ctx.tape = None
         return dak, da0, None
 
 
@@ -92,15 +110,25 @@ class SamMap:
     handle: sam.Handle; ak_struct / a0_struct: (indptr, indices) int32 device
     tensors of A_k and A_0; pattern: sam.Pattern (e.g. from
     handle.sam_pattern_build); precision "fp32r" (FP32 QR + FP64 refinement)
-    or "fp64"."""
+    or "fp64".  keep_factors: the forward keeps the column problems' R
+    factors in device memory for the backward (a factor tape), which then
+    skips the QR; the gradients are the same."""
 
-    def __init__(self, handle, ak_struct, a0_struct, pattern, precision="fp32r", refine_steps=1):
+    def __init__(self, handle, ak_struct, a0_struct, pattern, precision="fp32r", refine_steps=1,
+                 keep_factors=False):
         self.handle, self.pattern = handle, pattern
         self.ak_rp, self.ak_ci = ak_struct
         self.a0_rp, self.a0_ci = a0_struct
         self.n = int(self.ak_rp.shape[0] - 1)
         self.precision, self.refine_steps = precision, refine_steps
+        self.keep_factors = keep_factors
+        self._tape_bytes = None
         self.indptr = self.indices = None
+
+    def tape_bytes(self):
+        if self._tape_bytes is None:
+            self._tape_bytes = self.handle.sam_factor_tape_bytes([self.pattern], self.precision)
+        return self._tape_bytes
 
     def __call__(self, ak_val, a0_val):
         return _BuildFn.apply(ak_val, a0_val, self)

@@ -6,9 +6,10 @@
 // r = c - B m, g = dM(J_j, j) and lambda = (B^T B)^{-1} g:
 //   dL/dB = r lambda^T - (B lambda) m^T - 2 w r m^T   (stored entries only)
 //   dL/dc = B lambda + 2 w r,   dL/dA_0(i, j) = 2 w A_0(i, j) outside I_j.
-// The QR is recomputed (not stored): lambda comes from the FP32 R with
-// `refine_steps` corrections whose residuals g - B^T (B lambda) are FP64
-// (or from the FP64 R in FP64 mode).
+// The QR is recomputed, or R is read from the forward build's factor tape
+// (sam_set_factor_tape): lambda comes from the FP32 R with `refine_steps`
+// corrections whose residuals g - B^T (B lambda) are FP64 (or from the FP64
+// R in FP64 mode).
 //
 // Deterministic reduction.  Column problem j writes its dL/dB entries, in
 // the gather order (columns c of J_j, each in A_k's CSC order), to its own
@@ -22,7 +23,7 @@
 namespace sam {
 namespace {
 
-template <class TL, bool FP64>
+template <class TL, bool FP64, bool TAPE>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) adjoint_kernel(LsqArgs args, int bin) {
     using T = typename TL::T;
     constexpr int P = TL::P, PPW = TL::PPW, RS = TL::RS, CS = TL::CS, JQ = TL::JQ, IQ = TL::IQ;
@@ -51,13 +52,20 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) adjoint_kernel(LsqArgs ar
         Column<TL> C;
         C.begin_at(args, item, total, jj_cur);
         const int ll = C.ll;
-        C.gather(args, S);
-        T a[RS][CS];
-        C.load_tile(S, a);
-        C.build_rows(S);
-        C.park(S);
-        C.factor(S, a);
-        C.unpark(S);
+        if constexpr (TAPE) {
+            // R from the forward build's factor tape: no tile, no QR
+            C.template gather<false>(args, S);
+            C.build_rows(S);
+            C.tape_load(args, S);
+        } else {
+            C.gather(args, S);
+            T a[RS][CS];
+            C.load_tile(S, a);
+            C.build_rows(S);
+            C.park(S);
+            C.factor(S, a);
+            C.unpark(S);
+        }
         const int nJ = C.nJ, nI = C.nI;
         // ---- m (the forward map) and the incoming gradient g
         double mq[JQ], gq[JQ];
@@ -203,19 +211,29 @@ __global__ void __launch_bounds__(kReduceThreads) adjoint_reduce_kernel(int N, c
     }
     const int G = 32 / len;
     const int g = lane / len, p = lane - g * len;
+    // the column's block offsets are read a chunk of W = G floor(32 / G)
+    // pattern entries at a time, one per lane, and handed to the groups by
+    // shuffles: group g's entries in the chunk are t0 + g + k G (k < W / G),
+    // the same sequence as a stride-G walk, so the sums keep their order;
+    // their dL/dB values are loaded kLoads at a time, all before the adds
+    constexpr int kLoads = 4;
+    const int W = G * (32 / G), KC = W / G;
     double acc = 0.0;
-    if (g < G) {
-        int t = tb + g;
-        for (; t + G < te; t += 2 * G) {
-            const int64_t b0 = dbase[t], b1 = dbase[t + G];
-            const double v0 = b0 >= 0 ? dB[b0 + p] : 0.0;
-            const double v1 = b1 >= 0 ? dB[b1 + p] : 0.0;
-            acc += v0;
-            acc += v1;
-        }
-        if (t < te) {
-            const int64_t b0 = dbase[t];
-            if (b0 >= 0) acc += dB[b0 + p];
+    for (int t0 = tb; t0 < te; t0 += W) {
+        const int64_t mine = (lane < W && t0 + lane < te) ? dbase[t0 + lane] : -1;
+        for (int k0 = 0; k0 < KC; k0 += kLoads) {
+            int64_t b[kLoads];
+            double v[kLoads];
+#pragma unroll
+            for (int u = 0; u < kLoads; ++u) {
+                const int src = g + (k0 + u) * G;
+                b[u] = shfl(mine, src & 31);
+                if (!(g < G && k0 + u < KC && t0 + src < te)) b[u] = -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kLoads; ++u) v[u] = b[u] >= 0 ? dB[b[u] + p] : 0.0;
+#pragma unroll
+            for (int u = 0; u < kLoads; ++u) acc += v[u];
         }
     }
     part[warp][lane] = acc;
@@ -243,7 +261,7 @@ __global__ void permute_scatter_kernel(int64_t nnz, const int32_t *perm, const d
 template <class TL, bool FP64>
 cudaError_t launch_one(sam_handle h, const LsqArgs &a, int bin) {
     const size_t smem = sizeof(ProbSmem<TL>) * TL::PPW * kWarpsPerBlock;
-    auto kern = adjoint_kernel<TL, FP64>;
+    auto kern = a.fac_mode == kTapeReplay ? adjoint_kernel<TL, FP64, true> : adjoint_kernel<TL, FP64, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

@@ -49,6 +49,10 @@ struct sam_handle_t {
     // number of steps >= 1): columns per outcome, and a pinned mirror
     int64_t *d_refine = nullptr;
     int64_t *h_refine = nullptr;
+    // factor tape (sam_set_factor_tape): the caller's device buffer
+    int tape_mode = sam::kTapeOff;
+    void *tape_buf = nullptr;
+    int64_t tape_bytes = 0;
 };
 
 namespace {
@@ -1298,6 +1302,37 @@ sam_status block_diag_values(sam_handle h, Scratch &sc, const std::vector<DevCsr
 }
 
 // K maps of order n against NT = 1 shared target or NT = K targets (one per map)
+// Factor tape of a batch on pattern group g: slot offsets (device, [N+1])
+// and the bytes they need, read back (synchronises the handle's stream).
+sam_status tape_layout(sam_handle h, Scratch &sc, const PatternGroup *g, int64_t N, int precision, int64_t **off,
+                       int64_t *bytes) {
+    int64_t *sizes = sc.get<int64_t>((size_t)(N > 0 ? N : 1));
+    *off = sc.get<int64_t>((size_t)N + 1);
+    if (!sizes || !*off) return SAM_ERR_OOM;
+    int64_t tot = 0;
+    if (tape_offsets(h, N, g->jcp, sizes, *off) != cudaSuccess ||
+        cudaMemcpyAsync(&tot, *off + N, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return SAM_ERR_CUDA;
+    *bytes = tot * (precision == SAM_FP64 ? (int64_t)sizeof(double) : (int64_t)sizeof(float));
+    return SAM_OK;
+}
+
+// the handle's tape, if it is in `mode`, for a batch on group g: sets the
+// launch arguments, or fails if the caller's buffer is too small
+sam_status tape_args(sam_handle h, Scratch &sc, const PatternGroup *g, int64_t N, int precision, int mode,
+                     LsqArgs &a) {
+    if (h->tape_mode != mode) return SAM_OK;
+    int64_t *off = nullptr, bytes = 0;
+    sam_status s = tape_layout(h, sc, g, N, precision, &off, &bytes);
+    if (s != SAM_OK) return s;
+    if (bytes > h->tape_bytes) return SAM_ERR_INVALID_ARG;
+    a.fac = h->tape_buf;
+    a.fac_off = off;
+    a.fac_mode = mode;
+    return SAM_OK;
+}
+
 sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0, int NT, const sam_pattern *S,
                       int precision, int refine_steps, const int64_t *M_offsets, int32_t *M_row_ptr,
                       int32_t *M_col_idx, double *M_val, int32_t *col_status, double *res2, double *fro) {
@@ -1494,6 +1529,7 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     a.work = work;
     a.bin_off = bin_off;
     a.refine_steps = refine_steps;
+    if ((s = tape_args(h, sc, g, N, precision, kTapeRecord, a)) != SAM_OK) return s;
     int32_t *work2 = nullptr, *bin_off2 = nullptr;
     if (guarded) {
         a.refine_used = sc.get<uint8_t>((size_t)N);
@@ -2032,6 +2068,7 @@ sam_status backward_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr 
     a.dmres = d_dmr;
     a.dbase = dbase;
     a.znnz = zn;
+    if ((s = tape_args(h, sc, g, N, precision, kTapeReplay, a)) != SAM_OK) return s;
     if (launch_adjoint(h, precision, a) != cudaSuccess) return SAM_ERR_CUDA;
     if (adjoint_reduce(h, (int)N, kcp, g->mrp, dbase, dB, dak_csc) != cudaSuccess ||
         permute_scatter_f64(h, kn, kperm, dak_csc, d_dak) != cudaSuccess ||
@@ -2062,6 +2099,48 @@ sam_status sam_build_backward_batched(sam_handle h, int K, const sam_csr *A_k, c
                                       double resid_weight, double *dA_k_val, double *dA_0_val, double *dM_resid) {
     return backward_impl(h, K, A_k, A_0, S, precision, refine_steps, M_offsets, M_val, dM_val, resid_weight,
                          dA_k_val, dA_0_val, dM_resid);
+}
+
+sam_status sam_factor_tape_bytes(sam_handle h, int K, const sam_pattern *S, int precision, int64_t *bytes) {
+    if (!h || K < 1 || !S || !bytes) return SAM_ERR_INVALID_ARG;
+    if (precision != SAM_FP64 && precision != SAM_FP32_REFINE) return SAM_ERR_INVALID_ARG;
+    for (int k = 0; k < K; ++k)
+        if (!S[k] || S[k]->n != S[0]->n) return SAM_ERR_INVALID_ARG;
+    if ((int64_t)K * S[0]->n > INT32_MAX - 1) return SAM_ERR_INVALID_ARG;
+    PatternGroup *g = nullptr;
+    bool temp = false;
+    sam_status s = group_for(h, K, S, &g, &temp);
+    if (s != SAM_OK) return s;
+    {
+        Scratch sc(h);
+        int64_t *off = nullptr;
+        s = tape_layout(h, sc, g, (int64_t)K * S[0]->n, precision, &off, bytes);
+    }
+    if (temp) group_release(g);
+    return s;
+}
+
+sam_status sam_set_factor_tape(sam_handle h, int mode, void *buf, int64_t bytes) {
+    if (!h) return SAM_ERR_INVALID_ARG;
+    if (mode == SAM_TAPE_OFF) {
+        h->tape_mode = kTapeOff;
+        h->tape_buf = nullptr;
+        h->tape_bytes = 0;
+        return SAM_OK;
+    }
+    if ((mode != SAM_TAPE_RECORD && mode != SAM_TAPE_REPLAY) || !buf || bytes < 0 ||
+        (reinterpret_cast<uintptr_t>(buf) & 15) != 0)
+        return SAM_ERR_INVALID_ARG;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, buf) != cudaSuccess || (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) ||
+        (at.type == cudaMemoryTypeDevice && at.device != h->device)) {
+        cudaGetLastError();
+        return SAM_ERR_INVALID_ARG;
+    }
+    h->tape_mode = mode == SAM_TAPE_RECORD ? kTapeRecord : kTapeReplay;
+    h->tape_buf = buf;
+    h->tape_bytes = bytes;
+    return SAM_OK;
 }
 
 sam_status sam_set_tile_variants(sam_handle h, const int *variants, int count) {
@@ -2135,7 +2214,10 @@ sam_status sam_tune(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_0,
     }
     BinSchedule ident;
     for (int b = 0; b < kNumBins; ++b) ident.to[b] = (uint8_t)b;
+    const int saved_tape = h->tape_mode;  // the trial builds record no factors
+    h->tape_mode = kTapeOff;
     auto restore = [&](sam_status result, const int *chosen, const BinSchedule &sched) {
+        h->tape_mode = saved_tape;
         h->profiling = prof;
         h->launches = launches;
         h->record_hist = false;

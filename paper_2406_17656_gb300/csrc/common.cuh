@@ -55,6 +55,17 @@ constexpr double kU32 = 5.9604644775390625e-8;  // unit roundoff of FP32, 2^-24
 constexpr double kRhoSafety = 8.0;
 constexpr double kNoise2 = 1e-28;  // |d|^2 / |m|^2 below which a correction is rounding noise of the FP64 residual
 
+// Factor tape (sam_set_factor_tape): a build on a recording handle writes
+// every register-class column's triangular factor R; an adjoint on a
+// replaying handle reads it instead of gathering B into a tile and
+// factoring it again.  Column j's R is stored packed (row k from its
+// diagonal, rows in order, in the tile's type) at element fac_off[j], in a
+// slot of tape_elems(|J_j|) elements (a multiple of four: 16-byte aligned).
+constexpr int kTapeOff = 0, kTapeRecord = 1, kTapeReplay = 2;
+__host__ __device__ __forceinline__ int64_t tape_elems(int nJ) {
+    return (nJ >= 1 && nJ <= kJCap) ? (((int64_t)nJ * (nJ + 1) / 2 + 3) & ~(int64_t)3) : 0;
+}
+
 // Source CSR of one map (device pointers) for the batch concatenation.
 struct CsrPtrs {
     const int32_t *rp;
@@ -104,6 +115,11 @@ struct LsqArgs {
     double *dmres;               // dL/dM direct residual part, map CSR order (nullable)
     int64_t *dbase;              // per pattern entry (map CSR order): offset of its column block in dB
     int64_t znnz;                // nnz(A_0)
+    // factor tape: kTapeRecord (the least-squares kernels write R) or
+    // kTapeReplay (the adjoint reads it); fac holds the tile's type
+    void *fac;
+    const int64_t *fac_off;      // [N+1] element offsets of the columns' slots
+    int fac_mode;
 };
 
 // --------------------------------------------------------------- helpers
@@ -214,6 +230,9 @@ cudaError_t adjoint_reduce(sam_handle h, int N, const int32_t *kcp, const int32_
                            const double *dB, double *dak_csc);
 // out[i] = (float) in[i]
 cudaError_t round_to_f32(sam_handle h, int64_t n, const double *in, float *out);
+// factor tape slots: off[j] = sum over columns i < j of tape_elems(|J_i|),
+// off[N] = the total (sizes: int64[N] workspace)
+cudaError_t tape_offsets(sam_handle h, int64_t N, const int32_t *jcp, int64_t *sizes, int64_t *off);
 // out[perm[p]] = in[p]
 cudaError_t permute_scatter_f64(sam_handle h, int64_t nnz, const int32_t *perm, const double *in, double *out);
 

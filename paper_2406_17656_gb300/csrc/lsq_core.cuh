@@ -452,6 +452,9 @@ struct Column {
 
     // J columns, shadow rows, zeroed tile, gathered B and c (tile + FP64 c),
     // column masks, local rows of every entry, out-of-shadow ||A_0||^2
+    // (TILE = false: everything but the tile, for an adjoint that reads R
+    // from a factor tape)
+    template <bool TILE = true>
     __device__ __forceinline__ void gather(const LsqArgs &args, ProbSmem<TL> &S) {
 #pragma unroll
         for (int q = 0; q < JQ; ++q) {
@@ -480,7 +483,7 @@ struct Column {
             S.mask[i] = 0u;
             S.c[i] = 0.0;
         }
-        {
+        if constexpr (TILE) {
             uint4 *tl = reinterpret_cast<uint4 *>(&S.u.tile[0]);
             constexpr int NV = (int)(sizeof(S.u.tile) / sizeof(uint4));
             for (int e = ll; e < NV; e += P) tl[e] = make_uint4(0u, 0u, 0u, 0u);
@@ -501,7 +504,7 @@ struct Column {
 #pragma unroll
                 for (int u = 0; u < kGatherRegs; ++u) {
                     rows[u] = (u < len) ? (int)lr[u] : -1;
-                    vals[u] = (u < len) ? tile_value<T>(args.kcv, args.kcv32, colA[q] + u) : T(0);
+                    if constexpr (TILE) vals[u] = (u < len) ? tile_value<T>(args.kcv, args.kcv32, colA[q] + u) : T(0);
                 }
 #pragma unroll
                 for (int u = 0; u < kGatherRegs; ++u) {
@@ -512,7 +515,7 @@ struct Column {
                         i = 0;
                     }
                     S.locr[colB[q] + u] = (unsigned char)i;
-                    S.u.tile[tile_pos<TL>(i, c)] = vals[u];
+                    if constexpr (TILE) S.u.tile[tile_pos<TL>(i, c)] = vals[u];
                     atomicOr(&S.mask[i], 1u << c);
                 }
             }
@@ -522,7 +525,8 @@ struct Column {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     rows[u] = (p0 + u < len) ? (int)lr[p0 + u] : -1;
-                    vals[u] = (p0 + u < len) ? tile_value<T>(args.kcv, args.kcv32, colA[q] + p0 + u) : T(0);
+                    if constexpr (TILE)
+                        vals[u] = (p0 + u < len) ? tile_value<T>(args.kcv, args.kcv32, colA[q] + p0 + u) : T(0);
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -533,7 +537,7 @@ struct Column {
                         i = 0;
                     }
                     S.locr[colB[q] + p0 + u] = (unsigned char)i;
-                    S.u.tile[tile_pos<TL>(i, c)] = vals[u];
+                    if constexpr (TILE) S.u.tile[tile_pos<TL>(i, c)] = vals[u];
                     atomicOr(&S.mask[i], 1u << c);
                 }
             }
@@ -544,7 +548,7 @@ struct Column {
             const double v = args.zcv[t];
             if (i >= 0) {
                 S.c[i] = v;
-                S.u.tile[tile_pos<TL>(i, NCOL - 1)] = tile_value<T>(args.zcv, args.zcv32, t);
+                if constexpr (TILE) S.u.tile[tile_pos<TL>(i, NCOL - 1)] = tile_value<T>(args.zcv, args.zcv32, t);
             } else {
                 out2 = fma(v, v, out2);
             }
@@ -686,6 +690,12 @@ struct Column {
                 if (col == NCOL - 1 && i < nJ) S.u.s.y[i] = a[s][t];
             }
         __syncwarp();
+        pivots(S);
+    }
+
+    // the diagonal of R in shared memory: 1/R_kk, the status (zero or
+    // non-finite pivots clear nJ: no further work) and the kappa estimate
+    __device__ __forceinline__ void pivots(ProbSmem<TL> &S) {
         int st = kStOk;
         float rmax = 0.f, rmin = FLT_MAX;  // |R_kk| range, in FP32 (an estimate only)
         for (int k = ll; k < nJ; k += P) {
@@ -710,6 +720,71 @@ struct Column {
             S.kap2 = kap * kap;
         }
         if (status != kStOk) nJ = 0;
+    }
+
+    // factor tape: R (from shared memory, after factor) to the column's slot,
+    // packed (row k from its diagonal, rows in order)
+    __device__ __forceinline__ void tape_store(const LsqArgs &args, const ProbSmem<TL> &S) const {
+        T *dst = reinterpret_cast<T *>(args.fac) + args.fac_off[jj];
+        int base = 0;
+        for (int k = 0; k < nJ; ++k) {
+            for (int c = k + ll; c < nJ; c += P) dst[base + c - k] = S.u.s.R[k * TL::RSTR + c];
+            base += nJ - k;
+        }
+    }
+
+    // factor tape: the column's R from its slot into shared memory (in place
+    // of factor).  The packed rows are copied as 16-byte vectors to the start
+    // of R's array, then moved to their rows from the last one down: row k's
+    // packed start k nJ - k (k - 1) / 2 is at most its place k RSTR + k, so
+    // no row overwrites one that has not moved yet.
+    __device__ __forceinline__ void tape_load(const LsqArgs &args, ProbSmem<TL> &S) {
+        kmax = nJ;
+#pragma unroll
+        for (int o = P; o < 32; o <<= 1) kmax = max(kmax, shfl_xor(kmax, o));
+        constexpr int EV = 16 / (int)sizeof(T);                          // elements per vector
+        constexpr int NVMAX = ((MAXJ * (MAXJ + 1) / 2 + EV - 1) / EV + P - 1) / P;  // vectors per lane
+        const int nel = nJ * (nJ + 1) / 2, nvec = (nel + EV - 1) / EV;
+        const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const T *>(args.fac) +
+                                                           (valid ? args.fac_off[jj] : 0));
+        uint4 v[NVMAX];
+#pragma unroll
+        for (int u = 0; u < NVMAX; ++u)
+            if (ll + u * P < nvec) v[u] = src[ll + u * P];
+#pragma unroll
+        for (int u = 0; u < NVMAX; ++u) {
+            const int e0 = (ll + u * P) * EV;
+            if (ll + u * P < nvec) {
+                union {
+                    uint4 w;
+                    T e[EV];
+                } x;
+                x.w = v[u];
+#pragma unroll
+                for (int q = 0; q < EV; ++q)
+                    if (e0 + q < nel) S.u.s.R[e0 + q] = x.e[q];
+            }
+        }
+        __syncwarp();
+        constexpr int RQ = (MAXJ + P - 1) / P;
+        for (int k = kmax - 1; k >= 1; --k) {  // warp-uniform bounds: the moves need the whole warp's barriers
+            const int ps = k * nJ - k * (k - 1) / 2;
+            T t[RQ];
+#pragma unroll
+            for (int q = 0; q < RQ; ++q) {
+                const int c = k + ll + q * P;
+                if (k < nJ && c < nJ) t[q] = S.u.s.R[ps + c - k];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < RQ; ++q) {
+                const int c = k + ll + q * P;
+                if (k < nJ && c < nJ) S.u.s.R[k * TL::RSTR + c] = t[q];
+            }
+            __syncwarp();
+        }
+        pivots(S);
+        __syncwarp();
     }
 
     // (R^T R)^{-1} applied in place to x (layout c = ll + P q)

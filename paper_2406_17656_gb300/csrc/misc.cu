@@ -296,6 +296,24 @@ cudaError_t round_to_f32(sam_handle h, int64_t n, const double *in, float *out) 
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void tape_sizes_kernel(int64_t N, const int32_t *jcp, int64_t *sizes) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x)
+        sizes[j] = tape_elems(jcp[j + 1] - jcp[j]);
+}
+}  // namespace
+
+cudaError_t tape_offsets(sam_handle h, int64_t N, const int32_t *jcp, int64_t *sizes, int64_t *off) {
+    if (N > 0) {
+        int64_t blocks = (N + 255) / 256;
+        if (blocks > (int64_t)handle_sms(h) * 8) blocks = (int64_t)handle_sms(h) * 8;
+        tape_sizes_kernel<<<(unsigned)blocks, 256, 0, handle_stream(h)>>>(N, jcp, sizes);
+        count_launch(h);
+        if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
+    }
+    return exclusive_scan_i64(h, sizes, off, N);
+}
+
 cudaError_t status_reduce(sam_handle h, const int32_t *colstat, int64_t n, int32_t *flag) {
     if (n == 0) return cudaSuccess;
     int64_t blocks = (n + 255) / 256;

@@ -34,6 +34,7 @@ SAM_FP32_REFINE = 1
 SAM_FLAG_TRUSTED = 1
 SAM_STATIC_MAX_ROWS = 1 << 19  # largest order sam_residual_static accepts
 SAM_NUM_SIZE_CLASSES = 6
+SAM_TAPE_OFF, SAM_TAPE_RECORD, SAM_TAPE_REPLAY = 0, 1, 2
 
 PRECISIONS = {"fp64": SAM_FP64, "fp32r": SAM_FP32_REFINE}
 SPARSIFY_MODES = {"global": 0, "tau": 1, "lfil": 2}
@@ -116,6 +117,8 @@ _SIGS = [
     ("sam_get_tile_variants", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("sam_set_bin_schedule", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("sam_get_bin_schedule", ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    ("sam_factor_tape_bytes", ctypes.c_int32, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.c_int, _i64p]),
+    ("sam_set_factor_tape", ctypes.c_int32, [_vp, ctypes.c_int, _vp, ctypes.c_int64]),
     ("sam_profile", ctypes.c_int32, [_vp, ctypes.c_int]),
     ("sam_profile_read", ctypes.c_int32, [_vp, _i64p, ctypes.POINTER(ctypes.c_double), _i64p]),
     ("sam_peak_flops", ctypes.c_int32, [_vp, ctypes.c_double, _f64p, _f64p]),
@@ -654,6 +657,24 @@ class Handle:
         v = (ctypes.c_int * SAM_NUM_SIZE_CLASSES)()
         _check(load().sam_get_bin_schedule(self.ptr, v, SAM_NUM_SIZE_CLASSES), "sam_get_bin_schedule")
         return list(v)
+
+    def sam_factor_tape_bytes(self, Ss: list, precision="fp32r") -> int:
+        """Bytes of the factor tape of the maps on patterns Ss."""
+        pats = (_vp * len(Ss))(*[s.ptr for s in Ss])
+        out = ctypes.c_int64(0)
+        _check(load().sam_factor_tape_bytes(self.ptr, len(Ss), pats, int(PRECISIONS.get(precision, precision)),
+                                            ctypes.byref(out)), "sam_factor_tape_bytes")
+        return int(out.value)
+
+    def sam_set_factor_tape(self, mode: int, buf=None):
+        """SAM_TAPE_RECORD / SAM_TAPE_REPLAY with a device buffer (a tensor
+        of at least sam_factor_tape_bytes bytes), or SAM_TAPE_OFF."""
+        if mode == SAM_TAPE_OFF or buf is None:
+            _check(load().sam_set_factor_tape(self.ptr, int(mode), None, 0), "sam_set_factor_tape")
+            return
+        nbytes = buf.numel() * buf.element_size()
+        _check(load().sam_set_factor_tape(self.ptr, int(mode), ctypes.c_void_p(buf.data_ptr()), nbytes),
+               "sam_set_factor_tape")
 
     def sam_refine_stats(self):
         """[one step, two steps, FP64 re-solve] column counts of the last
