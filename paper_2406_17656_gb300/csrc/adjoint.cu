@@ -23,8 +23,20 @@
 namespace sam {
 namespace {
 
-template <class TL, bool FP64, bool TAPE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) adjoint_kernel(LsqArgs args, int bin) {
+// blocks per SM that a shape's shared memory allows (1..4); the register
+// budget of the factor-tape shapes is held to it, so registers never lower
+// the occupancy that their smaller shared memory buys
+template <class TL>
+struct AdjBlocks {
+    static constexpr int bytes = (int)sizeof(ProbSmem<TL>) * TL::PPW * kWarpsPerBlock + 1024;
+    static constexpr int raw = 233472 / bytes;
+    static constexpr int value = !TL::LEAN ? 1 : (raw < 1 ? 1 : (raw > 4 ? 4 : raw));
+};
+
+// TL::LEAN: R comes from the forward build's factor tape
+template <class TL, bool FP64>
+__device__ __forceinline__ void adjoint_body(const LsqArgs &args, int bin) {
+    constexpr bool TAPE = TL::LEAN;
     using T = typename TL::T;
     constexpr int P = TL::P, PPW = TL::PPW, RS = TL::RS, CS = TL::CS, JQ = TL::JQ, IQ = TL::IQ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -179,6 +191,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) adjoint_kernel(LsqArgs ar
     }
 }
 
+template <class TL, bool FP64>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) adjoint_kernel(LsqArgs args, int bin) {
+    adjoint_body<TL, FP64>(args, bin);
+}
+
+template <class TL, bool FP64>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, AdjBlocks<TL>::value) adjoint_tape_kernel(LsqArgs args,
+                                                                                                 int bin) {
+    adjoint_body<TL, FP64>(args, bin);
+}
+
 constexpr int kReduceThreads = 256;
 
 // dA(e) for the stored entries e of column c (one warp per column).  The
@@ -261,7 +284,9 @@ __global__ void permute_scatter_kernel(int64_t nnz, const int32_t *perm, const d
 template <class TL, bool FP64>
 cudaError_t launch_one(sam_handle h, const LsqArgs &a, int bin) {
     const size_t smem = sizeof(ProbSmem<TL>) * TL::PPW * kWarpsPerBlock;
-    auto kern = a.fac_mode == kTapeReplay ? adjoint_kernel<TL, FP64, true> : adjoint_kernel<TL, FP64, false>;
+    void (*kern)(LsqArgs, int);
+    if constexpr (TL::LEAN) kern = adjoint_tape_kernel<TL, FP64>;
+    else kern = adjoint_kernel<TL, FP64>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -277,7 +302,20 @@ cudaError_t launch_one(sam_handle h, const LsqArgs &a, int bin) {
 
 cudaError_t launch_adjoint(sam_handle h, int precision, const LsqArgs &args) {
     cudaError_t e;
-    if (precision == SAM_FP64) {
+    const bool tape = args.fac_mode == kTapeReplay;
+    if (precision == SAM_FP64 && tape) {
+        if ((e = launch_one<D0L, true>(h, args, 0)) != cudaSuccess) return e;
+        if ((e = launch_one<D1L, true>(h, args, 1)) != cudaSuccess) return e;
+        if ((e = launch_one<D2L, true>(h, args, 2)) != cudaSuccess) return e;
+        if ((e = launch_one<D3L, true>(h, args, 3)) != cudaSuccess) return e;
+        if ((e = launch_one<D4L, true>(h, args, 4)) != cudaSuccess) return e;
+    } else if (tape) {
+        if ((e = launch_one<F0L, false>(h, args, 0)) != cudaSuccess) return e;
+        if ((e = launch_one<F1L, false>(h, args, 1)) != cudaSuccess) return e;
+        if ((e = launch_one<F2L, false>(h, args, 2)) != cudaSuccess) return e;
+        if ((e = launch_one<F3L, false>(h, args, 3)) != cudaSuccess) return e;
+        if ((e = launch_one<F4L, false>(h, args, 4)) != cudaSuccess) return e;
+    } else if (precision == SAM_FP64) {
         if ((e = launch_one<D0, true>(h, args, 0)) != cudaSuccess) return e;
         if ((e = launch_one<D1, true>(h, args, 1)) != cudaSuccess) return e;
         if ((e = launch_one<D2, true>(h, args, 2)) != cudaSuccess) return e;

@@ -18,8 +18,12 @@ constexpr int kWarpsPerBlock = 4;
 constexpr int kGatherRegs = 12;  // entries per source column gathered with one round of loads
 constexpr int kRowRegs = 8;      // entries per row of B loaded with one round in the residual passes
 
-template <int RG_, int CG_, int RS_, int CS_, typename T_, int MAXI_BIN_>
+// LEAN_: the shape of an adjoint that reads R from a factor tape: no
+// register tile and no staging buffer for it, R packed in shared memory
+// (more problems per SM).
+template <int RG_, int CG_, int RS_, int CS_, typename T_, int MAXI_BIN_, bool LEAN_ = false>
 struct Tile {
+    static constexpr bool LEAN = LEAN_;
     static constexpr int RG = RG_, CG = CG_, RS = RS_, CS = CS_;
     static constexpr int P = RG * CG;    // lanes per column problem
     static constexpr int PPW = 32 / P;   // problems per warp
@@ -31,6 +35,13 @@ struct Tile {
     static constexpr int JQ = (MAXJ + P - 1) / P;  // unknowns per lane (solves)
     static constexpr int IQ = (MAXI + P - 1) / P;  // rows per lane (residuals)
     static constexpr int RSTR = (MAXJ % 2) ? MAXJ : MAXJ + 1;  // odd row stride of R
+    static constexpr int RELEMS = LEAN ? MAXJ * (MAXJ + 1) / 2 : MAXJ * RSTR;  // R's shared-memory elements
+    // position of R(i, k), i <= k: rows of RSTR elements, or (LEAN) packed
+    // rows of MAXJ - i elements from the diagonal
+    static __device__ __forceinline__ int rpos(int i, int k) {
+        if constexpr (LEAN) return i * MAXJ - (i * (i - 1)) / 2 + (k - i);
+        else return i * RSTR + k;
+    }
     static constexpr int VEC = 16 / (int)sizeof(T_);            // elements per 16-byte chunk
     static constexpr int NCH0 = (RS + VEC - 1) / VEC;
     static constexpr int NCH = NCH0 <= 1 ? 1 : NCH0 <= 2 ? 2 : NCH0 <= 4 ? 4 : NCH0 <= 8 ? 8 : 16;  // chunks per lane row
@@ -48,7 +59,7 @@ struct ProbSmem {
     int I[TL::MAXI];
     // column state parked across the QR (Column::park): every lane's colA and
     // (colB << 16 | clen), and the group's scalars
-    int park[2 * TL::P * TL::JQ];
+    int park[TL::LEAN ? 1 : 2 * TL::P * TL::JQ];
     int park_i[8];
     long long park_l[2];
     unsigned mask[TL::MAXI];
@@ -61,7 +72,7 @@ struct ProbSmem {
     unsigned char locr[TL::NBCAP];
     union U {
         // [B c], only until registers are loaded (see tile_pos)
-        __align__(16) T tile[TL::NCOL * TL::RG * TL::RSP];
+        __align__(16) T tile[TL::LEAN ? 16 / sizeof(T) : TL::NCOL * TL::RG * TL::RSP];
         struct S {
             int rowstart[TL::MAXI + 1];
             int rowent[TL::NBCAP];
@@ -70,7 +81,7 @@ struct ProbSmem {
             double w[TL::MAXI];  // B lambda (adjoint only)
             T y[TL::MAXJ];
             T dinv[TL::MAXJ];
-            T R[TL::MAXJ * TL::RSTR];
+            T R[TL::RELEMS];
         } s;
     } u;
 };
@@ -284,7 +295,7 @@ struct SolveUpper {  // R x = y, k from high to low
                 for (int q = 0; q <= Q; ++q) {
                     const int i = ll + q * P;
                     // rows of R at k >= n were never written: do not touch them
-                    if (i < k && k < n) x[q] = fma(-R[i * TL::RSTR + k], xk, x[q]);
+                    if (i < k && k < n) x[q] = fma(-R[TL::rpos(i, k)], xk, x[q]);
                 }
             }
             SolveUpper<TL, Q - 1>::run(R, dinv, x, n, ll, gbase);
@@ -308,7 +319,7 @@ struct SolveUpperT {  // R^T x = y, k from low to high
 #pragma unroll
                 for (int q = Q; q < TL::JQ; ++q) {
                     const int i = ll + q * P;
-                    if (i > k && i < n) x[q] = fma(-R[k * TL::RSTR + i], xk, x[q]);
+                    if (i > k && i < n) x[q] = fma(-R[TL::rpos(k, i)], xk, x[q]);
                 }
             }
             SolveUpperT<TL, Q + 1>::run(R, dinv, x, n, ll, gbase);
@@ -379,6 +390,17 @@ using F1b = Tile<2, 4, 13, 3, float, 26>;
 using F2b = Tile<4, 8, 10, 3, float, 40>;
 using F3b = Tile<4, 8, 13, 4, float, 52>;
 using F4b = Tile<4, 8, 16, 4, float, 64>;
+// the adjoint's shapes when R comes from a factor tape
+using F0L = Tile<2, 2, 7, 3, float, 14, true>;
+using F1L = Tile<2, 2, 13, 5, float, 26, true>;
+using F2L = Tile<4, 4, 10, 6, float, 40, true>;
+using F3L = Tile<4, 4, 13, 7, float, 52, true>;
+using F4L = Tile<4, 4, 16, 7, float, 64, true>;
+using D0L = Tile<2, 2, 7, 3, double, 14, true>;
+using D1L = Tile<2, 4, 13, 3, double, 26, true>;
+using D2L = Tile<4, 8, 10, 3, double, 40, true>;
+using D3L = Tile<4, 8, 13, 4, double, 52, true>;
+using D4L = Tile<4, 8, 16, 4, double, 64, true>;
 
 static_assert(F0::MAXI >= 14 && F0::MAXJ >= 5, "bin 0");
 static_assert(F1b::MAXI >= 26 && F1b::MAXJ >= 9 && F2b::MAXI >= 40 && F2b::MAXJ >= 23, "variants");
@@ -686,7 +708,7 @@ struct Column {
 #pragma unroll
             for (int t = 0; t < CS; ++t) {
                 const int i = s * RG + rg, col = t * CG + cg;
-                if (col < MAXJ && i <= col && col < nJ) S.u.s.R[i * TL::RSTR + col] = a[s][t];
+                if (col < MAXJ && i <= col && col < nJ) S.u.s.R[TL::rpos(i, col)] = a[s][t];
                 if (col == NCOL - 1 && i < nJ) S.u.s.y[i] = a[s][t];
             }
         __syncwarp();
@@ -699,7 +721,7 @@ struct Column {
         int st = kStOk;
         float rmax = 0.f, rmin = FLT_MAX;  // |R_kk| range, in FP32 (an estimate only)
         for (int k = ll; k < nJ; k += P) {
-            const T rkk = S.u.s.R[k * TL::RSTR + k];
+            const T rkk = S.u.s.R[TL::rpos(k, k)];
             const double d = to_f64<T>(rkk);
             if (!finite64(d)) st = max(st, (int)kStNonfinite);
             else if (d == 0.0) st = max(st, (int)kStRank);
@@ -728,7 +750,7 @@ struct Column {
         T *dst = reinterpret_cast<T *>(args.fac) + args.fac_off[jj];
         int base = 0;
         for (int k = 0; k < nJ; ++k) {
-            for (int c = k + ll; c < nJ; c += P) dst[base + c - k] = S.u.s.R[k * TL::RSTR + c];
+            for (int c = k + ll; c < nJ; c += P) dst[base + c - k] = S.u.s.R[TL::rpos(k, c)];
             base += nJ - k;
         }
     }
@@ -736,8 +758,9 @@ struct Column {
     // factor tape: the column's R from its slot into shared memory (in place
     // of factor).  The packed rows are copied as 16-byte vectors to the start
     // of R's array, then moved to their rows from the last one down: row k's
-    // packed start k nJ - k (k - 1) / 2 is at most its place k RSTR + k, so
-    // no row overwrites one that has not moved yet.
+    // packed start k nJ - k (k - 1) / 2 is at most its place rpos(k, k)
+    // (k RSTR + k, or k MAXJ - k (k - 1) / 2 packed), so no row overwrites
+    // one that has not moved yet.
     __device__ __forceinline__ void tape_load(const LsqArgs &args, ProbSmem<TL> &S) {
         kmax = nJ;
 #pragma unroll
@@ -779,7 +802,7 @@ struct Column {
 #pragma unroll
             for (int q = 0; q < RQ; ++q) {
                 const int c = k + ll + q * P;
-                if (k < nJ && c < nJ) S.u.s.R[k * TL::RSTR + c] = t[q];
+                if (k < nJ && c < nJ) S.u.s.R[TL::rpos(k, c)] = t[q];
             }
             __syncwarp();
         }
