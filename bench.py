@@ -98,6 +98,10 @@ def parse():
     ap.add_argument("--profile-sparsify", type=int, default=0, metavar="CALLS",
                     help="profiling aid: run CALLS batched column-tau (0.8) sparsifications of the benchmark's maps "
                          "and exit (no JSON line)")
+    ap.add_argument("--profile-build", type=int, default=0, metavar="STEPS",
+                    help="profiling aid: run STEPS batched builds of the sequence (--nx, --maps, --level, "
+                         "--refine; patterns built once) and print the time per build")
+    ap.add_argument("--fp64", action="store_true", help="with --profile-build and --refine 0: the plain FP64 build")
     ap.add_argument("--tape", action="store_true",
                     help="with --profile-adjoint: the build records a factor tape and the adjoints replay it")
     ap.add_argument("--profile-adjoint", type=int, default=0, metavar="STEPS",
@@ -789,6 +793,20 @@ def config_figures(h, sam, torch, dev, stream, nsteps=7):
     ex.update(accuracy(a1s, a0s, 1, 2, n5, ms5, (pairs[-1][1], pairs[-1][0]), seed=5))
     line("q1_pairs_512x512_x32_level1", 32 * n5, 32, ms5, ex,
          roof=([p[1] for p in pairs], 1, "fp32r", 2), orc=(pairs[0][1], pairs[0][0], 1))
+    # level-3 maps (the paper's "level 2", Sec. 5.1) of the benchmark's Q1 sequence, 2 maps: interior
+    # columns of 81 x 49 go to the large size class (one thread block per column, FP32 tile in shared
+    # memory + one guarded FP64 step; the FP64 arm solves them with an FP64 tile)
+    seq = W.config2(nmat=2)
+    aks = [sam.Csr.from_host(m, dev) for m in seq.mats]
+    nq = aks[0].n
+    h.sam_set_tile_variants([0] * 6)
+    h.sam_set_bin_schedule(list(range(6)))
+    msq = timed(build_step(aks, aks[0], 3, "fp32r", 1), 3)
+    ex = accuracy(aks, aks[0], 3, 1, nq, msq, (seq.mats[-1], seq.mats[0]), nsample=60, seed=6)
+    ex["note"] = "interior columns (81 x 49) are solved by the large size class (a thread block per column)"
+    line("q1_diffusion_256x256_seq2_level3", len(aks) * nq, len(aks), msq, ex, roof=(seq.mats, 3, "fp32r", 1))
+    del aks
+    torch.cuda.empty_cache()
     h.sam_set_tile_variants(saved_variants)
     h.sam_set_bin_schedule(saved_schedule)
     return out
@@ -877,6 +895,19 @@ def main():
     a0 = sam.Csr.from_host(a0h, dev)
     if args.profile_gmres > 0:
         profile_gmres(h, sam, torch, dev, aks, a0, n, args.level, args.profile_gmres)
+        h.close()
+        return
+    if args.profile_build > 0:
+        pats = h.sam_pattern_build_batched(aks, args.level)
+        prec = "fp64" if args.refine == 0 and args.fp64 else "fp32r"
+        out = h.sam_build_batched(aks, a0, pats, prec, args.refine)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.profile_build):
+            h.sam_build_batched(aks, a0, pats, prec, args.refine, M_val=out[3])
+        torch.cuda.synchronize()
+        print("build: %d batched builds of %d maps, level %d, %s, %.3f ms per build" % (
+            args.profile_build, K, args.level, prec, (time.perf_counter() - t) * 1e3 / args.profile_build))
         h.close()
         return
     if args.profile_sparsify > 0:

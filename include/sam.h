@@ -85,7 +85,8 @@ enum {
  * 4 |d_1|^2 > 1e-12 |m|^2 or the prediction after step 1 misses; after the
  * last step (2 in automatic mode, s otherwise) a predicted error above
  * 1e-10 |m|, or rho >= 1/2, sends the column to an FP64 Householder
- * re-solve (the large class's kernel).  sam_refine_stats counts the
+ * re-solve (the large class's FP64 kernel).  The large class's FP32 tile
+ * takes the same steps under the same test.  sam_refine_stats counts the
  * outcomes.
  */
 #define SAM_REFINE_AUTO (-1)
@@ -122,9 +123,10 @@ void sam_limits(int32_t *max_rows, int32_t *max_cols);
  * |I_j| (|J_j| + 1) <= max_tile[b]; a column that fits none is
  * SAM_ERR_UNSUPPORTED.  Classes 0..4 are register tiles with
  * FP32 or FP64 arithmetic; class 5 (SAM_NUM_SIZE_CLASSES - 1) is one thread
- * block per column with an FP64 tile in shared memory, whatever the
- * precision asked for, and no adjoint (sam_build_backward reports its
- * columns as SAM_ERR_UNSUPPORTED).  variants[b]: tile shapes of class b
+ * block per column with the tile in shared memory (FP64 for SAM_FP64; FP32
+ * with the FP64 refinement steps and their guard for SAM_FP32_REFINE), and
+ * no adjoint (sam_build_backward reports its columns as
+ * SAM_ERR_UNSUPPORTED).  variants[b]: tile shapes of class b
  * (sam_tune, sam_set_tile_variants).  count must be SAM_NUM_SIZE_CLASSES;
  * any output may be NULL.
  */
@@ -526,8 +528,8 @@ sam_status sam_get_bin_schedule(sam_handle h, int *to, int count);
  * sam_refine_stats -- outcome counts of the last guarded SAM_FP32_REFINE
  * build on this handle (refine_steps = SAM_REFINE_AUTO or >= 1):
  * counts[0] columns that kept their solution after one step, counts[1]
- * after two or more, counts[2] solved in FP64 (re-solved after missing the
- * target, or in the large size class) (count must be 3).
+ * after two or more, counts[2] re-solved in FP64 after missing the target
+ * (count must be 3).
  * Synchronises the handle's stream.
  */
 sam_status sam_refine_stats(sam_handle h, int64_t *counts, int count);

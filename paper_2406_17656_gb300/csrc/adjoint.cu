@@ -244,7 +244,8 @@ __global__ void __launch_bounds__(kReduceThreads) adjoint_reduce_kernel(int N, c
     double acc = 0.0;
     for (int t0 = tb; t0 < te; t0 += W) {
         const int64_t mine = (lane < W && t0 + lane < te) ? dbase[t0 + lane] : -1;
-        for (int k0 = 0; k0 < KC; k0 += kLoads) {
+        const int kc = min(KC, (te - t0 + G - 1) / G);  // the most entries a group has in this chunk
+        for (int k0 = 0; k0 < kc; k0 += kLoads) {
             int64_t b[kLoads];
             double v[kLoads];
 #pragma unroll
@@ -304,14 +305,16 @@ cudaError_t launch_adjoint(sam_handle h, int precision, const LsqArgs &args) {
     cudaError_t e;
     const bool tape = args.fac_mode == kTapeReplay;
     if (precision == SAM_FP64 && tape) {
-        if ((e = launch_one<D0L, true>(h, args, 0)) != cudaSuccess) return e;
-        if ((e = launch_one<D1L, true>(h, args, 1)) != cudaSuccess) return e;
+        if ((e = launch_one<D0, true>(h, args, 0)) != cudaSuccess) return e;
+        if ((e = launch_one<D1, true>(h, args, 1)) != cudaSuccess) return e;
         if ((e = launch_one<D2L, true>(h, args, 2)) != cudaSuccess) return e;
         if ((e = launch_one<D3L, true>(h, args, 3)) != cudaSuccess) return e;
         if ((e = launch_one<D4L, true>(h, args, 4)) != cudaSuccess) return e;
     } else if (tape) {
-        if ((e = launch_one<F0L, false>(h, args, 0)) != cudaSuccess) return e;
-        if ((e = launch_one<F1L, false>(h, args, 1)) != cudaSuccess) return e;
+        // the two smallest classes recompute R: their QR (at most 9
+        // unknowns) costs less than reading and unpacking the tape
+        if ((e = launch_one<F0, false>(h, args, 0)) != cudaSuccess) return e;
+        if ((e = launch_one<F1, false>(h, args, 1)) != cudaSuccess) return e;
         if ((e = launch_one<F2L, false>(h, args, 2)) != cudaSuccess) return e;
         if ((e = launch_one<F3L, false>(h, args, 3)) != cudaSuccess) return e;
         if ((e = launch_one<F4L, false>(h, args, 4)) != cudaSuccess) return e;

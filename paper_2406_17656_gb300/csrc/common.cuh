@@ -219,9 +219,10 @@ cudaError_t launch_refine_fallback(sam_handle h, const LsqArgs &args, int N, int
 
 // Least-squares launches for every size class.
 cudaError_t launch_lsq(sam_handle h, int precision, const LsqArgs &args);
-// the large class (any precision: solved in FP64); profile: time it as
-// size class `bin` with the handle's tracing events
-cudaError_t launch_lsq_big(sam_handle h, const LsqArgs &args, int bin, bool profile = true);
+// the large class; profile: time it as size class `bin` with the handle's
+// tracing events; fp32: FP32 tile and QR with the refinement steps of
+// args.refine_steps (SAM_FP32_REFINE builds), else FP64 throughout
+cudaError_t launch_lsq_big(sam_handle h, const LsqArgs &args, int bin, bool profile = true, bool fp32 = false);
 // one size class (the items args.item_lo/item_hi select, else all of it)
 cudaError_t launch_lsq_bin(sam_handle h, int precision, const LsqArgs &args, int bin);
 cudaError_t launch_adjoint(sam_handle h, int precision, const LsqArgs &args);

@@ -305,7 +305,7 @@ cudaError_t launch_one(sam_handle h, const LsqArgs &a, int bin) {
 }  // namespace
 
 cudaError_t launch_lsq_bin(sam_handle h, int precision, const LsqArgs &args, int bin) {
-    if (bin == kBinBig) return launch_lsq_big(h, args, bin);
+    if (bin == kBinBig) return launch_lsq_big(h, args, bin, true, precision == SAM_FP32_REFINE);
     if (precision == SAM_FP64) {
         switch (bin) {
             case 0: return launch_one<D0, true>(h, args, 0);

@@ -14,15 +14,22 @@
 //     outside I_j go to the residual only;
 //   * textbook Householder QR of [B c] (Golub & Van Loan, Matrix
 //     Computations, Alg. 5.2.1, with the right-hand side as the last
-//     column): one warp forms reflector k, the block's warps apply it to
-//     the remaining columns, one column per warp, the dot products summed
-//     lane-wise then by a fixed xor tree (deterministic);
+//     column): the block's warps apply reflector k to the remaining
+//     columns, one column per warp, the dot products summed lane-wise then
+//     by a fixed xor tree (deterministic); the warp that updates column
+//     k + 1 forms reflector k + 1 at once (one barrier per reflector);
 //   * back substitution R m = (Q^T c)(1:|J_j|) by one warp;
 //   * the residual r = c - B m from its definition in FP64 (the stored
 //     entries of B, column by column), ||r||^2 plus the target's entries
 //     outside I_j.
-// The class is solved in FP64 whatever precision the build asks for: these
-// columns are rare, and the FP64 solve meets both accuracy bars.
+// Two arithmetic types.  FP64 (SAM_FP64 builds, and the re-solve of every
+// column that the refinement's guard flags): tile, QR and solves in FP64.
+// FP32 (SAM_FP32_REFINE builds): the tile, the QR and the triangular solves
+// in FP32 (half the shared memory: two blocks per SM), then the corrected
+// semi-normal-equation steps of the register classes, g = B^T r in FP64,
+// R^T R d = g in FP32, m += d, r -= B d in FP64, under the same accuracy
+// guard; a column that misses it is re-solved by the FP64 kernel.
+#include <cfloat>
 #include <climits>
 
 #include "common.cuh"
@@ -33,9 +40,10 @@ namespace {
 constexpr int kBigThreads = 512;
 constexpr int kBigWarps = kBigThreads / 32;
 
-enum { kSUk = 0, kSTau, kSBeta, kSOut2, kSRes2, kSNum };
+enum { kSOut2 = 0, kSRes2, kSKap2, kSMsq, kSDprev, kSNum };
+enum { kRStop = 0, kRMiss, kRUsed, kRNum };
 
-struct BigHdr {
+struct __align__(16) BigHdr {
     long long colA[kBigJCap];  // value offset of column c of B (this map's values)
     int J[kBigJCap];
     int kcol[kBigJCap];        // structure offset of column c (kcp of the source column)
@@ -43,9 +51,13 @@ struct BigHdr {
     int cb[kBigJCap + 1];      // prefix of clen: gather order of the candidates
     int I[kBigICap];           // shadow rows, ascending
     double r[kBigICap];        // c, then the residual
-    double y[kBigJCap];        // (Q^T c)(1:|J|)
+    double y[kBigJCap];        // (Q^T c)(1:|J|), in the tile's type
     double m[kBigJCap];        // the solution
+    double g[kBigJCap];        // refinement: B^T r (rounded to FP32)
+    float dv[kBigJCap];        // refinement: the correction d
     int wsum[kBigWarps];
+    int rstate[kRNum];         // refinement: stop, guard missed, steps taken
+    double qp[2][4];           // reflectors k and k + 1: u_k, tau', beta (in the tile's type)
     double scal[kSNum];
     int status;                // of the current column (uniform after a barrier)
     int nI;
@@ -53,11 +65,28 @@ struct BigHdr {
 };
 static_assert(sizeof(BigHdr) % 16 == 0, "the tile after the header must stay 16-byte aligned");
 
-__device__ __forceinline__ double warp_sum_f64(double v) {
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+__device__ __forceinline__ double warp_sum_f64(double v) { return warp_sum<double>(v); }
+
+// a value of [B c] in the tile's type: FP64 as stored, FP32 from the rounded
+// copy the build made for the FP32 tiles
+template <typename TT>
+__device__ __forceinline__ TT big_value(const double *v, const float *v32, int64_t i) {
+    if constexpr (sizeof(TT) == 4) return v32[i];
+    else return v[i];
+}
+
+// blocks per SM: the FP64 tile fills the shared memory of one, the FP32 tile
+// half of it
+template <typename TT>
+struct BigBlocks {
+    static constexpr int value = sizeof(TT) == 4 ? 2 : 1;
+};
 
 __device__ __forceinline__ int search_rows(const int *I, int nI, int key) {
     int lo = 0, hi = nI - 1;
@@ -74,10 +103,73 @@ __device__ __forceinline__ void set_status(BigHdr &H, int st) {
     atomicMax(&H.status, st);
 }
 
-__global__ void __launch_bounds__(kBigThreads, 1) lsq_big_kernel(LsqArgs args, int bin) {
+// Reflector k (u_k, tau') applied by one warp to the NQ columns t0, t0 + 16,
+// ... of the tile: each column's dot product summed lane-wise then by a
+// fixed xor tree, as one column at a time would
+template <typename TT, int NQ>
+__device__ __forceinline__ void apply_cols(TT *T, int ld, int nI, int k, int t0, int lane, TT uk, TT taup) {
+    TT w[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) w[q] = TT(0);
+    for (int i = k + 1 + lane; i < nI; i += 32) {
+        const TT v = T[i + ld * k];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) w[q] = fma(v, T[i + ld * (t0 + q * kBigWarps)], w[q]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) w[q] += __shfl_xor_sync(0xffffffffu, w[q], o);
+    TT coef[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) coef[q] = taup * fma(uk, T[k + ld * (t0 + q * kBigWarps)], w[q]);
+    __syncwarp();
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int t = t0 + q * kBigWarps;
+            T[k + ld * t] = fma(-coef[q], uk, T[k + ld * t]);
+        }
+    }
+    for (int i = k + 1 + lane; i < nI; i += 32) {
+        const TT v = T[i + ld * k];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int t = t0 + q * kBigWarps;
+            T[i + ld * t] = fma(-coef[q], v, T[i + ld * t]);
+        }
+    }
+}
+
+// Householder reflector of column k of the tile (rows k..nI-1), by one warp:
+// out = {u_k, tau', beta} with beta = -sign(alpha) ||x||, u_k = alpha - beta
+// and tau' = -1 / (beta u_k) (0 when the column is already zero below the
+// diagonal); the sum of squares lane-wise, then by a fixed xor tree
+template <typename TT>
+__device__ __forceinline__ void reflector(const TT *T, int ld, int nI, int k, int lane, TT *out) {
+    TT s = TT(0);
+    for (int i = k + 1 + lane; i < nI; i += 32) {
+        const TT x = T[i + ld * k];
+        s = fma(x, x, s);
+    }
+    s = warp_sum<TT>(s);
+    if (lane == 0) {
+        const TT alpha = T[k + ld * k];
+        const TT nrm = sqrt(fma(alpha, alpha, s));
+        const TT beta = (s == TT(0)) ? alpha : ((alpha >= TT(0)) ? -nrm : nrm);
+        const TT uk = alpha - beta;
+        out[0] = uk;
+        out[1] = (s == TT(0)) ? TT(0) : TT(-1) / (beta * uk);
+        out[2] = beta;
+    }
+}
+
+template <typename TT>
+__global__ void __launch_bounds__(kBigThreads, BigBlocks<TT>::value) lsq_big_kernel(LsqArgs args, int bin) {
+    constexpr bool F32 = sizeof(TT) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BigHdr &H = *reinterpret_cast<BigHdr *>(smem_raw);
-    double *T = reinterpret_cast<double *>(smem_raw + sizeof(BigHdr));
+    TT *T = reinterpret_cast<TT *>(smem_raw + sizeof(BigHdr));
     int *keys = reinterpret_cast<int *>(T);  // the candidate rows, before the tile exists
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -190,9 +282,18 @@ __global__ void __launch_bounds__(kBigThreads, 1) lsq_big_kernel(LsqArgs args, i
         __syncthreads();
         const int nI = H.nI;
         const int ld = nI;
+        TT *yT = reinterpret_cast<TT *>(H.y);
+        // FP32 tile: the local row of every stored entry of B, kept after the
+        // tile when it fits there (the refinement passes then skip the row
+        // searches); lr[H.cb[c] + e] for entry e of column c
+        // and their FP64 values after those (8-byte aligned): no global loads
+        // in the passes
+        int *lr = reinterpret_cast<int *>(T + (size_t)ld * (nJ + 1));
+        const bool keep_lr = F32 && H.status == kStOk && 3 * (int64_t)H.cb[nJ] + 1 + (int64_t)ld * (nJ + 1) <= kBigTileDoubles;
+        double *bv = reinterpret_cast<double *>(lr + ((ld * (nJ + 1) + (keep_lr ? H.cb[nJ] : 0)) & 1) + (keep_lr ? H.cb[nJ] : 0));
         // ---- the tile [B c] and the target column
         if (H.status == kStOk) {
-            for (int q = tid; q < ld * (nJ + 1); q += kBigThreads) T[q] = 0.0;
+            for (int q = tid; q < ld * (nJ + 1); q += kBigThreads) T[q] = TT(0);
             for (int i = tid; i < nI; i += kBigThreads) H.r[i] = 0.0;
         }
         __syncthreads();
@@ -200,8 +301,12 @@ __global__ void __launch_bounds__(kBigThreads, 1) lsq_big_kernel(LsqArgs args, i
             for (int c = warp; c < nJ; c += kBigWarps)
                 for (int e = lane; e < H.clen[c]; e += 32) {
                     const int p = search_rows(H.I, nI, args.kri[H.kcol[c] + e]);
-                    if (p >= 0) T[p + ld * c] = args.kcv[H.colA[c] + e];
+                    if (p >= 0) T[p + ld * c] = big_value<TT>(args.kcv, args.kcv32, H.colA[c] + e);
                     else set_status(H, kStUnsupported);  // impossible: every row of B is in I_j
+                    if (keep_lr) {
+                        lr[H.cb[c] + e] = p;
+                        bv[H.cb[c] + e] = args.kcv[H.colA[c] + e];
+                    }
                 }
             if (warp == kBigWarps - 1) {
                 const int zb = args.zcp[zc], ze = args.zcp[zc + 1];
@@ -210,7 +315,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) lsq_big_kernel(LsqArgs args, i
                     const double v = args.zcv[t];
                     const int p = search_rows(H.I, nI, args.zri[t] + zro);
                     if (p >= 0) {
-                        T[p + ld * nJ] = v;
+                        T[p + ld * nJ] = big_value<TT>(args.zcv, args.zcv32, t);
                         H.r[p] = v;
                     } else {
                         o2 = fma(v, v, o2);
@@ -221,42 +326,37 @@ __global__ void __launch_bounds__(kBigThreads, 1) lsq_big_kernel(LsqArgs args, i
             }
         }
         __syncthreads();
-        // ---- Householder QR of [B c]
+        // ---- Householder QR of [B c].  Reflector k + 1 is formed by warp 0
+        // right after it applied reflector k to column k + 1 (its parameters
+        // double-buffered), so each reflector costs one block barrier.
         if (H.status == kStOk) {
+            TT *qp = reinterpret_cast<TT *>(&H.qp[0][0]);  // qp[4 b + q], b = reflector parity
+            if (warp == 0) reflector<TT>(T, ld, nI, 0, lane, qp);
+            __syncthreads();
             for (int k = 0; k < nJ; ++k) {
-                if (warp == 0) {
-                    double s = 0.0;
-                    for (int i = k + 1 + lane; i < nI; i += 32) {
-                        const double x = T[i + ld * k];
-                        s = fma(x, x, s);
+                const TT *qk = qp + 4 * (k & 1);
+                const TT uk = qk[0], taup = qk[1];
+                if (taup != TT(0)) {
+                    // FP32: a warp's columns t, t + 16, t + 32, t + 48 at once
+                    // (independent dot products and updates; the FP64 pipe
+                    // gains nothing from it and pays for idle slots)
+                    constexpr int G = F32 ? 4 : 1;
+                    for (int t0 = k + 1 + warp; t0 <= nJ; t0 += G * kBigWarps) {
+                        const int nq = min(G, (nJ - t0) / kBigWarps + 1);
+                        if (nq >= 4) apply_cols<TT, 4>(T, ld, nI, k, t0, lane, uk, taup);
+                        else if (nq == 3) apply_cols<TT, 3>(T, ld, nI, k, t0, lane, uk, taup);
+                        else if (nq == 2) apply_cols<TT, 2>(T, ld, nI, k, t0, lane, uk, taup);
+                        else apply_cols<TT, 1>(T, ld, nI, k, t0, lane, uk, taup);
+                        if (t0 == k + 1 && t0 < nJ) {  // warp 0: column k + 1 is final below row k
+                            __syncwarp();
+                            reflector<TT>(T, ld, nI, t0, lane, qp + 4 * (t0 & 1));
+                        }
                     }
-                    s = warp_sum_f64(s);
-                    if (lane == 0) {
-                        const double alpha = T[k + ld * k];
-                        const double nrm = sqrt(fma(alpha, alpha, s));
-                        const double beta = (s == 0.0) ? alpha : ((alpha >= 0.0) ? -nrm : nrm);
-                        const double uk = alpha - beta;
-                        H.scal[kSUk] = uk;
-                        H.scal[kSTau] = (s == 0.0) ? 0.0 : -1.0 / (beta * uk);
-                        H.scal[kSBeta] = beta;
-                    }
+                } else if (warp == 0 && k + 1 < nJ) {
+                    reflector<TT>(T, ld, nI, k + 1, lane, qp + 4 * ((k + 1) & 1));
                 }
+                if (tid == 0) T[k + ld * k] = qk[2];
                 __syncthreads();
-                const double uk = H.scal[kSUk], taup = H.scal[kSTau];
-                if (taup != 0.0) {
-                    for (int t = k + 1 + warp; t <= nJ; t += kBigWarps) {
-                        double w = 0.0;
-                        for (int i = k + 1 + lane; i < nI; i += 32) w = fma(T[i + ld * k], T[i + ld * t], w);
-                        w = warp_sum_f64(w);
-                        w = fma(uk, T[k + ld * t], w);
-                        const double coef = taup * w;
-                        __syncwarp();
-                        if (lane == 0) T[k + ld * t] = fma(-coef, uk, T[k + ld * t]);
-                        for (int i = k + 1 + lane; i < nI; i += 32) T[i + ld * t] = fma(-coef, T[i + ld * k], T[i + ld * t]);
-                    }
-                }
-                __syncthreads();
-                if (tid == 0) T[k + ld * k] = H.scal[kSBeta];
             }
         }
         __syncthreads();
@@ -264,20 +364,20 @@ __global__ void __launch_bounds__(kBigThreads, 1) lsq_big_kernel(LsqArgs args, i
         if (H.status == kStOk && warp == 0) {
             int st = kStOk;
             for (int k = lane; k < nJ; k += 32) {
-                const double d = T[k + ld * k];
+                const double d = (double)T[k + ld * k];
                 if (!isfinite(d)) st = max(st, (int)kStNonfinite);
                 else if (d == 0.0) st = max(st, (int)kStRank);
-                H.y[k] = T[k + ld * nJ];
+                yT[k] = T[k + ld * nJ];
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) st = max(st, __shfl_xor_sync(0xffffffffu, st, o));
             __syncwarp();
             if (st == kStOk) {
                 for (int k = nJ - 1; k >= 0; --k) {
-                    const double mk = H.y[k] / T[k + ld * k];
+                    const TT mk = yT[k] / T[k + ld * k];
                     __syncwarp();
-                    for (int i = lane; i < k; i += 32) H.y[i] = fma(-T[i + ld * k], mk, H.y[i]);
-                    if (lane == 0) H.m[k] = mk;
+                    for (int i = lane; i < k; i += 32) yT[i] = fma(-T[i + ld * k], mk, yT[i]);
+                    if (lane == 0) H.m[k] = (double)mk;
                     __syncwarp();
                 }
                 int nf = 0;
@@ -285,8 +385,9 @@ __global__ void __launch_bounds__(kBigThreads, 1) lsq_big_kernel(LsqArgs args, i
                     const double mc = H.m[c];
                     nf |= !isfinite(mc);
                     for (int e = lane; e < H.clen[c]; e += 32) {
-                        const int p = search_rows(H.I, nI, args.kri[H.kcol[c] + e]);
-                        if (p >= 0) H.r[p] = fma(-args.kcv[H.colA[c] + e], mc, H.r[p]);
+                        const int p = keep_lr ? lr[H.cb[c] + e] : search_rows(H.I, nI, args.kri[H.kcol[c] + e]);
+                        const double b = keep_lr ? bv[H.cb[c] + e] : args.kcv[H.colA[c] + e];
+                        if (p >= 0) H.r[p] = fma(-b, mc, H.r[p]);
                     }
                     __syncwarp();
                 }
@@ -298,7 +399,123 @@ __global__ void __launch_bounds__(kBigThreads, 1) lsq_big_kernel(LsqArgs args, i
             }
             if (lane == 0 && st != kStOk) set_status(H, st);
         }
+        if (tid == 0) {
+            H.rstate[kRMiss] = 0;
+            H.rstate[kRUsed] = kAutoSteps + 1;  // solved in FP64
+        }
         __syncthreads();
+        // ---- FP32 tile: corrected semi-normal-equation steps, r = c - B m0 above
+        if constexpr (F32) {
+            const bool autoref = args.refine_steps < 0;
+            const int steps = autoref ? kAutoSteps : args.refine_steps;
+            if (H.status == kStOk && steps > 0) {
+                float *gf = reinterpret_cast<float *>(H.g);
+                if (tid == 0) {  // the guard's kappa estimate (|R_kk| range) and |m_0|^2
+                    float rmax = 0.f, rmin = FLT_MAX;
+                    double m2 = 0.0;
+                    for (int k = 0; k < nJ; ++k) {
+                        const float a = fabsf((float)T[k + ld * k]);
+                        rmax = fmaxf(rmax, a);
+                        rmin = fminf(rmin, a);
+                        m2 = fma(H.m[k], H.m[k], m2);
+                    }
+                    const float kap = rmax / rmin;
+                    H.scal[kSKap2] = kap * kap;
+                    H.scal[kSMsq] = m2;
+                    H.rstate[kRStop] = 0;
+                }
+                __syncthreads();
+                for (int step = 0; step < steps; ++step) {
+                    // g = B^T r (FP64), a warp per column
+                    for (int c = warp; c < nJ; c += kBigWarps) {
+                        double acc = 0.0;
+                        for (int e = lane; e < H.clen[c]; e += 32) {
+                            const int p = keep_lr ? lr[H.cb[c] + e] : search_rows(H.I, nI, args.kri[H.kcol[c] + e]);
+                            const double b = keep_lr ? bv[H.cb[c] + e] : args.kcv[H.colA[c] + e];
+                            if (p >= 0) acc = fma(b, H.r[p], acc);
+                        }
+                        acc = warp_sum_f64(acc);
+                        if (lane == 0) gf[c] = (float)acc;  // the FP32 solve's right-hand side
+                    }
+                    __syncthreads();
+                    if (warp == 0) {
+                        // R^T y = g, then R d = y (FP32; R in the tile's upper triangle)
+                        for (int k = 0; k < nJ; ++k) {
+                            float sk = 0.f;
+                            for (int i = lane; i < k; i += 32) sk = fmaf((float)T[i + ld * k], H.dv[i], sk);
+                            sk = warp_sum<float>(sk);
+                            if (lane == 0) H.dv[k] = (gf[k] - sk) / (float)T[k + ld * k];
+                            __syncwarp();
+                        }
+                        for (int k = nJ - 1; k >= 0; --k) {
+                            const float dk = H.dv[k] / (float)T[k + ld * k];
+                            __syncwarp();
+                            for (int i = lane; i < k; i += 32) H.dv[i] = fmaf(-(float)T[i + ld * k], dk, H.dv[i]);
+                            if (lane == 0) H.dv[k] = dk;
+                            __syncwarp();
+                        }
+                        // m += d (FP64), r -= B d (FP64, column by column)
+                        float dsq = 0.f;
+                        for (int c = lane; c < nJ; c += 32) {
+                            const float d = H.dv[c];
+                            const double dd = (double)d;
+                            H.m[c] += dd;
+                            H.y[c] = dd;  // d in FP64 for r -= B d
+                            dsq = fmaf(d, d, dsq);
+                        }
+                        __syncwarp();
+                        dsq = warp_sum<float>(dsq);
+                        for (int c = 0; c < nJ; ++c) {
+                            const double dc = H.y[c];
+                            for (int e = lane; e < H.clen[c]; e += 32) {
+                                const int p = keep_lr ? lr[H.cb[c] + e] : search_rows(H.I, nI, args.kri[H.kcol[c] + e]);
+                                const double b = keep_lr ? bv[H.cb[c] + e] : args.kcv[H.colA[c] + e];
+                                if (p >= 0) H.r[p] = fma(-b, dc, H.r[p]);
+                            }
+                            __syncwarp();
+                        }
+                        if (lane == 0) {
+                            // the register classes' accuracy guard (lsq.cu), on the whole column
+                            constexpr float kTol = (float)kFallbackTol, kTol2 = kTol * kTol, kC = (float)kAutoC;
+                            const float msq = (float)H.scal[kSMsq];
+                            const float rk = (float)(kRhoSafety * kU32) * (float)H.scal[kSKap2];
+                            bool miss = !(rk < 0.5f) || rk * rk * dsq > kTol2 * (1.f - rk) * (1.f - rk) * msq;
+                            if (step == 0) {
+                                miss = miss || 4.f * kC * kC * dsq >= msq || 2.f * kC * dsq > kTol * msq;
+                            } else if (dsq > (float)kNoise2 * msq) {
+                                const float dprev2 = (float)H.scal[kSDprev];
+                                miss = miss || 4.f * dsq >= dprev2 || 4.f * dsq * dsq > kTol2 * msq * dprev2;
+                            }
+                            H.scal[kSDprev] = dsq;
+                            H.rstate[kRUsed] = step + 1;
+                            if (autoref) {
+                                if (step == 0 && !(kC * dsq > (float)kAutoTol * msq || miss)) H.rstate[kRStop] = 1;
+                                if (step == steps - 1) H.rstate[kRMiss] = miss ? 1 : 0;
+                            } else if (step == steps - 1) {
+                                H.rstate[kRMiss] = miss ? 1 : 0;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    if (H.rstate[kRStop]) break;
+                }
+                // the final residual and the solution's finiteness
+                if (warp == 0) {
+                    double s2 = 0.0;
+                    int nf = 0;
+                    for (int i = lane; i < nI; i += 32) s2 = fma(H.r[i], H.r[i], s2);
+                    for (int c = lane; c < nJ; c += 32) nf |= !isfinite(H.m[c]);
+                    s2 = warp_sum_f64(s2);
+                    nf = __any_sync(0xffffffffu, nf);
+                    if (lane == 0) {
+                        H.scal[kSRes2] = s2;
+                        if (nf || !isfinite(s2)) set_status(H, kStNonfinite);
+                        else if (H.rstate[kRMiss]) set_status(H, kStRefine);  // re-solved by the FP64 kernel
+                    }
+                }
+                __syncthreads();
+            }
+        }
         // ---- outputs
         if (warp == 0) {
             const int status = H.status;
@@ -309,7 +526,8 @@ __global__ void __launch_bounds__(kBigThreads, 1) lsq_big_kernel(LsqArgs args, i
                 const double r2 = H.scal[kSRes2];
                 args.colres[jj] = ok ? (r2 > 0.0 ? r2 : 0.0) + H.scal[kSOut2] : 0.0;
                 args.colstat[jj] = status;
-                if (args.refine_used) args.refine_used[jj] = (uint8_t)(kAutoSteps + 1);  // solved in FP64
+                if (args.refine_used)
+                    args.refine_used[jj] = (uint8_t)(status == kStRefine ? kAutoSteps + 1 : H.rstate[kRUsed]);
             }
         }
         __syncthreads();  // the next column reuses the shared memory
@@ -318,12 +536,13 @@ __global__ void __launch_bounds__(kBigThreads, 1) lsq_big_kernel(LsqArgs args, i
 
 }  // namespace
 
-cudaError_t launch_lsq_big(sam_handle h, const LsqArgs &args, int bin, bool profile) {
-    const size_t smem = sizeof(BigHdr) + sizeof(double) * (size_t)kBigTileDoubles;
-    const cudaError_t e = cudaFuncSetAttribute(lsq_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_lsq_big(sam_handle h, const LsqArgs &args, int bin, bool profile, bool fp32) {
+    const size_t smem = sizeof(BigHdr) + (fp32 ? sizeof(float) : sizeof(double)) * (size_t)kBigTileDoubles;
+    auto kern = fp32 ? lsq_big_kernel<float> : lsq_big_kernel<double>;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (profile) profile_begin(h, bin);
-    lsq_big_kernel<<<handle_sms(h), kBigThreads, smem, handle_stream(h)>>>(args, bin);
+    kern<<<handle_sms(h) * (fp32 ? BigBlocks<float>::value : 1), kBigThreads, smem, handle_stream(h)>>>(args, bin);
     count_launch(h);
     if (profile) profile_end(h, bin);
     return cudaGetLastError();

@@ -390,14 +390,11 @@ using F1b = Tile<2, 4, 13, 3, float, 26>;
 using F2b = Tile<4, 8, 10, 3, float, 40>;
 using F3b = Tile<4, 8, 13, 4, float, 52>;
 using F4b = Tile<4, 8, 16, 4, float, 64>;
-// the adjoint's shapes when R comes from a factor tape
-using F0L = Tile<2, 2, 7, 3, float, 14, true>;
-using F1L = Tile<2, 2, 13, 5, float, 26, true>;
+// the adjoint's shapes when R comes from a factor tape (size classes 2-4;
+// the two smallest recompute their small QR)
 using F2L = Tile<4, 4, 10, 6, float, 40, true>;
 using F3L = Tile<4, 4, 13, 7, float, 52, true>;
 using F4L = Tile<4, 4, 16, 7, float, 64, true>;
-using D0L = Tile<2, 2, 7, 3, double, 14, true>;
-using D1L = Tile<2, 4, 13, 3, double, 26, true>;
 using D2L = Tile<4, 8, 10, 3, double, 40, true>;
 using D3L = Tile<4, 8, 13, 4, double, 52, true>;
 using D4L = Tile<4, 8, 16, 4, double, 64, true>;
