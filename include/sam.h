@@ -124,9 +124,8 @@ void sam_limits(int32_t *max_rows, int32_t *max_cols);
  * SAM_ERR_UNSUPPORTED.  Classes 0..4 are register tiles with
  * FP32 or FP64 arithmetic; class 5 (SAM_NUM_SIZE_CLASSES - 1) is one thread
  * block per column with the tile in shared memory (FP64 for SAM_FP64; FP32
- * with the FP64 refinement steps and their guard for SAM_FP32_REFINE), and
- * no adjoint (sam_build_backward reports its columns as
- * SAM_ERR_UNSUPPORTED).  variants[b]: tile shapes of class b
+ * with the FP64 refinement steps and their guard for SAM_FP32_REFINE); its
+ * adjoint (sam_build_backward) runs in FP64 for either precision.  variants[b]: tile shapes of class b
  * (sam_tune, sam_set_tile_variants).  count must be SAM_NUM_SIZE_CLASSES;
  * any output may be NULL.
  */
@@ -443,8 +442,10 @@ sam_status sam_build_backward_batched(sam_handle h, int K, const sam_csr *A_k, c
  * SAM_FP32_REFINE, FP64 for SAM_FP64), rows in order, each from its
  * diagonal, in a slot of |J_j| (|J_j| + 1) / 2 elements rounded up to a
  * multiple of four; slots follow the columns of the batch in order (map k's
- * columns after map k-1's).  Columns of the large class (sam_size_classes)
- * write nothing and have no adjoint.
+ * columns after map k-1's).  Columns with more than 27 unknowns have no slot
+ * and columns of the large class (sam_size_classes) write nothing: their
+ * adjoint always factors B again (in FP64), as do the two smallest classes,
+ * whose QR costs less than reading the tape.
  *
  * sam_factor_tape_bytes -- bytes of the tape of the K maps on patterns S
  * (one slot per column of each pattern) at `precision`.  Synchronises.

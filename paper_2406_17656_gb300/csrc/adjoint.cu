@@ -269,14 +269,6 @@ __global__ void __launch_bounds__(kReduceThreads) adjoint_reduce_kernel(int N, c
     }
 }
 
-// columns of the large class have no adjoint kernel: their status says so
-// (their dL/dB blocks stay unwritten and unread: dbase keeps -1)
-__global__ void adjoint_unsupported_kernel(const int32_t *work, const int32_t *bin_off, int bin, int32_t *colstat) {
-    const int w0 = bin_off[bin], cnt = bin_off[bin + 1] - w0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x)
-        colstat[work[w0 + t]] = kStUnsupported;
-}
-
 __global__ void permute_scatter_kernel(int64_t nnz, const int32_t *perm, const double *in, double *out) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p < nnz) out[perm[p]] = in[p];
@@ -331,10 +323,7 @@ cudaError_t launch_adjoint(sam_handle h, int precision, const LsqArgs &args) {
         if ((e = launch_one<F3, false>(h, args, 3)) != cudaSuccess) return e;
         if ((e = launch_one<F4, false>(h, args, 4)) != cudaSuccess) return e;
     }
-    adjoint_unsupported_kernel<<<handle_sms(h), 256, 0, handle_stream(h)>>>(args.work, args.bin_off, kBinBig,
-                                                                           args.colstat);
-    count_launch(h);
-    return cudaGetLastError();
+    return launch_adjoint_big(h, args, kBinBig);
 }
 
 cudaError_t adjoint_reduce(sam_handle h, int N, const int32_t *kcp, const int32_t *mrp, const int64_t *dbase,

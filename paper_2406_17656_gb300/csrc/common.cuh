@@ -226,6 +226,8 @@ cudaError_t launch_lsq_big(sam_handle h, const LsqArgs &args, int bin, bool prof
 // one size class (the items args.item_lo/item_hi select, else all of it)
 cudaError_t launch_lsq_bin(sam_handle h, int precision, const LsqArgs &args, int bin);
 cudaError_t launch_adjoint(sam_handle h, int precision, const LsqArgs &args);
+// the adjoint of the large class's columns (FP64, lsq_big.cu)
+cudaError_t launch_adjoint_big(sam_handle h, const LsqArgs &args, int bin);
 // dA(e) = sum over map entries t of row c(e): dB[dbase[t] + (e - kcp[c])], CSC order of A
 cudaError_t adjoint_reduce(sam_handle h, int N, const int32_t *kcp, const int32_t *mrp, const int64_t *dbase,
                            const double *dB, double *dak_csc);

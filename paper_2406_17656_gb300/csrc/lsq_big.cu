@@ -164,9 +164,80 @@ __device__ __forceinline__ void reflector(const TT *T, int ld, int nI, int k, in
     }
 }
 
-template <typename TT>
+// The adjoint of one large column (FP64; R in the tile's upper triangle, r =
+// c - B m in H.r): lambda = (R^T R)^{-1} g, w = B lambda (after the tile),
+// dL/dB(i, c) = r_i (lambda_c - 2 rho m_c) - w_i m_c into the column's
+// block (gather order) with the block offsets of its pattern entries,
+// dL/dM's direct residual part -2 rho (B^T r), dL/dA_0 of the target column.
+__device__ __forceinline__ void big_adjoint(const LsqArgs &args, BigHdr &H, double *T, int ld, int nI, int nJ,
+                                            int jj, int jb, int64_t poff, int zc, int zro, int64_t zoff, int tid,
+                                            int lane, int warp) {
+    double *wv = T + (size_t)ld * (nJ + 1);
+    if (tid == 0 && H.status == kStOk && (int64_t)ld * (nJ + 2) > kBigTileDoubles) H.status = kStUnsupported;
+    __syncthreads();
+    const double rho = args.resid_weight;
+    if (H.status == kStOk && warp == 0) {
+        for (int k = 0; k < nJ; ++k) {  // R^T y = g
+            double sk = 0.0;
+            for (int i = lane; i < k; i += 32) sk = fma(T[i + ld * k], H.y[i], sk);
+            sk = warp_sum_f64(sk);
+            if (lane == 0) H.y[k] = (H.g[k] - sk) / T[k + ld * k];
+            __syncwarp();
+        }
+        for (int k = nJ - 1; k >= 0; --k) {  // R lambda = y
+            const double lk = H.y[k] / T[k + ld * k];
+            __syncwarp();
+            for (int i = lane; i < k; i += 32) H.y[i] = fma(-T[i + ld * k], lk, H.y[i]);
+            if (lane == 0) H.y[k] = lk;
+            __syncwarp();
+        }
+        for (int i = lane; i < nI; i += 32) wv[i] = 0.0;
+        __syncwarp();
+        for (int c = 0; c < nJ; ++c) {  // w = B lambda, column by column
+            const double lc = H.y[c];
+            for (int e = lane; e < H.clen[c]; e += 32) {
+                const int p = search_rows(H.I, nI, args.kri[H.kcol[c] + e]);
+                if (p >= 0) wv[p] = fma(args.kcv[H.colA[c] + e], lc, wv[p]);
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    if (H.status == kStOk) {
+        const int64_t blk = args.dB_off[jj];
+        for (int c = warp; c < nJ; c += kBigWarps) {
+            const double ac = fma(-2.0 * rho, H.m[c], H.y[c]), nm = -H.m[c];
+            double bt = 0.0;
+            for (int e = lane; e < H.clen[c]; e += 32) {
+                const int p = search_rows(H.I, nI, args.kri[H.kcol[c] + e]);
+                const double rp = p >= 0 ? H.r[p] : 0.0, wp = p >= 0 ? wv[p] : 0.0;
+                args.dB[blk + H.cb[c] + e] = fma(rp, ac, wp * nm);
+                bt = fma(args.kcv[H.colA[c] + e], rp, bt);
+            }
+            bt = warp_sum_f64(bt);
+            if (lane == 0) {
+                const int64_t t = (int64_t)args.csr_pos[jb + c] + poff;
+                args.dbase[t] = blk + H.cb[c];
+                if (args.dmres) args.dmres[t] = -2.0 * rho * bt;
+            }
+        }
+        const int zb = args.zcp[zc], ze = args.zcp[zc + 1];
+        for (int t = zb + tid; t < ze; t += kBigThreads) {
+            const int p = search_rows(H.I, nI, args.zri[t] + zro);
+            args.dzval[zoff + t] = (p >= 0) ? wv[p] + 2.0 * rho * H.r[p] : 2.0 * rho * args.zcv[t];
+        }
+    }
+    if (tid == 0) args.colstat[jj] = H.status;
+}
+
+// ADJ: the adjoint of the column solves (as adjoint.cu for the register
+// classes) instead of the solve: m and dL/dm from the map, lambda by the FP64
+// triangular solves with R, dL/dB blocks, dL/dc, and the residual's direct
+// partials.
+template <typename TT, bool ADJ = false>
 __global__ void __launch_bounds__(kBigThreads, BigBlocks<TT>::value) lsq_big_kernel(LsqArgs args, int bin) {
     constexpr bool F32 = sizeof(TT) == 4;
+    static_assert(!(ADJ && F32), "the large class's adjoint runs in FP64");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BigHdr &H = *reinterpret_cast<BigHdr *>(smem_raw);
     TT *T = reinterpret_cast<TT *>(smem_raw + sizeof(BigHdr));
@@ -373,12 +444,21 @@ __global__ void __launch_bounds__(kBigThreads, BigBlocks<TT>::value) lsq_big_ker
             for (int o = 16; o > 0; o >>= 1) st = max(st, __shfl_xor_sync(0xffffffffu, st, o));
             __syncwarp();
             if (st == kStOk) {
-                for (int k = nJ - 1; k >= 0; --k) {
-                    const TT mk = yT[k] / T[k + ld * k];
+                if constexpr (ADJ) {  // the forward map's column and the incoming gradient
+                    for (int c = lane; c < nJ; c += 32) {
+                        const int64_t t = (int64_t)args.csr_pos[jb + c] + poff;
+                        H.m[c] = args.mval[t];
+                        H.g[c] = args.dmval ? args.dmval[t] : 0.0;
+                    }
                     __syncwarp();
-                    for (int i = lane; i < k; i += 32) yT[i] = fma(-T[i + ld * k], mk, yT[i]);
-                    if (lane == 0) H.m[k] = (double)mk;
-                    __syncwarp();
+                } else {
+                    for (int k = nJ - 1; k >= 0; --k) {
+                        const TT mk = yT[k] / T[k + ld * k];
+                        __syncwarp();
+                        for (int i = lane; i < k; i += 32) yT[i] = fma(-T[i + ld * k], mk, yT[i]);
+                        if (lane == 0) H.m[k] = (double)mk;
+                        __syncwarp();
+                    }
                 }
                 int nf = 0;
                 for (int c = 0; c < nJ; ++c) {
@@ -404,6 +484,12 @@ __global__ void __launch_bounds__(kBigThreads, BigBlocks<TT>::value) lsq_big_ker
             H.rstate[kRUsed] = kAutoSteps + 1;  // solved in FP64
         }
         __syncthreads();
+        if constexpr (ADJ) {
+            big_adjoint(args, H, reinterpret_cast<double *>(T), ld, nI, nJ, jj, jb, poff, args.zbig ? jj : jl,
+                        zro, args.zbig ? 0 : (int64_t)kmap * args.znnz, tid, lane, warp);
+            __syncthreads();  // the next column reuses the shared memory
+            continue;
+        }
         // ---- FP32 tile: corrected semi-normal-equation steps, r = c - B m0 above
         if constexpr (F32) {
             const bool autoref = args.refine_steps < 0;
@@ -535,6 +621,16 @@ __global__ void __launch_bounds__(kBigThreads, BigBlocks<TT>::value) lsq_big_ker
 }
 
 }  // namespace
+
+cudaError_t launch_adjoint_big(sam_handle h, const LsqArgs &args, int bin) {
+    const size_t smem = sizeof(BigHdr) + sizeof(double) * (size_t)kBigTileDoubles;
+    auto kern = lsq_big_kernel<double, true>;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<handle_sms(h), kBigThreads, smem, handle_stream(h)>>>(args, bin);
+    count_launch(h);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_lsq_big(sam_handle h, const LsqArgs &args, int bin, bool profile, bool fp32) {
     const size_t smem = sizeof(BigHdr) + (fp32 ? sizeof(float) : sizeof(double)) * (size_t)kBigTileDoubles;

@@ -110,18 +110,51 @@ def test_large_columns_in_a_shared_batch_multi_target_and_plan(sam, handle):
         colcheck.assert_columns(cp, got, ref["mval"], "fp32r", what="map %d" % k)
 
 
-def test_adjoint_reports_large_columns_as_unsupported(sam, handle):
-    seq = W.config2(nx=16, nmat=2)
-    A1, A0 = sam.Csr.from_host(seq.mats[1]), sam.Csr.from_host(seq.mats[0])
+@pytest.mark.parametrize("precision,steps", [("fp64", 0), ("fp32r", 2)])
+def test_adjoint_of_large_columns_matches_oracle(sam, handle, precision, steps):
+    """Level-3 maps mix register-class columns (the boundary) and large
+    columns (the interior); the adjoint of both against the oracle's FP64
+    adjoint, batched and single calls bit for bit."""
+    import scipy.sparse as sp
+    import torch
+
+    seq = W.config2(nx=14, nmat=2)
+    a0, a1 = seq.mats[0], seq.mats[1]
+    n = a1.n
+    I, J, nB = _sizes(a1, 3)
+    assert ((I > 64) | (J > 27) | (nB > 512)).sum() > 20
+    cp, ri = oracle.pattern(a1, 3)
+    fwd = oracle.build(a1, a0, cp, ri)
+    gbar = np.random.default_rng(9).standard_normal(len(ri))
+    want_k, want_0, want_m = oracle.adjoint(a1, a0, cp, ri, fwd["mval"], gbar, 0.7, want_dmres=True)
+
+    def csr_vals(vals_csc):
+        m = sp.csc_matrix((vals_csc, ri, cp), shape=(n, n)).tocsr()
+        m.sort_indices()
+        return m.data
+
+    A1, A0 = sam.Csr.from_host(a1), sam.Csr.from_host(a0)
     S = handle.sam_pattern_build(A1, 3)
-    _, _, mv = handle.sam_build(A1, A0, S, "fp32r", 1)
+    m_csr = torch.from_numpy(csr_vals(fwd["mval"])).cuda()
+    g_csr = torch.from_numpy(csr_vals(gbar)).cuda()
+    dmres = torch.empty_like(m_csr)
+    dk, d0 = handle.sam_build_backward(A1, A0, S, m_csr, g_csr, precision, steps, 0.7, dM_resid=dmres)
     handle.sam_sync()
-    with pytest.raises(sam.SamError) as e:
-        handle.sam_build_backward(A1, A0, S, mv, mv, "fp32r", 1, 0.0)
-        handle.sam_sync()
-    assert e.value.status == sam.SAM_ERR_UNSUPPORTED
-    # the handle stays usable
-    S2 = handle.sam_pattern_build(A1, 2)
-    _, _, mv2 = handle.sam_build(A1, A0, S2, "fp32r", 1)
-    handle.sam_build_backward(A1, A0, S2, mv2, mv2, "fp32r", 1, 0.0)
+    scale = max(np.abs(want_k).max(), np.abs(want_0).max())
+    tol = 1e-10
+    assert np.abs(dk.cpu().numpy() - want_k).max() <= tol * scale
+    assert np.abs(d0.cpu().numpy() - want_0).max() <= tol * scale
+    mm = sp.csc_matrix((want_m, ri, cp), shape=(n, n)).tocsr()
+    mm.sort_indices()
+    assert np.abs(dmres.cpu().numpy() - mm.data).max() <= 1e-9 * max(np.abs(gbar).max(), 1.0)
+    # batched (two maps, one structure) = single calls, bit for bit
+    A2 = sam.Csr.from_host(seq.mats[1])
+    pats = handle.sam_pattern_build_batched([A1, A2], 3)
+    mm2 = torch.cat([m_csr, m_csr])
+    gg2 = torch.cat([g_csr, g_csr])
+    dkb, d0b = handle.sam_build_backward_batched([A1, A2], [A0, A0], pats, mm2, gg2, precision, steps, 0.7)
     handle.sam_sync()
+    assert torch.equal(dkb[:a1.nnz], dk) and torch.equal(dkb[a1.nnz:], dk)
+    assert torch.equal(d0b[:a0.nnz], d0) and torch.equal(d0b[a0.nnz:], d0)
+    for p in pats:
+        p.destroy()
