@@ -26,7 +26,7 @@ constexpr int kJCap = 27;    // max |J_j| (unknowns) of one column problem
 constexpr int kRegBins = 5;  // register-tile size classes (see lsq.cu)
 constexpr int kLCap = 512;   // max stored entries of one column's B (8 per shadow row)
 // The large class (lsq_big.cu): one thread block per column, [B c] as a
-// dense FP64 tile in shared memory.
+// dense tile in shared memory (FP64, or FP32 for FP32 + refinement builds).
 constexpr int kBinBig = kRegBins;  // its size-class index
 constexpr int kNumBins = kRegBins + 1;
 constexpr int kBigJCap = 128;                  // max |J_j|

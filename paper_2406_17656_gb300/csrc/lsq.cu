@@ -95,7 +95,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
         C.factor(S, a);
         C.unpark(S);
         const int nJ = C.nJ, nI = C.nI;
-        if (args.fac_mode == kTapeRecord && C.valid && C.status == kStOk) C.tape_store(args, S);
+        if (args.fac_mode == kTapeRecord && C.valid && (C.status == kStOk || C.status == kStRank ||
+                                                        C.status == kStNonfinite))
+            C.tape_store(args, S, args.jcp[C.js + 1] - C.jb);
         // ---- m0 = R^{-1} (Q^T c)(1:nJ)
         T x[JQ];
 #pragma unroll

@@ -742,13 +742,15 @@ struct Column {
     }
 
     // factor tape: R (from shared memory, after factor) to the column's slot,
-    // packed (row k from its diagonal, rows in order)
-    __device__ __forceinline__ void tape_store(const LsqArgs &args, const ProbSmem<TL> &S) const {
+    // packed (row k from its diagonal, rows in order).  n: the column's
+    // unknowns, also when a zero or non-finite pivot cleared nJ, so that a
+    // replaying adjoint meets the same pivots and reports the same status
+    __device__ __forceinline__ void tape_store(const LsqArgs &args, const ProbSmem<TL> &S, int n) const {
         T *dst = reinterpret_cast<T *>(args.fac) + args.fac_off[jj];
         int base = 0;
-        for (int k = 0; k < nJ; ++k) {
-            for (int c = k + ll; c < nJ; c += P) dst[base + c - k] = S.u.s.R[TL::rpos(k, c)];
-            base += nJ - k;
+        for (int k = 0; k < n; ++k) {
+            for (int c = k + ll; c < n; c += P) dst[base + c - k] = S.u.s.R[TL::rpos(k, c)];
+            base += n - k;
         }
     }
 

@@ -206,3 +206,41 @@ def test_autograd_keep_factors_gives_the_same_gradients(sam, handle):
         loss.backward()
         grads.append((ak.grad.clone(), az.grad.clone()))
     assert torch.equal(grads[0][0], grads[1][0]) and torch.equal(grads[0][1], grads[1][1])
+
+
+def test_zero_pivot_is_reported_through_the_tape(sam, handle):
+    """A column of A_k whose stored values are all zero makes the problems
+    that gather it rank deficient; the replaying adjoint meets the same zero
+    pivots as the recomputing one and reports the same status."""
+    import torch
+
+    seq = W.config2(nx=12, nmat=2)
+    a = seq.mats[1].to_scipy().tocsc()
+    a.data[a.indptr[40]:a.indptr[41]] = 0.0  # stored, numerically zero
+    ak = W.CSR.from_scipy(a.tocsr())
+    A1, A0 = sam.Csr.from_host(ak), sam.Csr.from_host(seq.mats[0])
+    S = handle.sam_pattern_build(A1, 1)
+    tape = _tape(torch, handle.sam_factor_tape_bytes([S], "fp32r"))
+    st = torch.zeros(ak.n, dtype=torch.int32, device="cuda")
+    handle.sam_set_factor_tape(sam.SAM_TAPE_RECORD, tape)
+    try:
+        _, _, mv = handle.sam_build(A1, A0, S, "fp32r", 1, col_status=st)
+        with pytest.raises(sam.SamError) as e:
+            handle.sam_sync()
+    finally:
+        handle.sam_set_factor_tape(sam.SAM_TAPE_OFF)
+    assert e.value.status == sam.SAM_ERR_RANK_DEFICIENT
+    bad = np.flatnonzero(st.cpu().numpy() != 0)
+    assert len(bad) > 0
+    statuses = []
+    for mode in (None, sam.SAM_TAPE_REPLAY):
+        if mode is not None:
+            handle.sam_set_factor_tape(mode, tape)
+        try:
+            with pytest.raises(sam.SamError) as e:
+                handle.sam_build_backward(A1, A0, S, mv, mv, "fp32r", 1, 0.0)
+                handle.sam_sync()
+            statuses.append(e.value.status)
+        finally:
+            handle.sam_set_factor_tape(sam.SAM_TAPE_OFF)
+    assert statuses == [sam.SAM_ERR_RANK_DEFICIENT] * 2
