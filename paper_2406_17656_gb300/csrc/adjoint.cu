@@ -24,13 +24,14 @@ namespace sam {
 namespace {
 
 // blocks per SM that a shape's shared memory allows (1..4); the register
-// budget of the factor-tape shapes is held to it, so registers never lower
-// the occupancy that their smaller shared memory buys
+// budget of the FP32 shapes is held to it, so registers never lower the
+// occupancy that shared memory permits (the FP64 shapes keep the compiler's
+// choice: at 128 registers they spill)
 template <class TL>
 struct AdjBlocks {
     static constexpr int bytes = (int)sizeof(ProbSmem<TL>) * TL::PPW * kWarpsPerBlock + 1024;
     static constexpr int raw = 233472 / bytes;
-    static constexpr int value = !TL::LEAN ? 1 : (raw < 1 ? 1 : (raw > 4 ? 4 : raw));
+    static constexpr int value = raw < 1 ? 1 : (raw > 4 ? 4 : raw);
 };
 
 // TL::LEAN: R comes from the forward build's factor tape
@@ -66,13 +67,12 @@ __device__ __forceinline__ void adjoint_body(const LsqArgs &args, int bin) {
         const int ll = C.ll;
         if constexpr (TAPE) {
             // R from the forward build's factor tape: no tile, no QR
-            C.template gather<false>(args, S);
+            C.gather_sparse(args, S);
             C.build_rows(S);
             C.tape_load(args, S);
         } else {
-            C.gather(args, S);
             T a[RS][CS];
-            C.load_tile(S, a);
+            C.gather_tile(args, S, a);
             C.build_rows(S);
             C.park(S);
             C.factor(S, a);
@@ -197,6 +197,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) adjoint_kernel(LsqArgs ar
 }
 
 template <class TL, bool FP64>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, AdjBlocks<TL>::value) adjoint_f32_kernel(LsqArgs args,
+                                                                                                int bin) {
+    adjoint_body<TL, FP64>(args, bin);
+}
+
+template <class TL, bool FP64>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, AdjBlocks<TL>::value) adjoint_tape_kernel(LsqArgs args,
                                                                                                  int bin) {
     adjoint_body<TL, FP64>(args, bin);
@@ -279,7 +285,8 @@ cudaError_t launch_one(sam_handle h, const LsqArgs &a, int bin) {
     const size_t smem = sizeof(ProbSmem<TL>) * TL::PPW * kWarpsPerBlock;
     void (*kern)(LsqArgs, int);
     if constexpr (TL::LEAN) kern = adjoint_tape_kernel<TL, FP64>;
-    else kern = adjoint_kernel<TL, FP64>;
+    else if constexpr (FP64) kern = adjoint_kernel<TL, FP64>;
+    else kern = adjoint_f32_kernel<TL, FP64>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

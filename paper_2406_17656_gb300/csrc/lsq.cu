@@ -47,14 +47,16 @@
 namespace sam {
 namespace {
 
-// blocks per SM that the shared memory of a tile allows (1..4): the
-// register budget is held to the same count, so registers never lower the
-// occupancy that shared memory permits
+// blocks per SM that the shared memory of a tile allows (1..4; 1..3 for the
+// FP64 tiles, whose registers do not fit 128 per thread without spilling):
+// the register budget is held to the same count, so registers never lower
+// the occupancy that shared memory permits
 template <class TL>
 struct MinBlocks {
     static constexpr int bytes = (int)sizeof(ProbSmem<TL>) * TL::PPW * kWarpsPerBlock + 1024;
     static constexpr int raw = 233472 / bytes;
-    static constexpr int value = raw < 1 ? 1 : (raw > 4 ? 4 : raw);
+    static constexpr int cap = sizeof(typename TL::T) == 8 ? 3 : 4;
+    static constexpr int value = raw < 1 ? 1 : (raw > cap ? cap : raw);
 };
 
 template <class TL, bool FP64>
@@ -87,9 +89,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
         Column<TL> C;
         C.begin_at(args, item, total, jj_cur);
         const int ll = C.ll;
-        C.gather(args, S);
         T a[RS][CS];
-        C.load_tile(S, a);
+        C.gather_tile(args, S, a);
         C.build_rows(S);
         C.park(S);
         C.factor(S, a);

@@ -34,14 +34,14 @@ struct Tile {
     static constexpr int NBCAP = 8 * MAXI_BIN_;     // max stored entries of B
     static constexpr int JQ = (MAXJ + P - 1) / P;  // unknowns per lane (solves)
     static constexpr int IQ = (MAXI + P - 1) / P;  // rows per lane (residuals)
-    static constexpr int RSTR = (MAXJ % 2) ? MAXJ : MAXJ + 1;  // odd row stride of R
-    static constexpr int RELEMS = LEAN ? MAXJ * (MAXJ + 1) / 2 : MAXJ * RSTR;  // R's shared-memory elements
-    // position of R(i, k), i <= k: rows of RSTR elements, or (LEAN) packed
-    // rows of MAXJ - i elements from the diagonal
-    static __device__ __forceinline__ int rpos(int i, int k) {
-        if constexpr (LEAN) return i * MAXJ - (i * (i - 1)) / 2 + (k - i);
-        else return i * RSTR + k;
-    }
+    static constexpr int RELEMS = MAXJ * (MAXJ + 1) / 2;  // R's shared-memory elements
+    // position of R(i, k), i <= k: packed rows of MAXJ - i elements from the
+    // diagonal
+    static __device__ __forceinline__ int rpos(int i, int k) { return i * MAXJ - (i * (i - 1)) / 2 + (k - i); }
+    // column slots staged per gather pass: the wide tiles stage [B c] in two
+    // passes of half the columns (half the staging buffer: more problems
+    // per SM); the narrow ones in one
+    static constexpr int CSH = (MAXJ >= 20 && CS >= 2) ? (CS + 1) / 2 : CS;
     static constexpr int VEC = 16 / (int)sizeof(T_);            // elements per 16-byte chunk
     static constexpr int NCH0 = (RS + VEC - 1) / VEC;
     static constexpr int NCH = NCH0 <= 1 ? 1 : NCH0 <= 2 ? 2 : NCH0 <= 4 ? 4 : NCH0 <= 8 ? 8 : 16;  // chunks per lane row
@@ -72,7 +72,7 @@ struct ProbSmem {
     unsigned char locr[TL::NBCAP];
     union U {
         // [B c], only until registers are loaded (see tile_pos)
-        __align__(16) T tile[TL::LEAN ? 16 / sizeof(T) : TL::NCOL * TL::RG * TL::RSP];
+        __align__(16) T tile[TL::LEAN ? 16 / sizeof(T) : TL::CSH * TL::CG * TL::RG * TL::RSP];
         struct S {
             int rowstart[TL::MAXI + 1];
             int rowent[TL::NBCAP];
@@ -469,12 +469,9 @@ struct Column {
         status = kStOk;
     }
 
-    // J columns, shadow rows, zeroed tile, gathered B and c (tile + FP64 c),
-    // column masks, local rows of every entry, out-of-shadow ||A_0||^2
-    // (TILE = false: everything but the tile, for an adjoint that reads R
-    // from a factor tape)
-    template <bool TILE = true>
-    __device__ __forceinline__ void gather(const LsqArgs &args, ProbSmem<TL> &S) {
+    // J columns (value offsets, lengths, gather offsets), shadow rows when
+    // needed, cleared row masks and c
+    __device__ __forceinline__ void gather_begin(const LsqArgs &args, ProbSmem<TL> &S) {
 #pragma unroll
         for (int q = 0; q < JQ; ++q) {
             const int c = ll + q * P;
@@ -502,16 +499,23 @@ struct Column {
             S.mask[i] = 0u;
             S.c[i] = 0.0;
         }
-        if constexpr (TILE) {
-            uint4 *tl = reinterpret_cast<uint4 *>(&S.u.tile[0]);
-            constexpr int NV = (int)(sizeof(S.u.tile) / sizeof(uint4));
-            for (int e = ll; e < NV; e += P) tl[e] = make_uint4(0u, 0u, 0u, 0u);
-        }
-        __syncwarp();
+    }
+
+    __device__ __forceinline__ void zero_stage(ProbSmem<TL> &S) {
+        uint4 *tl = reinterpret_cast<uint4 *>(&S.u.tile[0]);
+        constexpr int NV = (int)(sizeof(S.u.tile) / sizeof(uint4));
+        for (int e = ll; e < NV; e += P) tl[e] = make_uint4(0u, 0u, 0u, 0u);
+    }
+
+    // the entries of the lane's columns c in [c_lo, c_hi): local rows, row
+    // masks and (TILE) the values at column c - c_lo of the staging tile
+    template <bool TILE>
+    __device__ __forceinline__ void gather_entries(const LsqArgs &args, ProbSmem<TL> &S, int c_lo, int c_hi) {
 #pragma unroll
         for (int q = 0; q < JQ; ++q) {
             const int c = ll + q * P;
-            const int len = clen[q];
+            const int len = (c >= c_lo && c < c_hi) ? clen[q] : 0;
+            const int cs = c - c_lo;
             // local shadow rows of the entries, computed with the shadow rows
             // (read straight from global memory: staging them through shared
             // memory first measured 2x slower in the FP64 kernel)
@@ -534,7 +538,7 @@ struct Column {
                         i = 0;
                     }
                     S.locr[colB[q] + u] = (unsigned char)i;
-                    if constexpr (TILE) S.u.tile[tile_pos<TL>(i, c)] = vals[u];
+                    if constexpr (TILE) S.u.tile[tile_pos<TL>(i, cs)] = vals[u];
                     atomicOr(&S.mask[i], 1u << c);
                 }
             }
@@ -556,24 +560,62 @@ struct Column {
                         i = 0;
                     }
                     S.locr[colB[q] + p0 + u] = (unsigned char)i;
-                    if constexpr (TILE) S.u.tile[tile_pos<TL>(i, c)] = vals[u];
+                    if constexpr (TILE) S.u.tile[tile_pos<TL>(i, cs)] = vals[u];
                     atomicOr(&S.mask[i], 1u << c);
                 }
             }
         }
+    }
+
+    // the target column: c in FP64, out-of-shadow ||A_0(., j)||^2, and (TILE)
+    // the right-hand side at column NCOL - 1 - c_lo of the staging tile
+    template <bool TILE>
+    __device__ __forceinline__ void gather_target(const LsqArgs &args, ProbSmem<TL> &S, int c_lo) {
         out2 = 0.0;
         for (int t = zb + ll; t < ze; t += P) {
             const int i = target_row(args, S, t - zb, t);
             const double v = args.zcv[t];
             if (i >= 0) {
                 S.c[i] = v;
-                if constexpr (TILE) S.u.tile[tile_pos<TL>(i, NCOL - 1)] = tile_value<T>(args.zcv, args.zcv32, t);
+                if constexpr (TILE) S.u.tile[tile_pos<TL>(i, NCOL - 1 - c_lo)] = tile_value<T>(args.zcv, args.zcv32, t);
             } else {
                 out2 = fma(v, v, out2);
             }
         }
         out2 = group_sum<P>(out2);
+    }
+
+    // everything but the tile, for an adjoint that reads R from a factor
+    // tape: local rows, row masks, c, out-of-shadow ||A_0(., j)||^2
+    __device__ __forceinline__ void gather_sparse(const LsqArgs &args, ProbSmem<TL> &S) {
+        gather_begin(args, S);
         __syncwarp();
+        gather_entries<false>(args, S, 0, NCOL);
+        gather_target<false>(args, S, 0);
+        __syncwarp();
+    }
+
+    // [B c] into the register tile a: in passes of CSH column slots, each
+    // staged (zeroed, scattered) in shared memory in the chunk-swizzled
+    // layout of tile_pos and loaded into its slots; plus everything
+    // gather_sparse provides
+    __device__ __forceinline__ void gather_tile(const LsqArgs &args, ProbSmem<TL> &S, T (&a)[RS][CS]) {
+        constexpr int CSH = TL::CSH, NST = CSH * CG;
+        gather_begin(args, S);
+        zero_stage(S);
+        __syncwarp();
+        gather_entries<true>(args, S, 0, NST);
+        if constexpr (CSH == CS) gather_target<true>(args, S, 0);
+        __syncwarp();
+        load_slots<0>(S, a);
+        if constexpr (CSH < CS) {
+            zero_stage(S);
+            __syncwarp();
+            gather_entries<true>(args, S, NST, NCOL);
+            gather_target<true>(args, S, NST);
+            __syncwarp();
+            load_slots<1>(S, a);
+        }
     }
 
     // The column's state that the QR does not use, parked in shared memory
@@ -638,11 +680,13 @@ struct Column {
         return find_sorted(S.I, nI, args.zri[t] + zro);
     }
 
-    __device__ __forceinline__ void load_tile(ProbSmem<TL> &S, T (&a)[RS][CS]) {
-        constexpr int VEC = TL::VEC;
+    // the register slots t of staging pass H from the staging tile
+    template <int H>
+    __device__ __forceinline__ void load_slots(ProbSmem<TL> &S, T (&a)[RS][CS]) {
+        constexpr int VEC = TL::VEC, CSH = TL::CSH;
 #pragma unroll
-        for (int t = 0; t < CS; ++t) {
-            const int r = (t * CG + cg) * RG + rg;
+        for (int t = H * CSH; t < CS && t < (H + 1) * CSH; ++t) {
+            const int r = ((t - H * CSH) * CG + cg) * RG + rg;
             const uint4 *row = reinterpret_cast<const uint4 *>(&S.u.tile[r * TL::RSP]);
             const int swz = (r >> 1) & TL::SWZ;
 #pragma unroll
