@@ -251,6 +251,11 @@ struct QRPhase {
                     if (s == SK) x = (rg > rk) ? x : ((rg == rk) ? uk : T(0));
                     u[s - SK] = x;
                 }
+                // the dot products of all live column slots, then their
+                // reductions interleaved (independent shuffles in flight
+                // together), then the updates; per column the same operations
+                // in the same order as one column slot at a time
+                T w[CS - TK];
 #pragma unroll
                 for (int t = TK; t < CS; ++t) {
                     T w0 = T(0), w1 = T(0);
@@ -258,11 +263,16 @@ struct QRPhase {
                     for (int s = SK; s < RS; ++s) {
                         if ((s - SK) & 1) w1 = fma(u[s - SK], a[s][t], w1); else w0 = fma(u[s - SK], a[s][t], w0);
                     }
-                    T w = w0 + w1;
+                    w[t - TK] = w0 + w1;
+                }
 #pragma unroll
-                    for (int o = 1; o < RG; o <<= 1) w += shfl_xor(w, o);
+                for (int o = 1; o < RG; o <<= 1)
+#pragma unroll
+                    for (int t = TK; t < CS; ++t) w[t - TK] += shfl_xor(w[t - TK], o);
+#pragma unroll
+                for (int t = TK; t < CS; ++t) {
                     // columns of slots after TK are all > k (L divides CG)
-                    const T coef = (t > TK || t * CG + cg > k) ? taup * w : T(0);
+                    const T coef = (t > TK || t * CG + cg > k) ? taup * w[t - TK] : T(0);
 #pragma unroll
                     for (int s = SK; s < RS; ++s) a[s][t] = fma(-coef, u[s - SK], a[s][t]);
                 }
