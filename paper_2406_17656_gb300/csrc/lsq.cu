@@ -26,7 +26,7 @@
 // register slots holding only finished rows/columns drop out of the code.
 // The right-hand side is the last column, so Q^T c falls out of the sweep.
 // Triangular solves with R run in registers (unknown c on lane c % P) with
-// one shuffle per step; R sits in shared memory with an odd row stride.
+// one shuffle per step; R sits in shared memory, packed by rows.
 //
 // Precision.  SAM_FP64: tile, solves and residual are FP64.
 // SAM_FP32_REFINE: QR and triangular solves in FP32; accuracy is won back by

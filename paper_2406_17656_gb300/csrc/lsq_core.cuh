@@ -19,8 +19,7 @@ constexpr int kGatherRegs = 12;  // entries per source column gathered with one 
 constexpr int kRowRegs = 8;      // entries per row of B loaded with one round in the residual passes
 
 // LEAN_: the shape of an adjoint that reads R from a factor tape: no
-// register tile and no staging buffer for it, R packed in shared memory
-// (more problems per SM).
+// register tile and no staging buffer for it (more problems per SM).
 template <int RG_, int CG_, int RS_, int CS_, typename T_, int MAXI_BIN_, bool LEAN_ = false>
 struct Tile {
     static constexpr bool LEAN = LEAN_;
@@ -747,7 +746,7 @@ struct Column {
         }
     }
 
-    // QR of [B c]; R (odd stride), 1/R_kk and Q^T c to shared memory; a zero
+    // QR of [B c]; R (packed rows), 1/R_kk and Q^T c to shared memory; a zero
     // or non-finite pivot sets the status and clears nJ (no further work)
     __device__ __forceinline__ void factor(ProbSmem<TL> &S, T (&a)[RS][CS]) {
         kmax = nJ;
@@ -812,7 +811,7 @@ struct Column {
     // of factor).  The packed rows are copied as 16-byte vectors to the start
     // of R's array, then moved to their rows from the last one down: row k's
     // packed start k nJ - k (k - 1) / 2 is at most its place rpos(k, k)
-    // (k RSTR + k, or k MAXJ - k (k - 1) / 2 packed), so no row overwrites
+    // (k MAXJ - k (k - 1) / 2, rows of MAXJ - k), so no row overwrites
     // one that has not moved yet.
     __device__ __forceinline__ void tape_load(const LsqArgs &args, ProbSmem<TL> &S) {
         kmax = nJ;
