@@ -287,14 +287,15 @@ def measured_hbm_gbs() -> float:
 
 def kernel_hash() -> str:
     """sha256 over the sources the least-squares kernel is compiled from: its
-    two files and the device part of common.cuh (constants, LsqArgs, device
-    helpers; the host-side declarations after them do not enter the kernel).
-    A recorded ncu traffic figure is only reported while these are unchanged."""
+    kernel header, its translation unit, the shared column routines and the
+    device part of common.cuh (constants, LsqArgs, device helpers; the
+    host-side declarations after them do not enter the kernel).  A recorded
+    ncu traffic figure is only reported while these are unchanged."""
     import hashlib
 
     csrc = os.path.join(HERE, "paper_2406_17656_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("lsq.cu", "lsq_core.cuh"):
+    for f in ("lsq_kernel.cuh", "lsq.cu", "lsq_core.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     common = open(os.path.join(csrc, "common.cuh"), "rb").read()
     cut = common.find(b"// ------------------------------------------------------- host-side helpers")

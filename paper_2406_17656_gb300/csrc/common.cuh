@@ -225,7 +225,14 @@ cudaError_t launch_lsq(sam_handle h, int precision, const LsqArgs &args);
 cudaError_t launch_lsq_big(sam_handle h, const LsqArgs &args, int bin, bool profile = true, bool fp32 = false);
 // one size class (the items args.item_lo/item_hi select, else all of it)
 cudaError_t launch_lsq_bin(sam_handle h, int precision, const LsqArgs &args, int bin);
+// the FP64 register tiles of size classes 0-4 (lsq_fp64.cu)
+cudaError_t launch_lsq_fp64_bin(sam_handle h, const LsqArgs &args, int bin);
 cudaError_t launch_adjoint(sam_handle h, int precision, const LsqArgs &args);
+// the adjoint of one register size class: FP32 tiles recomputing R
+// (adjoint_f32.cu), and the lean shapes reading the factor tape, classes
+// 2-4 (adjoint_tape.cu)
+cudaError_t launch_adjoint_f32_bin(sam_handle h, const LsqArgs &args, int bin);
+cudaError_t launch_adjoint_tape_bin(sam_handle h, int precision, const LsqArgs &args, int bin);
 // the adjoint of the large class's columns (FP64, lsq_big.cu)
 cudaError_t launch_adjoint_big(sam_handle h, const LsqArgs &args, int bin);
 // dA(e) = sum over map entries t of row c(e): dB[dbase[t] + (e - kcp[c])], CSC order of A
