@@ -65,3 +65,19 @@ def test_bench_size_classes_are_the_librarys():
     rows, cols = np.zeros(1, np.int32), np.zeros(1, np.int32)
     sam.load().sam_limits(rows.ctypes.data_as(sam._i32p), cols.ctypes.data_as(sam._i32p))
     assert rows[0] == c["max_rows"][-1] and cols[0] == c["max_cols"][-1]
+
+
+def test_adjoint_flops_with_a_factor_tape_drop_only_the_qr():
+    """The adjoint's algorithmic work with R from a factor tape is the
+    recomputing adjoint's minus the forward's QR of [B c] (the same FP64
+    work), for every step count."""
+    I = np.array([49, 81, 25], dtype=np.int64)
+    J = np.array([25, 49, 9], dtype=np.int64)
+    nB = np.array([225, 441, 81], dtype=np.int64)
+    m, n = I.astype(float), J.astype(float)
+    qr = 2 * n * n * (m - n / 3) + (4 * m * n - 2 * n * n) + n * n
+    for steps in (0, 1, 2):
+        f32r, f64r = bench.adjoint_algorithmic_flops(I, J, nB, steps)
+        f32t, f64t = bench.adjoint_algorithmic_flops(I, J, nB, steps, tape=True)
+        assert np.allclose(f32r - f32t, qr)
+        assert np.array_equal(f64r, f64t)

@@ -244,3 +244,42 @@ def test_zero_pivot_is_reported_through_the_tape(sam, handle):
         finally:
             handle.sam_set_factor_tape(sam.SAM_TAPE_OFF)
     assert statuses == [sam.SAM_ERR_RANK_DEFICIENT] * 2
+
+
+def test_tape_with_large_columns(sam, handle):
+    """A level-3 batch mixes register-class columns (the boundary: tape
+    slots) and large columns (no slot for more than 27 unknowns; their
+    adjoint factors B again in FP64): replaying equals recomputing."""
+    import torch
+
+    seq = W.config2(nx=14, nmat=2)
+    aks = [sam.Csr.from_host(m) for m in seq.mats]
+    pats = handle.sam_pattern_build_batched(aks, 3)
+    n = seq.mats[0].n
+    sizes = []
+    for A in seq.mats:
+        cp, _ = oracle.pattern(A, 3)
+        sizes += [_slot(int(x)) for x in np.diff(cp)]
+    nbytes = handle.sam_factor_tape_bytes(pats, "fp32r")
+    assert nbytes == 4 * int(np.sum(sizes))
+    assert any(s == 0 for s in sizes) and any(s > 0 for s in sizes)
+    tape = _tape(torch, nbytes)
+    handle.sam_set_factor_tape(sam.SAM_TAPE_RECORD, tape)
+    try:
+        offs, _, _, mv, _ = handle.sam_build_batched(aks, aks[0], pats, "fp32r", 1)
+    finally:
+        handle.sam_set_factor_tape(sam.SAM_TAPE_OFF)
+    gbar = torch.randn(mv.numel(), dtype=torch.float64, device="cuda",
+                       generator=torch.Generator(device="cuda").manual_seed(6))
+    dk0, d00 = handle.sam_build_backward_batched(aks, [aks[0]] * 2, pats, mv, gbar, "fp32r", 1, 0.3, offsets=offs)
+    handle.sam_set_factor_tape(sam.SAM_TAPE_REPLAY, tape)
+    try:
+        dk1, d01 = handle.sam_build_backward_batched(aks, [aks[0]] * 2, pats, mv, gbar, "fp32r", 1, 0.3,
+                                                     offsets=offs)
+    finally:
+        handle.sam_set_factor_tape(sam.SAM_TAPE_OFF)
+    handle.sam_sync()
+    assert torch.equal(dk0, dk1) and torch.equal(d00, d01)
+    assert n == aks[0].n
+    for p in pats:
+        p.destroy()
