@@ -82,7 +82,10 @@ enum {
  * max |R_kk| / min |R_kk| (a lower bound on kappa(B), hence the factor 8),
  * and 4 |d_1| / |m| after step 1 or
  * |d_s| / |d_{s-1}| after later steps.  Automatic mode takes step 2 when
- * 4 |d_1|^2 > 1e-12 |m|^2 or the prediction after step 1 misses; after the
+ * 4 |d_1|^2 > 1e-12 |m|^2 or the prediction after step 1 misses (such a
+ * column is solved again with two steps by a launch of its own, so that its
+ * result equals the two-step build's and every other column's equals the
+ * one-step build's, bit for bit); after the
  * last step (2 in automatic mode, s otherwise) a predicted error above
  * 1e-10 |m|, or rho >= 1/2, sends the column to an FP64 Householder
  * re-solve (the large class's FP64 kernel).  The large class's FP32 tile

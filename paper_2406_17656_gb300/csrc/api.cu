@@ -1531,12 +1531,22 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
     a.refine_steps = refine_steps;
     if ((s = tape_args(h, sc, g, N, precision, kTapeRecord, a)) != SAM_OK) return s;
     int32_t *work2 = nullptr, *bin_off2 = nullptr;
+    RedoLists redo;
     if (guarded) {
         a.refine_used = sc.get<uint8_t>((size_t)N);
         work2 = sc.get<int32_t>((size_t)N);
         bin_off2 = sc.get<int32_t>(2);
         if (!a.refine_used || !work2 || !bin_off2) return SAM_ERR_OOM;
         cudaMemsetAsync(a.refine_used, 0, (size_t)N, st);
+    }
+    if (autoref) {
+        // columns that ask for a second step are solved again by a launch of their own
+        redo.bin = bin;
+        redo.bins2 = sc.get<uint8_t>((size_t)N);
+        redo.work = sc.get<int32_t>((size_t)N);
+        redo.bin_off = sc.get<int32_t>(kNumBins + 1);
+        redo.ws = sc.get<int32_t>(2 * kNumBins);
+        if (!redo.bins2 || !redo.work || !redo.bin_off || !redo.ws) return SAM_ERR_OOM;
     }
     if (!chunked) {
         if (launch_lsq(h, precision, a) != cudaSuccess) return SAM_ERR_CUDA;
@@ -1566,7 +1576,7 @@ sam_status build_impl(sam_handle h, int K, const sam_csr *A_k, const sam_csr *A_
                 return SAM_ERR_CUDA;
         }
     }
-    if (guarded && launch_refine_fallback(h, a, (int)N, work2, bin_off2, h->d_refine) != cudaSuccess)
+    if (guarded && launch_refine_fallback(h, a, (int)N, work2, bin_off2, h->d_refine, redo) != cudaSuccess)
         return SAM_ERR_CUDA;
     // chunked host values were copied before the re-solves: their count comes
     // back with the final synchronisation, and re-solved columns are copied again
@@ -2462,7 +2472,9 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
     if (s != SAM_OK) return s;
     if ((s = block_diag_csc(h, keep, ak, n, &kcp, &kri, &kcv, &kperm, &kn, &tmp, ksym)) != SAM_OK) return s;
     int32_t *ish = keep.get<int32_t>((size_t)N * kICap), *icnt = keep.get<int32_t>((size_t)N);
-    uint8_t *bin = tmp.get<uint8_t>((size_t)N);
+    // (automatic refinement reads the size classes at every replay)
+    uint8_t *bin = refine_steps < 0 && precision == SAM_FP32_REFINE ? keep.get<uint8_t>((size_t)N)
+                                                                     : tmp.get<uint8_t>((size_t)N);
     int32_t *work = keep.get<int32_t>((size_t)N);
     int32_t *bin_off = keep.get<int32_t>(kNumBins + 1);
     int32_t *d_st = col_status ? col_status : keep.get<int32_t>((size_t)N);
@@ -2483,6 +2495,17 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
     int32_t *work2 = autoref ? keep.get<int32_t>((size_t)N) : nullptr;
     int32_t *bin_off2 = autoref ? keep.get<int32_t>(kNumBins + 1) : nullptr;
     if (autoref && (!refine_used || !work2 || !bin_off2)) return SAM_ERR_OOM;
+    // automatic refinement: the two-step launch's own lists (the first
+    // launch's work list is read again at every replay)
+    RedoLists redo;
+    if (refine_steps < 0 && precision == SAM_FP32_REFINE) {
+        redo.bin = bin;
+        redo.bins2 = keep.get<uint8_t>((size_t)N);
+        redo.work = keep.get<int32_t>((size_t)N);
+        redo.bin_off = keep.get<int32_t>(kNumBins + 1);
+        redo.ws = keep.get<int32_t>(2 * kNumBins);
+        if (!redo.bins2 || !redo.work || !redo.bin_off || !redo.ws) return SAM_ERR_OOM;
+    }
     // value sources: per-matrix pointers and CSC offsets
     std::vector<const double *> kptr(K), zptr(NT);
     std::vector<int64_t> koff(K + 1, 0), zoff(NT + 1, 0);
@@ -2567,7 +2590,7 @@ sam_status sam_plan_create(sam_handle h, int K, const sam_csr *A_k, const sam_cs
                   cudaMemsetAsync(d_r2, 0, sizeof(double) * (size_t)N, cs) == cudaSuccess &&
                   (!autoref || cudaMemsetAsync(refine_used, 0, (size_t)N, cs) == cudaSuccess) &&
                   launch_lsq(h, precision, a) == cudaSuccess &&
-                  (!autoref || launch_refine_fallback(h, a, (int)N, work2, bin_off2, h->d_refine) == cudaSuccess) &&
+                  (!autoref || launch_refine_fallback(h, a, (int)N, work2, bin_off2, h->d_refine, redo) == cudaSuccess) &&
                   status_reduce(h, d_st, N, h->d_flag) == cudaSuccess &&
                   (!fro2 || segmented_sum_f64(h, d_r2, K, n, fro2, false, seg_work) == cudaSuccess);
         cudaGraph_t graph = nullptr;

@@ -46,6 +46,9 @@ constexpr int kStUnsupported = SAM_ERR_UNSUPPORTED;
 // internal: the FP32 solve missed the accuracy target; the FP64 kernel
 // re-solves the column (never left in a status array)
 constexpr int kStRefine = 100;
+// internal: automatic refinement asks for a second step; a launch with two
+// steps solves the column again (never left in a status array)
+constexpr int kStStep2 = 101;
 // automatic refinement (refine_steps = SAM_REFINE_AUTO)
 constexpr int kAutoSteps = 2;
 constexpr double kAutoC = 4.0, kAutoTol = 1e-12, kFallbackTol = 1e-10;
@@ -211,11 +214,21 @@ cudaError_t build_work_list(sam_handle h, int N, const uint8_t *bin, int32_t *wo
                             int32_t *ws = nullptr);
 // out[j] = bin[j] where colstat[j] == flag, else no size class
 cudaError_t flagged_bins(sam_handle h, int N, const uint8_t *bin, const int32_t *colstat, int32_t flag, uint8_t *out);
-// guarded refinement: FP64 re-solve of the columns the FP32 kernel flagged
-// (list: int32[N] workspace, list_off: int32[2]), then the per-outcome
-// column counts (counts[kAutoSteps + 1], nullable)
+// automatic refinement's two-step launch (refine_steps < 0): the size class of
+// every column (bin), and workspace for the flagged columns' classes (bins2,
+// uint8[N]), their work list (work, int32[N]), its offsets (bin_off,
+// int32[kNumBins + 1]) and the list's counters (ws, int32[2 kNumBins])
+struct RedoLists {
+    const uint8_t *bin = nullptr;
+    uint8_t *bins2 = nullptr;
+    int32_t *work = nullptr, *bin_off = nullptr, *ws = nullptr;
+};
+// guarded refinement: in the automatic mode, the two-step solve of the columns
+// that automatic refinement flagged (redo); then the FP64 re-solve of the
+// columns the FP32 kernel flagged (list: int32[N] workspace, list_off:
+// int32[2]), then the per-outcome column counts (counts[kAutoSteps + 1], nullable)
 cudaError_t launch_refine_fallback(sam_handle h, const LsqArgs &args, int N, int32_t *list, int32_t *list_off,
-                                   int64_t *counts);
+                                   int64_t *counts, const RedoLists &redo = RedoLists());
 
 // Least-squares launches for every size class.
 cudaError_t launch_lsq(sam_handle h, int precision, const LsqArgs &args);

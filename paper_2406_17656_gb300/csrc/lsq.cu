@@ -68,10 +68,28 @@ __global__ void flag_list_kernel(int N, const int32_t *colstat, int32_t *list, i
 }  // namespace
 
 cudaError_t launch_refine_fallback(sam_handle h, const LsqArgs &args, int N, int32_t *list, int32_t *list_off,
-                                   int64_t *counts) {
+                                   int64_t *counts, const RedoLists &redo) {
     cudaStream_t st = handle_stream(h);
-    cudaError_t e = cudaMemsetAsync(list_off, 0, sizeof(int32_t) * 2, st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if (args.refine_steps < 0) {
+        // automatic refinement: the columns whose first step asked for a
+        // second, solved again from the start with two steps, by their size
+        // classes' kernels (the guard after the second step sends a miss to
+        // the FP64 re-solve below)
+        if (!redo.bin || !redo.bins2 || !redo.work || !redo.bin_off || !redo.ws) return cudaErrorInvalidValue;
+        if ((e = flagged_bins(h, N, redo.bin, args.colstat, kStStep2, redo.bins2)) != cudaSuccess ||
+            (e = build_work_list(h, N, redo.bins2, redo.work, redo.bin_off, redo.ws)) != cudaSuccess)
+            return e;
+        LsqArgs a2 = args;
+        a2.work = redo.work;
+        a2.bin_off = redo.bin_off;
+        a2.item_lo = a2.item_hi = 0;
+        a2.refine_steps = kAutoSteps;
+        // (the large class never flags a column: its kernel takes its own steps)
+        for (int b = 0; b < kBinBig; ++b)
+            if ((e = launch_lsq_bin(h, SAM_FP32_REFINE, a2, b)) != cudaSuccess) return e;
+    }
+    if ((e = cudaMemsetAsync(list_off, 0, sizeof(int32_t) * 2, st)) != cudaSuccess) return e;
     if (N > 0) {
         flag_list_kernel<<<(N + 255) / 256, 256, 0, st>>>(N, args.colstat, list, list_off);
         count_launch(h);

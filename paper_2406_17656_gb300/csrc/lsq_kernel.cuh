@@ -136,17 +136,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
         double r2 = 0.0;
         bool need_final = true;
         bool fallback = false;
+        bool redo = false;  // automatic refinement: solved again with two steps
         if constexpr (!FP64) {
-            // fixed number of steps, or (refine_steps < 0) up to kAutoSteps
-            // with the stopping test below
+            // A fixed number of steps, or (refine_steps < 0, automatic) one
+            // step and the stopping test below.  A column whose test asks
+            // for a second step leaves with status kStStep2, and a launch of
+            // its own solves it again with kAutoSteps steps
+            // (launch_refine_fallback).  Taking the second step in place, in
+            // the warps that hold such a column, was slower by far more than
+            // the step's own work: those warps' code runs apart from the
+            // others' and instruction fetch stalls every warp of the SM
             const bool autoref = args.refine_steps < 0;
-            const int steps = autoref ? kAutoSteps : args.refine_steps;
-            // automatic mode: this column takes the current step.  The loop
-            // is warp-uniform (the passes use shuffles), so a warp runs step
-            // 2 when any of its columns needs it, but a column that stopped
-            // after step 1 discards step 2's correction: its result does not
-            // depend on which columns share its warp
-            bool active = true;
+            const int steps = autoref ? 1 : args.refine_steps;
             for (int step = 0; step < steps; ++step) {
                 // r = c - B m (FP64), g = B^T r (FP64), d = (R^T R)^{-1} g (FP32)
                 residual_rows<TL, false>(S, args.kcv, nI, ll);
@@ -163,11 +164,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
                 for (int q = 0; q < JQ; ++q) {
                     const int c = ll + q * P;
                     if (c < nJ) {
-                        const T xq = active ? x[q] : T(0);
-                        mq[q] += to_f64<T>(xq);
+                        mq[q] += to_f64<T>(x[q]);
                         S.m[c] = mq[q];
-                        S.u.s.y[c] = xq;  // (zero when the step is discarded: the final residual is r itself)
-                        dsq = fmaf(xq, xq, dsq);
+                        S.u.s.y[c] = x[q];
+                        dsq = fmaf(x[q], x[q], dsq);
                     }
                 }
                 __syncwarp();
@@ -201,18 +201,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
                 }
                 __syncwarp();
                 if (C.ll == 0) S.dprev2 = dsq;  // (shared memory: no register across the next step)
-                if (autoref) {
-                    // automatic: a second step when step 1 left the column above
-                    // kAutoTol (kAutoC |d_1|^2 > kAutoTol |m|^2) or predicted above
-                    // the target; after it, a miss falls back to FP64
-                    if (step == 0) {
-                        active = kC * dsq > (float)kAutoTol * msq || miss;
-                        if (!__any_sync(0xffffffffu, active)) break;  // warp-uniform
-                    } else {
-                        fallback = active && miss;
-                    }
-                } else if (step == steps - 1) {
-                    fallback = miss;
+                if (step == steps - 1) {
+                    // automatic: a second step when step 1 left the column
+                    // above kAutoTol (kAutoC |d_1|^2 > kAutoTol |m|^2) or
+                    // predicted above the target; with a fixed number of
+                    // steps, a miss after the last falls back to FP64
+                    if (autoref)
+                        redo = kC * dsq > (float)kAutoTol * msq || miss;
+                    else
+                        fallback = miss;
                 }
             }
             if (steps > 0) {
@@ -261,7 +258,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
             if (C.valid && ll == 0 && args.refine_used)
                 args.refine_used[C.jj] = (uint8_t)((fallback && C.status == kStOk)
                                                        ? kAutoSteps + 1
-                                                       : (autoref ? (active ? 2 : 1) : (steps < 2 ? steps : 2)));
+                                                       : (steps < 2 ? steps : 2));
         }
         if (need_final) {
             r2 = residual_rows<TL>(S, args.kcv, nI, ll);
@@ -278,6 +275,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, MinBlocks<TL>::value) lsq
             int status = C.status;
             if (status == kStOk && (nf || !finite64(r2))) status = kStNonfinite;
             if (status == kStOk && fallback) status = kStRefine;  // re-solved by the FP64 kernel
+            if (status == kStOk && redo) status = kStStep2;       // solved again with two steps
             const int njo = args.jcp[C.js + 1] - C.jb;
 #pragma unroll
             for (int q = 0; q < JQ; ++q) {

@@ -122,3 +122,45 @@ def test_result_does_not_depend_on_column_grouping(sam, handle, steps):
     for k in range(len(aks)):
         _, _, vk = handle.sam_build(aks[k], A0, Ss[k], "fp32r", steps)
         assert torch.equal(vk, v[offs[k]:offs[k + 1]])
+
+
+@pytest.mark.parametrize("plan", [False, True])
+def test_auto_columns_equal_one_or_two_fixed_steps(sam, handle, plan):
+    """In the automatic mode a column that stops after its first step keeps
+    the one-step solution, and a column whose first step asks for a second is
+    solved again with two steps: every column of the automatic build equals,
+    bit for bit, the same column of the one-step or of the two-step build,
+    and the two-step columns are those the outcome counts name."""
+    import torch
+
+    seq = W.config2(nx=40, nmat=3, level=2)
+    a0 = sam.Csr.from_host(seq.mats[0])
+    aks = [sam.Csr.from_host(m) for m in seq.mats]
+    Ss = handle.sam_pattern_build_batched(aks, 2)
+    if plan:
+        p = handle.sam_plan_create(aks, a0, Ss, "fp32r", "auto")
+        p.execute()
+        torch.cuda.synchronize()
+        va, rp, ci = p.M_val.clone(), p.M_row_ptr.clone(), p.M_col_idx.clone()
+        p.destroy()
+    else:
+        _, rp, ci, va, _ = handle.sam_build_batched(aks, a0, Ss, "fp32r", "auto")
+    one, two, fb = handle.sam_refine_stats()
+    assert fb == 0 and two > 0 and one > 0
+    _, _, _, v1, _ = handle.sam_build_batched(aks, a0, Ss, "fp32r", 1)
+    _, _, _, v2, _ = handle.sam_build_batched(aks, a0, Ss, "fp32r", 2)
+    va, v1, v2 = va.cpu().numpy(), v1.cpu().numpy(), v2.cpu().numpy()
+    n = seq.mats[0].n
+    # column of every stored entry (maps stacked: map k's columns are k n + j)
+    ci = ci.cpu().numpy().astype(np.int64)
+    rp = rp.cpu().numpy().astype(np.int64)
+    mapk = np.repeat(np.arange(len(aks)), [int(rp[(k + 1) * (n + 1) - 1]) for k in range(len(aks))])
+    col = mapk * n + ci
+    ncol = len(aks) * n
+    not1 = np.bincount(col, weights=(va != v1), minlength=ncol) > 0
+    not2 = np.bincount(col, weights=(va != v2), minlength=ncol) > 0
+    assert not np.any(not1 & not2)
+    # columns that differ from the one-step build took two steps (a column
+    # whose second step changes nothing counts as two steps but matches both)
+    assert int(np.sum(not1)) <= two
+    assert int(np.sum(not2)) <= one
