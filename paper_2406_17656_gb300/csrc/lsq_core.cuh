@@ -211,31 +211,80 @@ __device__ __forceinline__ int group_excl_scan(int v, int ll, int *total) {
 template <class TL, int PH>
 struct QRPhase {
     using T = typename TL::T;
-    static constexpr int RG = TL::RG, CG = TL::CG, RS = TL::RS, CS = TL::CS, L = TL::L;
+    static constexpr int RG = TL::RG, CG = TL::CG, RS = TL::RS, CS = TL::CS, L = TL::L, P = TL::P;
     static constexpr int K0 = PH * L;
     static constexpr int SK = K0 / RG;  // row slot of this phase's pivots
     static constexpr int TK = K0 / CG;  // column slot of this phase's pivots
     static constexpr int NPH = (TL::MAXJ + L - 1) / L;
+    // every reflector takes the row slots SK..SE-1 (the head); the slots
+    // after it (the tail) only when its row band reaches them
+    static constexpr int SE = SK + (RS + 1) / 2 < RS ? SK + (RS + 1) / 2 : RS;
 
-    static __device__ __forceinline__ void run(T (&a)[RS][CS], int rg, int cg, int gbase, int nJ, int kmax) {
+    // band[k]: the row slot of the last row that holds an entry of columns
+    // 0..k of B (Column::build_rows).  Householder reflectors 0..k leave
+    // every later row as it was (by induction: such a row is zero in
+    // columns 0..k, so reflector k's vector is zero there), so reflector k
+    // acts on the row slots SK..band[k] only.  Rows are in the order of the
+    // source's numbering, where a stencil's or mesh's band keeps most
+    // reflectors inside the head.  The bound is the largest over the warp's
+    // problems: the tail's branches are warp-uniform.
+    static __device__ __forceinline__ void run(T (&a)[RS][CS], int rg, int cg, int gbase, int nJ, int kmax,
+                                               const unsigned char *band) {
         if constexpr (PH < NPH) {
             if (K0 >= kmax) return;
             const int kend = (K0 + L < kmax) ? K0 + L : kmax;
             for (int k = K0; k < kend; ++k) {
                 const int ck = k - TK * CG;  // column group owning column k
                 const int rk = k - SK * RG;  // row group of row k inside slot SK
+                const int own = gbase + ck * RG + rg;  // owner of this lane's rows of column k
                 const bool active = k < nJ;
+                bool tail = false;
+                if constexpr (SE < RS) {
+                    int sh = band[k];
+#pragma unroll
+                    for (int o = P; o < 32; o <<= 1) sh = max(sh, shfl_xor(sh, o));
+                    tail = sh >= SE;
+                }
                 // squared norm of column k below the diagonal (two chains)
                 T sig0 = T(0), sig1 = T(0);
 #pragma unroll
-                for (int s = SK; s < RS; ++s) {
+                for (int s = SK; s < SE; ++s) {
                     T x = a[s][TK];
                     if (s == SK) x = (rg > rk) ? x : T(0);
                     if ((s - SK) & 1) sig1 = fma(x, x, sig1); else sig0 = fma(x, x, sig0);
                 }
+                if (tail) {
+#pragma unroll
+                    for (int s = SE; s < RS; ++s) {
+                        if ((s - SK) & 1) sig1 = fma(a[s][TK], a[s][TK], sig1); else sig0 = fma(a[s][TK], a[s][TK], sig0);
+                    }
+                }
                 T sig = sig0 + sig1;
 #pragma unroll
                 for (int o = 1; o < RG; o <<= 1) sig += shfl_xor(sig, o);
+                // column k of the rows below the pivot slot, from its owners,
+                // and their part of the dot products: independent of the
+                // reflector's norm, so they overlap its reductions and square
+                // root; the pivot slot's part follows once u_k is known
+                T u[SE - SK];
+                T w[CS - TK];
+#pragma unroll
+                for (int t = TK; t < CS; ++t) w[t - TK] = T(0);
+#pragma unroll
+                for (int s = SK + 1; s < SE; ++s) {
+                    const T x = shfl(a[s][TK], own);
+                    u[s - SK] = x;
+#pragma unroll
+                    for (int t = TK; t < CS; ++t) w[t - TK] = fma(x, a[s][t], w[t - TK]);
+                }
+                if (tail) {
+#pragma unroll
+                    for (int s = SE; s < RS; ++s) {
+                        const T x = shfl(a[s][TK], own);
+#pragma unroll
+                        for (int t = TK; t < CS; ++t) w[t - TK] = fma(x, a[s][t], w[t - TK]);
+                    }
+                }
                 const T alpha = shfl(a[SK][TK], gbase + ck * RG + rk);
                 const T sigma = shfl(sig, gbase + ck * RG);
                 // reflector H = I - taup u u^T, u = x with u_k = alpha - beta
@@ -243,27 +292,15 @@ struct QRPhase {
                 const T beta = (sigma == T(0)) ? alpha : ((alpha >= T(0)) ? -nrm : nrm);
                 const T uk = alpha - beta;
                 const T taup = (sigma == T(0) || !active) ? T(0) : refl_neg_rcp(beta * uk);
-                T u[RS - SK];
+                {
+                    T x = shfl(a[SK][TK], own);
+                    x = (rg > rk) ? x : ((rg == rk) ? uk : T(0));
+                    u[0] = x;
 #pragma unroll
-                for (int s = SK; s < RS; ++s) {
-                    T x = shfl(a[s][TK], gbase + ck * RG + rg);
-                    if (s == SK) x = (rg > rk) ? x : ((rg == rk) ? uk : T(0));
-                    u[s - SK] = x;
+                    for (int t = TK; t < CS; ++t) w[t - TK] = fma(x, a[SK][t], w[t - TK]);
                 }
-                // the dot products of all live column slots, then their
                 // reductions interleaved (independent shuffles in flight
-                // together), then the updates; per column the same operations
-                // in the same order as one column slot at a time
-                T w[CS - TK];
-#pragma unroll
-                for (int t = TK; t < CS; ++t) {
-                    T w0 = T(0), w1 = T(0);
-#pragma unroll
-                    for (int s = SK; s < RS; ++s) {
-                        if ((s - SK) & 1) w1 = fma(u[s - SK], a[s][t], w1); else w0 = fma(u[s - SK], a[s][t], w0);
-                    }
-                    w[t - TK] = w0 + w1;
-                }
+                // together), then the updates
 #pragma unroll
                 for (int o = 1; o < RG; o <<= 1)
 #pragma unroll
@@ -271,13 +308,25 @@ struct QRPhase {
 #pragma unroll
                 for (int t = TK; t < CS; ++t) {
                     // columns of slots after TK are all > k (L divides CG)
-                    const T coef = (t > TK || t * CG + cg > k) ? taup * w[t - TK] : T(0);
+                    w[t - TK] = (t > TK || t * CG + cg > k) ? taup * w[t - TK] : T(0);
+                }
 #pragma unroll
-                    for (int s = SK; s < RS; ++s) a[s][t] = fma(-coef, u[s - SK], a[s][t]);
+                for (int s = SK; s < SE; ++s)
+#pragma unroll
+                    for (int t = TK; t < CS; ++t) a[s][t] = fma(-w[t - TK], u[s - SK], a[s][t]);
+                if (tail) {
+                    // (the owners' column k is left as it was by the update:
+                    // its coefficient is zero)
+#pragma unroll
+                    for (int s = SE; s < RS; ++s) {
+                        const T x = shfl(a[s][TK], own);
+#pragma unroll
+                        for (int t = TK; t < CS; ++t) a[s][t] = fma(-w[t - TK], x, a[s][t]);
+                    }
                 }
                 if (active && cg == ck && rg == rk) a[SK][TK] = beta;
             }
-            QRPhase<TL, PH + 1>::run(a, rg, cg, gbase, nJ, kmax);
+            QRPhase<TL, PH + 1>::run(a, rg, cg, gbase, nJ, kmax, band);
         }
     }
 };
@@ -734,14 +783,38 @@ struct Column {
         }
         if (ll == 0) S.u.s.rowstart[nI] = tot;
         __syncwarp();
+        int last[JQ];  // last local row holding an entry of column c
 #pragma unroll
         for (int q = 0; q < JQ; ++q) {
             const int c = ll + q * P;
+            last[q] = -1;
             for (int p = 0; p < clen[q]; ++p) {
                 const int i = S.locr[colB[q] + p];
                 const int pos = S.u.s.rowstart[i] + __popc(S.mask[i] & ((1u << c) - 1u));
                 S.u.s.rowent[pos] = colA[q] + p;
                 S.u.s.rowcol[pos] = (unsigned char)c;
+                last[q] = max(last[q], i);
+            }
+        }
+        if constexpr (!TL::LEAN) {
+            // the QR's row band (QRPhase): the row slot of the last row with
+            // an entry in columns 0..c, at least the slot of row c, as a
+            // prefix maximum over the columns (c = ll + q P); kept in the
+            // bytes of dinv, which the QR does not use before its pivots
+            unsigned char *band = reinterpret_cast<unsigned char *>(S.u.s.dinv);
+            int carry = -1;
+#pragma unroll
+            for (int q = 0; q < JQ; ++q) {
+                const int c = ll + q * P;
+                int v = last[q];
+#pragma unroll
+                for (int o = 1; o < P; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, v, o);
+                    if (ll >= o) v = max(v, y);
+                }
+                v = max(v, carry);
+                carry = __shfl_sync(0xffffffffu, v, (int)(threadIdx.x & 31) | (P - 1));
+                if (c < MAXJ) band[c] = (unsigned char)((c < nJ ? max(v, c) : 0) / RG);
             }
         }
     }
@@ -749,10 +822,11 @@ struct Column {
     // QR of [B c]; R (packed rows), 1/R_kk and Q^T c to shared memory; a zero
     // or non-finite pivot sets the status and clears nJ (no further work)
     __device__ __forceinline__ void factor(ProbSmem<TL> &S, T (&a)[RS][CS]) {
+        __syncwarp();  // the row band (build_rows) is read by every lane of the group
         kmax = nJ;
 #pragma unroll
         for (int o = P; o < 32; o <<= 1) kmax = max(kmax, shfl_xor(kmax, o));
-        QRPhase<TL, 0>::run(a, rg, cg, gbase, nJ, kmax);
+        QRPhase<TL, 0>::run(a, rg, cg, gbase, nJ, kmax, reinterpret_cast<const unsigned char *>(S.u.s.dinv));
 #pragma unroll
         for (int s = 0; s < RS; ++s)
 #pragma unroll
