@@ -49,6 +49,13 @@ struct __align__(16) BigHdr {
     int kcol[kBigJCap];        // structure offset of column c (kcp of the source column)
     int clen[kBigJCap + 1];
     int cb[kBigJCap + 1];      // prefix of clen: gather order of the candidates
+    // the QR's band: rband[k] = 1 + the last row holding an entry of columns
+    // 0..k (at least k + 1), cband[k] = 1 + the last column whose first row
+    // is below rband[k] (at least k + 1); built from each column's last and
+    // first rows
+    short rband[kBigJCap];
+    short cband[kBigJCap];
+    short cfirst[kBigJCap];    // first row of column c, then the suffix minimum
     int I[kBigICap];           // shadow rows, ascending
     double r[kBigICap];        // c, then the residual
     double y[kBigJCap];        // (Q^T c)(1:|J|), in the tile's type
@@ -103,18 +110,20 @@ __device__ __forceinline__ void set_status(BigHdr &H, int st) {
     atomicMax(&H.status, st);
 }
 
-// Reflector k (u_k, tau') applied by one warp to the NQ columns t0, t0 + 16,
-// ... of the tile: each column's dot product summed lane-wise then by a
-// fixed xor tree, as one column at a time would
+// Reflector k (u_k, tau') applied by one warp to the NQ columns tq[] of the
+// tile, rows k..re-1 (the rows after re are zero in column k): each column's
+// dot product summed lane-wise then by a fixed xor tree, as one column at a
+// time would
 template <typename TT, int NQ>
-__device__ __forceinline__ void apply_cols(TT *T, int ld, int nI, int k, int t0, int lane, TT uk, TT taup) {
+__device__ __forceinline__ void apply_cols(TT *T, int ld, int re, int k, const int (&tq)[4], int lane, TT uk,
+                                           TT taup) {
     TT w[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) w[q] = TT(0);
-    for (int i = k + 1 + lane; i < nI; i += 32) {
+    for (int i = k + 1 + lane; i < re; i += 32) {
         const TT v = T[i + ld * k];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) w[q] = fma(v, T[i + ld * (t0 + q * kBigWarps)], w[q]);
+        for (int q = 0; q < NQ; ++q) w[q] = fma(v, T[i + ld * tq[q]], w[q]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
@@ -122,33 +131,28 @@ __device__ __forceinline__ void apply_cols(TT *T, int ld, int nI, int k, int t0,
         for (int q = 0; q < NQ; ++q) w[q] += __shfl_xor_sync(0xffffffffu, w[q], o);
     TT coef[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) coef[q] = taup * fma(uk, T[k + ld * (t0 + q * kBigWarps)], w[q]);
+    for (int q = 0; q < NQ; ++q) coef[q] = taup * fma(uk, T[k + ld * tq[q]], w[q]);
     __syncwarp();
     if (lane == 0) {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int t = t0 + q * kBigWarps;
-            T[k + ld * t] = fma(-coef[q], uk, T[k + ld * t]);
-        }
+        for (int q = 0; q < NQ; ++q) T[k + ld * tq[q]] = fma(-coef[q], uk, T[k + ld * tq[q]]);
     }
-    for (int i = k + 1 + lane; i < nI; i += 32) {
+    for (int i = k + 1 + lane; i < re; i += 32) {
         const TT v = T[i + ld * k];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int t = t0 + q * kBigWarps;
-            T[i + ld * t] = fma(-coef[q], v, T[i + ld * t]);
-        }
+        for (int q = 0; q < NQ; ++q) T[i + ld * tq[q]] = fma(-coef[q], v, T[i + ld * tq[q]]);
     }
 }
 
-// Householder reflector of column k of the tile (rows k..nI-1), by one warp:
-// out = {u_k, tau', beta} with beta = -sign(alpha) ||x||, u_k = alpha - beta
-// and tau' = -1 / (beta u_k) (0 when the column is already zero below the
-// diagonal); the sum of squares lane-wise, then by a fixed xor tree
+// Householder reflector of column k of the tile (rows k..re-1; the rows
+// after re are zero in column k), by one warp: out = {u_k, tau', beta} with
+// beta = -sign(alpha) ||x||, u_k = alpha - beta and tau' = -1 / (beta u_k)
+// (0 when the column is already zero below the diagonal); the sum of
+// squares lane-wise, then by a fixed xor tree
 template <typename TT>
-__device__ __forceinline__ void reflector(const TT *T, int ld, int nI, int k, int lane, TT *out) {
+__device__ __forceinline__ void reflector(const TT *T, int ld, int re, int k, int lane, TT *out) {
     TT s = TT(0);
-    for (int i = k + 1 + lane; i < nI; i += 32) {
+    for (int i = k + 1 + lane; i < re; i += 32) {
         const TT x = T[i + ld * k];
         s = fma(x, x, s);
     }
@@ -369,16 +373,32 @@ __global__ void __launch_bounds__(kBigThreads, BigBlocks<TT>::value) lsq_big_ker
         }
         __syncthreads();
         if (H.status == kStOk) {
-            for (int c = warp; c < nJ; c += kBigWarps)
+            for (int c = warp; c < nJ; c += kBigWarps) {
+                int plo = INT_MAX, phi = -1;  // first and last row of column c
                 for (int e = lane; e < H.clen[c]; e += 32) {
                     const int p = search_rows(H.I, nI, args.kri[H.kcol[c] + e]);
-                    if (p >= 0) T[p + ld * c] = big_value<TT>(args.kcv, args.kcv32, H.colA[c] + e);
-                    else set_status(H, kStUnsupported);  // impossible: every row of B is in I_j
+                    if (p >= 0) {
+                        T[p + ld * c] = big_value<TT>(args.kcv, args.kcv32, H.colA[c] + e);
+                        plo = min(plo, p);
+                        phi = max(phi, p);
+                    } else {
+                        set_status(H, kStUnsupported);  // impossible: every row of B is in I_j
+                    }
                     if (keep_lr) {
                         lr[H.cb[c] + e] = p;
                         bv[H.cb[c] + e] = args.kcv[H.colA[c] + e];
                     }
                 }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    plo = min(plo, __shfl_xor_sync(0xffffffffu, plo, o));
+                    phi = max(phi, __shfl_xor_sync(0xffffffffu, phi, o));
+                }
+                if (lane == 0) {
+                    H.cfirst[c] = (short)min(plo, kBigICap);
+                    H.rband[c] = (short)phi;
+                }
+            }
             if (warp == kBigWarps - 1) {
                 const int zb = args.zcp[zc], ze = args.zcp[zc + 1];
                 double o2 = 0.0;
@@ -397,34 +417,72 @@ __global__ void __launch_bounds__(kBigThreads, BigBlocks<TT>::value) lsq_big_ker
             }
         }
         __syncthreads();
+        // ---- the QR's band.  Rows are in ascending order of the source's
+        // numbering, so B has a staircase profile: Householder reflectors
+        // 0..k leave every row after the last row holding an entry of
+        // columns 0..k as it was (by induction: such a row is zero in those
+        // columns, so the reflectors' vectors are zero there), and a column
+        // whose first row is after that row is zero in all the rows they
+        // touch (its dot products vanish): reflector k acts on rows
+        // k..rband[k]-1 of columns k+1..cband[k]-1 and of c.
+        if (tid == 0 && H.status == kStOk) {
+            int mx = -1;
+            for (int k = 0; k < nJ; ++k) {
+                mx = max(mx, (int)H.rband[k]);
+                H.rband[k] = (short)(max(mx, k) + 1);
+            }
+            int mn = INT_MAX;
+            for (int t = nJ - 1; t >= 0; --t) {
+                mn = min(mn, (int)H.cfirst[t]);
+                H.cfirst[t] = (short)mn;
+            }
+            // the suffix minimum is ascending: the last column with a first
+            // row below the band's end moves forward with k
+            int t = -1;
+            for (int k = 0; k < nJ; ++k) {
+                while (t + 1 < nJ && H.cfirst[t + 1] < H.rband[k]) ++t;
+                H.cband[k] = (short)(max(t, k) + 1);
+            }
+        }
+        __syncthreads();
         // ---- Householder QR of [B c].  Reflector k + 1 is formed by warp 0
         // right after it applied reflector k to column k + 1 (its parameters
         // double-buffered), so each reflector costs one block barrier.
         if (H.status == kStOk) {
             TT *qp = reinterpret_cast<TT *>(&H.qp[0][0]);  // qp[4 b + q], b = reflector parity
-            if (warp == 0) reflector<TT>(T, ld, nI, 0, lane, qp);
+            if (warp == 0) reflector<TT>(T, ld, H.rband[0], 0, lane, qp);
             __syncthreads();
             for (int k = 0; k < nJ; ++k) {
                 const TT *qk = qp + 4 * (k & 1);
                 const TT uk = qk[0], taup = qk[1];
+                const int re = H.rband[k];
                 if (taup != TT(0)) {
-                    // FP32: a warp's columns t, t + 16, t + 32, t + 48 at once
-                    // (independent dot products and updates; the FP64 pipe
-                    // gains nothing from it and pays for idle slots)
+                    // the band's columns after k, then c: nv columns, v = 0
+                    // being column k + 1 (or c).  FP32: a warp's columns v,
+                    // v + 16, v + 32, v + 48 at once (independent dot products
+                    // and updates; the FP64 pipe gains nothing from it and
+                    // pays for idle slots)
                     constexpr int G = F32 ? 4 : 1;
-                    for (int t0 = k + 1 + warp; t0 <= nJ; t0 += G * kBigWarps) {
-                        const int nq = min(G, (nJ - t0) / kBigWarps + 1);
-                        if (nq >= 4) apply_cols<TT, 4>(T, ld, nI, k, t0, lane, uk, taup);
-                        else if (nq == 3) apply_cols<TT, 3>(T, ld, nI, k, t0, lane, uk, taup);
-                        else if (nq == 2) apply_cols<TT, 2>(T, ld, nI, k, t0, lane, uk, taup);
-                        else apply_cols<TT, 1>(T, ld, nI, k, t0, lane, uk, taup);
-                        if (t0 == k + 1 && t0 < nJ) {  // warp 0: column k + 1 is final below row k
+                    const int nb = H.cband[k] - (k + 1), nv = nb + 1;
+                    for (int v0 = warp; v0 < nv; v0 += G * kBigWarps) {
+                        const int nq = min(G, (nv - 1 - v0) / kBigWarps + 1);
+                        int tq[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int v = v0 + q * kBigWarps;
+                            tq[q] = v < nb ? k + 1 + v : nJ;
+                        }
+                        if (nq >= 4) apply_cols<TT, 4>(T, ld, re, k, tq, lane, uk, taup);
+                        else if (nq == 3) apply_cols<TT, 3>(T, ld, re, k, tq, lane, uk, taup);
+                        else if (nq == 2) apply_cols<TT, 2>(T, ld, re, k, tq, lane, uk, taup);
+                        else apply_cols<TT, 1>(T, ld, re, k, tq, lane, uk, taup);
+                        if (v0 == 0 && k + 1 < nJ) {  // warp 0: column k + 1 is final below row k
                             __syncwarp();
-                            reflector<TT>(T, ld, nI, t0, lane, qp + 4 * (t0 & 1));
+                            reflector<TT>(T, ld, H.rband[k + 1], k + 1, lane, qp + 4 * ((k + 1) & 1));
                         }
                     }
                 } else if (warp == 0 && k + 1 < nJ) {
-                    reflector<TT>(T, ld, nI, k + 1, lane, qp + 4 * ((k + 1) & 1));
+                    reflector<TT>(T, ld, H.rband[k + 1], k + 1, lane, qp + 4 * ((k + 1) & 1));
                 }
                 if (tid == 0) T[k + ld * k] = qk[2];
                 __syncthreads();
