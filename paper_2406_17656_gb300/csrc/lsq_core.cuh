@@ -16,13 +16,21 @@ namespace {
 
 constexpr int kWarpsPerBlock = 4;
 constexpr int kGatherRegs = 12;  // entries per source column gathered with one round of loads
-constexpr int kRowRegs = 8;      // entries per row of B loaded with one round in the residual passes
+constexpr int kRowRegs = 10;     // entries per row of B loaded with one round in the residual passes
+constexpr int kColRegs = 10;     // entries per column of B loaded with one round in the B^T v passes
 
 // LEAN_: the shape of an adjoint that reads R from a factor tape: no
 // register tile and no staging buffer for it (more problems per SM).
-template <int RG_, int CG_, int RS_, int CS_, typename T_, int MAXI_BIN_, bool LEAN_ = false>
+// BAND_: the QR keeps to the row band of each reflector (QRPhase); on for the
+// size classes of 2-D level-2 columns, whose band spans a third to a half of
+// the rows (measured: the class-3 launch of the 10-map Q1 level-2 build 7%
+// faster), off where the band spans nearly every row and its branches only
+// cost (level-1 columns of classes 0-1, 3-D level-2 columns of class 4:
+// measured about 5% slower with it).
+template <int RG_, int CG_, int RS_, int CS_, typename T_, int MAXI_BIN_, bool LEAN_ = false, bool BAND_ = false>
 struct Tile {
     static constexpr bool LEAN = LEAN_;
+    static constexpr bool BAND = BAND_ && !LEAN_;
     static constexpr int RG = RG_, CG = CG_, RS = RS_, CS = CS_;
     static constexpr int P = RG * CG;    // lanes per column problem
     static constexpr int PPW = 32 / P;   // problems per warp
@@ -218,7 +226,7 @@ struct QRPhase {
     static constexpr int NPH = (TL::MAXJ + L - 1) / L;
     // every reflector takes the row slots SK..SE-1 (the head); the slots
     // after it (the tail) only when its row band reaches them
-    static constexpr int SE = SK + (RS + 1) / 2 < RS ? SK + (RS + 1) / 2 : RS;
+    static constexpr int SE = TL::BAND && SK + (RS + 1) / 2 < RS ? SK + (RS + 1) / 2 : RS;
 
     // band[k]: the row slot of the last row that holds an entry of columns
     // 0..k of B (Column::build_rows).  Householder reflectors 0..k leave
@@ -433,20 +441,20 @@ __device__ __forceinline__ double residual_rows(ProbSmem<TL> &S, const double *k
 // FP32 tiles per size class (bins: |I| <= 14/26/40/52/64, |J| <= 5/9/23/27/27)
 using F0 = Tile<2, 2, 7, 3, float, 14>;
 using F1 = Tile<2, 2, 13, 5, float, 26>;
-using F2 = Tile<4, 4, 10, 6, float, 40>;
-using F3 = Tile<4, 4, 13, 7, float, 52>;
+using F2 = Tile<4, 4, 10, 6, float, 40, false, true>;
+using F3 = Tile<4, 4, 13, 7, float, 52, false, true>;
 using F4 = Tile<4, 4, 16, 7, float, 64>;
 // FP64 tiles
 using D0 = Tile<2, 2, 7, 3, double, 14>;
 using D1 = Tile<2, 4, 13, 3, double, 26>;
-using D2 = Tile<4, 8, 10, 3, double, 40>;
-using D3 = Tile<4, 8, 13, 4, double, 52>;
+using D2 = Tile<4, 8, 10, 3, double, 40, false, true>;
+using D3 = Tile<4, 8, 13, 4, double, 52, false, true>;
 using D4 = Tile<4, 8, 16, 4, double, 64>;
 
 // alternative shapes for the autotuner: one problem per 8 or 32 lanes
 using F1b = Tile<2, 4, 13, 3, float, 26>;
-using F2b = Tile<4, 8, 10, 3, float, 40>;
-using F3b = Tile<4, 8, 13, 4, float, 52>;
+using F2b = Tile<4, 8, 10, 3, float, 40, false, true>;
+using F3b = Tile<4, 8, 13, 4, float, 52, false, true>;
 using F4b = Tile<4, 8, 16, 4, float, 64>;
 // the adjoint's shapes when R comes from a factor tape (size classes 2-4;
 // the two smallest recompute their small QR)
@@ -567,10 +575,12 @@ struct Column {
 
     // the entries of the lane's columns c in [c_lo, c_hi): local rows, row
     // masks and (TILE) the values at column c - c_lo of the staging tile
-    template <bool TILE>
-    __device__ __forceinline__ void gather_entries(const LsqArgs &args, ProbSmem<TL> &S, int c_lo, int c_hi) {
+    // (compile-time bounds: a column slot q outside them costs nothing)
+    template <bool TILE, int c_lo, int c_hi>
+    __device__ __forceinline__ void gather_entries(const LsqArgs &args, ProbSmem<TL> &S) {
 #pragma unroll
         for (int q = 0; q < JQ; ++q) {
+            if (q * P + P <= c_lo || q * P >= c_hi) continue;
             const int c = ll + q * P;
             const int len = (c >= c_lo && c < c_hi) ? clen[q] : 0;
             const int cs = c - c_lo;
@@ -648,7 +658,7 @@ struct Column {
     __device__ __forceinline__ void gather_sparse(const LsqArgs &args, ProbSmem<TL> &S) {
         gather_begin(args, S);
         __syncwarp();
-        gather_entries<false>(args, S, 0, NCOL);
+        gather_entries<false, 0, NCOL>(args, S);
         gather_target<false>(args, S, 0);
         __syncwarp();
     }
@@ -662,14 +672,14 @@ struct Column {
         gather_begin(args, S);
         zero_stage(S);
         __syncwarp();
-        gather_entries<true>(args, S, 0, NST);
+        gather_entries<true, 0, NST>(args, S);
         if constexpr (CSH == CS) gather_target<true>(args, S, 0);
         __syncwarp();
         load_slots<0>(S, a);
         if constexpr (CSH < CS) {
             zero_stage(S);
             __syncwarp();
-            gather_entries<true>(args, S, NST, NCOL);
+            gather_entries<true, NST, NCOL>(args, S);
             gather_target<true>(args, S, NST);
             __syncwarp();
             load_slots<1>(S, a);
@@ -796,7 +806,7 @@ struct Column {
                 last[q] = max(last[q], i);
             }
         }
-        if constexpr (!TL::LEAN) {
+        if constexpr (TL::BAND) {
             // the QR's row band (QRPhase): the row slot of the last row with
             // an entry in columns 0..c, at least the slot of row c, as a
             // prefix maximum over the columns (c = ll + q P); kept in the
@@ -950,13 +960,13 @@ struct Column {
         constexpr int JG = JQ < 2 ? JQ : 2;
 #pragma unroll
         for (int q0 = 0; q0 < JQ; q0 += JG) {
-            double bv[JG][kGatherRegs];
+            double bv[JG][kColRegs];
 #pragma unroll
             for (int g = 0; g < JG; ++g) {
                 const int q = q0 + g < JQ ? q0 + g : JQ - 1;
                 const int len = q0 + g < JQ ? clen[q] : 0;
 #pragma unroll
-                for (int u = 0; u < kGatherRegs; ++u) bv[g][u] = (u < len) ? args.kcv[colA[q] + u] : 0.0;
+                for (int u = 0; u < kColRegs; ++u) bv[g][u] = (u < len) ? args.kcv[colA[q] + u] : 0.0;
             }
 #pragma unroll
             for (int g = 0; g < JG; ++g) {
@@ -964,9 +974,9 @@ struct Column {
                     const int q = q0 + g, len = clen[q];
                     double acc = 0.0;
 #pragma unroll
-                    for (int u = 0; u < kGatherRegs; ++u)
+                    for (int u = 0; u < kColRegs; ++u)
                         if (u < len) acc = fma(bv[g][u], v[S.locr[colB[q] + u]], acc);
-                    for (int p = kGatherRegs; p < len; ++p) acc = fma(args.kcv[colA[q] + p], v[S.locr[colB[q] + p]], acc);
+                    for (int p = kColRegs; p < len; ++p) acc = fma(args.kcv[colA[q] + p], v[S.locr[colB[q] + p]], acc);
                     out[q] = acc;
                 }
             }
@@ -977,13 +987,13 @@ struct Column {
     __device__ __forceinline__ double bt_times(const LsqArgs &args, ProbSmem<TL> &S, const double *v, int q) {
         double acc = 0.0;
         const int len = clen[q];
-        double bv[kGatherRegs];
+        double bv[kColRegs];
 #pragma unroll
-        for (int u = 0; u < kGatherRegs; ++u) bv[u] = (u < len) ? args.kcv[colA[q] + u] : 0.0;
+        for (int u = 0; u < kColRegs; ++u) bv[u] = (u < len) ? args.kcv[colA[q] + u] : 0.0;
 #pragma unroll
-        for (int u = 0; u < kGatherRegs; ++u)
+        for (int u = 0; u < kColRegs; ++u)
             if (u < len) acc = fma(bv[u], v[S.locr[colB[q] + u]], acc);
-        for (int p = kGatherRegs; p < len; ++p) acc = fma(args.kcv[colA[q] + p], v[S.locr[colB[q] + p]], acc);
+        for (int p = kColRegs; p < len; ++p) acc = fma(args.kcv[colA[q] + p], v[S.locr[colB[q] + p]], acc);
         return acc;
     }
 };
