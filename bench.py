@@ -285,21 +285,31 @@ def measured_hbm_gbs() -> float:
         return 6800.0
 
 
+def _code_only(src: bytes) -> bytes:
+    """C++ source without its comments and blank lines (string literals kept)."""
+    import re
+
+    pat = re.compile(rb'"(?:\\.|[^"\\\n])*"|//[^\n]*|/\*.*?\*/', re.S)
+    out = pat.sub(lambda m: m.group(0) if m.group(0).startswith(b'"') else b"", src)
+    return b"\n".join(line.rstrip() for line in out.split(b"\n") if line.strip())
+
+
 def kernel_hash() -> str:
-    """sha256 over the sources the least-squares kernel is compiled from: its
+    """sha256 over the code the least-squares kernel is compiled from: its
     kernel header, its translation unit, the shared column routines and the
     device part of common.cuh (constants, LsqArgs, device helpers; the
-    host-side declarations after them do not enter the kernel).  A recorded
-    ncu traffic figure is only reported while these are unchanged."""
+    host-side declarations after them do not enter the kernel), comments and
+    blank lines left out.  A recorded ncu traffic figure is only reported
+    while this code is unchanged."""
     import hashlib
 
     csrc = os.path.join(HERE, "paper_2406_17656_gb300", "csrc")
     h = hashlib.sha256()
     for f in ("lsq_kernel.cuh", "lsq.cu", "lsq_core.cuh"):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        h.update(_code_only(open(os.path.join(csrc, f), "rb").read()))
     common = open(os.path.join(csrc, "common.cuh"), "rb").read()
     cut = common.find(b"// ------------------------------------------------------- host-side helpers")
-    h.update(common if cut < 0 else common[:cut])
+    h.update(_code_only(common if cut < 0 else common[:cut]))
     return h.hexdigest()
 
 

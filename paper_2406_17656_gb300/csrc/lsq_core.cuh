@@ -225,7 +225,8 @@ struct QRPhase {
     static constexpr int TK = K0 / CG;  // column slot of this phase's pivots
     static constexpr int NPH = (TL::MAXJ + L - 1) / L;
     // every reflector takes the row slots SK..SE-1 (the head); the slots
-    // after it (the tail) only when its row band reaches them
+    // after it (the tail) only when its row band reaches them (tiles
+    // without BAND: the head is every slot, and no band is read)
     static constexpr int SE = TL::BAND && SK + (RS + 1) / 2 < RS ? SK + (RS + 1) / 2 : RS;
 
     // band[k]: the row slot of the last row that holds an entry of columns

@@ -29,6 +29,10 @@
 // The k loop is split into phases of L = min(RG, CG) steps; within a phase
 // the first live row slot and column slot are compile-time constants, so
 // register slots holding only finished rows/columns drop out of the code.
+// Rows follow the source's numbering, so B has a staircase profile: in the
+// size classes of 2-D level-2 columns each reflector takes a fixed head of
+// row slots and the rest only when the rows holding entries of columns
+// 0..k reach them (QRPhase).
 // The right-hand side is the last column, so Q^T c falls out of the sweep.
 // Triangular solves with R run in registers (unknown c on lane c % P) with
 // one shuffle per step; R sits in shared memory, packed by rows.
