@@ -81,3 +81,13 @@ def test_adjoint_flops_with_a_factor_tape_drop_only_the_qr():
         f32t, f64t = bench.adjoint_algorithmic_flops(I, J, nB, steps, tape=True)
         assert np.allclose(f32r - f32t, qr)
         assert np.array_equal(f64r, f64t)
+
+
+def test_kernel_hash_covers_code_not_comments():
+    """The recorded ncu traffic is tied to the kernel's code: comments and
+    blank lines do not change the hash, code and string literals do."""
+    src = b'int a; // note\n/* block\n   comment */\nconst char *s = "x // kept";\n\n  int b;  \n'
+    assert bench._code_only(src) == b'int a;\nconst char *s = "x // kept";\n  int b;'
+    assert bench._code_only(src.replace(b"note", b"other note")) == bench._code_only(src)
+    assert bench._code_only(src.replace(b"int b", b"int c")) != bench._code_only(src)
+    assert len(bench.kernel_hash()) == 64
